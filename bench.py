@@ -1,0 +1,322 @@
+"""Benchmark of the fused coupled LB step on GB300 (one JSON line on rank 0).
+
+Workload: the 512 x 512 sessile-droplet freezing case (Sec. 4.3 shape:
+droplet R = 100 on a cold solid layer, seeded contact angle and Stefan
+number), all three lattices, FP32 populations.  One bench step is one full
+time step of the hot path (rows a1-a9, including the fused FP64
+diagnostics) over the whole grid.  The FP32 working set (~70 MB) fits in the
+129 MB L2, so the L2 is flushed (a 256 MB write) before every timed step and
+each step is timed alone with CUDA events on the launching stream: the
+number is the HBM-bound one.  Under torchrun every rank advances its own
+replica (weak scaling, no collective on the data path).
+
+``--impl reference`` times the FP64 CPU oracle on the same workload instead
+(a bounded sample of steps per bench step), on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import ctypes
+import hashlib
+import json
+import os
+import re
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "coupled MLUPS (512^2 droplet, FP32 populations)"
+WORKLOAD = "sessile droplet freezing 512x512 (R=100, cold solid layer), 3 lattices, seed 0"
+L2_FLUSH_BYTES = 256 << 20
+
+
+def algorithmic_bytes_per_node(esize: int, has_mask: bool) -> int:
+    """27 populations read and written, 6 lag fields read and written, phi0
+    read, mask byte read."""
+    return 2 * 27 * esize + 2 * 6 * esize + esize + (1 if has_mask else 0)
+
+
+def measured_peak():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    for f in sorted(os.listdir(os.path.join(ROOT, "paper_2510_18688_gb300", "csrc"))):
+        with open(os.path.join(ROOT, "paper_2510_18688_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic():
+    """DRAM bytes per launch of the step kernel from the committed ncu
+    summary, if it was taken on the current kernel source."""
+    path = os.path.join(ROOT, "profiles", "lbm_step_f32_droplet512.md")
+    if not os.path.exists(path):
+        return None
+    txt = open(path).read()
+    m = re.search(r"kernel source hash:\s*([0-9a-f]+)", txt)
+    t = re.search(r"dram bytes per launch:\s*([0-9.eE+]+)", txt)
+    if not m or not t or m.group(1) != kernel_source_hash():
+        return None
+    return float(t.group(1))
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    def __init__(self, index: int):
+        self.index = index
+        self.samples = []
+        self._stop = threading.Event()
+        self._proc = None
+
+    def __enter__(self):
+        q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+             "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+             "clocks_event_reasons.sw_power_cap")
+        try:
+            self._proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={q}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self._t = threading.Thread(target=self._read, daemon=True)
+            self._t.start()
+        except (FileNotFoundError, OSError):
+            self._proc = None
+        return self
+
+    def _read(self):
+        for line in self._proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 7:
+                self.samples.append(parts)
+
+    def __exit__(self, *exc):
+        if self._proc:
+            self._proc.terminate()
+            try:
+                self._proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self._proc.kill()
+
+    def summary(self):
+        if not self.samples:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(s[0]) for s in self.samples if s[0].replace(".", "").isdigit()]
+        mx = [float(s[1]) for s in self.samples if s[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for s in self.samples for k in range(4)
+                          if s[3 + k].lower() == "active"})
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(self.samples)}
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def reference_arm(args, rank, world):
+    """The FP64 CPU oracle timed on the host cores (a bounded sample)."""
+    if rank != 0:
+        return
+    from oracle import oracle as O
+    from paper_2510_18688_gb300 import workloads as W
+    wl = W.sessile_droplet(512, seed=0)
+    o = O.from_workload(wl)
+    cores = O.set_threads(0)
+    n = wl[0]["nx"] * wl[0]["ny"]
+    for _ in range(args.warmup):
+        o.step(1)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        o.step(1)
+    dt = time.perf_counter() - t0
+    mlups = n * args.steps / dt / 1e6
+    line = {
+        "impl": "reference", "metric": METRIC, "value": mlups, "unit": "MLUPS",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "grid": [512, 512], "l2": "n/a (CPU)"},
+        "cpu_baseline": {"value": mlups, "unit": "MLUPS", "cores": cores, "kind": "oracle",
+                         "sample": f"{args.steps} full time steps of the 512x512 workload"},
+        "e2e": {"value": mlups, "unit": "MLUPS", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def cpu_baseline_sample(target_s: float = 12.0):
+    """Time the oracle on the same workload for about target_s seconds."""
+    from oracle import oracle as O
+    from paper_2510_18688_gb300 import workloads as W
+    wl = W.sessile_droplet(512, seed=0)
+    o = O.from_workload(wl)
+    cores = O.set_threads(0)
+    n = wl[0]["nx"] * wl[0]["ny"]
+    t0 = time.perf_counter()
+    o.step(1)
+    one = time.perf_counter() - t0
+    k = max(2, min(200, int(target_s / max(one, 1e-3))))
+    t0 = time.perf_counter()
+    o.step(k)
+    dt = time.perf_counter() - t0
+    return {"value": n * k / dt / 1e6, "unit": "MLUPS", "cores": cores, "kind": "oracle",
+            "sample": f"{k} time steps of the 512x512 droplet workload (FP64 oracle)"}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    rank, world, local = dist_env()
+
+    if args.impl == "reference":
+        reference_arm(args, rank, world)
+        return
+
+    import torch
+    torch.cuda.set_device(local)
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+        pg = dist
+    from paper_2510_18688_gb300 import build, lbm, workloads as W
+    build.build()
+    L = lbm.load()
+
+    cfg, arr = W.sessile_droplet(512, seed=rank)
+    n = cfg["nx"] * cfg["ny"]
+    stream = torch.cuda.current_stream()
+    sptr = ctypes.c_void_p(stream.cuda_stream)
+    solver = lbm.Solver(cfg, precision=args.precision, diag_every=1).set_geometry(arr)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+
+    for _ in range(args.warmup):
+        flush.zero_()
+        lbm.lbm_step(solver.ctx, 1, sptr)
+    torch.cuda.synchronize()
+
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    if pg:
+        pg.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        wall0 = time.perf_counter()
+        for k in range(args.steps):
+            flush.zero_()
+            starts[k].record(stream)
+            lbm.lbm_step(solver.ctx, 1, sptr)
+            ends[k].record(stream)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - wall0
+    if pg:
+        pg.barrier()
+    times = np.array([s.elapsed_time(e) for s, e in zip(starts, ends)])  # ms
+    t_step = float(times.mean())
+    t_tot = float(times.sum())
+    if pg:
+        t = torch.tensor([t_tot], device="cuda")
+        pg.all_reduce(t, op=pg.ReduceOp.MAX)
+        t_tot = float(t.item())
+    diag = solver.diagnostics(compute=False)
+
+    # end to end through the C ABI with host buffers: geometry upload,
+    # the same K steps, fields (phi, fl, T) read back to host memory
+    e2e = None
+    def pinned(a, dtype):
+        t = torch.empty(a.shape, dtype=dtype, pin_memory=True)
+        t.numpy()[...] = a
+        return t
+
+    host_t = {k: pinned(arr[k], torch.float64) for k in ("phi0", "phi", "T", "fl")}
+    host = {k: v.numpy() for k, v in host_t.items()}
+    hmask_t = pinned(arr["mask"], torch.uint8)
+    hmask = hmask_t.numpy()
+    outs_t = {k: torch.empty((cfg["ny"], cfg["nx"]), dtype=torch.float64, pin_memory=True)
+              for k in ("phi", "fl", "T")}
+    outs = {k: v.numpy() for k, v in outs_t.items()}
+    ptrs = [outs[k].ctypes.data if k in outs else None for k in lbm.FIELDS]
+    fmask = lbm.FIELD_BIT["phi"] | lbm.FIELD_BIT["fl"] | lbm.FIELD_BIT["T"]
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    lbm.lbm_set_geometry(solver.ctx, host["phi0"].ctypes.data, hmask.ctypes.data,
+                         host["phi"].ctypes.data, host["T"].ctypes.data, host["fl"].ctypes.data,
+                         lbm.LBM_HOST, sptr)
+    lbm.lbm_step(solver.ctx, args.steps, sptr)
+    lbm.lbm_read_fields(solver.ctx, fmask, ptrs, lbm.LBM_HOST, sptr)
+    e2e_s = time.perf_counter() - t0
+    h2d = 4 * n * 8 + n
+    d2h = 3 * n * 8
+    e2e = {"value": n * args.steps / e2e_s / 1e6, "unit": "MLUPS",
+           "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": d2h / args.steps,
+           "note": "one job per measurement: host geometry upload, K steps, phi/fl/T download"}
+
+    # steady state with the grid resident in L2 (context only, not the value)
+    g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    g0.record(stream)
+    lbm.lbm_step(solver.ctx, args.steps, sptr)
+    g1.record(stream)
+    torch.cuda.synchronize()
+    l2_ms = g0.elapsed_time(g1) / args.steps
+
+    if rank != 0:
+        if pg:
+            pg.destroy_process_group()
+        return
+    esize = 4 if args.precision == "fp32" else 8
+    bpn = algorithmic_bytes_per_node(esize, True)
+    peak, peak_src = measured_peak()
+    achieved = bpn * n / (t_step * 1e-3) / 1e9
+    value = world * n * args.steps / (t_tot * 1e-3) / 1e6
+    line = {
+        "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_step,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32" if esize == 4 else "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "grid": [512, 512], "precision": args.precision,
+                   "l2": "flushed before every timed step (256 MB write)",
+                   "parallelism": f"replicas x{world}"},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": profiled_traffic(),
+                     "peak_source": peak_src, "bytes_per_node": bpn},
+        "gpu_launches": args.steps,
+        "e2e": e2e,
+        "l2_resident_mlups": n / (l2_ms * 1e-3) / 1e6,
+        "diag_last": {k: diag[k] for k in ("material_mass", "frozen_volume", "nonfinite", "step")},
+        "clocks": clk.summary(),
+        "wall_s_timed_region": wall,
+    }
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline_sample()
+    print(json.dumps(line), flush=True)
+    if pg:
+        pg.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,193 @@
+/*
+ * lbm.h -- C ABI of the GB300 (sm_103a) implementation of the coupled
+ * three-lattice lattice Boltzmann (LB) time step for three-phase freezing of
+ * Huang, Zhan, Chai & Huang, arXiv 2510.18688 ("A diffuse-interface method
+ * for the containerless freezing of three-phase flows in complex
+ * geometries").
+ *
+ * One context owns the device state of one 2-D D2Q9 grid: the flow
+ * populations f (Sec. 3.1, Eqs. (11)-(17)), the phase-field populations g
+ * (Sec. 3.2, Eqs. (18)-(22)), the total-enthalpy populations h (Sec. 3.3,
+ * Eqs. (23)-(28)), the lagged fields one step needs (liquid fraction,
+ * material weight, pressure, phi*u, enthalpy source) and the static solid
+ * field phi0 (Sec. 2) with an optional cold mask.  Lattice units:
+ * dx = dt = 1, cs^2 = 1/3, melting temperature T_m = 0.
+ *
+ * Conventions for every call:
+ *   - Return value is an lbm_status; no call aborts or throws across the
+ *     ABI.  lbm_last_error() describes the most recent failure of a context.
+ *   - Grid arrays are row-major [ny][nx] with x fastest, no padding.
+ *   - `where` is LBM_HOST (plain host memory, pinned or pageable) or
+ *     LBM_DEVICE (device memory of the current CUDA device, for example
+ *     torch.Tensor.data_ptr()).  Caller buffers stay owned by the caller and
+ *     are only accessed during the call (device inputs until the call's work
+ *     on `stream` completes).
+ *   - `stream` is a cudaStream_t (NULL = legacy default stream).  lbm_step
+ *     and lbm_compute_diagnostics only enqueue work; lbm_set_geometry with
+ *     host inputs, lbm_read_fields with host outputs, lbm_read_diagnostics
+ *     and the state calls synchronise the stream they use.
+ *   - A context is not thread-safe; use one context per host thread.
+ */
+#ifndef LBM_GB300_H
+#define LBM_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lbm_ctx lbm_ctx;
+
+typedef enum {
+  LBM_OK = 0,
+  LBM_ERR_ARG = -1,         /* null pointer, bad size or bad enum value      */
+  LBM_ERR_PARAM = -2,       /* physically invalid parameter (tau <= 1/2 ...)  */
+  LBM_ERR_CUDA = -3,        /* a CUDA runtime call failed                     */
+  LBM_ERR_OOM = -4,         /* device or pinned host allocation failed        */
+  LBM_ERR_NONFINITE = -5,   /* diagnostics found non-finite populations       */
+  LBM_ERR_UNSUPPORTED = -6, /* valid request this build does not implement    */
+  LBM_ERR_STATE = -8        /* call out of order (e.g. step before geometry)  */
+} lbm_status;
+
+typedef enum { LBM_FP64 = 0, LBM_FP32 = 1 } lbm_precision;
+
+enum { LBM_BC_PERIODIC = 0, LBM_BC_DIRICHLET = 1, LBM_BC_ADIABATIC = 2 };
+enum { LBM_LAT_FLOW = 1, LBM_LAT_PHASE = 2, LBM_LAT_HEAT = 4 };
+enum { LBM_HOST = 0, LBM_DEVICE = 1 };
+
+/* Field selection for lbm_read_fields (bit k selects out[k]). */
+enum {
+  LBM_F_PHI = 1u << 0,  /* order parameter phi, Eq. (22)                    */
+  LBM_F_FS = 1u << 1,   /* solid fraction (pre-existing solid + ice)       */
+  LBM_F_FL = 1u << 2,   /* liquid fraction of the material, Eq. (8)       */
+  LBM_F_T = 1u << 3,    /* temperature, Eq. (8)                            */
+  LBM_F_RHOH = 1u << 4, /* total enthalpy rho H, Eq. (28)                  */
+  LBM_F_P = 1u << 5,    /* pressure, Eq. (17c)                             */
+  LBM_F_UX = 1u << 6,   /* velocity x, Eq. (17b)                           */
+  LBM_F_UY = 1u << 7,   /* velocity y, Eq. (17b)                           */
+  LBM_F_RHO = 1u << 8,  /* density, Eq. (10)                               */
+  LBM_F_MU = 1u << 9,   /* chemical potential mu_phi, Eq. (6)              */
+  LBM_F_W = 1u << 10,   /* material (liquid-side) weight (1 - phi0 + phi)/2 */
+  LBM_F_MDOT = 1u << 11 /* mass source (1 - rho_s/rho_l) dfs/dt, Eq. (1)   */
+};
+#define LBM_NUM_FIELDS 12
+
+/* Problem statement (Secs. 2-4).  Densities, viscosities (dynamic),
+ * conductivities and specific heats are given per phase: liquid l, solid s
+ * (ice and the pre-existing solid Omega_0), gas g; each property is
+ * interpolated by Eq. (10).  latent = L with Ste = Cp_l (T_m - T_w) / L,
+ * Eq. (29).  rho_ref multiplies Cp_ref = 2 Cp_s Cp_l / (Cp_s + Cp_l) in the
+ * enthalpy equilibrium Eq. (25) and in Eq. (26).  sigma, eps: surface
+ * tension and interface width of Eq. (4); mobility = M of Eq. (21) with the
+ * factor eta; theta_deg: contact angle on Omega_0, psi_deg: angle on the ice
+ * (Eq. (4)).  (gx, gy): body force G = rho g.  T_cold: temperature imposed on
+ * cold-mask nodes.  bc[k] for x-low, x-high, y-low, y-high; T_wall[k] used
+ * where bc[k] == LBM_BC_DIRICHLET.  readings: bit 0 selects the variant of
+ * the modified force that adds cs^2 S I to u Ft + Ft u in Eq. (16).
+ * diag_every = k > 0 makes every k-th step also reduce the diagnostics of
+ * its input state (0: only on request). */
+typedef struct {
+  int32_t nx, ny;
+  int32_t precision; /* lbm_precision */
+  uint32_t lattices; /* LBM_LAT_* bits */
+  int32_t bc[4];
+  double T_wall[4];
+  double rho_l, rho_s, rho_g;
+  double mu_l, mu_s, mu_g;
+  double lambda_l, lambda_s, lambda_g;
+  double cp_l, cp_s, cp_g;
+  double rho_ref, latent;
+  double sigma, eps, mobility, eta;
+  double theta_deg, psi_deg;
+  double gx, gy;
+  double T_cold;
+  uint32_t readings;
+  int32_t diag_every;
+} lbm_params;
+
+/* Global FP64 sums over the grid of one state (row a9 of the hot path). */
+typedef struct {
+  double mass;            /* sum rho                                        */
+  double material_mass;   /* sum w (rho_s (1 - fl) + rho_l fl)              */
+  double rhoH;            /* sum rho H                                      */
+  double liquid_volume;   /* sum w fl                                       */
+  double material_volume; /* sum w                                          */
+  double frozen_volume;   /* sum w (1 - fl)                                 */
+  double phi_sum;         /* sum phi                                        */
+  double kinetic;         /* sum rho |u|^2 / 2                              */
+  double nonfinite;       /* nodes whose population sums are not finite     */
+  int64_t step;           /* index of the state these sums describe        */
+} lbm_diag;
+
+/* Validates *params, derives the relaxation times (Sec. 3: tau_f = nu/cs^2
+ * + 1/2 per node, tau_g from Eq. (21), tau_a from Eq. (26), tau_s from
+ * Eq. (27)) and allocates the device state on the current CUDA device.
+ * Errors: LBM_ERR_ARG (null, grid < 2, unpaired periodic axis),
+ * LBM_ERR_PARAM (non-positive property, relaxation time <= 1/2 for any
+ * phase), LBM_ERR_OOM, LBM_ERR_CUDA.  On success *out owns the memory until
+ * lbm_destroy. */
+int lbm_create(const lbm_params* params, lbm_ctx** out);
+
+/* Sets the static solid field phi0 (1 in Omega_0, 0 in the fluid), the
+ * optional cold mask (nonzero = enthalpy reset to T_cold each step; may be
+ * NULL) and the initial phi, T and fl, then builds the initial populations:
+ * f at rest (p = 0, u = 0), g = g_eq(phi, mu_phi, u = 0) (Eq. (19)),
+ * h = h_eq(rho H, T, u = 0) (Eq. (25)); lag fields fl, w from the inputs,
+ * p = phi u = Q = 0.  All five arrays are [ny][nx] doubles (mask: bytes) in
+ * `where` memory.  Resets the step counter.  Synchronises `stream` when
+ * where == LBM_HOST. */
+int lbm_set_geometry(lbm_ctx* ctx, const double* phi0, const uint8_t* cold_mask,
+                     const double* phi, const double* T, const double* fl, int where,
+                     void* stream);
+
+/* Enqueues nsteps >= 0 fused time steps on `stream` (rows a1-a9: enthalpy
+ * inversion, order parameter and properties, finite-difference stencils and
+ * chemical potential, velocity and pressure, three collisions, streaming
+ * with wall conditions and cold mask, lag store; diagnostics every
+ * diag_every steps).  Asynchronous.  Errors: LBM_ERR_STATE before
+ * lbm_set_geometry, LBM_ERR_ARG for nsteps < 0, LBM_ERR_CUDA on launch
+ * failure. */
+int lbm_step(lbm_ctx* ctx, int64_t nsteps, void* stream);
+
+/* Writes the fields selected by field_mask for the current state (the
+ * values the next step would compute in rows a1-a4), as [ny][nx] doubles,
+ * into out[k] for every selected bit k (out[k] may be NULL otherwise).
+ * where = LBM_HOST copies through a context-owned device staging buffer and
+ * synchronises `stream`. */
+int lbm_read_fields(lbm_ctx* ctx, uint32_t field_mask, double* const* out, int where,
+                    void* stream);
+
+/* Enqueues the diagnostic reduction of the current state (no time step). */
+int lbm_compute_diagnostics(lbm_ctx* ctx, void* stream);
+
+/* Synchronises the context's last stream and copies the most recent
+ * diagnostics into *out.  Returns LBM_ERR_NONFINITE (with *out filled) when
+ * any node's populations were not finite, LBM_ERR_STATE if no diagnostics
+ * were ever computed. */
+int lbm_read_diagnostics(lbm_ctx* ctx, lbm_diag* out);
+
+/* Bytes of a checkpoint (populations, lag fields, step counter, header). */
+int lbm_state_size(const lbm_ctx* ctx, size_t* bytes);
+
+/* Copies the current state into host_buf (capacity >= lbm_state_size).
+ * Synchronises `stream`.  Restoring it with lbm_load_state into a context
+ * with the same parameters and geometry reproduces later steps bit for bit. */
+int lbm_save_state(lbm_ctx* ctx, void* host_buf, size_t capacity, void* stream);
+int lbm_load_state(lbm_ctx* ctx, const void* host_buf, size_t size, void* stream);
+
+/* Number of time steps taken since lbm_set_geometry (or restored). */
+int64_t lbm_step_count(const lbm_ctx* ctx);
+
+const char* lbm_last_error(const lbm_ctx* ctx);
+const char* lbm_status_string(int status);
+
+/* Frees the context and all memory it owns (NULL is allowed). */
+void lbm_destroy(lbm_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LBM_GB300_H */

@@ -1,0 +1,482 @@
+// lbm_api.cu -- host implementation of the C ABI declared in include/lbm.h.
+//
+// The context owns every device buffer of one grid: two population buffers
+// (27 planes each, A/B), two lag-field buffers (6 planes each), the static
+// phi0 plane and the cold-mask byte plane, the diagnostic partial sums and
+// result, and staging buffers for host transfers.  All work is enqueued on
+// the caller's stream; nothing here computes physics on the host beyond the
+// derived constants of the parameter set.
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+
+#include <cuda_runtime.h>
+
+#include "../../include/lbm.h"
+#include "lbm_launch.h"
+
+using lbmk::Args;
+using lbmk::Coef;
+using lbmk::Geom;
+using lbmk::InitArgs;
+
+struct lbm_ctx {
+  lbm_params p;
+  Geom g;
+  Coef<float> cf;
+  Coef<double> cd;
+  size_t esize;          // bytes per real
+  void* pop[2];
+  void* lag[2];
+  void* phi0;
+  uint8_t* mask;
+  double* diag_partial;
+  double* diag_out;      // NDIAG + 1
+  unsigned* counter;
+  double* staging;       // NFIELD * nx * ny doubles, for host reads (lazy)
+  void* in_stage;        // 4 * nx * ny doubles + nx * ny bytes, for host inputs (lazy)
+  double* h_diag;        // pinned, NDIAG + 1
+  int cur;
+  int64_t step;
+  bool have_geometry;
+  bool have_diag;
+  cudaStream_t last_stream;
+  int nblocks;
+  char err[512];
+};
+
+namespace {
+
+const uint32_t kMagic = 0x4c424d46u;  // "LBMF"
+const uint32_t kVersion = 1u;
+
+struct StateHeader {
+  uint32_t magic, version;
+  int32_t nx, ny, precision, lattices;
+  int64_t step;
+};
+
+int fail(lbm_ctx* c, int code, const char* fmt, const char* detail = "") {
+  if (c) std::snprintf(c->err, sizeof(c->err), fmt, detail);
+  return code;
+}
+
+int cuda_fail(lbm_ctx* c, cudaError_t e, const char* what) {
+  if (c) std::snprintf(c->err, sizeof(c->err), "%s: %s", what, cudaGetErrorString(e));
+  return e == cudaErrorMemoryAllocation ? LBM_ERR_OOM : LBM_ERR_CUDA;
+}
+
+bool positive(double v) { return std::isfinite(v) && v > 0.0; }
+
+template <typename R>
+Coef<R> make_coef(const lbm_params& p) {
+  Coef<R> c;
+  const double pi = 3.14159265358979323846;
+  c.rho_l = (R)p.rho_l; c.rho_s = (R)p.rho_s; c.rho_g = (R)p.rho_g;
+  c.mu_l = (R)p.mu_l; c.mu_s = (R)p.mu_s; c.mu_g = (R)p.mu_g;
+  c.lam_l = (R)p.lambda_l; c.lam_s = (R)p.lambda_s; c.lam_g = (R)p.lambda_g;
+  c.cp_l = (R)p.cp_l; c.cp_s = (R)p.cp_s; c.cp_g = (R)p.cp_g;
+  // Cp_ref = 2 Cp_s Cp_l / (Cp_s + Cp_l) (Sec. 3.3)
+  c.rr = (R)(p.rho_ref * (2.0 * p.cp_s * p.cp_l / (p.cp_s + p.cp_l)));
+  c.latent = (R)p.latent;
+  c.sigma = (R)p.sigma;
+  c.eps = (R)p.eps;
+  c.eta = (R)p.eta;
+  c.cos_th = (R)std::cos(p.theta_deg * pi / 180.0);
+  c.cos_ps = (R)std::cos(p.psi_deg * pi / 180.0);
+  c.gx = (R)p.gx;
+  c.gy = (R)p.gy;
+  c.tau_g = (R)(0.5 + p.mobility / (p.eta / 3.0));  // Eq. (21)
+  c.T_cold = (R)p.T_cold;
+  c.one_m_ratio = (R)(1.0 - p.rho_s / p.rho_l);
+  for (int k = 0; k < 4; k++) c.T_wall[k] = (R)p.T_wall[k];
+  c.readings = p.readings;
+  return c;
+}
+
+int validate(const lbm_params* p, char* err, size_t n) {
+  if (!p) return LBM_ERR_ARG;
+  if (p->nx < 2 || p->ny < 2) {
+    std::snprintf(err, n, "grid must be at least 2 x 2 (got %d x %d)", p->nx, p->ny);
+    return LBM_ERR_ARG;
+  }
+  if ((long long)p->nx * p->ny > (1LL << 31) / 27) {
+    std::snprintf(err, n, "grid of %d x %d nodes is too large", p->nx, p->ny);
+    return LBM_ERR_ARG;
+  }
+  if (p->precision != LBM_FP32 && p->precision != LBM_FP64) {
+    std::snprintf(err, n, "unknown precision %d", p->precision);
+    return LBM_ERR_ARG;
+  }
+  if (p->lattices == 0 || (p->lattices & ~7u)) {
+    std::snprintf(err, n, "lattices must be a nonzero subset of flow|phase|heat (got %u)",
+                  p->lattices);
+    return LBM_ERR_ARG;
+  }
+  for (int k = 0; k < 4; k++) {
+    if (p->bc[k] < LBM_BC_PERIODIC || p->bc[k] > LBM_BC_ADIABATIC) {
+      std::snprintf(err, n, "unknown boundary type %d on side %d", p->bc[k], k);
+      return LBM_ERR_ARG;
+    }
+  }
+  if ((p->bc[0] == LBM_BC_PERIODIC) != (p->bc[1] == LBM_BC_PERIODIC) ||
+      (p->bc[2] == LBM_BC_PERIODIC) != (p->bc[3] == LBM_BC_PERIODIC)) {
+    std::snprintf(err, n, "a periodic side needs a periodic opposite side");
+    return LBM_ERR_ARG;
+  }
+  if (p->diag_every < 0) {
+    std::snprintf(err, n, "diag_every must be >= 0");
+    return LBM_ERR_ARG;
+  }
+  const double props[] = {p->rho_l, p->rho_s,    p->rho_g,    p->mu_l,     p->mu_s,
+                          p->mu_g,  p->lambda_l, p->lambda_s, p->lambda_g, p->cp_l,
+                          p->cp_s,  p->cp_g,     p->rho_ref,  p->eps,      p->mobility,
+                          p->eta};
+  for (double v : props) {
+    // every relaxation time of Sec. 3 is 1/2 plus a positive property ratio,
+    // so positivity of the properties is what keeps tau > 1/2
+    if (!positive(v)) {
+      std::snprintf(err, n, "densities, viscosities, conductivities, heat capacities, "
+                            "rho_ref, eps, mobility and eta must be positive and finite");
+      return LBM_ERR_PARAM;
+    }
+  }
+  if (!(std::isfinite(p->latent) && p->latent >= 0.0) ||
+      !(std::isfinite(p->sigma) && p->sigma >= 0.0)) {
+    std::snprintf(err, n, "latent heat and surface tension must be finite and >= 0");
+    return LBM_ERR_PARAM;
+  }
+  return LBM_OK;
+}
+
+template <typename R>
+Args<R> step_args(lbm_ctx* c, const Coef<R>& coef) {
+  Args<R> a;
+  std::memset(&a, 0, sizeof(a));
+  a.g = c->g;
+  a.c = coef;
+  a.pin = (const R*)c->pop[c->cur];
+  a.pout = (R*)c->pop[c->cur ^ 1];
+  a.lin = (const R*)c->lag[c->cur];
+  a.lout = (R*)c->lag[c->cur ^ 1];
+  a.phi0 = (const R*)c->phi0;
+  a.mask = c->mask;
+  a.diag_partial = c->diag_partial;
+  a.diag_out = c->diag_out;
+  a.diag_counter = c->counter;
+  a.step_index = c->step;
+  return a;
+}
+
+cudaError_t launch(lbm_ctx* c, int mode, bool diag, double* const* outs, cudaStream_t s) {
+  if (c->p.precision == LBM_FP32) {
+    Args<float> a = step_args<float>(c, c->cf);
+    if (outs)
+      for (int k = 0; k < lbmk::NFIELD; k++) a.out[k] = outs[k];
+    return lbmk::launch_step_f32(a, mode, diag, s);
+  }
+  Args<double> a = step_args<double>(c, c->cd);
+  if (outs)
+    for (int k = 0; k < lbmk::NFIELD; k++) a.out[k] = outs[k];
+  return lbmk::launch_step_f64(a, mode, diag, s);
+}
+
+void free_all(lbm_ctx* c) {
+  void* dev[] = {c->pop[0], c->pop[1], c->lag[0],     c->lag[1],    c->phi0,   c->mask,
+                 c->diag_partial, c->diag_out, c->counter, c->staging, c->in_stage};
+  for (void* p : dev)
+    if (p) cudaFree(p);
+  if (c->h_diag) cudaFreeHost(c->h_diag);
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* lbm_status_string(int status) {
+  switch (status) {
+    case LBM_OK: return "ok";
+    case LBM_ERR_ARG: return "invalid argument";
+    case LBM_ERR_PARAM: return "invalid physical parameter";
+    case LBM_ERR_CUDA: return "CUDA error";
+    case LBM_ERR_OOM: return "out of memory";
+    case LBM_ERR_NONFINITE: return "non-finite state";
+    case LBM_ERR_UNSUPPORTED: return "unsupported";
+    case LBM_ERR_STATE: return "call out of order";
+    default: return "unknown status";
+  }
+}
+
+const char* lbm_last_error(const lbm_ctx* c) { return c ? c->err : "null context"; }
+
+int64_t lbm_step_count(const lbm_ctx* c) { return c ? c->step : -1; }
+
+int lbm_create(const lbm_params* params, lbm_ctx** out) {
+  if (!params || !out) return LBM_ERR_ARG;
+  *out = nullptr;
+  char err[512] = {0};
+  int st = validate(params, err, sizeof(err));
+  if (st != LBM_OK) {
+    std::fprintf(stderr, "lbm_create: %s\n", err);
+    return st;
+  }
+  lbm_ctx* c = new (std::nothrow) lbm_ctx();
+  if (!c) return LBM_ERR_OOM;
+  std::memset(c, 0, sizeof(*c));
+  c->p = *params;
+  c->esize = params->precision == LBM_FP32 ? sizeof(float) : sizeof(double);
+  c->g.nx = params->nx;
+  c->g.ny = params->ny;
+  c->g.pitch = (params->nx + 31) / 32 * 32;
+  long long plane = (long long)c->g.pitch * params->ny;
+  c->g.plane = (plane + 63) / 64 * 64;
+  c->g.lattices = (int)params->lattices;
+  for (int k = 0; k < 4; k++) c->g.bc[k] = params->bc[k];
+  c->g.has_mask = 0;
+  c->cf = make_coef<float>(*params);
+  c->cd = make_coef<double>(*params);
+  const dim3 gd = lbmk::grid_dims(c->g);
+  c->nblocks = (int)(gd.x * gd.y);
+  const size_t P = (size_t)c->g.plane;
+  cudaError_t e = cudaSuccess;
+  for (int b = 0; b < 2 && e == cudaSuccess; b++) {
+    e = cudaMalloc(&c->pop[b], 27 * P * c->esize);
+    if (e == cudaSuccess) e = cudaMalloc(&c->lag[b], lbmk::NLAG * P * c->esize);
+  }
+  if (e == cudaSuccess) e = cudaMalloc(&c->phi0, P * c->esize);
+  if (e == cudaSuccess) e = cudaMalloc(&c->mask, P);
+  if (e == cudaSuccess)
+    e = cudaMalloc(&c->diag_partial, (size_t)lbmk::NDIAG * c->nblocks * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&c->diag_out, (lbmk::NDIAG + 1) * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&c->counter, sizeof(unsigned));
+  if (e == cudaSuccess) e = cudaMemset(c->counter, 0, sizeof(unsigned));
+  if (e == cudaSuccess) e = cudaMemset(c->mask, 0, P);
+  if (e == cudaSuccess) e = cudaHostAlloc(&c->h_diag, (lbmk::NDIAG + 1) * sizeof(double), 0);
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) {
+    int code = cuda_fail(c, e, "lbm_create allocation");
+    std::fprintf(stderr, "lbm_create: %s\n", c->err);
+    free_all(c);
+    delete c;
+    return code;
+  }
+  *out = c;
+  return LBM_OK;
+}
+
+void lbm_destroy(lbm_ctx* c) {
+  if (!c) return;
+  free_all(c);
+  delete c;
+}
+
+int lbm_set_geometry(lbm_ctx* c, const double* phi0, const uint8_t* cold_mask,
+                     const double* phi, const double* T, const double* fl, int where,
+                     void* stream) {
+  if (!c) return LBM_ERR_ARG;
+  if (!phi0 || !phi || !T || !fl) return fail(c, LBM_ERR_ARG, "null input array%s");
+  if (where != LBM_HOST && where != LBM_DEVICE) return fail(c, LBM_ERR_ARG, "bad `where`%s");
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t N = (size_t)c->g.nx * c->g.ny;
+  const double* d_phi0 = phi0;
+  const double* d_phi = phi;
+  const double* d_T = T;
+  const double* d_fl = fl;
+  const uint8_t* d_mask = cold_mask;
+  cudaError_t e;
+  if (where == LBM_HOST) {
+    if (!c->in_stage) {
+      e = cudaMalloc(&c->in_stage, 4 * N * sizeof(double) + N);
+      if (e != cudaSuccess) return cuda_fail(c, e, "input staging allocation");
+    }
+    double* base = (double*)c->in_stage;
+    const double* src[4] = {phi0, phi, T, fl};
+    for (int k = 0; k < 4; k++) {
+      e = cudaMemcpyAsync(base + k * N, src[k], N * sizeof(double), cudaMemcpyHostToDevice, s);
+      if (e != cudaSuccess) return cuda_fail(c, e, "input upload");
+    }
+    d_phi0 = base;
+    d_phi = base + N;
+    d_T = base + 2 * N;
+    d_fl = base + 3 * N;
+    if (cold_mask) {
+      uint8_t* mb = (uint8_t*)(base + 4 * N);
+      e = cudaMemcpyAsync(mb, cold_mask, N, cudaMemcpyHostToDevice, s);
+      if (e != cudaSuccess) return cuda_fail(c, e, "mask upload");
+      d_mask = mb;
+    }
+  }
+  c->g.has_mask = cold_mask ? 1 : 0;
+  c->cur = 0;
+  if (c->p.precision == LBM_FP32) {
+    InitArgs<float> a;
+    std::memset(&a, 0, sizeof(a));
+    a.g = c->g; a.c = c->cf;
+    a.pout = (float*)c->pop[0]; a.lout = (float*)c->lag[0]; a.phi0_out = (float*)c->phi0;
+    a.mask_out = c->mask; a.phi0 = d_phi0; a.mask = d_mask; a.phi = d_phi; a.T = d_T; a.fl = d_fl;
+    e = lbmk::launch_init_f32(a, s);
+  } else {
+    InitArgs<double> a;
+    std::memset(&a, 0, sizeof(a));
+    a.g = c->g; a.c = c->cd;
+    a.pout = (double*)c->pop[0]; a.lout = (double*)c->lag[0]; a.phi0_out = (double*)c->phi0;
+    a.mask_out = c->mask; a.phi0 = d_phi0; a.mask = d_mask; a.phi = d_phi; a.T = d_T; a.fl = d_fl;
+    e = lbmk::launch_init_f64(a, s);
+  }
+  if (e != cudaSuccess) return cuda_fail(c, e, "init kernel launch");
+  if (where == LBM_HOST) {
+    e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(c, e, "set_geometry synchronisation");
+  }
+  c->step = 0;
+  c->have_geometry = true;
+  c->have_diag = false;
+  c->last_stream = s;
+  return LBM_OK;
+}
+
+int lbm_step(lbm_ctx* c, int64_t nsteps, void* stream) {
+  if (!c) return LBM_ERR_ARG;
+  if (nsteps < 0) return fail(c, LBM_ERR_ARG, "nsteps must be >= 0%s");
+  if (!c->have_geometry) return fail(c, LBM_ERR_STATE, "lbm_step before lbm_set_geometry%s");
+  cudaStream_t s = (cudaStream_t)stream;
+  for (int64_t k = 0; k < nsteps; k++) {
+    const bool diag = c->p.diag_every > 0 && (c->step % c->p.diag_every) == 0;
+    cudaError_t e = launch(c, lbmk::MODE_STEP, diag, nullptr, s);
+    if (e != cudaSuccess) return cuda_fail(c, e, "step kernel launch");
+    if (diag) c->have_diag = true;
+    c->cur ^= 1;
+    c->step++;
+  }
+  c->last_stream = s;
+  return LBM_OK;
+}
+
+int lbm_read_fields(lbm_ctx* c, uint32_t field_mask, double* const* out, int where,
+                    void* stream) {
+  if (!c) return LBM_ERR_ARG;
+  if (!out) return fail(c, LBM_ERR_ARG, "null output table%s");
+  if (where != LBM_HOST && where != LBM_DEVICE) return fail(c, LBM_ERR_ARG, "bad `where`%s");
+  if (field_mask >> lbmk::NFIELD) return fail(c, LBM_ERR_ARG, "unknown field bits%s");
+  if (!c->have_geometry) return fail(c, LBM_ERR_STATE, "read before lbm_set_geometry%s");
+  for (int k = 0; k < lbmk::NFIELD; k++)
+    if ((field_mask >> k & 1u) && !out[k]) return fail(c, LBM_ERR_ARG, "selected field has null output%s");
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t N = (size_t)c->g.nx * c->g.ny;
+  double* outs[lbmk::NFIELD] = {nullptr};
+  cudaError_t e;
+  if (where == LBM_HOST) {
+    if (!c->staging) {
+      e = cudaMalloc(&c->staging, lbmk::NFIELD * N * sizeof(double));
+      if (e != cudaSuccess) return cuda_fail(c, e, "read-out staging allocation");
+    }
+    for (int k = 0; k < lbmk::NFIELD; k++)
+      if (field_mask >> k & 1u) outs[k] = c->staging + k * N;
+  } else {
+    for (int k = 0; k < lbmk::NFIELD; k++)
+      if (field_mask >> k & 1u) outs[k] = out[k];
+  }
+  e = launch(c, lbmk::MODE_READ, false, outs, s);
+  if (e != cudaSuccess) return cuda_fail(c, e, "read-out kernel launch");
+  if (where == LBM_HOST) {
+    for (int k = 0; k < lbmk::NFIELD; k++) {
+      if (!(field_mask >> k & 1u)) continue;
+      e = cudaMemcpyAsync(out[k], outs[k], N * sizeof(double), cudaMemcpyDeviceToHost, s);
+      if (e != cudaSuccess) return cuda_fail(c, e, "field download");
+    }
+    e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(c, e, "read_fields synchronisation");
+  }
+  c->last_stream = s;
+  return LBM_OK;
+}
+
+int lbm_compute_diagnostics(lbm_ctx* c, void* stream) {
+  if (!c) return LBM_ERR_ARG;
+  if (!c->have_geometry) return fail(c, LBM_ERR_STATE, "diagnostics before lbm_set_geometry%s");
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaError_t e = launch(c, lbmk::MODE_READ, true, nullptr, s);
+  if (e != cudaSuccess) return cuda_fail(c, e, "diagnostics kernel launch");
+  c->have_diag = true;
+  c->last_stream = s;
+  return LBM_OK;
+}
+
+int lbm_read_diagnostics(lbm_ctx* c, lbm_diag* out) {
+  if (!c || !out) return LBM_ERR_ARG;
+  if (!c->have_diag) return fail(c, LBM_ERR_STATE, "no diagnostics computed yet%s");
+  cudaError_t e = cudaMemcpyAsync(c->h_diag, c->diag_out, (lbmk::NDIAG + 1) * sizeof(double),
+                                  cudaMemcpyDeviceToHost, c->last_stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->last_stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "diagnostics download");
+  const double* d = c->h_diag;
+  out->mass = d[0];
+  out->material_mass = d[1];
+  out->rhoH = d[2];
+  out->liquid_volume = d[3];
+  out->material_volume = d[4];
+  out->frozen_volume = d[5];
+  out->phi_sum = d[6];
+  out->kinetic = d[7];
+  out->nonfinite = d[8];
+  out->step = (int64_t)d[9];
+  if (d[8] != 0.0) return fail(c, LBM_ERR_NONFINITE, "non-finite populations in the state%s");
+  return LBM_OK;
+}
+
+int lbm_state_size(const lbm_ctx* c, size_t* bytes) {
+  if (!c || !bytes) return LBM_ERR_ARG;
+  *bytes = sizeof(StateHeader) + (27 + lbmk::NLAG) * (size_t)c->g.plane * c->esize;
+  return LBM_OK;
+}
+
+int lbm_save_state(lbm_ctx* c, void* host_buf, size_t capacity, void* stream) {
+  if (!c || !host_buf) return LBM_ERR_ARG;
+  if (!c->have_geometry) return fail(c, LBM_ERR_STATE, "save before lbm_set_geometry%s");
+  size_t need;
+  lbm_state_size(c, &need);
+  if (capacity < need) return fail(c, LBM_ERR_ARG, "state buffer too small%s");
+  cudaStream_t s = (cudaStream_t)stream;
+  StateHeader h = {kMagic, kVersion, c->g.nx, c->g.ny, c->p.precision, (int32_t)c->p.lattices,
+                   c->step};
+  std::memcpy(host_buf, &h, sizeof(h));
+  char* dst = (char*)host_buf + sizeof(h);
+  const size_t pb = 27 * (size_t)c->g.plane * c->esize;
+  cudaError_t e = cudaMemcpyAsync(dst, c->pop[c->cur], pb, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(dst + pb, c->lag[c->cur], lbmk::NLAG * (size_t)c->g.plane * c->esize,
+                        cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_fail(c, e, "state download");
+  return LBM_OK;
+}
+
+int lbm_load_state(lbm_ctx* c, const void* host_buf, size_t size, void* stream) {
+  if (!c || !host_buf) return LBM_ERR_ARG;
+  if (!c->have_geometry) return fail(c, LBM_ERR_STATE, "load before lbm_set_geometry%s");
+  size_t need;
+  lbm_state_size(c, &need);
+  if (size < need) return fail(c, LBM_ERR_ARG, "state buffer too small%s");
+  StateHeader h;
+  std::memcpy(&h, host_buf, sizeof(h));
+  if (h.magic != kMagic || h.version != kVersion || h.nx != c->g.nx || h.ny != c->g.ny ||
+      h.precision != c->p.precision || h.lattices != (int32_t)c->p.lattices)
+    return fail(c, LBM_ERR_ARG, "state does not match this context%s");
+  cudaStream_t s = (cudaStream_t)stream;
+  const char* src = (const char*)host_buf + sizeof(h);
+  const size_t pb = 27 * (size_t)c->g.plane * c->esize;
+  cudaError_t e = cudaMemcpyAsync(c->pop[c->cur], src, pb, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(c->lag[c->cur], src + pb, lbmk::NLAG * (size_t)c->g.plane * c->esize,
+                        cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_fail(c, e, "state upload");
+  c->step = h.step;
+  c->have_diag = false;
+  c->last_stream = s;
+  return LBM_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,22 @@
+// lbm_launch.h -- host-side launchers of the sm_103a kernels (internal to
+// the library; the public interface is include/lbm.h).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "lbm_kernels.cuh"
+
+namespace lbmk {
+
+inline dim3 block_dims() { return dim3(TX, TY, 1); }
+inline dim3 grid_dims(const Geom& g) {
+  return dim3((unsigned)((g.nx + TX - 1) / TX), (unsigned)((g.ny + TY - 1) / TY), 1);
+}
+
+// MODE_STEP or MODE_READ, with or without the fused diagnostics.
+cudaError_t launch_step_f32(const Args<float>& a, int mode, bool diag, cudaStream_t s);
+cudaError_t launch_step_f64(const Args<double>& a, int mode, bool diag, cudaStream_t s);
+cudaError_t launch_init_f32(const InitArgs<float>& a, cudaStream_t s);
+cudaError_t launch_init_f64(const InitArgs<double>& a, cudaStream_t s);
+
+}  // namespace lbmk

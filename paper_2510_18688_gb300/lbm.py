@@ -1,0 +1,283 @@
+"""Python binding of the C ABI in ``include/lbm.h`` (argument marshalling only).
+
+Every computation happens in ``_lib/liblbm_gb300.so`` (sm_103a kernels).  The
+functions below keep the C names; ``Solver`` wraps one context with PyTorch
+tensors for device memory and PyTorch's current CUDA stream.  There is no CPU
+path: loading fails loudly when the library is missing.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "liblbm_gb300.so")
+
+LBM_OK, LBM_ERR_NONFINITE = 0, -5
+LBM_FP64, LBM_FP32 = 0, 1
+LBM_HOST, LBM_DEVICE = 0, 1
+BC = {"periodic": 0, "dirichlet": 1, "adiabatic": 2}
+FIELDS = ("phi", "fs", "fl", "T", "rhoH", "p", "ux", "uy", "rho", "mu", "w", "mdot")
+FIELD_BIT = {k: 1 << i for i, k in enumerate(FIELDS)}
+
+
+class LbmParams(ctypes.Structure):
+    _fields_ = [
+        ("nx", ctypes.c_int32), ("ny", ctypes.c_int32),
+        ("precision", ctypes.c_int32), ("lattices", ctypes.c_uint32),
+        ("bc", ctypes.c_int32 * 4), ("T_wall", ctypes.c_double * 4),
+        ("rho_l", ctypes.c_double), ("rho_s", ctypes.c_double), ("rho_g", ctypes.c_double),
+        ("mu_l", ctypes.c_double), ("mu_s", ctypes.c_double), ("mu_g", ctypes.c_double),
+        ("lambda_l", ctypes.c_double), ("lambda_s", ctypes.c_double),
+        ("lambda_g", ctypes.c_double),
+        ("cp_l", ctypes.c_double), ("cp_s", ctypes.c_double), ("cp_g", ctypes.c_double),
+        ("rho_ref", ctypes.c_double), ("latent", ctypes.c_double),
+        ("sigma", ctypes.c_double), ("eps", ctypes.c_double),
+        ("mobility", ctypes.c_double), ("eta", ctypes.c_double),
+        ("theta_deg", ctypes.c_double), ("psi_deg", ctypes.c_double),
+        ("gx", ctypes.c_double), ("gy", ctypes.c_double),
+        ("T_cold", ctypes.c_double),
+        ("readings", ctypes.c_uint32),
+        ("diag_every", ctypes.c_int32),
+    ]
+
+
+class LbmDiag(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_double) for k in (
+        "mass", "material_mass", "rhoH", "liquid_volume", "material_volume",
+        "frozen_volume", "phi_sum", "kinetic", "nonfinite")] + [("step", ctypes.c_int64)]
+
+
+EXPORTS = ("lbm_create", "lbm_set_geometry", "lbm_step", "lbm_read_fields",
+           "lbm_compute_diagnostics", "lbm_read_diagnostics", "lbm_state_size",
+           "lbm_save_state", "lbm_load_state", "lbm_step_count", "lbm_last_error",
+           "lbm_status_string", "lbm_destroy")
+
+_lib = None
+
+
+def load(path: str = LIB_PATH) -> ctypes.CDLL:
+    """Load the CUDA library (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is missing: build it with paper_2510_18688_gb300/build.py "
+                           "(there is no CPU fallback)")
+    L = ctypes.CDLL(path)
+    vp, dp = ctypes.c_void_p, ctypes.POINTER(ctypes.c_double)
+    L.lbm_create.argtypes = [ctypes.POINTER(LbmParams), ctypes.POINTER(vp)]
+    L.lbm_set_geometry.argtypes = [vp, vp, vp, vp, vp, vp, ctypes.c_int, vp]
+    L.lbm_step.argtypes = [vp, ctypes.c_int64, vp]
+    L.lbm_read_fields.argtypes = [vp, ctypes.c_uint32, ctypes.POINTER(vp), ctypes.c_int, vp]
+    L.lbm_compute_diagnostics.argtypes = [vp, vp]
+    L.lbm_read_diagnostics.argtypes = [vp, ctypes.POINTER(LbmDiag)]
+    L.lbm_state_size.argtypes = [vp, ctypes.POINTER(ctypes.c_size_t)]
+    L.lbm_save_state.argtypes = [vp, vp, ctypes.c_size_t, vp]
+    L.lbm_load_state.argtypes = [vp, vp, ctypes.c_size_t, vp]
+    L.lbm_step_count.argtypes = [vp]
+    L.lbm_step_count.restype = ctypes.c_int64
+    L.lbm_last_error.argtypes = [vp]
+    L.lbm_last_error.restype = ctypes.c_char_p
+    L.lbm_status_string.argtypes = [ctypes.c_int]
+    L.lbm_status_string.restype = ctypes.c_char_p
+    L.lbm_destroy.argtypes = [vp]
+    L.lbm_destroy.restype = None
+    for fn in ("lbm_create", "lbm_set_geometry", "lbm_step", "lbm_read_fields",
+               "lbm_compute_diagnostics", "lbm_read_diagnostics", "lbm_state_size",
+               "lbm_save_state", "lbm_load_state"):
+        getattr(L, fn).restype = ctypes.c_int
+    _lib = L
+    return L
+
+
+class LbmError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{msg} (status {status})")
+        self.status = status
+
+
+def make_params(cfg: dict, precision: str = "fp32", diag_every: int = 0) -> LbmParams:
+    p = LbmParams()
+    p.nx, p.ny = int(cfg["nx"]), int(cfg["ny"])
+    p.precision = LBM_FP32 if precision == "fp32" else LBM_FP64
+    p.lattices = int(cfg["lattices"])
+    for k in range(4):
+        p.bc[k] = BC[cfg["bc"][k]]
+        p.T_wall[k] = float(cfg["T_wall"][k])
+    for name in ("rho_l", "rho_s", "rho_g", "mu_l", "mu_s", "mu_g", "lambda_l", "lambda_s",
+                 "lambda_g", "cp_l", "cp_s", "cp_g", "rho_ref", "latent", "sigma", "eps",
+                 "mobility", "eta", "theta_deg", "psi_deg", "gx", "gy", "T_cold"):
+        setattr(p, name, float(cfg[name]))
+    p.readings = int(cfg.get("readings", 0))
+    p.diag_every = int(diag_every)
+    return p
+
+
+# --- the C entry points, same names ------------------------------------------
+
+def _check(ctx, st, what):
+    if st != LBM_OK:
+        msg = load().lbm_last_error(ctx).decode() if ctx else ""
+        raise LbmError(st, f"{what}: {load().lbm_status_string(st).decode()} {msg}")
+
+
+def lbm_create(params: LbmParams) -> ctypes.c_void_p:
+    h = ctypes.c_void_p()
+    _check(None, load().lbm_create(ctypes.byref(params), ctypes.byref(h)), "lbm_create")
+    return h
+
+
+def lbm_set_geometry(ctx, phi0, cold_mask, phi, T, fl, where, stream=None):
+    _check(ctx, load().lbm_set_geometry(ctx, phi0, cold_mask, phi, T, fl, where, stream),
+           "lbm_set_geometry")
+
+
+def lbm_step(ctx, nsteps: int, stream=None):
+    _check(ctx, load().lbm_step(ctx, int(nsteps), stream), "lbm_step")
+
+
+def lbm_read_fields(ctx, field_mask: int, out_ptrs, where, stream=None):
+    arr = (ctypes.c_void_p * len(FIELDS))(*[p or None for p in out_ptrs])
+    _check(ctx, load().lbm_read_fields(ctx, field_mask, arr, where, stream), "lbm_read_fields")
+
+
+def lbm_compute_diagnostics(ctx, stream=None):
+    _check(ctx, load().lbm_compute_diagnostics(ctx, stream), "lbm_compute_diagnostics")
+
+
+def lbm_read_diagnostics(ctx) -> dict:
+    d = LbmDiag()
+    st = load().lbm_read_diagnostics(ctx, ctypes.byref(d))
+    if st not in (LBM_OK, LBM_ERR_NONFINITE):
+        _check(ctx, st, "lbm_read_diagnostics")
+    return {k: getattr(d, k) for k, _ in LbmDiag._fields_}
+
+
+def lbm_state_size(ctx) -> int:
+    n = ctypes.c_size_t()
+    _check(ctx, load().lbm_state_size(ctx, ctypes.byref(n)), "lbm_state_size")
+    return n.value
+
+
+def lbm_save_state(ctx, stream=None) -> bytes:
+    n = lbm_state_size(ctx)
+    buf = ctypes.create_string_buffer(n)
+    _check(ctx, load().lbm_save_state(ctx, buf, n, stream), "lbm_save_state")
+    return buf.raw
+
+
+def lbm_load_state(ctx, blob: bytes, stream=None):
+    buf = ctypes.create_string_buffer(blob, len(blob))
+    _check(ctx, load().lbm_load_state(ctx, buf, len(blob), stream), "lbm_load_state")
+
+
+def lbm_step_count(ctx) -> int:
+    return int(load().lbm_step_count(ctx))
+
+
+def lbm_last_error(ctx) -> str:
+    return load().lbm_last_error(ctx).decode()
+
+
+def lbm_status_string(status: int) -> str:
+    return load().lbm_status_string(int(status)).decode()
+
+
+def lbm_destroy(ctx):
+    if ctx:
+        load().lbm_destroy(ctx)
+
+
+# --- convenience wrapper with torch tensors ----------------------------------
+
+def _stream():
+    import torch
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+class Solver:
+    """One GPU context.  Inputs: the workload dict and arrays of
+    ``paper_2510_18688_gb300.workloads``; fields come back as torch tensors
+    on the device (or numpy arrays with ``host=True``)."""
+
+    def __init__(self, cfg: dict, precision: str = "fp32", diag_every: int = 0):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("Solver needs a CUDA device (no CPU path)")
+        load()
+        self.cfg = dict(cfg)
+        self.nx, self.ny = int(cfg["nx"]), int(cfg["ny"])
+        self.precision = precision
+        self.params = make_params(cfg, precision, diag_every)
+        self.ctx = lbm_create(self.params)
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            lbm_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_geometry(self, arrays: dict, on_device: bool = True):
+        import torch
+        keys = ("phi0", "phi", "T", "fl")
+        if on_device:
+            t = {k: torch.as_tensor(np.ascontiguousarray(arrays[k], dtype=np.float64),
+                                    device="cuda") for k in keys}
+            m = arrays.get("mask")
+            tm = None if m is None else torch.as_tensor(
+                np.ascontiguousarray(m, dtype=np.uint8), device="cuda")
+            lbm_set_geometry(self.ctx, t["phi0"].data_ptr(), None if tm is None else tm.data_ptr(),
+                             t["phi"].data_ptr(), t["T"].data_ptr(), t["fl"].data_ptr(),
+                             LBM_DEVICE, _stream())
+            torch.cuda.current_stream().synchronize()
+        else:
+            h = {k: np.ascontiguousarray(arrays[k], dtype=np.float64) for k in keys}
+            m = arrays.get("mask")
+            hm = None if m is None else np.ascontiguousarray(m, dtype=np.uint8)
+            lbm_set_geometry(self.ctx, h["phi0"].ctypes.data, None if hm is None else hm.ctypes.data,
+                             h["phi"].ctypes.data, h["T"].ctypes.data, h["fl"].ctypes.data,
+                             LBM_HOST, _stream())
+        return self
+
+    def step(self, n: int = 1):
+        lbm_step(self.ctx, n, _stream())
+        return self
+
+    @property
+    def steps_done(self) -> int:
+        return lbm_step_count(self.ctx)
+
+    def fields(self, names=FIELDS, host: bool = True) -> dict:
+        import torch
+        mask = 0
+        ptrs = [None] * len(FIELDS)
+        out = {}
+        for k in names:
+            mask |= FIELD_BIT[k]
+            if host:
+                out[k] = np.empty((self.ny, self.nx), dtype=np.float64)
+                ptrs[FIELDS.index(k)] = out[k].ctypes.data
+            else:
+                out[k] = torch.empty((self.ny, self.nx), dtype=torch.float64, device="cuda")
+                ptrs[FIELDS.index(k)] = out[k].data_ptr()
+        lbm_read_fields(self.ctx, mask, ptrs, LBM_HOST if host else LBM_DEVICE, _stream())
+        return out
+
+    def diagnostics(self, compute: bool = True) -> dict:
+        if compute:
+            lbm_compute_diagnostics(self.ctx, _stream())
+        return lbm_read_diagnostics(self.ctx)
+
+    def save(self) -> bytes:
+        return lbm_save_state(self.ctx, _stream())
+
+    def load(self, blob: bytes):
+        lbm_load_state(self.ctx, blob, _stream())

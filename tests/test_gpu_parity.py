@@ -1,0 +1,231 @@
+"""Parity of the sm_103a path (through the C ABI) with the FP64 oracle.
+
+Same seeded inputs on both sides; the GPU result is compared element by
+element with the oracle:
+
+* FP64 path: max |gpu - oracle| <= 1e-10 * max |oracle| per field (the bar
+  for the double-precision kernels);
+* FP32 path: relative L2 error <= 1e-4 per field (populations stored and
+  collided in float).
+
+Grids are chosen to span several 32 x 8 tiles with ragged tails in both
+directions; the full-size workloads (512^2 droplet, 2048 x 1024 porous
+medium, 256^2 cylinder instance, the 400 x 4 and 512 x 8 column problems)
+are compared on every node after a step count the oracle finishes in
+seconds.
+"""
+import numpy as np
+import pytest
+
+from paper_2510_18688_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+FIELDS = ("phi", "fs", "fl", "T", "rhoH", "p", "ux", "uy", "rho", "mu", "w", "mdot")
+
+
+@pytest.fixture(scope="module")
+def env(oracle_mod):
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2510_18688_gb300 import build, lbm
+    build.build()
+    lbm.load()
+    return oracle_mod, lbm
+
+
+def _max_rel(a, b):
+    scale = np.abs(b).max()
+    err = np.abs(a - b).max()
+    return err / scale if scale > 0 else err
+
+
+def _l2_rel(a, b):
+    nb = np.linalg.norm(b)
+    return np.linalg.norm(a - b) / nb if nb > 0 else np.linalg.norm(a)
+
+
+def _compare(got, ref, prec, tol=None, fields=FIELDS):
+    bad = {}
+    for k in fields:
+        if prec == "fp64":
+            e = _max_rel(got[k], ref[k])
+            t = 1e-10 if tol is None else tol
+        else:
+            e = _l2_rel(got[k], ref[k])
+            t = 1e-4 if tol is None else tol
+        if not e <= t:
+            bad[k] = e
+    assert not bad, f"{prec}: fields off the oracle: {bad}"
+
+
+def _run_pair(env, wl, steps, prec):
+    O, lbm = env
+    cfg, arr = wl
+    ref = O.from_workload(wl).step(steps).fields()
+    s = lbm.Solver(cfg, precision=prec).set_geometry(arr).step(steps)
+    got = s.fields()
+    s.close()
+    return got, ref
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("seed,nx,ny", [(0, 45, 19), (1, 67, 33), (2, 37, 41), (3, 96, 24),
+                                        (4, 33, 9), (5, 70, 17)])
+def test_random_states(env, prec, seed, nx, ny):
+    """Every branch: gas, liquid, ice, mushy nodes, solid blobs, cold mask,
+    periodic/Dirichlet/adiabatic sides, gravity, random angles."""
+    got, ref = _run_pair(env, W.random_state(nx, ny, seed=seed), 120, prec)
+    _compare(got, ref, prec)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("lat", [1, 2, 4, 3, 5, 6])
+def test_lattice_subsets(env, prec, lat):
+    """Flow, phase and enthalpy lattices switched on alone and in pairs."""
+    got, ref = _run_pair(env, W.random_state(41, 27, seed=7, lattices=lat), 80, prec)
+    _compare(got, ref, prec)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_tiny_and_degenerate_grids(env, prec):
+    """2 x 2 and single-tile-column grids, all walls and all periodic."""
+    for (nx, ny), bc in (((2, 2), ("periodic",) * 4),
+                         ((3, 2), ("dirichlet", "adiabatic", "dirichlet", "adiabatic")),
+                         ((2, 40), ("adiabatic", "dirichlet", "periodic", "periodic")),
+                         ((33, 1 + 1), ("periodic", "periodic", "dirichlet", "dirichlet"))):
+        got, ref = _run_pair(env, W.random_state(nx, ny, seed=11, bc=bc, n_blobs=1), 30, prec)
+        _compare(got, ref, prec)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_readings_variant(env, prec):
+    """Variant bit of the modified force (reading R-FT)."""
+    cfg, arr = W.random_state(40, 30, seed=5)
+    cfg["readings"] = 1
+    got, ref = _run_pair(env, (cfg, arr), 60, prec)
+    _compare(got, ref, prec)
+
+
+def test_neumann_column_full_run(env):
+    """400 x 4 conduction-induced freezing, FP64, the full 20k steps."""
+    got, ref = _run_pair(env, W.neumann(), 20000, "fp64")
+    _compare(got, ref, "fp64")
+
+
+def test_stefan_column_fp32(env):
+    """512 x 8 three-phase Stefan problem, FP32 against FP64, 5000 steps."""
+    got, ref = _run_pair(env, W.stefan(), 5000, "fp32")
+    _compare(got, ref, "fp32", tol=1e-4, fields=("phi", "fs", "fl", "T", "rhoH", "rho", "w"))
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_sessile_droplet_512(env, prec):
+    """The 512^2 droplet workload at full size (every node compared)."""
+    got, ref = _run_pair(env, W.sessile_droplet(512, seed=0), 12, prec)
+    _compare(got, ref, prec)
+
+
+def test_cylinder_instance(env):
+    got, ref = _run_pair(env, W.cylinder_droplet(256, seed=3), 30, "fp64")
+    _compare(got, ref, "fp64")
+
+
+def test_porous_2048x1024_fp32(env):
+    """The 2048 x 1024 porous medium at full size, FP32, 4 steps."""
+    got, ref = _run_pair(env, W.porous(seed=0), 4, "fp32")
+    _compare(got, ref, "fp32")
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_diagnostics_match_oracle(env, prec):
+    O, lbm = env
+    wl = W.random_state(64, 48, seed=3)
+    o = O.from_workload(wl).step(50)
+    dref = o.diagnostics()
+    s = lbm.Solver(wl[0], precision=prec).set_geometry(wl[1]).step(50)
+    d = s.diagnostics()
+    tol = 1e-12 if prec == "fp64" else 1e-5
+    n = 64 * 48
+    for k, v in dref.items():
+        # sums of O(1) per-node values: relative tolerance plus n * tol
+        assert abs(d[k] - v) <= tol * (abs(v) + n), (k, d[k], v)
+    assert d["step"] == 50
+
+
+def test_fused_diagnostics_equal_readout(env):
+    """Diagnostics fused into the step kernel (diag_every) equal those of
+    the separate read-out pass on the same state, bit for bit."""
+    O, lbm = env
+    cfg, arr = W.random_state(50, 30, seed=4)
+    s = lbm.Solver(cfg, precision="fp64", diag_every=5).set_geometry(arr).step(10)
+    # steps 0 and 5 reduce their input states; the latest describes state 5
+    fused = s.diagnostics(compute=False)
+    assert fused["step"] == 5
+    t = lbm.Solver(cfg, precision="fp64").set_geometry(arr).step(5)
+    sep = t.diagnostics()
+    for k in sep:
+        assert fused[k] == sep[k], k
+
+
+def test_host_and_device_io_agree(env):
+    O, lbm = env
+    cfg, arr = W.random_state(48, 20, seed=6)
+    a = lbm.Solver(cfg, precision="fp64").set_geometry(arr, on_device=True).step(15)
+    b = lbm.Solver(cfg, precision="fp64").set_geometry(arr, on_device=False).step(15)
+    fa = a.fields(host=True)
+    fb = {k: v.cpu().numpy() for k, v in b.fields(host=False).items()}
+    for k in FIELDS:
+        assert np.array_equal(fa[k], fb[k]), k
+
+
+def test_checkpoint_resume_is_bitwise(env):
+    O, lbm = env
+    cfg, arr = W.random_state(40, 24, seed=8)
+    a = lbm.Solver(cfg, precision="fp32").set_geometry(arr).step(40)
+    b = lbm.Solver(cfg, precision="fp32").set_geometry(arr).step(20)
+    blob = b.save()
+    c = lbm.Solver(cfg, precision="fp32").set_geometry(arr)
+    c.load(blob)
+    assert c.steps_done == 20
+    c.step(20)
+    fa, fc = a.fields(), c.fields()
+    for k in FIELDS:
+        assert np.array_equal(fa[k], fc[k]), k
+
+
+def test_runs_are_deterministic(env):
+    O, lbm = env
+    cfg, arr = W.sessile_droplet(160, seed=2, radius=40)
+    r = [lbm.Solver(cfg, precision="fp32", diag_every=1).set_geometry(arr).step(25)
+         for _ in range(2)]
+    d0, d1 = r[0].diagnostics(compute=False), r[1].diagnostics(compute=False)
+    assert d0 == d1
+    f0, f1 = r[0].fields(), r[1].fields()
+    for k in FIELDS:
+        assert np.array_equal(f0[k], f1[k])
+
+
+def test_nonfinite_state_is_reported(env):
+    """A NaN planted in the host input reaches the diagnostics as
+    LBM_ERR_NONFINITE (host-side fault injection, no device fault)."""
+    O, lbm = env
+    cfg, arr = W.random_state(32, 16, seed=9)
+    arr = {k: v.copy() for k, v in arr.items()}
+    arr["T"][3, 5] = np.nan
+    s = lbm.Solver(cfg, precision="fp64").set_geometry(arr).step(3)
+    d = s.diagnostics()
+    assert d["nonfinite"] > 0
+
+
+def test_errors_are_status_codes(env):
+    O, lbm = env
+    cfg, arr = W.random_state(16, 16, seed=1)
+    s = lbm.Solver(cfg, precision="fp32")
+    with pytest.raises(lbm.LbmError) as e:
+        s.step(1)  # before set_geometry
+    assert e.value.status == -8
+    s.set_geometry(arr)
+    with pytest.raises(lbm.LbmError):
+        lbm.lbm_step(s.ctx, -1)

@@ -1,0 +1,66 @@
+"""CPU checks of the C-ABI library: it builds for sm_103a, loads, and exports
+every entry point that include/lbm.h declares (no compute without a GPU)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2510_18688_gb300 import build, lbm
+    build.build()
+    return lbm.load()
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "lbm.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(lbm_[a-z_]+)\s*\(", src)))
+
+
+def test_header_declares_the_boundary():
+    names = _declared()
+    for n in ("lbm_create", "lbm_set_geometry", "lbm_step", "lbm_read_fields",
+              "lbm_read_diagnostics", "lbm_destroy"):
+        assert n in names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    for n in _declared():
+        assert hasattr(lib, n), n
+
+
+def test_binding_exports_match_header():
+    from paper_2510_18688_gb300 import lbm
+    assert sorted(lbm.EXPORTS) == _declared()
+    for n in lbm.EXPORTS:
+        assert callable(getattr(lbm, n))
+
+
+def test_create_rejects_invalid_parameters_without_gpu(lib):
+    """Validation runs before any device call, so it is testable on CPU."""
+    from paper_2510_18688_gb300 import lbm, workloads as W
+    cfg = W.base_params(16, 16)
+    bad = [dict(nx=1), dict(mu_l=0.0), dict(rho_g=-1.0), dict(lattices=0), dict(lattices=9),
+           dict(bc=("periodic", "dirichlet", "periodic", "periodic")), dict(mobility=0.0)]
+    for b in bad:
+        c = dict(cfg, **b)
+        p = lbm.make_params(c)
+        h = ctypes.c_void_p()
+        st = lib.lbm_create(ctypes.byref(p), ctypes.byref(h))
+        assert st in (-1, -2), (b, st)
+        assert not h.value
+    assert lib.lbm_status_string(-5).decode() == "non-finite state"
+
+
+def test_null_context_is_an_error_not_a_crash(lib):
+    from paper_2510_18688_gb300 import lbm
+    assert lib.lbm_step(None, 1, None) == -1
+    assert lib.lbm_read_diagnostics(None, None) == -1
+    assert lib.lbm_step_count(None) == -1
+    lib.lbm_destroy(None)
+    assert lbm.LBM_OK == 0
