@@ -102,7 +102,9 @@ int validate(const lbm_params* p, char* err, size_t n) {
     std::snprintf(err, n, "grid must be at least 2 x 2 (got %d x %d)", p->nx, p->ny);
     return LBM_ERR_ARG;
   }
-  if ((long long)p->nx * p->ny > (1LL << 31) / 27) {
+  // the kernels index the 27 population planes with 32-bit offsets
+  const long long plane = ((long long)((p->nx + 31) / 32 * 32) * p->ny + 63) / 64 * 64;
+  if (plane * 27 >= (1LL << 31)) {
     std::snprintf(err, n, "grid of %d x %d nodes is too large", p->nx, p->ny);
     return LBM_ERR_ARG;
   }

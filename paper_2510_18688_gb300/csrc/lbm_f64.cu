@@ -4,14 +4,23 @@
 
 namespace lbmk {
 
-cudaError_t launch_step_f64(const Args<double>& a, int mode, bool diag, cudaStream_t s) {
+template <int MODE, bool DIAG>
+static void launch_one(const Args<double>& a, cudaStream_t s) {
   const dim3 grid = grid_dims(a.g), block = block_dims();
+  // the all-lattices case is specialised at compile time
+  if (a.g.lattices == (LAT_FLOW | LAT_PHASE | LAT_HEAT))
+    lbm_step_kernel<double, MODE, DIAG, 7><<<grid, block, 0, s>>>(a);
+  else
+    lbm_step_kernel<double, MODE, DIAG, 0><<<grid, block, 0, s>>>(a);
+}
+
+cudaError_t launch_step_f64(const Args<double>& a, int mode, bool diag, cudaStream_t s) {
   if (mode == MODE_STEP) {
-    if (diag) lbm_step_kernel<double, MODE_STEP, true><<<grid, block, 0, s>>>(a);
-    else lbm_step_kernel<double, MODE_STEP, false><<<grid, block, 0, s>>>(a);
+    if (diag) launch_one<MODE_STEP, true>(a, s);
+    else launch_one<MODE_STEP, false>(a, s);
   } else {
-    if (diag) lbm_step_kernel<double, MODE_READ, true><<<grid, block, 0, s>>>(a);
-    else lbm_step_kernel<double, MODE_READ, false><<<grid, block, 0, s>>>(a);
+    if (diag) launch_one<MODE_READ, true>(a, s);
+    else launch_one<MODE_READ, false>(a, s);
   }
   return cudaGetLastError();
 }

@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 
 #include "lbm_kernels.cuh"
+#include "lbm_step.cuh"
 
 namespace lbmk {
 

@@ -1,0 +1,453 @@
+// lbm_step.cuh -- the fused time step (MODE_STEP) and the field read-out
+// (MODE_READ) kernel for sm_103a, built on the helpers of lbm_kernels.cuh.
+//
+// Register budget drives the structure: the populations are never all live
+// at once.  Phase A keeps only the sums of the phase and enthalpy
+// populations (the loads go through the read-only path with an opaque load so
+// that phase B re-reads them from L1 instead of holding them in registers
+// across the barriers); the flow populations are prefetched before the
+// barriers.  Phase B collides and pushes one lattice at a time.  Links that
+// stay inside the grid take a branch-free streaming path; nodes on the grid
+// edge take the general path with wrap, bounce-back and anti-bounce-back.
+#pragma once
+
+#include "lbm_kernels.cuh"
+
+namespace lbmk {
+
+// Loads that the compiler may not merge with later loads of the same
+// address (read-only, non-coherent path; the input buffer is never written
+// during a launch).
+__device__ __forceinline__ float ld_sum(const float* p) {
+  float v;
+  asm volatile("ld.global.nc.f32 %0, [%1];" : "=f"(v) : "l"(p));
+  return v;
+}
+__device__ __forceinline__ double ld_sum(const double* p) {
+  double v;
+  asm volatile("ld.global.nc.f64 %0, [%1];" : "=d"(v) : "l"(p));
+  return v;
+}
+
+// Store of one post-collision population of direction i from node (x, y)
+// (index n) into the destination buffer.  INNER: the link stays in the grid.
+// For the enthalpy lattice (HEAT) a link leaving through a Dirichlet wall
+// returns by anti-bounce-back, through an adiabatic wall by bounce-back.
+template <typename R, bool INNER, bool HEAT>
+__device__ __forceinline__ void push(const Geom& g, const Coef<R>& c, R* __restrict__ plane0,
+                                     int P, int i, int x, int y, int n, R v) {
+  if (INNER) {
+    plane0[i * P + n + qy(i) * g.pitch + qx(i)] = v;
+  } else {
+    int wall;
+    const long long t = stream_target(g, x, y, qx(i), qy(i), wall);
+    if (t >= 0) {
+      plane0[i * P + (int)t] = v;
+    } else {
+      if (HEAT && g.bc[wall] == BC_DIRICHLET) v = -v + R(2) * qw<R>(i) * c.rr * c.T_wall[wall];
+      plane0[qopp(i) * P + n] = v;
+    }
+  }
+}
+
+// Macroscopic quantities of one node that the collisions need.
+template <typename R>
+struct Macro {
+  R ux, uy, uu, pr, S, Ftx, Fty, uFt, Gx, Gy, tauf, muphi, phux, phuy, cap;
+};
+
+// Flow collision Eqs. (11), (14)-(16) and push.
+template <typename R, bool INNER>
+__device__ __forceinline__ void collide_flow(const Geom& g, const Coef<R>& c, R* __restrict__ out,
+                                             int P, int x, int y, int n, const R* f, R rho,
+                                             const Macro<R>& M) {
+  const R itau = qdiv(R(1), M.tauf);
+  const R fcoef = R(1) - R(0.5) * itau;
+  const bool iso = (c.readings & 1u) != 0;
+#pragma unroll
+  for (int i = 0; i < 9; i++) {
+    const R cu = R(qx(i)) * M.ux + R(qy(i)) * M.uy;
+    const R si = qw<R>(i) * (R(3) * cu + R(4.5) * cu * cu - R(1.5) * M.uu);
+    const R feq = M.pr * R(3) * (qw<R>(i) - (i == 0 ? R(1) : R(0))) + rho * si;
+    const R cF = R(qx(i)) * M.Gx + R(qy(i)) * M.Gy;
+    const R cFt = R(qx(i)) * M.Ftx + R(qy(i)) * M.Fty;
+    R tens = R(2) * cu * cFt - R(2) / R(3) * M.uFt;
+    if (iso) tens += M.S / R(3) * (R(qx(i) * qx(i) + qy(i) * qy(i)) - R(2) / R(3));
+    const R Fi = qw<R>(i) * (M.S + R(3) * cF + R(4.5) * tens);
+    const R post = f[i] - (f[i] - feq) * itau + fcoef * Fi;
+    push<R, INNER, false>(g, c, out, P, i, x, y, n, post);
+  }
+}
+
+// Phase-field collision Eqs. (18)-(20) and push.
+template <typename R, bool INNER>
+__device__ __forceinline__ void collide_phase(const Geom& g, const Coef<R>& c,
+                                              R* __restrict__ out, int P, int x, int y, int n,
+                                              const R* gq, R phi, R mdot, R phuxp, R phuyp,
+                                              const Macro<R>& M) {
+  const R itg = qdiv(R(1), c.tau_g);
+  const R gcoef = R(1) - R(0.5) * itg;
+  const R dphx = M.phux - phuxp, dphy = M.phuy - phuyp;
+  const R emu = c.eta * M.muphi;
+#pragma unroll
+  for (int i = 0; i < 9; i++) {
+    const R wi = qw<R>(i);
+    const R cph = R(qx(i)) * M.phux + R(qy(i)) * M.phuy;
+    const R geq = (i == 0) ? phi + (wi - R(1)) * emu : wi * emu + wi * R(3) * cph;
+    const R Gi = wi * (R(qx(i)) * dphx + R(qy(i)) * dphy) * R(3) + wi * phi * mdot;
+    const R post = gq[i] - (gq[i] - geq) * itg + gcoef * Gi;
+    push<R, INNER, false>(g, c, out, P, i, x, y, n, post);
+  }
+}
+
+// Enthalpy TRT collision Eqs. (23)-(27) and push.
+template <typename R, bool INNER>
+__device__ __forceinline__ void collide_heat(const Geom& g, const Coef<R>& c, R* __restrict__ out,
+                                             int P, int x, int y, int n, const R* h, R fs, R w,
+                                             R T, R rhoH, R mdot, const Macro<R>& M) {
+  const R lam = interp(fs, w, c.lam_s, c.lam_l, c.lam_g);
+  const R taua = R(0.5) + qdiv(lam, c.rr / R(3));
+  const R taus = qdiv(taua, R(2) * taua - R(1));
+  const R ia = qdiv(R(1), taua), is = qdiv(R(1), taus);
+  const R hcoef = R(1) - R(0.5) * ia;
+  const R rrC = qdiv(c.rr, M.cap);
+  const R Hsrc = M.cap * T * mdot;
+  R he[9];
+#pragma unroll
+  for (int i = 0; i < 9; i++) he[i] = heq_i<R>(i, rhoH, M.cap, T, c.rr, rrC, M.ux, M.uy, M.uu);
+#pragma unroll
+  for (int i = 0; i < 9; i++) {
+    const int o = qopp(i);
+    const R hs = R(0.5) * (h[i] + h[o]), ha = R(0.5) * (h[i] - h[o]);
+    const R es = R(0.5) * (he[i] + he[o]), ea = R(0.5) * (he[i] - he[o]);
+    const R post = h[i] - (ha - ea) * ia - (hs - es) * is + hcoef * qw<R>(i) * Hsrc;
+    push<R, INNER, true>(g, c, out, P, i, x, y, n, post);
+  }
+}
+
+// LATC: compile-time lattice set (7 = all three) or 0 (read at run time).
+template <typename R, int MODE, bool DIAG, int LATC>
+__global__ void __launch_bounds__(NT, sizeof(R) == 4 ? 3 : 1)
+    lbm_step_kernel(const Args<R> a) {
+  const Geom& g = a.g;
+  const Coef<R>& c = a.c;
+  const int lat = LATC ? LATC : g.lattices;
+  const int P = (int)g.plane;  // 27 planes fit in 31 bits (checked at create)
+
+  __shared__ R s_phi[HN], s_fs[HN], s_rho[HN], s_p[HN], s_phi0[HN];
+  __shared__ R s_rsg[RING][NPART], s_rsh[RING][NPART];
+  __shared__ R s_rfl[RING], s_rw[RING], s_rQ[RING];
+  __shared__ int s_rmask[RING];
+  __shared__ double s_red[NT / 32][NDIAG];
+  __shared__ int s_last;
+
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  const int tid = ty * TX + tx;
+  const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
+  const int gx = x0 + tx, gy = y0 + ty;
+  const bool valid = gx < g.nx && gy < g.ny;
+  const int mx = wrap_or_clamp(gx, g.nx, g.bc[0], g.bc[1]);
+  const int my = wrap_or_clamp(gy, g.ny, g.bc[2], g.bc[3]);
+  const int n = my * g.pitch + mx;
+
+  // ---- phase A0: a third of one ring node's phase/enthalpy populations ----
+  if (tid < RING * NPART) {
+    const int k = tid / NPART, part = tid - k * NPART;
+    int hx, hy;
+    ring_pos(k, hx, hy);
+    const int rx = wrap_or_clamp(x0 + hx - 1, g.nx, g.bc[0], g.bc[1]);
+    const int ry = wrap_or_clamp(y0 + hy - 1, g.ny, g.bc[2], g.bc[3]);
+    const int m = ry * g.pitch + rx;
+    const bool masked = g.has_mask && a.mask[m];
+    const R* pm = a.pin + m;
+    // part 0: g0..g5; part 1: g6..g8 and h0..h2; part 2: h3..h8
+    R sgp = R(0), shp = R(0);
+    if (part == 0) {
+      if (lat & LAT_PHASE) {
+        R v[6];
+#pragma unroll
+        for (int i = 0; i < 6; i++) v[i] = pm[(9 + i) * P];
+        sgp = v[0] + v[1] + v[2] + v[3] + v[4] + v[5];
+      }
+      const int hi = hy * HX + hx;
+      s_phi0[hi] = a.phi0[m];
+      s_p[hi] = a.lin[LAG_P * P + m];
+      s_rfl[k] = a.lin[LAG_FL * P + m];
+      s_rw[k] = a.lin[LAG_W * P + m];
+      s_rQ[k] = a.lin[LAG_Q * P + m];
+      s_rmask[k] = masked ? 1 : 0;
+    } else if (part == 1) {
+      if (lat & LAT_PHASE) sgp = pm[15 * P] + pm[16 * P] + pm[17 * P];
+      if ((lat & LAT_HEAT) && !masked) shp = pm[18 * P] + pm[19 * P] + pm[20 * P];
+    } else {
+      if ((lat & LAT_HEAT) && !masked) {
+        R v[6];
+#pragma unroll
+        for (int i = 0; i < 6; i++) v[i] = pm[(21 + i) * P];
+        shp = v[0] + v[1] + v[2] + v[3] + v[4] + v[5];
+      }
+    }
+    s_rsg[k][part] = sgp;
+    s_rsh[k][part] = shp;
+  }
+
+  // ---- phase A1: own node (sums only; f prefetched for phase B) ----------
+  const R* pn = a.pin + n;
+  const R phi0 = a.phi0[n];
+  const R flp = a.lin[LAG_FL * P + n];
+  const R wp = a.lin[LAG_W * P + n];
+  const R pp = a.lin[LAG_P * P + n];
+  const R Qp = a.lin[LAG_Q * P + n];
+  const bool masked = (lat & LAT_HEAT) && g.has_mask && a.mask[n];
+  R f[9];
+  if (lat & LAT_FLOW) {
+#pragma unroll
+    for (int i = 0; i < 9; i++) f[i] = pn[i * P];
+  }
+  R sg = R(0), sh = R(0);
+  if (lat & LAT_PHASE) {
+    R v[9];
+#pragma unroll
+    for (int i = 0; i < 9; i++) v[i] = ld_sum(pn + (9 + i) * P);
+    sg = sum_g(v);
+  }
+  if (lat & LAT_HEAT) {
+    R v[9];
+    if (masked) {
+      cold_mask_h(c, wp, phi0, v);
+    } else {
+#pragma unroll
+      for (int i = 0; i < 9; i++) v[i] = ld_sum(pn + (18 + i) * P);
+    }
+    sh = sum_h(v);
+  }
+  const Local<R> L = local_state(c, lat, sg, sh, flp, wp, Qp, phi0);
+  {
+    const int hi = (ty + 1) * HX + (tx + 1);
+    s_phi[hi] = L.phi;
+    s_fs[hi] = L.fs;
+    s_rho[hi] = L.rho;
+    s_p[hi] = pp;
+    s_phi0[hi] = phi0;
+  }
+  __syncthreads();
+
+  // ---- phase A2: rows a1-a2 of the ring ------------------------------------
+  if (tid < RING) {
+    const int k = tid;
+    int hx, hy;
+    ring_pos(k, hx, hy);
+    const int hi = hy * HX + hx;
+    const R q0 = s_phi0[hi];
+    const R wq = s_rw[k];
+    const R sgq = s_rsg[k][0] + s_rsg[k][1];
+    R shq;
+    if ((lat & LAT_HEAT) && s_rmask[k]) {
+      R hq[9];
+      cold_mask_h(c, wq, q0, hq);
+      shq = sum_h(hq);
+    } else {
+      shq = s_rsh[k][1] + s_rsh[k][2];
+    }
+    const Local<R> Lq = local_state(c, lat, sgq, shq, s_rfl[k], wq, s_rQ[k], q0);
+    s_phi[hi] = Lq.phi;
+    s_fs[hi] = Lq.fs;
+    s_rho[hi] = Lq.rho;
+  }
+  __syncthreads();
+
+  // ---- phase B: stencils, macros, collisions, streaming -------------------
+  R dvals[NDIAG];
+  if (valid) {
+    const int hc = (ty + 1) * HX + (tx + 1);
+    // isotropic stencils (reading R-FD): grad = 3 sum w_i c_i chi(x + c_i),
+    // lap = 6 sum w_i (chi(x + c_i) - chi(x))
+    R gphx = R(0), gphy = R(0), lphi = R(0), lphi0 = R(0), lfs = R(0);
+    R grx = R(0), gry = R(0), gpx = R(0), gpy = R(0);
+#pragma unroll
+    for (int i = 1; i < 9; i++) {
+      const int hn = hc + qy(i) * HX + qx(i);
+      const R wi = qw<R>(i);
+      const R cxi = R(qx(i)), cyi = R(qy(i));
+      if (lat & LAT_PHASE) {
+        const R ph = s_phi[hn];
+        gphx += wi * cxi * ph;
+        gphy += wi * cyi * ph;
+        lphi += R(2) * wi * (ph - s_phi[hc]);
+        lphi0 += R(2) * wi * (s_phi0[hn] - s_phi0[hc]);
+        lfs += R(2) * wi * (s_fs[hn] - s_fs[hc]);
+      }
+      if (lat & LAT_FLOW) {
+        const R rq = s_rho[hn], pq = s_p[hn];
+        grx += wi * cxi * rq;
+        gry += wi * cyi * rq;
+        gpx += wi * cxi * pq;
+        gpy += wi * cyi * pq;
+      }
+    }
+    gphx *= R(3); gphy *= R(3); lphi *= R(3); lphi0 *= R(3); lfs *= R(3);
+    grx *= R(3); gry *= R(3); gpx *= R(3); gpy *= R(3);
+
+    const R phi = L.phi, fs = L.fs, rho = L.rho, T = L.T, mdot = L.mdot;
+    Macro<R> M;
+    M.muphi = R(0);
+    R Fx, Fy;
+    {
+      R Fsx = R(0), Fsy = R(0);
+      if (lat & LAT_PHASE) {
+        M.muphi = chem_local(c, phi, phi0, fs) -
+                  R(3) * c.eps * c.sigma / R(8) * (lphi + c.cos_th * lphi0 + c.cos_ps * lfs);
+        Fsx = M.muphi * gphx;
+        Fsy = M.muphi * gphy;
+      }
+      Fx = Fsx + rho * c.gx;
+      Fy = Fsy + rho * c.gy;
+    }
+    M.ux = R(0); M.uy = R(0); M.uu = R(0); M.pr = R(0);
+    if (lat & LAT_FLOW) {
+      const R mu = interp(fs, L.w, c.mu_s, c.mu_l, c.mu_g);
+      const R jx = (f[1] - f[3]) + (f[5] - f[6]) + (f[8] - f[7]);
+      const R jy = (f[2] - f[4]) + (f[5] + f[6]) - (f[7] + f[8]);
+      const R snz = (f[1] + f[2] + f[3] + f[4]) + (f[5] + f[6] + f[7] + f[8]);
+      // Eq. (17a,b) with the penalty force f = fs (u_s - u*), u_s = 0
+      const R usx = qdiv(jx + R(0.5) * Fx, rho), usy = qdiv(jy + R(0.5) * Fy, rho);
+      const R fpx = -fs * usx, fpy = -fs * usy;
+      M.ux = usx + R(0.5) * fpx;
+      M.uy = usy + R(0.5) * fpy;
+      M.uu = M.ux * M.ux + M.uy * M.uy;
+      M.S = rho * mdot + M.ux * grx + M.uy * gry;
+      // modified force (reading R-FT), lagged pressure (reading R-FP)
+      M.Ftx = Fx - (gpx - grx / R(3));
+      M.Fty = Fy - (gpy - gry / R(3));
+      M.uFt = M.ux * M.Ftx + M.uy * M.Fty;
+      M.tauf = qdiv(mu, rho / R(3)) + R(0.5);
+      M.Gx = Fx + rho * fpx;
+      M.Gy = Fy + rho * fpy;
+      // F_0 of Eq. (16)
+      R F0 = qw<R>(0) * (M.S + (R(0) - R(2) / R(3) * M.uFt) * R(4.5));
+      if (c.readings & 1u) F0 += qw<R>(0) * (M.S * (R(0) - R(2) / R(3)) * R(1.5));
+      const R s0 = qw<R>(0) * (-M.uu * R(1.5));
+      M.pr = (R(1) / R(3)) / (R(1) - qw<R>(0)) *
+             (snz + R(0.5) * M.S + (M.tauf - R(0.5)) * F0 + rho * s0);  // Eq. (17c)
+    }
+    M.phux = phi * M.ux;
+    M.phuy = phi * M.uy;
+    M.cap = rho * interp(fs, L.w, c.cp_s, c.cp_l, c.cp_g);
+
+    if (MODE == MODE_STEP) {
+      // links that stay inside the grid need no boundary logic
+      const bool inner = gx > 0 && gx < g.nx - 1 && gy > 0 && gy < g.ny - 1;
+      R* out = a.pout;
+      if (lat & LAT_FLOW) {
+        if (inner) collide_flow<R, true>(g, c, out, P, gx, gy, n, f, rho, M);
+        else collide_flow<R, false>(g, c, out, P, gx, gy, n, f, rho, M);
+      }
+      if (lat & LAT_PHASE) {
+        R gq[9];
+#pragma unroll
+        for (int i = 0; i < 9; i++) gq[i] = pn[(9 + i) * P];
+        const R phuxp = a.lin[LAG_PHUX * P + n];
+        const R phuyp = a.lin[LAG_PHUY * P + n];
+        if (inner) collide_phase<R, true>(g, c, out + 9 * P, P, gx, gy, n, gq, phi, mdot, phuxp, phuyp, M);
+        else collide_phase<R, false>(g, c, out + 9 * P, P, gx, gy, n, gq, phi, mdot, phuxp, phuyp, M);
+      }
+      if (lat & LAT_HEAT) {
+        R hq[9];
+        if (masked) {
+          cold_mask_h(c, wp, phi0, hq);
+        } else {
+#pragma unroll
+          for (int i = 0; i < 9; i++) hq[i] = pn[(18 + i) * P];
+        }
+        if (inner) collide_heat<R, true>(g, c, out + 18 * P, P, gx, gy, n, hq, fs, L.w, T, L.rhoH, mdot, M);
+        else collide_heat<R, false>(g, c, out + 18 * P, P, gx, gy, n, hq, fs, L.w, T, L.rhoH, mdot, M);
+      }
+      a.lout[LAG_FL * P + n] = L.fl;
+      a.lout[LAG_W * P + n] = L.w;
+      a.lout[LAG_P * P + n] = (lat & LAT_FLOW) ? M.pr : R(0);
+      a.lout[LAG_PHUX * P + n] = (lat & LAT_PHASE) ? M.phux : R(0);
+      a.lout[LAG_PHUY * P + n] = (lat & LAT_PHASE) ? M.phuy : R(0);
+      a.lout[LAG_Q * P + n] = (lat & LAT_HEAT) ? M.cap * T * mdot : R(0);
+    } else {
+      const long long d = (long long)gy * g.nx + gx;
+      const R vals[NFIELD] = {phi, fs, L.fl, T, L.rhoH, M.pr, M.ux, M.uy, rho, M.muphi, L.w, mdot};
+#pragma unroll
+      for (int k = 0; k < NFIELD; k++)
+        if (a.out[k]) a.out[k][d] = (double)vals[k];
+    }
+    if (DIAG) {
+      dvals[0] = rho;
+      dvals[1] = L.w * (c.rho_s * (R(1) - L.fl) + c.rho_l * L.fl);
+      dvals[2] = L.rhoH;
+      dvals[3] = L.w * L.fl;
+      dvals[4] = L.w;
+      dvals[5] = L.w * (R(1) - L.fl);
+      dvals[6] = phi;
+      dvals[7] = R(0.5) * rho * M.uu;
+      // a non-finite population anywhere makes one of the sums non-finite
+      R tot = sg + sh;
+      if (lat & LAT_FLOW) {
+#pragma unroll
+        for (int i = 0; i < 9; i++) tot += f[i];
+      }
+      dvals[8] = isfinite(tot) ? R(0) : R(1);
+    }
+  } else if (DIAG) {
+#pragma unroll
+    for (int k = 0; k < NDIAG; k++) dvals[k] = R(0);
+  }
+
+  if (DIAG) {
+    // warp sums in R, then per-block and a last-block pass in FP64, all in a
+    // fixed order
+    const int lane = tid & 31, warp = tid >> 5;
+#pragma unroll
+    for (int k = 0; k < NDIAG; k++) {
+      const R v = warp_sum(dvals[k]);
+      if (lane == 0) s_red[warp][k] = (double)v;
+    }
+    __syncthreads();
+    const int nb = gridDim.x * gridDim.y;
+    const int b = blockIdx.y * gridDim.x + blockIdx.x;
+    if (tid < NDIAG) {
+      double s = 0.0;
+#pragma unroll
+      for (int w = 0; w < NT / 32; w++) s += s_red[w][tid];
+      a.diag_partial[(long long)tid * nb + b] = s;
+      __threadfence();  // publish the partial before the ticket
+    }
+    __syncthreads();
+    if (tid == 0) s_last = (atomicAdd(a.diag_counter, 1u) == (unsigned)(nb - 1));
+    __syncthreads();
+    if (s_last) {
+      __threadfence();
+      double acc[NDIAG];
+#pragma unroll
+      for (int k = 0; k < NDIAG; k++) acc[k] = 0.0;
+      for (int j = tid; j < nb; j += NT) {
+#pragma unroll
+        for (int k = 0; k < NDIAG; k++) acc[k] += __ldcg(&a.diag_partial[(long long)k * nb + j]);
+      }
+#pragma unroll
+      for (int k = 0; k < NDIAG; k++) {
+        double v = acc[k];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (lane == 0) s_red[warp][k] = v;
+      }
+      __syncthreads();
+      if (tid < NDIAG) {
+        double s = 0.0;
+#pragma unroll
+        for (int w = 0; w < NT / 32; w++) s += s_red[w][tid];
+        a.diag_out[tid] = s;
+      }
+      if (tid == 0) {
+        a.diag_out[NDIAG] = (double)a.step_index;
+        *a.diag_counter = 0u;
+      }
+    }
+  }
+}
+
+}  // namespace lbmk
