@@ -52,6 +52,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
     os.makedirs(OUT_DIR, exist_ok=True)
     tool = nvcc()
     base = [tool, ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC"]
+    base += os.environ.get("LBM_NVCC_EXTRA", "").split()
     if verbose:
         base += ["-Xptxas", "-v"]
 

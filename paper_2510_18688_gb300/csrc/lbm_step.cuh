@@ -13,6 +13,11 @@
 
 #include "lbm_kernels.cuh"
 
+// resident CTAs per SM the float kernel is compiled for (register budget)
+#ifndef LBM_MIN_BLOCKS_F32
+#define LBM_MIN_BLOCKS_F32 4
+#endif
+
 namespace lbmk {
 
 // Loads that the compiler may not merge with later loads of the same
@@ -56,26 +61,50 @@ struct Macro {
   R ux, uy, uu, pr, S, Ftx, Fty, uFt, Gx, Gy, tauf, muphi, phux, phuy, cap;
 };
 
+// The three collisions are evaluated pairwise over (i, opposite of i): in
+// every equilibrium and source of Eqs. (14)-(16), (19)-(20) and (25) the
+// terms even in c_i are shared by the pair and the odd terms change sign, so
+// each pair costs one evaluation of each part.  Pairs: (1,3), (2,4) with
+// weight 1/9 and (5,7), (6,8) with weight 1/36.
+
 // Flow collision Eqs. (11), (14)-(16) and push.
 template <typename R, bool INNER>
 __device__ __forceinline__ void collide_flow(const Geom& g, const Coef<R>& c, R* __restrict__ out,
                                              int P, int x, int y, int n, const R* f, R rho,
                                              const Macro<R>& M) {
   const R itau = qdiv(R(1), M.tauf);
+  const R omi = R(1) - itau;
   const R fcoef = R(1) - R(0.5) * itau;
   const bool iso = (c.readings & 1u) != 0;
+  // terms shared by all directions
+  const R sym0 = rho * (-R(1.5) * M.uu);           // rho s_i / w_i without c_i terms
+  const R fsym0 = M.S - R(3) * M.uFt;              // F_i / w_i without c_i terms
+  // rest population
+  {
+    R F0 = fsym0;
+    if (iso) F0 += M.S * (R(0) - R(2) / R(3)) * R(1.5);
+    const R feq0 = M.pr * R(3) * (qw<R>(0) - R(1)) + rho * qw<R>(0) * (-R(1.5) * M.uu);
+    push<R, INNER, false>(g, c, out, P, 0, x, y, n,
+                          f[0] * omi + itau * feq0 + fcoef * qw<R>(0) * F0);
+  }
 #pragma unroll
-  for (int i = 0; i < 9; i++) {
+  for (int i = 1; i <= 8; i++) {
+    if (i == 3 || i == 4 || i == 7 || i == 8) continue;  // handled with its pair
+    const int o = qopp(i);
+    const R wi = qw<R>(i);
     const R cu = R(qx(i)) * M.ux + R(qy(i)) * M.uy;
-    const R si = qw<R>(i) * (R(3) * cu + R(4.5) * cu * cu - R(1.5) * M.uu);
-    const R feq = M.pr * R(3) * (qw<R>(i) - (i == 0 ? R(1) : R(0))) + rho * si;
     const R cF = R(qx(i)) * M.Gx + R(qy(i)) * M.Gy;
     const R cFt = R(qx(i)) * M.Ftx + R(qy(i)) * M.Fty;
-    R tens = R(2) * cu * cFt - R(2) / R(3) * M.uFt;
-    if (iso) tens += M.S / R(3) * (R(qx(i) * qx(i) + qy(i) * qy(i)) - R(2) / R(3));
-    const R Fi = qw<R>(i) * (M.S + R(3) * cF + R(4.5) * tens);
-    const R post = f[i] - (f[i] - feq) * itau + fcoef * Fi;
-    push<R, INNER, false>(g, c, out, P, i, x, y, n, post);
+    // even parts (equilibrium and source), odd parts
+    const R eqS = M.pr * R(3) + rho * (R(4.5) * cu * cu) + sym0;
+    const R eqA = rho * (R(3) * cu);
+    R srcS = fsym0 + R(9) * cu * cFt;
+    if (iso) srcS += M.S * (R(qx(i) * qx(i) + qy(i) * qy(i)) - R(2) / R(3)) * R(1.5);
+    const R srcA = R(3) * cF;
+    const R Ps = wi * (itau * eqS + fcoef * srcS);
+    const R Pa = wi * (itau * eqA + fcoef * srcA);
+    push<R, INNER, false>(g, c, out, P, i, x, y, n, f[i] * omi + Ps + Pa);
+    push<R, INNER, false>(g, c, out, P, o, x, y, n, f[o] * omi + Ps - Pa);
   }
 }
 
@@ -86,17 +115,28 @@ __device__ __forceinline__ void collide_phase(const Geom& g, const Coef<R>& c,
                                               const R* gq, R phi, R mdot, R phuxp, R phuyp,
                                               const Macro<R>& M) {
   const R itg = qdiv(R(1), c.tau_g);
+  const R omg = R(1) - itg;
   const R gcoef = R(1) - R(0.5) * itg;
-  const R dphx = M.phux - phuxp, dphy = M.phuy - phuyp;
   const R emu = c.eta * M.muphi;
+  // even part per unit weight: itg * eta mu + gcoef * phi mdot;
+  // odd part: 3 c_i . (itg * phi u + gcoef * d(phi u)/dt)
+  const R Zs = itg * emu + gcoef * phi * mdot;
+  const R Vx = R(3) * (itg * M.phux + gcoef * (M.phux - phuxp));
+  const R Vy = R(3) * (itg * M.phuy + gcoef * (M.phuy - phuyp));
+  {
+    const R geq0 = phi + (qw<R>(0) - R(1)) * emu;
+    push<R, INNER, false>(g, c, out, P, 0, x, y, n,
+                          gq[0] * omg + itg * geq0 + gcoef * qw<R>(0) * phi * mdot);
+  }
 #pragma unroll
-  for (int i = 0; i < 9; i++) {
+  for (int i = 1; i <= 8; i++) {
+    if (i == 3 || i == 4 || i == 7 || i == 8) continue;
+    const int o = qopp(i);
     const R wi = qw<R>(i);
-    const R cph = R(qx(i)) * M.phux + R(qy(i)) * M.phuy;
-    const R geq = (i == 0) ? phi + (wi - R(1)) * emu : wi * emu + wi * R(3) * cph;
-    const R Gi = wi * (R(qx(i)) * dphx + R(qy(i)) * dphy) * R(3) + wi * phi * mdot;
-    const R post = gq[i] - (gq[i] - geq) * itg + gcoef * Gi;
-    push<R, INNER, false>(g, c, out, P, i, x, y, n, post);
+    const R Ps = wi * Zs;
+    const R Pa = wi * (R(qx(i)) * Vx + R(qy(i)) * Vy);
+    push<R, INNER, false>(g, c, out, P, i, x, y, n, gq[i] * omg + Ps + Pa);
+    push<R, INNER, false>(g, c, out, P, o, x, y, n, gq[o] * omg + Ps - Pa);
   }
 }
 
@@ -110,24 +150,34 @@ __device__ __forceinline__ void collide_heat(const Geom& g, const Coef<R>& c, R*
   const R taus = qdiv(taua, R(2) * taua - R(1));
   const R ia = qdiv(R(1), taua), is = qdiv(R(1), taus);
   const R hcoef = R(1) - R(0.5) * ia;
-  const R rrC = qdiv(c.rr, M.cap);
-  const R Hsrc = M.cap * T * mdot;
-  R he[9];
+  const R CT = M.cap * T;
+  const R Hsrc = hcoef * CT * mdot;
+  const R rrT = c.rr * T;
+  {
+    // rest population: purely symmetric
+    const R heq0 = rhoH - rrT + qw<R>(0) * (rrT - CT * M.uu * R(1.5));
+    push<R, INNER, true>(g, c, out, P, 0, x, y, n,
+                         h[0] - (h[0] - heq0) * is + qw<R>(0) * Hsrc);
+  }
 #pragma unroll
-  for (int i = 0; i < 9; i++) he[i] = heq_i<R>(i, rhoH, M.cap, T, c.rr, rrC, M.ux, M.uy, M.uu);
-#pragma unroll
-  for (int i = 0; i < 9; i++) {
+  for (int i = 1; i <= 8; i++) {
+    if (i == 3 || i == 4 || i == 7 || i == 8) continue;
     const int o = qopp(i);
+    const R wi = qw<R>(i);
+    const R cu = R(qx(i)) * M.ux + R(qy(i)) * M.uy;
+    const R es = wi * (rrT + CT * (R(4.5) * cu * cu - R(1.5) * M.uu));
+    const R ea = wi * (CT * (R(3) * cu));
     const R hs = R(0.5) * (h[i] + h[o]), ha = R(0.5) * (h[i] - h[o]);
-    const R es = R(0.5) * (he[i] + he[o]), ea = R(0.5) * (he[i] - he[o]);
-    const R post = h[i] - (ha - ea) * ia - (hs - es) * is + hcoef * qw<R>(i) * Hsrc;
-    push<R, INNER, true>(g, c, out, P, i, x, y, n, post);
+    const R Da = (ha - ea) * ia;
+    const R Ds = (hs - es) * is - wi * Hsrc;
+    push<R, INNER, true>(g, c, out, P, i, x, y, n, h[i] - Da - Ds);
+    push<R, INNER, true>(g, c, out, P, o, x, y, n, h[o] + Da - Ds);
   }
 }
 
 // LATC: compile-time lattice set (7 = all three) or 0 (read at run time).
 template <typename R, int MODE, bool DIAG, int LATC>
-__global__ void __launch_bounds__(NT, sizeof(R) == 4 ? 3 : 1)
+__global__ void __launch_bounds__(NT, sizeof(R) == 4 ? LBM_MIN_BLOCKS_F32 : 1)
     lbm_step_kernel(const Args<R> a) {
   const Geom& g = a.g;
   const Coef<R>& c = a.c;
