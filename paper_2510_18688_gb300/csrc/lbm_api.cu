@@ -15,6 +15,7 @@
 #include <cuda_runtime.h>
 
 #include "../../include/lbm.h"
+#include "lbm_host.h"
 #include "lbm_launch.h"
 
 using lbmk::Args;
@@ -66,91 +67,6 @@ int fail(lbm_ctx* c, int code, const char* fmt, const char* detail = "") {
 int cuda_fail(lbm_ctx* c, cudaError_t e, const char* what) {
   if (c) std::snprintf(c->err, sizeof(c->err), "%s: %s", what, cudaGetErrorString(e));
   return e == cudaErrorMemoryAllocation ? LBM_ERR_OOM : LBM_ERR_CUDA;
-}
-
-bool positive(double v) { return std::isfinite(v) && v > 0.0; }
-
-template <typename R>
-Coef<R> make_coef(const lbm_params& p) {
-  Coef<R> c;
-  const double pi = 3.14159265358979323846;
-  c.rho_l = (R)p.rho_l; c.rho_s = (R)p.rho_s; c.rho_g = (R)p.rho_g;
-  c.mu_l = (R)p.mu_l; c.mu_s = (R)p.mu_s; c.mu_g = (R)p.mu_g;
-  c.lam_l = (R)p.lambda_l; c.lam_s = (R)p.lambda_s; c.lam_g = (R)p.lambda_g;
-  c.cp_l = (R)p.cp_l; c.cp_s = (R)p.cp_s; c.cp_g = (R)p.cp_g;
-  // Cp_ref = 2 Cp_s Cp_l / (Cp_s + Cp_l) (Sec. 3.3)
-  c.rr = (R)(p.rho_ref * (2.0 * p.cp_s * p.cp_l / (p.cp_s + p.cp_l)));
-  c.latent = (R)p.latent;
-  c.sigma = (R)p.sigma;
-  c.eps = (R)p.eps;
-  c.eta = (R)p.eta;
-  c.cos_th = (R)std::cos(p.theta_deg * pi / 180.0);
-  c.cos_ps = (R)std::cos(p.psi_deg * pi / 180.0);
-  c.gx = (R)p.gx;
-  c.gy = (R)p.gy;
-  c.tau_g = (R)(0.5 + p.mobility / (p.eta / 3.0));  // Eq. (21)
-  c.T_cold = (R)p.T_cold;
-  c.one_m_ratio = (R)(1.0 - p.rho_s / p.rho_l);
-  for (int k = 0; k < 4; k++) c.T_wall[k] = (R)p.T_wall[k];
-  c.readings = p.readings;
-  return c;
-}
-
-int validate(const lbm_params* p, char* err, size_t n) {
-  if (!p) return LBM_ERR_ARG;
-  if (p->nx < 2 || p->ny < 2) {
-    std::snprintf(err, n, "grid must be at least 2 x 2 (got %d x %d)", p->nx, p->ny);
-    return LBM_ERR_ARG;
-  }
-  // the kernels index the 27 population planes with 32-bit offsets
-  const long long plane = ((long long)((p->nx + 31) / 32 * 32) * p->ny + 63) / 64 * 64;
-  if (plane * 27 >= (1LL << 31)) {
-    std::snprintf(err, n, "grid of %d x %d nodes is too large", p->nx, p->ny);
-    return LBM_ERR_ARG;
-  }
-  if (p->precision != LBM_FP32 && p->precision != LBM_FP64) {
-    std::snprintf(err, n, "unknown precision %d", p->precision);
-    return LBM_ERR_ARG;
-  }
-  if (p->lattices == 0 || (p->lattices & ~7u)) {
-    std::snprintf(err, n, "lattices must be a nonzero subset of flow|phase|heat (got %u)",
-                  p->lattices);
-    return LBM_ERR_ARG;
-  }
-  for (int k = 0; k < 4; k++) {
-    if (p->bc[k] < LBM_BC_PERIODIC || p->bc[k] > LBM_BC_ADIABATIC) {
-      std::snprintf(err, n, "unknown boundary type %d on side %d", p->bc[k], k);
-      return LBM_ERR_ARG;
-    }
-  }
-  if ((p->bc[0] == LBM_BC_PERIODIC) != (p->bc[1] == LBM_BC_PERIODIC) ||
-      (p->bc[2] == LBM_BC_PERIODIC) != (p->bc[3] == LBM_BC_PERIODIC)) {
-    std::snprintf(err, n, "a periodic side needs a periodic opposite side");
-    return LBM_ERR_ARG;
-  }
-  if (p->diag_every < 0) {
-    std::snprintf(err, n, "diag_every must be >= 0");
-    return LBM_ERR_ARG;
-  }
-  const double props[] = {p->rho_l, p->rho_s,    p->rho_g,    p->mu_l,     p->mu_s,
-                          p->mu_g,  p->lambda_l, p->lambda_s, p->lambda_g, p->cp_l,
-                          p->cp_s,  p->cp_g,     p->rho_ref,  p->eps,      p->mobility,
-                          p->eta};
-  for (double v : props) {
-    // every relaxation time of Sec. 3 is 1/2 plus a positive property ratio,
-    // so positivity of the properties is what keeps tau > 1/2
-    if (!positive(v)) {
-      std::snprintf(err, n, "densities, viscosities, conductivities, heat capacities, "
-                            "rho_ref, eps, mobility and eta must be positive and finite");
-      return LBM_ERR_PARAM;
-    }
-  }
-  if (!(std::isfinite(p->latent) && p->latent >= 0.0) ||
-      !(std::isfinite(p->sigma) && p->sigma >= 0.0)) {
-    std::snprintf(err, n, "latent heat and surface tension must be finite and >= 0");
-    return LBM_ERR_PARAM;
-  }
-  return LBM_OK;
 }
 
 template <typename R>
@@ -219,7 +135,7 @@ int lbm_create(const lbm_params* params, lbm_ctx** out) {
   if (!params || !out) return LBM_ERR_ARG;
   *out = nullptr;
   char err[512] = {0};
-  int st = validate(params, err, sizeof(err));
+  int st = lbmh::validate(params, err, sizeof(err));
   if (st != LBM_OK) {
     std::fprintf(stderr, "lbm_create: %s\n", err);
     return st;
@@ -229,16 +145,9 @@ int lbm_create(const lbm_params* params, lbm_ctx** out) {
   std::memset(c, 0, sizeof(*c));
   c->p = *params;
   c->esize = params->precision == LBM_FP32 ? sizeof(float) : sizeof(double);
-  c->g.nx = params->nx;
-  c->g.ny = params->ny;
-  c->g.pitch = (params->nx + 31) / 32 * 32;
-  long long plane = (long long)c->g.pitch * params->ny;
-  c->g.plane = (plane + 63) / 64 * 64;
-  c->g.lattices = (int)params->lattices;
-  for (int k = 0; k < 4; k++) c->g.bc[k] = params->bc[k];
-  c->g.has_mask = 0;
-  c->cf = make_coef<float>(*params);
-  c->cd = make_coef<double>(*params);
+  c->g = lbmh::make_geom(*params);
+  c->cf = lbmh::make_coef<float>(*params);
+  c->cd = lbmh::make_coef<double>(*params);
   const dim3 gd = lbmk::grid_dims(c->g);
   c->nblocks = (int)(gd.x * gd.y);
   const size_t P = (size_t)c->g.plane;
