@@ -186,6 +186,49 @@ const char* lbm_status_string(int status);
 /* Frees the context and all memory it owns (NULL is allowed). */
 void lbm_destroy(lbm_ctx* ctx);
 
+/* Largest grid lbm_diagnostics_noalloc accepts, in tiles of 32 x 8 nodes
+ * (4096 tiles = 1,048,576 nodes, e.g. 1024 x 1024). */
+#define LBM_NOALLOC_MAX_BLOCKS 4096
+
+/* Diagnostics of a state the caller holds, without any device allocation.
+ * The paper has no counterpart: this is a service of the library.
+ *
+ * Who needs it: callers that may not call cudaMalloc -- code that runs inside
+ * a framework whose caching allocator or fixed memory pool owns all device
+ * memory, latency-critical loops where the implicit synchronisation of an
+ * allocation is not acceptable, and plug-ins that are handed device buffers
+ * but are not allowed to create their own.  Everything else should use a
+ * context and lbm_compute_diagnostics.
+ *
+ * Inputs (device memory of the current device, element type float for
+ * LBM_FP32 and double for LBM_FP64 in params->precision): `pops`, 27 planes
+ * in the order f0..f8, g0..g8, h0..h8; `lags`, 6 planes in the order fl, w,
+ * p, phi ux, phi uy, Q; `phi0`, one plane; `cold_mask`, one plane of bytes or
+ * NULL.  A plane holds ny rows of pitch elements, pitch = nx rounded up to a
+ * multiple of 32, and planes start every `plane` elements, plane =
+ * pitch * ny rounded up to a multiple of 64.  This is the layout that
+ * lbm_save_state writes after its header.  Output: `out`, device memory for
+ * 10 doubles, receives the nine sums of lbm_diag in declaration order and 0.
+ *
+ * Scratch: the per-tile partial sums and a completion counter live in one
+ * static device array of LBM_NOALLOC_MAX_BLOCKS * 9 + 1 doubles (about
+ * 288 KB) that every device which loads the library keeps until the process
+ * exits.  The counter is cleared on `stream` before each launch; all calls
+ * share the array, so calls whose work overlaps on the GPU (different
+ * streams without ordering) race and give wrong sums.  The first call on a
+ * device looks up the array's device address (cudaGetSymbolAddress), so make
+ * that first call before any stream capture.  Enqueues on `stream`; does not
+ * synchronise.
+ *
+ * Errors: LBM_ERR_ARG for a null pointer or invalid grid, LBM_ERR_PARAM for
+ * invalid parameters (the checks of lbm_create), LBM_ERR_UNSUPPORTED for a
+ * grid of more than LBM_NOALLOC_MAX_BLOCKS tiles (message on stderr),
+ * LBM_ERR_CUDA if the address lookup or the launch fails.  No call to
+ * cudaMalloc, cudaFree or any allocating library routine is made. */
+int lbm_diagnostics_noalloc(const lbm_params* params, const void* pops, const void* lags,
+                            const void* phi0, const uint8_t* cold_mask, double* out,
+                            void* stream);
+
 #ifdef __cplusplus
 }
 #endif

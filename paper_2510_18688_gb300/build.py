@@ -24,6 +24,7 @@ UNITS = {
     "lbm_api.cu": [],
     "lbm_f32.cu": [],
     "lbm_f64.cu": ["--fmad=false"],
+    "lbm_static.cu": [],
 }
 
 

@@ -53,7 +53,7 @@ class LbmDiag(ctypes.Structure):
 EXPORTS = ("lbm_create", "lbm_set_geometry", "lbm_step", "lbm_read_fields",
            "lbm_compute_diagnostics", "lbm_read_diagnostics", "lbm_state_size",
            "lbm_save_state", "lbm_load_state", "lbm_step_count", "lbm_last_error",
-           "lbm_status_string", "lbm_destroy")
+           "lbm_status_string", "lbm_destroy", "lbm_diagnostics_noalloc")
 
 _lib = None
 
@@ -85,9 +85,10 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     L.lbm_status_string.restype = ctypes.c_char_p
     L.lbm_destroy.argtypes = [vp]
     L.lbm_destroy.restype = None
+    L.lbm_diagnostics_noalloc.argtypes = [ctypes.POINTER(LbmParams), vp, vp, vp, vp, vp, vp]
     for fn in ("lbm_create", "lbm_set_geometry", "lbm_step", "lbm_read_fields",
                "lbm_compute_diagnostics", "lbm_read_diagnostics", "lbm_state_size",
-               "lbm_save_state", "lbm_load_state"):
+               "lbm_save_state", "lbm_load_state", "lbm_diagnostics_noalloc"):
         getattr(L, fn).restype = ctypes.c_int
     _lib = L
     return L
@@ -176,6 +177,14 @@ def lbm_load_state(ctx, blob: bytes, stream=None):
 
 def lbm_step_count(ctx) -> int:
     return int(load().lbm_step_count(ctx))
+
+
+def lbm_diagnostics_noalloc(params: LbmParams, pops, lags, phi0, cold_mask, out,
+                            stream=None) -> int:
+    """Diagnostics of a caller-held device state without device allocation
+    (see include/lbm.h); returns the status code."""
+    return int(load().lbm_diagnostics_noalloc(ctypes.byref(params), pops, lags, phi0,
+                                              cold_mask, out, stream))
 
 
 def lbm_last_error(ctx) -> str:
