@@ -36,6 +36,28 @@ WORKLOAD = "sessile droplet freezing 512x512 (R=100, cold solid layer), 3 lattic
 L2_FLUSH_BYTES = 256 << 20
 
 
+def _droplet512(seed):
+    from paper_2510_18688_gb300 import workloads as W
+    return W.sessile_droplet(512, seed=seed)
+
+
+def _droplet1024(seed):
+    from paper_2510_18688_gb300 import workloads as W
+    return W.sessile_droplet(1024, seed=seed, radius=200.0)
+
+
+def _porous(seed):
+    from paper_2510_18688_gb300 import workloads as W
+    return W.porous(seed=seed)
+
+
+WORKLOADS = {
+    "droplet512": (_droplet512, "sessile droplet freezing 512x512 (R=100, cold solid layer), 3 lattices"),
+    "droplet1024": (_droplet1024, "sessile droplet freezing 1024x1024 (R=200, cold solid layer), 3 lattices"),
+    "porous2048x1024": (_porous, "freezing in a porous medium 2048x1024 (porosity 0.6, saturation 0.5), 3 lattices"),
+}
+
+
 def algorithmic_bytes_per_node(esize: int, has_mask: bool) -> int:
     """27 populations read and written, 6 lag fields read and written, phi0
     read, mask byte read."""
@@ -189,6 +211,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default="droplet512", choices=sorted(WORKLOADS),
+                    help="droplet512 is the headline; the others are context lines")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     rank, world, local = dist_env()
@@ -208,7 +232,8 @@ def main():
     build.build()
     L = lbm.load()
 
-    cfg, arr = W.sessile_droplet(512, seed=rank)
+    make, workload_name = WORKLOADS[args.workload]
+    cfg, arr = make(rank)
     n = cfg["nx"] * cfg["ny"]
     stream = torch.cuda.current_stream()
     sptr = ctypes.c_void_p(stream.cuda_stream)
@@ -255,8 +280,8 @@ def main():
 
     host_t = {k: pinned(arr[k], torch.float64) for k in ("phi0", "phi", "T", "fl")}
     host = {k: v.numpy() for k, v in host_t.items()}
-    hmask_t = pinned(arr["mask"], torch.uint8)
-    hmask = hmask_t.numpy()
+    hmask_t = pinned(arr["mask"], torch.uint8) if "mask" in arr else None
+    hmask = hmask_t.numpy() if hmask_t is not None else None
     outs_t = {k: torch.empty((cfg["ny"], cfg["nx"]), dtype=torch.float64, pin_memory=True)
               for k in ("phi", "fl", "T")}
     outs = {k: v.numpy() for k, v in outs_t.items()}
@@ -264,13 +289,14 @@ def main():
     fmask = lbm.FIELD_BIT["phi"] | lbm.FIELD_BIT["fl"] | lbm.FIELD_BIT["T"]
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    lbm.lbm_set_geometry(solver.ctx, host["phi0"].ctypes.data, hmask.ctypes.data,
+    lbm.lbm_set_geometry(solver.ctx, host["phi0"].ctypes.data,
+                         hmask.ctypes.data if hmask is not None else None,
                          host["phi"].ctypes.data, host["T"].ctypes.data, host["fl"].ctypes.data,
                          lbm.LBM_HOST, sptr)
     lbm.lbm_step(solver.ctx, args.steps, sptr)
     lbm.lbm_read_fields(solver.ctx, fmask, ptrs, lbm.LBM_HOST, sptr)
     e2e_s = time.perf_counter() - t0
-    h2d = 4 * n * 8 + n
+    h2d = 4 * n * 8 + (n if hmask is not None else 0)
     d2h = 3 * n * 8
     e2e = {"value": n * args.steps / e2e_s / 1e6, "unit": "MLUPS",
            "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": d2h / args.steps,
@@ -289,7 +315,7 @@ def main():
             pg.destroy_process_group()
         return
     esize = 4 if args.precision == "fp32" else 8
-    bpn = algorithmic_bytes_per_node(esize, True)
+    bpn = algorithmic_bytes_per_node(esize, "mask" in arr)
     peak, peak_src = measured_peak()
     achieved = bpn * n / (t_step * 1e-3) / 1e9
     value = world * n * args.steps / (t_tot * 1e-3) / 1e6
@@ -298,7 +324,8 @@ def main():
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_step,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32" if esize == 4 else "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "grid": [512, 512], "precision": args.precision,
+        "config": {"workload": workload_name + f", seed {rank}", "grid": [cfg["nx"], cfg["ny"]],
+                   "precision": args.precision,
                    "l2": "flushed before every timed step (256 MB write)",
                    "parallelism": f"replicas x{world}"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",

@@ -210,15 +210,15 @@ void lbm_destroy(lbm_ctx* ctx);
  * lbm_save_state writes after its header.  Output: `out`, device memory for
  * 10 doubles, receives the nine sums of lbm_diag in declaration order and 0.
  *
- * Scratch: the per-tile partial sums and a completion counter live in one
- * static device array of LBM_NOALLOC_MAX_BLOCKS * 9 + 1 doubles (about
- * 288 KB) that every device which loads the library keeps until the process
- * exits.  The counter is cleared on `stream` before each launch; all calls
- * share the array, so calls whose work overlaps on the GPU (different
- * streams without ordering) race and give wrong sums.  The first call on a
- * device looks up the array's device address (cudaGetSymbolAddress), so make
- * that first call before any stream capture.  Enqueues on `stream`; does not
- * synchronise.
+ * Scratch: the per-tile partial sums live in one static device array of
+ * LBM_NOALLOC_MAX_BLOCKS * 9 doubles (288 KB) that every device which loads
+ * the library keeps until the process exits.  Each call overwrites the slots
+ * it uses before a second kernel on `stream` sums them, so nothing needs
+ * clearing, but all calls share the array: calls whose work overlaps on the
+ * GPU (different streams without ordering) race and give wrong sums.  The
+ * first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress), so make that first call before any stream
+ * capture.  Enqueues on `stream`; does not synchronise.
  *
  * Errors: LBM_ERR_ARG for a null pointer or invalid grid, LBM_ERR_PARAM for
  * invalid parameters (the checks of lbm_create), LBM_ERR_UNSUPPORTED for a

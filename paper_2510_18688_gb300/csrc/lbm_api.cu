@@ -35,14 +35,17 @@ struct lbm_ctx {
   uint8_t* mask;
   double* diag_partial;
   double* diag_out;      // NDIAG + 1
-  unsigned* counter;
   double* staging;       // NFIELD * nx * ny doubles, for host reads (lazy)
   void* in_stage;        // 4 * nx * ny doubles + nx * ny bytes, for host inputs (lazy)
   double* h_diag;        // pinned, NDIAG + 1
+  void* scratch;         // NSCRATCH planes (phi, fs, rho) of the two-kernel step
+  bool split;            // step as macro + collide kernels, or fused (default)
   int cur;
   int64_t step;
   bool have_geometry;
   bool have_diag;
+  bool diag_pending;     // partials written, grid-wide sum not yet taken
+  int64_t diag_step;     // state index of the pending partials
   cudaStream_t last_stream;
   int nblocks;
   char err[512];
@@ -82,13 +85,22 @@ Args<R> step_args(lbm_ctx* c, const Coef<R>& coef) {
   a.phi0 = (const R*)c->phi0;
   a.mask = c->mask;
   a.diag_partial = c->diag_partial;
-  a.diag_out = c->diag_out;
-  a.diag_counter = c->counter;
-  a.step_index = c->step;
   return a;
 }
 
 cudaError_t launch(lbm_ctx* c, int mode, bool diag, double* const* outs, cudaStream_t s) {
+  if (mode == lbmk::MODE_STEP && c->split) {
+    if (c->p.precision == LBM_FP32) {
+      lbmk::SplitArgs<float> a;
+      a.a = step_args<float>(c, c->cf);
+      a.sc = (float*)c->scratch;
+      return lbmk::launch_split_f32(a, diag, s);
+    }
+    lbmk::SplitArgs<double> a;
+    a.a = step_args<double>(c, c->cd);
+    a.sc = (double*)c->scratch;
+    return lbmk::launch_split_f64(a, diag, s);
+  }
   if (c->p.precision == LBM_FP32) {
     Args<float> a = step_args<float>(c, c->cf);
     if (outs)
@@ -103,7 +115,8 @@ cudaError_t launch(lbm_ctx* c, int mode, bool diag, double* const* outs, cudaStr
 
 void free_all(lbm_ctx* c) {
   void* dev[] = {c->pop[0], c->pop[1], c->lag[0],     c->lag[1],    c->phi0,   c->mask,
-                 c->diag_partial, c->diag_out, c->counter, c->staging, c->in_stage};
+                 c->diag_partial, c->diag_out, c->staging, c->in_stage,
+                 c->scratch};
   for (void* p : dev)
     if (p) cudaFree(p);
   if (c->h_diag) cudaFreeHost(c->h_diag);
@@ -146,6 +159,12 @@ int lbm_create(const lbm_params* params, lbm_ctx** out) {
   c->p = *params;
   c->esize = params->precision == LBM_FP32 ? sizeof(float) : sizeof(double);
   c->g = lbmh::make_geom(*params);
+  {
+    // LBM_STEP_KERNEL=split selects the two-kernel step (macro pass +
+    // collide pass); the default is the fused one-kernel step
+    const char* k = std::getenv("LBM_STEP_KERNEL");
+    c->split = k && std::strcmp(k, "split") == 0;
+  }
   c->cf = lbmh::make_coef<float>(*params);
   c->cd = lbmh::make_coef<double>(*params);
   const dim3 gd = lbmk::grid_dims(c->g);
@@ -157,12 +176,11 @@ int lbm_create(const lbm_params* params, lbm_ctx** out) {
     if (e == cudaSuccess) e = cudaMalloc(&c->lag[b], lbmk::NLAG * P * c->esize);
   }
   if (e == cudaSuccess) e = cudaMalloc(&c->phi0, P * c->esize);
+  if (e == cudaSuccess) e = cudaMalloc(&c->scratch, lbmk::NSCRATCH * P * c->esize);
   if (e == cudaSuccess) e = cudaMalloc(&c->mask, P);
   if (e == cudaSuccess)
     e = cudaMalloc(&c->diag_partial, (size_t)lbmk::NDIAG * c->nblocks * sizeof(double));
   if (e == cudaSuccess) e = cudaMalloc(&c->diag_out, (lbmk::NDIAG + 1) * sizeof(double));
-  if (e == cudaSuccess) e = cudaMalloc(&c->counter, sizeof(unsigned));
-  if (e == cudaSuccess) e = cudaMemset(c->counter, 0, sizeof(unsigned));
   if (e == cudaSuccess) e = cudaMemset(c->mask, 0, P);
   if (e == cudaSuccess) e = cudaHostAlloc(&c->h_diag, (lbmk::NDIAG + 1) * sizeof(double), 0);
   if (e == cudaSuccess) e = cudaDeviceSynchronize();
@@ -244,6 +262,7 @@ int lbm_set_geometry(lbm_ctx* c, const double* phi0, const uint8_t* cold_mask,
   c->step = 0;
   c->have_geometry = true;
   c->have_diag = false;
+  c->diag_pending = false;
   c->last_stream = s;
   return LBM_OK;
 }
@@ -257,7 +276,11 @@ int lbm_step(lbm_ctx* c, int64_t nsteps, void* stream) {
     const bool diag = c->p.diag_every > 0 && (c->step % c->p.diag_every) == 0;
     cudaError_t e = launch(c, lbmk::MODE_STEP, diag, nullptr, s);
     if (e != cudaSuccess) return cuda_fail(c, e, "step kernel launch");
-    if (diag) c->have_diag = true;
+    if (diag) {
+      c->have_diag = true;
+      c->diag_pending = true;
+      c->diag_step = c->step;
+    }
     c->cur ^= 1;
     c->step++;
   }
@@ -311,6 +334,8 @@ int lbm_compute_diagnostics(lbm_ctx* c, void* stream) {
   cudaError_t e = launch(c, lbmk::MODE_READ, true, nullptr, s);
   if (e != cudaSuccess) return cuda_fail(c, e, "diagnostics kernel launch");
   c->have_diag = true;
+  c->diag_pending = true;
+  c->diag_step = c->step;
   c->last_stream = s;
   return LBM_OK;
 }
@@ -318,7 +343,14 @@ int lbm_compute_diagnostics(lbm_ctx* c, void* stream) {
 int lbm_read_diagnostics(lbm_ctx* c, lbm_diag* out) {
   if (!c || !out) return LBM_ERR_ARG;
   if (!c->have_diag) return fail(c, LBM_ERR_STATE, "no diagnostics computed yet%s");
-  cudaError_t e = cudaMemcpyAsync(c->h_diag, c->diag_out, (lbmk::NDIAG + 1) * sizeof(double),
+  cudaError_t e = cudaSuccess;
+  if (c->diag_pending) {
+    e = lbmk::launch_diag_finalize(c->diag_partial, c->nblocks, c->diag_out, c->diag_step,
+                                   c->last_stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "diagnostics finalize launch");
+    c->diag_pending = false;
+  }
+  e = cudaMemcpyAsync(c->h_diag, c->diag_out, (lbmk::NDIAG + 1) * sizeof(double),
                                   cudaMemcpyDeviceToHost, c->last_stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(c->last_stream);
   if (e != cudaSuccess) return cuda_fail(c, e, "diagnostics download");
@@ -386,6 +418,7 @@ int lbm_load_state(lbm_ctx* c, const void* host_buf, size_t size, void* stream) 
   if (e != cudaSuccess) return cuda_fail(c, e, "state upload");
   c->step = h.step;
   c->have_diag = false;
+  c->diag_pending = false;
   c->last_stream = s;
   return LBM_OK;
 }

@@ -25,8 +25,29 @@ cudaError_t launch_step_f64(const Args<double>& a, int mode, bool diag, cudaStre
   return cudaGetLastError();
 }
 
+cudaError_t launch_split_f64(const SplitArgs<double>& a, bool diag, cudaStream_t s) {
+  const dim3 grid = grid_dims(a.a.g), block = block_dims();
+  const bool all = a.a.g.lattices == (LAT_FLOW | LAT_PHASE | LAT_HEAT);
+  if (all) lbm_macro_kernel<double, 7><<<grid, block, 0, s>>>(a);
+  else lbm_macro_kernel<double, 0><<<grid, block, 0, s>>>(a);
+  if (all) {
+    if (diag) lbm_collide_kernel<double, true, 7><<<grid, block, 0, s>>>(a);
+    else lbm_collide_kernel<double, false, 7><<<grid, block, 0, s>>>(a);
+  } else {
+    if (diag) lbm_collide_kernel<double, true, 0><<<grid, block, 0, s>>>(a);
+    else lbm_collide_kernel<double, false, 0><<<grid, block, 0, s>>>(a);
+  }
+  return cudaGetLastError();
+}
+
 cudaError_t launch_init_f64(const InitArgs<double>& a, cudaStream_t s) {
   lbm_init_kernel<double><<<grid_dims(a.g), block_dims(), 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_diag_finalize(const double* partial, int nb, double* out, long long step,
+                                 cudaStream_t s) {
+  lbm_diag_finalize_kernel<<<1, NT, 0, s>>>(partial, nb, out, step);
   return cudaGetLastError();
 }
 

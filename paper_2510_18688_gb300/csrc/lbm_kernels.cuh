@@ -94,10 +94,7 @@ struct Args {
   const R* __restrict__ phi0;
   const uint8_t* __restrict__ mask;
   double* out[NFIELD];         // MODE_READ: dense [ny][nx] outputs (or null)
-  double* diag_partial;        // [NDIAG][nblocks]
-  double* diag_out;            // NDIAG values + step index (as double)
-  unsigned* diag_counter;
-  long long step_index;
+  double* diag_partial;        // [NDIAG][nblocks] per-CTA partial sums
 };
 
 template <typename R>
@@ -284,6 +281,60 @@ __device__ __forceinline__ R warp_sum(R v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   return v;
+}
+
+// Per-CTA partial sums of the diagnostics in a fixed order (warp shuffles,
+// then the warps in order), written to partial[k * nb + b].  Every thread of
+// the CTA calls it.  The grid-wide sum is lbm_diag_finalize_kernel.
+template <typename R>
+__device__ __forceinline__ void block_diag(const R* dvals, double (*s_red)[NDIAG],
+                                           double* __restrict__ partial, int tid) {
+  const int lane = tid & 31, warp = tid >> 5;
+#pragma unroll
+  for (int k = 0; k < NDIAG; k++) {
+    const R v = warp_sum(dvals[k]);
+    if (lane == 0) s_red[warp][k] = (double)v;
+  }
+  __syncthreads();
+  if (tid < NDIAG) {
+    const int nb = gridDim.x * gridDim.y;
+    const int b = blockIdx.y * gridDim.x + blockIdx.x;
+    double acc = 0.0;
+#pragma unroll
+    for (int w = 0; w < NT / 32; w++) acc += s_red[w][tid];
+    partial[(long long)tid * nb + b] = acc;
+  }
+}
+
+// Grid-wide FP64 diagnostics from the per-CTA partials, one CTA, fixed order
+// (bitwise reproducible): out[0..NDIAG-1] = sums, out[NDIAG] = step index.
+static __global__ void __launch_bounds__(NT) lbm_diag_finalize_kernel(const double* __restrict__ partial,
+                                                               int nb, double* __restrict__ out,
+                                                               long long step) {
+  __shared__ double s_red[NT / 32][NDIAG];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  double acc[NDIAG];
+#pragma unroll
+  for (int k = 0; k < NDIAG; k++) acc[k] = 0.0;
+  for (int j = tid; j < nb; j += NT) {
+#pragma unroll
+    for (int k = 0; k < NDIAG; k++) acc[k] += partial[(long long)k * nb + j];
+  }
+#pragma unroll
+  for (int k = 0; k < NDIAG; k++) {
+    double v = acc[k];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (lane == 0) s_red[warp][k] = v;
+  }
+  __syncthreads();
+  if (tid < NDIAG) {
+    double t = 0.0;
+#pragma unroll
+    for (int w = 0; w < NT / 32; w++) t += s_red[w][tid];
+    out[tid] = t;
+  }
+  if (tid == 0) out[NDIAG] = (double)step;
 }
 
 // ---------------------------------------------------------------------------

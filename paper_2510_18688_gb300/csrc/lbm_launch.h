@@ -6,6 +6,7 @@
 
 #include "lbm_kernels.cuh"
 #include "lbm_step.cuh"
+#include "lbm_split.cuh"
 
 namespace lbmk {
 
@@ -17,7 +18,13 @@ inline dim3 grid_dims(const Geom& g) {
 // MODE_STEP or MODE_READ, with or without the fused diagnostics.
 cudaError_t launch_step_f32(const Args<float>& a, int mode, bool diag, cudaStream_t s);
 cudaError_t launch_step_f64(const Args<double>& a, int mode, bool diag, cudaStream_t s);
+// Two-kernel form of MODE_STEP (macro pass, then collide pass).
+cudaError_t launch_split_f32(const SplitArgs<float>& a, bool diag, cudaStream_t s);
+cudaError_t launch_split_f64(const SplitArgs<double>& a, bool diag, cudaStream_t s);
 cudaError_t launch_init_f32(const InitArgs<float>& a, cudaStream_t s);
+// Grid-wide diagnostics from the per-CTA partials (one CTA).
+cudaError_t launch_diag_finalize(const double* partial, int nb, double* out, long long step,
+                                 cudaStream_t s);
 cudaError_t launch_init_f64(const InitArgs<double>& a, cudaStream_t s);
 
 }  // namespace lbmk

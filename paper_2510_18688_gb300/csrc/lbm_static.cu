@@ -1,11 +1,11 @@
 // lbm_static.cu -- the allocation-free entry point lbm_diagnostics_noalloc.
 //
 // It runs the same read-out kernel with fused diagnostics as
-// lbm_compute_diagnostics, on a state the caller already holds in device
-// memory, with the kernel's scratch (one FP64 partial per diagnostic per
-// CTA, and the completion counter of the last-block reduction) in a
-// file-scope device array instead of context-owned memory.  Nothing here
-// calls cudaMalloc, cudaFree or any allocating routine.
+// lbm_compute_diagnostics, and the same one-CTA finalize kernel, on a state
+// the caller already holds in device memory, with the scratch (one FP64
+// partial per diagnostic per CTA) in a file-scope device array instead of
+// context-owned memory.  Nothing here calls cudaMalloc, cudaFree or any
+// allocating routine.
 #include <cstdio>
 #include <cstring>
 
@@ -21,8 +21,9 @@ namespace {
 // (1,048,576 nodes, e.g. 1024 x 1024).
 constexpr int kMaxBlocks = LBM_NOALLOC_MAX_BLOCKS;
 constexpr size_t kPartials = (size_t)lbmk::NDIAG * kMaxBlocks;
-// partials, then one slot whose first four bytes hold the counter
-static __device__ __align__(256) double g_noalloc_scratch[kPartials + 1];
+// per-CTA partial sums; every launch overwrites the slots it uses, so
+// nothing has to be cleared between calls
+static __device__ __align__(256) double g_noalloc_scratch[kPartials];
 
 constexpr int kMaxDevices = 64;
 double* g_scratch_addr[kMaxDevices] = {nullptr};
@@ -74,12 +75,8 @@ extern "C" int lbm_diagnostics_noalloc(const lbm_params* params, const void* pop
                  cudaGetErrorString(e));
     return LBM_ERR_CUDA;
   }
-  unsigned* counter = (unsigned*)(scratch + kPartials);
   cudaStream_t s = (cudaStream_t)stream;
-  // the completion counter must start at zero (the kernel leaves it at zero,
-  // an interrupted earlier launch might not have)
-  e = cudaMemsetAsync(counter, 0, sizeof(unsigned), s);
-  if (e == cudaSuccess) {
+  {
     if (params->precision == LBM_FP32) {
       lbmk::Args<float> a;
       std::memset(&a, 0, sizeof(a));
@@ -90,9 +87,6 @@ extern "C" int lbm_diagnostics_noalloc(const lbm_params* params, const void* pop
       a.phi0 = (const float*)phi0;
       a.mask = cold_mask;
       a.diag_partial = scratch;
-      a.diag_out = out;
-      a.diag_counter = counter;
-      a.step_index = 0;
       e = lbmk::launch_step_f32(a, lbmk::MODE_READ, true, s);
     } else {
       lbmk::Args<double> a;
@@ -104,12 +98,10 @@ extern "C" int lbm_diagnostics_noalloc(const lbm_params* params, const void* pop
       a.phi0 = (const double*)phi0;
       a.mask = cold_mask;
       a.diag_partial = scratch;
-      a.diag_out = out;
-      a.diag_counter = counter;
-      a.step_index = 0;
       e = lbmk::launch_step_f64(a, lbmk::MODE_READ, true, s);
     }
   }
+  if (e == cudaSuccess) e = lbmk::launch_diag_finalize(scratch, (int)nb, out, 0, s);
   if (e != cudaSuccess) {
     std::fprintf(stderr, "lbm_diagnostics_noalloc: launch failed: %s\n", cudaGetErrorString(e));
     return LBM_ERR_CUDA;

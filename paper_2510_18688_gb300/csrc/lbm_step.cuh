@@ -189,7 +189,6 @@ __global__ void __launch_bounds__(NT, sizeof(R) == 4 ? LBM_MIN_BLOCKS_F32 : 1)
   __shared__ R s_rfl[RING], s_rw[RING], s_rQ[RING];
   __shared__ int s_rmask[RING];
   __shared__ double s_red[NT / 32][NDIAG];
-  __shared__ int s_last;
 
   const int tx = threadIdx.x, ty = threadIdx.y;
   const int tid = ty * TX + tx;
@@ -447,57 +446,7 @@ __global__ void __launch_bounds__(NT, sizeof(R) == 4 ? LBM_MIN_BLOCKS_F32 : 1)
     for (int k = 0; k < NDIAG; k++) dvals[k] = R(0);
   }
 
-  if (DIAG) {
-    // warp sums in R, then per-block and a last-block pass in FP64, all in a
-    // fixed order
-    const int lane = tid & 31, warp = tid >> 5;
-#pragma unroll
-    for (int k = 0; k < NDIAG; k++) {
-      const R v = warp_sum(dvals[k]);
-      if (lane == 0) s_red[warp][k] = (double)v;
-    }
-    __syncthreads();
-    const int nb = gridDim.x * gridDim.y;
-    const int b = blockIdx.y * gridDim.x + blockIdx.x;
-    if (tid < NDIAG) {
-      double s = 0.0;
-#pragma unroll
-      for (int w = 0; w < NT / 32; w++) s += s_red[w][tid];
-      a.diag_partial[(long long)tid * nb + b] = s;
-      __threadfence();  // publish the partial before the ticket
-    }
-    __syncthreads();
-    if (tid == 0) s_last = (atomicAdd(a.diag_counter, 1u) == (unsigned)(nb - 1));
-    __syncthreads();
-    if (s_last) {
-      __threadfence();
-      double acc[NDIAG];
-#pragma unroll
-      for (int k = 0; k < NDIAG; k++) acc[k] = 0.0;
-      for (int j = tid; j < nb; j += NT) {
-#pragma unroll
-        for (int k = 0; k < NDIAG; k++) acc[k] += __ldcg(&a.diag_partial[(long long)k * nb + j]);
-      }
-#pragma unroll
-      for (int k = 0; k < NDIAG; k++) {
-        double v = acc[k];
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-        if (lane == 0) s_red[warp][k] = v;
-      }
-      __syncthreads();
-      if (tid < NDIAG) {
-        double s = 0.0;
-#pragma unroll
-        for (int w = 0; w < NT / 32; w++) s += s_red[w][tid];
-        a.diag_out[tid] = s;
-      }
-      if (tid == 0) {
-        a.diag_out[NDIAG] = (double)a.step_index;
-        *a.diag_counter = 0u;
-      }
-    }
-  }
+  if (DIAG) block_diag(dvals, s_red, a.diag_partial, tid);
 }
 
 }  // namespace lbmk

@@ -82,6 +82,18 @@ def test_random_states(env, prec, seed, nx, ny):
 
 
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("seed", [0, 3])
+def test_two_kernel_step(env, prec, seed, monkeypatch):
+    """The two-kernel form of the step (macro pass, then collide pass),
+    selected with LBM_STEP_KERNEL=split when a context is created."""
+    monkeypatch.setenv("LBM_STEP_KERNEL", "split")
+    got, ref = _run_pair(env, W.random_state(53, 29, seed=seed), 90, prec)
+    _compare(got, ref, prec)
+    got, ref = _run_pair(env, W.random_state(47, 31, seed=seed, lattices=5), 40, prec)
+    _compare(got, ref, prec)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
 @pytest.mark.parametrize("lat", [1, 2, 4, 3, 5, 6])
 def test_lattice_subsets(env, prec, lat):
     """Flow, phase and enthalpy lattices switched on alone and in pairs."""
