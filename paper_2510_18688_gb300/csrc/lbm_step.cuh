@@ -184,6 +184,11 @@ __global__ void __launch_bounds__(NT, sizeof(R) == 4 ? LBM_MIN_BLOCKS_F32 : 1)
   const int lat = LATC ? LATC : g.lattices;
   const int P = (int)g.plane;  // 27 planes fit in 31 bits (checked at create)
 
+  // FP32 steps keep the own node's phase and enthalpy populations in shared
+  // memory between phase A and phase B (18 KB per CTA) instead of reading
+  // them again through L1/L2
+  constexpr bool STASH = sizeof(R) == 4 && MODE == MODE_STEP;
+  __shared__ R s_pop[STASH ? 18 : 1][NT];
   __shared__ R s_phi[HN], s_fs[HN], s_rho[HN], s_p[HN], s_phi0[HN];
   __shared__ R s_rsg[RING][NPART], s_rsh[RING][NPART];
   __shared__ R s_rfl[RING], s_rw[RING], s_rQ[RING];
@@ -257,8 +262,12 @@ __global__ void __launch_bounds__(NT, sizeof(R) == 4 ? LBM_MIN_BLOCKS_F32 : 1)
   if (lat & LAT_PHASE) {
     R v[9];
 #pragma unroll
-    for (int i = 0; i < 9; i++) v[i] = ld_sum(pn + (9 + i) * P);
+    for (int i = 0; i < 9; i++) v[i] = STASH ? pn[(9 + i) * P] : ld_sum(pn + (9 + i) * P);
     sg = sum_g(v);
+    if (STASH) {
+#pragma unroll
+      for (int i = 0; i < 9; i++) s_pop[i][tid] = v[i];
+    }
   }
   if (lat & LAT_HEAT) {
     R v[9];
@@ -266,9 +275,13 @@ __global__ void __launch_bounds__(NT, sizeof(R) == 4 ? LBM_MIN_BLOCKS_F32 : 1)
       cold_mask_h(c, wp, phi0, v);
     } else {
 #pragma unroll
-      for (int i = 0; i < 9; i++) v[i] = ld_sum(pn + (18 + i) * P);
+      for (int i = 0; i < 9; i++) v[i] = STASH ? pn[(18 + i) * P] : ld_sum(pn + (18 + i) * P);
     }
     sh = sum_h(v);
+    if (STASH) {
+#pragma unroll
+      for (int i = 0; i < 9; i++) s_pop[STASH ? 9 + i : 0][tid] = v[i];
+    }
   }
   const Local<R> L = local_state(c, lat, sg, sh, flp, wp, Qp, phi0);
   {
@@ -394,7 +407,7 @@ __global__ void __launch_bounds__(NT, sizeof(R) == 4 ? LBM_MIN_BLOCKS_F32 : 1)
       if (lat & LAT_PHASE) {
         R gq[9];
 #pragma unroll
-        for (int i = 0; i < 9; i++) gq[i] = pn[(9 + i) * P];
+        for (int i = 0; i < 9; i++) gq[i] = STASH ? s_pop[i][tid] : pn[(9 + i) * P];
         const R phuxp = a.lin[LAG_PHUX * P + n];
         const R phuyp = a.lin[LAG_PHUY * P + n];
         if (inner) collide_phase<R, true>(g, c, out + 9 * P, P, gx, gy, n, gq, phi, mdot, phuxp, phuyp, M);
@@ -402,7 +415,10 @@ __global__ void __launch_bounds__(NT, sizeof(R) == 4 ? LBM_MIN_BLOCKS_F32 : 1)
       }
       if (lat & LAT_HEAT) {
         R hq[9];
-        if (masked) {
+        if (STASH) {
+#pragma unroll
+          for (int i = 0; i < 9; i++) hq[i] = s_pop[STASH ? 9 + i : 0][tid];
+        } else if (masked) {
           cold_mask_h(c, wp, phi0, hq);
         } else {
 #pragma unroll
