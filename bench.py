@@ -211,6 +211,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--diag-every", type=int, default=1,
+                    help="steps between fused FP64 diagnostic reductions (row a9)")
     ap.add_argument("--workload", default="droplet512", choices=sorted(WORKLOADS),
                     help="droplet512 is the headline; the others are context lines")
     args = ap.parse_args()
@@ -237,7 +239,8 @@ def main():
     n = cfg["nx"] * cfg["ny"]
     stream = torch.cuda.current_stream()
     sptr = ctypes.c_void_p(stream.cuda_stream)
-    solver = lbm.Solver(cfg, precision=args.precision, diag_every=1).set_geometry(arr)
+    solver = lbm.Solver(cfg, precision=args.precision,
+                        diag_every=args.diag_every).set_geometry(arr)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
 
     for _ in range(args.warmup):
@@ -268,7 +271,8 @@ def main():
         t = torch.tensor([t_tot], device="cuda")
         pg.all_reduce(t, op=pg.ReduceOp.MAX)
         t_tot = float(t.item())
-    diag = solver.diagnostics(compute=False)
+    # the fused reduction of the last diagnosed step, or one on request
+    diag = solver.diagnostics(compute=args.diag_every == 0)
 
     # end to end through the C ABI with host buffers: geometry upload,
     # the same K steps, fields (phi, fl, T) read back to host memory
@@ -327,6 +331,7 @@ def main():
         "config": {"workload": workload_name + f", seed {rank}", "grid": [cfg["nx"], cfg["ny"]],
                    "precision": args.precision,
                    "l2": "flushed before every timed step (256 MB write)",
+                   "diag_every": args.diag_every,
                    "parallelism": f"replicas x{world}"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": profiled_traffic(),

@@ -72,6 +72,11 @@ struct Coef {
   R T_cold;
   R one_m_ratio; // 1 - rho_s / rho_l
   R T_wall[4];
+  // per-context products the kernels would otherwise form per node
+  R s3, s9;      // 3 sigma / eps, 9 sigma / eps (Eq. (6))
+  R klap;        // 3 eps sigma / 8 (Eq. (6))
+  R rr3;         // rho_ref Cp_ref cs^2 (Eq. (26))
+  R inv_tau_g;   // 1 / tau_g
   uint32_t readings;
 };
 
@@ -229,7 +234,7 @@ __device__ __forceinline__ Local<R> local_state(const Coef<R>& c, int lat, R sg,
 // Eq. (6) without the Laplacian terms.
 template <typename R>
 __device__ __forceinline__ R chem_local(const Coef<R>& c, R phi, R phi0, R fs) {
-  R s3 = R(3) * c.sigma / c.eps, s9 = R(9) * c.sigma / c.eps;
+  const R s3 = c.s3, s9 = c.s9;
   return s3 * phi * (phi - R(1)) * (phi + R(1)) + s9 * phi0 * phi0 * phi +
          s3 * c.cos_th * phi0 * (R(3) * phi * phi + phi0 * phi0 - R(1)) + s9 * fs * fs * phi +
          s3 * c.cos_ps * fs * (R(3) * phi * phi + fs * fs - R(1));
@@ -384,7 +389,7 @@ __global__ void __launch_bounds__(NT) lbm_init_kernel(const InitArgs<R> a) {
   }
   lphi *= R(3); lphi0 *= R(3); lfs *= R(3);
   const R muphi = chem_local(c, phi, q0, fs) -
-                  R(3) * c.eps * c.sigma / R(8) * (lphi + c.cos_th * lphi0 + c.cos_ps * lfs);
+                  c.klap * (lphi + c.cos_th * lphi0 + c.cos_ps * lfs);
   const R ell = w * c.rho_l * c.latent;
   R fsf = q0 + w;
   fsf = fsf > R(1) ? R(1) : fsf;

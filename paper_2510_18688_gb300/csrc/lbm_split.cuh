@@ -169,7 +169,7 @@ __global__ void __launch_bounds__(NT, sizeof(R) == 4 ? LBM_MIN_BLOCKS_F32 : 1)
       R Fsx = R(0), Fsy = R(0);
       if (lat & LAT_PHASE) {
         M.muphi = chem_local(c, phi, phi0, fs) -
-                  R(3) * c.eps * c.sigma / R(8) * (lphi + c.cos_th * lphi0 + c.cos_ps * lfs);
+                  c.klap * (lphi + c.cos_th * lphi0 + c.cos_ps * lfs);
         Fsx = M.muphi * gphx;
         Fsy = M.muphi * gphy;
       }
@@ -190,10 +190,10 @@ __global__ void __launch_bounds__(NT, sizeof(R) == 4 ? LBM_MIN_BLOCKS_F32 : 1)
       M.uu = M.ux * M.ux + M.uy * M.uy;
       M.S = rho * mdot + M.ux * grx + M.uy * gry;
       // modified force (reading R-FT), lagged pressure (reading R-FP)
-      M.Ftx = Fx - (gpx - grx / R(3));
-      M.Fty = Fy - (gpy - gry / R(3));
+      M.Ftx = Fx - (gpx - grx * R(1.0 / 3.0));
+      M.Fty = Fy - (gpy - gry * R(1.0 / 3.0));
       M.uFt = M.ux * M.Ftx + M.uy * M.Fty;
-      M.tauf = qdiv(mu, rho / R(3)) + R(0.5);
+      M.tauf = qdiv(mu, rho * R(1.0 / 3.0)) + R(0.5);
       M.Gx = Fx + rho * fpx;
       M.Gy = Fy + rho * fpy;
       R F0 = qw<R>(0) * (M.S + (R(0) - R(2) / R(3) * M.uFt) * R(4.5));

@@ -17,6 +17,10 @@
 #ifndef LBM_MIN_BLOCKS_F32
 #define LBM_MIN_BLOCKS_F32 4
 #endif
+// 1: the float step also keeps the flow populations in shared memory
+#ifndef LBM_STASH_F
+#define LBM_STASH_F 0
+#endif
 
 namespace lbmk {
 
@@ -114,7 +118,7 @@ __device__ __forceinline__ void collide_phase(const Geom& g, const Coef<R>& c,
                                               R* __restrict__ out, int P, int x, int y, int n,
                                               const R* gq, R phi, R mdot, R phuxp, R phuyp,
                                               const Macro<R>& M) {
-  const R itg = qdiv(R(1), c.tau_g);
+  const R itg = c.inv_tau_g;
   const R omg = R(1) - itg;
   const R gcoef = R(1) - R(0.5) * itg;
   const R emu = c.eta * M.muphi;
@@ -146,7 +150,7 @@ __device__ __forceinline__ void collide_heat(const Geom& g, const Coef<R>& c, R*
                                              int P, int x, int y, int n, const R* h, R fs, R w,
                                              R T, R rhoH, R mdot, const Macro<R>& M) {
   const R lam = interp(fs, w, c.lam_s, c.lam_l, c.lam_g);
-  const R taua = R(0.5) + qdiv(lam, c.rr / R(3));
+  const R taua = R(0.5) + qdiv(lam, c.rr3);
   const R taus = qdiv(taua, R(2) * taua - R(1));
   const R ia = qdiv(R(1), taua), is = qdiv(R(1), taus);
   const R hcoef = R(1) - R(0.5) * ia;
@@ -188,7 +192,9 @@ __global__ void __launch_bounds__(NT, sizeof(R) == 4 ? LBM_MIN_BLOCKS_F32 : 1)
   // memory between phase A and phase B (18 KB per CTA) instead of reading
   // them again through L1/L2
   constexpr bool STASH = sizeof(R) == 4 && MODE == MODE_STEP;
+  constexpr bool STASHF = STASH && LBM_STASH_F;
   __shared__ R s_pop[STASH ? 18 : 1][NT];
+  __shared__ R s_fpop[STASHF ? 9 : 1][NT];
   __shared__ R s_phi[HN], s_fs[HN], s_rho[HN], s_p[HN], s_phi0[HN];
   __shared__ R s_rsg[RING][NPART], s_rsh[RING][NPART];
   __shared__ R s_rfl[RING], s_rw[RING], s_rQ[RING];
@@ -257,6 +263,10 @@ __global__ void __launch_bounds__(NT, sizeof(R) == 4 ? LBM_MIN_BLOCKS_F32 : 1)
   if (lat & LAT_FLOW) {
 #pragma unroll
     for (int i = 0; i < 9; i++) f[i] = pn[i * P];
+    if (STASHF) {
+#pragma unroll
+      for (int i = 0; i < 9; i++) s_fpop[STASHF ? i : 0][tid] = f[i];
+    }
   }
   R sg = R(0), sh = R(0);
   if (lat & LAT_PHASE) {
@@ -358,7 +368,7 @@ __global__ void __launch_bounds__(NT, sizeof(R) == 4 ? LBM_MIN_BLOCKS_F32 : 1)
       R Fsx = R(0), Fsy = R(0);
       if (lat & LAT_PHASE) {
         M.muphi = chem_local(c, phi, phi0, fs) -
-                  R(3) * c.eps * c.sigma / R(8) * (lphi + c.cos_th * lphi0 + c.cos_ps * lfs);
+                  c.klap * (lphi + c.cos_th * lphi0 + c.cos_ps * lfs);
         Fsx = M.muphi * gphx;
         Fsy = M.muphi * gphy;
       }
@@ -366,6 +376,10 @@ __global__ void __launch_bounds__(NT, sizeof(R) == 4 ? LBM_MIN_BLOCKS_F32 : 1)
       Fy = Fsy + rho * c.gy;
     }
     M.ux = R(0); M.uy = R(0); M.uu = R(0); M.pr = R(0);
+    if (STASHF && (lat & LAT_FLOW)) {
+#pragma unroll
+      for (int i = 0; i < 9; i++) f[i] = s_fpop[STASHF ? i : 0][tid];
+    }
     if (lat & LAT_FLOW) {
       const R mu = interp(fs, L.w, c.mu_s, c.mu_l, c.mu_g);
       const R jx = (f[1] - f[3]) + (f[5] - f[6]) + (f[8] - f[7]);
@@ -379,10 +393,10 @@ __global__ void __launch_bounds__(NT, sizeof(R) == 4 ? LBM_MIN_BLOCKS_F32 : 1)
       M.uu = M.ux * M.ux + M.uy * M.uy;
       M.S = rho * mdot + M.ux * grx + M.uy * gry;
       // modified force (reading R-FT), lagged pressure (reading R-FP)
-      M.Ftx = Fx - (gpx - grx / R(3));
-      M.Fty = Fy - (gpy - gry / R(3));
+      M.Ftx = Fx - (gpx - grx * R(1.0 / 3.0));
+      M.Fty = Fy - (gpy - gry * R(1.0 / 3.0));
       M.uFt = M.ux * M.Ftx + M.uy * M.Fty;
-      M.tauf = qdiv(mu, rho / R(3)) + R(0.5);
+      M.tauf = qdiv(mu, rho * R(1.0 / 3.0)) + R(0.5);
       M.Gx = Fx + rho * fpx;
       M.Gy = Fy + rho * fpy;
       // F_0 of Eq. (16)
