@@ -38,23 +38,32 @@ L2_FLUSH_BYTES = 256 << 20
 
 def _droplet512(seed):
     from paper_2510_18688_gb300 import workloads as W
-    return W.sessile_droplet(512, seed=seed)
+    return [W.sessile_droplet(512, seed=seed)]
 
 
 def _droplet1024(seed):
     from paper_2510_18688_gb300 import workloads as W
-    return W.sessile_droplet(1024, seed=seed, radius=200.0)
+    return [W.sessile_droplet(1024, seed=seed, radius=200.0)]
 
 
 def _porous(seed):
     from paper_2510_18688_gb300 import workloads as W
-    return W.porous(seed=seed)
+    return [W.porous(seed=seed)]
+
+
+def _batch64(seed):
+    """64 droplets on cold cylinders, sides drawn from {128, 256, 384, 512}."""
+    from paper_2510_18688_gb300 import workloads as W
+    r = W.rng(1000 + seed)
+    sides = r.choice([128, 256, 384, 512], size=64)
+    return [W.cylinder_droplet(int(sd), seed=64 * seed + i) for i, sd in enumerate(sides)]
 
 
 WORKLOADS = {
     "droplet512": (_droplet512, "sessile droplet freezing 512x512 (R=100, cold solid layer), 3 lattices"),
     "droplet1024": (_droplet1024, "sessile droplet freezing 1024x1024 (R=200, cold solid layer), 3 lattices"),
     "porous2048x1024": (_porous, "freezing in a porous medium 2048x1024 (porosity 0.6, saturation 0.5), 3 lattices"),
+    "batch64": (_batch64, "64 droplets on cold cylinders, sides in {128,256,384,512}, one persistent launch per step"),
 }
 
 
@@ -81,10 +90,17 @@ def kernel_source_hash() -> str:
     return h.hexdigest()[:16]
 
 
-def profiled_traffic():
+PROFILE_OF = {"droplet512": "lbm_step_f32_droplet512.md",
+              "porous2048x1024": "lbm_step_f32_porous2048x1024.md",
+              "batch64": "lbm_batch_f32_batch64.md"}
+
+
+def profiled_traffic(workload="droplet512"):
     """DRAM bytes per launch of the step kernel from the committed ncu
     summary, if it was taken on the current kernel source."""
-    path = os.path.join(ROOT, "profiles", "lbm_step_f32_droplet512.md")
+    if workload not in PROFILE_OF:
+        return None
+    path = os.path.join(ROOT, "profiles", PROFILE_OF[workload])
     if not os.path.exists(path):
         return None
     txt = open(path).read()
@@ -252,17 +268,25 @@ def main():
     L = lbm.load()
 
     make, workload_name = WORKLOADS[args.workload]
-    cfg, arr = make(rank)
-    n = cfg["nx"] * cfg["ny"]
+    wls = make(rank)
+    n = sum(c["nx"] * c["ny"] for c, _ in wls)
     stream = torch.cuda.current_stream()
     sptr = ctypes.c_void_p(stream.cuda_stream)
-    solver = lbm.Solver(cfg, precision=args.precision,
-                        diag_every=args.diag_every).set_geometry(arr)
+    solvers = [lbm.Solver(c, precision=args.precision, diag_every=args.diag_every).set_geometry(a)
+               for c, a in wls]
+    batch = lbm.Batch(solvers) if len(solvers) > 1 else None
+
+    def step(k):
+        if batch is not None:
+            lbm.lbm_batch_step(batch.handle, k, sptr)
+        else:
+            lbm.lbm_step(solvers[0].ctx, k, sptr)
+
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
 
     for _ in range(args.warmup):
         flush.zero_()
-        lbm.lbm_step(solver.ctx, 1, sptr)
+        step(1)
     torch.cuda.synchronize()
 
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
@@ -275,7 +299,7 @@ def main():
         for k in range(args.steps):
             flush.zero_()
             starts[k].record(stream)
-            lbm.lbm_step(solver.ctx, 1, sptr)
+            step(1)
             ends[k].record(stream)
         torch.cuda.synchronize()
         wall = time.perf_counter() - wall0
@@ -285,46 +309,50 @@ def main():
     t_step = float(times.mean())
     t_tot = max_over_ranks(float(times.sum()), pg)
     # the fused reduction of the last diagnosed step, or one on request
-    diag = solver.diagnostics(compute=args.diag_every == 0)
+    diag = solvers[0].diagnostics(compute=args.diag_every == 0)
 
     # end to end through the C ABI with host buffers: geometry upload,
     # the same K steps, fields (phi, fl, T) read back to host memory
-    e2e = None
     def pinned(a, dtype):
         t = torch.empty(a.shape, dtype=dtype, pin_memory=True)
         t.numpy()[...] = a
         return t
 
-    host_t = {k: pinned(arr[k], torch.float64) for k in ("phi0", "phi", "T", "fl")}
-    host = {k: v.numpy() for k, v in host_t.items()}
-    hmask_t = pinned(arr["mask"], torch.uint8) if "mask" in arr else None
-    hmask = hmask_t.numpy() if hmask_t is not None else None
-    outs_t = {k: torch.empty((cfg["ny"], cfg["nx"]), dtype=torch.float64, pin_memory=True)
-              for k in ("phi", "fl", "T")}
-    outs = {k: v.numpy() for k, v in outs_t.items()}
-    ptrs = [outs[k].ctypes.data if k in outs else None for k in lbm.FIELDS]
+    keep = []
+    uploads, downloads = [], []
     fmask = lbm.FIELD_BIT["phi"] | lbm.FIELD_BIT["fl"] | lbm.FIELD_BIT["T"]
+    h2d = d2h = 0
+    for (c, a), sv in zip(wls, solvers):
+        ht = {k: pinned(a[k], torch.float64) for k in ("phi0", "phi", "T", "fl")}
+        hm = pinned(a["mask"], torch.uint8) if "mask" in a else None
+        ot = {k: torch.empty((c["ny"], c["nx"]), dtype=torch.float64, pin_memory=True)
+              for k in ("phi", "fl", "T")}
+        keep += [ht, hm, ot]
+        h = {k: v.numpy() for k, v in ht.items()}
+        uploads.append((sv.ctx, h["phi0"].ctypes.data, hm.numpy().ctypes.data if hm is not None else None,
+                        h["phi"].ctypes.data, h["T"].ctypes.data, h["fl"].ctypes.data))
+        ptrs = [ot[k].numpy().ctypes.data if k in ot else None for k in lbm.FIELDS]
+        downloads.append((sv.ctx, ptrs))
+        h2d += 4 * c["nx"] * c["ny"] * 8 + (c["nx"] * c["ny"] if hm is not None else 0)
+        d2h += 3 * c["nx"] * c["ny"] * 8
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    lbm.lbm_set_geometry(solver.ctx, host["phi0"].ctypes.data,
-                         hmask.ctypes.data if hmask is not None else None,
-                         host["phi"].ctypes.data, host["T"].ctypes.data, host["fl"].ctypes.data,
-                         lbm.LBM_HOST, sptr)
-    lbm.lbm_step(solver.ctx, args.steps, sptr)
-    lbm.lbm_read_fields(solver.ctx, fmask, ptrs, lbm.LBM_HOST, sptr)
+    for u in uploads:
+        lbm.lbm_set_geometry(*u, lbm.LBM_HOST, sptr)
+    step(args.steps)
+    for ctx, ptrs in downloads:
+        lbm.lbm_read_fields(ctx, fmask, ptrs, lbm.LBM_HOST, sptr)
     e2e_s = time.perf_counter() - t0
-    h2d = 4 * n * 8 + (n if hmask is not None else 0)
-    d2h = 3 * n * 8
     e2e = {"value": n * args.steps / e2e_s / 1e6, "unit": "MLUPS",
            "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": d2h / args.steps,
            "note": ("one job through the C ABI: pinned-host geometry upload, K steps back to "
-                    "back (the grid stays L2-resident, unlike the flushed per-step timing of "
-                    "value), phi/fl/T download to pinned host memory")}
+                    "back (no L2 flush between them, unlike the per-step timing of value), "
+                    "phi/fl/T download to pinned host memory")}
 
-    # steady state with the grid resident in L2 (context only, not the value)
+    # steady state without flushes (context only, not the value)
     g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     g0.record(stream)
-    lbm.lbm_step(solver.ctx, args.steps, sptr)
+    step(args.steps)
     g1.record(stream)
     torch.cuda.synchronize()
     l2_ms = g0.elapsed_time(g1) / args.steps
@@ -334,7 +362,9 @@ def main():
             pg.destroy_process_group()
         return
     esize = 4 if args.precision == "fp32" else 8
-    bpn = algorithmic_bytes_per_node(esize, "mask" in arr)
+    # node-weighted bytes per node (grids with a cold mask read one more byte)
+    bpn = sum(algorithmic_bytes_per_node(esize, "mask" in a) * c["nx"] * c["ny"]
+              for c, a in wls) / n
     peak, peak_src = measured_peak()
     achieved = bpn * n / (t_step * 1e-3) / 1e9
     value = whole_job_mlups(n, world, args.steps, t_tot)
@@ -343,13 +373,15 @@ def main():
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_step,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32" if esize == 4 else "f64", "data": "synthetic",
-        "config": {"workload": workload_name + f", seed {rank}", "grid": [cfg["nx"], cfg["ny"]],
+        "config": {"workload": workload_name + f", seed {rank}",
+                   "grid": ([wls[0][0]["nx"], wls[0][0]["ny"]] if len(wls) == 1
+                            else f"{len(wls)} grids, {n} nodes"),
                    "precision": args.precision,
                    "l2": "flushed before every timed step (256 MB write)",
                    "diag_every": args.diag_every,
                    "parallelism": f"replicas x{world}"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": profiled_traffic(),
+                     "frac": achieved / peak, "traffic": profiled_traffic(args.workload),
                      "peak_source": peak_src, "bytes_per_node": bpn},
         "gpu_launches": args.steps,
         "e2e": e2e,

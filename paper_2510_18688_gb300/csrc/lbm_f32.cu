@@ -40,6 +40,19 @@ cudaError_t launch_split_f32(const SplitArgs<float>& a, bool diag, cudaStream_t 
   return cudaGetLastError();
 }
 
+cudaError_t launch_batch_f32(const BatchArgs<float>& b, bool diag, bool all, int ctas,
+                             cudaStream_t s) {
+  const dim3 block = block_dims();
+  if (all) {
+    if (diag) lbm_batch_kernel<float, true, 7><<<ctas, block, 0, s>>>(b);
+    else lbm_batch_kernel<float, false, 7><<<ctas, block, 0, s>>>(b);
+  } else {
+    if (diag) lbm_batch_kernel<float, true, 0><<<ctas, block, 0, s>>>(b);
+    else lbm_batch_kernel<float, false, 0><<<ctas, block, 0, s>>>(b);
+  }
+  return cudaGetLastError();
+}
+
 cudaError_t launch_init_f32(const InitArgs<float>& a, cudaStream_t s) {
   lbm_init_kernel<float><<<grid_dims(a.g), block_dims(), 0, s>>>(a);
   return cudaGetLastError();

@@ -288,12 +288,25 @@ __device__ __forceinline__ R warp_sum(R v) {
   return v;
 }
 
-// Per-CTA partial sums of the diagnostics in a fixed order (warp shuffles,
-// then the warps in order), written to partial[k * nb + b].  Every thread of
-// the CTA calls it.  The grid-wide sum is lbm_diag_finalize_kernel.
+// Per-tile partial sums of the diagnostics in a fixed order (warp shuffles,
+// then the warps in order), written to partial[k * nb + b] for tile b of nb.
+// Every thread of the CTA calls it.  The grid-wide sum is
+// lbm_diag_finalize_kernel.
+template <typename R>
+__device__ __forceinline__ void block_diag(const R* dvals, double (*s_red)[NDIAG],
+                                           double* __restrict__ partial, int tid, int b, int nb);
+
+// Single-grid launch: the tile is the CTA.
 template <typename R>
 __device__ __forceinline__ void block_diag(const R* dvals, double (*s_red)[NDIAG],
                                            double* __restrict__ partial, int tid) {
+  block_diag(dvals, s_red, partial, tid, blockIdx.y * gridDim.x + blockIdx.x,
+             gridDim.x * gridDim.y);
+}
+
+template <typename R>
+__device__ __forceinline__ void block_diag(const R* dvals, double (*s_red)[NDIAG],
+                                           double* __restrict__ partial, int tid, int b, int nb) {
   const int lane = tid & 31, warp = tid >> 5;
 #pragma unroll
   for (int k = 0; k < NDIAG; k++) {
@@ -302,8 +315,6 @@ __device__ __forceinline__ void block_diag(const R* dvals, double (*s_red)[NDIAG
   }
   __syncthreads();
   if (tid < NDIAG) {
-    const int nb = gridDim.x * gridDim.y;
-    const int b = blockIdx.y * gridDim.x + blockIdx.x;
     double acc = 0.0;
 #pragma unroll
     for (int w = 0; w < NT / 32; w++) acc += s_red[w][tid];

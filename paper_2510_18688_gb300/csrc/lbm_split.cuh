@@ -258,7 +258,9 @@ __global__ void __launch_bounds__(NT, sizeof(R) == 4 ? LBM_MIN_BLOCKS_F32 : 1)
     for (int k = 0; k < NDIAG; k++) dvals[k] = R(0);
   }
 
-  if (DIAG) block_diag(dvals, s_red, a.diag_partial, tid);
+  if (DIAG)
+    block_diag(dvals, s_red, a.diag_partial, tid, blockIdx.y * gridDim.x + blockIdx.x,
+               gridDim.x * gridDim.y);
 }
 
 }  // namespace lbmk

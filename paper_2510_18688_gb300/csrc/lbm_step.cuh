@@ -179,10 +179,12 @@ __device__ __forceinline__ void collide_heat(const Geom& g, const Coef<R>& c, R*
   }
 }
 
-// LATC: compile-time lattice set (7 = all three) or 0 (read at run time).
+// One tile (bx, by) of one grid: the whole step (or read-out) for its
+// TX x TY nodes.  b / nb: the tile's index and the grid's tile count for the
+// diagnostic partials (b < 0: taken from the CTA's position in its grid).  LATC: compile-time lattice set (7 = all three) or 0
+// (read at run time).  Every thread of the CTA calls it.
 template <typename R, int MODE, bool DIAG, int LATC>
-__global__ void __launch_bounds__(NT, sizeof(R) == 4 ? LBM_MIN_BLOCKS_F32 : 1)
-    lbm_step_kernel(const Args<R> a) {
+__device__ __forceinline__ void step_tile(const Args<R>& a, int bx, int by, int b, int nb) {
   const Geom& g = a.g;
   const Coef<R>& c = a.c;
   const int lat = LATC ? LATC : g.lattices;
@@ -203,7 +205,7 @@ __global__ void __launch_bounds__(NT, sizeof(R) == 4 ? LBM_MIN_BLOCKS_F32 : 1)
 
   const int tx = threadIdx.x, ty = threadIdx.y;
   const int tid = ty * TX + tx;
-  const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
+  const int x0 = bx * TX, y0 = by * TY;
   const int gx = x0 + tx, gy = y0 + ty;
   const bool valid = gx < g.nx && gy < g.ny;
   const int mx = wrap_or_clamp(gx, g.nx, g.bc[0], g.bc[1]);
@@ -476,7 +478,42 @@ __global__ void __launch_bounds__(NT, sizeof(R) == 4 ? LBM_MIN_BLOCKS_F32 : 1)
     for (int k = 0; k < NDIAG; k++) dvals[k] = R(0);
   }
 
-  if (DIAG) block_diag(dvals, s_red, a.diag_partial, tid);
+  if (DIAG) {
+    if (b < 0) block_diag(dvals, s_red, a.diag_partial, tid);
+    else block_diag(dvals, s_red, a.diag_partial, tid, b, nb);
+  }
+}
+
+template <typename R, int MODE, bool DIAG, int LATC>
+__global__ void __launch_bounds__(NT, sizeof(R) == 4 ? LBM_MIN_BLOCKS_F32 : 1)
+    lbm_step_kernel(const Args<R> a) {
+  step_tile<R, MODE, DIAG, LATC>(a, blockIdx.x, blockIdx.y, -1, 0);
+}
+
+// Many independent grids (uneven sizes and parameters) advanced in one
+// persistent launch: CTAs walk the concatenated tile list of all grids;
+// tile t belongs to grid tile_grid[t], whose arguments (buffers, geometry,
+// constants) are args[tile_grid[t]] and whose first tile is tile_base[grid].
+template <typename R>
+struct BatchArgs {
+  const Args<R>* __restrict__ args;
+  const int* __restrict__ tile_grid;
+  const int* __restrict__ tile_base;
+  int total_tiles;
+};
+
+template <typename R, bool DIAG, int LATC>
+__global__ void __launch_bounds__(NT, sizeof(R) == 4 ? LBM_MIN_BLOCKS_F32 : 1)
+    lbm_batch_kernel(const BatchArgs<R> B) {
+  for (int t = blockIdx.x; t < B.total_tiles; t += gridDim.x) {
+    const int gi = B.tile_grid[t];
+    const Args<R>& a = B.args[gi];
+    const int local = t - B.tile_base[gi];
+    const int tiles_x = (a.g.nx + TX - 1) / TX;
+    const int ntiles = tiles_x * ((a.g.ny + TY - 1) / TY);
+    __syncthreads();  // the previous tile's shared-memory reads are done
+    step_tile<R, MODE_STEP, DIAG, LATC>(a, local % tiles_x, local / tiles_x, local, ntiles);
+  }
 }
 
 }  // namespace lbmk

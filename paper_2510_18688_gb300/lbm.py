@@ -53,7 +53,8 @@ class LbmDiag(ctypes.Structure):
 EXPORTS = ("lbm_create", "lbm_set_geometry", "lbm_step", "lbm_read_fields",
            "lbm_compute_diagnostics", "lbm_read_diagnostics", "lbm_state_size",
            "lbm_save_state", "lbm_load_state", "lbm_step_count", "lbm_last_error",
-           "lbm_status_string", "lbm_destroy", "lbm_diagnostics_noalloc")
+           "lbm_status_string", "lbm_destroy", "lbm_diagnostics_noalloc",
+           "lbm_batch_create", "lbm_batch_step", "lbm_batch_destroy")
 
 _lib = None
 
@@ -86,9 +87,14 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     L.lbm_destroy.argtypes = [vp]
     L.lbm_destroy.restype = None
     L.lbm_diagnostics_noalloc.argtypes = [ctypes.POINTER(LbmParams), vp, vp, vp, vp, vp, vp]
+    L.lbm_batch_create.argtypes = [ctypes.POINTER(vp), ctypes.c_int, ctypes.POINTER(vp)]
+    L.lbm_batch_step.argtypes = [vp, ctypes.c_int64, vp]
+    L.lbm_batch_destroy.argtypes = [vp]
+    L.lbm_batch_destroy.restype = None
     for fn in ("lbm_create", "lbm_set_geometry", "lbm_step", "lbm_read_fields",
                "lbm_compute_diagnostics", "lbm_read_diagnostics", "lbm_state_size",
-               "lbm_save_state", "lbm_load_state", "lbm_diagnostics_noalloc"):
+               "lbm_save_state", "lbm_load_state", "lbm_diagnostics_noalloc",
+               "lbm_batch_create", "lbm_batch_step"):
         getattr(L, fn).restype = ctypes.c_int
     _lib = L
     return L
@@ -185,6 +191,23 @@ def lbm_diagnostics_noalloc(params: LbmParams, pops, lags, phi0, cold_mask, out,
     (see include/lbm.h); returns the status code."""
     return int(load().lbm_diagnostics_noalloc(ctypes.byref(params), pops, lags, phi0,
                                               cold_mask, out, stream))
+
+
+def lbm_batch_create(ctxs) -> ctypes.c_void_p:
+    arr = (ctypes.c_void_p * len(ctxs))(*[c.value if isinstance(c, ctypes.c_void_p) else c
+                                           for c in ctxs])
+    h = ctypes.c_void_p()
+    _check(None, load().lbm_batch_create(arr, len(ctxs), ctypes.byref(h)), "lbm_batch_create")
+    return h
+
+
+def lbm_batch_step(batch, nsteps: int, stream=None):
+    _check(None, load().lbm_batch_step(batch, int(nsteps), stream), "lbm_batch_step")
+
+
+def lbm_batch_destroy(batch):
+    if batch:
+        load().lbm_batch_destroy(batch)
 
 
 def lbm_last_error(ctx) -> str:
@@ -290,3 +313,26 @@ class Solver:
 
     def load(self, blob: bytes):
         lbm_load_state(self.ctx, blob, _stream())
+
+
+class Batch:
+    """Several Solvers advanced together, one persistent launch per step."""
+
+    def __init__(self, solvers):
+        self.solvers = list(solvers)
+        self.handle = lbm_batch_create([s.ctx for s in self.solvers])
+
+    def step(self, n: int = 1):
+        lbm_batch_step(self.handle, n, _stream())
+        return self
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lbm_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

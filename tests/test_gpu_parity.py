@@ -244,3 +244,67 @@ def test_errors_are_status_codes(env):
     s.set_geometry(arr)
     with pytest.raises(lbm.LbmError):
         lbm.lbm_step(s.ctx, -1)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_batched_grids_match_single_grids_and_oracle(env, prec):
+    """Grids of uneven sizes and parameters advanced by one persistent launch
+    per step give, grid by grid, the results of lbm_step on each grid alone
+    (bit for bit in FP64, which is built without FMA contraction; within a
+    few FP32 roundings in FP32, where the compiler may contract the two
+    kernels' copies of the step differently), and the oracle's within the
+    parity bar."""
+    O, lbm = env
+    wls = [W.random_state(45, 19, seed=0), W.random_state(96, 24, seed=3),
+           W.random_state(37, 41, seed=2), W.random_state(70, 17, seed=5),
+           W.cylinder_droplet(64, seed=1)]
+    steps = 60
+    batch_solvers = [lbm.Solver(c, precision=prec, diag_every=10).set_geometry(a) for c, a in wls]
+    b = lbm.Batch(batch_solvers).step(31)  # odd: the second call starts on the other parity
+    b.step(steps - 31)
+    for (cfg, arr), s in zip(wls, batch_solvers):
+        alone = lbm.Solver(cfg, precision=prec, diag_every=10).set_geometry(arr).step(steps)
+        fa, fb = alone.fields(), s.fields()
+        for k in FIELDS:
+            if prec == "fp64":
+                assert np.array_equal(fa[k], fb[k]), k
+            else:
+                scale = np.abs(fa[k]).max() + 1e-6
+                assert np.abs(fa[k] - fb[k]).max() <= 1e-5 * scale, (k, np.abs(fa[k] - fb[k]).max())
+        da, db = alone.diagnostics(compute=False), s.diagnostics(compute=False)
+        if prec == "fp64":
+            assert da == db
+        else:
+            for k, v in da.items():
+                assert abs(db[k] - v) <= 1e-5 * (abs(v) + cfg["nx"] * cfg["ny"]), k
+        assert s.steps_done == steps
+        ref = O.from_workload((cfg, arr)).step(steps).fields()
+        _compare(fb, ref, prec)
+    b.close()
+
+
+def test_batch_with_mixed_lattice_sets(env):
+    O, lbm = env
+    wls = [W.random_state(40, 30, seed=1), W.random_state(33, 21, seed=2, lattices=5),
+           W.random_state(50, 12, seed=4, lattices=2)]
+    ss = [lbm.Solver(c, precision="fp64").set_geometry(a) for c, a in wls]
+    lbm.Batch(ss).step(25)
+    for (cfg, arr), s in zip(wls, ss):
+        ref = O.from_workload((cfg, arr)).step(25).fields()
+        _compare(s.fields(), ref, "fp64")
+
+
+def test_batch_after_a_single_grid_step(env):
+    """A grid stepped on its own between batch steps moves to the other
+    buffer parity than the rest of the batch; the batch must follow it."""
+    O, lbm = env
+    wls = [W.random_state(40, 30, seed=6), W.random_state(52, 22, seed=7)]
+    ss = [lbm.Solver(c, precision="fp64").set_geometry(a) for c, a in wls]
+    b = lbm.Batch(ss).step(4)
+    ss[1].step(1)
+    b.step(5)
+    assert [s.steps_done for s in ss] == [9, 10]
+    for (cfg, arr), s in zip(wls, ss):
+        ref = O.from_workload((cfg, arr)).step(s.steps_done).fields()
+        _compare(s.fields(), ref, "fp64")
+    b.close()
