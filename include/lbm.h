@@ -187,24 +187,29 @@ const char* lbm_status_string(int status);
 void lbm_destroy(lbm_ctx* ctx);
 
 /* A batch groups `count` existing contexts of the same precision (grids of
- * any sizes, parameters and geometries) so that lbm_batch_step advances all
- * of them together: one persistent launch per time step walks the
- * concatenated tile lists of all grids, each tile evaluated exactly as
- * lbm_step would (same results bit for bit).  This is how many small
- * problems fill the GPU (the batched-droplet workloads of Sec. 4.3-4.4).
- * The batch does not own the contexts; they stay usable on their own
- * (lbm_read_fields, diagnostics, checkpoints) and must outlive the batch.
+ * any sizes, parameters and geometries, each stepped by Eqs. (11)-(25) as
+ * lbm_step does) so that lbm_batch_step advances all of them together: one
+ * launch per time step and per 64 grids covers the concatenated tile lists
+ * of those grids, each tile evaluated as lbm_step would (the same results bit
+ * for bit in FP64; in FP32 the compiler may contract the two kernels' copies
+ * of the arithmetic differently, a difference of FP32 rounding).  This is how
+ * many small problems fill the GPU.  The batch holds the context pointers
+ * only and allocates no device memory; the contexts stay usable on their own
+ * (lbm_step, lbm_read_fields, diagnostics, checkpoints) and must outlive the
+ * batch.
  * Errors: LBM_ERR_ARG (null, count < 1, mixed precision, a context twice),
- * LBM_ERR_OOM, LBM_ERR_CUDA. */
+ * LBM_ERR_OOM (host memory). */
 typedef struct lbm_batch lbm_batch;
 int lbm_batch_create(lbm_ctx* const* ctxs, int count, lbm_batch** out);
 
 /* Enqueues nsteps time steps of every context of the batch on `stream`
- * (diagnostics every diag_every steps of the first context, for all).
- * Errors: LBM_ERR_STATE if a context has no geometry, LBM_ERR_CUDA. */
+ * (host-asynchronous; diagnostics every diag_every steps of the first
+ * context, for all contexts).
+ * Errors: LBM_ERR_ARG (null batch, nsteps < 0), LBM_ERR_STATE if a context
+ * has no geometry, LBM_ERR_CUDA. */
 int lbm_batch_step(lbm_batch* batch, int64_t nsteps, void* stream);
 
-/* Frees the batch's own tables (not the contexts; NULL is allowed). */
+/* Frees the batch (not the contexts; NULL is allowed). */
 void lbm_batch_destroy(lbm_batch* batch);
 
 /* Largest grid lbm_diagnostics_noalloc accepts, in tiles of 32 x 8 nodes

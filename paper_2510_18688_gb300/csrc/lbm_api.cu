@@ -11,6 +11,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <algorithm>
+#include <memory>
 #include <new>
 #include <vector>
 
@@ -434,78 +435,52 @@ int lbm_load_state(lbm_ctx* c, const void* host_buf, size_t size, void* stream) 
 struct lbm_batch {
   std::vector<lbm_ctx*> ctx;
   int precision;
-  bool all;               // every grid has all three lattices
-  int total_tiles;
-  int* d_tile_grid;
-  int* d_tile_base;
-  void* d_args[2];        // argument tables, indexed by the buffer parity of grid 0
-  std::vector<unsigned char> h_args[2];  // what was last uploaded to d_args
-  size_t args_bytes;
-  int sms;
-  int per_sm[2];          // resident CTAs per SM without / with diagnostics
   char err[512];
 };
 
 namespace {
 
-// Argument table q holds every grid's step arguments for the step taken
-// while grid 0 reads buffer q; the grids' parities move together.
+// One launch covers up to BATCH_MAX_GRIDS consecutive contexts; the table
+// holds each one's step arguments (buffers by its current parity).
 template <typename R>
-void fill_table(lbm_batch* b, int q, std::vector<unsigned char>& out) {
-  const int n = (int)b->ctx.size();
-  std::vector<Args<R>> t(n);
-  const int q0 = b->ctx[0]->cur;
-  for (int i = 0; i < n; i++) {
-    lbm_ctx* c = b->ctx[i];
+bool fill_table(lbm_batch* b, int first, int count, lbmk::BatchTable<R>& t) {
+  bool all = true;
+  t.ngrids = count;
+  t.tile_base[0] = 0;
+  for (int i = 0; i < count; i++) {
+    lbm_ctx* c = b->ctx[first + i];
     const Coef<R>* coef;
     if (sizeof(R) == 4) coef = (const Coef<R>*)(const void*)&c->cf;
     else coef = (const Coef<R>*)(const void*)&c->cd;
-    const int keep = c->cur;
-    c->cur = keep ^ q0 ^ q;
-    t[i] = step_args<R>(c, *coef);
-    c->cur = keep;
+    t.args[i] = step_args<R>(c, *coef);
+    t.tile_base[i + 1] = t.tile_base[i] + c->nblocks;
+    if (c->p.lattices != 7u) all = false;
   }
-  out.assign((const unsigned char*)t.data(), (const unsigned char*)t.data() + n * sizeof(Args<R>));
+  return all;
 }
 
 template <typename R>
 int batch_step_impl(lbm_batch* b, int64_t nsteps, cudaStream_t s) {
-  // the tables change only when a context's buffers or parity change
-  // relative to grid 0 (e.g. after a single-grid step); upload on change
-  cudaError_t e = cudaSuccess;
-  for (int q = 0; q < 2 && e == cudaSuccess; q++) {
-    std::vector<unsigned char> t;
-    fill_table<R>(b, q, t);
-    if (t != b->h_args[q]) {
-      // pageable source: staged before the call returns
-      e = cudaMemcpyAsync(b->d_args[q], t.data(), t.size(), cudaMemcpyHostToDevice, s);
-      b->h_args[q].swap(t);
-    }
-  }
-  if (e != cudaSuccess) {
-    b->h_args[0].clear();
-    b->h_args[1].clear();
-    std::snprintf(b->err, sizeof(b->err), "batch table upload: %s", cudaGetErrorString(e));
-    return LBM_ERR_CUDA;
-  }
+  const int n = (int)b->ctx.size();
+  std::unique_ptr<lbmk::BatchTable<R>> t(new (std::nothrow) lbmk::BatchTable<R>());
+  if (!t) return LBM_ERR_OOM;
   lbm_ctx* c0 = b->ctx[0];
   for (int64_t k = 0; k < nsteps; k++) {
     const bool diag = c0->p.diag_every > 0 && (c0->step % c0->p.diag_every) == 0;
-    lbmk::BatchArgs<R> ba;
-    ba.args = (const Args<R>*)b->d_args[c0->cur];
-    ba.tile_grid = b->d_tile_grid;
-    ba.tile_base = b->d_tile_base;
-    ba.total_tiles = b->total_tiles;
-    const int ctas = std::min(b->total_tiles, b->per_sm[diag ? 1 : 0] * b->sms);
-    if (sizeof(R) == 4)
-      e = lbmk::launch_batch_f32(*(const lbmk::BatchArgs<float>*)(const void*)&ba, diag, b->all,
-                                 ctas, s);
-    else
-      e = lbmk::launch_batch_f64(*(const lbmk::BatchArgs<double>*)(const void*)&ba, diag,
-                                 b->all, ctas, s);
-    if (e != cudaSuccess) {
-      std::snprintf(b->err, sizeof(b->err), "batch kernel launch: %s", cudaGetErrorString(e));
-      return LBM_ERR_CUDA;
+    for (int first = 0; first < n; first += lbmk::BATCH_MAX_GRIDS) {
+      const int count = std::min(n - first, lbmk::BATCH_MAX_GRIDS);
+      const bool all = fill_table<R>(b, first, count, *t);
+      cudaError_t e;
+      if (sizeof(R) == 4)
+        e = lbmk::launch_batch_f32(*(const lbmk::BatchTable<float>*)(const void*)t.get(), diag,
+                                   all, s);
+      else
+        e = lbmk::launch_batch_f64(*(const lbmk::BatchTable<double>*)(const void*)t.get(), diag,
+                                   all, s);
+      if (e != cudaSuccess) {
+        std::snprintf(b->err, sizeof(b->err), "batch kernel launch: %s", cudaGetErrorString(e));
+        return LBM_ERR_CUDA;
+      }
     }
     for (lbm_ctx* c : b->ctx) {
       if (diag) {
@@ -538,38 +513,6 @@ int lbm_batch_create(lbm_ctx* const* ctxs, int count, lbm_batch** out) {
   if (!b) return LBM_ERR_OOM;
   b->ctx.assign(ctxs, ctxs + count);
   b->precision = ctxs[0]->p.precision;
-  b->all = true;
-  std::vector<int> tile_grid, tile_base(count);
-  for (int i = 0; i < count; i++) {
-    const lbm_ctx* c = ctxs[i];
-    if (c->p.lattices != 7u) b->all = false;
-    tile_base[i] = (int)tile_grid.size();
-    tile_grid.insert(tile_grid.end(), (size_t)c->nblocks, i);
-  }
-  b->total_tiles = (int)tile_grid.size();
-  b->args_bytes = (size_t)count * (b->precision == LBM_FP32 ? sizeof(Args<float>) : sizeof(Args<double>));
-  cudaError_t e = cudaMalloc(&b->d_tile_grid, tile_grid.size() * sizeof(int));
-  if (e == cudaSuccess) e = cudaMalloc(&b->d_tile_base, tile_base.size() * sizeof(int));
-  if (e == cudaSuccess) e = cudaMalloc(&b->d_args[0], b->args_bytes);
-  if (e == cudaSuccess) e = cudaMalloc(&b->d_args[1], b->args_bytes);
-  if (e == cudaSuccess)
-    e = cudaMemcpy(b->d_tile_grid, tile_grid.data(), tile_grid.size() * sizeof(int),
-                   cudaMemcpyHostToDevice);
-  if (e == cudaSuccess)
-    e = cudaMemcpy(b->d_tile_base, tile_base.data(), tile_base.size() * sizeof(int),
-                   cudaMemcpyHostToDevice);
-  int dev = 0;
-  if (e == cudaSuccess) e = cudaGetDevice(&dev);
-  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, dev);
-  for (int d = 0; d < 2 && e == cudaSuccess; d++) {
-    b->per_sm[d] = lbmk::batch_ctas_per_sm(b->precision == LBM_FP32, d == 1, b->all);
-    if (b->per_sm[d] < 1) e = cudaErrorInvalidConfiguration;
-  }
-  if (e != cudaSuccess) {
-    std::fprintf(stderr, "lbm_batch_create: %s\n", cudaGetErrorString(e));
-    lbm_batch_destroy(b);
-    return e == cudaErrorMemoryAllocation ? LBM_ERR_OOM : LBM_ERR_CUDA;
-  }
   *out = b;
   return LBM_OK;
 }
@@ -589,12 +532,6 @@ int lbm_batch_step(lbm_batch* b, int64_t nsteps, void* stream) {
                                   : batch_step_impl<double>(b, nsteps, s);
 }
 
-void lbm_batch_destroy(lbm_batch* b) {
-  if (!b) return;
-  void* dev[] = {b->d_tile_grid, b->d_tile_base, b->d_args[0], b->d_args[1]};
-  for (void* p : dev)
-    if (p) cudaFree(p);
-  delete b;
-}
+void lbm_batch_destroy(lbm_batch* b) { delete b; }
 
 }  // extern "C"

@@ -40,9 +40,9 @@ cudaError_t launch_split_f32(const SplitArgs<float>& a, bool diag, cudaStream_t 
   return cudaGetLastError();
 }
 
-cudaError_t launch_batch_f32(const BatchArgs<float>& b, bool diag, bool all, int ctas,
-                             cudaStream_t s) {
+cudaError_t launch_batch_f32(const BatchTable<float>& b, bool diag, bool all, cudaStream_t s) {
   const dim3 block = block_dims();
+  const int ctas = b.tile_base[b.ngrids];
   if (all) {
     if (diag) lbm_batch_kernel<float, true, 7><<<ctas, block, 0, s>>>(b);
     else lbm_batch_kernel<float, false, 7><<<ctas, block, 0, s>>>(b);

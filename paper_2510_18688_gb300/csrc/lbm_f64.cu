@@ -40,9 +40,9 @@ cudaError_t launch_split_f64(const SplitArgs<double>& a, bool diag, cudaStream_t
   return cudaGetLastError();
 }
 
-cudaError_t launch_batch_f64(const BatchArgs<double>& b, bool diag, bool all, int ctas,
-                             cudaStream_t s) {
+cudaError_t launch_batch_f64(const BatchTable<double>& b, bool diag, bool all, cudaStream_t s) {
   const dim3 block = block_dims();
+  const int ctas = b.tile_base[b.ngrids];
   if (all) {
     if (diag) lbm_batch_kernel<double, true, 7><<<ctas, block, 0, s>>>(b);
     else lbm_batch_kernel<double, false, 7><<<ctas, block, 0, s>>>(b);
@@ -56,24 +56,6 @@ cudaError_t launch_batch_f64(const BatchArgs<double>& b, bool diag, bool all, in
 cudaError_t launch_init_f64(const InitArgs<double>& a, cudaStream_t s) {
   lbm_init_kernel<double><<<grid_dims(a.g), block_dims(), 0, s>>>(a);
   return cudaGetLastError();
-}
-
-int batch_ctas_per_sm(bool fp32, bool diag, bool all) {
-  int n = 0;
-  const int threads = NT;
-  cudaError_t e;
-  if (fp32) {
-    if (all) e = diag ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, lbm_batch_kernel<float, true, 7>, threads, 0)
-                      : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, lbm_batch_kernel<float, false, 7>, threads, 0);
-    else e = diag ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, lbm_batch_kernel<float, true, 0>, threads, 0)
-                  : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, lbm_batch_kernel<float, false, 0>, threads, 0);
-  } else {
-    if (all) e = diag ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, lbm_batch_kernel<double, true, 7>, threads, 0)
-                      : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, lbm_batch_kernel<double, false, 7>, threads, 0);
-    else e = diag ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, lbm_batch_kernel<double, true, 0>, threads, 0)
-                  : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, lbm_batch_kernel<double, false, 0>, threads, 0);
-  }
-  return (e == cudaSuccess && n > 0) ? n : 1;
 }
 
 cudaError_t launch_diag_finalize(const double* partial, int nb, double* out, long long step,

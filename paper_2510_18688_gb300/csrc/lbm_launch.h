@@ -22,13 +22,9 @@ cudaError_t launch_step_f64(const Args<double>& a, int mode, bool diag, cudaStre
 cudaError_t launch_split_f32(const SplitArgs<float>& a, bool diag, cudaStream_t s);
 cudaError_t launch_split_f64(const SplitArgs<double>& a, bool diag, cudaStream_t s);
 cudaError_t launch_init_f32(const InitArgs<float>& a, cudaStream_t s);
-// Many grids in one persistent launch (grid = `ctas` CTAs).
-cudaError_t launch_batch_f32(const BatchArgs<float>& b, bool diag, bool all, int ctas,
-                             cudaStream_t s);
-cudaError_t launch_batch_f64(const BatchArgs<double>& b, bool diag, bool all, int ctas,
-                             cudaStream_t s);
-// Resident CTAs per SM of the batched kernel (for sizing the persistent grid).
-int batch_ctas_per_sm(bool fp32, bool diag, bool all);
+// Up to BATCH_MAX_GRIDS grids in one launch, one CTA per tile.
+cudaError_t launch_batch_f32(const BatchTable<float>& b, bool diag, bool all, cudaStream_t s);
+cudaError_t launch_batch_f64(const BatchTable<double>& b, bool diag, bool all, cudaStream_t s);
 // Grid-wide diagnostics from the per-CTA partials (one CTA).
 cudaError_t launch_diag_finalize(const double* partial, int nb, double* out, long long step,
                                  cudaStream_t s);

@@ -491,29 +491,36 @@ __global__ void __launch_bounds__(NT, sizeof(R) == 4 ? LBM_MIN_BLOCKS_F32 : 1)
 }
 
 // Many independent grids (uneven sizes and parameters) advanced in one
-// persistent launch: CTAs walk the concatenated tile list of all grids;
-// tile t belongs to grid tile_grid[t], whose arguments (buffers, geometry,
-// constants) are args[tile_grid[t]] and whose first tile is tile_base[grid].
+// launch.  The whole table -- every grid's arguments and the prefix sums of
+// the grids' tile counts -- travels in the kernel's parameter space (up to
+// 32 KB on sm_70 and later), so the per-grid constants are read through the
+// constant cache, like those of the single-grid kernel, and nothing of the
+// table lives in device memory.  CTA t takes tile t of the concatenated tile
+// list; its grid is found by bisection over the prefix sums.
+constexpr int BATCH_MAX_GRIDS = 64;
+
 template <typename R>
-struct BatchArgs {
-  const Args<R>* __restrict__ args;
-  const int* __restrict__ tile_grid;
-  const int* __restrict__ tile_base;
-  int total_tiles;
+struct BatchTable {
+  int ngrids;
+  int tile_base[BATCH_MAX_GRIDS + 1];  // first tile of each grid; [ngrids] = total
+  Args<R> args[BATCH_MAX_GRIDS];
 };
 
 template <typename R, bool DIAG, int LATC>
 __global__ void __launch_bounds__(NT, sizeof(R) == 4 ? LBM_MIN_BLOCKS_F32 : 1)
-    lbm_batch_kernel(const BatchArgs<R> B) {
-  for (int t = blockIdx.x; t < B.total_tiles; t += gridDim.x) {
-    const int gi = B.tile_grid[t];
-    const Args<R>& a = B.args[gi];
-    const int local = t - B.tile_base[gi];
-    const int tiles_x = (a.g.nx + TX - 1) / TX;
-    const int ntiles = tiles_x * ((a.g.ny + TY - 1) / TY);
-    __syncthreads();  // the previous tile's shared-memory reads are done
-    step_tile<R, MODE_STEP, DIAG, LATC>(a, local % tiles_x, local / tiles_x, local, ntiles);
+    lbm_batch_kernel(const __grid_constant__ BatchTable<R> B) {
+  const int t = blockIdx.x;
+  int lo = 0, hi = B.ngrids;  // tile_base[lo] <= t < tile_base[hi]
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (B.tile_base[mid] <= t) lo = mid;
+    else hi = mid;
   }
+  const Args<R>& a = B.args[lo];
+  const int local = t - B.tile_base[lo];
+  const int tiles_x = (a.g.nx + TX - 1) / TX;
+  const int ntiles = B.tile_base[lo + 1] - B.tile_base[lo];
+  step_tile<R, MODE_STEP, DIAG, LATC>(a, local % tiles_x, local / tiles_x, local, ntiles);
 }
 
 }  // namespace lbmk
