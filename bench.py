@@ -82,30 +82,34 @@ def measured_peak():
     return 6800.0, "fallback"
 
 
+# the sources the step kernels are compiled from (host API and probes excluded)
+KERNEL_SOURCES = ("lbm_kernels.cuh", "lbm_step.cuh", "lbm_split.cuh", "lbm_launch.h",
+                  "lbm_f32.cu", "lbm_f64.cu")
+
+
 def kernel_source_hash() -> str:
     h = hashlib.sha256()
-    for f in sorted(os.listdir(os.path.join(ROOT, "paper_2510_18688_gb300", "csrc"))):
+    for f in KERNEL_SOURCES:
         with open(os.path.join(ROOT, "paper_2510_18688_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
 
 
-PROFILE_OF = {"droplet512": "lbm_step_f32_droplet512.md",
-              "porous2048x1024": "lbm_step_f32_porous2048x1024.md",
-              "batch64": "lbm_batch_f32_batch64.md"}
+def profile_name(workload: str, precision: str) -> str:
+    kind = "batch" if workload.startswith("batch") else "step"
+    return f"lbm_{kind}_{'f32' if precision == 'fp32' else 'f64'}_{workload}.md"
 
 
-def profiled_traffic(workload="droplet512"):
-    """DRAM bytes per launch of the step kernel from the committed ncu
-    summary, if it was taken on the current kernel source."""
-    if workload not in PROFILE_OF:
-        return None
-    path = os.path.join(ROOT, "profiles", PROFILE_OF[workload])
+def profiled_value(workload: str, precision: str, key: str):
+    """A per-launch figure (e.g. "dram bytes per launch") from the committed
+    ncu summary of this workload, if it was taken on the current kernel
+    source; else None."""
+    path = os.path.join(ROOT, "profiles", profile_name(workload, precision))
     if not os.path.exists(path):
         return None
     txt = open(path).read()
     m = re.search(r"kernel source hash:\s*([0-9a-f]+)", txt)
-    t = re.search(r"dram bytes per launch:\s*([0-9.eE+]+)", txt)
+    t = re.search(re.escape(key) + r":\s*([0-9.eE+]+)", txt)
     if not m or not t or m.group(1) != kernel_source_hash():
         return None
     return float(t.group(1))
@@ -367,6 +371,22 @@ def main():
               for c, a in wls) / n
     peak, peak_src = measured_peak()
     achieved = bpn * n / (t_step * 1e-3) / 1e9
+    traffic = profiled_value(args.workload, args.precision, "dram bytes per launch")
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": traffic,
+                "peak_source": peak_src, "bytes_per_node": bpn}
+    if args.precision == "fp64":
+        # the FP64 pipe, not HBM, bounds the double-precision step on this
+        # part: compare its executed FP64 flops with the FMA rate measured now
+        fma = lbm.lbm_probe_fma_rate("fp64", sptr)
+        fpn = profiled_value(args.workload, args.precision, "fp64 flops per node")
+        ach = fpn * n / (t_step * 1e-3) / 1e12 if fpn else None
+        roofline = {"bound": "alu", "achieved": ach, "peak": fma / 1e12, "unit": "TFLOP/s",
+                    "frac": ach / (fma / 1e12) if ach else None, "traffic": traffic,
+                    "peak_source": "FP64 FMA rate measured in this run (lbm_probe_fma_rate)",
+                    "flops_per_node": fpn,
+                    "hbm": {"achieved": achieved, "peak": peak, "unit": "GB/s",
+                            "frac": achieved / peak, "bytes_per_node": bpn}}
     value = whole_job_mlups(n, world, args.steps, t_tot)
     line = {
         "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world,
@@ -380,9 +400,7 @@ def main():
                    "l2": "flushed before every timed step (256 MB write)",
                    "diag_every": args.diag_every,
                    "parallelism": f"replicas x{world}"},
-        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": profiled_traffic(args.workload),
-                     "peak_source": peak_src, "bytes_per_node": bpn},
+        "roofline": roofline,
         "gpu_launches": args.steps,
         "e2e": e2e,
         "l2_resident_mlups": n / (l2_ms * 1e-3) / 1e6,

@@ -255,6 +255,18 @@ int lbm_diagnostics_noalloc(const lbm_params* params, const void* pops, const vo
                             const void* phi0, const uint8_t* cold_mask, double* out,
                             void* stream);
 
+/* Measures the fused multiply-add throughput of the current device in the
+ * given precision (LBM_FP64 or LBM_FP32): 8 CTAs per SM run independent FMA
+ * chains; the best of three timed launches (after one warm-up) gives
+ * *flops_per_s = 2 * FMAs / time.  It is the arithmetic ceiling of the
+ * double-precision step, which the FP64 pipe, not its HBM traffic, bounds
+ * on this part (the paper gives no cost model; this is a measuring aid).
+ * Runs on `stream` and synchronises it; allocates and frees a small output
+ * buffer (8 x 256 x SMs elements).  Takes tens of milliseconds.
+ * Errors: LBM_ERR_ARG (null output, other precision), LBM_ERR_OOM,
+ * LBM_ERR_CUDA. */
+int lbm_probe_fma_rate(int precision, double* flops_per_s, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -1,6 +1,7 @@
 """Build the sm_103a shared library ``_lib/liblbm_gb300.so`` with nvcc.
 
-The three translation units (host API, FP32 kernels, FP64 kernels) compile
+The translation units (host API, FP32 kernels, FP64 kernels, the
+allocation-free diagnostics, the FMA-rate probe) compile
 in parallel and link into one C-ABI library.  The FP64 kernels are built
 without fused multiply-add contraction so that their rounding follows the
 plain double-precision arithmetic they are checked against; the FP32
@@ -25,6 +26,7 @@ UNITS = {
     "lbm_f32.cu": [],
     "lbm_f64.cu": ["--fmad=false"],
     "lbm_static.cu": [],
+    "lbm_probe.cu": [],
 }
 
 

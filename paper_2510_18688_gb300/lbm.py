@@ -54,7 +54,7 @@ EXPORTS = ("lbm_create", "lbm_set_geometry", "lbm_step", "lbm_read_fields",
            "lbm_compute_diagnostics", "lbm_read_diagnostics", "lbm_state_size",
            "lbm_save_state", "lbm_load_state", "lbm_step_count", "lbm_last_error",
            "lbm_status_string", "lbm_destroy", "lbm_diagnostics_noalloc",
-           "lbm_batch_create", "lbm_batch_step", "lbm_batch_destroy")
+           "lbm_batch_create", "lbm_batch_step", "lbm_batch_destroy", "lbm_probe_fma_rate")
 
 _lib = None
 
@@ -91,10 +91,11 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     L.lbm_batch_step.argtypes = [vp, ctypes.c_int64, vp]
     L.lbm_batch_destroy.argtypes = [vp]
     L.lbm_batch_destroy.restype = None
+    L.lbm_probe_fma_rate.argtypes = [ctypes.c_int, dp, vp]
     for fn in ("lbm_create", "lbm_set_geometry", "lbm_step", "lbm_read_fields",
                "lbm_compute_diagnostics", "lbm_read_diagnostics", "lbm_state_size",
                "lbm_save_state", "lbm_load_state", "lbm_diagnostics_noalloc",
-               "lbm_batch_create", "lbm_batch_step"):
+               "lbm_batch_create", "lbm_batch_step", "lbm_probe_fma_rate"):
         getattr(L, fn).restype = ctypes.c_int
     _lib = L
     return L
@@ -191,6 +192,15 @@ def lbm_diagnostics_noalloc(params: LbmParams, pops, lags, phi0, cold_mask, out,
     (see include/lbm.h); returns the status code."""
     return int(load().lbm_diagnostics_noalloc(ctypes.byref(params), pops, lags, phi0,
                                               cold_mask, out, stream))
+
+
+def lbm_probe_fma_rate(precision: str = "fp64", stream=None) -> float:
+    """Measured FMA throughput of the current device in FLOP/s (2 per FMA)."""
+    v = ctypes.c_double()
+    st = load().lbm_probe_fma_rate(LBM_FP64 if precision == "fp64" else LBM_FP32,
+                                   ctypes.byref(v), stream)
+    _check(None, st, "lbm_probe_fma_rate")
+    return v.value
 
 
 def lbm_batch_create(ctxs) -> ctypes.c_void_p:
