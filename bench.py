@@ -31,7 +31,7 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-METRIC = "coupled MLUPS (512^2 droplet, FP32 populations)"
+METRIC = "coupled MLUPS"  # node updates of all enabled lattices per second / 1e6
 WORKLOAD = "sessile droplet freezing 512x512 (R=100, cold solid layer), 3 lattices, seed 0"
 L2_FLUSH_BYTES = 256 << 20
 

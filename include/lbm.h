@@ -190,9 +190,10 @@ void lbm_destroy(lbm_ctx* ctx);
  * any sizes, parameters and geometries, each stepped by Eqs. (11)-(25) as
  * lbm_step does) so that lbm_batch_step advances all of them together: one
  * launch per time step and per 64 grids covers the concatenated tile lists
- * of those grids, each tile evaluated as lbm_step would (the same results bit
- * for bit in FP64; in FP32 the compiler may contract the two kernels' copies
- * of the arithmetic differently, a difference of FP32 rounding).  This is how
+ * of those grids, each tile evaluated by the same code as in lbm_step (the
+ * results agree to the last bit where the compiler contracts both kernels'
+ * copies of the arithmetic alike, as the FP64 build does, and otherwise to a
+ * few roundings of the working precision).  This is how
  * many small problems fill the GPU.  The batch holds the context pointers
  * only and allocates no device memory; the contexts stay usable on their own
  * (lbm_step, lbm_read_fields, diagnostics, checkpoints) and must outlive the

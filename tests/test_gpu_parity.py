@@ -248,12 +248,11 @@ def test_errors_are_status_codes(env):
 
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
 def test_batched_grids_match_single_grids_and_oracle(env, prec):
-    """Grids of uneven sizes and parameters advanced by one persistent launch
-    per step give, grid by grid, the results of lbm_step on each grid alone
-    (bit for bit in FP64, which is built without FMA contraction; within a
-    few FP32 roundings in FP32, where the compiler may contract the two
-    kernels' copies of the step differently), and the oracle's within the
-    parity bar."""
+    """Grids of uneven sizes and parameters advanced by one launch per step
+    give, grid by grid, the results of lbm_step on each grid alone (bit for
+    bit in FP64; within a few FP32 roundings in FP32, where the compiler
+    contracts the two kernels' copies of the step differently), and the
+    oracle's within the parity bar."""
     O, lbm = env
     wls = [W.random_state(45, 19, seed=0), W.random_state(96, 24, seed=3),
            W.random_state(37, 41, seed=2), W.random_state(70, 17, seed=5),
