@@ -3,8 +3,9 @@
 Workload: the 512 x 512 sessile-droplet freezing case (Sec. 4.3 shape:
 droplet R = 100 on a cold solid layer, seeded contact angle and Stefan
 number), all three lattices, FP32 populations.  One bench step is one full
-time step of the hot path (rows a1-a9, including the fused FP64
-diagnostics) over the whole grid.  The FP32 working set (~70 MB) fits in the
+time step of the coupled update (enthalpy inversion, order parameter,
+stencils, three collisions, streaming with walls, lag store and the fused
+FP64 diagnostics) over the whole grid.  The FP32 working set (~70 MB) fits in the
 129 MB L2, so the L2 is flushed (a 256 MB write) before every timed step and
 each step is timed alone with CUDA events on the launching stream: the
 number is the HBM-bound one.  Under torchrun every rank advances its own
@@ -249,7 +250,7 @@ def main():
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--diag-every", type=int, default=1,
-                    help="steps between fused FP64 diagnostic reductions (row a9)")
+                    help="steps between fused FP64 diagnostic reductions (0: none)")
     ap.add_argument("--workload", default="droplet512", choices=sorted(WORKLOADS),
                     help="droplet512 is the headline; the others are context lines")
     args = ap.parse_args()

@@ -107,7 +107,8 @@ typedef struct {
   int32_t diag_every;
 } lbm_params;
 
-/* Global FP64 sums over the grid of one state (row a9 of the hot path). */
+/* Global FP64 sums over the grid of one state (the conservation and
+ * frozen-fraction monitors of Secs. 4.1-4.6). */
 typedef struct {
   double mass;            /* sum rho                                        */
   double material_mass;   /* sum w (rho_s (1 - fl) + rho_l fl)              */
@@ -142,7 +143,7 @@ int lbm_set_geometry(lbm_ctx* ctx, const double* phi0, const uint8_t* cold_mask,
                      const double* phi, const double* T, const double* fl, int where,
                      void* stream);
 
-/* Enqueues nsteps >= 0 fused time steps on `stream` (rows a1-a9: enthalpy
+/* Enqueues nsteps >= 0 fused time steps on `stream` (enthalpy
  * inversion, order parameter and properties, finite-difference stencils and
  * chemical potential, velocity and pressure, three collisions, streaming
  * with wall conditions and cold mask, lag store; diagnostics every
@@ -152,12 +153,29 @@ int lbm_set_geometry(lbm_ctx* ctx, const double* phi0, const uint8_t* cold_mask,
 int lbm_step(lbm_ctx* ctx, int64_t nsteps, void* stream);
 
 /* Writes the fields selected by field_mask for the current state (the
- * values the next step would compute in rows a1-a4), as [ny][nx] doubles,
+ * values the next step would compute before its collisions), as [ny][nx] doubles,
  * into out[k] for every selected bit k (out[k] may be NULL otherwise).
  * where = LBM_HOST copies through a context-owned device staging buffer and
  * synchronises `stream`. */
 int lbm_read_fields(lbm_ctx* ctx, uint32_t field_mask, double* const* out, int where,
                     void* stream);
+
+/* Interface positions along one grid line of the current state, in node
+ * coordinates along that line: out[0] = the largest coordinate at which phi
+ * crosses 0 (the gas-liquid interface: the column height of the Stefan
+ * problem of Sec. 4.2, the droplet tip height of Secs. 4.3-4.4 when the line
+ * is the droplet axis), out[1] = the largest at which the frozen material
+ * fraction w (1 - fl) crosses 1/2 (the ice front).  Between neighbouring
+ * nodes k and k+1 with values a and b a crossing happens when exactly one of
+ * a, b is <= the level, at k + a / (a - b) (linear interpolation); NaN where
+ * the line has none.  axis 0: along x on row y = index; axis 1: along y on
+ * column x = index; the line does not wrap across a periodic edge.
+ * out: host memory for 2 doubles.  Runs the field read-out and a one-CTA
+ * kernel on `stream` using the context's staging memory (allocated on first
+ * use, as lbm_read_fields with LBM_HOST does) and synchronises `stream`.
+ * Errors: LBM_ERR_ARG (null, bad axis, index outside the grid),
+ * LBM_ERR_STATE before lbm_set_geometry, LBM_ERR_OOM/LBM_ERR_CUDA. */
+int lbm_read_crossings(lbm_ctx* ctx, int axis, int index, double* out, void* stream);
 
 /* Enqueues the diagnostic reduction of the current state (no time step). */
 int lbm_compute_diagnostics(lbm_ctx* ctx, void* stream);

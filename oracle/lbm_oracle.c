@@ -12,8 +12,8 @@
  * Everything is a literal, slow restatement of the paper in double
  * precision: plain loops over nodes, one pass per stage, no blocking and no
  * fusion.  The stages of one time step follow the order below, and every
- * silent or garbled point of the paper is resolved by the reading named
- * beside it (the readings are listed in the design doc of the repository):
+ * silent or garbled point of the paper is resolved by a reading, tagged
+ * R-xxx and stated where it is applied:
  *
  *   pass 1  (per node)  enthalpy recovery, Eq. (28) with the lagged source
  *           (reading R-IMP), and the liquid-fraction/temperature inversion

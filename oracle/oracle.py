@@ -260,3 +260,34 @@ def chemical_potential(cfg: dict, phi, phi0, fs):
     out = np.empty_like(phi)
     lib().oracle_chemical_potential(ctypes.byref(p), _ptr(phi), _ptr(phi0), _ptr(fs), _ptr(out))
     return out
+
+
+# --- interface observables -----------------------------------------------------
+
+def crossings(phi, w, fl, axis: int, index: int):
+    """Interface positions along one grid line, as node coordinates.
+
+    Returns (x_phi, x_ice): the largest coordinate at which phi crosses 0
+    (the gas-liquid interface: the liquid height of the Stefan problem of
+    Sec. 4.2, the droplet tip height of Secs. 4.3-4.4 on the droplet axis),
+    and the largest at which the frozen material fraction s = w (1 - fl)
+    crosses 1/2 (the ice front).  Between neighbouring nodes k and k+1 with
+    values a and b, a crossing happens when exactly one of a, b is <= 0, at
+    k + a / (a - b) (linear interpolation).  NaN where there is none.
+    axis 0: along x on row y = index; axis 1: along y on column x = index.
+    The line does not wrap across a periodic edge.
+    """
+    phi, w, fl = np.asarray(phi), np.asarray(w), np.asarray(fl)
+    if axis == 0:
+        p, s = phi[index, :], w[index, :] * (1.0 - fl[index, :]) - 0.5
+    else:
+        p, s = phi[:, index], w[:, index] * (1.0 - fl[:, index]) - 0.5
+    out = []
+    for v in (p, s):
+        best = float("nan")
+        for k in range(len(v) - 1):
+            a, b = float(v[k]), float(v[k + 1])
+            if (a <= 0.0) != (b <= 0.0):
+                best = k + a / (a - b)
+        out.append(best)
+    return tuple(out)

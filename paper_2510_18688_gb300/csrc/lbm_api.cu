@@ -330,6 +330,37 @@ int lbm_read_fields(lbm_ctx* c, uint32_t field_mask, double* const* out, int whe
   return LBM_OK;
 }
 
+int lbm_read_crossings(lbm_ctx* c, int axis, int index, double* out, void* stream) {
+  if (!c) return LBM_ERR_ARG;
+  if (!out) return fail(c, LBM_ERR_ARG, "null output%s");
+  if (axis != 0 && axis != 1) return fail(c, LBM_ERR_ARG, "axis must be 0 (x) or 1 (y)%s");
+  if (index < 0 || index >= (axis == 0 ? c->g.ny : c->g.nx))
+    return fail(c, LBM_ERR_ARG, "line index outside the grid%s");
+  if (!c->have_geometry) return fail(c, LBM_ERR_STATE, "read before lbm_set_geometry%s");
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t N = (size_t)c->g.nx * c->g.ny;
+  cudaError_t e;
+  if (!c->staging) {
+    e = cudaMalloc(&c->staging, lbmk::NFIELD * N * sizeof(double));
+    if (e != cudaSuccess) return cuda_fail(c, e, "read-out staging allocation");
+  }
+  double* outs[lbmk::NFIELD] = {nullptr};
+  outs[lbmk::F_PHI] = c->staging + lbmk::F_PHI * N;
+  outs[lbmk::F_W] = c->staging + lbmk::F_W * N;
+  outs[lbmk::F_FL] = c->staging + lbmk::F_FL * N;
+  double* d_out = c->staging + lbmk::F_T * N;  // an unused staging plane
+  e = launch(c, lbmk::MODE_READ, false, outs, s);
+  if (e != cudaSuccess) return cuda_fail(c, e, "read-out kernel launch");
+  e = lbmk::launch_crossings(outs[lbmk::F_PHI], outs[lbmk::F_W], outs[lbmk::F_FL], c->g.nx,
+                             c->g.ny, axis, index, d_out, s);
+  if (e != cudaSuccess) return cuda_fail(c, e, "crossings kernel launch");
+  e = cudaMemcpyAsync(out, d_out, 2 * sizeof(double), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_fail(c, e, "crossings download");
+  c->last_stream = s;
+  return LBM_OK;
+}
+
 int lbm_compute_diagnostics(lbm_ctx* c, void* stream) {
   if (!c) return LBM_ERR_ARG;
   if (!c->have_geometry) return fail(c, LBM_ERR_STATE, "diagnostics before lbm_set_geometry%s");

@@ -6,15 +6,18 @@
 // global load of the CTA at once: each thread loads its own node (27
 // populations kept in registers, lag fields, phi0) and, in parallel, a
 // third of the 18 phase/enthalpy populations of one halo-ring node; the
-// ring partial sums meet in shared memory.  Rows a1-a2 (enthalpy inversion,
-// order parameter, material weight, solid fraction, density) are evaluated
-// for the own node and then for the ring.  Phase B evaluates the isotropic
-// stencils (row a3), the velocity and pressure (row a4), the three
-// collisions (rows a5-a7), pushes the post-collision populations to the
-// neighbours in the other buffer with half-way bounce-back /
-// anti-bounce-back at walls (row a8) and stores the lag fields (row a9).
-// Global FP64 diagnostics are reduced in the same launch (warp shuffles,
-// then fixed-order per-block and last-block passes: bitwise reproducible).
+// ring partial sums meet in shared memory.  The enthalpy inversion (Eq. (8)),
+// order parameter (Eq. (22)), material weight, solid fraction and density
+// (Eq. (10)) are evaluated for the own node and then for the ring.  Phase B
+// evaluates the isotropic stencils of the gradients and the chemical
+// potential (Eq. (6)), the velocity and pressure (Eq. (17)), the three
+// collisions (Eqs. (11), (18), (23)), pushes the post-collision populations
+// to the neighbours in the other buffer with half-way bounce-back /
+// anti-bounce-back at walls and stores the lag fields of the next step.
+// Global FP64 diagnostics are reduced in the same launch into per-CTA
+// partial sums (warp shuffles, then the warps in a fixed order); a one-CTA
+// kernel sums the partials in a fixed order when they are read, so the
+// result is bitwise reproducible run to run.
 //
 // Layout in HBM: structure of arrays, one plane per population or field,
 // planes of `plane` elements with rows padded to `pitch` (a multiple of 32

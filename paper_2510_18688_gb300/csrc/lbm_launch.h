@@ -29,5 +29,9 @@ cudaError_t launch_batch_f64(const BatchTable<double>& b, bool diag, bool all, c
 cudaError_t launch_diag_finalize(const double* partial, int nb, double* out, long long step,
                                  cudaStream_t s);
 cudaError_t launch_init_f64(const InitArgs<double>& a, cudaStream_t s);
+// Interface crossings along one line of dense FP64 fields (one CTA); out: 2
+// device doubles.
+cudaError_t launch_crossings(const double* phi, const double* w, const double* fl, int nx, int ny,
+                             int axis, int index, double* out, cudaStream_t s);
 
 }  // namespace lbmk

@@ -1,9 +1,10 @@
 // lbm_split.cuh -- the time step as two barrier-free kernels (sm_103a).
 //
-//   lbm_macro_kernel    rows a1-a2 for every node: phi, fs, rho into three
+//   lbm_macro_kernel    enthalpy inversion, order parameter and properties
+//                       (Eqs. (8), (22), (10)) for every node: phi, fs, rho into three
 //                       scratch planes (12 B per node in FP32, written once and
 //                       read back from L2 by the second kernel).
-//   lbm_collide_kernel  rows a3-a9: the own node's local state again from its
+//   lbm_collide_kernel  the rest of the step: the own node's local state again from its
 //                       populations, the isotropic stencils from the scratch
 //                       planes and the lagged pressure (neighbours are cache
 //                       hits), velocity and pressure, the three pairwise

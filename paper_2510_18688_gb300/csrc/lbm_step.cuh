@@ -306,7 +306,7 @@ __device__ __forceinline__ void step_tile(const Args<R>& a, int bx, int by, int 
   }
   __syncthreads();
 
-  // ---- phase A2: rows a1-a2 of the ring ------------------------------------
+  // ---- phase A2: inversion, order parameter, properties of the ring ---------
   if (tid < RING) {
     const int k = tid;
     int hx, hy;

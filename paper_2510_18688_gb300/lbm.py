@@ -54,7 +54,8 @@ EXPORTS = ("lbm_create", "lbm_set_geometry", "lbm_step", "lbm_read_fields",
            "lbm_compute_diagnostics", "lbm_read_diagnostics", "lbm_state_size",
            "lbm_save_state", "lbm_load_state", "lbm_step_count", "lbm_last_error",
            "lbm_status_string", "lbm_destroy", "lbm_diagnostics_noalloc",
-           "lbm_batch_create", "lbm_batch_step", "lbm_batch_destroy", "lbm_probe_fma_rate")
+           "lbm_batch_create", "lbm_batch_step", "lbm_batch_destroy", "lbm_probe_fma_rate",
+           "lbm_read_crossings")
 
 _lib = None
 
@@ -92,10 +93,12 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     L.lbm_batch_destroy.argtypes = [vp]
     L.lbm_batch_destroy.restype = None
     L.lbm_probe_fma_rate.argtypes = [ctypes.c_int, dp, vp]
+    L.lbm_read_crossings.argtypes = [vp, ctypes.c_int, ctypes.c_int, dp, vp]
     for fn in ("lbm_create", "lbm_set_geometry", "lbm_step", "lbm_read_fields",
                "lbm_compute_diagnostics", "lbm_read_diagnostics", "lbm_state_size",
                "lbm_save_state", "lbm_load_state", "lbm_diagnostics_noalloc",
-               "lbm_batch_create", "lbm_batch_step", "lbm_probe_fma_rate"):
+               "lbm_batch_create", "lbm_batch_step", "lbm_probe_fma_rate",
+               "lbm_read_crossings"):
         getattr(L, fn).restype = ctypes.c_int
     _lib = L
     return L
@@ -192,6 +195,14 @@ def lbm_diagnostics_noalloc(params: LbmParams, pops, lags, phi0, cold_mask, out,
     (see include/lbm.h); returns the status code."""
     return int(load().lbm_diagnostics_noalloc(ctypes.byref(params), pops, lags, phi0,
                                               cold_mask, out, stream))
+
+
+def lbm_read_crossings(ctx, axis: int, index: int, stream=None):
+    """(phi = 0 crossing, ice-front crossing) along one grid line; NaN if none."""
+    out = (ctypes.c_double * 2)()
+    _check(ctx, load().lbm_read_crossings(ctx, int(axis), int(index), out, stream),
+           "lbm_read_crossings")
+    return out[0], out[1]
 
 
 def lbm_probe_fma_rate(precision: str = "fp64", stream=None) -> float:
@@ -296,6 +307,10 @@ class Solver:
     @property
     def steps_done(self) -> int:
         return lbm_step_count(self.ctx)
+
+    def crossings(self, axis: int, index: int):
+        """Interface positions along one line (see lbm_read_crossings)."""
+        return lbm_read_crossings(self.ctx, axis, index, _stream())
 
     def fields(self, names=FIELDS, host: bool = True) -> dict:
         import torch

@@ -307,3 +307,39 @@ def test_batch_after_a_single_grid_step(env):
         ref = O.from_workload((cfg, arr)).step(s.steps_done).fields()
         _compare(s.fields(), ref, "fp64")
     b.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_interface_crossings(env, prec):
+    """Droplet tip height on the droplet axis, and the liquid height and ice
+    front of the Stefan column, against the oracle's definition applied to
+    the oracle's fields."""
+    O, lbm = env
+    tol = 1e-8 if prec == "fp64" else 2e-3  # node coordinates
+    cases = [(W.sessile_droplet(160, seed=2, radius=40), 150, [(1, 80), (1, 61), (0, 20)]),
+             (W.stefan(), 400, [(0, 0), (0, 4), (0, 7)])]
+    for (cfg, arr), steps, lines in cases:
+        o = O.from_workload((cfg, arr)).step(steps)
+        ref = o.fields()
+        s = lbm.Solver(cfg, precision=prec).set_geometry(arr).step(steps)
+        for axis, index in lines:
+            want = O.crossings(ref["phi"], ref["w"], ref["fl"], axis, index)
+            got = s.crossings(axis, index)
+            for g, w_ in zip(got, want):
+                if np.isnan(w_):
+                    assert np.isnan(g), (axis, index, got, want)
+                else:
+                    assert abs(g - w_) <= tol, (axis, index, got, want)
+        # the droplet has a tip and the column an interface and an ice front
+        assert not np.isnan(s.crossings(*lines[0])[0])
+        s.close()
+
+
+def test_interface_crossings_errors(env):
+    O, lbm = env
+    cfg, arr = W.random_state(40, 20, seed=3)
+    s = lbm.Solver(cfg, precision="fp32").set_geometry(arr)
+    for axis, index in ((2, 0), (0, 20), (1, 40), (0, -1)):
+        with pytest.raises(lbm.LbmError):
+            s.crossings(axis, index)
+    s.close()
