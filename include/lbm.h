@@ -147,9 +147,16 @@ int lbm_set_geometry(lbm_ctx* ctx, const double* phi0, const uint8_t* cold_mask,
  * inversion, order parameter and properties, finite-difference stencils and
  * chemical potential, velocity and pressure, three collisions, streaming
  * with wall conditions and cold mask, lag store; diagnostics every
- * diag_every steps).  Asynchronous.  Errors: LBM_ERR_STATE before
- * lbm_set_geometry, LBM_ERR_ARG for nsteps < 0, LBM_ERR_CUDA on launch
- * failure. */
+ * diag_every steps).  Asynchronous.  Whole periods of the step sequence
+ * (2 steps, or diag_every steps rounded up to an even count, at most 256)
+ * are replayed from a CUDA graph captured once per context on a private
+ * stream, so a long call costs one graph launch per period instead of one
+ * kernel launch per step; the kernels and their order are those of single
+ * steps, so results do not depend on how steps are grouped into calls.  No
+ * graph is used when `stream` is itself being captured, or when the
+ * environment sets LBM_STEP_GRAPHS=0 at lbm_create.  Errors: LBM_ERR_STATE
+ * before lbm_set_geometry, LBM_ERR_ARG for nsteps < 0, LBM_ERR_CUDA on
+ * launch or capture failure. */
 int lbm_step(lbm_ctx* ctx, int64_t nsteps, void* stream);
 
 /* Writes the fields selected by field_mask for the current state (the
@@ -223,7 +230,9 @@ int lbm_batch_create(lbm_ctx* const* ctxs, int count, lbm_batch** out);
 
 /* Enqueues nsteps time steps of every context of the batch on `stream`
  * (host-asynchronous; diagnostics every diag_every steps of the first
- * context, for all contexts).
+ * context, for all contexts).  Whole periods are replayed from a captured
+ * CUDA graph as in lbm_step (recaptured when a context's parity, geometry
+ * or state changed since).
  * Errors: LBM_ERR_ARG (null batch, nsteps < 0), LBM_ERR_STATE if a context
  * has no geometry, LBM_ERR_CUDA. */
 int lbm_batch_step(lbm_batch* batch, int64_t nsteps, void* stream);

@@ -51,6 +51,14 @@ struct lbm_ctx {
   int64_t diag_step;     // state index of the pending partials
   cudaStream_t last_stream;
   int nblocks;
+  // captured steps: one period of the step sequence, replayed whole
+  bool graphs;           // replay captured periods (default; LBM_STEP_GRAPHS=0 disables)
+  cudaStream_t cap_stream;
+  cudaGraphExec_t graph;
+  int graph_cur;         // buffer parity the graph starts from
+  int64_t graph_phase;   // step index modulo the period it starts from
+  uint64_t gen;          // bumped when geometry or state is replaced
+  uint64_t graph_gen;
   char err[512];
 };
 
@@ -116,7 +124,98 @@ cudaError_t launch(lbm_ctx* c, int mode, bool diag, double* const* outs, cudaStr
   return lbmk::launch_step_f64(a, mode, diag, s);
 }
 
+// Steps of one captured period: the buffer parity repeats every two steps
+// and the diagnostic schedule every diag_every steps.
+int graph_period(int diag_every) {
+  if (diag_every <= 0) return 2;
+  return diag_every % 2 == 0 ? diag_every : 2 * diag_every;
+}
+constexpr int kMaxGraphSteps = 256;
+
+// True when `s` is not being captured by the caller (a captured replay
+// inside a caller's capture is left to plain launches).
+bool stream_free(cudaStream_t s) {
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(s, &cs) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return cs == cudaStreamCaptureStatusNone;
+}
+
+// Records, after a span of steps [first, end) with diagnostics every d > 0
+// steps, that the last diagnosed state is pending.
+void note_diag_span(lbm_ctx* c, int64_t first, int64_t end) {
+  const int64_t d = c->p.diag_every;
+  if (d <= 0 || end <= first) return;
+  const int64_t last = (end - 1) - ((end - 1) % d);
+  if (last < first) return;
+  c->have_diag = true;
+  c->diag_pending = true;
+  c->diag_step = last;
+}
+
+cudaError_t step_launches(lbm_ctx* c, int64_t nsteps, cudaStream_t s) {
+  for (int64_t k = 0; k < nsteps; k++) {
+    const bool diag = c->p.diag_every > 0 && (c->step % c->p.diag_every) == 0;
+    cudaError_t e = launch(c, lbmk::MODE_STEP, diag, nullptr, s);
+    if (e != cudaSuccess) return e;
+    note_diag_span(c, c->step, c->step + 1);
+    c->cur ^= 1;
+    c->step++;
+  }
+  return cudaSuccess;
+}
+
+// The captured period that starts from the context's current parity and
+// phase, captured on a private stream the first time it is needed.
+cudaError_t step_graph(lbm_ctx* c, int period, cudaGraphExec_t* out) {
+  const int64_t phase = c->step % period;
+  if (c->graph && c->graph_cur == c->cur && c->graph_phase == phase && c->graph_gen == c->gen) {
+    *out = c->graph;
+    return cudaSuccess;
+  }
+  if (c->graph) {
+    cudaGraphExecDestroy(c->graph);
+    c->graph = nullptr;
+  }
+  cudaError_t e = cudaSuccess;
+  if (!c->cap_stream) e = cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking);
+  if (e != cudaSuccess) return e;
+  const int cur = c->cur;
+  const int64_t step = c->step, diag_step = c->diag_step;
+  const bool have_diag = c->have_diag, pending = c->diag_pending;
+  e = cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) return e;
+  cudaError_t el = step_launches(c, period, c->cap_stream);
+  cudaGraph_t g = nullptr;
+  e = cudaStreamEndCapture(c->cap_stream, &g);
+  // capture enqueues nothing: the host-side state goes back to the start
+  c->cur = cur;
+  c->step = step;
+  c->diag_step = diag_step;
+  c->have_diag = have_diag;
+  c->diag_pending = pending;
+  if (el != cudaSuccess || e != cudaSuccess) {
+    if (g) cudaGraphDestroy(g);
+    return el != cudaSuccess ? el : e;
+  }
+  e = cudaGraphInstantiate(&c->graph, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) {
+    c->graph = nullptr;
+    return e;
+  }
+  c->graph_cur = cur;
+  c->graph_phase = phase;
+  c->graph_gen = c->gen;
+  *out = c->graph;
+  return cudaSuccess;
+}
+
 void free_all(lbm_ctx* c) {
+  if (c->graph) cudaGraphExecDestroy(c->graph);
+  if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
   void* dev[] = {c->pop[0], c->pop[1], c->lag[0],     c->lag[1],    c->phi0,   c->mask,
                  c->diag_partial, c->diag_out, c->staging, c->in_stage,
                  c->scratch};
@@ -167,6 +266,10 @@ int lbm_create(const lbm_params* params, lbm_ctx** out) {
     // collide pass); the default is the fused one-kernel step
     const char* k = std::getenv("LBM_STEP_KERNEL");
     c->split = k && std::strcmp(k, "split") == 0;
+    // LBM_STEP_GRAPHS=0 launches every step on its own instead of
+    // replaying captured periods
+    const char* gr = std::getenv("LBM_STEP_GRAPHS");
+    c->graphs = !(gr && std::strcmp(gr, "0") == 0);
   }
   c->cf = lbmh::make_coef<float>(*params);
   c->cd = lbmh::make_coef<double>(*params);
@@ -263,6 +366,7 @@ int lbm_set_geometry(lbm_ctx* c, const double* phi0, const uint8_t* cold_mask,
     if (e != cudaSuccess) return cuda_fail(c, e, "set_geometry synchronisation");
   }
   c->step = 0;
+  c->gen++;  // captured steps of the old geometry are stale
   c->have_geometry = true;
   c->have_diag = false;
   c->diag_pending = false;
@@ -275,18 +379,24 @@ int lbm_step(lbm_ctx* c, int64_t nsteps, void* stream) {
   if (nsteps < 0) return fail(c, LBM_ERR_ARG, "nsteps must be >= 0%s");
   if (!c->have_geometry) return fail(c, LBM_ERR_STATE, "lbm_step before lbm_set_geometry%s");
   cudaStream_t s = (cudaStream_t)stream;
-  for (int64_t k = 0; k < nsteps; k++) {
-    const bool diag = c->p.diag_every > 0 && (c->step % c->p.diag_every) == 0;
-    cudaError_t e = launch(c, lbmk::MODE_STEP, diag, nullptr, s);
-    if (e != cudaSuccess) return cuda_fail(c, e, "step kernel launch");
-    if (diag) {
-      c->have_diag = true;
-      c->diag_pending = true;
-      c->diag_step = c->step;
+  int64_t left = nsteps;
+  const int period = graph_period(c->p.diag_every);
+  if (c->graphs && period <= kMaxGraphSteps && left >= period && stream_free(s)) {
+    // whole periods replay one captured graph (same kernels, same order)
+    cudaGraphExec_t g = nullptr;
+    cudaError_t e = step_graph(c, period, &g);
+    if (e != cudaSuccess) return cuda_fail(c, e, "step graph capture");
+    const int64_t reps = left / period;
+    for (int64_t r = 0; r < reps; r++) {
+      e = cudaGraphLaunch(g, s);
+      if (e != cudaSuccess) return cuda_fail(c, e, "step graph launch");
     }
-    c->cur ^= 1;
-    c->step++;
+    note_diag_span(c, c->step, c->step + reps * period);
+    c->step += reps * period;  // the period is even: the parity is unchanged
+    left -= reps * period;
   }
+  cudaError_t e = step_launches(c, left, s);
+  if (e != cudaSuccess) return cuda_fail(c, e, "step kernel launch");
   c->last_stream = s;
   return LBM_OK;
 }
@@ -451,6 +561,7 @@ int lbm_load_state(lbm_ctx* c, const void* host_buf, size_t size, void* stream) 
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return cuda_fail(c, e, "state upload");
   c->step = h.step;
+  c->gen++;  // captured steps start from another parity or phase
   c->have_diag = false;
   c->diag_pending = false;
   c->last_stream = s;
@@ -466,6 +577,9 @@ int lbm_load_state(lbm_ctx* c, const void* host_buf, size_t size, void* stream) 
 struct lbm_batch {
   std::vector<lbm_ctx*> ctx;
   int precision;
+  cudaStream_t cap_stream;
+  cudaGraphExec_t graph;               // one captured period of batch steps
+  std::vector<uint64_t> graph_key;     // (parity, generation) per context, phase
   char err[512];
 };
 
@@ -490,39 +604,142 @@ bool fill_table(lbm_batch* b, int first, int count, lbmk::BatchTable<R>& t) {
   return all;
 }
 
+// Marks, for every context, the state of the batch's last diagnosed step in
+// a span of `n` steps that starts at the first context's step `first0`.
+void note_batch_diag(lbm_batch* b, int64_t first0, int64_t n) {
+  lbm_ctx* c0 = b->ctx[0];
+  const int64_t d = c0->p.diag_every;
+  if (d <= 0 || n <= 0) return;
+  const int64_t end = first0 + n;
+  const int64_t last = (end - 1) - ((end - 1) % d);
+  if (last < first0) return;
+  for (lbm_ctx* c : b->ctx) {
+    c->have_diag = true;
+    c->diag_pending = true;
+    c->diag_step = c->step + (last - first0);
+  }
+}
+
 template <typename R>
-int batch_step_impl(lbm_batch* b, int64_t nsteps, cudaStream_t s) {
+cudaError_t batch_launches(lbm_batch* b, int64_t nsteps, cudaStream_t s,
+                           lbmk::BatchTable<R>& t) {
   const int n = (int)b->ctx.size();
-  std::unique_ptr<lbmk::BatchTable<R>> t(new (std::nothrow) lbmk::BatchTable<R>());
-  if (!t) return LBM_ERR_OOM;
   lbm_ctx* c0 = b->ctx[0];
   for (int64_t k = 0; k < nsteps; k++) {
     const bool diag = c0->p.diag_every > 0 && (c0->step % c0->p.diag_every) == 0;
     for (int first = 0; first < n; first += lbmk::BATCH_MAX_GRIDS) {
       const int count = std::min(n - first, lbmk::BATCH_MAX_GRIDS);
-      const bool all = fill_table<R>(b, first, count, *t);
+      const bool all = fill_table<R>(b, first, count, t);
       cudaError_t e;
       if (sizeof(R) == 4)
-        e = lbmk::launch_batch_f32(*(const lbmk::BatchTable<float>*)(const void*)t.get(), diag,
-                                   all, s);
+        e = lbmk::launch_batch_f32(*(const lbmk::BatchTable<float>*)(const void*)&t, diag, all, s);
       else
-        e = lbmk::launch_batch_f64(*(const lbmk::BatchTable<double>*)(const void*)t.get(), diag,
-                                   all, s);
-      if (e != cudaSuccess) {
-        std::snprintf(b->err, sizeof(b->err), "batch kernel launch: %s", cudaGetErrorString(e));
-        return LBM_ERR_CUDA;
-      }
+        e = lbmk::launch_batch_f64(*(const lbmk::BatchTable<double>*)(const void*)&t, diag, all,
+                                   s);
+      if (e != cudaSuccess) return e;
     }
+    note_batch_diag(b, c0->step, 1);
     for (lbm_ctx* c : b->ctx) {
-      if (diag) {
-        c->have_diag = true;
-        c->diag_pending = true;
-        c->diag_step = c->step;
-      }
       c->cur ^= 1;
       c->step++;
-      c->last_stream = s;
     }
+  }
+  return cudaSuccess;
+}
+
+std::vector<uint64_t> batch_key(const lbm_batch* b, int period) {
+  std::vector<uint64_t> k;
+  k.reserve(2 * b->ctx.size() + 1);
+  for (const lbm_ctx* c : b->ctx) {
+    k.push_back((uint64_t)c->cur);
+    k.push_back(c->gen);
+  }
+  k.push_back((uint64_t)(b->ctx[0]->step % period));
+  return k;
+}
+
+// The captured period of batch steps from the contexts' current parities
+// and phase (captured on a private stream when first needed).
+template <typename R>
+cudaError_t batch_graph(lbm_batch* b, int period, lbmk::BatchTable<R>& t, cudaGraphExec_t* out) {
+  std::vector<uint64_t> key = batch_key(b, period);
+  if (b->graph && key == b->graph_key) {
+    *out = b->graph;
+    return cudaSuccess;
+  }
+  if (b->graph) {
+    cudaGraphExecDestroy(b->graph);
+    b->graph = nullptr;
+  }
+  cudaError_t e = cudaSuccess;
+  if (!b->cap_stream) e = cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking);
+  if (e != cudaSuccess) return e;
+  struct Saved {
+    int cur;
+    int64_t step, diag_step;
+    bool have_diag, pending;
+  };
+  std::vector<Saved> saved;
+  for (const lbm_ctx* c : b->ctx)
+    saved.push_back({c->cur, c->step, c->diag_step, c->have_diag, c->diag_pending});
+  e = cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) return e;
+  cudaError_t el = batch_launches<R>(b, period, b->cap_stream, t);
+  cudaGraph_t g = nullptr;
+  e = cudaStreamEndCapture(b->cap_stream, &g);
+  for (size_t i = 0; i < b->ctx.size(); i++) {
+    lbm_ctx* c = b->ctx[i];
+    c->cur = saved[i].cur;
+    c->step = saved[i].step;
+    c->diag_step = saved[i].diag_step;
+    c->have_diag = saved[i].have_diag;
+    c->diag_pending = saved[i].pending;
+  }
+  if (el != cudaSuccess || e != cudaSuccess) {
+    if (g) cudaGraphDestroy(g);
+    return el != cudaSuccess ? el : e;
+  }
+  e = cudaGraphInstantiate(&b->graph, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) {
+    b->graph = nullptr;
+    return e;
+  }
+  b->graph_key.swap(key);
+  *out = b->graph;
+  return cudaSuccess;
+}
+
+template <typename R>
+int batch_step_impl(lbm_batch* b, int64_t nsteps, cudaStream_t s) {
+  std::unique_ptr<lbmk::BatchTable<R>> t(new (std::nothrow) lbmk::BatchTable<R>());
+  if (!t) return LBM_ERR_OOM;
+  lbm_ctx* c0 = b->ctx[0];
+  int64_t left = nsteps;
+  const int period = graph_period(c0->p.diag_every);
+  cudaError_t e = cudaSuccess;
+  if (c0->graphs && period <= kMaxGraphSteps && left >= period && stream_free(s)) {
+    cudaGraphExec_t g = nullptr;
+    e = batch_graph<R>(b, period, *t, &g);
+    if (e != cudaSuccess) {
+      std::snprintf(b->err, sizeof(b->err), "batch graph capture: %s", cudaGetErrorString(e));
+      return LBM_ERR_CUDA;
+    }
+    const int64_t reps = left / period;
+    for (int64_t r = 0; r < reps && e == cudaSuccess; r++) e = cudaGraphLaunch(g, s);
+    if (e != cudaSuccess) {
+      std::snprintf(b->err, sizeof(b->err), "batch graph launch: %s", cudaGetErrorString(e));
+      return LBM_ERR_CUDA;
+    }
+    note_batch_diag(b, c0->step, reps * period);
+    for (lbm_ctx* c : b->ctx) c->step += reps * period;  // even period: parities unchanged
+    left -= reps * period;
+  }
+  e = batch_launches<R>(b, left, s, *t);
+  for (lbm_ctx* c : b->ctx) c->last_stream = s;
+  if (e != cudaSuccess) {
+    std::snprintf(b->err, sizeof(b->err), "batch kernel launch: %s", cudaGetErrorString(e));
+    return LBM_ERR_CUDA;
   }
   return LBM_OK;
 }
@@ -563,6 +780,11 @@ int lbm_batch_step(lbm_batch* b, int64_t nsteps, void* stream) {
                                   : batch_step_impl<double>(b, nsteps, s);
 }
 
-void lbm_batch_destroy(lbm_batch* b) { delete b; }
+void lbm_batch_destroy(lbm_batch* b) {
+  if (!b) return;
+  if (b->graph) cudaGraphExecDestroy(b->graph);
+  if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
+  delete b;
+}
 
 }  // extern "C"

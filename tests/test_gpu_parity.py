@@ -343,3 +343,53 @@ def test_interface_crossings_errors(env):
         with pytest.raises(lbm.LbmError):
             s.crossings(axis, index)
     s.close()
+
+
+@pytest.mark.parametrize("prec,diag_every", [("fp32", 0), ("fp32", 3), ("fp64", 4)])
+def test_captured_periods_match_single_launches(env, prec, diag_every):
+    """Steps replayed from a captured graph (long calls) give the state,
+    step count and diagnostics of the same steps launched one by one, from
+    any starting parity and phase."""
+    O, lbm = env
+    cfg, arr = W.random_state(70, 45, seed=21)
+    a = lbm.Solver(cfg, precision=prec, diag_every=diag_every).set_geometry(arr)
+    b = lbm.Solver(cfg, precision=prec, diag_every=diag_every).set_geometry(arr)
+    a.step(1).step(37).step(20)
+    for _ in range(58):
+        b.step(1)
+    assert a.steps_done == b.steps_done == 58
+    fa, fb = a.fields(), b.fields()
+    for k in FIELDS:
+        assert np.array_equal(fa[k], fb[k]), k
+    if diag_every:
+        assert a.diagnostics(compute=False) == b.diagnostics(compute=False)
+    # a new geometry invalidates what was captured for the old one
+    _, arr2 = W.random_state(70, 45, seed=22)
+    a.set_geometry(arr2).step(30)
+    c = lbm.Solver(cfg, precision=prec, diag_every=diag_every).set_geometry(arr2)
+    for _ in range(30):
+        c.step(1)
+    fa, fc = a.fields(), c.fields()
+    for k in FIELDS:
+        assert np.array_equal(fa[k], fc[k]), k
+    for s in (a, b, c):
+        s.close()
+
+
+def test_batch_captured_periods_match_single_launches(env):
+    O, lbm = env
+    wls = [W.random_state(45, 19, seed=30), W.random_state(66, 40, seed=31)]
+    sa = [lbm.Solver(c, precision="fp32", diag_every=5).set_geometry(a) for c, a in wls]
+    sb = [lbm.Solver(c, precision="fp32", diag_every=5).set_geometry(a) for c, a in wls]
+    ba, bb = lbm.Batch(sa), lbm.Batch(sb)
+    ba.step(3).step(41)
+    for _ in range(44):
+        bb.step(1)
+    for x, y in zip(sa, sb):
+        assert x.steps_done == y.steps_done == 44
+        fx, fy = x.fields(), y.fields()
+        for k in FIELDS:
+            assert np.array_equal(fx[k], fy[k]), k
+        assert x.diagnostics(compute=False) == y.diagnostics(compute=False)
+    ba.close()
+    bb.close()
