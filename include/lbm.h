@@ -148,7 +148,7 @@ int lbm_set_geometry(lbm_ctx* ctx, const double* phi0, const uint8_t* cold_mask,
  * chemical potential, velocity and pressure, three collisions, streaming
  * with wall conditions and cold mask, lag store; diagnostics every
  * diag_every steps).  Asynchronous.  Whole periods of the step sequence
- * (2 steps, or diag_every steps rounded up to an even count, at most 256)
+ * (a multiple of 2 and of diag_every, at least 32 steps; none above 256)
  * are replayed from a CUDA graph captured once per context on a private
  * stream, so a long call costs one graph launch per period instead of one
  * kernel launch per step; the kernels and their order are those of single

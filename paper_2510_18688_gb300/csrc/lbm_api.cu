@@ -125,10 +125,12 @@ cudaError_t launch(lbm_ctx* c, int mode, bool diag, double* const* outs, cudaStr
 }
 
 // Steps of one captured period: the buffer parity repeats every two steps
-// and the diagnostic schedule every diag_every steps.
+// and the diagnostic schedule every diag_every steps; short periods are
+// repeated up to at least 32 steps so that one graph launch covers many
+// kernels.
 int graph_period(int diag_every) {
-  if (diag_every <= 0) return 2;
-  return diag_every % 2 == 0 ? diag_every : 2 * diag_every;
+  const int base = diag_every <= 0 ? 2 : (diag_every % 2 == 0 ? diag_every : 2 * diag_every);
+  return base >= 32 ? base : base * ((32 + base - 1) / base);
 }
 constexpr int kMaxGraphSteps = 256;
 

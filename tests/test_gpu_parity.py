@@ -354,10 +354,10 @@ def test_captured_periods_match_single_launches(env, prec, diag_every):
     cfg, arr = W.random_state(70, 45, seed=21)
     a = lbm.Solver(cfg, precision=prec, diag_every=diag_every).set_geometry(arr)
     b = lbm.Solver(cfg, precision=prec, diag_every=diag_every).set_geometry(arr)
-    a.step(1).step(37).step(20)
-    for _ in range(58):
+    a.step(1).step(77).step(40)
+    for _ in range(118):
         b.step(1)
-    assert a.steps_done == b.steps_done == 58
+    assert a.steps_done == b.steps_done == 118
     fa, fb = a.fields(), b.fields()
     for k in FIELDS:
         assert np.array_equal(fa[k], fb[k]), k
@@ -365,9 +365,9 @@ def test_captured_periods_match_single_launches(env, prec, diag_every):
         assert a.diagnostics(compute=False) == b.diagnostics(compute=False)
     # a new geometry invalidates what was captured for the old one
     _, arr2 = W.random_state(70, 45, seed=22)
-    a.set_geometry(arr2).step(30)
+    a.set_geometry(arr2).step(70)
     c = lbm.Solver(cfg, precision=prec, diag_every=diag_every).set_geometry(arr2)
-    for _ in range(30):
+    for _ in range(70):
         c.step(1)
     fa, fc = a.fields(), c.fields()
     for k in FIELDS:
@@ -382,11 +382,11 @@ def test_batch_captured_periods_match_single_launches(env):
     sa = [lbm.Solver(c, precision="fp32", diag_every=5).set_geometry(a) for c, a in wls]
     sb = [lbm.Solver(c, precision="fp32", diag_every=5).set_geometry(a) for c, a in wls]
     ba, bb = lbm.Batch(sa), lbm.Batch(sb)
-    ba.step(3).step(41)
-    for _ in range(44):
+    ba.step(3).step(81)
+    for _ in range(84):
         bb.step(1)
     for x, y in zip(sa, sb):
-        assert x.steps_done == y.steps_done == 44
+        assert x.steps_done == y.steps_done == 84
         fx, fy = x.fields(), y.fields()
         for k in FIELDS:
             assert np.array_equal(fx[k], fy[k]), k
