@@ -68,10 +68,10 @@ WORKLOADS = {
 }
 
 
-def algorithmic_bytes_per_node(esize: int, has_mask: bool) -> int:
+def algorithmic_bytes_per_node(esize: int, has_mask: bool, pop_bytes: int = 0) -> int:
     """27 populations read and written, 6 lag fields read and written, phi0
     read, mask byte read."""
-    return 2 * 27 * esize + 2 * 6 * esize + esize + (1 if has_mask else 0)
+    return 2 * 27 * (pop_bytes or esize) + 2 * 6 * esize + esize + (1 if has_mask else 0)
 
 
 def measured_peak():
@@ -98,7 +98,8 @@ def kernel_source_hash() -> str:
 
 def profile_name(workload: str, precision: str) -> str:
     kind = "batch" if workload.startswith("batch") else "step"
-    return f"lbm_{kind}_{'f32' if precision == 'fp32' else 'f64'}_{workload}.md"
+    tag = {"fp32": "f32", "fp64": "f64", "fp16s": "f16s"}[precision]
+    return f"lbm_{kind}_{tag}_{workload}.md"
 
 
 def profiled_value(workload: str, precision: str, key: str):
@@ -247,7 +248,8 @@ def main():
     ap.add_argument("--steps", type=int, default=4000)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64", "fp16s"],
+                    help="fp16s: FP16 population storage, FP32 arithmetic")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--diag-every", type=int, default=1,
                     help="steps between fused FP64 diagnostic reductions (0: none)")
@@ -366,9 +368,10 @@ def main():
         if pg:
             pg.destroy_process_group()
         return
-    esize = 4 if args.precision == "fp32" else 8
+    esize = 8 if args.precision == "fp64" else 4
+    pop_bytes = 2 if args.precision == "fp16s" else esize
     # node-weighted bytes per node (grids with a cold mask read one more byte)
-    bpn = sum(algorithmic_bytes_per_node(esize, "mask" in a) * c["nx"] * c["ny"]
+    bpn = sum(algorithmic_bytes_per_node(esize, "mask" in a, pop_bytes) * c["nx"] * c["ny"]
               for c, a in wls) / n
     peak, peak_src = measured_peak()
     achieved = bpn * n / (t_step * 1e-3) / 1e9
@@ -393,7 +396,8 @@ def main():
         "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_step,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f32" if esize == 4 else "f64", "data": "synthetic",
+        "dtype": {"fp32": "f32", "fp64": "f64", "fp16s": "f32 (f16 storage)"}[args.precision],
+        "data": "synthetic",
         "config": {"workload": workload_name + f", seed {rank}",
                    "grid": ([wls[0][0]["nx"], wls[0][0]["ny"]] if len(wls) == 1
                             else f"{len(wls)} grids, {n} nodes"),

@@ -31,7 +31,8 @@ struct lbm_ctx {
   Geom g;
   Coef<float> cf;
   Coef<double> cd;
-  size_t esize;          // bytes per real
+  size_t esize;          // bytes per real of the lag fields and phi0
+  size_t pop_esize;      // bytes per stored population
   void* pop[2];
   void* lag[2];
   void* phi0;
@@ -83,14 +84,14 @@ int cuda_fail(lbm_ctx* c, cudaError_t e, const char* what) {
   return e == cudaErrorMemoryAllocation ? LBM_ERR_OOM : LBM_ERR_CUDA;
 }
 
-template <typename R>
-Args<R> step_args(lbm_ctx* c, const Coef<R>& coef) {
-  Args<R> a;
+template <typename R, typename S = R>
+Args<R, S> step_args(lbm_ctx* c, const Coef<R>& coef) {
+  Args<R, S> a;
   std::memset(&a, 0, sizeof(a));
   a.g = c->g;
   a.c = coef;
-  a.pin = (const R*)c->pop[c->cur];
-  a.pout = (R*)c->pop[c->cur ^ 1];
+  a.pin = (const S*)c->pop[c->cur];
+  a.pout = (S*)c->pop[c->cur ^ 1];
   a.lin = (const R*)c->lag[c->cur];
   a.lout = (R*)c->lag[c->cur ^ 1];
   a.phi0 = (const R*)c->phi0;
@@ -117,6 +118,12 @@ cudaError_t launch(lbm_ctx* c, int mode, bool diag, double* const* outs, cudaStr
     if (outs)
       for (int k = 0; k < lbmk::NFIELD; k++) a.out[k] = outs[k];
     return lbmk::launch_step_f32(a, mode, diag, s);
+  }
+  if (c->p.precision == LBM_FP16S) {
+    Args<float, __half> a = step_args<float, __half>(c, c->cf);
+    if (outs)
+      for (int k = 0; k < lbmk::NFIELD; k++) a.out[k] = outs[k];
+    return lbmk::launch_step_f16s(a, mode, diag, s);
   }
   Args<double> a = step_args<double>(c, c->cd);
   if (outs)
@@ -261,13 +268,14 @@ int lbm_create(const lbm_params* params, lbm_ctx** out) {
   if (!c) return LBM_ERR_OOM;
   std::memset(c, 0, sizeof(*c));
   c->p = *params;
-  c->esize = params->precision == LBM_FP32 ? sizeof(float) : sizeof(double);
+  c->esize = params->precision == LBM_FP64 ? sizeof(double) : sizeof(float);
+  c->pop_esize = params->precision == LBM_FP16S ? sizeof(__half) : c->esize;
   c->g = lbmh::make_geom(*params);
   {
     // LBM_STEP_KERNEL=split selects the two-kernel step (macro pass +
     // collide pass); the default is the fused one-kernel step
     const char* k = std::getenv("LBM_STEP_KERNEL");
-    c->split = k && std::strcmp(k, "split") == 0;
+    c->split = k && std::strcmp(k, "split") == 0 && params->precision != LBM_FP16S;
     // LBM_STEP_GRAPHS=0 launches every step on its own instead of
     // replaying captured periods
     const char* gr = std::getenv("LBM_STEP_GRAPHS");
@@ -280,7 +288,7 @@ int lbm_create(const lbm_params* params, lbm_ctx** out) {
   const size_t P = (size_t)c->g.plane;
   cudaError_t e = cudaSuccess;
   for (int b = 0; b < 2 && e == cudaSuccess; b++) {
-    e = cudaMalloc(&c->pop[b], 27 * P * c->esize);
+    e = cudaMalloc(&c->pop[b], 27 * P * c->pop_esize);
     if (e == cudaSuccess) e = cudaMalloc(&c->lag[b], lbmk::NLAG * P * c->esize);
   }
   if (e == cudaSuccess) e = cudaMalloc(&c->phi0, P * c->esize);
@@ -354,6 +362,13 @@ int lbm_set_geometry(lbm_ctx* c, const double* phi0, const uint8_t* cold_mask,
     a.pout = (float*)c->pop[0]; a.lout = (float*)c->lag[0]; a.phi0_out = (float*)c->phi0;
     a.mask_out = c->mask; a.phi0 = d_phi0; a.mask = d_mask; a.phi = d_phi; a.T = d_T; a.fl = d_fl;
     e = lbmk::launch_init_f32(a, s);
+  } else if (c->p.precision == LBM_FP16S) {
+    InitArgs<float, __half> a;
+    std::memset(&a, 0, sizeof(a));
+    a.g = c->g; a.c = c->cf;
+    a.pout = (__half*)c->pop[0]; a.lout = (float*)c->lag[0]; a.phi0_out = (float*)c->phi0;
+    a.mask_out = c->mask; a.phi0 = d_phi0; a.mask = d_mask; a.phi = d_phi; a.T = d_T; a.fl = d_fl;
+    e = lbmk::launch_init_f16s(a, s);
   } else {
     InitArgs<double> a;
     std::memset(&a, 0, sizeof(a));
@@ -517,7 +532,7 @@ int lbm_read_diagnostics(lbm_ctx* c, lbm_diag* out) {
 
 int lbm_state_size(const lbm_ctx* c, size_t* bytes) {
   if (!c || !bytes) return LBM_ERR_ARG;
-  *bytes = sizeof(StateHeader) + (27 + lbmk::NLAG) * (size_t)c->g.plane * c->esize;
+  *bytes = sizeof(StateHeader) + (27 * c->pop_esize + lbmk::NLAG * c->esize) * (size_t)c->g.plane;
   return LBM_OK;
 }
 
@@ -532,7 +547,7 @@ int lbm_save_state(lbm_ctx* c, void* host_buf, size_t capacity, void* stream) {
                    c->step};
   std::memcpy(host_buf, &h, sizeof(h));
   char* dst = (char*)host_buf + sizeof(h);
-  const size_t pb = 27 * (size_t)c->g.plane * c->esize;
+  const size_t pb = 27 * (size_t)c->g.plane * c->pop_esize;
   cudaError_t e = cudaMemcpyAsync(dst, c->pop[c->cur], pb, cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(dst + pb, c->lag[c->cur], lbmk::NLAG * (size_t)c->g.plane * c->esize,
@@ -555,7 +570,7 @@ int lbm_load_state(lbm_ctx* c, const void* host_buf, size_t size, void* stream) 
     return fail(c, LBM_ERR_ARG, "state does not match this context%s");
   cudaStream_t s = (cudaStream_t)stream;
   const char* src = (const char*)host_buf + sizeof(h);
-  const size_t pb = 27 * (size_t)c->g.plane * c->esize;
+  const size_t pb = 27 * (size_t)c->g.plane * c->pop_esize;
   cudaError_t e = cudaMemcpyAsync(c->pop[c->cur], src, pb, cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(c->lag[c->cur], src + pb, lbmk::NLAG * (size_t)c->g.plane * c->esize,
@@ -756,6 +771,7 @@ int lbm_batch_create(lbm_ctx* const* ctxs, int count, lbm_batch** out) {
   for (int i = 0; i < count; i++) {
     if (!ctxs[i]) return LBM_ERR_ARG;
     if (ctxs[i]->p.precision != ctxs[0]->p.precision) return LBM_ERR_ARG;
+    if (ctxs[i]->p.precision == LBM_FP16S) return LBM_ERR_UNSUPPORTED;
     for (int j = 0; j < i; j++)
       if (ctxs[j] == ctxs[i]) return LBM_ERR_ARG;
   }

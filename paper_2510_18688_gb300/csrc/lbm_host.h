@@ -58,7 +58,7 @@ inline int validate(const lbm_params* p, char* err, size_t n) {
     std::snprintf(err, n, "grid of %d x %d nodes is too large", p->nx, p->ny);
     return LBM_ERR_ARG;
   }
-  if (p->precision != LBM_FP32 && p->precision != LBM_FP64) {
+  if (p->precision != LBM_FP32 && p->precision != LBM_FP64 && p->precision != LBM_FP16S) {
     std::snprintf(err, n, "unknown precision %d", p->precision);
     return LBM_ERR_ARG;
   }

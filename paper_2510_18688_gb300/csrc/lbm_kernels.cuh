@@ -27,6 +27,9 @@
 #pragma once
 
 #include <cstdint>
+#include <type_traits>
+
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 namespace lbmk {
@@ -91,12 +94,14 @@ struct Geom {
   int has_mask;
 };
 
-template <typename R>
+// R: arithmetic type; S: storage type of the populations (R, or __half
+// for FP16 storage with FP32 arithmetic).
+template <typename R, typename S = R>
 struct Args {
   Geom g;
   Coef<R> c;
-  const R* __restrict__ pin;   // 27 planes
-  R* __restrict__ pout;        // 27 planes
+  const S* __restrict__ pin;   // 27 planes
+  S* __restrict__ pout;        // 27 planes
   const R* __restrict__ lin;   // NLAG planes
   R* __restrict__ lout;        // NLAG planes
   const R* __restrict__ phi0;
@@ -105,11 +110,11 @@ struct Args {
   double* diag_partial;        // [NDIAG][nblocks] per-CTA partial sums
 };
 
-template <typename R>
+template <typename R, typename S = R>
 struct InitArgs {
   Geom g;
   Coef<R> c;
-  R* __restrict__ pout;
+  S* __restrict__ pout;
   R* __restrict__ lout;
   R* __restrict__ phi0_out;
   uint8_t* __restrict__ mask_out;
@@ -193,6 +198,36 @@ __device__ __forceinline__ void cold_mask_h(const Coef<R>& c, R w, R phi0, R* h)
 // Canonical summation order of the phase and enthalpy populations, shared
 // by the own-node and the ring paths so that a node's sums do not depend on
 // which CTA evaluates it: g = (g0..g5) + (g6..g8), h = (h0..h2) + (h3..h8).
+// ---------------------------------------------------------------------------
+// population storage: the arithmetic type itself, or FP16 (round to nearest)
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ float ldp(const float* p) { return *p; }
+__device__ __forceinline__ double ldp(const double* p) { return *p; }
+__device__ __forceinline__ float ldp(const __half* p) { return __half2float(*p); }
+__device__ __forceinline__ void stp(float* p, float v) { *p = v; }
+__device__ __forceinline__ void stp(double* p, double v) { *p = v; }
+__device__ __forceinline__ void stp(__half* p, float v) { *p = __float2half_rn(v); }
+
+// With FP16 storage the rest populations g0 and h0, which carry the order
+// parameter and the enthalpy (values of order 1 to 10), are stored as
+// differences from references that the writer and the next reader of the
+// same node both hold in FP32: 2 w - 1 + phi0 (= phi where w is not
+// clamped) for g0 and w rho_l L fl (the latent part of rho H, Eq. (8)) for
+// h0, from the lag fields w, fl written with them.  FP16 then holds only the
+// small remainders.  Other populations and other storage types: no shift.
+template <typename S>
+constexpr bool kShiftRest = std::is_same<S, __half>::value;
+
+template <typename R>
+__device__ __forceinline__ R rest_ref_g(R w, R phi0) {
+  return R(2) * w - R(1) + phi0;
+}
+template <typename R>
+__device__ __forceinline__ R rest_ref_h(const Coef<R>& c, R w, R fl) {
+  return w * c.rho_l * c.latent * fl;
+}
+
 template <typename R>
 __device__ __forceinline__ R sum_g(const R* v) {
   return (v[0] + v[1] + v[2] + v[3] + v[4] + v[5]) + (v[6] + v[7] + v[8]);
@@ -360,8 +395,8 @@ static __global__ void __launch_bounds__(NT) lbm_diag_finalize_kernel(const doub
 // initial state
 // ---------------------------------------------------------------------------
 
-template <typename R>
-__global__ void __launch_bounds__(NT) lbm_init_kernel(const InitArgs<R> a) {
+template <typename R, typename S = R>
+__global__ void __launch_bounds__(NT) lbm_init_kernel(const InitArgs<R, S> a) {
   const Geom& g = a.g;
   const Coef<R>& c = a.c;
   const long long P = g.plane;
@@ -412,11 +447,15 @@ __global__ void __launch_bounds__(NT) lbm_init_kernel(const InitArgs<R> a) {
   const R C = heat_cap(c, fs, w);
   const R rrC = qdiv(c.rr, C);
   const R emu = c.eta * muphi;
+  const R sg0 = kShiftRest<S> ? rest_ref_g(w, q0) : R(0);
+  const R sh0 = kShiftRest<S> ? rest_ref_h(c, w, fl) : R(0);
 #pragma unroll
   for (int i = 0; i < 9; i++) {
-    a.pout[i * P + n] = R(0);
-    a.pout[(9 + i) * P + n] = (i == 0) ? phi + (qw<R>(0) - R(1)) * emu : qw<R>(i) * emu;
-    a.pout[(18 + i) * P + n] = heq_i<R>(i, rhoH, C, T, c.rr, rrC, R(0), R(0), R(0));
+    stp(a.pout + i * P + n, R(0));
+    stp(a.pout + (9 + i) * P + n,
+        (i == 0) ? phi + (qw<R>(0) - R(1)) * emu - sg0 : qw<R>(i) * emu);
+    stp(a.pout + (18 + i) * P + n,
+        heq_i<R>(i, rhoH, C, T, c.rr, rrC, R(0), R(0), R(0)) - (i == 0 ? sh0 : R(0)));
   }
   a.lout[LAG_FL * P + n] = fl;
   a.lout[LAG_W * P + n] = w;

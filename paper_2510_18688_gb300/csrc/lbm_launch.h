@@ -22,6 +22,9 @@ cudaError_t launch_step_f64(const Args<double>& a, int mode, bool diag, cudaStre
 cudaError_t launch_split_f32(const SplitArgs<float>& a, bool diag, cudaStream_t s);
 cudaError_t launch_split_f64(const SplitArgs<double>& a, bool diag, cudaStream_t s);
 cudaError_t launch_init_f32(const InitArgs<float>& a, cudaStream_t s);
+// FP16 population storage, FP32 arithmetic.
+cudaError_t launch_step_f16s(const Args<float, __half>& a, int mode, bool diag, cudaStream_t s);
+cudaError_t launch_init_f16s(const InitArgs<float, __half>& a, cudaStream_t s);
 // Up to BATCH_MAX_GRIDS grids in one launch, one CTA per tile.
 cudaError_t launch_batch_f32(const BatchTable<float>& b, bool diag, bool all, cudaStream_t s);
 cudaError_t launch_batch_f64(const BatchTable<double>& b, bool diag, bool all, cudaStream_t s);

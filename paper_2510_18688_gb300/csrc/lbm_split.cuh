@@ -218,8 +218,8 @@ __global__ void __launch_bounds__(NT, sizeof(R) == 4 ? LBM_MIN_BLOCKS_F32 : 1)
       for (int i = 0; i < 9; i++) gq[i] = pn[(9 + i) * P];
       const R phuxp = a.lin[LAG_PHUX * P + n];
       const R phuyp = a.lin[LAG_PHUY * P + n];
-      if (inner) collide_phase<R, true>(g, c, out + 9 * P, P, gx, gy, n, gq, phi, mdot, phuxp, phuyp, M);
-      else collide_phase<R, false>(g, c, out + 9 * P, P, gx, gy, n, gq, phi, mdot, phuxp, phuyp, M);
+      if (inner) collide_phase<R, true>(g, c, out + 9 * P, P, gx, gy, n, gq, phi, mdot, phuxp, phuyp, M, R(0));
+      else collide_phase<R, false>(g, c, out + 9 * P, P, gx, gy, n, gq, phi, mdot, phuxp, phuyp, M, R(0));
     }
     if (lat & LAT_HEAT) {
       R hq[9];
@@ -229,8 +229,8 @@ __global__ void __launch_bounds__(NT, sizeof(R) == 4 ? LBM_MIN_BLOCKS_F32 : 1)
 #pragma unroll
         for (int i = 0; i < 9; i++) hq[i] = pn[(18 + i) * P];
       }
-      if (inner) collide_heat<R, true>(g, c, out + 18 * P, P, gx, gy, n, hq, fs, L.w, T, L.rhoH, mdot, M);
-      else collide_heat<R, false>(g, c, out + 18 * P, P, gx, gy, n, hq, fs, L.w, T, L.rhoH, mdot, M);
+      if (inner) collide_heat<R, true>(g, c, out + 18 * P, P, gx, gy, n, hq, fs, L.w, T, L.rhoH, mdot, M, R(0));
+      else collide_heat<R, false>(g, c, out + 18 * P, P, gx, gy, n, hq, fs, L.w, T, L.rhoH, mdot, M, R(0));
     }
     a.lout[LAG_FL * P + n] = L.fl;
     a.lout[LAG_W * P + n] = L.w;

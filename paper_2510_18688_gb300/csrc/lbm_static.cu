@@ -57,6 +57,10 @@ extern "C" int lbm_diagnostics_noalloc(const lbm_params* params, const void* pop
     std::fprintf(stderr, "lbm_diagnostics_noalloc: %s\n", err);
     return st;
   }
+  if (params->precision == LBM_FP16S) {
+    std::fprintf(stderr, "lbm_diagnostics_noalloc: FP16 population storage is not supported\n");
+    return LBM_ERR_UNSUPPORTED;
+  }
   lbmk::Geom g = lbmh::make_geom(*params);
   g.has_mask = cold_mask ? 1 : 0;
   const dim3 grid = lbmk::grid_dims(g);

@@ -38,23 +38,31 @@ __device__ __forceinline__ double ld_sum(const double* p) {
   return v;
 }
 
+// Own-node population load: plain (kept in shared memory afterwards) or
+// through ld_sum (re-read in phase B).
+template <bool PLAIN, typename S>
+__device__ __forceinline__ auto ld_pop(const S* p) {
+  if constexpr (PLAIN || std::is_same<S, __half>::value) return ldp(p);
+  else return ld_sum(p);
+}
+
 // Store of one post-collision population of direction i from node (x, y)
 // (index n) into the destination buffer.  INNER: the link stays in the grid.
 // For the enthalpy lattice (HEAT) a link leaving through a Dirichlet wall
 // returns by anti-bounce-back, through an adiabatic wall by bounce-back.
-template <typename R, bool INNER, bool HEAT>
-__device__ __forceinline__ void push(const Geom& g, const Coef<R>& c, R* __restrict__ plane0,
+template <typename R, bool INNER, bool HEAT, typename S>
+__device__ __forceinline__ void push(const Geom& g, const Coef<R>& c, S* __restrict__ plane0,
                                      int P, int i, int x, int y, int n, R v) {
   if (INNER) {
-    plane0[i * P + n + qy(i) * g.pitch + qx(i)] = v;
+    stp(plane0 + i * P + n + qy(i) * g.pitch + qx(i), v);
   } else {
     int wall;
     const long long t = stream_target(g, x, y, qx(i), qy(i), wall);
     if (t >= 0) {
-      plane0[i * P + (int)t] = v;
+      stp(plane0 + i * P + (int)t, v);
     } else {
       if (HEAT && g.bc[wall] == BC_DIRICHLET) v = -v + R(2) * qw<R>(i) * c.rr * c.T_wall[wall];
-      plane0[qopp(i) * P + n] = v;
+      stp(plane0 + qopp(i) * P + n, v);
     }
   }
 }
@@ -72,8 +80,8 @@ struct Macro {
 // weight 1/9 and (5,7), (6,8) with weight 1/36.
 
 // Flow collision Eqs. (11), (14)-(16) and push.
-template <typename R, bool INNER>
-__device__ __forceinline__ void collide_flow(const Geom& g, const Coef<R>& c, R* __restrict__ out,
+template <typename R, bool INNER, typename S>
+__device__ __forceinline__ void collide_flow(const Geom& g, const Coef<R>& c, S* __restrict__ out,
                                              int P, int x, int y, int n, const R* f, R rho,
                                              const Macro<R>& M) {
   const R itau = qdiv(R(1), M.tauf);
@@ -113,11 +121,12 @@ __device__ __forceinline__ void collide_flow(const Geom& g, const Coef<R>& c, R*
 }
 
 // Phase-field collision Eqs. (18)-(20) and push.
-template <typename R, bool INNER>
+// rest0: subtracted from the stored rest population (FP16 storage shift).
+template <typename R, bool INNER, typename S>
 __device__ __forceinline__ void collide_phase(const Geom& g, const Coef<R>& c,
-                                              R* __restrict__ out, int P, int x, int y, int n,
+                                              S* __restrict__ out, int P, int x, int y, int n,
                                               const R* gq, R phi, R mdot, R phuxp, R phuyp,
-                                              const Macro<R>& M) {
+                                              const Macro<R>& M, R rest0) {
   const R itg = c.inv_tau_g;
   const R omg = R(1) - itg;
   const R gcoef = R(1) - R(0.5) * itg;
@@ -130,7 +139,7 @@ __device__ __forceinline__ void collide_phase(const Geom& g, const Coef<R>& c,
   {
     const R geq0 = phi + (qw<R>(0) - R(1)) * emu;
     push<R, INNER, false>(g, c, out, P, 0, x, y, n,
-                          gq[0] * omg + itg * geq0 + gcoef * qw<R>(0) * phi * mdot);
+                          gq[0] * omg + itg * geq0 + gcoef * qw<R>(0) * phi * mdot - rest0);
   }
 #pragma unroll
   for (int i = 1; i <= 8; i++) {
@@ -145,10 +154,10 @@ __device__ __forceinline__ void collide_phase(const Geom& g, const Coef<R>& c,
 }
 
 // Enthalpy TRT collision Eqs. (23)-(27) and push.
-template <typename R, bool INNER>
-__device__ __forceinline__ void collide_heat(const Geom& g, const Coef<R>& c, R* __restrict__ out,
+template <typename R, bool INNER, typename S>
+__device__ __forceinline__ void collide_heat(const Geom& g, const Coef<R>& c, S* __restrict__ out,
                                              int P, int x, int y, int n, const R* h, R fs, R w,
-                                             R T, R rhoH, R mdot, const Macro<R>& M) {
+                                             R T, R rhoH, R mdot, const Macro<R>& M, R rest0) {
   const R lam = interp(fs, w, c.lam_s, c.lam_l, c.lam_g);
   const R taua = R(0.5) + qdiv(lam, c.rr3);
   const R taus = qdiv(taua, R(2) * taua - R(1));
@@ -161,7 +170,7 @@ __device__ __forceinline__ void collide_heat(const Geom& g, const Coef<R>& c, R*
     // rest population: purely symmetric
     const R heq0 = rhoH - rrT + qw<R>(0) * (rrT - CT * M.uu * R(1.5));
     push<R, INNER, true>(g, c, out, P, 0, x, y, n,
-                         h[0] - (h[0] - heq0) * is + qw<R>(0) * Hsrc);
+                         h[0] - (h[0] - heq0) * is + qw<R>(0) * Hsrc - rest0);
   }
 #pragma unroll
   for (int i = 1; i <= 8; i++) {
@@ -183,8 +192,8 @@ __device__ __forceinline__ void collide_heat(const Geom& g, const Coef<R>& c, R*
 // TX x TY nodes.  b / nb: the tile's index and the grid's tile count for the
 // diagnostic partials (b < 0: taken from the CTA's position in its grid).  LATC: compile-time lattice set (7 = all three) or 0
 // (read at run time).  Every thread of the CTA calls it.
-template <typename R, int MODE, bool DIAG, int LATC>
-__device__ __forceinline__ void step_tile(const Args<R>& a, int bx, int by, int b, int nb) {
+template <typename R, int MODE, bool DIAG, int LATC, typename S = R>
+__device__ __forceinline__ void step_tile(const Args<R, S>& a, int bx, int by, int b, int nb) {
   const Geom& g = a.g;
   const Coef<R>& c = a.c;
   const int lat = LATC ? LATC : g.lattices;
@@ -221,14 +230,14 @@ __device__ __forceinline__ void step_tile(const Args<R>& a, int bx, int by, int 
     const int ry = wrap_or_clamp(y0 + hy - 1, g.ny, g.bc[2], g.bc[3]);
     const int m = ry * g.pitch + rx;
     const bool masked = g.has_mask && a.mask[m];
-    const R* pm = a.pin + m;
+    const S* pm = a.pin + m;
     // part 0: g0..g5; part 1: g6..g8 and h0..h2; part 2: h3..h8
     R sgp = R(0), shp = R(0);
     if (part == 0) {
       if (lat & LAT_PHASE) {
         R v[6];
 #pragma unroll
-        for (int i = 0; i < 6; i++) v[i] = pm[(9 + i) * P];
+        for (int i = 0; i < 6; i++) v[i] = ldp(pm + (9 + i) * P);
         sgp = v[0] + v[1] + v[2] + v[3] + v[4] + v[5];
       }
       const int hi = hy * HX + hx;
@@ -239,13 +248,13 @@ __device__ __forceinline__ void step_tile(const Args<R>& a, int bx, int by, int 
       s_rQ[k] = a.lin[LAG_Q * P + m];
       s_rmask[k] = masked ? 1 : 0;
     } else if (part == 1) {
-      if (lat & LAT_PHASE) sgp = pm[15 * P] + pm[16 * P] + pm[17 * P];
-      if ((lat & LAT_HEAT) && !masked) shp = pm[18 * P] + pm[19 * P] + pm[20 * P];
+      if (lat & LAT_PHASE) sgp = ldp(pm + 15 * P) + ldp(pm + 16 * P) + ldp(pm + 17 * P);
+      if ((lat & LAT_HEAT) && !masked) shp = ldp(pm + 18 * P) + ldp(pm + 19 * P) + ldp(pm + 20 * P);
     } else {
       if ((lat & LAT_HEAT) && !masked) {
         R v[6];
 #pragma unroll
-        for (int i = 0; i < 6; i++) v[i] = pm[(21 + i) * P];
+        for (int i = 0; i < 6; i++) v[i] = ldp(pm + (21 + i) * P);
         shp = v[0] + v[1] + v[2] + v[3] + v[4] + v[5];
       }
     }
@@ -254,7 +263,7 @@ __device__ __forceinline__ void step_tile(const Args<R>& a, int bx, int by, int 
   }
 
   // ---- phase A1: own node (sums only; f prefetched for phase B) ----------
-  const R* pn = a.pin + n;
+  const S* pn = a.pin + n;
   const R phi0 = a.phi0[n];
   const R flp = a.lin[LAG_FL * P + n];
   const R wp = a.lin[LAG_W * P + n];
@@ -264,7 +273,7 @@ __device__ __forceinline__ void step_tile(const Args<R>& a, int bx, int by, int 
   R f[9];
   if (lat & LAT_FLOW) {
 #pragma unroll
-    for (int i = 0; i < 9; i++) f[i] = pn[i * P];
+    for (int i = 0; i < 9; i++) f[i] = ldp(pn + i * P);
     if (STASHF) {
 #pragma unroll
       for (int i = 0; i < 9; i++) s_fpop[STASHF ? i : 0][tid] = f[i];
@@ -274,8 +283,13 @@ __device__ __forceinline__ void step_tile(const Args<R>& a, int bx, int by, int 
   if (lat & LAT_PHASE) {
     R v[9];
 #pragma unroll
-    for (int i = 0; i < 9; i++) v[i] = STASH ? pn[(9 + i) * P] : ld_sum(pn + (9 + i) * P);
+    for (int i = 0; i < 9; i++) v[i] = ld_pop<STASH>(pn + (9 + i) * P);
     sg = sum_g(v);
+    if (kShiftRest<S>) {
+      const R r0 = rest_ref_g(wp, phi0);
+      sg += r0;
+      v[0] += r0;
+    }
     if (STASH) {
 #pragma unroll
       for (int i = 0; i < 9; i++) s_pop[i][tid] = v[i];
@@ -287,9 +301,14 @@ __device__ __forceinline__ void step_tile(const Args<R>& a, int bx, int by, int 
       cold_mask_h(c, wp, phi0, v);
     } else {
 #pragma unroll
-      for (int i = 0; i < 9; i++) v[i] = STASH ? pn[(18 + i) * P] : ld_sum(pn + (18 + i) * P);
+      for (int i = 0; i < 9; i++) v[i] = ld_pop<STASH>(pn + (18 + i) * P);
     }
     sh = sum_h(v);
+    if (kShiftRest<S> && !masked) {
+      const R r0 = rest_ref_h(c, wp, flp);
+      sh += r0;
+      v[0] += r0;
+    }
     if (STASH) {
 #pragma unroll
       for (int i = 0; i < 9; i++) s_pop[STASH ? 9 + i : 0][tid] = v[i];
@@ -314,7 +333,8 @@ __device__ __forceinline__ void step_tile(const Args<R>& a, int bx, int by, int 
     const int hi = hy * HX + hx;
     const R q0 = s_phi0[hi];
     const R wq = s_rw[k];
-    const R sgq = s_rsg[k][0] + s_rsg[k][1];
+    R sgq = s_rsg[k][0] + s_rsg[k][1];
+    if (kShiftRest<S>) sgq += rest_ref_g(wq, q0);
     R shq;
     if ((lat & LAT_HEAT) && s_rmask[k]) {
       R hq[9];
@@ -322,6 +342,7 @@ __device__ __forceinline__ void step_tile(const Args<R>& a, int bx, int by, int 
       shq = sum_h(hq);
     } else {
       shq = s_rsh[k][1] + s_rsh[k][2];
+      if (kShiftRest<S>) shq += rest_ref_h(c, wq, s_rfl[k]);
     }
     const Local<R> Lq = local_state(c, lat, sgq, shq, s_rfl[k], wq, s_rQ[k], q0);
     s_phi[hi] = Lq.phi;
@@ -415,7 +436,7 @@ __device__ __forceinline__ void step_tile(const Args<R>& a, int bx, int by, int 
     if (MODE == MODE_STEP) {
       // links that stay inside the grid need no boundary logic
       const bool inner = gx > 0 && gx < g.nx - 1 && gy > 0 && gy < g.ny - 1;
-      R* out = a.pout;
+      S* out = a.pout;
       if (lat & LAT_FLOW) {
         if (inner) collide_flow<R, true>(g, c, out, P, gx, gy, n, f, rho, M);
         else collide_flow<R, false>(g, c, out, P, gx, gy, n, f, rho, M);
@@ -423,11 +444,13 @@ __device__ __forceinline__ void step_tile(const Args<R>& a, int bx, int by, int 
       if (lat & LAT_PHASE) {
         R gq[9];
 #pragma unroll
-        for (int i = 0; i < 9; i++) gq[i] = STASH ? s_pop[i][tid] : pn[(9 + i) * P];
+        for (int i = 0; i < 9; i++) gq[i] = STASH ? s_pop[i][tid] : ldp(pn + (9 + i) * P);
         const R phuxp = a.lin[LAG_PHUX * P + n];
         const R phuyp = a.lin[LAG_PHUY * P + n];
-        if (inner) collide_phase<R, true>(g, c, out + 9 * P, P, gx, gy, n, gq, phi, mdot, phuxp, phuyp, M);
-        else collide_phase<R, false>(g, c, out + 9 * P, P, gx, gy, n, gq, phi, mdot, phuxp, phuyp, M);
+        // the reference the next step's reader of this node will add back
+        const R r0 = kShiftRest<S> ? rest_ref_g(L.w, phi0) : R(0);
+        if (inner) collide_phase<R, true>(g, c, out + 9 * P, P, gx, gy, n, gq, phi, mdot, phuxp, phuyp, M, r0);
+        else collide_phase<R, false>(g, c, out + 9 * P, P, gx, gy, n, gq, phi, mdot, phuxp, phuyp, M, r0);
       }
       if (lat & LAT_HEAT) {
         R hq[9];
@@ -438,10 +461,11 @@ __device__ __forceinline__ void step_tile(const Args<R>& a, int bx, int by, int 
           cold_mask_h(c, wp, phi0, hq);
         } else {
 #pragma unroll
-          for (int i = 0; i < 9; i++) hq[i] = pn[(18 + i) * P];
+          for (int i = 0; i < 9; i++) hq[i] = ldp(pn + (18 + i) * P);
         }
-        if (inner) collide_heat<R, true>(g, c, out + 18 * P, P, gx, gy, n, hq, fs, L.w, T, L.rhoH, mdot, M);
-        else collide_heat<R, false>(g, c, out + 18 * P, P, gx, gy, n, hq, fs, L.w, T, L.rhoH, mdot, M);
+        const R r0 = kShiftRest<S> ? rest_ref_h(c, L.w, L.fl) : R(0);
+        if (inner) collide_heat<R, true>(g, c, out + 18 * P, P, gx, gy, n, hq, fs, L.w, T, L.rhoH, mdot, M, r0);
+        else collide_heat<R, false>(g, c, out + 18 * P, P, gx, gy, n, hq, fs, L.w, T, L.rhoH, mdot, M, r0);
       }
       a.lout[LAG_FL * P + n] = L.fl;
       a.lout[LAG_W * P + n] = L.w;
@@ -484,10 +508,10 @@ __device__ __forceinline__ void step_tile(const Args<R>& a, int bx, int by, int 
   }
 }
 
-template <typename R, int MODE, bool DIAG, int LATC>
+template <typename R, int MODE, bool DIAG, int LATC, typename S = R>
 __global__ void __launch_bounds__(NT, sizeof(R) == 4 ? LBM_MIN_BLOCKS_F32 : 1)
-    lbm_step_kernel(const Args<R> a) {
-  step_tile<R, MODE, DIAG, LATC>(a, blockIdx.x, blockIdx.y, -1, 0);
+    lbm_step_kernel(const Args<R, S> a) {
+  step_tile<R, MODE, DIAG, LATC, S>(a, blockIdx.x, blockIdx.y, -1, 0);
 }
 
 // Many independent grids (uneven sizes and parameters) advanced in one

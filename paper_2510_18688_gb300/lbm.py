@@ -16,7 +16,8 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_lib", "liblbm_gb300.so")
 
 LBM_OK, LBM_ERR_NONFINITE = 0, -5
-LBM_FP64, LBM_FP32 = 0, 1
+LBM_FP64, LBM_FP32, LBM_FP16S = 0, 1, 2
+PRECISION = {"fp64": LBM_FP64, "fp32": LBM_FP32, "fp16s": LBM_FP16S}
 LBM_HOST, LBM_DEVICE = 0, 1
 BC = {"periodic": 0, "dirichlet": 1, "adiabatic": 2}
 FIELDS = ("phi", "fs", "fl", "T", "rhoH", "p", "ux", "uy", "rho", "mu", "w", "mdot")
@@ -113,7 +114,7 @@ class LbmError(RuntimeError):
 def make_params(cfg: dict, precision: str = "fp32", diag_every: int = 0) -> LbmParams:
     p = LbmParams()
     p.nx, p.ny = int(cfg["nx"]), int(cfg["ny"])
-    p.precision = LBM_FP32 if precision == "fp32" else LBM_FP64
+    p.precision = PRECISION[precision]
     p.lattices = int(cfg["lattices"])
     for k in range(4):
         p.bc[k] = BC[cfg["bc"][k]]
