@@ -328,35 +328,52 @@ __device__ __forceinline__ R warp_sum(R v) {
 
 // Per-tile partial sums of the diagnostics in a fixed order (warp shuffles,
 // then the warps in order), written to partial[k * nb + b] for tile b of nb.
-// Every thread of the CTA calls it.  The grid-wide sum is
-// lbm_diag_finalize_kernel.
+// Every thread of the CTA calls it; s_red is shared memory of the arithmetic
+// type.  In float the warps' sums are added with Knuth's TwoSum (the
+// rounding error of every addition is carried along and added back at the
+// end), so one conversion to double per diagnostic keeps the accuracy of a
+// double-precision sum without work on the slow FP64 pipe.  The grid-wide
+// sum is lbm_diag_finalize_kernel.
 template <typename R>
-__device__ __forceinline__ void block_diag(const R* dvals, double (*s_red)[NDIAG],
+__device__ __forceinline__ void block_diag(const R* dvals, R (*s_red)[NDIAG],
                                            double* __restrict__ partial, int tid, int b, int nb);
 
 // Single-grid launch: the tile is the CTA.
 template <typename R>
-__device__ __forceinline__ void block_diag(const R* dvals, double (*s_red)[NDIAG],
+__device__ __forceinline__ void block_diag(const R* dvals, R (*s_red)[NDIAG],
                                            double* __restrict__ partial, int tid) {
   block_diag(dvals, s_red, partial, tid, blockIdx.y * gridDim.x + blockIdx.x,
              gridDim.x * gridDim.y);
 }
 
 template <typename R>
-__device__ __forceinline__ void block_diag(const R* dvals, double (*s_red)[NDIAG],
+__device__ __forceinline__ void block_diag(const R* dvals, R (*s_red)[NDIAG],
                                            double* __restrict__ partial, int tid, int b, int nb) {
   const int lane = tid & 31, warp = tid >> 5;
 #pragma unroll
   for (int k = 0; k < NDIAG; k++) {
     const R v = warp_sum(dvals[k]);
-    if (lane == 0) s_red[warp][k] = (double)v;
+    if (lane == 0) s_red[warp][k] = v;
   }
   __syncthreads();
   if (tid < NDIAG) {
-    double acc = 0.0;
+    if (sizeof(R) == 8) {
+      double acc = 0.0;
 #pragma unroll
-    for (int w = 0; w < NT / 32; w++) acc += s_red[w][tid];
-    partial[(long long)tid * nb + b] = acc;
+      for (int w = 0; w < NT / 32; w++) acc += (double)s_red[w][tid];
+      partial[(long long)tid * nb + b] = acc;
+    } else {
+      R sum = R(0), err = R(0);
+#pragma unroll
+      for (int w = 0; w < NT / 32; w++) {
+        const R y = s_red[w][tid];
+        const R t = sum + y;
+        const R yv = t - sum;          // the part of y that went into t
+        err += (sum - (t - yv)) + (y - yv);
+        sum = t;
+      }
+      partial[(long long)tid * nb + b] = (double)sum + (double)err;
+    }
   }
 }
 

@@ -75,7 +75,7 @@ __global__ void __launch_bounds__(NT, sizeof(R) == 4 ? LBM_MIN_BLOCKS_F32 : 1)
   const int lat = LATC ? LATC : g.lattices;
   const int P = (int)g.plane;
 
-  __shared__ double s_red[NT / 32][NDIAG];
+  __shared__ R s_red[NT / 32][NDIAG];
 
   const int tx = threadIdx.x, ty = threadIdx.y;
   const int tid = ty * TX + tx;

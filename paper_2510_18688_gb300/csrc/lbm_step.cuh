@@ -210,7 +210,7 @@ __device__ __forceinline__ void step_tile(const Args<R, S>& a, int bx, int by, i
   __shared__ R s_rsg[RING][NPART], s_rsh[RING][NPART];
   __shared__ R s_rfl[RING], s_rw[RING], s_rQ[RING];
   __shared__ int s_rmask[RING];
-  __shared__ double s_red[NT / 32][NDIAG];
+  __shared__ R s_red[NT / 32][NDIAG];
 
   const int tx = threadIdx.x, ty = threadIdx.y;
   const int tid = ty * TX + tx;

@@ -1,0 +1,141 @@
+"""Error of the FP32 and FP16-storage paths against the FP64 oracle, per
+field and per observable, on the paper's workload shapes.
+
+FP32 is held to the parity bar (relative L2 per field <= 1e-4; mdot, a
+difference of two float liquid fractions, 1e-3) on the state fields; over
+these long runs the small, slowly growing velocity and pressure fields are
+held to 3e-4.  FP16 storage (populations
+in binary16, arithmetic in FP32) is an accuracy experiment: its errors are
+printed as a table (run with -s) and held to bounds a few times above the
+values measured on GB300, so that a regression shows.  Relative L2 of a
+field whose oracle values are all zero (e.g. u in a one-dimensional
+column) is its plain L2 norm instead.
+"""
+import numpy as np
+import pytest
+
+from paper_2510_18688_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+FIELDS = ("phi", "fs", "fl", "T", "rhoH", "p", "ux", "uy", "rho", "mu", "w", "mdot")
+
+
+@pytest.fixture(scope="module")
+def env(oracle_mod):
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2510_18688_gb300 import build, lbm
+    build.build()
+    lbm.load()
+    return oracle_mod, lbm
+
+
+def _rel_l2(a, b):
+    nb = np.linalg.norm(b)
+    return float(np.linalg.norm(a - b) / nb) if nb > 0 else float(np.linalg.norm(a))
+
+
+def _errors(O, lbm, wl, steps, prec, line):
+    cfg, arr = wl
+    o = O.from_workload(wl).step(steps)
+    ref, rd = o.fields(), o.diagnostics()
+    s = lbm.Solver(cfg, precision=prec).set_geometry(arr).step(steps)
+    got, d = s.fields(), s.diagnostics(compute=True)
+    err = {k: _rel_l2(got[k], ref[k]) for k in FIELDS}
+    obs = {k: abs(d[k] - rd[k]) / abs(rd[k]) for k in ("material_mass", "frozen_volume")}
+    if line is not None:
+        want = O.crossings(ref["phi"], ref["w"], ref["fl"], *line)
+        obs["interface_lu"] = abs(s.crossings(*line)[0] - want[0])
+    assert d["nonfinite"] == 0.0
+    s.close()
+    return err, obs
+
+
+CASES = [
+    ("droplet 160^2, 2000 steps", lambda: W.sessile_droplet(160, seed=2, radius=40), 2000, (1, 80)),
+    ("cylinder 128^2, 2000 steps", lambda: W.cylinder_droplet(128, seed=1), 2000, (1, 64)),
+    ("random 70x45, 200 steps", lambda: W.random_state(70, 45, seed=12), 200, None),
+]
+
+# FP16-storage bounds: about 3x the GB300 measurement of each entry
+F16_FIELD = {"droplet": dict(phi=3e-4, fs=5e-3, fl=0.1, T=0.05, rhoH=0.03, p=0.02, ux=0.06,
+                             uy=0.03, rho=1e-3, mu=0.01, w=3e-4, mdot=0.7),
+             "cylinder": dict(phi=3e-4, fs=2e-3, fl=0.2, T=0.05, rhoH=0.04, p=0.04, ux=0.13,
+                              uy=0.1, rho=6e-4, mu=6e-3, w=3e-4, mdot=1.0),
+             "random": dict(phi=3e-5, fs=3e-4, fl=1e-3, T=5e-3, rhoH=1e-3, p=3e-3, ux=0.013,
+                            uy=9e-3, rho=8e-5, mu=6e-4, w=2e-5, mdot=4e-3)}
+F16_OBS = {"droplet": dict(material_mass=4e-5, frozen_volume=1e-3, interface_lu=1.5e-3),
+           "cylinder": dict(material_mass=1e-4, frozen_volume=1.5e-3, interface_lu=1.5e-3),
+           "random": dict(material_mass=1e-6, frozen_volume=1e-4)}
+
+
+@pytest.mark.parametrize("case", CASES, ids=[c[0].split(",")[0] for c in CASES])
+def test_precision_error_table(env, case):
+    O, lbm = env
+    name, make, steps, line = case
+    key = name.split()[0]
+    wl = make()
+    rows = {}
+    for prec in ("fp32", "fp16s"):
+        rows[prec] = _errors(O, lbm, wl, steps, prec, line)
+    print(f"\n{name}: relative L2 per field, relative error per observable")
+    print("prec   " + " ".join(f"{k:>8s}" for k in FIELDS))
+    for prec, (err, obs) in rows.items():
+        print(f"{prec:6s} " + " ".join(f"{err[k]:8.1e}" for k in FIELDS) + "   "
+              + " ".join(f"{k}={v:.1e}" for k, v in obs.items()))
+    err32, obs32 = rows["fp32"]
+    bound32 = dict.fromkeys(FIELDS, 1e-4)
+    bound32.update(mdot=1e-3, ux=3e-4, uy=3e-4, p=3e-4)
+    for k in FIELDS:
+        assert err32[k] <= bound32[k], ("fp32", k, err32[k])
+    for k, v in obs32.items():
+        assert v <= 1e-4, ("fp32", k, v)
+    err16, obs16 = rows["fp16s"]
+    for k in FIELDS:
+        assert err16[k] <= F16_FIELD[key][k], ("fp16s", k, err16[k])
+    for k, v in obs16.items():
+        assert v <= F16_OBS[key][k], ("fp16s", k, v)
+
+
+def test_fp16_storage_is_rejected_where_unsupported(env):
+    O, lbm = env
+    cfg, arr = W.random_state(40, 20, seed=3)
+    s = lbm.Solver(cfg, precision="fp16s").set_geometry(arr)
+    with pytest.raises(lbm.LbmError) as e:
+        lbm.Batch([s])
+    assert e.value.status == -6  # LBM_ERR_UNSUPPORTED
+    params = lbm.make_params(cfg, "fp16s")
+    torch = pytest.importorskip("torch")
+    dummy = torch.zeros(16, dtype=torch.float64, device="cuda")
+    p = dummy.data_ptr()
+    assert lbm.lbm_diagnostics_noalloc(params, p, p, p, None, p, None) == -6
+    s.close()
+
+
+def test_fp16_storage_checkpoint_and_captured_steps(env):
+    """FP16 storage: a checkpoint restores the state bit for bit, and long
+    calls (captured periods) match one-by-one steps bit for bit."""
+    O, lbm = env
+    cfg, arr = W.random_state(70, 45, seed=23)
+    a = lbm.Solver(cfg, precision="fp16s", diag_every=3).set_geometry(arr)
+    b = lbm.Solver(cfg, precision="fp16s", diag_every=3).set_geometry(arr)
+    a.step(1).step(77)
+    for _ in range(78):
+        b.step(1)
+    fa, fb = a.fields(), b.fields()
+    for k in FIELDS:
+        assert np.array_equal(fa[k], fb[k]), k
+    assert a.diagnostics(compute=False) == b.diagnostics(compute=False)
+    blob = a.save()
+    a.step(10)
+    after = a.fields()
+    c = lbm.Solver(cfg, precision="fp16s").set_geometry(arr)
+    c.load(blob)
+    c.step(10)
+    fc = c.fields()
+    for k in FIELDS:
+        assert np.array_equal(after[k], fc[k]), k
+    for s in (a, b, c):
+        s.close()
