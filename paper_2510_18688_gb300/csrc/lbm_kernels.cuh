@@ -346,14 +346,55 @@ __device__ __forceinline__ void block_diag(const R* dvals, R (*s_red)[NDIAG],
              gridDim.x * gridDim.y);
 }
 
+// Reduce-scatter of eight per-lane values over a warp: each exchange
+// halves the number of values a lane carries, so the eight warp sums take 9
+// shuffles instead of 40.  On return lane l holds the warp sum of value
+// (l >> 2) & 7.
+template <typename R>
+__device__ __forceinline__ R warp_sum8(const R* v, int lane) {
+  const bool b4 = lane & 16, b3 = lane & 8, b2 = lane & 4;
+  R a[4];
+#pragma unroll
+  for (int j = 0; j < 4; j++) {
+    const R keep = b4 ? v[4 + j] : v[j], send = b4 ? v[j] : v[4 + j];
+    a[j] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+  }
+  R h[2];
+#pragma unroll
+  for (int j = 0; j < 2; j++) {
+    const R keep = b3 ? a[2 + j] : a[j], send = b3 ? a[j] : a[2 + j];
+    h[j] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+  }
+  R q;
+  {
+    const R keep = b2 ? h[1] : h[0], send = b2 ? h[0] : h[1];
+    q = keep + __shfl_xor_sync(0xffffffffu, send, 4);
+  }
+  q += __shfl_xor_sync(0xffffffffu, q, 2);
+  q += __shfl_xor_sync(0xffffffffu, q, 1);
+  return q;
+}
+
+#ifndef LBM_DIAG_BUTTERFLY
+#define LBM_DIAG_BUTTERFLY 0
+#endif
+
 template <typename R>
 __device__ __forceinline__ void block_diag(const R* dvals, R (*s_red)[NDIAG],
                                            double* __restrict__ partial, int tid, int b, int nb) {
   const int lane = tid & 31, warp = tid >> 5;
+  static_assert(NDIAG == 9, "the reduce-scatter covers diagnostics 0-7, the ninth is separate");
+  if (LBM_DIAG_BUTTERFLY && sizeof(R) == 4) {
+    const R v = warp_sum8(dvals, lane);
+    if ((lane & 3) == 0) s_red[warp][(lane >> 2) & 7] = v;
+    const R v8 = warp_sum(dvals[8]);
+    if (lane == 0) s_red[warp][8] = v8;
+  } else {
 #pragma unroll
-  for (int k = 0; k < NDIAG; k++) {
-    const R v = warp_sum(dvals[k]);
-    if (lane == 0) s_red[warp][k] = v;
+    for (int k = 0; k < NDIAG; k++) {
+      const R v = warp_sum(dvals[k]);
+      if (lane == 0) s_red[warp][k] = v;
+    }
   }
   __syncthreads();
   if (tid < NDIAG) {
