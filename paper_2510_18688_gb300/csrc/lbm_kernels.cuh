@@ -334,18 +334,6 @@ __device__ __forceinline__ R warp_sum(R v) {
 // end), so one conversion to double per diagnostic keeps the accuracy of a
 // double-precision sum without work on the slow FP64 pipe.  The grid-wide
 // sum is lbm_diag_finalize_kernel.
-template <typename R>
-__device__ __forceinline__ void block_diag(const R* dvals, R (*s_red)[NDIAG],
-                                           double* __restrict__ partial, int tid, int b, int nb);
-
-// Single-grid launch: the tile is the CTA.
-template <typename R>
-__device__ __forceinline__ void block_diag(const R* dvals, R (*s_red)[NDIAG],
-                                           double* __restrict__ partial, int tid) {
-  block_diag(dvals, s_red, partial, tid, blockIdx.y * gridDim.x + blockIdx.x,
-             gridDim.x * gridDim.y);
-}
-
 // Reduce-scatter of eight per-lane values over a warp: each exchange
 // halves the number of values a lane carries, so the eight warp sums take 9
 // shuffles instead of 40.  On return lane l holds the warp sum of value
@@ -376,12 +364,13 @@ __device__ __forceinline__ R warp_sum8(const R* v, int lane) {
 }
 
 #ifndef LBM_DIAG_BUTTERFLY
-#define LBM_DIAG_BUTTERFLY 0
+#define LBM_DIAG_BUTTERFLY 1
 #endif
 
+// Stage 1 (every thread, no barrier): the warp's sums of the nine values
+// into s_red[warp][k].
 template <typename R>
-__device__ __forceinline__ void block_diag(const R* dvals, R (*s_red)[NDIAG],
-                                           double* __restrict__ partial, int tid, int b, int nb) {
+__device__ __forceinline__ void block_diag_warps(const R* dvals, R (*s_red)[NDIAG], int tid) {
   const int lane = tid & 31, warp = tid >> 5;
   static_assert(NDIAG == 9, "the reduce-scatter covers diagnostics 0-7, the ninth is separate");
   if (LBM_DIAG_BUTTERFLY && sizeof(R) == 4) {
@@ -396,6 +385,14 @@ __device__ __forceinline__ void block_diag(const R* dvals, R (*s_red)[NDIAG],
       if (lane == 0) s_red[warp][k] = v;
     }
   }
+}
+
+// Stage 2 (every thread; one barrier): the warps' sums in order into
+// partial[k * nb + b] for tile b of nb.
+template <typename R>
+__device__ __forceinline__ void block_diag_finish(const R (*s_red)[NDIAG],
+                                                  double* __restrict__ partial, int tid, int b,
+                                                  int nb) {
   __syncthreads();
   if (tid < NDIAG) {
     if (sizeof(R) == 8) {
@@ -416,6 +413,29 @@ __device__ __forceinline__ void block_diag(const R* dvals, R (*s_red)[NDIAG],
       partial[(long long)tid * nb + b] = (double)sum + (double)err;
     }
   }
+}
+
+// Per-tile partial sums of the diagnostics in a fixed order (warp sums, then
+// the warps in order), written to partial[k * nb + b] for tile b of nb.
+// Every thread of the CTA calls it; s_red is shared memory of the arithmetic
+// type.  In float the warps' sums are added with Knuth's TwoSum (the
+// rounding error of every addition is carried along and added back at the
+// end), so one conversion to double per diagnostic keeps the accuracy of a
+// double-precision sum without work on the slow FP64 pipe.  The grid-wide
+// sum is lbm_diag_finalize_kernel.
+template <typename R>
+__device__ __forceinline__ void block_diag(const R* dvals, R (*s_red)[NDIAG],
+                                           double* __restrict__ partial, int tid, int b, int nb) {
+  block_diag_warps(dvals, s_red, tid);
+  block_diag_finish(s_red, partial, tid, b, nb);
+}
+
+// Single-grid launch: the tile is the CTA.
+template <typename R>
+__device__ __forceinline__ void block_diag(const R* dvals, R (*s_red)[NDIAG],
+                                           double* __restrict__ partial, int tid) {
+  block_diag(dvals, s_red, partial, tid, blockIdx.y * gridDim.x + blockIdx.x,
+             gridDim.x * gridDim.y);
 }
 
 // Grid-wide FP64 diagnostics from the per-CTA partials, one CTA, fixed order

@@ -353,6 +353,7 @@ __device__ __forceinline__ void step_tile(const Args<R, S>& a, int bx, int by, i
 
   // ---- phase B: stencils, macros, collisions, streaming -------------------
   R dvals[NDIAG];
+  Macro<R> M;
   if (valid) {
     const int hc = (ty + 1) * HX + (tx + 1);
     // isotropic stencils (reading R-FD): grad = 3 sum w_i c_i chi(x + c_i),
@@ -383,8 +384,7 @@ __device__ __forceinline__ void step_tile(const Args<R, S>& a, int bx, int by, i
     gphx *= R(3); gphy *= R(3); lphi *= R(3); lphi0 *= R(3); lfs *= R(3);
     grx *= R(3); gry *= R(3); gpx *= R(3); gpy *= R(3);
 
-    const R phi = L.phi, fs = L.fs, rho = L.rho, T = L.T, mdot = L.mdot;
-    Macro<R> M;
+    const R phi = L.phi, fs = L.fs, rho = L.rho, mdot = L.mdot;
     M.muphi = R(0);
     R Fx, Fy;
     {
@@ -432,6 +432,33 @@ __device__ __forceinline__ void step_tile(const Args<R, S>& a, int bx, int by, i
     M.phux = phi * M.ux;
     M.phuy = phi * M.uy;
     M.cap = rho * interp(fs, L.w, c.cp_s, c.cp_l, c.cp_g);
+    // diagnostics of this state, reduced over the warp before the
+    // collisions so that none of their inputs stays live through them
+    if (DIAG) {
+      dvals[0] = rho;
+      dvals[1] = L.w * (c.rho_s * (R(1) - L.fl) + c.rho_l * L.fl);
+      dvals[2] = L.rhoH;
+      dvals[3] = L.w * L.fl;
+      dvals[4] = L.w;
+      dvals[5] = L.w * (R(1) - L.fl);
+      dvals[6] = phi;
+      dvals[7] = R(0.5) * rho * M.uu;
+      // a non-finite population anywhere makes one of the sums non-finite
+      R tot = sg + sh;
+      if (lat & LAT_FLOW) {
+#pragma unroll
+        for (int i = 0; i < 9; i++) tot += f[i];
+      }
+      dvals[8] = isfinite(tot) ? R(0) : R(1);
+    }
+  } else if (DIAG) {
+#pragma unroll
+    for (int k = 0; k < NDIAG; k++) dvals[k] = R(0);
+  }
+  if (DIAG) block_diag_warps(dvals, s_red, tid);
+
+  if (valid) {
+    const R phi = L.phi, fs = L.fs, rho = L.rho, T = L.T, mdot = L.mdot;
 
     if (MODE == MODE_STEP) {
       // links that stay inside the grid need no boundary logic
@@ -480,31 +507,11 @@ __device__ __forceinline__ void step_tile(const Args<R, S>& a, int bx, int by, i
       for (int k = 0; k < NFIELD; k++)
         if (a.out[k]) a.out[k][d] = (double)vals[k];
     }
-    if (DIAG) {
-      dvals[0] = rho;
-      dvals[1] = L.w * (c.rho_s * (R(1) - L.fl) + c.rho_l * L.fl);
-      dvals[2] = L.rhoH;
-      dvals[3] = L.w * L.fl;
-      dvals[4] = L.w;
-      dvals[5] = L.w * (R(1) - L.fl);
-      dvals[6] = phi;
-      dvals[7] = R(0.5) * rho * M.uu;
-      // a non-finite population anywhere makes one of the sums non-finite
-      R tot = sg + sh;
-      if (lat & LAT_FLOW) {
-#pragma unroll
-        for (int i = 0; i < 9; i++) tot += f[i];
-      }
-      dvals[8] = isfinite(tot) ? R(0) : R(1);
-    }
-  } else if (DIAG) {
-#pragma unroll
-    for (int k = 0; k < NDIAG; k++) dvals[k] = R(0);
   }
-
   if (DIAG) {
-    if (b < 0) block_diag(dvals, s_red, a.diag_partial, tid);
-    else block_diag(dvals, s_red, a.diag_partial, tid, b, nb);
+    if (b < 0) block_diag_finish(s_red, a.diag_partial, tid, blockIdx.y * gridDim.x + blockIdx.x,
+                                 gridDim.x * gridDim.y);
+    else block_diag_finish(s_red, a.diag_partial, tid, b, nb);
   }
 }
 
