@@ -206,6 +206,7 @@ __device__ __forceinline__ void step_tile(const Args<R, S>& a, int bx, int by, i
   constexpr bool STASHF = STASH && LBM_STASH_F;
   __shared__ R s_pop[STASH ? 18 : 1][NT];
   __shared__ R s_fpop[STASHF ? 9 : 1][NT];
+  __shared__ R s_phu[STASH ? 2 : 1][NT];  // lagged phi u of the own node
   __shared__ R s_phi[HN], s_fs[HN], s_rho[HN], s_p[HN], s_phi0[HN];
   __shared__ R s_rsg[RING][NPART], s_rsh[RING][NPART];
   __shared__ R s_rfl[RING], s_rw[RING], s_rQ[RING];
@@ -269,6 +270,17 @@ __device__ __forceinline__ void step_tile(const Args<R, S>& a, int bx, int by, i
   const R wp = a.lin[LAG_W * P + n];
   const R pp = a.lin[LAG_P * P + n];
   const R Qp = a.lin[LAG_Q * P + n];
+  // the lagged phi u is needed only by the phase collision in phase B; it is
+  // loaded here with everything else so that no load waits in phase B
+  R phuxp = R(0), phuyp = R(0);
+  if (MODE == MODE_STEP && (lat & LAT_PHASE)) {
+    phuxp = a.lin[LAG_PHUX * P + n];
+    phuyp = a.lin[LAG_PHUY * P + n];
+    if (STASH) {
+      s_phu[0][tid] = phuxp;
+      s_phu[STASH ? 1 : 0][tid] = phuyp;
+    }
+  }
   const bool masked = (lat & LAT_HEAT) && g.has_mask && a.mask[n];
   R f[9];
   if (lat & LAT_FLOW) {
@@ -472,8 +484,10 @@ __device__ __forceinline__ void step_tile(const Args<R, S>& a, int bx, int by, i
         R gq[9];
 #pragma unroll
         for (int i = 0; i < 9; i++) gq[i] = STASH ? s_pop[i][tid] : ldp(pn + (9 + i) * P);
-        const R phuxp = a.lin[LAG_PHUX * P + n];
-        const R phuyp = a.lin[LAG_PHUY * P + n];
+        if (STASH) {
+          phuxp = s_phu[0][tid];
+          phuyp = s_phu[STASH ? 1 : 0][tid];
+        }
         // the reference the next step's reader of this node will add back
         const R r0 = kShiftRest<S> ? rest_ref_g(L.w, phi0) : R(0);
         if (inner) collide_phase<R, true>(g, c, out + 9 * P, P, gx, gy, n, gq, phi, mdot, phuxp, phuyp, M, r0);
