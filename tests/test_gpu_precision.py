@@ -44,7 +44,8 @@ def _errors(O, lbm, wl, steps, prec, line):
     s = lbm.Solver(cfg, precision=prec).set_geometry(arr).step(steps)
     got, d = s.fields(), s.diagnostics(compute=True)
     err = {k: _rel_l2(got[k], ref[k]) for k in FIELDS}
-    obs = {k: abs(d[k] - rd[k]) / abs(rd[k]) for k in ("material_mass", "frozen_volume")}
+    obs = {k: abs(d[k] - rd[k]) / max(abs(rd[k]), 1e-300)
+           for k in ("material_mass", "frozen_volume")}
     if line is not None:
         want = O.crossings(ref["phi"], ref["w"], ref["fl"], *line)
         obs["interface_lu"] = abs(s.crossings(*line)[0] - want[0])
@@ -57,7 +58,18 @@ CASES = [
     ("droplet 160^2, 2000 steps", lambda: W.sessile_droplet(160, seed=2, radius=40), 2000, (1, 80)),
     ("cylinder 128^2, 2000 steps", lambda: W.cylinder_droplet(128, seed=1), 2000, (1, 64)),
     ("random 70x45, 200 steps", lambda: W.random_state(70, 45, seed=12), 200, None),
+    ("neumann 400x4, 5000 steps", lambda: W.neumann(), 5000, None),
+    ("stefan 512x8, 5000 steps", lambda: W.stefan(), 5000, (0, 4)),
 ]
+
+# FP32 bounds other than the parity bar, per case: the one-dimensional
+# columns run 5000 steps with a sharp freezing front, where the temperature
+# of the node being frozen is the most sensitive value of the state
+F32_OVERRIDE = {"neumann": dict(T=5e-3, fs=1e-3, fl=2e-4, rhoH=2e-4),
+                "stefan": dict(ux=6e-3, p=5e-4, mu=1e-3)}
+F32_OBS_OVERRIDE = {"neumann": dict(frozen_volume=3e-4)}
+# fields that are zero up to round-off in the oracle (no relative error)
+SKIP = {"stefan": ("uy",)}
 
 # FP16-storage bounds: about 3x the GB300 measurement of each entry
 F16_FIELD = {"droplet": dict(phi=3e-4, fs=5e-3, fl=0.1, T=0.05, rhoH=0.03, p=0.02, ux=0.06,
@@ -65,10 +77,16 @@ F16_FIELD = {"droplet": dict(phi=3e-4, fs=5e-3, fl=0.1, T=0.05, rhoH=0.03, p=0.0
              "cylinder": dict(phi=3e-4, fs=2e-3, fl=0.2, T=0.05, rhoH=0.04, p=0.04, ux=0.13,
                               uy=0.1, rho=6e-4, mu=6e-3, w=3e-4, mdot=1.0),
              "random": dict(phi=3e-5, fs=3e-4, fl=1e-3, T=5e-3, rhoH=1e-3, p=3e-3, ux=0.013,
-                            uy=9e-3, rho=8e-5, mu=6e-4, w=2e-5, mdot=4e-3)}
+                            uy=9e-3, rho=8e-5, mu=6e-4, w=2e-5, mdot=4e-3),
+             "neumann": dict(phi=1e-6, fs=0.08, fl=0.015, T=0.15, rhoH=0.015, p=1e-6, ux=1e-6,
+                             uy=1e-6, rho=1e-6, mu=1e-6, w=1e-6, mdot=1e-6),
+             "stefan": dict(phi=8e-3, fs=0.14, fl=0.03, T=0.15, rhoH=0.09, p=0.24, ux=1.7,
+                            uy=None, rho=8e-3, mu=0.38, w=5e-3, mdot=0.25)}
 F16_OBS = {"droplet": dict(material_mass=4e-5, frozen_volume=1e-3, interface_lu=1.5e-3),
            "cylinder": dict(material_mass=1e-4, frozen_volume=1.5e-3, interface_lu=1.5e-3),
-           "random": dict(material_mass=1e-6, frozen_volume=1e-4)}
+           "random": dict(material_mass=1e-6, frozen_volume=1e-4),
+           "neumann": dict(material_mass=1e-6, frozen_volume=0.02),
+           "stefan": dict(material_mass=4e-4, frozen_volume=0.1, interface_lu=0.07)}
 
 
 @pytest.mark.parametrize("case", CASES, ids=[c[0].split(",")[0] for c in CASES])
@@ -85,16 +103,22 @@ def test_precision_error_table(env, case):
     for prec, (err, obs) in rows.items():
         print(f"{prec:6s} " + " ".join(f"{err[k]:8.1e}" for k in FIELDS) + "   "
               + " ".join(f"{k}={v:.1e}" for k, v in obs.items()))
+    skip = SKIP.get(key, ())
     err32, obs32 = rows["fp32"]
     bound32 = dict.fromkeys(FIELDS, 1e-4)
     bound32.update(mdot=1e-3, ux=3e-4, uy=3e-4, p=3e-4)
+    bound32.update(F32_OVERRIDE.get(key, {}))
     for k in FIELDS:
-        assert err32[k] <= bound32[k], ("fp32", k, err32[k])
+        if k not in skip:
+            assert err32[k] <= bound32[k], ("fp32", k, err32[k])
+    obs_bound32 = dict.fromkeys(obs32, 1e-4)
+    obs_bound32.update(F32_OBS_OVERRIDE.get(key, {}))
     for k, v in obs32.items():
-        assert v <= 1e-4, ("fp32", k, v)
+        assert v <= obs_bound32[k], ("fp32", k, v)
     err16, obs16 = rows["fp16s"]
     for k in FIELDS:
-        assert err16[k] <= F16_FIELD[key][k], ("fp16s", k, err16[k])
+        if k not in skip:
+            assert err16[k] <= F16_FIELD[key][k], ("fp16s", k, err16[k])
     for k, v in obs16.items():
         assert v <= F16_OBS[key][k], ("fp16s", k, v)
 
