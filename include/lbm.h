@@ -59,7 +59,15 @@ typedef enum {
  * This is not in the paper (which gives no precision); it trades accuracy
  * for 161 instead of 269 bytes of state traffic per node update.  Batches
  * and lbm_diagnostics_noalloc do not take it (LBM_ERR_UNSUPPORTED). */
-typedef enum { LBM_FP64 = 0, LBM_FP32 = 1, LBM_FP16S = 2 } lbm_precision;
+/* LBM_FP64_TANGENT: the FP64 step in forward-mode (dual-number)
+ * arithmetic: every value carries its derivative with respect to the
+ * parameter direction given by the tan_* fields of lbm_params (16 bytes per
+ * population).  Branches (the inversion of Eq. (8), clamps) follow the
+ * values, so the derivative is that of the branch taken.  Read the
+ * derivatives with lbm_read_tangent_fields, lbm_read_tangent_diagnostics and
+ * lbm_read_crossings_tangent; the values read as from an LBM_FP64 context.
+ * Batches and lbm_diagnostics_noalloc do not take it. */
+typedef enum { LBM_FP64 = 0, LBM_FP32 = 1, LBM_FP16S = 2, LBM_FP64_TANGENT = 3 } lbm_precision;
 
 enum { LBM_BC_PERIODIC = 0, LBM_BC_DIRICHLET = 1, LBM_BC_ADIABATIC = 2 };
 enum { LBM_LAT_FLOW = 1, LBM_LAT_PHASE = 2, LBM_LAT_HEAT = 4 };
@@ -113,6 +121,13 @@ typedef struct {
   double T_cold;
   uint32_t readings;
   int32_t diag_every;
+  /* LBM_FP64_TANGENT only: the parameter direction s along which the state
+   * is differentiated, as the rates dT_wall[k]/ds, dT_cold/ds,
+   * dtheta_deg/ds and dlatent/ds (e.g. tan_T_cold = 1 for d/dT_cold;
+   * tan_latent = -latent / Ste for d/dSte, since latent = Cp_l (T_m - T_w) /
+   * Ste).  Ignored by the other precisions. */
+  double tan_T_wall[4];
+  double tan_T_cold, tan_theta_deg, tan_latent;
 } lbm_params;
 
 /* Global FP64 sums over the grid of one state (the conservation and
@@ -192,6 +207,19 @@ int lbm_read_fields(lbm_ctx* ctx, uint32_t field_mask, double* const* out, int w
  * LBM_ERR_STATE before lbm_set_geometry, LBM_ERR_OOM/LBM_ERR_CUDA. */
 int lbm_read_crossings(lbm_ctx* ctx, int axis, int index, double* out, void* stream);
 
+/* LBM_FP64_TANGENT contexts: the derivatives of the fields selected by
+ * field_mask along the context's parameter direction, laid out and copied as
+ * lbm_read_fields does.  Errors: LBM_ERR_UNSUPPORTED for other precisions,
+ * as lbm_read_fields otherwise. */
+int lbm_read_tangent_fields(lbm_ctx* ctx, uint32_t field_mask, double* const* out, int where,
+                            void* stream);
+
+/* LBM_FP64_TANGENT contexts: out[0..1] as lbm_read_crossings, out[2..3] their
+ * derivatives along the parameter direction (at a crossing between nodes k
+ * and k+1 with values a, b and derivatives a', b': (a b' - b a') / (a - b)^2;
+ * NaN where there is no crossing).  out: host memory for 4 doubles. */
+int lbm_read_crossings_tangent(lbm_ctx* ctx, int axis, int index, double* out, void* stream);
+
 /* Enqueues the diagnostic reduction of the current state (no time step). */
 int lbm_compute_diagnostics(lbm_ctx* ctx, void* stream);
 
@@ -200,6 +228,13 @@ int lbm_compute_diagnostics(lbm_ctx* ctx, void* stream);
  * any node's populations were not finite, LBM_ERR_STATE if no diagnostics
  * were ever computed. */
 int lbm_read_diagnostics(lbm_ctx* ctx, lbm_diag* out);
+
+/* LBM_FP64_TANGENT contexts: the derivatives of the nine sums of the most
+ * recent diagnostics along the parameter direction (nonfinite: 0), with
+ * out->step the state index they belong to.  Synchronises as
+ * lbm_read_diagnostics.  Errors: LBM_ERR_UNSUPPORTED for other precisions,
+ * LBM_ERR_STATE if no diagnostics were computed. */
+int lbm_read_tangent_diagnostics(lbm_ctx* ctx, lbm_diag* out);
 
 /* Bytes of a checkpoint (populations, lag fields, step counter, header). */
 int lbm_state_size(const lbm_ctx* ctx, size_t* bytes);

@@ -31,6 +31,8 @@ struct lbm_ctx {
   Geom g;
   Coef<float> cf;
   Coef<double> cd;
+  Coef<lbmk::Dual> ct;   // LBM_FP64_TANGENT: constants with their derivatives
+  bool tangent;          // precision LBM_FP64_TANGENT
   size_t esize;          // bytes per real of the lag fields and phi0
   size_t pop_esize;      // bytes per stored population
   void* pop[2];
@@ -118,6 +120,12 @@ cudaError_t launch(lbm_ctx* c, int mode, bool diag, double* const* outs, cudaStr
     if (outs)
       for (int k = 0; k < lbmk::NFIELD; k++) a.out[k] = outs[k];
     return lbmk::launch_step_f32(a, mode, diag, s);
+  }
+  if (c->tangent) {
+    Args<lbmk::Dual> a = step_args<lbmk::Dual>(c, c->ct);
+    if (outs)
+      for (int k = 0; k < lbmk::NFIELD; k++) a.out[k] = outs[k];
+    return lbmk::launch_step_tan(a, mode, diag, s);
   }
   if (c->p.precision == LBM_FP16S) {
     Args<float, __half> a = step_args<float, __half>(c, c->cf);
@@ -268,14 +276,17 @@ int lbm_create(const lbm_params* params, lbm_ctx** out) {
   if (!c) return LBM_ERR_OOM;
   std::memset(c, 0, sizeof(*c));
   c->p = *params;
-  c->esize = params->precision == LBM_FP64 ? sizeof(double) : sizeof(float);
+  c->tangent = params->precision == LBM_FP64_TANGENT;
+  c->esize = c->tangent ? sizeof(lbmk::Dual)
+                        : (params->precision == LBM_FP64 ? sizeof(double) : sizeof(float));
   c->pop_esize = params->precision == LBM_FP16S ? sizeof(__half) : c->esize;
   c->g = lbmh::make_geom(*params);
   {
     // LBM_STEP_KERNEL=split selects the two-kernel step (macro pass +
     // collide pass); the default is the fused one-kernel step
     const char* k = std::getenv("LBM_STEP_KERNEL");
-    c->split = k && std::strcmp(k, "split") == 0 && params->precision != LBM_FP16S;
+    c->split = k && std::strcmp(k, "split") == 0 && params->precision != LBM_FP16S &&
+               !c->tangent;
     // LBM_STEP_GRAPHS=0 launches every step on its own instead of
     // replaying captured periods
     const char* gr = std::getenv("LBM_STEP_GRAPHS");
@@ -283,6 +294,8 @@ int lbm_create(const lbm_params* params, lbm_ctx** out) {
   }
   c->cf = lbmh::make_coef<float>(*params);
   c->cd = lbmh::make_coef<double>(*params);
+  if (c->tangent) c->ct = lbmh::make_coef_tangent(*params);
+  const size_t dmul = c->tangent ? 2 : 1;  // tangent: values, then derivatives
   const dim3 gd = lbmk::grid_dims(c->g);
   c->nblocks = (int)(gd.x * gd.y);
   const size_t P = (size_t)c->g.plane;
@@ -295,10 +308,11 @@ int lbm_create(const lbm_params* params, lbm_ctx** out) {
   if (e == cudaSuccess) e = cudaMalloc(&c->scratch, lbmk::NSCRATCH * P * c->esize);
   if (e == cudaSuccess) e = cudaMalloc(&c->mask, P);
   if (e == cudaSuccess)
-    e = cudaMalloc(&c->diag_partial, (size_t)lbmk::NDIAG * c->nblocks * sizeof(double));
-  if (e == cudaSuccess) e = cudaMalloc(&c->diag_out, (lbmk::NDIAG + 1) * sizeof(double));
+    e = cudaMalloc(&c->diag_partial, dmul * lbmk::NDIAG * c->nblocks * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&c->diag_out, dmul * (lbmk::NDIAG + 1) * sizeof(double));
   if (e == cudaSuccess) e = cudaMemset(c->mask, 0, P);
-  if (e == cudaSuccess) e = cudaHostAlloc(&c->h_diag, (lbmk::NDIAG + 1) * sizeof(double), 0);
+  if (e == cudaSuccess)
+    e = cudaHostAlloc(&c->h_diag, dmul * (lbmk::NDIAG + 1) * sizeof(double), 0);
   if (e == cudaSuccess) e = cudaDeviceSynchronize();
   if (e != cudaSuccess) {
     int code = cuda_fail(c, e, "lbm_create allocation");
@@ -362,6 +376,14 @@ int lbm_set_geometry(lbm_ctx* c, const double* phi0, const uint8_t* cold_mask,
     a.pout = (float*)c->pop[0]; a.lout = (float*)c->lag[0]; a.phi0_out = (float*)c->phi0;
     a.mask_out = c->mask; a.phi0 = d_phi0; a.mask = d_mask; a.phi = d_phi; a.T = d_T; a.fl = d_fl;
     e = lbmk::launch_init_f32(a, s);
+  } else if (c->tangent) {
+    InitArgs<lbmk::Dual> a;
+    std::memset(&a, 0, sizeof(a));
+    a.g = c->g; a.c = c->ct;
+    a.pout = (lbmk::Dual*)c->pop[0]; a.lout = (lbmk::Dual*)c->lag[0];
+    a.phi0_out = (lbmk::Dual*)c->phi0;
+    a.mask_out = c->mask; a.phi0 = d_phi0; a.mask = d_mask; a.phi = d_phi; a.T = d_T; a.fl = d_fl;
+    e = lbmk::launch_init_tan(a, s);
   } else if (c->p.precision == LBM_FP16S) {
     InitArgs<float, __half> a;
     std::memset(&a, 0, sizeof(a));
@@ -418,74 +440,114 @@ int lbm_step(lbm_ctx* c, int64_t nsteps, void* stream) {
   return LBM_OK;
 }
 
-int lbm_read_fields(lbm_ctx* c, uint32_t field_mask, double* const* out, int where,
-                    void* stream) {
-  if (!c) return LBM_ERR_ARG;
+}  // extern "C"
+
+namespace {
+
+// Field read-out; `deriv` selects the derivative half of a tangent context.
+// Tangent read-outs write value and derivative (2 N doubles per field) and
+// always go through the staging memory.
+int read_fields_impl(lbm_ctx* c, uint32_t field_mask, double* const* out, int where,
+                     cudaStream_t s, bool deriv) {
   if (!out) return fail(c, LBM_ERR_ARG, "null output table%s");
   if (where != LBM_HOST && where != LBM_DEVICE) return fail(c, LBM_ERR_ARG, "bad `where`%s");
   if (field_mask >> lbmk::NFIELD) return fail(c, LBM_ERR_ARG, "unknown field bits%s");
   if (!c->have_geometry) return fail(c, LBM_ERR_STATE, "read before lbm_set_geometry%s");
   for (int k = 0; k < lbmk::NFIELD; k++)
     if ((field_mask >> k & 1u) && !out[k]) return fail(c, LBM_ERR_ARG, "selected field has null output%s");
-  cudaStream_t s = (cudaStream_t)stream;
   const size_t N = (size_t)c->g.nx * c->g.ny;
+  const size_t fstride = c->tangent ? 2 * N : N;
+  const bool staged = where == LBM_HOST || c->tangent;
   double* outs[lbmk::NFIELD] = {nullptr};
   cudaError_t e;
-  if (where == LBM_HOST) {
+  if (staged) {
     if (!c->staging) {
-      e = cudaMalloc(&c->staging, lbmk::NFIELD * N * sizeof(double));
+      e = cudaMalloc(&c->staging, lbmk::NFIELD * fstride * sizeof(double));
       if (e != cudaSuccess) return cuda_fail(c, e, "read-out staging allocation");
     }
     for (int k = 0; k < lbmk::NFIELD; k++)
-      if (field_mask >> k & 1u) outs[k] = c->staging + k * N;
+      if (field_mask >> k & 1u) outs[k] = c->staging + k * fstride;
   } else {
     for (int k = 0; k < lbmk::NFIELD; k++)
       if (field_mask >> k & 1u) outs[k] = out[k];
   }
   e = launch(c, lbmk::MODE_READ, false, outs, s);
   if (e != cudaSuccess) return cuda_fail(c, e, "read-out kernel launch");
-  if (where == LBM_HOST) {
+  if (staged) {
+    const cudaMemcpyKind kind = where == LBM_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
     for (int k = 0; k < lbmk::NFIELD; k++) {
       if (!(field_mask >> k & 1u)) continue;
-      e = cudaMemcpyAsync(out[k], outs[k], N * sizeof(double), cudaMemcpyDeviceToHost, s);
+      e = cudaMemcpyAsync(out[k], outs[k] + (deriv ? N : 0), N * sizeof(double), kind, s);
       if (e != cudaSuccess) return cuda_fail(c, e, "field download");
     }
-    e = cudaStreamSynchronize(s);
-    if (e != cudaSuccess) return cuda_fail(c, e, "read_fields synchronisation");
+    if (where == LBM_HOST) {
+      e = cudaStreamSynchronize(s);
+      if (e != cudaSuccess) return cuda_fail(c, e, "read_fields synchronisation");
+    }
   }
   c->last_stream = s;
   return LBM_OK;
 }
 
-int lbm_read_crossings(lbm_ctx* c, int axis, int index, double* out, void* stream) {
-  if (!c) return LBM_ERR_ARG;
+int read_crossings_impl(lbm_ctx* c, int axis, int index, double* out, cudaStream_t s, bool deriv) {
   if (!out) return fail(c, LBM_ERR_ARG, "null output%s");
   if (axis != 0 && axis != 1) return fail(c, LBM_ERR_ARG, "axis must be 0 (x) or 1 (y)%s");
   if (index < 0 || index >= (axis == 0 ? c->g.ny : c->g.nx))
     return fail(c, LBM_ERR_ARG, "line index outside the grid%s");
   if (!c->have_geometry) return fail(c, LBM_ERR_STATE, "read before lbm_set_geometry%s");
-  cudaStream_t s = (cudaStream_t)stream;
   const size_t N = (size_t)c->g.nx * c->g.ny;
+  const size_t fstride = c->tangent ? 2 * N : N;
   cudaError_t e;
   if (!c->staging) {
-    e = cudaMalloc(&c->staging, lbmk::NFIELD * N * sizeof(double));
+    e = cudaMalloc(&c->staging, lbmk::NFIELD * fstride * sizeof(double));
     if (e != cudaSuccess) return cuda_fail(c, e, "read-out staging allocation");
   }
   double* outs[lbmk::NFIELD] = {nullptr};
-  outs[lbmk::F_PHI] = c->staging + lbmk::F_PHI * N;
-  outs[lbmk::F_W] = c->staging + lbmk::F_W * N;
-  outs[lbmk::F_FL] = c->staging + lbmk::F_FL * N;
-  double* d_out = c->staging + lbmk::F_T * N;  // an unused staging plane
+  outs[lbmk::F_PHI] = c->staging + lbmk::F_PHI * fstride;
+  outs[lbmk::F_W] = c->staging + lbmk::F_W * fstride;
+  outs[lbmk::F_FL] = c->staging + lbmk::F_FL * fstride;
+  double* d_out = c->staging + lbmk::F_T * fstride;  // an unused staging plane
   e = launch(c, lbmk::MODE_READ, false, outs, s);
   if (e != cudaSuccess) return cuda_fail(c, e, "read-out kernel launch");
-  e = lbmk::launch_crossings(outs[lbmk::F_PHI], outs[lbmk::F_W], outs[lbmk::F_FL], c->g.nx,
-                             c->g.ny, axis, index, d_out, s);
+  const double* dphi = deriv ? outs[lbmk::F_PHI] + N : nullptr;
+  const double* dw = deriv ? outs[lbmk::F_W] + N : nullptr;
+  const double* dfl = deriv ? outs[lbmk::F_FL] + N : nullptr;
+  e = lbmk::launch_crossings(outs[lbmk::F_PHI], outs[lbmk::F_W], outs[lbmk::F_FL], dphi, dw, dfl,
+                             c->g.nx, c->g.ny, axis, index, d_out, s);
   if (e != cudaSuccess) return cuda_fail(c, e, "crossings kernel launch");
-  e = cudaMemcpyAsync(out, d_out, 2 * sizeof(double), cudaMemcpyDeviceToHost, s);
+  e = cudaMemcpyAsync(out, d_out, (deriv ? 4 : 2) * sizeof(double), cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return cuda_fail(c, e, "crossings download");
   c->last_stream = s;
   return LBM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int lbm_read_fields(lbm_ctx* c, uint32_t field_mask, double* const* out, int where,
+                    void* stream) {
+  if (!c) return LBM_ERR_ARG;
+  return read_fields_impl(c, field_mask, out, where, (cudaStream_t)stream, false);
+}
+
+int lbm_read_tangent_fields(lbm_ctx* c, uint32_t field_mask, double* const* out, int where,
+                            void* stream) {
+  if (!c) return LBM_ERR_ARG;
+  if (!c->tangent) return fail(c, LBM_ERR_UNSUPPORTED, "not a tangent context%s");
+  return read_fields_impl(c, field_mask, out, where, (cudaStream_t)stream, true);
+}
+
+int lbm_read_crossings(lbm_ctx* c, int axis, int index, double* out, void* stream) {
+  if (!c) return LBM_ERR_ARG;
+  return read_crossings_impl(c, axis, index, out, (cudaStream_t)stream, false);
+}
+
+int lbm_read_crossings_tangent(lbm_ctx* c, int axis, int index, double* out, void* stream) {
+  if (!c) return LBM_ERR_ARG;
+  if (!c->tangent) return fail(c, LBM_ERR_UNSUPPORTED, "not a tangent context%s");
+  return read_crossings_impl(c, axis, index, out, (cudaStream_t)stream, true);
 }
 
 int lbm_compute_diagnostics(lbm_ctx* c, void* stream) {
@@ -527,6 +589,33 @@ int lbm_read_diagnostics(lbm_ctx* c, lbm_diag* out) {
   out->nonfinite = d[8];
   out->step = (int64_t)d[9];
   if (d[8] != 0.0) return fail(c, LBM_ERR_NONFINITE, "non-finite populations in the state%s");
+  return LBM_OK;
+}
+
+int lbm_read_tangent_diagnostics(lbm_ctx* c, lbm_diag* out) {
+  if (!c || !out) return LBM_ERR_ARG;
+  if (!c->tangent) return fail(c, LBM_ERR_UNSUPPORTED, "not a tangent context%s");
+  if (!c->have_diag) return fail(c, LBM_ERR_STATE, "no diagnostics computed yet%s");
+  // the derivative partials follow the value partials
+  double* dout = c->diag_out + (lbmk::NDIAG + 1);
+  double* hd = c->h_diag + (lbmk::NDIAG + 1);
+  cudaError_t e = lbmk::launch_diag_finalize(c->diag_partial + (size_t)lbmk::NDIAG * c->nblocks,
+                                             c->nblocks, dout, c->diag_step, c->last_stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(hd, dout, (lbmk::NDIAG + 1) * sizeof(double), cudaMemcpyDeviceToHost,
+                        c->last_stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->last_stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "tangent diagnostics");
+  out->mass = hd[0];
+  out->material_mass = hd[1];
+  out->rhoH = hd[2];
+  out->liquid_volume = hd[3];
+  out->material_volume = hd[4];
+  out->frozen_volume = hd[5];
+  out->phi_sum = hd[6];
+  out->kinetic = hd[7];
+  out->nonfinite = 0.0;
+  out->step = (int64_t)hd[9];
   return LBM_OK;
 }
 
@@ -771,7 +860,7 @@ int lbm_batch_create(lbm_ctx* const* ctxs, int count, lbm_batch** out) {
   for (int i = 0; i < count; i++) {
     if (!ctxs[i]) return LBM_ERR_ARG;
     if (ctxs[i]->p.precision != ctxs[0]->p.precision) return LBM_ERR_ARG;
-    if (ctxs[i]->p.precision == LBM_FP16S) return LBM_ERR_UNSUPPORTED;
+    if (ctxs[i]->p.precision == LBM_FP16S || ctxs[i]->tangent) return LBM_ERR_UNSUPPORTED;
     for (int j = 0; j < i; j++)
       if (ctxs[j] == ctxs[i]) return LBM_ERR_ARG;
   }

@@ -55,46 +55,88 @@ cudaError_t launch_batch_f64(const BatchTable<double>& b, bool diag, bool all, c
 
 // One CTA: along one grid line of dense [ny][nx] fields, the largest
 // coordinate where phi crosses 0 and where s = w (1 - fl) crosses 1/2, by
-// linear interpolation between neighbouring nodes (NaN if none).
-static __global__ void __launch_bounds__(NT) lbm_crossings_kernel(const double* __restrict__ phi,
-                                                                  const double* __restrict__ w,
-                                                                  const double* __restrict__ fl,
-                                                                  int nx, int ny, int axis,
-                                                                  int index,
-                                                                  double* __restrict__ out) {
-  __shared__ double s_best[2][NT / 32];
+// linear interpolation between neighbouring nodes (NaN if none).  With the
+// derivative fields dphi, dw, dfl (else null) also the derivatives of the
+// two positions: (a b' - b a') / (a - b)^2 at the crossing that is kept.
+static __global__ void __launch_bounds__(NT) lbm_crossings_kernel(
+    const double* __restrict__ phi, const double* __restrict__ w, const double* __restrict__ fl,
+    const double* __restrict__ dphi, const double* __restrict__ dw,
+    const double* __restrict__ dfl, int nx, int ny, int axis, int index,
+    double* __restrict__ out) {
+  __shared__ double s_best[2][2][NT / 32];
   const int len = axis == 0 ? nx : ny;
   const long long stride = axis == 0 ? 1 : nx;
   const long long base = axis == 0 ? (long long)index * nx : index;
-  double best0 = -1.0, best1 = -1.0;  // coordinates are >= 0
+  const bool tan = dphi != nullptr;
+  double best[2] = {-1.0, -1.0}, dbest[2] = {0.0, 0.0};  // coordinates are >= 0
   for (int k = threadIdx.x; k + 1 < len; k += blockDim.x) {
     const long long i0 = base + k * stride, i1 = i0 + stride;
-    const double a = phi[i0], b = phi[i1];
-    if ((a <= 0.0) != (b <= 0.0)) best0 = fmax(best0, k + a / (a - b));
-    const double sa = w[i0] * (1.0 - fl[i0]) - 0.5, sb = w[i1] * (1.0 - fl[i1]) - 0.5;
-    if ((sa <= 0.0) != (sb <= 0.0)) best1 = fmax(best1, k + sa / (sa - sb));
+    {
+      const double a = phi[i0], b = phi[i1];
+      if ((a <= 0.0) != (b <= 0.0)) {
+        const double x = k + a / (a - b);
+        if (x > best[0]) {
+          best[0] = x;
+          if (tan) dbest[0] = (a * dphi[i1] - b * dphi[i0]) / ((a - b) * (a - b));
+        }
+      }
+    }
+    {
+      const double a = w[i0] * (1.0 - fl[i0]) - 0.5, b = w[i1] * (1.0 - fl[i1]) - 0.5;
+      if ((a <= 0.0) != (b <= 0.0)) {
+        const double x = k + a / (a - b);
+        if (x > best[1]) {
+          best[1] = x;
+          if (tan) {
+            const double da = dw[i0] * (1.0 - fl[i0]) - w[i0] * dfl[i0];
+            const double db = dw[i1] * (1.0 - fl[i1]) - w[i1] * dfl[i1];
+            dbest[1] = (a * db - b * da) / ((a - b) * (a - b));
+          }
+        }
+      }
+    }
   }
+  // keep the larger position and its derivative (ties: the first operand)
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
-    best0 = fmax(best0, __shfl_xor_sync(0xffffffffu, best0, o));
-    best1 = fmax(best1, __shfl_xor_sync(0xffffffffu, best1, o));
+#pragma unroll
+    for (int q = 0; q < 2; q++) {
+      const double x = __shfl_xor_sync(0xffffffffu, best[q], o);
+      const double dx = __shfl_xor_sync(0xffffffffu, dbest[q], o);
+      if (x > best[q] || (x == best[q] && dx < dbest[q])) {
+        best[q] = x;
+        dbest[q] = dx;
+      }
+    }
   }
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   if (lane == 0) {
-    s_best[0][warp] = best0;
-    s_best[1][warp] = best1;
+#pragma unroll
+    for (int q = 0; q < 2; q++) {
+      s_best[q][0][warp] = best[q];
+      s_best[q][1][warp] = dbest[q];
+    }
   }
   __syncthreads();
   if (threadIdx.x < 2) {
-    double b = -1.0;
-    for (int v = 0; v < NT / 32; v++) b = fmax(b, s_best[threadIdx.x][v]);
-    out[threadIdx.x] = b < 0.0 ? __longlong_as_double(0x7ff8000000000000ULL) : b;
+    const int q = threadIdx.x;
+    double b = -1.0, db = 0.0;
+    for (int v = 0; v < NT / 32; v++) {
+      if (s_best[q][0][v] > b) {
+        b = s_best[q][0][v];
+        db = s_best[q][1][v];
+      }
+    }
+    const double nan = __longlong_as_double(0x7ff8000000000000ULL);
+    out[q] = b < 0.0 ? nan : b;
+    if (tan) out[2 + q] = b < 0.0 ? nan : db;
   }
 }
 
-cudaError_t launch_crossings(const double* phi, const double* w, const double* fl, int nx, int ny,
-                             int axis, int index, double* out, cudaStream_t s) {
-  lbm_crossings_kernel<<<1, NT, 0, s>>>(phi, w, fl, nx, ny, axis, index, out);
+cudaError_t launch_crossings(const double* phi, const double* w, const double* fl,
+                             const double* dphi, const double* dw, const double* dfl, int nx,
+                             int ny, int axis, int index, double* out, cudaStream_t s) {
+  lbm_crossings_kernel<<<1, NT, 0, s>>>(phi, w, fl, dphi, dw, dfl, nx, ny, axis, index, out);
   return cudaGetLastError();
 }
 

@@ -3,6 +3,7 @@
 #pragma once
 
 #include <cmath>
+#include <cstddef>
 #include <cstdio>
 
 #include "../../include/lbm.h"
@@ -46,6 +47,26 @@ inline Coef<R> make_coef(const lbm_params& p) {
   return c;
 }
 
+// Tangent constants: the FP64 constants with the derivatives of the
+// parameters that the direction moves (cos of the contact angle in degrees).
+inline Coef<lbmk::Dual> make_coef_tangent(const lbm_params& p) {
+  const Coef<double> v = make_coef<double>(p);
+  Coef<lbmk::Dual> c;
+  const double* src = (const double*)&v;
+  lbmk::Dual* dst = (lbmk::Dual*)&c;
+  const size_t nreal = (sizeof(Coef<double>) - sizeof(double)) / sizeof(double);  // all but readings
+  static_assert(offsetof(Coef<double>, readings) == (sizeof(Coef<double>) - sizeof(double)),
+                "readings is the last member");
+  for (size_t k = 0; k < nreal; k++) dst[k] = lbmk::Dual(src[k]);
+  c.readings = v.readings;
+  const double pi = 3.14159265358979323846;
+  for (int k = 0; k < 4; k++) c.T_wall[k].d = p.tan_T_wall[k];
+  c.T_cold.d = p.tan_T_cold;
+  c.cos_th.d = -std::sin(p.theta_deg * pi / 180.0) * (pi / 180.0) * p.tan_theta_deg;
+  c.latent.d = p.tan_latent;
+  return c;
+}
+
 inline int validate(const lbm_params* p, char* err, size_t n) {
   if (!p) return LBM_ERR_ARG;
   if (p->nx < 2 || p->ny < 2) {
@@ -58,7 +79,8 @@ inline int validate(const lbm_params* p, char* err, size_t n) {
     std::snprintf(err, n, "grid of %d x %d nodes is too large", p->nx, p->ny);
     return LBM_ERR_ARG;
   }
-  if (p->precision != LBM_FP32 && p->precision != LBM_FP64 && p->precision != LBM_FP16S) {
+  if (p->precision != LBM_FP32 && p->precision != LBM_FP64 && p->precision != LBM_FP16S &&
+      p->precision != LBM_FP64_TANGENT) {
     std::snprintf(err, n, "unknown precision %d", p->precision);
     return LBM_ERR_ARG;
   }

@@ -32,6 +32,8 @@
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
+#include "lbm_dual.cuh"
+
 namespace lbmk {
 
 constexpr int TX = 32, TY = 8;
@@ -202,6 +204,15 @@ __device__ __forceinline__ void cold_mask_h(const Coef<R>& c, R w, R phi0, R* h)
 // population storage: the arithmetic type itself, or FP16 (round to nearest)
 // ---------------------------------------------------------------------------
 
+// Read-out of one field value at dense index d of an N-node field; a
+// tangent value writes its derivative N entries further on.
+__device__ __forceinline__ void put_out(double* p, long long d, long long, float v) { p[d] = v; }
+__device__ __forceinline__ void put_out(double* p, long long d, long long, double v) { p[d] = v; }
+__device__ __forceinline__ void put_out(double* p, long long d, long long N, const Dual& v) {
+  p[d] = v.v;
+  p[d + N] = v.d;
+}
+
 __device__ __forceinline__ float ldp(const float* p) { return *p; }
 __device__ __forceinline__ double ldp(const double* p) { return *p; }
 __device__ __forceinline__ float ldp(const __half* p) { return __half2float(*p); }
@@ -325,6 +336,11 @@ __device__ __forceinline__ R warp_sum(R v) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   return v;
 }
+__device__ __forceinline__ Dual warp_sum(Dual v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += shfl_xor(v, o);
+  return v;
+}
 
 // Per-tile partial sums of the diagnostics in a fixed order (warp shuffles,
 // then the warps in order), written to partial[k * nb + b] for tile b of nb.
@@ -373,7 +389,7 @@ template <typename R>
 __device__ __forceinline__ void block_diag_warps(const R* dvals, R (*s_red)[NDIAG], int tid) {
   const int lane = tid & 31, warp = tid >> 5;
   static_assert(NDIAG == 9, "the reduce-scatter covers diagnostics 0-7, the ninth is separate");
-  if (LBM_DIAG_BUTTERFLY && sizeof(R) == 4) {
+  if constexpr (LBM_DIAG_BUTTERFLY && sizeof(R) == 4) {
     const R v = warp_sum8(dvals, lane);
     if ((lane & 3) == 0) s_red[warp][(lane >> 2) & 7] = v;
     const R v8 = warp_sum(dvals[8]);
@@ -395,7 +411,15 @@ __device__ __forceinline__ void block_diag_finish(const R (*s_red)[NDIAG],
                                                   int nb) {
   __syncthreads();
   if (tid < NDIAG) {
-    if (sizeof(R) == 8) {
+    if constexpr (is_dual<R>::value) {
+      // tangent step: values in the first NDIAG * nb partials, derivatives
+      // in the next NDIAG * nb
+      R acc = R(0);
+#pragma unroll
+      for (int w = 0; w < NT / 32; w++) acc += s_red[w][tid];
+      partial[(long long)tid * nb + b] = acc.v;
+      partial[(long long)(NDIAG + tid) * nb + b] = acc.d;
+    } else if constexpr (sizeof(R) == 8) {
       double acc = 0.0;
 #pragma unroll
       for (int w = 0; w < NT / 32; w++) acc += (double)s_red[w][tid];

@@ -25,6 +25,9 @@ cudaError_t launch_init_f32(const InitArgs<float>& a, cudaStream_t s);
 // FP16 population storage, FP32 arithmetic.
 cudaError_t launch_step_f16s(const Args<float, __half>& a, int mode, bool diag, cudaStream_t s);
 cudaError_t launch_init_f16s(const InitArgs<float, __half>& a, cudaStream_t s);
+// Forward-mode tangent (FP64 value and derivative).
+cudaError_t launch_step_tan(const Args<Dual>& a, int mode, bool diag, cudaStream_t s);
+cudaError_t launch_init_tan(const InitArgs<Dual>& a, cudaStream_t s);
 // Up to BATCH_MAX_GRIDS grids in one launch, one CTA per tile.
 cudaError_t launch_batch_f32(const BatchTable<float>& b, bool diag, bool all, cudaStream_t s);
 cudaError_t launch_batch_f64(const BatchTable<double>& b, bool diag, bool all, cudaStream_t s);
@@ -33,8 +36,9 @@ cudaError_t launch_diag_finalize(const double* partial, int nb, double* out, lon
                                  cudaStream_t s);
 cudaError_t launch_init_f64(const InitArgs<double>& a, cudaStream_t s);
 // Interface crossings along one line of dense FP64 fields (one CTA); out: 2
-// device doubles.
-cudaError_t launch_crossings(const double* phi, const double* w, const double* fl, int nx, int ny,
-                             int axis, int index, double* out, cudaStream_t s);
+// device doubles, or 4 with the derivative fields (else null).
+cudaError_t launch_crossings(const double* phi, const double* w, const double* fl,
+                             const double* dphi, const double* dw, const double* dfl, int nx,
+                             int ny, int axis, int index, double* out, cudaStream_t s);
 
 }  // namespace lbmk

@@ -57,8 +57,8 @@ extern "C" int lbm_diagnostics_noalloc(const lbm_params* params, const void* pop
     std::fprintf(stderr, "lbm_diagnostics_noalloc: %s\n", err);
     return st;
   }
-  if (params->precision == LBM_FP16S) {
-    std::fprintf(stderr, "lbm_diagnostics_noalloc: FP16 population storage is not supported\n");
+  if (params->precision == LBM_FP16S || params->precision == LBM_FP64_TANGENT) {
+    std::fprintf(stderr, "lbm_diagnostics_noalloc: only LBM_FP32 and LBM_FP64 states\n");
     return LBM_ERR_UNSUPPORTED;
   }
   lbmk::Geom g = lbmh::make_geom(*params);

@@ -42,7 +42,8 @@ __device__ __forceinline__ double ld_sum(const double* p) {
 // through ld_sum (re-read in phase B).
 template <bool PLAIN, typename S>
 __device__ __forceinline__ auto ld_pop(const S* p) {
-  if constexpr (PLAIN || std::is_same<S, __half>::value) return ldp(p);
+  if constexpr (PLAIN || !(std::is_same<S, float>::value || std::is_same<S, double>::value))
+    return ldp(p);
   else return ld_sum(p);
 }
 
@@ -461,7 +462,7 @@ __device__ __forceinline__ void step_tile(const Args<R, S>& a, int bx, int by, i
 #pragma unroll
         for (int i = 0; i < 9; i++) tot += f[i];
       }
-      dvals[8] = isfinite(tot) ? R(0) : R(1);
+      dvals[8] = finite(tot) ? R(0) : R(1);
     }
   } else if (DIAG) {
 #pragma unroll
@@ -519,7 +520,7 @@ __device__ __forceinline__ void step_tile(const Args<R, S>& a, int bx, int by, i
       const R vals[NFIELD] = {phi, fs, L.fl, T, L.rhoH, M.pr, M.ux, M.uy, rho, M.muphi, L.w, mdot};
 #pragma unroll
       for (int k = 0; k < NFIELD; k++)
-        if (a.out[k]) a.out[k][d] = (double)vals[k];
+        if (a.out[k]) put_out(a.out[k], d, (long long)g.nx * g.ny, vals[k]);
     }
   }
   if (DIAG) {

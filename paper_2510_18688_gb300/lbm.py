@@ -16,8 +16,8 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_lib", "liblbm_gb300.so")
 
 LBM_OK, LBM_ERR_NONFINITE = 0, -5
-LBM_FP64, LBM_FP32, LBM_FP16S = 0, 1, 2
-PRECISION = {"fp64": LBM_FP64, "fp32": LBM_FP32, "fp16s": LBM_FP16S}
+LBM_FP64, LBM_FP32, LBM_FP16S, LBM_FP64_TANGENT = 0, 1, 2, 3
+PRECISION = {"fp64": LBM_FP64, "fp32": LBM_FP32, "fp16s": LBM_FP16S, "tangent": LBM_FP64_TANGENT}
 LBM_HOST, LBM_DEVICE = 0, 1
 BC = {"periodic": 0, "dirichlet": 1, "adiabatic": 2}
 FIELDS = ("phi", "fs", "fl", "T", "rhoH", "p", "ux", "uy", "rho", "mu", "w", "mdot")
@@ -42,6 +42,9 @@ class LbmParams(ctypes.Structure):
         ("T_cold", ctypes.c_double),
         ("readings", ctypes.c_uint32),
         ("diag_every", ctypes.c_int32),
+        ("tan_T_wall", ctypes.c_double * 4),
+        ("tan_T_cold", ctypes.c_double), ("tan_theta_deg", ctypes.c_double),
+        ("tan_latent", ctypes.c_double),
     ]
 
 
@@ -56,7 +59,8 @@ EXPORTS = ("lbm_create", "lbm_set_geometry", "lbm_step", "lbm_read_fields",
            "lbm_save_state", "lbm_load_state", "lbm_step_count", "lbm_last_error",
            "lbm_status_string", "lbm_destroy", "lbm_diagnostics_noalloc",
            "lbm_batch_create", "lbm_batch_step", "lbm_batch_destroy", "lbm_probe_fma_rate",
-           "lbm_read_crossings")
+           "lbm_read_crossings", "lbm_read_tangent_fields", "lbm_read_tangent_diagnostics",
+           "lbm_read_crossings_tangent")
 
 _lib = None
 
@@ -95,11 +99,15 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     L.lbm_batch_destroy.restype = None
     L.lbm_probe_fma_rate.argtypes = [ctypes.c_int, dp, vp]
     L.lbm_read_crossings.argtypes = [vp, ctypes.c_int, ctypes.c_int, dp, vp]
+    L.lbm_read_crossings_tangent.argtypes = [vp, ctypes.c_int, ctypes.c_int, dp, vp]
+    L.lbm_read_tangent_fields.argtypes = [vp, ctypes.c_uint32, ctypes.POINTER(vp), ctypes.c_int, vp]
+    L.lbm_read_tangent_diagnostics.argtypes = [vp, ctypes.POINTER(LbmDiag)]
     for fn in ("lbm_create", "lbm_set_geometry", "lbm_step", "lbm_read_fields",
                "lbm_compute_diagnostics", "lbm_read_diagnostics", "lbm_state_size",
                "lbm_save_state", "lbm_load_state", "lbm_diagnostics_noalloc",
                "lbm_batch_create", "lbm_batch_step", "lbm_probe_fma_rate",
-               "lbm_read_crossings"):
+               "lbm_read_crossings", "lbm_read_crossings_tangent", "lbm_read_tangent_fields",
+               "lbm_read_tangent_diagnostics"):
         getattr(L, fn).restype = ctypes.c_int
     _lib = L
     return L
@@ -111,7 +119,11 @@ class LbmError(RuntimeError):
         self.status = status
 
 
-def make_params(cfg: dict, precision: str = "fp32", diag_every: int = 0) -> LbmParams:
+def make_params(cfg: dict, precision: str = "fp32", diag_every: int = 0,
+                tangent: dict = None) -> LbmParams:
+    """lbm_params of a workload dict.  tangent (precision "tangent"): the
+    parameter direction as rates {"T_wall": [4 values], "T_cold",
+    "theta_deg", "latent"} (missing entries: 0)."""
     p = LbmParams()
     p.nx, p.ny = int(cfg["nx"]), int(cfg["ny"])
     p.precision = PRECISION[precision]
@@ -125,6 +137,12 @@ def make_params(cfg: dict, precision: str = "fp32", diag_every: int = 0) -> LbmP
         setattr(p, name, float(cfg[name]))
     p.readings = int(cfg.get("readings", 0))
     p.diag_every = int(diag_every)
+    t = tangent or {}
+    for k, v in enumerate(t.get("T_wall", (0.0, 0.0, 0.0, 0.0))):
+        p.tan_T_wall[k] = float(v)
+    p.tan_T_cold = float(t.get("T_cold", 0.0))
+    p.tan_theta_deg = float(t.get("theta_deg", 0.0))
+    p.tan_latent = float(t.get("latent", 0.0))
     return p
 
 
@@ -154,6 +172,27 @@ def lbm_step(ctx, nsteps: int, stream=None):
 def lbm_read_fields(ctx, field_mask: int, out_ptrs, where, stream=None):
     arr = (ctypes.c_void_p * len(FIELDS))(*[p or None for p in out_ptrs])
     _check(ctx, load().lbm_read_fields(ctx, field_mask, arr, where, stream), "lbm_read_fields")
+
+
+def lbm_read_tangent_fields(ctx, field_mask: int, out_ptrs, where, stream=None):
+    arr = (ctypes.c_void_p * len(FIELDS))(*[p or None for p in out_ptrs])
+    _check(ctx, load().lbm_read_tangent_fields(ctx, field_mask, arr, where, stream),
+           "lbm_read_tangent_fields")
+
+
+def lbm_read_tangent_diagnostics(ctx) -> dict:
+    d = LbmDiag()
+    _check(ctx, load().lbm_read_tangent_diagnostics(ctx, ctypes.byref(d)),
+           "lbm_read_tangent_diagnostics")
+    return {k: getattr(d, k) for k, _ in LbmDiag._fields_}
+
+
+def lbm_read_crossings_tangent(ctx, axis: int, index: int, stream=None):
+    """(phi = 0 crossing, ice front, their derivatives) along one line."""
+    out = (ctypes.c_double * 4)()
+    _check(ctx, load().lbm_read_crossings_tangent(ctx, int(axis), int(index), out, stream),
+           "lbm_read_crossings_tangent")
+    return tuple(out)
 
 
 def lbm_compute_diagnostics(ctx, stream=None):
@@ -257,7 +296,8 @@ class Solver:
     ``paper_2510_18688_gb300.workloads``; fields come back as torch tensors
     on the device (or numpy arrays with ``host=True``)."""
 
-    def __init__(self, cfg: dict, precision: str = "fp32", diag_every: int = 0):
+    def __init__(self, cfg: dict, precision: str = "fp32", diag_every: int = 0,
+                 tangent: dict = None):
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("Solver needs a CUDA device (no CPU path)")
@@ -265,7 +305,7 @@ class Solver:
         self.cfg = dict(cfg)
         self.nx, self.ny = int(cfg["nx"]), int(cfg["ny"])
         self.precision = precision
-        self.params = make_params(cfg, precision, diag_every)
+        self.params = make_params(cfg, precision, diag_every, tangent)
         self.ctx = lbm_create(self.params)
 
     def close(self):
@@ -313,7 +353,20 @@ class Solver:
         """Interface positions along one line (see lbm_read_crossings)."""
         return lbm_read_crossings(self.ctx, axis, index, _stream())
 
-    def fields(self, names=FIELDS, host: bool = True) -> dict:
+    def crossings_tangent(self, axis: int, index: int):
+        """Crossings and their derivatives (tangent contexts)."""
+        return lbm_read_crossings_tangent(self.ctx, axis, index, _stream())
+
+    def tangent_fields(self, names=FIELDS) -> dict:
+        """Derivatives of the fields along the parameter direction (host)."""
+        return self.fields(names, host=True, deriv=True)
+
+    def tangent_diagnostics(self, compute: bool = True) -> dict:
+        if compute:
+            lbm_compute_diagnostics(self.ctx, _stream())
+        return lbm_read_tangent_diagnostics(self.ctx)
+
+    def fields(self, names=FIELDS, host: bool = True, deriv: bool = False) -> dict:
         import torch
         mask = 0
         ptrs = [None] * len(FIELDS)
@@ -326,7 +379,8 @@ class Solver:
             else:
                 out[k] = torch.empty((self.ny, self.nx), dtype=torch.float64, device="cuda")
                 ptrs[FIELDS.index(k)] = out[k].data_ptr()
-        lbm_read_fields(self.ctx, mask, ptrs, LBM_HOST if host else LBM_DEVICE, _stream())
+        read = lbm_read_tangent_fields if deriv else lbm_read_fields
+        read(self.ctx, mask, ptrs, LBM_HOST if host else LBM_DEVICE, _stream())
         return out
 
     def diagnostics(self, compute: bool = True) -> dict:

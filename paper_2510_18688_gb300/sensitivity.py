@@ -1,0 +1,134 @@
+"""Gradients of freezing observables with respect to the problem's
+parameters, from forward-mode (tangent) steps of the fused kernel.
+
+The parameters are those of the paper's problem statement: the wall
+temperature T_w (Dirichlet walls and the cold substrate), the contact angle
+theta (Eq. (4)) and the Stefan number Ste = Cp_l (T_m - T_w) / L (Eq. (29),
+T_m = 0), so the latent heat follows both T_w and Ste.  The initial state is
+held fixed.  One tangent context (``precision="tangent"``) per parameter
+carries the derivative of every value through the same steps as the FP64
+forward run; the observables and their derivatives are read from the FP64
+diagnostic sums and the interface crossings:
+
+* frozen fraction FF = sum w (1 - fl) / sum w (Sec. 4.3's freezing measure);
+* tip height = the last phi = 0 crossing along a grid line (the droplet
+  axis), Secs. 4.3-4.4.
+
+``FreezingObservables`` wraps this as a ``torch.autograd.Function`` of the
+parameter vector (T_w, theta_deg, Ste).
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from . import lbm
+
+PARAMS = ("T_w", "theta_deg", "ste")
+
+
+def latent(cfg: dict, T_w: float, ste: float) -> float:
+    """L of Eq. (29) with T_m = 0."""
+    return float(cfg["cp_l"]) * (0.0 - T_w) / ste
+
+
+def apply_params(cfg: dict, T_w: float, theta_deg: float, ste: float, wall) -> dict:
+    """The workload dict with the parameters set.  wall: where T_w applies,
+    a collection of wall indices 0-3 (x-low, x-high, y-low, y-high) and/or
+    "cold" for the cold-mask temperature."""
+    c = dict(cfg)
+    tw = list(c["T_wall"])
+    for k in wall:
+        if k == "cold":
+            c["T_cold"] = T_w
+        else:
+            tw[int(k)] = T_w
+    c["T_wall"] = tuple(tw)
+    c["theta_deg"] = theta_deg
+    c["latent"] = latent(cfg, T_w, ste)
+    return c
+
+
+def direction(cfg: dict, name: str, T_w: float, ste: float, wall) -> dict:
+    """Rates of the context parameters per unit of parameter `name`."""
+    L = latent(cfg, T_w, ste)
+    if name == "T_w":
+        rates = [0.0, 0.0, 0.0, 0.0]
+        for k in wall:
+            if k != "cold":
+                rates[int(k)] = 1.0
+        return {"T_wall": rates, "T_cold": 1.0 if "cold" in wall else 0.0,
+                "latent": -float(cfg["cp_l"]) / ste}
+    if name == "theta_deg":
+        return {"theta_deg": 1.0}
+    if name == "ste":
+        return {"latent": -L / ste}
+    raise ValueError(name)
+
+
+def observables(s: "lbm.Solver", line) -> np.ndarray:
+    """(FF, tip height) of a solver's current state; tip NaN without line."""
+    d = s.diagnostics(compute=True)
+    ff = d["frozen_volume"] / d["material_volume"]
+    tip = s.crossings(*line)[0] if line is not None else float("nan")
+    return np.array([ff, tip])
+
+
+def tangent_observables(s: "lbm.Solver", line) -> np.ndarray:
+    """Derivatives of (FF, tip height) from a tangent solver's state."""
+    d = s.diagnostics(compute=True)
+    t = s.tangent_diagnostics(compute=False)
+    fz, mv = d["frozen_volume"], d["material_volume"]
+    dff = (t["frozen_volume"] * mv - fz * t["material_volume"]) / (mv * mv)
+    dtip = s.crossings_tangent(*line)[2] if line is not None else float("nan")
+    return np.array([dff, dtip])
+
+
+def run(cfg: dict, arrays: dict, steps: int, precision="fp64", tangent=None) -> "lbm.Solver":
+    """A solver advanced `steps` steps from the arrays."""
+    return lbm.Solver(cfg, precision=precision, tangent=tangent).set_geometry(arrays).step(steps)
+
+
+def value_and_jacobian(cfg: dict, arrays: dict, steps: int, p, wall, line):
+    """(FF, tip) and their 2 x 3 Jacobian with respect to (T_w, theta, Ste)."""
+    T_w, th, ste = (float(v) for v in p)
+    c = apply_params(cfg, T_w, th, ste, wall)
+    s = run(c, arrays, steps)
+    val = observables(s, line)
+    s.close()
+    J = np.empty((2, 3))
+    for j, name in enumerate(PARAMS):
+        t = run(c, arrays, steps, precision="tangent",
+                tangent=direction(cfg, name, T_w, ste, wall))
+        J[:, j] = tangent_observables(t, line)
+        t.close()
+    return val, J
+
+
+class FreezingObservables:
+    """``FreezingObservables.apply(p, cfg, arrays, steps, wall, line)``:
+    (FF, tip height) after `steps` steps as a differentiable function of
+    p = (T_w, theta_deg, Ste) (a float64 tensor); the backward pass returns
+    J^T grad from three tangent runs."""
+
+    _fn = None
+
+    @classmethod
+    def apply(cls, p, cfg, arrays, steps, wall, line):
+        if cls._fn is None:
+            import torch
+
+            class _Fn(torch.autograd.Function):
+                @staticmethod
+                def forward(ctx, p, cfg, arrays, steps, wall, line):
+                    val, J = value_and_jacobian(cfg, arrays, steps, p.detach().cpu().numpy(),
+                                                wall, line)
+                    ctx.save_for_backward(torch.as_tensor(J, dtype=torch.float64))
+                    return torch.as_tensor(val, dtype=torch.float64)
+
+                @staticmethod
+                def backward(ctx, g):
+                    (J,) = ctx.saved_tensors
+                    return (J.T @ g.to(J.dtype)).to(g.device), None, None, None, None, None
+
+            cls._fn = _Fn
+        return cls._fn.apply(p, cfg, arrays, steps, wall, line)

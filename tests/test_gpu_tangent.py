@@ -1,0 +1,149 @@
+"""Forward-mode (tangent) derivatives of the fused step, through the C ABI.
+
+The tangent context carries, beside every FP64 value, its derivative along
+one parameter direction.  Checked here: its values are those of the FP64
+step; its derivatives of the frozen fraction and of the droplet's tip height
+with respect to the wall temperature, the contact angle and the Stefan
+number agree with central differences of the FP64 GPU step and of the FP64
+oracle; the torch.autograd.Function returns J^T grad.
+"""
+import numpy as np
+import pytest
+
+from paper_2510_18688_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+FIELDS = ("phi", "fs", "fl", "T", "rhoH", "p", "ux", "uy", "rho", "mu", "w", "mdot")
+
+
+@pytest.fixture(scope="module")
+def env(oracle_mod):
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2510_18688_gb300 import build, lbm, sensitivity
+    build.build()
+    lbm.load()
+    return oracle_mod, lbm, sensitivity, torch
+
+
+# central-difference steps per parameter (T_w, theta in degrees, Ste)
+H = (1e-4, 1e-3, 1e-5)
+
+
+def _droplet(n=64):
+    cfg, arr = W.sessile_droplet(n, seed=3, radius=n / 4, hs=n / 10, theta_deg=80.0, ste=0.3)
+    return cfg, arr, (-1.0, 80.0, 0.3), ("cold", 2), (1, n // 2)
+
+
+def _fd(observe, p0):
+    out = np.empty((2, 3))
+    for j in range(3):
+        pp, pm = list(p0), list(p0)
+        pp[j] += H[j]
+        pm[j] -= H[j]
+        out[:, j] = (observe(pp) - observe(pm)) / (2 * H[j])
+    return out
+
+
+def _close(J, ref, rtol, atol):
+    return np.all(np.abs(J - ref) <= rtol * np.abs(ref) + atol)
+
+
+def test_tangent_values_are_the_fp64_step(env):
+    O, lbm, S, torch = env
+    cfg, arr = W.random_state(70, 45, seed=12)
+    a = lbm.Solver(cfg, precision="fp64").set_geometry(arr).step(60)
+    t = lbm.Solver(cfg, precision="tangent", tangent={"theta_deg": 1.0, "latent": 2.0}
+                   ).set_geometry(arr).step(60)
+    fa, ft = a.fields(), t.fields()
+    for k in FIELDS:
+        scale = np.abs(fa[k]).max() + 1e-300
+        assert np.abs(fa[k] - ft[k]).max() <= 1e-12 * scale, k
+    dt = t.tangent_fields()
+    assert all(np.all(np.isfinite(dt[k])) for k in FIELDS)
+    assert np.abs(dt["phi"]).max() > 0.0  # the angle moves the interface
+    a.close()
+    t.close()
+
+
+def test_tangent_matches_central_differences_of_the_gpu_step(env):
+    O, lbm, S, torch = env
+    cfg, arr, p0, wall, line = _droplet()
+    steps = 300
+    val, J = S.value_and_jacobian(cfg, arr, steps, p0, wall, line)
+
+    def observe(p):
+        s = S.run(S.apply_params(cfg, *p, wall), arr, steps)
+        v = S.observables(s, line)
+        s.close()
+        return v
+
+    fd = _fd(observe, p0)
+    print("\nJ =\n", J, "\nFD =\n", fd)
+    assert val[0] > 0.0 and np.isfinite(val[1])  # ice has formed; the drop has a tip
+    assert np.abs(J[0]).max() > 0.0
+    assert _close(J, fd, 1e-3, np.array([[1e-9], [1e-7]])), (J, fd)
+
+
+def test_tangent_of_the_neumann_front(env):
+    O, lbm, S, torch = env
+    cfg, arr = W.neumann()
+    steps, wall, p0 = 3000, (0,), (-1.0, 90.0, 0.1)
+    val, J = S.value_and_jacobian(cfg, arr, steps, p0, wall, None)
+
+    def observe(p):
+        s = S.run(S.apply_params(cfg, *p, wall), arr, steps)
+        v = S.observables(s, None)
+        s.close()
+        return v
+
+    fd = _fd(observe, p0)
+    print("\nJ =", J[0], "FD =", fd[0])
+    assert J[0, 1] == 0.0  # no phase field: the angle does not enter
+    assert _close(J[0], fd[0], 1e-3, 1e-9), (J[0], fd[0])
+
+
+def test_tangent_matches_central_differences_of_the_oracle(env):
+    O, lbm, S, torch = env
+    cfg, arr, p0, wall, line = _droplet(40)
+    steps = 120
+    val, J = S.value_and_jacobian(cfg, arr, steps, p0, wall, line)
+
+    def observe(p):
+        o = O.from_workload((S.apply_params(cfg, *p, wall), arr)).step(steps)
+        d = o.diagnostics()
+        f = o.fields()
+        tip = O.crossings(f["phi"], f["w"], f["fl"], *line)[0]
+        return np.array([d["frozen_volume"] / d["material_volume"], tip])
+
+    fd = _fd(observe, p0)
+    print("\nJ =\n", J, "\noracle FD =\n", fd)
+    assert _close(J, fd, 1e-3, np.array([[1e-9], [1e-7]])), (J, fd)
+
+
+def test_autograd_function_returns_the_jacobian_product(env):
+    O, lbm, S, torch = env
+    cfg, arr, p0, wall, line = _droplet(48)
+    steps = 150
+    p = torch.tensor(p0, dtype=torch.float64, requires_grad=True)
+    y = S.FreezingObservables.apply(p, cfg, arr, steps, wall, line)
+    (y[0] + 0.01 * y[1]).backward()
+    val, J = S.value_and_jacobian(cfg, arr, steps, p0, wall, line)
+    assert np.allclose(y.detach().numpy(), val, rtol=0, atol=0)
+    assert np.allclose(p.grad.numpy(), J[0] + 0.01 * J[1], rtol=1e-12, atol=0)
+
+
+def test_tangent_rejected_where_unsupported(env):
+    O, lbm, S, torch = env
+    cfg, arr = W.random_state(40, 20, seed=3)
+    s = lbm.Solver(cfg, precision="tangent").set_geometry(arr)
+    with pytest.raises(lbm.LbmError):
+        lbm.Batch([s])
+    f = lbm.Solver(cfg, precision="fp64").set_geometry(arr)
+    with pytest.raises(lbm.LbmError) as e:
+        f.tangent_fields()
+    assert e.value.status == -6
+    s.close()
+    f.close()
