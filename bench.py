@@ -99,7 +99,7 @@ def kernel_source_hash() -> str:
 
 def profile_name(workload: str, precision: str) -> str:
     kind = "batch" if workload.startswith("batch") else "step"
-    tag = {"fp32": "f32", "fp64": "f64", "fp16s": "f16s"}[precision]
+    tag = {"fp32": "f32", "fp64": "f64", "fp16s": "f16s", "tangent": "tan"}[precision]
     return f"lbm_{kind}_{tag}_{workload}.md"
 
 
@@ -266,8 +266,9 @@ def main():
     ap.add_argument("--steps", type=int, default=4000)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64", "fp16s"],
-                    help="fp16s: FP16 population storage, FP32 arithmetic")
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64", "fp16s", "tangent"],
+                    help="fp16s: FP16 population storage, FP32 arithmetic; tangent: FP64 "
+                         "step with its derivative along the wall temperature")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--diag-every", type=int, default=1,
                     help="steps between fused FP64 diagnostic reductions (0: none)")
@@ -297,8 +298,10 @@ def main():
     n = sum(c["nx"] * c["ny"] for c, _ in wls)
     stream = torch.cuda.current_stream()
     sptr = ctypes.c_void_p(stream.cuda_stream)
-    solvers = [lbm.Solver(c, precision=args.precision, diag_every=args.diag_every).set_geometry(a)
-               for c, a in wls]
+    # tangent: derivative along the wall temperature (cold substrate and walls)
+    tan = {"T_cold": 1.0, "T_wall": [1.0, 1.0, 1.0, 1.0]} if args.precision == "tangent" else None
+    solvers = [lbm.Solver(c, precision=args.precision, diag_every=args.diag_every,
+                          tangent=tan).set_geometry(a) for c, a in wls]
     batch = lbm.Batch(solvers) if len(solvers) > 1 else None
 
     def step(k):
@@ -386,7 +389,7 @@ def main():
         if pg:
             pg.destroy_process_group()
         return
-    esize = 8 if args.precision == "fp64" else 4
+    esize = {"fp64": 8, "tangent": 16}.get(args.precision, 4)
     pop_bytes = 2 if args.precision == "fp16s" else esize
     # node-weighted bytes per node (grids with a cold mask read one more byte)
     bpn = sum(algorithmic_bytes_per_node(esize, "mask" in a, pop_bytes) * c["nx"] * c["ny"]
@@ -397,7 +400,7 @@ def main():
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "traffic": traffic,
                 "peak_source": peak_src, "bytes_per_node": bpn}
-    if args.precision == "fp64":
+    if args.precision in ("fp64", "tangent"):
         # the FP64 pipe, not HBM, bounds the double-precision step on this
         # part: compare its executed FP64 flops with the FMA rate measured now
         fma = lbm.lbm_probe_fma_rate("fp64", sptr)
@@ -414,7 +417,8 @@ def main():
         "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_step,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": {"fp32": "f32", "fp64": "f64", "fp16s": "f32 (f16 storage)"}[args.precision],
+        "dtype": {"fp32": "f32", "fp64": "f64", "fp16s": "f32 (f16 storage)",
+                  "tangent": "f64 (value and derivative)"}[args.precision],
         "data": "synthetic",
         "config": {"workload": workload_name + f", seed {rank}",
                    "grid": ([wls[0][0]["nx"], wls[0][0]["ny"]] if len(wls) == 1

@@ -12,7 +12,9 @@ diagnostic sums and the interface crossings:
 
 * frozen fraction FF = sum w (1 - fl) / sum w (Sec. 4.3's freezing measure);
 * tip height = the last phi = 0 crossing along a grid line (the droplet
-  axis), Secs. 4.3-4.4.
+  axis), Secs. 4.3-4.4;
+* freezing time = the first time FF reaches a level (0.99), interpolated
+  linearly between the two steps that bracket it.
 
 ``FreezingObservables`` wraps this as a ``torch.autograd.Function`` of the
 parameter vector (T_w, theta_deg, Ste).
@@ -102,6 +104,42 @@ def value_and_jacobian(cfg: dict, arrays: dict, steps: int, p, wall, line):
         J[:, j] = tangent_observables(t, line)
         t.close()
     return val, J
+
+
+def _ff(d: dict) -> float:
+    return d["frozen_volume"] / d["material_volume"]
+
+
+def _dff(d: dict, t: dict) -> float:
+    fz, mv = d["frozen_volume"], d["material_volume"]
+    return (t["frozen_volume"] * mv - fz * t["material_volume"]) / (mv * mv)
+
+
+def freezing_time(cfg: dict, arrays: dict, p, wall, name: str, level: float = 0.99,
+                  max_steps: int = 200000):
+    """(t*, dt*/d name): t* = n0 + (level - FF(n0)) / (FF(n0 + 1) - FF(n0)) for
+    the step n0 after which FF first reaches `level`; its derivative is the
+    exact derivative of that expression, from the tangent diagnostics of the
+    two steps.  (nan, nan) if FF stays below `level` for max_steps steps."""
+    T_w, th, ste = (float(v) for v in p)
+    c = apply_params(cfg, T_w, th, ste, wall)
+    t = run(c, arrays, 0, precision="tangent", tangent=direction(cfg, name, T_w, ste, wall))
+    prev = None
+    try:
+        for n in range(max_steps + 1):
+            d = t.diagnostics(compute=True)
+            ff, dff = _ff(d), _dff(d, t.tangent_diagnostics(compute=False))
+            if prev is not None and ff >= level:
+                ff0, dff0 = prev
+                span = ff - ff0
+                frac = (level - ff0) / span
+                dfrac = (-dff0 * span - (level - ff0) * (dff - dff0)) / (span * span)
+                return (n - 1) + frac, dfrac
+            prev = (ff, dff)
+            t.step(1)
+    finally:
+        t.close()
+    return float("nan"), float("nan")
 
 
 class FreezingObservables:

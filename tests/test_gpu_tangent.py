@@ -156,3 +156,37 @@ def test_tangent_rejected_where_unsupported(env):
     assert e.value.status == -6
     s.close()
     f.close()
+
+
+def test_freezing_time_derivative(env):
+    """d t*/d T_w and d t*/d Ste of the time at which the frozen fraction of
+    a small droplet first reaches 0.9, against central differences of the
+    same interpolated time from FP64 runs."""
+    O, lbm, S, torch = env
+    cfg, arr, p0, wall, line = _droplet(32)
+    level = 0.9
+
+    def tstar(p):
+        c = S.apply_params(cfg, *p, wall)
+        s = lbm.Solver(c, precision="fp64").set_geometry(arr)
+        prev = None
+        for n in range(200000):
+            d = s.diagnostics(compute=True)
+            ff = d["frozen_volume"] / d["material_volume"]
+            if prev is not None and ff >= level:
+                s.close()
+                return (n - 1) + (level - prev) / (ff - prev)
+            prev = ff
+            s.step(1)
+        raise AssertionError("the droplet did not freeze")
+
+    for j, name in ((0, "T_w"), (2, "ste")):
+        t0, dt = S.freezing_time(cfg, arr, p0, wall, name, level=level)
+        h = (1e-6, None, 1e-7)[j]
+        pp, pm = list(p0), list(p0)
+        pp[j] += h
+        pm[j] -= h
+        fd = (tstar(pp) - tstar(pm)) / (2 * h)
+        print(f"\nt* = {t0:.3f}, dt*/d{name}: tangent {dt:.6f}, FD {fd:.6f}")
+        assert np.isfinite(t0) and t0 > 0
+        assert abs(dt - fd) <= 1e-3 * abs(fd), (name, dt, fd)
