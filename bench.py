@@ -85,8 +85,8 @@ def measured_peak():
 
 
 # the sources the step kernels are compiled from (host API and probes excluded)
-KERNEL_SOURCES = ("lbm_kernels.cuh", "lbm_step.cuh", "lbm_split.cuh", "lbm_launch.h",
-                  "lbm_f32.cu", "lbm_f64.cu")
+KERNEL_SOURCES = ("lbm_kernels.cuh", "lbm_dual.cuh", "lbm_step.cuh", "lbm_split.cuh",
+                  "lbm_launch.h", "lbm_f32.cu", "lbm_f64.cu", "lbm_f16.cu", "lbm_tan.cu")
 
 
 def kernel_source_hash() -> str:
