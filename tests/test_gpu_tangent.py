@@ -190,3 +190,34 @@ def test_freezing_time_derivative(env):
         print(f"\nt* = {t0:.3f}, dt*/d{name}: tangent {dt:.6f}, FD {fd:.6f}")
         assert np.isfinite(t0) and t0 > 0
         assert abs(dt - fd) <= 1e-3 * abs(fd), (name, dt, fd)
+
+
+@pytest.mark.slow
+def test_porous_medium_gradient_over_4000_steps(env):
+    """Freezing of gas-liquid flow in a porous medium (cold wall at x = 0,
+    Sec. 4.6 shape, here 1024 x 512): the frozen fraction after 4000 steps
+    and its derivatives with respect to the cold-wall temperature and the
+    contact angle, against central differences of the FP64 GPU step."""
+    O, lbm, S, torch = env
+    cfg, arr = W.porous(1024, 512, seed=0)
+    steps, wall, p0 = 4000, (0,), (-1.0, 60.0, 0.1)
+    val, J = S.value_and_jacobian(cfg, arr, steps, p0, wall, None)
+
+    def observe(p):
+        s = S.run(S.apply_params(cfg, *p, wall), arr, steps)
+        v = S.observables(s, None)
+        s.close()
+        return v
+
+    h = (1e-6, 1e-4, 1e-7)
+    fd = np.empty(3)
+    for j in (0, 1):
+        pp, pm = list(p0), list(p0)
+        pp[j] += h[j]
+        pm[j] -= h[j]
+        fd[j] = (observe(pp)[0] - observe(pm)[0]) / (2 * h[j])
+    print(f"\nFF = {val[0]:.6f}; dFF/dT_w tangent {J[0, 0]:.8f} FD {fd[0]:.8f}; "
+          f"dFF/dtheta tangent {J[0, 1]:.3e} FD {fd[1]:.3e}; dFF/dSte {J[0, 2]:.6f}")
+    assert val[0] > 0.0
+    assert abs(J[0, 0] - fd[0]) <= 1e-3 * abs(fd[0])
+    assert abs(J[0, 1] - fd[1]) <= 1e-3 * abs(fd[1]) + 1e-10
