@@ -283,6 +283,23 @@ int lbm_batch_step(lbm_batch* batch, int64_t nsteps, void* stream);
 /* Frees the batch (not the contexts; NULL is allowed). */
 void lbm_batch_destroy(lbm_batch* batch);
 
+/* Autotuner (the paper gives no implementation; a measuring aid of this
+ * library): times the step forms this build has on the context's own grid
+ * and state and keeps the fastest for later lbm_step calls.  Variants, in
+ * this order: the fused one-kernel step with captured periods of at least
+ * 32 steps, the same with at least 256, and (LBM_FP32 and LBM_FP64 only)
+ * the two-kernel split with 32 and with 256.  Each variant runs
+ * steps_per_trial steps twice from the same saved state (the first run
+ * warms up and captures; the second is timed with CUDA events on `stream`).
+ * The state, step counter and diagnostics are restored afterwards, so the
+ * call does not advance the simulation.  out_us (4 doubles, may be NULL):
+ * microseconds per step of each variant (-1 where not run); chosen (may be
+ * NULL): the index kept.  Allocates a backup of the state (27 population
+ * and 6 lag planes) for the duration of the call and synchronises `stream`.
+ * Errors: LBM_ERR_ARG (steps_per_trial < 2), LBM_ERR_STATE before
+ * lbm_set_geometry, LBM_ERR_OOM/LBM_ERR_CUDA. */
+int lbm_autotune(lbm_ctx* ctx, int steps_per_trial, void* stream, double* out_us, int* chosen);
+
 /* Largest grid lbm_diagnostics_noalloc accepts, in tiles of 32 x 8 nodes
  * (4096 tiles = 1,048,576 nodes, e.g. 1024 x 1024). */
 #define LBM_NOALLOC_MAX_BLOCKS 4096

@@ -62,6 +62,8 @@ struct lbm_ctx {
   int64_t graph_phase;   // step index modulo the period it starts from
   uint64_t gen;          // bumped when geometry or state is replaced
   uint64_t graph_gen;
+  int graph_min;         // shortest captured period (32; lbm_autotune may change it)
+  int graph_len;         // steps in the captured graph
   char err[512];
 };
 
@@ -143,9 +145,9 @@ cudaError_t launch(lbm_ctx* c, int mode, bool diag, double* const* outs, cudaStr
 // and the diagnostic schedule every diag_every steps; short periods are
 // repeated up to at least 32 steps so that one graph launch covers many
 // kernels.
-int graph_period(int diag_every) {
+int graph_period(int diag_every, int min_steps = 32) {
   const int base = diag_every <= 0 ? 2 : (diag_every % 2 == 0 ? diag_every : 2 * diag_every);
-  return base >= 32 ? base : base * ((32 + base - 1) / base);
+  return base >= min_steps ? base : base * ((min_steps + base - 1) / base);
 }
 constexpr int kMaxGraphSteps = 256;
 
@@ -188,7 +190,8 @@ cudaError_t step_launches(lbm_ctx* c, int64_t nsteps, cudaStream_t s) {
 // phase, captured on a private stream the first time it is needed.
 cudaError_t step_graph(lbm_ctx* c, int period, cudaGraphExec_t* out) {
   const int64_t phase = c->step % period;
-  if (c->graph && c->graph_cur == c->cur && c->graph_phase == phase && c->graph_gen == c->gen) {
+  if (c->graph && c->graph_cur == c->cur && c->graph_phase == phase && c->graph_gen == c->gen &&
+      c->graph_len == period) {
     *out = c->graph;
     return cudaSuccess;
   }
@@ -226,6 +229,7 @@ cudaError_t step_graph(lbm_ctx* c, int period, cudaGraphExec_t* out) {
   c->graph_cur = cur;
   c->graph_phase = phase;
   c->graph_gen = c->gen;
+  c->graph_len = period;
   *out = c->graph;
   return cudaSuccess;
 }
@@ -291,6 +295,7 @@ int lbm_create(const lbm_params* params, lbm_ctx** out) {
     // replaying captured periods
     const char* gr = std::getenv("LBM_STEP_GRAPHS");
     c->graphs = !(gr && std::strcmp(gr, "0") == 0);
+    c->graph_min = 32;
   }
   c->cf = lbmh::make_coef<float>(*params);
   c->cd = lbmh::make_coef<double>(*params);
@@ -419,7 +424,7 @@ int lbm_step(lbm_ctx* c, int64_t nsteps, void* stream) {
   if (!c->have_geometry) return fail(c, LBM_ERR_STATE, "lbm_step before lbm_set_geometry%s");
   cudaStream_t s = (cudaStream_t)stream;
   int64_t left = nsteps;
-  const int period = graph_period(c->p.diag_every);
+  const int period = graph_period(c->p.diag_every, c->graph_min);
   if (c->graphs && period <= kMaxGraphSteps && left >= period && stream_free(s)) {
     // whole periods replay one captured graph (same kernels, same order)
     cudaGraphExec_t g = nullptr;
@@ -677,6 +682,93 @@ int lbm_load_state(lbm_ctx* c, const void* host_buf, size_t size, void* stream) 
 }  // extern "C"
 
 // ---------------------------------------------------------------------------
+// autotuning of the step form on the context's own grid
+// ---------------------------------------------------------------------------
+
+extern "C" int lbm_autotune(lbm_ctx* c, int steps_per_trial, void* stream, double* out_us,
+                            int* chosen) {
+  if (!c) return LBM_ERR_ARG;
+  if (steps_per_trial < 2) return fail(c, LBM_ERR_ARG, "steps_per_trial must be >= 2%s");
+  if (!c->have_geometry) return fail(c, LBM_ERR_STATE, "autotune before lbm_set_geometry%s");
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t P = (size_t)c->g.plane;
+  const size_t pb = 27 * P * c->pop_esize, lb = lbmk::NLAG * P * c->esize;
+  void* backup = nullptr;
+  cudaError_t e = cudaMalloc(&backup, pb + lb);
+  if (e != cudaSuccess) return cuda_fail(c, e, "autotune backup allocation");
+  // the state the trials start from, and the host-side step bookkeeping
+  const int cur = c->cur;
+  const int64_t step = c->step, diag_step = c->diag_step;
+  const bool have_diag = c->have_diag, pending = c->diag_pending;
+  const bool split0 = c->split, graphs0 = c->graphs;
+  const int gmin0 = c->graph_min;
+  e = cudaMemcpyAsync(backup, c->pop[cur], pb, cudaMemcpyDeviceToDevice, s);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync((char*)backup + pb, c->lag[cur], lb, cudaMemcpyDeviceToDevice, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  // variants: kernel form (fused, split) x shortest captured period (32, 256)
+  const bool split_ok = c->p.precision == LBM_FP32 || c->p.precision == LBM_FP64;
+  double us[4] = {-1.0, -1.0, -1.0, -1.0};
+  cudaEvent_t t0 = nullptr, t1 = nullptr;
+  if (e == cudaSuccess) e = cudaEventCreate(&t0);
+  if (e == cudaSuccess) e = cudaEventCreate(&t1);
+  for (int v = 0; v < 4 && e == cudaSuccess; v++) {
+    if (v >= 2 && !split_ok) break;
+    c->split = v >= 2;
+    c->graphs = graphs0;
+    c->graph_min = (v & 1) ? 256 : 32;
+    c->gen++;  // another kernel form: nothing captured before applies
+    for (int rep = 0; rep < 2 && e == cudaSuccess; rep++) {  // rep 0 warms up and captures
+      e = cudaMemcpyAsync(c->pop[cur], backup, pb, cudaMemcpyDeviceToDevice, s);
+      if (e == cudaSuccess)
+        e = cudaMemcpyAsync(c->lag[cur], (char*)backup + pb, lb, cudaMemcpyDeviceToDevice, s);
+      c->cur = cur;
+      c->step = step;
+      if (e != cudaSuccess) break;
+      e = cudaEventRecord(t0, s);
+      if (e == cudaSuccess && lbm_step(c, steps_per_trial, s) != LBM_OK) e = cudaErrorUnknown;
+      if (e == cudaSuccess) e = cudaEventRecord(t1, s);
+      if (e == cudaSuccess) e = cudaEventSynchronize(t1);
+      float ms = 0.f;
+      if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, t0, t1);
+      if (e == cudaSuccess && rep == 1) us[v] = 1e3 * ms / steps_per_trial;
+    }
+  }
+  int best = 0;
+  for (int v = 1; v < 4; v++)
+    if (us[v] > 0.0 && us[v] < us[best]) best = v;
+  // restore the state, keep the fastest variant
+  cudaError_t er = cudaMemcpyAsync(c->pop[cur], backup, pb, cudaMemcpyDeviceToDevice, s);
+  if (er == cudaSuccess)
+    er = cudaMemcpyAsync(c->lag[cur], (char*)backup + pb, lb, cudaMemcpyDeviceToDevice, s);
+  if (er == cudaSuccess) er = cudaStreamSynchronize(s);
+  c->cur = cur;
+  c->step = step;
+  c->diag_step = diag_step;
+  c->have_diag = have_diag;
+  c->diag_pending = pending;
+  c->gen++;
+  c->graphs = graphs0;
+  if (e == cudaSuccess && er == cudaSuccess) {
+    c->split = best >= 2;
+    c->graph_min = (best & 1) ? 256 : 32;
+  } else {
+    c->split = split0;
+    c->graph_min = gmin0;
+  }
+  if (t0) cudaEventDestroy(t0);
+  if (t1) cudaEventDestroy(t1);
+  cudaFree(backup);
+  if (e != cudaSuccess) return cuda_fail(c, e, "autotune trial");
+  if (er != cudaSuccess) return cuda_fail(c, er, "autotune restore");
+  if (out_us)
+    for (int v = 0; v < 4; v++) out_us[v] = us[v];
+  if (chosen) *chosen = best;
+  c->last_stream = s;
+  return LBM_OK;
+}
+
+// ---------------------------------------------------------------------------
 // batches: several contexts advanced by one persistent launch per step
 // ---------------------------------------------------------------------------
 
@@ -761,6 +853,7 @@ std::vector<uint64_t> batch_key(const lbm_batch* b, int period) {
     k.push_back(c->gen);
   }
   k.push_back((uint64_t)(b->ctx[0]->step % period));
+  k.push_back((uint64_t)period);
   return k;
 }
 
@@ -822,7 +915,7 @@ int batch_step_impl(lbm_batch* b, int64_t nsteps, cudaStream_t s) {
   if (!t) return LBM_ERR_OOM;
   lbm_ctx* c0 = b->ctx[0];
   int64_t left = nsteps;
-  const int period = graph_period(c0->p.diag_every);
+  const int period = graph_period(c0->p.diag_every, c0->graph_min);
   cudaError_t e = cudaSuccess;
   if (c0->graphs && period <= kMaxGraphSteps && left >= period && stream_free(s)) {
     cudaGraphExec_t g = nullptr;

@@ -60,7 +60,7 @@ EXPORTS = ("lbm_create", "lbm_set_geometry", "lbm_step", "lbm_read_fields",
            "lbm_status_string", "lbm_destroy", "lbm_diagnostics_noalloc",
            "lbm_batch_create", "lbm_batch_step", "lbm_batch_destroy", "lbm_probe_fma_rate",
            "lbm_read_crossings", "lbm_read_tangent_fields", "lbm_read_tangent_diagnostics",
-           "lbm_read_crossings_tangent")
+           "lbm_read_crossings_tangent", "lbm_autotune")
 
 _lib = None
 
@@ -102,12 +102,13 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     L.lbm_read_crossings_tangent.argtypes = [vp, ctypes.c_int, ctypes.c_int, dp, vp]
     L.lbm_read_tangent_fields.argtypes = [vp, ctypes.c_uint32, ctypes.POINTER(vp), ctypes.c_int, vp]
     L.lbm_read_tangent_diagnostics.argtypes = [vp, ctypes.POINTER(LbmDiag)]
+    L.lbm_autotune.argtypes = [vp, ctypes.c_int, vp, dp, ctypes.POINTER(ctypes.c_int)]
     for fn in ("lbm_create", "lbm_set_geometry", "lbm_step", "lbm_read_fields",
                "lbm_compute_diagnostics", "lbm_read_diagnostics", "lbm_state_size",
                "lbm_save_state", "lbm_load_state", "lbm_diagnostics_noalloc",
                "lbm_batch_create", "lbm_batch_step", "lbm_probe_fma_rate",
                "lbm_read_crossings", "lbm_read_crossings_tangent", "lbm_read_tangent_fields",
-               "lbm_read_tangent_diagnostics"):
+               "lbm_read_tangent_diagnostics", "lbm_autotune"):
         getattr(L, fn).restype = ctypes.c_int
     _lib = L
     return L
@@ -191,8 +192,21 @@ def lbm_read_crossings_tangent(ctx, axis: int, index: int, stream=None):
     """(phi = 0 crossing, ice front, their derivatives) along one line."""
     out = (ctypes.c_double * 4)()
     _check(ctx, load().lbm_read_crossings_tangent(ctx, int(axis), int(index), out, stream),
-           "lbm_read_crossings_tangent")
+           "lbm_read_crossings_tangent", "lbm_autotune")
     return tuple(out)
+
+
+VARIANTS = ("fused, periods >= 32", "fused, periods >= 256", "split, periods >= 32",
+            "split, periods >= 256")
+
+
+def lbm_autotune(ctx, steps_per_trial: int = 64, stream=None):
+    """(microseconds per step of each variant, index kept); see include/lbm.h."""
+    us = (ctypes.c_double * 4)()
+    chosen = ctypes.c_int()
+    _check(ctx, load().lbm_autotune(ctx, int(steps_per_trial), stream, us, ctypes.byref(chosen)),
+           "lbm_autotune")
+    return list(us), chosen.value
 
 
 def lbm_compute_diagnostics(ctx, stream=None):
@@ -352,6 +366,10 @@ class Solver:
     def crossings(self, axis: int, index: int):
         """Interface positions along one line (see lbm_read_crossings)."""
         return lbm_read_crossings(self.ctx, axis, index, _stream())
+
+    def autotune(self, steps_per_trial: int = 64):
+        """Pick the fastest step form for this grid (state unchanged)."""
+        return lbm_autotune(self.ctx, steps_per_trial, _stream())
 
     def crossings_tangent(self, axis: int, index: int):
         """Crossings and their derivatives (tangent contexts)."""

@@ -393,3 +393,26 @@ def test_batch_captured_periods_match_single_launches(env):
         assert x.diagnostics(compute=False) == y.diagnostics(compute=False)
     ba.close()
     bb.close()
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp16s"])
+def test_autotune_keeps_the_state_and_picks_a_variant(env, prec):
+    """lbm_autotune times the step forms on the context's own state, restores
+    that state bit for bit, and the context then steps on as before (FP32:
+    within the parity bar of the oracle whichever form it kept)."""
+    O, lbm = env
+    cfg, arr = W.random_state(96, 40, seed=33)
+    s = lbm.Solver(cfg, precision=prec, diag_every=4).set_geometry(arr).step(5)
+    before = s.fields()
+    us, chosen = s.autotune(40)
+    after = s.fields()
+    for k in FIELDS:
+        assert np.array_equal(before[k], after[k]), k
+    assert s.steps_done == 5
+    n_variants = 4 if prec == "fp32" else 2
+    assert all(u > 0 for u in us[:n_variants]) and all(u == -1.0 for u in us[n_variants:])
+    assert 0 <= chosen < n_variants and us[chosen] == min(us[:n_variants])
+    s.step(40)
+    if prec == "fp32":
+        _compare(s.fields(), O.from_workload((cfg, arr)).step(45).fields(), prec)
+    s.close()
