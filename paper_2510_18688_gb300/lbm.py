@@ -192,7 +192,7 @@ def lbm_read_crossings_tangent(ctx, axis: int, index: int, stream=None):
     """(phi = 0 crossing, ice front, their derivatives) along one line."""
     out = (ctypes.c_double * 4)()
     _check(ctx, load().lbm_read_crossings_tangent(ctx, int(axis), int(index), out, stream),
-           "lbm_read_crossings_tangent", "lbm_autotune")
+           "lbm_read_crossings_tangent")
     return tuple(out)
 
 
