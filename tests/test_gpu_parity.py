@@ -416,3 +416,34 @@ def test_autotune_keeps_the_state_and_picks_a_variant(env, prec):
     if prec == "fp32":
         _compare(s.fields(), O.from_workload((cfg, arr)).step(45).fields(), prec)
     s.close()
+
+
+@pytest.mark.slow
+def test_droplet_on_a_cylinder_reaches_the_closed_form_height(env):
+    """P8 (Sec. 4.4, Eq. (37)): a drop of radius R0 = 50 placed on a cylinder
+    of radius Rs = 50 (300 x 300, sigma = 0.001, M = 0.1, no heat) spreads
+    to the equilibrium whose top lies at H_max = k + R from the cylinder axis,
+    with R and k fixed by the contact angle and the drop's area.  At 90
+    degrees the FP32 path reaches H_max within 2 % after 200,000 steps (the
+    contact line creeps: -9 % at 5,000 steps, -3 % at 100,000).  Larger angles
+    on the curved solid are not stable with the model as read (theta >= 105
+    degrees diverges after 30,000-50,000 steps, identically in FP32 and FP64),
+    so they are not part of this pin."""
+    import closed_forms as CF
+    O, lbm = env
+    L, Rs, R0, eps, theta = 300, 50.0, 50.0, 4.0, 90.0
+    cfg = W.base_params(L, L, lattices=W.FLOW | W.PHASE, theta_deg=theta, sigma=0.001,
+                        mobility=0.1, bc=("periodic", "periodic", "periodic", "periodic"))
+    X, Y = np.meshgrid(np.arange(L) + 0.5, np.arange(L) + 0.5)
+    cx, cy = L / 2, 0.35 * L
+    phi0 = 0.5 + 0.5 * np.tanh(2 * (Rs - np.hypot(X - cx, Y - cy)) / eps)
+    phi = (1 - phi0) * np.tanh(2 * (R0 - np.hypot(X - cx, Y - (cy + Rs))) / eps)
+    z = np.zeros((L, L))
+    s = lbm.Solver(cfg, precision="fp32").set_geometry(
+        {"phi0": phi0, "phi": phi, "T": z + 0.5, "fl": z + 1.0})
+    s.step(200000)
+    H = s.crossings(1, int(cx))[0] + 0.5 - cy
+    _, _, H_eq = CF.cylinder_droplet_equilibrium(R0, Rs, theta)
+    print(f"\nH_max {H:.2f}, closed form {H_eq:.2f}")
+    assert abs(H - H_eq) <= 0.02 * H_eq
+    s.close()
