@@ -161,8 +161,8 @@ __device__ __forceinline__ void collide_heat(const Geom& g, const Coef<R>& c, S*
                                              R T, R rhoH, R mdot, const Macro<R>& M, R rest0) {
   const R lam = interp(fs, w, c.lam_s, c.lam_l, c.lam_g);
   const R taua = R(0.5) + qdiv(lam, c.rr3);
-  const R taus = qdiv(taua, R(2) * taua - R(1));
-  const R ia = qdiv(R(1), taua), is = qdiv(R(1), taus);
+  // magic relation of the TRT (Eq. (27)): 1/tau_s + 1/tau_a = 2
+  const R ia = qdiv(R(1), taua), is = R(2) - ia;
   const R hcoef = R(1) - R(0.5) * ia;
   const R CT = M.cap * T;
   const R Hsrc = hcoef * CT * mdot;
@@ -422,7 +422,8 @@ __device__ __forceinline__ void step_tile(const Args<R, S>& a, int bx, int by, i
       const R jy = (f[2] - f[4]) + (f[5] + f[6]) - (f[7] + f[8]);
       const R snz = (f[1] + f[2] + f[3] + f[4]) + (f[5] + f[6] + f[7] + f[8]);
       // Eq. (17a,b) with the penalty force f = fs (u_s - u*), u_s = 0
-      const R usx = qdiv(jx + R(0.5) * Fx, rho), usy = qdiv(jy + R(0.5) * Fy, rho);
+      const R irho = qdiv(R(1), rho);
+      const R usx = (jx + R(0.5) * Fx) * irho, usy = (jy + R(0.5) * Fy) * irho;
       const R fpx = -fs * usx, fpy = -fs * usy;
       M.ux = usx + R(0.5) * fpx;
       M.uy = usy + R(0.5) * fpy;
@@ -432,7 +433,7 @@ __device__ __forceinline__ void step_tile(const Args<R, S>& a, int bx, int by, i
       M.Ftx = Fx - (gpx - grx * R(1.0 / 3.0));
       M.Fty = Fy - (gpy - gry * R(1.0 / 3.0));
       M.uFt = M.ux * M.Ftx + M.uy * M.Fty;
-      M.tauf = qdiv(mu, rho * R(1.0 / 3.0)) + R(0.5);
+      M.tauf = R(3) * mu * irho + R(0.5);
       M.Gx = Fx + rho * fpx;
       M.Gy = Fy + rho * fpy;
       // F_0 of Eq. (16)
