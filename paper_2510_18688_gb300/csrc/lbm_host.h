@@ -42,6 +42,7 @@ inline Coef<R> make_coef(const lbm_params& p) {
   c.s9 = (R)(9.0 * p.sigma / p.eps);
   c.klap = (R)(3.0 * p.eps * p.sigma / 8.0);
   c.rr3 = (R)(p.rho_ref * (2.0 * p.cp_s * p.cp_l / (p.cp_s + p.cp_l)) / 3.0);
+  c.inv_rr3 = (R)(3.0 / (p.rho_ref * (2.0 * p.cp_s * p.cp_l / (p.cp_s + p.cp_l))));
   c.inv_tau_g = (R)(1.0 / (0.5 + p.mobility / (p.eta / 3.0)));
   c.readings = p.readings;
   return c;

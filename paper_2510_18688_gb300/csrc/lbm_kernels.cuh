@@ -84,6 +84,7 @@ struct Coef {
   R s3, s9;      // 3 sigma / eps, 9 sigma / eps (Eq. (6))
   R klap;        // 3 eps sigma / 8 (Eq. (6))
   R rr3;         // rho_ref Cp_ref cs^2 (Eq. (26))
+  R inv_rr3;     // 1 / rr3
   R inv_tau_g;   // 1 / tau_g
   uint32_t readings;
 };
@@ -268,7 +269,14 @@ __device__ __forceinline__ Local<R> local_state(const Coef<R>& c, int lat, R sg,
     L.mdot = c.one_m_ratio * wp * (flp - L.fl);  // Eq. (1), phase-change part
   }
   if (lat & LAT_PHASE) {
-    L.phi = qdiv(sg, R(1) - R(0.5) * L.mdot);  // Eq. (22) solved for phi
+    // Eq. (22) solved for phi.  Without phase change the divisor is exactly
+    // 1, and the FP64 step (bound by its FP64 pipe, where a division costs
+    // about ten operations) skips it; a tangent still divides (the
+    // derivative of mdot need not vanish), and float division is cheap.
+    if constexpr (std::is_same<R, double>::value)
+      L.phi = L.mdot == R(0) ? sg : qdiv(sg, R(1) - R(0.5) * L.mdot);
+    else
+      L.phi = qdiv(sg, R(1) - R(0.5) * L.mdot);
     L.w = clamp01((R(1) - phi0 + L.phi) * R(0.5));
   } else {
     L.w = wp;

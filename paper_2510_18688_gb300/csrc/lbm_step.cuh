@@ -160,7 +160,7 @@ __device__ __forceinline__ void collide_heat(const Geom& g, const Coef<R>& c, S*
                                              int P, int x, int y, int n, const R* h, R fs, R w,
                                              R T, R rhoH, R mdot, const Macro<R>& M, R rest0) {
   const R lam = interp(fs, w, c.lam_s, c.lam_l, c.lam_g);
-  const R taua = R(0.5) + qdiv(lam, c.rr3);
+  const R taua = R(0.5) + lam * c.inv_rr3;
   // magic relation of the TRT (Eq. (27)): 1/tau_s + 1/tau_a = 2
   const R ia = qdiv(R(1), taua), is = R(2) - ia;
   const R hcoef = R(1) - R(0.5) * ia;
