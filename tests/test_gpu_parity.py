@@ -447,3 +447,26 @@ def test_droplet_on_a_cylinder_reaches_the_closed_form_height(env):
     print(f"\nH_max {H:.2f}, closed form {H_eq:.2f}")
     assert abs(H - H_eq) <= 0.02 * H_eq
     s.close()
+
+
+@pytest.mark.slow
+def test_stefan_column_fp32_full_run(env):
+    """The three-phase Stefan column (512 x 8) for the full 50,000 steps, FP32
+    against the FP64 oracle: the gas-liquid interface and the ice front
+    (crossings along a row) within 0.5 % of the column's liquid height, the
+    state fields within 1e-3 relative L2."""
+    O, lbm = env
+    cfg, arr = W.stefan()
+    steps = 50000
+    ref = O.from_workload((cfg, arr)).step(steps).fields()
+    s = lbm.Solver(cfg, precision="fp32").set_geometry(arr).step(steps)
+    got = s.fields()
+    errs = {k: _l2_rel(got[k], ref[k]) for k in ("phi", "fs", "fl", "T", "rhoH", "rho", "w")}
+    want = O.crossings(ref["phi"], ref["w"], ref["fl"], 0, 4)
+    have = s.crossings(0, 4)
+    print("\nfield errors", {k: f"{v:.1e}" for k, v in errs.items()}, "crossings", have, want)
+    column = 80.0 - 16.0  # liquid height h0 - hs of the workload
+    for g, w in zip(have, want):
+        assert abs(g - w) <= 0.005 * column, (have, want)
+    assert all(v <= 1e-3 for v in errs.values()), errs
+    s.close()

@@ -123,6 +123,32 @@ def test_precision_error_table(env, case):
         assert v <= F16_OBS[key][k], ("fp16s", k, v)
 
 
+def _freezing_time(lbm, cfg, arr, prec, level):
+    s = lbm.Solver(cfg, precision=prec).set_geometry(arr)
+    prev = None
+    for n in range(100000):
+        d = s.diagnostics(compute=True)
+        ff = d["frozen_volume"] / d["material_volume"]
+        if prev is not None and ff >= level:
+            s.close()
+            return (n - 1) + (level - prev) / (ff - prev)
+        prev = ff
+        s.step(1)
+    raise AssertionError("the droplet did not freeze")
+
+
+def test_freezing_time_in_each_precision(env):
+    """Freezing time (frozen fraction first reaching 0.9, interpolated
+    between steps) of a small droplet on a cold substrate: FP32 within 0.5 %
+    and FP16 storage within 2 % of FP64 (whose step matches the oracle)."""
+    O, lbm = env
+    cfg, arr = W.sessile_droplet(32, seed=3, radius=8.0, hs=3.2, theta_deg=80.0, ste=0.3)
+    t = {p: _freezing_time(lbm, cfg, arr, p, 0.9) for p in ("fp64", "fp32", "fp16s")}
+    print("\nfreezing time", t)
+    assert abs(t["fp32"] - t["fp64"]) <= 0.005 * t["fp64"]
+    assert abs(t["fp16s"] - t["fp64"]) <= 0.02 * t["fp64"]
+
+
 def test_fp16_storage_is_rejected_where_unsupported(env):
     O, lbm = env
     cfg, arr = W.random_state(40, 20, seed=3)
