@@ -470,3 +470,25 @@ def test_stefan_column_fp32_full_run(env):
         assert abs(g - w) <= 0.005 * column, (have, want)
     assert all(v <= 1e-3 for v in errs.values()), errs
     s.close()
+
+
+def test_batch64_full_size_sampled_grids(env):
+    """The benchmark's 64-grid batch (sides from {128, 256, 384, 512}, one
+    launch per step, captured periods) at full size: the smallest, a middle
+    and the largest grid compared with the oracle on every node after 40
+    steps (FP32 parity bar)."""
+    O, lbm = env
+    r = W.rng(1000)
+    sides = r.choice([128, 256, 384, 512], size=64)
+    wls = [W.cylinder_droplet(int(sd), seed=i) for i, sd in enumerate(sides)]
+    ss = [lbm.Solver(c, precision="fp32").set_geometry(a) for c, a in wls]
+    b = lbm.Batch(ss)
+    b.step(40)
+    order = np.argsort(sides, kind="stable")
+    for k in (order[0], order[31], order[-1]):
+        cfg, arr = wls[k]
+        ref = O.from_workload((cfg, arr)).step(40).fields()
+        _compare(ss[k].fields(), ref, "fp32")
+    b.close()
+    for s in ss:
+        s.close()
