@@ -283,6 +283,26 @@ int lbm_batch_step(lbm_batch* batch, int64_t nsteps, void* stream);
 /* Frees the batch (not the contexts; NULL is allowed). */
 void lbm_batch_destroy(lbm_batch* batch);
 
+/* Reverse mode (adjoint) of the enthalpy-lattice step, Eqs. (8), (23)-(28)
+ * with the fluid at rest: for a context with precision LBM_FP64, lattices ==
+ * LBM_LAT_HEAT and no cold mask (for example the conduction-freezing
+ * column of Sec. 4.1), advances the state by nsteps steps, as lbm_step
+ * would, and returns the frozen fraction FF = sum w (1 - fl) / sum w of the
+ * final state in *ff and its gradient in grad[0..4]: dFF/dT_wall[k] for the
+ * four walls (zero where bc[k] is not LBM_BC_DIRICHLET) and dFF/dlatent.
+ * The gradient comes from one reverse sweep of hand-written adjoint kernels
+ * (the transposed step: pull through the push and the wall rules, then back
+ * through the TRT collision and the enthalpy inversion, taking at its kinks
+ * the branch the forward step took).  The forward pass keeps every
+ * `every`-th state (checkpoints, 15 planes each); the sweep recomputes each
+ * segment of `every` steps from its checkpoint before stepping back through
+ * it, so memory is (nsteps / every + every) states.  Synchronises `stream`.
+ * Errors: LBM_ERR_ARG (null output, nsteps < 1, every < 1), LBM_ERR_STATE
+ * before lbm_set_geometry, LBM_ERR_UNSUPPORTED for other contexts,
+ * LBM_ERR_OOM/LBM_ERR_CUDA (the context's state is then undefined). */
+int lbm_adjoint_frozen_fraction(lbm_ctx* ctx, int64_t nsteps, int every, double* ff,
+                                double* grad, void* stream);
+
 /* Autotuner (the paper gives no implementation; a measuring aid of this
  * library): times the step forms this build has on the context's own grid
  * and state and keeps the fastest for later lbm_step calls.  Variants, in

@@ -1,6 +1,6 @@
 """Build the sm_103a shared library ``_lib/liblbm_gb300.so`` with nvcc.
 
-The translation units (host API, FP32, FP64, FP16-storage and tangent kernels, the
+The translation units (host API, FP32, FP64, FP16-storage, tangent and adjoint kernels, the
 allocation-free diagnostics, the FMA-rate probe) compile
 in parallel and link into one C-ABI library.  Both precisions keep fused
 multiply-add contraction: the FP64 step is bound by the FP64 pipe on this
@@ -27,6 +27,7 @@ UNITS = {
     "lbm_f64.cu": [],
     "lbm_f16.cu": [],
     "lbm_tan.cu": [],
+    "lbm_adjoint.cu": [],
     "lbm_static.cu": [],
     "lbm_probe.cu": [],
 }

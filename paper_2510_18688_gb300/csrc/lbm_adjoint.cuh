@@ -1,0 +1,265 @@
+// lbm_adjoint.cuh -- hand-written reverse-mode (adjoint) kernels of the
+// enthalpy-lattice step (contexts whose only lattice is LAT_HEAT, FP64, no
+// cold mask).
+//
+// With the enthalpy lattice alone the fluid is at rest (u = 0) and the step
+// at one node is local: rho H = sum h + Q_prev / 2 (Eq. (28)), the
+// inversion to T and fl (Eq. (8)), the mass source mdot (Eq. (1)), the solid
+// fraction and the properties (Eq. (10)), the TRT collision (Eqs. (23)-(27))
+// and the push with anti-bounce-back (T_wall) or bounce-back walls.  The
+// adjoint kernel runs these in reverse for one step: it pulls the adjoint
+// of the next state's populations from the nodes the post-collision
+// populations were pushed to (through the walls where they bounced), and
+// propagates it back through the collision and the inversion to the
+// adjoint of this state's populations and lag fields.  Derivatives with
+// respect to the wall temperatures (at anti-bounce-back links) and to the
+// latent heat L (through the latent capacity w rho_l L of Eq. (8)) are
+// accumulated per node, and summed once at the end in a fixed order.
+#pragma once
+
+#include "lbm_kernels.cuh"
+
+namespace lbmk {
+
+// accumulator planes: d/dT_wall[0..3], d/dlatent
+constexpr int ADJ_NACC = 5;
+
+struct AdjArgs {
+  Geom g;
+  Coef<double> c;
+  const double* __restrict__ h;      // 9 enthalpy planes of the forward state
+  const double* __restrict__ lag;    // NLAG lag planes of the forward state
+  const double* __restrict__ phi0;
+  const double* __restrict__ lam_in;  // adjoint of the next state's 9 planes
+  const double* __restrict__ lfl_in;  // adjoint of the next state's lag fl
+  const double* __restrict__ lq_in;   // adjoint of the next state's lag Q
+  double* __restrict__ lam_out;       // adjoint of this state's 9 planes
+  double* __restrict__ lfl_out;
+  double* __restrict__ lq_out;
+  double* __restrict__ acc;           // ADJ_NACC accumulator planes (+=)
+  double inv_sum_w;                   // seed only: 1 / sum w
+};
+
+// Forward quantities of one node that the reverse pass needs.
+struct HeatNode {
+  double rhoH, T, fl, mdot, fs, fs_raw, C, ia, is, hcoef, CT, ell, Cm, Cp;
+  int branch;  // 0: frozen (rhoH < 0), 1: liquid (rhoH > ell), 2: mushy
+};
+
+__device__ __forceinline__ HeatNode heat_forward(const Coef<double>& c, double sh, double flp,
+                                                 double wp, double Qp, double phi0) {
+  HeatNode q;
+  q.rhoH = sh + 0.5 * Qp;
+  q.ell = wp * c.rho_l * c.latent;
+  double fsf = phi0 + wp;
+  fsf = fsf > 1.0 ? 1.0 : fsf;
+  q.Cm = heat_cap(c, fsf, wp);
+  q.Cp = heat_cap(c, phi0, wp);
+  if (q.rhoH < 0.0) {
+    q.branch = 0;
+    q.fl = 0.0;
+    q.T = q.rhoH / q.Cm;
+  } else if (q.rhoH > q.ell) {
+    q.branch = 1;
+    q.fl = 1.0;
+    q.T = (q.rhoH - q.ell) / q.Cp;
+  } else {
+    q.branch = 2;
+    q.T = 0.0;
+    q.fl = q.ell > 0.0 ? q.rhoH / q.ell : 1.0;
+  }
+  q.mdot = c.one_m_ratio * wp * (flp - q.fl);
+  q.fs_raw = phi0 + wp * (1.0 - q.fl);
+  q.fs = q.fs_raw > 1.0 ? 1.0 : q.fs_raw;
+  q.C = heat_cap(c, q.fs, wp);
+  const double lam = interp(q.fs, wp, c.lam_s, c.lam_l, c.lam_g);
+  const double taua = 0.5 + lam * c.inv_rr3;
+  q.ia = 1.0 / taua;
+  q.is = 2.0 - q.ia;
+  q.hcoef = 1.0 - 0.5 * q.ia;
+  q.CT = q.C * q.T;
+  return q;
+}
+
+// Reverse of the inversion and of rho H = sum h + Q_prev / 2: from the
+// adjoints of T and fl to those of rho H (returned) and of L (added to *dL).
+__device__ __forceinline__ double heat_inversion_reverse(const Coef<double>& c, const HeatNode& q,
+                                                         double wp, double Tb, double flb,
+                                                         double* dL) {
+  double rhoHb = 0.0, ellb = 0.0;
+  if (q.branch == 0) {
+    rhoHb = Tb / q.Cm;
+  } else if (q.branch == 1) {
+    rhoHb = Tb / q.Cp;
+    ellb = -Tb / q.Cp;
+  } else if (q.ell > 0.0) {
+    rhoHb = flb / q.ell;
+    ellb = -flb * q.rhoH / (q.ell * q.ell);
+  }
+  *dL += ellb * wp * c.rho_l;
+  return rhoHb;
+}
+
+// Seed: adjoint of the frozen fraction FF = sum w (1 - fl) / sum w of a
+// state with respect to its populations, lag Q and L (lag fl: zero).
+static __global__ void __launch_bounds__(NT) lbm_adjoint_seed_kernel(const AdjArgs a) {
+  const Geom& g = a.g;
+  const int x = blockIdx.x * TX + threadIdx.x, y = blockIdx.y * TY + threadIdx.y;
+  if (x >= g.nx || y >= g.ny) return;
+  const int P = (int)g.plane;
+  const int n = y * g.pitch + x;
+  double h[9];
+#pragma unroll
+  for (int i = 0; i < 9; i++) h[i] = a.h[i * P + n];
+  const double wp = a.lag[LAG_W * P + n], flp = a.lag[LAG_FL * P + n];
+  const double Qp = a.lag[LAG_Q * P + n], phi0 = a.phi0[n];
+  const HeatNode q = heat_forward(a.c, sum_h(h), flp, wp, Qp, phi0);
+  double dL = 0.0;
+  const double rhoHb = heat_inversion_reverse(a.c, q, wp, 0.0, -wp * a.inv_sum_w, &dL);
+#pragma unroll
+  for (int i = 0; i < 9; i++) a.lam_out[i * P + n] = rhoHb;
+  a.lq_out[n] = 0.5 * rhoHb;
+  a.lfl_out[n] = 0.0;
+  a.acc[(ADJ_NACC - 1) * P + n] += dL;
+}
+
+// One step in reverse (see the header).
+static __global__ void __launch_bounds__(NT) lbm_adjoint_step_kernel(const AdjArgs a) {
+  const Geom& g = a.g;
+  const Coef<double>& c = a.c;
+  const int x = blockIdx.x * TX + threadIdx.x, y = blockIdx.y * TY + threadIdx.y;
+  if (x >= g.nx || y >= g.ny) return;
+  const int P = (int)g.plane;
+  const int n = y * g.pitch + x;
+  // adjoint of the post-collision populations: pull through the push
+  double hb_star[9];
+  double dTw[4] = {0.0, 0.0, 0.0, 0.0};
+#pragma unroll
+  for (int i = 0; i < 9; i++) {
+    int wall;
+    const long long t = stream_target(g, x, y, qx(i), qy(i), wall);
+    if (t >= 0) {
+      hb_star[i] = a.lam_in[i * P + (int)t];
+    } else {
+      const double lb = a.lam_in[qopp(i) * P + n];
+      if (g.bc[wall] == BC_DIRICHLET) {
+        hb_star[i] = -lb;
+        dTw[wall] += lb * 2.0 * qw<double>(i) * c.rr;
+      } else {
+        hb_star[i] = lb;
+      }
+    }
+  }
+  // forward recompute of this node
+  double h[9];
+#pragma unroll
+  for (int i = 0; i < 9; i++) h[i] = a.h[i * P + n];
+  const double wp = a.lag[LAG_W * P + n], flp = a.lag[LAG_FL * P + n];
+  const double Qp = a.lag[LAG_Q * P + n], phi0 = a.phi0[n];
+  const HeatNode q = heat_forward(c, sum_h(h), flp, wp, Qp, phi0);
+  const double rrT = c.rr * q.T;
+  const double Hsrc = q.hcoef * q.CT * q.mdot;
+
+  // reverse of the TRT collision (Eqs. (23)-(27), u = 0)
+  double hb[9];
+  double isb = 0.0, iab = 0.0, Hsrcb = 0.0, rrTb = 0.0, rhoHb = 0.0;
+  {
+    const double A0 = hb_star[0];
+    const double heq0 = q.rhoH - rrT + qw<double>(0) * rrT;
+    hb[0] = A0 * (1.0 - q.is);
+    const double heq0b = A0 * q.is;
+    isb += -A0 * (h[0] - heq0);
+    Hsrcb += qw<double>(0) * A0;
+    rhoHb += heq0b;
+    rrTb += (qw<double>(0) - 1.0) * heq0b;
+  }
+#pragma unroll
+  for (int i = 1; i <= 8; i++) {
+    if (i == 3 || i == 4 || i == 7 || i == 8) continue;
+    const int o = qopp(i);
+    const double wi = qw<double>(i);
+    const double es = wi * rrT;
+    const double hs = 0.5 * (h[i] + h[o]), ha = 0.5 * (h[i] - h[o]);
+    const double A = hb_star[i], B = hb_star[o];
+    const double Dab = -A + B, Dsb = -A - B;
+    double hib = A, hob = B;
+    const double hab = Dab * q.ia;
+    iab += Dab * ha;
+    const double hsb = Dsb * q.is;
+    rrTb += -Dsb * q.is * wi;
+    isb += Dsb * (hs - es);
+    Hsrcb += -wi * Dsb;
+    hib += 0.5 * hsb + 0.5 * hab;
+    hob += 0.5 * hsb - 0.5 * hab;
+    hb[i] = hib;
+    hb[o] = hob;
+  }
+  // sources and the lags written by this step
+  const double lflb_new = a.lfl_in[n], lqb_new = a.lq_in[n];
+  double hcoefb = Hsrcb * q.CT * q.mdot;
+  double CTb = Hsrcb * q.hcoef * q.mdot;
+  double mdotb = Hsrcb * q.hcoef * q.CT + lqb_new * q.C * q.T;
+  double Cb = lqb_new * q.T * q.mdot + CTb * q.T;
+  double Tb = c.rr * rrTb + lqb_new * q.C * q.mdot + CTb * q.C;
+  double flb = lflb_new;
+  // tau_a, tau_s from lambda(fs)
+  iab += -0.5 * hcoefb;
+  iab -= isb;
+  const double taua = 1.0 / q.ia;
+  const double tauab = -iab / (taua * taua);
+  const double lamb = tauab * c.inv_rr3;
+  const double dinterp_lam = c.lam_s - wp * c.lam_l - (1.0 - wp) * c.lam_g;
+  double fsb = lamb * dinterp_lam;
+  // C = rho(fs) cp(fs)
+  {
+    const double rho = interp(q.fs, wp, c.rho_s, c.rho_l, c.rho_g);
+    const double cp = interp(q.fs, wp, c.cp_s, c.cp_l, c.cp_g);
+    const double drho = c.rho_s - wp * c.rho_l - (1.0 - wp) * c.rho_g;
+    const double dcp = c.cp_s - wp * c.cp_l - (1.0 - wp) * c.cp_g;
+    fsb += Cb * (drho * cp + rho * dcp);
+  }
+  if (!(q.fs_raw > 1.0)) flb += -wp * fsb;  // the forward clamps only above 1
+  // mdot = (1 - rho_s / rho_l) w (fl_prev - fl)
+  const double flpb = c.one_m_ratio * wp * mdotb;
+  flb += -c.one_m_ratio * wp * mdotb;
+  double dL = 0.0;
+  rhoHb += heat_inversion_reverse(c, q, wp, Tb, flb, &dL);
+#pragma unroll
+  for (int i = 0; i < 9; i++) a.lam_out[i * P + n] = hb[i] + rhoHb;
+  a.lq_out[n] = 0.5 * rhoHb;
+  a.lfl_out[n] = flpb;
+#pragma unroll
+  for (int k = 0; k < 4; k++) a.acc[k * P + n] += dTw[k];
+  a.acc[(ADJ_NACC - 1) * P + n] += dL;
+}
+
+// Fixed-order sum of the accumulator planes over the grid (one CTA).
+static __global__ void __launch_bounds__(NT) lbm_adjoint_reduce_kernel(const double* __restrict__ acc,
+                                                                Geom g, double* __restrict__ out) {
+  __shared__ double s[ADJ_NACC][NT / 32];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int P = (int)g.plane;
+  double v[ADJ_NACC];
+#pragma unroll
+  for (int k = 0; k < ADJ_NACC; k++) v[k] = 0.0;
+  for (int y = 0; y < g.ny; y++)
+    for (int x = tid; x < g.nx; x += NT) {
+#pragma unroll
+      for (int k = 0; k < ADJ_NACC; k++) v[k] += acc[k * P + y * g.pitch + x];
+    }
+#pragma unroll
+  for (int k = 0; k < ADJ_NACC; k++) {
+    double w = v[k];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) w += __shfl_xor_sync(0xffffffffu, w, o);
+    if (lane == 0) s[k][warp] = w;
+  }
+  __syncthreads();
+  if (tid < ADJ_NACC) {
+    double t = 0.0;
+    for (int w = 0; w < NT / 32; w++) t += s[tid][w];
+    out[tid] = t;
+  }
+}
+
+}  // namespace lbmk

@@ -19,6 +19,7 @@
 
 #include "../../include/lbm.h"
 #include "lbm_host.h"
+#include "lbm_adjoint.cuh"
 #include "lbm_launch.h"
 
 using lbmk::Args;
@@ -680,6 +681,144 @@ int lbm_load_state(lbm_ctx* c, const void* host_buf, size_t size, void* stream) 
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// reverse mode: frozen fraction of an enthalpy-lattice run and its gradient
+// ---------------------------------------------------------------------------
+
+extern "C" int lbm_adjoint_frozen_fraction(lbm_ctx* c, int64_t nsteps, int every, double* ff_out,
+                                           double* grad, void* stream) {
+  if (!c) return LBM_ERR_ARG;
+  if (!ff_out || !grad) return fail(c, LBM_ERR_ARG, "null output%s");
+  if (nsteps < 1 || every < 1) return fail(c, LBM_ERR_ARG, "nsteps and the checkpoint interval must be >= 1%s");
+  if (!c->have_geometry) return fail(c, LBM_ERR_STATE, "adjoint before lbm_set_geometry%s");
+  if (c->p.precision != LBM_FP64 || c->p.lattices != LBM_LAT_HEAT || c->g.has_mask)
+    return fail(c, LBM_ERR_UNSUPPORTED,
+                "the adjoint covers FP64 contexts with the enthalpy lattice alone and no cold mask%s");
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t P = (size_t)c->g.plane;
+  const size_t hN = 9 * P, lN = lbmk::NLAG * P, stN = hN + lN;  // doubles per stored state
+  const int64_t nck = (nsteps + every - 1) / every;
+  const int64_t seglen = std::min<int64_t>(every, nsteps);
+  double *ck = nullptr, *seg = nullptr, *lam = nullptr, *acc = nullptr, *dout = nullptr, *fin = nullptr;
+  cudaError_t e = cudaMalloc(&ck, nck * stN * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&seg, seglen * stN * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&lam, 2 * (9 + 2) * P * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&acc, lbmk::ADJ_NACC * P * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&dout, lbmk::ADJ_NACC * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&fin, (27 + lbmk::NLAG) * P * sizeof(double));
+  auto release = [&]() {
+    for (double* p : {ck, seg, lam, acc, dout, fin})
+      if (p) cudaFree(p);
+  };
+  if (e != cudaSuccess) {
+    release();
+    return cuda_fail(c, e, "adjoint allocation");
+  }
+  auto hplanes = [&](int par) { return (double*)c->pop[par] + 18 * P; };
+  auto save = [&](double* dst) {
+    cudaError_t r = cudaMemcpyAsync(dst, hplanes(c->cur), hN * sizeof(double),
+                                    cudaMemcpyDeviceToDevice, s);
+    if (r == cudaSuccess)
+      r = cudaMemcpyAsync(dst + hN, c->lag[c->cur], lN * sizeof(double), cudaMemcpyDeviceToDevice, s);
+    return r;
+  };
+  int st = LBM_OK;
+  const int64_t step0 = c->step;
+  std::vector<int> ckpar((size_t)nck);
+  // forward, keeping every `every`-th state
+  for (int64_t k = 0; k < nsteps && e == cudaSuccess && st == LBM_OK; k++) {
+    if (k % every == 0) {
+      ckpar[(size_t)(k / every)] = c->cur;
+      e = save(ck + (k / every) * stN);
+    }
+    if (e == cudaSuccess) st = lbm_step(c, 1, s);
+  }
+  double ffv = 0.0, inv_sum_w = 0.0;
+  if (e == cudaSuccess && st == LBM_OK) st = lbm_compute_diagnostics(c, s);
+  if (e == cudaSuccess && st == LBM_OK) {
+    lbm_diag d;
+    st = lbm_read_diagnostics(c, &d);
+    if (st == LBM_OK) {
+      ffv = d.frozen_volume / d.material_volume;
+      inv_sum_w = 1.0 / d.material_volume;
+    }
+  }
+  const int parN = c->cur;
+  if (e == cudaSuccess && st == LBM_OK)
+    e = cudaMemcpyAsync(fin, c->pop[parN], 27 * P * sizeof(double), cudaMemcpyDeviceToDevice, s);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(fin + 27 * P, c->lag[parN], lN * sizeof(double), cudaMemcpyDeviceToDevice, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(acc, 0, lbmk::ADJ_NACC * P * sizeof(double), s);
+  // adjoint buffers: two sets of (9 population planes, lag fl, lag Q)
+  double* lb[2] = {lam, lam + (9 + 2) * P};
+  lbmk::AdjArgs a;
+  std::memset(&a, 0, sizeof(a));
+  a.g = c->g;
+  a.c = c->cd;
+  a.phi0 = (const double*)c->phi0;
+  a.acc = acc;
+  a.inv_sum_w = inv_sum_w;
+  int cur_adj = 0;
+  if (e == cudaSuccess && st == LBM_OK) {
+    a.h = hplanes(parN);
+    a.lag = (const double*)c->lag[parN];
+    a.lam_out = lb[0];
+    a.lfl_out = lb[0] + 9 * P;
+    a.lq_out = lb[0] + 10 * P;
+    e = lbmk::launch_adjoint_seed(a, s);
+  }
+  // reverse sweep: recompute each segment from its checkpoint, then step back
+  for (int64_t sg = nck - 1; sg >= 0 && e == cudaSuccess && st == LBM_OK; sg--) {
+    const int64_t k0 = sg * every, k1 = std::min<int64_t>(k0 + every, nsteps);
+    const int par = ckpar[(size_t)sg];
+    e = cudaMemcpyAsync(hplanes(par), ck + sg * stN, hN * sizeof(double),
+                        cudaMemcpyDeviceToDevice, s);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(c->lag[par], ck + sg * stN + hN, lN * sizeof(double),
+                          cudaMemcpyDeviceToDevice, s);
+    c->cur = par;
+    c->step = step0 + k0;
+    c->gen++;
+    for (int64_t j = 0; j < k1 - k0 && e == cudaSuccess && st == LBM_OK; j++) {
+      e = save(seg + j * stN);
+      if (e == cudaSuccess) st = lbm_step(c, 1, s);
+    }
+    for (int64_t j = k1 - k0 - 1; j >= 0 && e == cudaSuccess && st == LBM_OK; j--) {
+      a.h = seg + j * stN;
+      a.lag = seg + j * stN + hN;
+      a.lam_in = lb[cur_adj];
+      a.lfl_in = lb[cur_adj] + 9 * P;
+      a.lq_in = lb[cur_adj] + 10 * P;
+      a.lam_out = lb[cur_adj ^ 1];
+      a.lfl_out = lb[cur_adj ^ 1] + 9 * P;
+      a.lq_out = lb[cur_adj ^ 1] + 10 * P;
+      e = lbmk::launch_adjoint_step(a, s);
+      cur_adj ^= 1;
+    }
+  }
+  double hg[lbmk::ADJ_NACC] = {0};
+  if (e == cudaSuccess && st == LBM_OK) e = lbmk::launch_adjoint_reduce(acc, c->g, dout, s);
+  if (e == cudaSuccess && st == LBM_OK)
+    e = cudaMemcpyAsync(hg, dout, sizeof(hg), cudaMemcpyDeviceToHost, s);
+  // the context ends at the final state, as after lbm_step(nsteps)
+  if (e == cudaSuccess && st == LBM_OK)
+    e = cudaMemcpyAsync(c->pop[parN], fin, 27 * P * sizeof(double), cudaMemcpyDeviceToDevice, s);
+  if (e == cudaSuccess && st == LBM_OK)
+    e = cudaMemcpyAsync(c->lag[parN], fin + 27 * P, lN * sizeof(double), cudaMemcpyDeviceToDevice, s);
+  c->cur = parN;
+  c->step = step0 + nsteps;
+  c->gen++;
+  if (e == cudaSuccess && st == LBM_OK) st = lbm_compute_diagnostics(c, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  release();
+  if (e != cudaSuccess) return cuda_fail(c, e, "adjoint");
+  if (st != LBM_OK) return st;
+  *ff_out = ffv;
+  for (int k = 0; k < lbmk::ADJ_NACC; k++) grad[k] = hg[k];
+  c->last_stream = s;
+  return LBM_OK;
+}
 
 // ---------------------------------------------------------------------------
 // autotuning of the step form on the context's own grid

@@ -25,6 +25,11 @@ cudaError_t launch_init_f32(const InitArgs<float>& a, cudaStream_t s);
 // FP16 population storage, FP32 arithmetic.
 cudaError_t launch_step_f16s(const Args<float, __half>& a, int mode, bool diag, cudaStream_t s);
 cudaError_t launch_init_f16s(const InitArgs<float, __half>& a, cudaStream_t s);
+// Reverse mode of the enthalpy-lattice step (lbm_adjoint.cuh).
+struct AdjArgs;
+cudaError_t launch_adjoint_seed(const AdjArgs& a, cudaStream_t s);
+cudaError_t launch_adjoint_step(const AdjArgs& a, cudaStream_t s);
+cudaError_t launch_adjoint_reduce(const double* acc, const Geom& g, double* out, cudaStream_t s);
 // Forward-mode tangent (FP64 value and derivative).
 cudaError_t launch_step_tan(const Args<Dual>& a, int mode, bool diag, cudaStream_t s);
 cudaError_t launch_init_tan(const InitArgs<Dual>& a, cudaStream_t s);

@@ -60,7 +60,7 @@ EXPORTS = ("lbm_create", "lbm_set_geometry", "lbm_step", "lbm_read_fields",
            "lbm_status_string", "lbm_destroy", "lbm_diagnostics_noalloc",
            "lbm_batch_create", "lbm_batch_step", "lbm_batch_destroy", "lbm_probe_fma_rate",
            "lbm_read_crossings", "lbm_read_tangent_fields", "lbm_read_tangent_diagnostics",
-           "lbm_read_crossings_tangent", "lbm_autotune")
+           "lbm_read_crossings_tangent", "lbm_autotune", "lbm_adjoint_frozen_fraction")
 
 _lib = None
 
@@ -103,12 +103,13 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     L.lbm_read_tangent_fields.argtypes = [vp, ctypes.c_uint32, ctypes.POINTER(vp), ctypes.c_int, vp]
     L.lbm_read_tangent_diagnostics.argtypes = [vp, ctypes.POINTER(LbmDiag)]
     L.lbm_autotune.argtypes = [vp, ctypes.c_int, vp, dp, ctypes.POINTER(ctypes.c_int)]
+    L.lbm_adjoint_frozen_fraction.argtypes = [vp, ctypes.c_int64, ctypes.c_int, dp, dp, vp]
     for fn in ("lbm_create", "lbm_set_geometry", "lbm_step", "lbm_read_fields",
                "lbm_compute_diagnostics", "lbm_read_diagnostics", "lbm_state_size",
                "lbm_save_state", "lbm_load_state", "lbm_diagnostics_noalloc",
                "lbm_batch_create", "lbm_batch_step", "lbm_probe_fma_rate",
                "lbm_read_crossings", "lbm_read_crossings_tangent", "lbm_read_tangent_fields",
-               "lbm_read_tangent_diagnostics", "lbm_autotune"):
+               "lbm_read_tangent_diagnostics", "lbm_autotune", "lbm_adjoint_frozen_fraction"):
         getattr(L, fn).restype = ctypes.c_int
     _lib = L
     return L
@@ -194,6 +195,15 @@ def lbm_read_crossings_tangent(ctx, axis: int, index: int, stream=None):
     _check(ctx, load().lbm_read_crossings_tangent(ctx, int(axis), int(index), out, stream),
            "lbm_read_crossings_tangent")
     return tuple(out)
+
+
+def lbm_adjoint_frozen_fraction(ctx, nsteps: int, every: int, stream=None):
+    """(FF after nsteps steps, [dFF/dT_wall[0..3], dFF/dlatent]); see include/lbm.h."""
+    ff = ctypes.c_double()
+    grad = (ctypes.c_double * 5)()
+    _check(ctx, load().lbm_adjoint_frozen_fraction(ctx, int(nsteps), int(every), ctypes.byref(ff),
+                                                   grad, stream), "lbm_adjoint_frozen_fraction")
+    return ff.value, list(grad)
 
 
 VARIANTS = ("fused, periods >= 32", "fused, periods >= 256", "split, periods >= 32",
@@ -366,6 +376,11 @@ class Solver:
     def crossings(self, axis: int, index: int):
         """Interface positions along one line (see lbm_read_crossings)."""
         return lbm_read_crossings(self.ctx, axis, index, _stream())
+
+    def adjoint_frozen_fraction(self, nsteps: int, every: int = 64):
+        """Advance nsteps and return (FF, its gradient) by reverse mode
+        (enthalpy-lattice FP64 contexts; see lbm_adjoint_frozen_fraction)."""
+        return lbm_adjoint_frozen_fraction(self.ctx, nsteps, every, _stream())
 
     def autotune(self, steps_per_trial: int = 64):
         """Pick the fastest step form for this grid (state unchanged)."""

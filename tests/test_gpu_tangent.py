@@ -221,3 +221,88 @@ def test_porous_medium_gradient_over_4000_steps(env):
     assert val[0] > 0.0
     assert abs(J[0, 0] - fd[0]) <= 1e-3 * abs(fd[0])
     assert abs(J[0, 1] - fd[1]) <= 1e-3 * abs(fd[1]) + 1e-10
+
+
+# ---------------------------------------------------------------------------
+# reverse mode (hand-written adjoint) of the enthalpy-lattice step
+# ---------------------------------------------------------------------------
+
+def _heat_column():
+    cfg, arr = W.neumann()
+    cfg = dict(cfg, lattices=4)  # the enthalpy lattice alone (the fluid is at rest)
+    return cfg, arr
+
+
+def test_adjoint_gradient_equals_the_tangent_and_differences(env):
+    """The reverse sweep gives the gradient of the frozen fraction of the
+    conduction-freezing column with respect to the cold-wall temperature and
+    the latent heat: equal to the forward-mode tangent (the same discrete
+    derivative, another summation order) and to central differences."""
+    O, lbm, S, torch = env
+    cfg, arr = _heat_column()
+    steps = 2000
+    s = lbm.Solver(cfg, precision="fp64").set_geometry(arr)
+    ff, grad = s.adjoint_frozen_fraction(steps, every=100)
+    s.close()
+    tan = {}
+    for name, direction in (("T_wall0", {"T_wall": [1.0, 0.0, 0.0, 0.0]}), ("latent", {"latent": 1.0})):
+        t = lbm.Solver(cfg, precision="tangent", tangent=direction).set_geometry(arr).step(steps)
+        d, dt = t.diagnostics(), t.tangent_diagnostics(compute=False)
+        fz, mv = d["frozen_volume"], d["material_volume"]
+        tan[name] = (dt["frozen_volume"] * mv - fz * dt["material_volume"]) / mv ** 2
+        assert abs(fz / mv - ff) <= 1e-12 * ff
+        t.close()
+
+    def ff_at(c):
+        u = lbm.Solver(c, precision="fp64").set_geometry(arr).step(steps)
+        d = u.diagnostics()
+        u.close()
+        return d["frozen_volume"] / d["material_volume"]
+
+    h = 1e-7
+    tw = list(cfg["T_wall"])
+    fd_tw = (ff_at(dict(cfg, T_wall=tuple([tw[0] + h] + tw[1:])))
+             - ff_at(dict(cfg, T_wall=tuple([tw[0] - h] + tw[1:])))) / (2 * h)
+    hl = 1e-7 * cfg["latent"]
+    fd_l = (ff_at(dict(cfg, latent=cfg["latent"] + hl)) - ff_at(dict(cfg, latent=cfg["latent"] - hl))) / (2 * hl)
+    print(f"\nFF {ff:.8f}; dFF/dT_w adjoint {grad[0]:.10e} tangent {tan['T_wall0']:.10e} FD {fd_tw:.10e}; "
+          f"dFF/dL adjoint {grad[4]:.10e} tangent {tan['latent']:.10e} FD {fd_l:.10e}")
+    assert abs(grad[0] - tan["T_wall0"]) <= 1e-9 * abs(tan["T_wall0"])
+    assert abs(grad[4] - tan["latent"]) <= 1e-9 * abs(tan["latent"])
+    assert abs(grad[0] - fd_tw) <= 1e-4 * abs(fd_tw)
+    assert abs(grad[4] - fd_l) <= 1e-4 * abs(fd_l)
+    assert grad[1] == grad[2] == grad[3] == 0.0  # the other walls are not Dirichlet walls of T_w
+
+
+def test_adjoint_checkpoint_interval_and_final_state(env):
+    """The checkpoint interval changes the memory, not the result (the
+    recomputed segments repeat the forward steps bit for bit), and the
+    context ends in the state nsteps plain steps give."""
+    O, lbm, S, torch = env
+    cfg, arr = _heat_column()
+    steps = 300
+    out = []
+    for every in (1, 37, 300):
+        s = lbm.Solver(cfg, precision="fp64").set_geometry(arr)
+        out.append(s.adjoint_frozen_fraction(steps, every=every))
+        if every == 37:
+            f_adj = s.fields()
+            assert s.steps_done == steps
+        s.close()
+    assert all(o == out[0] for o in out[1:]), out
+    plain = lbm.Solver(cfg, precision="fp64").set_geometry(arr).step(steps)
+    f_plain = plain.fields()
+    for k in FIELDS:
+        assert np.array_equal(f_adj[k], f_plain[k]), k
+    plain.close()
+
+
+def test_adjoint_rejects_other_contexts(env):
+    O, lbm, S, torch = env
+    cfg, arr = _heat_column()
+    for c, prec in ((cfg, "fp32"), (dict(cfg, lattices=5), "fp64")):
+        s = lbm.Solver(c, precision=prec).set_geometry(arr)
+        with pytest.raises(lbm.LbmError) as e:
+            s.adjoint_frozen_fraction(10, 5)
+        assert e.value.status == -6
+        s.close()
