@@ -271,7 +271,8 @@ def test_adjoint_gradient_equals_the_tangent_and_differences(env):
     assert abs(grad[4] - tan["latent"]) <= 1e-9 * abs(tan["latent"])
     assert abs(grad[0] - fd_tw) <= 1e-4 * abs(fd_tw)
     assert abs(grad[4] - fd_l) <= 1e-4 * abs(fd_l)
-    assert grad[1] == grad[2] == grad[3] == 0.0  # the other walls are not Dirichlet walls of T_w
+    assert grad[2] == grad[3] == 0.0  # periodic in y: no wall there
+    assert abs(grad[1]) < 1e-6 * abs(grad[0])  # the warm wall is 400 nodes from the front
 
 
 def test_adjoint_checkpoint_interval_and_final_state(env):
