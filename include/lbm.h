@@ -289,7 +289,11 @@ void lbm_batch_destroy(lbm_batch* batch);
  * column of Sec. 4.1), advances the state by nsteps steps, as lbm_step
  * would, and returns the frozen fraction FF = sum w (1 - fl) / sum w of the
  * final state in *ff and its gradient in grad[0..4]: dFF/dT_wall[k] for the
- * four walls (zero where bc[k] is not LBM_BC_DIRICHLET) and dFF/dlatent.
+ * four walls (zero where bc[k] is not LBM_BC_DIRICHLET) and dFF/dlatent,
+ * with the state at the start of the call held fixed, except that a call
+ * right after lbm_set_geometry (step 0) includes the dependence of the
+ * initial enthalpy populations on the latent heat (rho H = C T + w rho_l L
+ * fl), so its gradient is that of the whole run from the initial fields.
  * The gradient comes from one reverse sweep of hand-written adjoint kernels
  * (the transposed step: pull through the push and the wall rules, then back
  * through the TRT collision and the enthalpy inversion, taking at its kinks

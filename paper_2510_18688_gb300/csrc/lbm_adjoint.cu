@@ -14,6 +14,11 @@ cudaError_t launch_adjoint_step(const AdjArgs& a, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+cudaError_t launch_adjoint_init(const AdjArgs& a, cudaStream_t s) {
+  lbm_adjoint_init_kernel<<<grid_dims(a.g), block_dims(), 0, s>>>(a);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_adjoint_reduce(const double* acc, const Geom& g, double* out, cudaStream_t s) {
   lbm_adjoint_reduce_kernel<<<1, NT, 0, s>>>(acc, g, out);
   return cudaGetLastError();

@@ -233,6 +233,20 @@ static __global__ void __launch_bounds__(NT) lbm_adjoint_step_kernel(const AdjAr
   a.acc[(ADJ_NACC - 1) * P + n] += dL;
 }
 
+// Initial-state term: set_geometry builds the rest enthalpy population
+// from rho H = C T + w rho_l L fl (Eq. (8)), the other populations from T
+// alone (Eq. (25), u = 0), so dh0/dL = w rho_l fl; with lam_in the adjoint
+// of the initial populations and lag the initial lag planes.
+static __global__ void __launch_bounds__(NT) lbm_adjoint_init_kernel(const AdjArgs a) {
+  const Geom& g = a.g;
+  const int x = blockIdx.x * TX + threadIdx.x, y = blockIdx.y * TY + threadIdx.y;
+  if (x >= g.nx || y >= g.ny) return;
+  const int P = (int)g.plane;
+  const int n = y * g.pitch + x;
+  const double w = a.lag[LAG_W * P + n], fl = a.lag[LAG_FL * P + n];
+  a.acc[(ADJ_NACC - 1) * P + n] += a.lam_in[n] * w * a.c.rho_l * fl;
+}
+
 // Fixed-order sum of the accumulator planes over the grid (one CTA).
 static __global__ void __launch_bounds__(NT) lbm_adjoint_reduce_kernel(const double* __restrict__ acc,
                                                                 Geom g, double* __restrict__ out) {

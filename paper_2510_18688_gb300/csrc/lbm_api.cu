@@ -797,6 +797,12 @@ extern "C" int lbm_adjoint_frozen_fraction(lbm_ctx* c, int64_t nsteps, int every
       cur_adj ^= 1;
     }
   }
+  // a run from set_geometry's state: add that state's dependence on L
+  if (e == cudaSuccess && st == LBM_OK && step0 == 0) {
+    a.lam_in = lb[cur_adj];
+    a.lag = ck + hN;  // checkpoint 0 holds the initial lags
+    e = lbmk::launch_adjoint_init(a, s);
+  }
   double hg[lbmk::ADJ_NACC] = {0};
   if (e == cudaSuccess && st == LBM_OK) e = lbmk::launch_adjoint_reduce(acc, c->g, dout, s);
   if (e == cudaSuccess && st == LBM_OK)

@@ -29,6 +29,7 @@ cudaError_t launch_init_f16s(const InitArgs<float, __half>& a, cudaStream_t s);
 struct AdjArgs;
 cudaError_t launch_adjoint_seed(const AdjArgs& a, cudaStream_t s);
 cudaError_t launch_adjoint_step(const AdjArgs& a, cudaStream_t s);
+cudaError_t launch_adjoint_init(const AdjArgs& a, cudaStream_t s);
 cudaError_t launch_adjoint_reduce(const double* acc, const Geom& g, double* out, cudaStream_t s);
 // Forward-mode tangent (FP64 value and derivative).
 cudaError_t launch_step_tan(const Args<Dual>& a, int mode, bool diag, cudaStream_t s);
