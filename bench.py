@@ -241,6 +241,52 @@ def reference_arm(args, rank, world, budget_s: float = 150.0):
     print(json.dumps(line), flush=True)
 
 
+def adjoint_line(args, rank, world, every: int = 64):
+    """Frozen fraction of a conduction-freezing column (Sec. 4.1 shape, 2048 x
+    256, enthalpy lattice alone, FP64) after K steps and its gradient by the
+    reverse sweep, timed against K forward steps of the same context."""
+    import torch
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
+    from paper_2510_18688_gb300 import build, lbm, workloads as W
+    build.build()
+    lbm.load()
+    cfg, arr = W.neumann(nx=2048, ny=256)
+    cfg = dict(cfg, lattices=W.HEAT)
+    n = cfg["nx"] * cfg["ny"]
+    stream = torch.cuda.current_stream()
+    sptr = ctypes.c_void_p(stream.cuda_stream)
+    K = args.steps
+    s = lbm.Solver(cfg, precision="fp64").set_geometry(arr)
+    s.step(args.warmup)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    lbm.lbm_step(s.ctx, K, sptr)
+    torch.cuda.synchronize()
+    t_fwd = time.perf_counter() - t0
+    s.set_geometry(arr)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    ff, grad = lbm.lbm_adjoint_frozen_fraction(s.ctx, K, every, sptr)
+    t_adj = time.perf_counter() - t0
+    s.close()
+    if rank != 0:
+        return
+    line = {
+        "metric": METRIC + " (forward + reverse sweep)", "value": n * K / t_adj / 1e6,
+        "unit": "MLUPS", "n_gpus": world, "steps": K, "warmup": args.warmup,
+        "ms_per_step": t_adj / K * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "conduction-freezing column 2048x256 (Sec. 4.1 shape), enthalpy "
+                               "lattice alone, frozen fraction and its gradient w.r.t. wall "
+                               "temperatures and latent heat", "checkpoint_every": every},
+        "adjoint_forward_ratio": t_adj / t_fwd,
+        "forward_ms_per_step": t_fwd / K * 1e3,
+        "ff": ff, "grad": {"T_wall": grad[:4], "latent": grad[4]},
+        "note": "host wall-clock around whole calls (synchronised); both include launch overheads",
+    }
+    print(json.dumps(line), flush=True)
+
+
 def cpu_baseline_sample(target_s: float = 12.0):
     """Time the oracle on the same workload for about target_s seconds."""
     from oracle import oracle as O
@@ -272,6 +318,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--diag-every", type=int, default=1,
                     help="steps between fused FP64 diagnostic reductions (0: none)")
+    ap.add_argument("--adjoint", action="store_true",
+                    help="time the reverse-mode gradient of the frozen fraction on the enthalpy "
+                         "lattice alone (conduction column 2048 x 256, FP64) against its forward run")
     ap.add_argument("--workload", default="droplet512", choices=sorted(WORKLOADS),
                     help="droplet512 is the headline; the others are context lines")
     args = ap.parse_args()
@@ -280,6 +329,9 @@ def main():
 
     if args.impl == "reference":
         reference_arm(args, rank, world)
+        return
+    if args.adjoint:
+        adjoint_line(args, rank, world)
         return
 
     import torch
