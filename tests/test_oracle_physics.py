@@ -275,3 +275,42 @@ def test_stefan_final_height_table1(O, rho_r, tol):
         assert abs(d["material_mass"] / m0 - 1) < 0.02
     else:
         assert abs(d["material_mass"] / m0 - 1) < 0.15
+
+
+def test_flat_interface_stays_stationary(O):
+    """P9: a flat gas-liquid interface started from the equilibrium profile
+    phi = tanh(2 x / eps) of Eq. (4) (two interfaces in a periodic column,
+    fluid at rest, no heat) stays where it is.  The continuum profile relaxes
+    to the discrete equilibrium of the isotropic stencils (a change of about
+    1e-2 near the interface, settling: the change between 5,000 and 10,000
+    steps is under 3e-3); the phi = 0 crossings move by less than 1e-3
+    lattice units and the bulk stays at phi = -1, +1 to 1e-5.  A wrong sign
+    or coefficient in the chemical potential of Eq. (6) widens, narrows or
+    moves the interface far beyond these bounds."""
+    nx, ny = 96, 4
+    cfg = W.base_params(nx, ny, lattices=W.FLOW | W.PHASE, sigma=0.001, mobility=0.1)
+    x = np.arange(nx) + 0.5
+    eps = cfg["eps"]
+    prof = np.tanh(2 * (x - 24) / eps) - np.tanh(2 * (x - 72) / eps) - 1.0
+    phi = np.tile(prof, (ny, 1))
+    z = np.zeros((ny, nx))
+    o = O.Oracle(cfg).init(z, phi, z + 0.5, z + 1.0)
+
+    def crossings(row):
+        out = []
+        for i in range(nx - 1):
+            a, b = row[i], row[i + 1]
+            if (a <= 0) != (b <= 0):
+                out.append(i + 0.5 + a / (a - b))
+        return np.array(out)
+
+    c0 = crossings(o.fields()["phi"][1])
+    o.step(5000)
+    mid = o.fields()["phi"]
+    o.step(5000)
+    f = o.fields()["phi"]
+    assert np.abs(f - np.tile(prof, (ny, 1))).max() < 2e-2
+    assert np.abs(f - mid).max() < 3e-3
+    c1 = crossings(f[1])
+    assert len(c1) == 2 and np.abs(c1 - c0).max() < 1e-3, (c0, c1)
+    assert abs(f[1, 48] - 1.0) < 1e-5 and abs(f[1, 0] + 1.0) < 1e-5
