@@ -284,9 +284,12 @@ int lbm_batch_step(lbm_batch* batch, int64_t nsteps, void* stream);
 void lbm_batch_destroy(lbm_batch* batch);
 
 /* Reverse mode (adjoint) of the enthalpy-lattice step, Eqs. (8), (23)-(28)
- * with the fluid at rest: for a context with precision LBM_FP64, lattices ==
- * LBM_LAT_HEAT and no cold mask (for example the conduction-freezing
- * column of Sec. 4.1), advances the state by nsteps steps, as lbm_step
+ * with the fluid at rest: for a context with precision LBM_FP64, no cold
+ * mask, and lattices == LBM_LAT_HEAT, or LBM_LAT_FLOW | LBM_LAT_HEAT with
+ * rho_s == rho_l and no body force (then no mass source and no force ever
+ * set the flow in motion, so its populations stay exactly zero: the
+ * conduction-freezing column of Sec. 4.1), advances the state by nsteps
+ * steps, as lbm_step
  * would, and returns the frozen fraction FF = sum w (1 - fl) / sum w of the
  * final state in *ff and its gradient in grad[0..4]: dFF/dT_wall[k] for the
  * four walls (zero where bc[k] is not LBM_BC_DIRICHLET) and dFF/dlatent,

@@ -692,9 +692,15 @@ extern "C" int lbm_adjoint_frozen_fraction(lbm_ctx* c, int64_t nsteps, int every
   if (!ff_out || !grad) return fail(c, LBM_ERR_ARG, "null output%s");
   if (nsteps < 1 || every < 1) return fail(c, LBM_ERR_ARG, "nsteps and the checkpoint interval must be >= 1%s");
   if (!c->have_geometry) return fail(c, LBM_ERR_STATE, "adjoint before lbm_set_geometry%s");
-  if (c->p.precision != LBM_FP64 || c->p.lattices != LBM_LAT_HEAT || c->g.has_mask)
+  // the enthalpy lattice alone, or with a flow lattice that stays exactly at
+  // rest (no mass source: rho_s = rho_l; no body force)
+  const bool resting_flow = c->p.lattices == (LBM_LAT_FLOW | LBM_LAT_HEAT) &&
+                            c->p.rho_s == c->p.rho_l && c->p.gx == 0.0 && c->p.gy == 0.0;
+  if (c->p.precision != LBM_FP64 || !(c->p.lattices == LBM_LAT_HEAT || resting_flow) ||
+      c->g.has_mask)
     return fail(c, LBM_ERR_UNSUPPORTED,
-                "the adjoint covers FP64 contexts with the enthalpy lattice alone and no cold mask%s");
+                "the adjoint covers FP64 contexts with the enthalpy lattice (alone, or with a flow "
+                "lattice that stays at rest: rho_s = rho_l, no body force) and no cold mask%s");
   cudaStream_t s = (cudaStream_t)stream;
   const size_t P = (size_t)c->g.plane;
   const size_t hN = 9 * P, lN = lbmk::NLAG * P, stN = hN + lN;  // doubles per stored state

@@ -298,10 +298,32 @@ def test_adjoint_checkpoint_interval_and_final_state(env):
     plain.close()
 
 
+def test_adjoint_of_the_conduction_column_with_its_resting_flow(env):
+    """The conduction-freezing column as configured (flow and enthalpy
+    lattices, rho_s = rho_l, no body force): the flow stays at rest, and the
+    adjoint gradient equals the tangent of the full step."""
+    O, lbm, S, torch = env
+    cfg, arr = W.neumann()
+    assert cfg["lattices"] == 5 and cfg["rho_s"] == cfg["rho_l"]
+    steps = 1500
+    s = lbm.Solver(cfg, precision="fp64").set_geometry(arr)
+    ff, grad = s.adjoint_frozen_fraction(steps, every=64)
+    assert np.abs(s.fields(("ux",))["ux"]).max() == 0.0
+    s.close()
+    t = lbm.Solver(cfg, precision="tangent", tangent={"T_wall": [1.0, 0.0, 0.0, 0.0]}
+                   ).set_geometry(arr).step(steps)
+    d, dt = t.diagnostics(), t.tangent_diagnostics(compute=False)
+    fz, mv = d["frozen_volume"], d["material_volume"]
+    tan = (dt["frozen_volume"] * mv - fz * dt["material_volume"]) / mv ** 2
+    t.close()
+    assert abs(grad[0] - tan) <= 1e-9 * abs(tan), (grad[0], tan)
+
+
 def test_adjoint_rejects_other_contexts(env):
     O, lbm, S, torch = env
     cfg, arr = _heat_column()
-    for c, prec in ((cfg, "fp32"), (dict(cfg, lattices=5), "fp64")):
+    for c, prec in ((cfg, "fp32"), (dict(cfg, lattices=7), "fp64"),
+                    (dict(cfg, lattices=5, rho_s=0.9), "fp64")):
         s = lbm.Solver(c, precision=prec).set_geometry(arr)
         with pytest.raises(lbm.LbmError) as e:
             s.adjoint_frozen_fraction(10, 5)
