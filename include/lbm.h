@@ -318,8 +318,9 @@ int lbm_adjoint_frozen_fraction(lbm_ctx* ctx, int64_t nsteps, int every, double*
  * the two-kernel split with 32 and with 256.  Each variant runs
  * steps_per_trial steps twice from the same saved state (the first run
  * warms up and captures; the second is timed with CUDA events on `stream`).
- * The state, step counter and diagnostics are restored afterwards, so the
- * call does not advance the simulation.  out_us (4 doubles, may be NULL):
+ * The state, step counter and diagnostics (including partial sums not yet
+ * read) are restored afterwards, so the call does not advance the
+ * simulation.  out_us (4 doubles, may be NULL):
  * microseconds per step of each variant (-1 where not run); chosen (may be
  * NULL): the index kept.  Allocates a backup of the state (27 population
  * and 6 lag planes) for the duration of the call and synchronises `stream`.

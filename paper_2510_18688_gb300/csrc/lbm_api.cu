@@ -844,8 +844,10 @@ extern "C" int lbm_autotune(lbm_ctx* c, int steps_per_trial, void* stream, doubl
   cudaStream_t s = (cudaStream_t)stream;
   const size_t P = (size_t)c->g.plane;
   const size_t pb = 27 * P * c->pop_esize, lb = lbmk::NLAG * P * c->esize;
+  // the diagnostic partials too: trial steps overwrite them
+  const size_t db = (c->tangent ? 2 : 1) * (size_t)lbmk::NDIAG * c->nblocks * sizeof(double);
   void* backup = nullptr;
-  cudaError_t e = cudaMalloc(&backup, pb + lb);
+  cudaError_t e = cudaMalloc(&backup, pb + lb + db);
   if (e != cudaSuccess) return cuda_fail(c, e, "autotune backup allocation");
   // the state the trials start from, and the host-side step bookkeeping
   const int cur = c->cur;
@@ -856,6 +858,8 @@ extern "C" int lbm_autotune(lbm_ctx* c, int steps_per_trial, void* stream, doubl
   e = cudaMemcpyAsync(backup, c->pop[cur], pb, cudaMemcpyDeviceToDevice, s);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync((char*)backup + pb, c->lag[cur], lb, cudaMemcpyDeviceToDevice, s);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync((char*)backup + pb + lb, c->diag_partial, db, cudaMemcpyDeviceToDevice, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   // variants: kernel form (fused, split) x shortest captured period (32, 256)
   const bool split_ok = c->p.precision == LBM_FP32 || c->p.precision == LBM_FP64;
@@ -892,6 +896,8 @@ extern "C" int lbm_autotune(lbm_ctx* c, int steps_per_trial, void* stream, doubl
   cudaError_t er = cudaMemcpyAsync(c->pop[cur], backup, pb, cudaMemcpyDeviceToDevice, s);
   if (er == cudaSuccess)
     er = cudaMemcpyAsync(c->lag[cur], (char*)backup + pb, lb, cudaMemcpyDeviceToDevice, s);
+  if (er == cudaSuccess)
+    er = cudaMemcpyAsync(c->diag_partial, (char*)backup + pb + lb, db, cudaMemcpyDeviceToDevice, s);
   if (er == cudaSuccess) er = cudaStreamSynchronize(s);
   c->cur = cur;
   c->step = step;
