@@ -364,7 +364,8 @@ int lbm_autotune(lbm_ctx* ctx, int steps_per_trial, void* stream, double* out_us
  *
  * Errors: LBM_ERR_ARG for a null pointer or invalid grid, LBM_ERR_PARAM for
  * invalid parameters (the checks of lbm_create), LBM_ERR_UNSUPPORTED for a
- * grid of more than LBM_NOALLOC_MAX_BLOCKS tiles (message on stderr),
+ * grid of more than LBM_NOALLOC_MAX_BLOCKS tiles or a precision other than
+ * LBM_FP32 and LBM_FP64 (message on stderr),
  * LBM_ERR_CUDA if the address lookup or the launch fails.  No call to
  * cudaMalloc, cudaFree or any allocating library routine is made. */
 int lbm_diagnostics_noalloc(const lbm_params* params, const void* pops, const void* lags,
