@@ -496,3 +496,24 @@ def test_batch64_full_size_sampled_grids(env):
     b.close()
     for s in ss:
         s.close()
+
+
+def test_batch_of_more_than_64_grids(env):
+    """More than 64 grids take several launches per step (64 grids per
+    argument table); every grid still matches its own lbm_step run bit for
+    bit (FP64), through captured periods and single steps."""
+    O, lbm = env
+    wls = [W.random_state(20 + (k % 7) * 3, 10 + (k % 5) * 4, seed=100 + k) for k in range(70)]
+    ss = [lbm.Solver(c, precision="fp64", diag_every=3).set_geometry(a) for c, a in wls]
+    b = lbm.Batch(ss)
+    b.step(5).step(40)
+    for (cfg, arr), s in zip(wls[::9] + [wls[-1]], ss[::9] + [ss[-1]]):
+        alone = lbm.Solver(cfg, precision="fp64", diag_every=3).set_geometry(arr).step(45)
+        fa, fb = alone.fields(), s.fields()
+        for k in FIELDS:
+            assert np.array_equal(fa[k], fb[k]), k
+        assert alone.diagnostics(compute=False) == s.diagnostics(compute=False)
+        alone.close()
+    b.close()
+    for s in ss:
+        s.close()
