@@ -53,6 +53,16 @@ def _porous(seed):
     return [W.porous(seed=seed)]
 
 
+def _neumann(seed):
+    from paper_2510_18688_gb300 import workloads as W
+    return [W.neumann()]
+
+
+def _stefan(seed):
+    from paper_2510_18688_gb300 import workloads as W
+    return [W.stefan()]
+
+
 def _batch64(seed):
     """64 droplets on cold cylinders, sides drawn from {128, 256, 384, 512}."""
     from paper_2510_18688_gb300 import workloads as W
@@ -65,6 +75,8 @@ WORKLOADS = {
     "droplet512": (_droplet512, "sessile droplet freezing 512x512 (R=100, cold solid layer), 3 lattices"),
     "droplet1024": (_droplet1024, "sessile droplet freezing 1024x1024 (R=200, cold solid layer), 3 lattices"),
     "porous2048x1024": (_porous, "freezing in a porous medium 2048x1024 (porosity 0.6, saturation 0.5), 3 lattices"),
+    "neumann400x4": (_neumann, "conduction-induced freezing column 400x4 (flow + enthalpy lattices)"),
+    "stefan512x8": (_stefan, "three-phase Stefan column 512x8, 3 lattices"),
     "batch64": (_batch64, "64 droplets on cold cylinders, sides in {128,256,384,512}, one persistent launch per step"),
 }
 
@@ -241,6 +253,56 @@ def reference_arm(args, rank, world, budget_s: float = 150.0):
     print(json.dumps(line), flush=True)
 
 
+def back_to_back_line(args, rank, world):
+    """Launch-overhead context for small grids: K steps in one lbm_step call
+    (whole periods replayed from a captured CUDA graph) against K calls of
+    one step each, both timed with CUDA events around the whole run.  The
+    grid stays in L2 (no flush): this measures launch cost, not HBM."""
+    import torch
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
+    from paper_2510_18688_gb300 import build, lbm
+    build.build()
+    lbm.load()
+    make, workload_name = WORKLOADS[args.workload]
+    (cfg, arr), = make(rank)
+    n = cfg["nx"] * cfg["ny"]
+    stream = torch.cuda.current_stream()
+    sptr = ctypes.c_void_p(stream.cuda_stream)
+    s = lbm.Solver(cfg, precision=args.precision, diag_every=args.diag_every).set_geometry(arr)
+    K = args.steps
+
+    def timed(fn):
+        fn(args.warmup)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        fn(K)
+        b.record(stream)
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / K  # ms per step
+
+    t_graph = timed(lambda k: lbm.lbm_step(s.ctx, k, sptr))
+    t_single = timed(lambda k: [lbm.lbm_step(s.ctx, 1, sptr) for _ in range(k)])
+    s.close()
+    if rank != 0:
+        return
+    line = {
+        "metric": METRIC, "value": n / (t_graph * 1e-3) / 1e6, "unit": "MLUPS", "n_gpus": world,
+        "steps": K, "warmup": args.warmup, "ms_per_step": t_graph,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": {"fp32": "f32", "fp64": "f64", "fp16s": "f32 (f16 storage)",
+                  "tangent": "f64 (value and derivative)"}[args.precision],
+        "data": "synthetic",
+        "config": {"workload": workload_name, "grid": [cfg["nx"], cfg["ny"]],
+                   "l2": "not flushed: back-to-back steps of a grid far smaller than L2 "
+                         "(a launch-overhead context line, not an HBM measurement)",
+                   "diag_every": args.diag_every},
+        "single_step_calls_ms_per_step": t_single,
+        "graph_speedup": t_single / t_graph,
+    }
+    print(json.dumps(line), flush=True)
+
+
 def adjoint_line(args, rank, world, every: int = 64):
     """Frozen fraction of a conduction-freezing column (Sec. 4.1 shape, 2048 x
     256, enthalpy lattice alone, FP64) after K steps and its gradient by the
@@ -318,6 +380,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--diag-every", type=int, default=1,
                     help="steps between fused FP64 diagnostic reductions (0: none)")
+    ap.add_argument("--back-to-back", action="store_true",
+                    help="context line for small grids: one call of K steps (captured CUDA "
+                         "graphs), no L2 flush, against K single-step calls")
     ap.add_argument("--adjoint", action="store_true",
                     help="time the reverse-mode gradient of the frozen fraction on the enthalpy "
                          "lattice alone (conduction column 2048 x 256, FP64) against its forward run")
@@ -332,6 +397,9 @@ def main():
         return
     if args.adjoint:
         adjoint_line(args, rank, world)
+        return
+    if args.back_to_back:
+        back_to_back_line(args, rank, world)
         return
 
     import torch
