@@ -304,16 +304,22 @@ def back_to_back_line(args, rank, world):
 
 
 def adjoint_line(args, rank, world, every: int = 64):
-    """Frozen fraction of a conduction-freezing column (Sec. 4.1 shape, 2048 x
-    256, enthalpy lattice alone, FP64) after K steps and its gradient by the
-    reverse sweep, timed against K forward steps of the same context."""
+    """Reverse sweep against K forward steps of the same context (FP64).
+    heat: frozen fraction of a conduction-freezing column (Sec. 4.1 shape,
+    2048 x 256, enthalpy lattice alone) and its gradient w.r.t. the wall
+    temperatures and L.  phase: the tip height of a 512^2 sessile droplet
+    (phase-field lattice alone) and its gradient w.r.t. theta and sigma."""
     import torch
     torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
     from paper_2510_18688_gb300 import build, lbm, workloads as W
     build.build()
     lbm.load()
-    cfg, arr = W.neumann(nx=2048, ny=256)
-    cfg = dict(cfg, lattices=W.HEAT)
+    if args.adjoint == "phase":
+        cfg, arr = W.sessile_droplet(512, seed=0)
+        cfg = dict(cfg, lattices=W.PHASE)
+    else:
+        cfg, arr = W.neumann(nx=2048, ny=256)
+        cfg = dict(cfg, lattices=W.HEAT)
     n = cfg["nx"] * cfg["ny"]
     stream = torch.cuda.current_stream()
     sptr = ctypes.c_void_p(stream.cuda_stream)
@@ -328,7 +334,10 @@ def adjoint_line(args, rank, world, every: int = 64):
     s.set_geometry(arr)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    ff, grad = lbm.lbm_adjoint_frozen_fraction(s.ctx, K, every, sptr)
+    if args.adjoint == "phase":
+        ff, grad = lbm.lbm_adjoint_crossing(s.ctx, K, every, 1, cfg["nx"] // 2, sptr)
+    else:
+        ff, grad = lbm.lbm_adjoint_frozen_fraction(s.ctx, K, every, sptr)
     t_adj = time.perf_counter() - t0
     s.close()
     if rank != 0:
@@ -338,12 +347,17 @@ def adjoint_line(args, rank, world, every: int = 64):
         "unit": "MLUPS", "n_gpus": world, "steps": K, "warmup": args.warmup,
         "ms_per_step": t_adj / K * 1e3, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": "conduction-freezing column 2048x256 (Sec. 4.1 shape), enthalpy "
-                               "lattice alone, frozen fraction and its gradient w.r.t. wall "
-                               "temperatures and latent heat", "checkpoint_every": every},
+        "config": {"workload": ("sessile droplet 512x512, phase-field lattice alone, tip height "
+                                "and its gradient w.r.t. contact angle and surface tension"
+                                if args.adjoint == "phase" else
+                                "conduction-freezing column 2048x256 (Sec. 4.1 shape), enthalpy "
+                                "lattice alone, frozen fraction and its gradient w.r.t. wall "
+                                "temperatures and latent heat"), "checkpoint_every": every},
         "adjoint_forward_ratio": t_adj / t_fwd,
         "forward_ms_per_step": t_fwd / K * 1e3,
-        "ff": ff, "grad": {"T_wall": grad[:4], "latent": grad[4]},
+        **({"tip": ff, "grad": {"theta_deg": grad[0], "sigma": grad[1]}}
+           if args.adjoint == "phase" else
+           {"ff": ff, "grad": {"T_wall": grad[:4], "latent": grad[4]}}),
         "note": "host wall-clock around whole calls (synchronised); both include launch overheads",
     }
     print(json.dumps(line), flush=True)
@@ -383,9 +397,10 @@ def main():
     ap.add_argument("--back-to-back", action="store_true",
                     help="context line for small grids: one call of K steps (captured CUDA "
                          "graphs), no L2 flush, against K single-step calls")
-    ap.add_argument("--adjoint", action="store_true",
-                    help="time the reverse-mode gradient of the frozen fraction on the enthalpy "
-                         "lattice alone (conduction column 2048 x 256, FP64) against its forward run")
+    ap.add_argument("--adjoint", nargs="?", const="heat", choices=("heat", "phase"),
+                    help="time a reverse-mode gradient against its forward run (FP64): heat, the "
+                         "frozen fraction of the conduction column 2048 x 256 (enthalpy lattice "
+                         "alone); phase, the tip height of the 512^2 droplet (phase field alone)")
     ap.add_argument("--workload", default="droplet512", choices=sorted(WORKLOADS),
                     help="droplet512 is the headline; the others are context lines")
     args = ap.parse_args()

@@ -310,6 +310,34 @@ void lbm_batch_destroy(lbm_batch* batch);
 int lbm_adjoint_frozen_fraction(lbm_ctx* ctx, int64_t nsteps, int every, double* ff,
                                 double* grad, void* stream);
 
+/* Reverse mode (adjoint) of the phase-field step, Eqs. (6) and (18)-(21)
+ * with the fluid at rest: for a context with precision LBM_FP64 and
+ * lattices == LBM_LAT_PHASE (no velocity, no mass source: the modified
+ * Cahn-Hilliard relaxation of a droplet on the solid phi0 with wetting),
+ * advances the state by nsteps steps, as lbm_step would, and returns in
+ * *pos the largest coordinate where phi crosses 0 along the grid line
+ * (axis, index) of the final state, as out[0] of lbm_read_crossings (a
+ * column: the tip height of a droplet; a row just above the substrate: its
+ * contact line), and in grad[0..1] its derivatives with respect to the
+ * contact angle theta (in degrees, through cos theta in Eq. (6)) and the
+ * surface tension sigma.
+ * The state at the start of the call is held fixed, except that a call
+ * right after lbm_set_geometry (step 0) includes the dependence of the
+ * initial phase populations on theta and sigma through their chemical
+ * potential, so its gradient is that of the whole run from the initial
+ * fields.  One reverse sweep of hand-written adjoint kernels: pull through
+ * the push and bounce-back, back through the collision to mu_phi, and the
+ * transposed Laplacian stencils (a scatter) back to phi and fs; kinks of
+ * the clamps take the branch the forward step took.  Checkpoints as in
+ * lbm_adjoint_frozen_fraction.  *pos is NaN (and the gradient zero) when
+ * phi does not cross 0 along the line.  Synchronises `stream`.
+ * Errors: LBM_ERR_ARG (null output, nsteps < 1, every < 1, axis not 0 or 1,
+ * index not a line of the grid), LBM_ERR_STATE before lbm_set_geometry,
+ * LBM_ERR_UNSUPPORTED for other contexts or sigma == 0,
+ * LBM_ERR_OOM/LBM_ERR_CUDA (the context's state is then undefined). */
+int lbm_adjoint_crossing(lbm_ctx* ctx, int64_t nsteps, int every, int axis, int index,
+                         double* pos, double* grad, void* stream);
+
 /* Autotuner (the paper gives no implementation; a measuring aid of this
  * library): times the step forms this build has on the context's own grid
  * and state and keeps the fastest for later lbm_step calls.  Variants, in

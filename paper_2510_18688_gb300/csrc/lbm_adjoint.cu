@@ -1,4 +1,4 @@
-// lbm_adjoint.cu -- launchers of the enthalpy-lattice adjoint kernels.
+// lbm_adjoint.cu -- launchers of the enthalpy-lattice and phase-field adjoint kernels.
 #include "lbm_adjoint.cuh"
 #include "lbm_launch.h"
 
@@ -21,6 +21,29 @@ cudaError_t launch_adjoint_init(const AdjArgs& a, cudaStream_t s) {
 
 cudaError_t launch_adjoint_reduce(const double* acc, const Geom& g, double* out, cudaStream_t s) {
   lbm_adjoint_reduce_kernel<<<1, NT, 0, s>>>(acc, g, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_phase_adjoint_fields(const PhaseAdjArgs& a, cudaStream_t s) {
+  lbm_phase_fields_kernel<<<grid_dims(a.g), block_dims(), 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_phase_adjoint_seed(const PhaseAdjArgs& a, cudaStream_t s) {
+  lbm_phase_seed_kernel<<<1, 32, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+// one reverse step: the scatter of part 1 accumulates into phib and fsb,
+// which the caller has zeroed
+cudaError_t launch_phase_adjoint_step(const PhaseAdjArgs& a, cudaStream_t s) {
+  lbm_phase_adjoint1_kernel<<<grid_dims(a.g), block_dims(), 0, s>>>(a);
+  lbm_phase_adjoint2_kernel<<<grid_dims(a.g), block_dims(), 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_phase_adjoint_init(const PhaseAdjArgs& a, cudaStream_t s) {
+  lbm_phase_init_kernel<<<grid_dims(a.g), block_dims(), 0, s>>>(a);
   return cudaGetLastError();
 }
 

@@ -276,4 +276,194 @@ static __global__ void __launch_bounds__(NT) lbm_adjoint_reduce_kernel(const dou
   }
 }
 
+// ---------------------------------------------------------------------------
+// reverse mode of the phase-field step (lattices == LAT_PHASE: the fluid at
+// rest, no heat): g* = (1 - 1/tau_g) g + g_eq / tau_g with g_eq of Eq. (19)
+// at u = 0 (Eq. (20) vanishes: no phi u, no mass source), mu_phi of Eq. (6)
+// from the isotropic Laplacians of phi, phi0 and fs, half-way bounce-back.
+// Observable: the last phi = 0 crossing along a grid line (a column: the
+// tip height; a row near the substrate: the contact line).
+// Parameters: the contact angle theta (through cos theta in Eq. (6)) and
+// sigma (mu_phi is proportional to it).
+// ---------------------------------------------------------------------------
+
+constexpr int PADJ_NACC = 2;  // d/dtheta_deg, d/dsigma
+
+struct PhaseAdjArgs {
+  Geom g;
+  Coef<double> c;
+  const double* __restrict__ gpop;   // 9 phase planes of the forward state
+  const double* __restrict__ lag;    // NLAG lag planes of the forward state
+  const double* __restrict__ phi0;
+  double* __restrict__ phi;          // forward phi, fs planes (fields kernel output)
+  double* __restrict__ fs;
+  const double* __restrict__ lam_in;  // adjoint of the next state's 9 planes
+  double* __restrict__ gs;            // 9 planes: adjoint of the post-collision populations
+  double* __restrict__ phib;          // adjoint of phi (accumulated, zeroed per step)
+  double* __restrict__ fsb;           // adjoint of fs (accumulated, zeroed per step)
+  double* __restrict__ lam_out;       // adjoint of this state's 9 planes
+  double* __restrict__ acc;           // PADJ_NACC accumulator planes (+=)
+  double dcos_dtheta;                 // d cos(theta) / d theta_deg
+  int axis, index;                    // seed: the grid line (as lbm_read_crossings)
+  double* __restrict__ out;           // seed: the crossing (1 double)
+};
+
+// phi = sum g and fs = min(phi0 + w (1 - fl), 1), w = clamp((1 - phi0 + phi) / 2)
+static __global__ void __launch_bounds__(NT) lbm_phase_fields_kernel(const PhaseAdjArgs a) {
+  const Geom& g = a.g;
+  const int x = blockIdx.x * TX + threadIdx.x, y = blockIdx.y * TY + threadIdx.y;
+  if (x >= g.nx || y >= g.ny) return;
+  const int P = (int)g.plane;
+  const int n = y * g.pitch + x;
+  double v[9];
+#pragma unroll
+  for (int i = 0; i < 9; i++) v[i] = a.gpop[i * P + n];
+  const double ph = sum_g(v);
+  const double q0 = a.phi0[n];
+  const double w = clamp01((1.0 - q0 + ph) * 0.5);
+  const double fs = q0 + w * (1.0 - a.lag[LAG_FL * P + n]);
+  a.phi[n] = ph;
+  a.fs[n] = fs > 1.0 ? 1.0 : fs;
+}
+
+__device__ __forceinline__ int stencil_index(const Geom& g, int x, int y, int i) {
+  const int xx = wrap_or_clamp(x + qx(i), g.nx, g.bc[0], g.bc[1]);
+  const int yy = wrap_or_clamp(y + qy(i), g.ny, g.bc[2], g.bc[3]);
+  return yy * g.pitch + xx;
+}
+
+// 6 sum_i w_i (chi(x + c_i) - chi(x)): the isotropic Laplacian (R-FD)
+__device__ __forceinline__ double lap6(const Geom& g, const double* chi, int x, int y, int n) {
+  double s = 0.0;
+#pragma unroll
+  for (int i = 1; i < 9; i++) s += 2.0 * qw<double>(i) * (chi[stencil_index(g, x, y, i)] - chi[n]);
+  return 3.0 * s;
+}
+
+// Seed: the position J = k + a / (a - b) of the last crossing of phi
+// through 0 along the line (one thread), dJ/dphi at the two nodes.
+static __global__ void lbm_phase_seed_kernel(const PhaseAdjArgs a) {
+  const Geom& g = a.g;
+  const int P = (int)g.plane;
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  const int len = a.axis == 0 ? g.nx : g.ny;
+  const int stride = a.axis == 0 ? 1 : g.pitch;
+  const int base = a.axis == 0 ? a.index * g.pitch : a.index;
+  double J = __longlong_as_double(0x7ff8000000000000ULL);
+  for (int k = len - 2; k >= 0; k--) {
+    const int n0 = base + k * stride, n1 = n0 + stride;
+    const double va = a.phi[n0], vb = a.phi[n1];
+    if ((va <= 0.0) != (vb <= 0.0)) {
+      const double d = va - vb;
+      J = k + va / d;
+      const double da = -vb / (d * d), db = va / (d * d);
+#pragma unroll
+      for (int i = 0; i < 9; i++) {
+        a.lam_out[i * P + n0] = da;
+        a.lam_out[i * P + n1] = db;
+      }
+      break;
+    }
+  }
+  a.out[0] = J;
+}
+
+// Shared pieces of Eq. (6): d chem / d phi, d chem / d fs, d chem / d cos(theta).
+__device__ __forceinline__ void chem_partials(const Coef<double>& c, double ph, double q0,
+                                              double fs, double* dphi, double* dfs,
+                                              double* dcos) {
+  *dphi = c.s3 * (3.0 * ph * ph - 1.0) + c.s9 * q0 * q0 + c.s3 * c.cos_th * q0 * 6.0 * ph +
+          c.s9 * fs * fs + c.s3 * c.cos_ps * fs * 6.0 * ph;
+  *dfs = c.s9 * 2.0 * fs * ph + c.s3 * c.cos_ps * (3.0 * ph * ph + 3.0 * fs * fs - 1.0);
+  *dcos = c.s3 * q0 * (3.0 * ph * ph + q0 * q0 - 1.0);
+}
+
+// Reverse step, part 1: pull the adjoint through the push, back through the
+// collision to mu_phi, and scatter mu_phi's adjoint over the stencils.
+static __global__ void __launch_bounds__(NT) lbm_phase_adjoint1_kernel(const PhaseAdjArgs a) {
+  const Geom& g = a.g;
+  const Coef<double>& c = a.c;
+  const int x = blockIdx.x * TX + threadIdx.x, y = blockIdx.y * TY + threadIdx.y;
+  if (x >= g.nx || y >= g.ny) return;
+  const int P = (int)g.plane;
+  const int n = y * g.pitch + x;
+  double gb[9];
+#pragma unroll
+  for (int i = 0; i < 9; i++) {
+    int wall;
+    const long long t = stream_target(g, x, y, qx(i), qy(i), wall);
+    gb[i] = t >= 0 ? a.lam_in[i * P + (int)t] : a.lam_in[qopp(i) * P + n];
+    a.gs[i * P + n] = gb[i];
+  }
+  const double itg = c.inv_tau_g;
+  double mub = (qw<double>(0) - 1.0) * gb[0];
+#pragma unroll
+  for (int i = 1; i < 9; i++) mub += qw<double>(i) * gb[i];
+  mub *= itg * c.eta;
+  const double ph = a.phi[n], q0 = a.phi0[n], fs = a.fs[n];
+  double dphi, dfs, dcos;
+  chem_partials(c, ph, q0, fs, &dphi, &dfs, &dcos);
+  const double lphi = lap6(g, a.phi, x, y, n), lphi0 = lap6(g, a.phi0, x, y, n);
+  const double lfs = lap6(g, a.fs, x, y, n);
+  const double mu = chem_local(c, ph, q0, fs) - c.klap * (lphi + c.cos_th * lphi0 + c.cos_ps * lfs);
+  // own node: the collision's phi, the local part of mu, the centre of the Laplacians
+  const double self = 6.0 * (1.0 - qw<double>(0));  // 6 sum_{i>0} w_i
+  atomicAdd(a.phib + n, itg * gb[0] + mub * dphi + c.klap * self * mub);
+  atomicAdd(a.fsb + n, mub * dfs + c.klap * c.cos_ps * self * mub);
+#pragma unroll
+  for (int i = 1; i < 9; i++) {
+    const int m = stencil_index(g, x, y, i);
+    atomicAdd(a.phib + m, -c.klap * 6.0 * qw<double>(i) * mub);
+    atomicAdd(a.fsb + m, -c.klap * c.cos_ps * 6.0 * qw<double>(i) * mub);
+  }
+  a.acc[n] += mub * (dcos - c.klap * lphi0) * a.dcos_dtheta;
+  a.acc[P + n] += mub * mu / c.sigma;
+}
+
+// Reverse step, part 2: fs -> w -> phi (local), phi = sum g.
+static __global__ void __launch_bounds__(NT) lbm_phase_adjoint2_kernel(const PhaseAdjArgs a) {
+  const Geom& g = a.g;
+  const int x = blockIdx.x * TX + threadIdx.x, y = blockIdx.y * TY + threadIdx.y;
+  if (x >= g.nx || y >= g.ny) return;
+  const int P = (int)g.plane;
+  const int n = y * g.pitch + x;
+  const double q0 = a.phi0[n], ph = a.phi[n], fl = a.lag[LAG_FL * P + n];
+  double phib = a.phib[n];
+  const double wraw = (1.0 - q0 + ph) * 0.5;
+  const double w = clamp01(wraw);
+  const double fsraw = q0 + w * (1.0 - fl);
+  if (!(fsraw > 1.0) && !(wraw < 0.0) && !(wraw > 1.0)) phib += a.fsb[n] * (1.0 - fl) * 0.5;
+  const double omg = 1.0 - a.c.inv_tau_g;
+#pragma unroll
+  for (int i = 0; i < 9; i++) a.lam_out[i * P + n] = omg * a.gs[i * P + n] + phib;
+}
+
+// Initial state (a run from set_geometry): g0 = g_eq(phi0_init, mu_phi0)
+// depends on theta and sigma through mu_phi0.
+static __global__ void __launch_bounds__(NT) lbm_phase_init_kernel(const PhaseAdjArgs a) {
+  const Geom& g = a.g;
+  const Coef<double>& c = a.c;
+  const int x = blockIdx.x * TX + threadIdx.x, y = blockIdx.y * TY + threadIdx.y;
+  if (x >= g.nx || y >= g.ny) return;
+  const int P = (int)g.plane;
+  const int n = y * g.pitch + x;
+  double mub = (qw<double>(0) - 1.0) * a.lam_in[n];
+#pragma unroll
+  for (int i = 1; i < 9; i++) mub += qw<double>(i) * a.lam_in[i * P + n];
+  mub *= c.eta;
+  const double ph = a.phi[n], q0 = a.phi0[n], fs = a.fs[n];
+  double dphi, dfs, dcos;
+  chem_partials(c, ph, q0, fs, &dphi, &dfs, &dcos);
+  const double lphi = lap6(g, a.phi, x, y, n), lphi0 = lap6(g, a.phi0, x, y, n);
+  const double lfs = lap6(g, a.fs, x, y, n);
+  const double mu = chem_local(c, ph, q0, fs) - c.klap * (lphi + c.cos_th * lphi0 + c.cos_ps * lfs);
+  a.acc[n] += mub * (dcos - c.klap * lphi0) * a.dcos_dtheta;
+  a.acc[P + n] += mub * mu / c.sigma;
+}
+
+cudaError_t launch_phase_adjoint_fields(const PhaseAdjArgs& a, cudaStream_t s);
+cudaError_t launch_phase_adjoint_seed(const PhaseAdjArgs& a, cudaStream_t s);
+cudaError_t launch_phase_adjoint_step(const PhaseAdjArgs& a, cudaStream_t s);
+cudaError_t launch_phase_adjoint_init(const PhaseAdjArgs& a, cudaStream_t s);
+
 }  // namespace lbmk

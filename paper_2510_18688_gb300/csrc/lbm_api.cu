@@ -833,6 +833,153 @@ extern "C" int lbm_adjoint_frozen_fraction(lbm_ctx* c, int64_t nsteps, int every
 }
 
 // ---------------------------------------------------------------------------
+// reverse mode: an interface crossing of a phase-field run and its gradient
+// ---------------------------------------------------------------------------
+
+extern "C" int lbm_adjoint_crossing(lbm_ctx* c, int64_t nsteps, int every, int axis, int index,
+                                    double* pos_out, double* grad, void* stream) {
+  if (!c) return LBM_ERR_ARG;
+  if (!pos_out || !grad) return fail(c, LBM_ERR_ARG, "null output%s");
+  if (nsteps < 1 || every < 1) return fail(c, LBM_ERR_ARG, "nsteps and the checkpoint interval must be >= 1%s");
+  if ((axis != 0 && axis != 1) || index < 0 || index >= (axis == 0 ? c->p.ny : c->p.nx))
+    return fail(c, LBM_ERR_ARG, "axis must be 0 or 1 and index a line of the grid%s");
+  if (!c->have_geometry) return fail(c, LBM_ERR_STATE, "adjoint before lbm_set_geometry%s");
+  if (c->p.precision != LBM_FP64 || c->p.lattices != LBM_LAT_PHASE || !(c->p.sigma > 0.0))
+    return fail(c, LBM_ERR_UNSUPPORTED,
+                "the phase-field adjoint covers FP64 contexts with the phase-field lattice alone "
+                "and sigma > 0%s");
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t P = (size_t)c->g.plane;
+  const size_t gN = 9 * P, lN = lbmk::NLAG * P, stN = gN + lN;  // doubles per stored state
+  const int64_t nck = (nsteps + every - 1) / every;
+  const int64_t seglen = std::min<int64_t>(every, nsteps);
+  // work planes: phi, fs, phib, fsb, 9 gs, 2 x 9 adjoint populations
+  const size_t wN = (4 + 9 + 18) * P;
+  double *ck = nullptr, *seg = nullptr, *wk = nullptr, *acc = nullptr, *dout = nullptr,
+         *fin = nullptr;
+  cudaError_t e = cudaMalloc(&ck, nck * stN * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&seg, seglen * stN * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&wk, wN * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&acc, lbmk::ADJ_NACC * P * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&dout, (lbmk::ADJ_NACC + 1) * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&fin, (27 + lbmk::NLAG) * P * sizeof(double));
+  auto release = [&]() {
+    for (double* p : {ck, seg, wk, acc, dout, fin})
+      if (p) cudaFree(p);
+  };
+  if (e != cudaSuccess) {
+    release();
+    return cuda_fail(c, e, "adjoint allocation");
+  }
+  auto gplanes = [&](int par) { return (double*)c->pop[par] + 9 * P; };
+  auto save = [&](double* dst) {
+    cudaError_t r = cudaMemcpyAsync(dst, gplanes(c->cur), gN * sizeof(double),
+                                    cudaMemcpyDeviceToDevice, s);
+    if (r == cudaSuccess)
+      r = cudaMemcpyAsync(dst + gN, c->lag[c->cur], lN * sizeof(double), cudaMemcpyDeviceToDevice, s);
+    return r;
+  };
+  int st = LBM_OK;
+  const int64_t step0 = c->step;
+  std::vector<int> ckpar((size_t)nck);
+  for (int64_t k = 0; k < nsteps && e == cudaSuccess && st == LBM_OK; k++) {
+    if (k % every == 0) {
+      ckpar[(size_t)(k / every)] = c->cur;
+      e = save(ck + (k / every) * stN);
+    }
+    if (e == cudaSuccess) st = lbm_step(c, 1, s);
+  }
+  const int parN = c->cur;
+  if (e == cudaSuccess && st == LBM_OK)
+    e = cudaMemcpyAsync(fin, c->pop[parN], 27 * P * sizeof(double), cudaMemcpyDeviceToDevice, s);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(fin + 27 * P, c->lag[parN], lN * sizeof(double), cudaMemcpyDeviceToDevice, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(acc, 0, lbmk::ADJ_NACC * P * sizeof(double), s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(wk, 0, wN * sizeof(double), s);
+  const double pi = 3.14159265358979323846;
+  double* lb[2] = {wk + 13 * P, wk + 22 * P};
+  lbmk::PhaseAdjArgs a;
+  std::memset(&a, 0, sizeof(a));
+  a.g = c->g;
+  a.c = c->cd;
+  a.phi0 = (const double*)c->phi0;
+  a.phi = wk;
+  a.fs = wk + P;
+  a.phib = wk + 2 * P;
+  a.fsb = wk + 3 * P;
+  a.gs = wk + 4 * P;
+  a.acc = acc;
+  a.dcos_dtheta = -std::sin(c->p.theta_deg * pi / 180.0) * (pi / 180.0);
+  a.axis = axis;
+  a.index = index;
+  a.out = dout + lbmk::ADJ_NACC;
+  int cur_adj = 0;
+  // seed: the crossing on the final state
+  if (e == cudaSuccess && st == LBM_OK) {
+    a.gpop = gplanes(parN);
+    a.lag = (const double*)c->lag[parN];
+    a.lam_out = lb[0];
+    e = lbmk::launch_phase_adjoint_fields(a, s);
+    if (e == cudaSuccess) e = lbmk::launch_phase_adjoint_seed(a, s);
+  }
+  // reverse sweep: recompute each segment from its checkpoint, then step back
+  for (int64_t sg = nck - 1; sg >= 0 && e == cudaSuccess && st == LBM_OK; sg--) {
+    const int64_t k0 = sg * every, k1 = std::min<int64_t>(k0 + every, nsteps);
+    const int par = ckpar[(size_t)sg];
+    e = cudaMemcpyAsync(gplanes(par), ck + sg * stN, gN * sizeof(double),
+                        cudaMemcpyDeviceToDevice, s);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(c->lag[par], ck + sg * stN + gN, lN * sizeof(double),
+                          cudaMemcpyDeviceToDevice, s);
+    c->cur = par;
+    c->step = step0 + k0;
+    c->gen++;
+    for (int64_t j = 0; j < k1 - k0 && e == cudaSuccess && st == LBM_OK; j++) {
+      e = save(seg + j * stN);
+      if (e == cudaSuccess) st = lbm_step(c, 1, s);
+    }
+    for (int64_t j = k1 - k0 - 1; j >= 0 && e == cudaSuccess && st == LBM_OK; j--) {
+      a.gpop = seg + j * stN;
+      a.lag = seg + j * stN + gN;
+      a.lam_in = lb[cur_adj];
+      a.lam_out = lb[cur_adj ^ 1];
+      e = lbmk::launch_phase_adjoint_fields(a, s);
+      if (e == cudaSuccess) e = cudaMemsetAsync(a.phib, 0, 2 * P * sizeof(double), s);
+      if (e == cudaSuccess) e = lbmk::launch_phase_adjoint_step(a, s);
+      cur_adj ^= 1;
+    }
+  }
+  // a run from set_geometry's state: add that state's dependence on theta
+  // and sigma (phi and fs of checkpoint 0 are still in the work planes)
+  if (e == cudaSuccess && st == LBM_OK && step0 == 0) {
+    a.lam_in = lb[cur_adj];
+    e = lbmk::launch_phase_adjoint_init(a, s);
+  }
+  double hg[lbmk::ADJ_NACC + 1] = {0};
+  if (e == cudaSuccess && st == LBM_OK) e = lbmk::launch_adjoint_reduce(acc, c->g, dout, s);
+  if (e == cudaSuccess && st == LBM_OK)
+    e = cudaMemcpyAsync(hg, dout, sizeof(hg), cudaMemcpyDeviceToHost, s);
+  // the context ends at the final state, as after lbm_step(nsteps)
+  if (e == cudaSuccess && st == LBM_OK)
+    e = cudaMemcpyAsync(c->pop[parN], fin, 27 * P * sizeof(double), cudaMemcpyDeviceToDevice, s);
+  if (e == cudaSuccess && st == LBM_OK)
+    e = cudaMemcpyAsync(c->lag[parN], fin + 27 * P, lN * sizeof(double), cudaMemcpyDeviceToDevice, s);
+  c->cur = parN;
+  c->step = step0 + nsteps;
+  c->gen++;
+  if (e == cudaSuccess && st == LBM_OK) st = lbm_compute_diagnostics(c, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  release();
+  if (e != cudaSuccess) return cuda_fail(c, e, "adjoint");
+  if (st != LBM_OK) return st;
+  *pos_out = hg[lbmk::ADJ_NACC];
+  grad[0] = hg[0];
+  grad[1] = hg[1];
+  c->last_stream = s;
+  return LBM_OK;
+}
+
+// ---------------------------------------------------------------------------
 // autotuning of the step form on the context's own grid
 // ---------------------------------------------------------------------------
 

@@ -60,7 +60,8 @@ EXPORTS = ("lbm_create", "lbm_set_geometry", "lbm_step", "lbm_read_fields",
            "lbm_status_string", "lbm_destroy", "lbm_diagnostics_noalloc",
            "lbm_batch_create", "lbm_batch_step", "lbm_batch_destroy", "lbm_probe_fma_rate",
            "lbm_read_crossings", "lbm_read_tangent_fields", "lbm_read_tangent_diagnostics",
-           "lbm_read_crossings_tangent", "lbm_autotune", "lbm_adjoint_frozen_fraction")
+           "lbm_read_crossings_tangent", "lbm_autotune", "lbm_adjoint_frozen_fraction",
+           "lbm_adjoint_crossing")
 
 _lib = None
 
@@ -104,12 +105,15 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     L.lbm_read_tangent_diagnostics.argtypes = [vp, ctypes.POINTER(LbmDiag)]
     L.lbm_autotune.argtypes = [vp, ctypes.c_int, vp, dp, ctypes.POINTER(ctypes.c_int)]
     L.lbm_adjoint_frozen_fraction.argtypes = [vp, ctypes.c_int64, ctypes.c_int, dp, dp, vp]
+    L.lbm_adjoint_crossing.argtypes = [vp, ctypes.c_int64, ctypes.c_int, ctypes.c_int,
+                                       ctypes.c_int, dp, dp, vp]
     for fn in ("lbm_create", "lbm_set_geometry", "lbm_step", "lbm_read_fields",
                "lbm_compute_diagnostics", "lbm_read_diagnostics", "lbm_state_size",
                "lbm_save_state", "lbm_load_state", "lbm_diagnostics_noalloc",
                "lbm_batch_create", "lbm_batch_step", "lbm_probe_fma_rate",
                "lbm_read_crossings", "lbm_read_crossings_tangent", "lbm_read_tangent_fields",
-               "lbm_read_tangent_diagnostics", "lbm_autotune", "lbm_adjoint_frozen_fraction"):
+               "lbm_read_tangent_diagnostics", "lbm_autotune", "lbm_adjoint_frozen_fraction",
+               "lbm_adjoint_crossing"):
         getattr(L, fn).restype = ctypes.c_int
     _lib = L
     return L
@@ -204,6 +208,17 @@ def lbm_adjoint_frozen_fraction(ctx, nsteps: int, every: int, stream=None):
     _check(ctx, load().lbm_adjoint_frozen_fraction(ctx, int(nsteps), int(every), ctypes.byref(ff),
                                                    grad, stream), "lbm_adjoint_frozen_fraction")
     return ff.value, list(grad)
+
+
+def lbm_adjoint_crossing(ctx, nsteps: int, every: int, axis: int, index: int, stream=None):
+    """(phi = 0 crossing along the line after nsteps steps, [d/dtheta_deg,
+    d/dsigma]); see include/lbm.h."""
+    pos = ctypes.c_double()
+    grad = (ctypes.c_double * 2)()
+    _check(ctx, load().lbm_adjoint_crossing(ctx, int(nsteps), int(every), int(axis), int(index),
+                                            ctypes.byref(pos), grad, stream),
+           "lbm_adjoint_crossing")
+    return pos.value, list(grad)
 
 
 VARIANTS = ("fused, periods >= 32", "fused, periods >= 256", "split, periods >= 32",
@@ -381,6 +396,12 @@ class Solver:
         """Advance nsteps and return (FF, its gradient) by reverse mode
         (enthalpy-lattice FP64 contexts; see lbm_adjoint_frozen_fraction)."""
         return lbm_adjoint_frozen_fraction(self.ctx, nsteps, every, _stream())
+
+    def adjoint_crossing(self, nsteps: int, axis: int, index: int, every: int = 64):
+        """Advance nsteps and return (the phi = 0 crossing along the line, its
+        gradient with respect to (theta_deg, sigma)) by reverse mode
+        (phase-field-only FP64 contexts; see lbm_adjoint_crossing)."""
+        return lbm_adjoint_crossing(self.ctx, nsteps, every, axis, index, _stream())
 
     def autotune(self, steps_per_trial: int = 64):
         """Pick the fastest step form for this grid (state unchanged)."""

@@ -329,3 +329,91 @@ def test_adjoint_rejects_other_contexts(env):
             s.adjoint_frozen_fraction(10, 5)
         assert e.value.status == -6
         s.close()
+
+
+def _phase_droplet(n=64):
+    """The droplet of _droplet with the phase-field lattice alone (fluid at
+    rest, no heat): its cap relaxes towards the contact angle by the
+    Cahn-Hilliard flux of Eqs. (18)-(21)."""
+    cfg, arr = W.sessile_droplet(n, seed=3, radius=n / 4, hs=n / 10, theta_deg=80.0, ste=0.3)
+    return dict(cfg, lattices=2), arr
+
+
+def test_phase_adjoint_gradient_equals_the_tangent_and_differences(env):
+    """The reverse sweep of the phase-field step gives the derivatives of an
+    interface crossing with respect to the contact angle and the surface
+    tension, from the initial fields: equal to the forward-mode tangent
+    (theta) and to central differences of the FP64 step.  Two lines: the
+    droplet's axis (the tip height, set by sigma; theta acts there only
+    through the slow Cahn-Hilliard relaxation of the cap) and a row just
+    above the substrate (the contact line, where the wetting terms of
+    Eq. (6) act)."""
+    O, lbm, S, torch = env
+    cfg, arr = _phase_droplet()
+    steps = 600
+    lines = ((1, cfg["nx"] // 2), (0, 9))
+
+    def pos_at(c, axis, index):
+        u = lbm.Solver(c, precision="fp64").set_geometry(arr).step(steps)
+        v = u.crossings(axis, index)[0]
+        u.close()
+        return v
+
+    for axis, index in lines:
+        s = lbm.Solver(cfg, precision="fp64").set_geometry(arr)
+        pos, grad = s.adjoint_crossing(steps, axis, index, every=50)
+        assert s.crossings(axis, index)[0] == pos
+        s.close()
+        t = lbm.Solver(cfg, precision="tangent", tangent={"theta_deg": 1.0}).set_geometry(arr)
+        t.step(steps)
+        pos_t, _, dpos_t, _ = t.crossings_tangent(axis, index)
+        t.close()
+        assert abs(pos_t - pos) <= 1e-12 * pos
+        ht, hs = 1e-3, 1e-5 * cfg["sigma"]
+        fd_t = (pos_at(dict(cfg, theta_deg=cfg["theta_deg"] + ht), axis, index)
+                - pos_at(dict(cfg, theta_deg=cfg["theta_deg"] - ht), axis, index)) / (2 * ht)
+        fd_s = (pos_at(dict(cfg, sigma=cfg["sigma"] + hs), axis, index)
+                - pos_at(dict(cfg, sigma=cfg["sigma"] - hs), axis, index)) / (2 * hs)
+        print(f"\nline {axis},{index}: crossing {pos:.8f}; d/dtheta adjoint {grad[0]:.10e} "
+              f"tangent {dpos_t:.10e} FD {fd_t:.10e}; d/dsigma adjoint {grad[1]:.10e} FD {fd_s:.10e}")
+        assert abs(grad[0] - dpos_t) <= 1e-9 * abs(dpos_t)
+        assert abs(grad[1] - fd_s) <= 1e-4 * abs(fd_s)
+        if axis == 0:
+            # the contact line moves with theta (slowly: the fluid is at
+            # rest), four orders of magnitude more than the tip
+            assert abs(grad[0]) > 1e-6
+            assert abs(grad[0] - fd_t) <= 1e-4 * abs(fd_t)
+
+
+def test_phase_adjoint_checkpoints_final_state_and_rejections(env):
+    """The checkpoint interval does not change the result; the context ends
+    in the state of plain steps; other contexts are refused."""
+    O, lbm, S, torch = env
+    cfg, arr = _phase_droplet()
+    steps, col = 120, cfg["nx"] // 2
+    out = []
+    for every in (1, 17, 120):
+        s = lbm.Solver(cfg, precision="fp64").set_geometry(arr)
+        out.append(s.adjoint_crossing(steps, 1, col, every=every))
+        if every == 17:
+            f_adj = s.fields()
+            assert s.steps_done == steps
+        s.close()
+    assert all(o == out[0] for o in out[1:]), out
+    plain = lbm.Solver(cfg, precision="fp64").set_geometry(arr).step(steps)
+    f_plain = plain.fields()
+    for k in FIELDS:
+        assert np.array_equal(f_adj[k], f_plain[k]), k
+    plain.close()
+    for c, prec in ((cfg, "fp32"), (dict(cfg, lattices=7), "fp64"), (dict(cfg, sigma=0.0), "fp64")):
+        s = lbm.Solver(c, precision=prec).set_geometry(arr)
+        with pytest.raises(lbm.LbmError) as e:
+            s.adjoint_crossing(10, 1, col, 5)
+        assert e.value.status == -6
+        s.close()
+    s = lbm.Solver(cfg, precision="fp64").set_geometry(arr)
+    for axis, index in ((1, cfg["nx"]), (0, cfg["ny"]), (2, 0), (0, -1)):
+        with pytest.raises(lbm.LbmError) as e:
+            s.adjoint_crossing(10, axis, index, 5)
+        assert e.value.status == -1
+    s.close()
