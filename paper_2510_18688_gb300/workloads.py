@@ -313,3 +313,143 @@ def random_state(nx, ny, seed=0, lattices=ALL, bc=None, n_blobs=3, mushy=True):
                     T_cold=-0.8, lattices=lattices)
     p["lambda_s"] = 0.3
     return p, _arrays(phi0, phi, T, fl, mask)
+
+
+# ---------------------------------------------------------------------------
+# three-dimensional (D3Q19) inputs: arrays are [nz, ny, nx], x fastest; the
+# parameter dictionary adds nz, gz, and six boundary types and wall
+# temperatures (x_lo, x_hi, y_lo, y_hi, z_lo, z_hi)
+# ---------------------------------------------------------------------------
+
+def extrude_z(wl, nz: int):
+    """A two-dimensional workload repeated along a periodic z axis."""
+    cfg, arr = wl
+    p = dict(cfg, nz=int(nz), gz=0.0, bc=tuple(cfg["bc"]) + ("periodic", "periodic"),
+             T_wall=tuple(cfg["T_wall"]) + (0.0, 0.0))
+    out = {k: np.ascontiguousarray(np.broadcast_to(v, (nz,) + v.shape)) for k, v in arr.items()}
+    return p, out
+
+
+def _grid3(nx: int, ny: int, nz: int):
+    x = np.arange(nx, dtype=np.float64) + 0.5
+    y = np.arange(ny, dtype=np.float64) + 0.5
+    z = np.arange(nz, dtype=np.float64) + 0.5
+    Z, Y, X = np.meshgrid(z, y, x, indexing="ij")  # each [nz, ny, nx]
+    return X, Y, Z
+
+
+def random_state3(nx, ny, nz, seed=0, lattices=ALL, bc=None, n_blobs=3, mushy=True):
+    """Small seeded three-phase state in 3-D that exercises every branch, as
+    random_state does in 2-D: solid blobs, liquid drops and gas, temperatures
+    on both sides of T_m with mushy nodes, random contact angle, gravity in
+    all three axes and a cold mask."""
+    r = rng(seed)
+    if bc is None:
+        bc = [("periodic", "periodic", "periodic", "periodic", "dirichlet", "adiabatic"),
+              ("dirichlet", "adiabatic", "periodic", "periodic", "periodic", "periodic"),
+              ("periodic", "periodic", "periodic", "periodic", "periodic", "periodic"),
+              ("dirichlet", "dirichlet", "adiabatic", "dirichlet", "adiabatic", "adiabatic")][seed % 4]
+    X, Y, Z = _grid3(nx, ny, nz)
+    eps = 4.0
+    per = (bc[0] == "periodic", bc[2] == "periodic", bc[4] == "periodic")
+
+    def dist(cx, cy, cz):
+        d = []
+        for V, c, n, pr in ((X, cx, nx, per[0]), (Y, cy, ny, per[1]), (Z, cz, nz, per[2])):
+            a = np.abs(V - c)
+            d.append(np.minimum(a, n - a) if pr else a)
+        return np.sqrt(d[0] ** 2 + d[1] ** 2 + d[2] ** 2)
+
+    shape = (nz, ny, nx)
+    phi0 = np.zeros(shape)
+    dl = np.full(shape, -1e30)
+    m = min(nx, ny, nz)
+    for _ in range(n_blobs):
+        c = (r.uniform(0, nx), r.uniform(0, ny), r.uniform(0, nz))
+        rad = r.uniform(2.0, max(3.0, m / 3.0))
+        phi0 = np.maximum(phi0, 0.5 + 0.5 * np.tanh(2.0 * (rad - dist(*c)) / eps))
+        c = (r.uniform(0, nx), r.uniform(0, ny), r.uniform(0, nz))
+        rad = r.uniform(3.0, max(4.0, m / 2.0))
+        dl = np.maximum(dl, rad - dist(*c))
+    phi = (1.0 - phi0) * np.tanh(2.0 * dl / eps)
+    T = (0.3 * np.sin(2 * np.pi * X / nx * r.integers(1, 3)) + 0.2 * r.standard_normal()
+         + 0.05 * np.cos(2 * np.pi * Y / ny) + 0.05 * np.sin(2 * np.pi * Z / nz))
+    T = np.where(phi < 0.9, np.maximum(T, 0.1), T)
+    fl = np.where(T < 0.0, 0.0, 1.0)
+    if mushy:
+        band = np.abs(T) < 0.05
+        fl = np.where(band, 0.5 + T / 0.1, fl)
+        T = np.where(band, 0.0, T)
+    mask = (phi0 > 0.7) & (r.uniform(size=shape) < 0.5)
+    p = base_params(nx, ny, rho_s=float(r.uniform(0.85, 1.1)), cp_s=0.8, lambda_l=0.12,
+                    latent=latent_from_stefan(float(r.uniform(0.1, 0.5))),
+                    theta_deg=float(r.uniform(40.0, 140.0)),
+                    psi_deg=float(r.uniform(70.0, 110.0)),
+                    gx=float(r.uniform(-1e-6, 1e-6)), gy=float(r.uniform(-1e-6, 1e-6)),
+                    bc=bc, T_wall=tuple(float(v) for v in r.uniform(-1.0, 0.5, size=6)),
+                    T_cold=-0.8, lattices=lattices)
+    p["nz"] = int(nz)
+    p["gz"] = float(r.uniform(-1e-6, 1e-6))
+    p["lambda_s"] = 0.3
+    return p, _arrays(phi0, phi, T, fl, mask)
+
+
+def _self_affine_pair(r, n: int, std: float, hurst: float, mismatch: float):
+    """Two periodic n x n rough surfaces with standard deviation std whose
+    Fourier modes share phases at wavelengths longer than `mismatch` and are
+    independent below it (spectral synthesis of a self-affine surface with
+    Hurst exponent H: amplitude ~ k^-(1+H))."""
+    k = np.fft.fftfreq(n) * n
+    KX, KY = np.meshgrid(k, k)
+    kk = np.hypot(KX, KY)
+    amp = np.where(kk > 0, np.maximum(kk, 1e-12) ** (-(1.0 + hurst)), 0.0)
+    ph_shared = r.uniform(0, 2 * np.pi, size=(n, n))
+    ph_own = r.uniform(0, 2 * np.pi, size=(2, n, n))
+    long_wave = kk < n / mismatch
+    out = []
+    for s in range(2):
+        ph = np.where(long_wave, ph_shared, ph_own[s])
+        h = np.real(np.fft.ifft2(amp * np.exp(1j * ph)))
+        out.append(h / h.std() * std)
+    return out
+
+
+def rough_fracture(nx=256, ny=128, nz=30, seed=0, fd=2.25, std=2.5, mismatch=30.0,
+                   aperture=12.0, theta_deg=60.0, T0=0.1, T_w=-1.0, ste=0.1, eps=4.0):
+    """Freezing in a rough fracture (Sec. 4.5 shape): a 128-wide self-affine
+    fracture of fractal dimension fd (Hurst exponent 3 - fd), standard
+    deviation std and mismatch length `mismatch`, repeated once along x; the
+    solid (phi0) lies outside the aperture along z.  A liquid column fills
+    x < 0.75 Lx with three gas bubbles of radii 0.075, 0.05 and 0.01 Lx at
+    (0.25, 0.25, 0.5), (0.5, 0.5, 0.5) and (0.25, 0.75, 0.5) (Lx, Ly, Lz);
+    T = T0 everywhere, the wall at x = 0 at T_w (the far wall adiabatic),
+    periodic in y and z.  The fracture surfaces are synthetic stand-ins for
+    the paper's generated fractures, from numpy's seeded generator."""
+    r = rng(seed)
+    tile = ny
+    lo, hi = _self_affine_pair(r, tile, std, 3.0 - fd, mismatch)
+    reps = -(-nx // tile)
+    lo = np.tile(lo, (1, reps))[:, :nx]   # [ny, nx]
+    hi = np.tile(hi, (1, reps))[:, :nx]
+    zc = nz / 2.0
+    z_lo = zc - aperture / 2.0 + lo
+    z_hi = np.maximum(zc + aperture / 2.0 + hi, z_lo + 2.0)
+    X, Y, Z = _grid3(nx, ny, nz)
+    d_solid = np.maximum(z_lo[None] - Z, Z - z_hi[None])  # > 0 inside the rock
+    phi0 = 0.5 + 0.5 * np.tanh(2.0 * d_solid / eps)
+    Lx, Ly, Lz = float(nx), float(ny), float(nz)
+    dl = 0.75 * Lx - X
+    for (cx, cy, cz), rad in (((0.25, 0.25, 0.5), 0.075), ((0.5, 0.5, 0.5), 0.05),
+                              ((0.25, 0.75, 0.5), 0.01)):
+        d = np.sqrt((X - cx * Lx) ** 2 + (Y - cy * Ly) ** 2 + (Z - cz * Lz) ** 2)
+        dl = np.minimum(dl, d - rad * Lx)
+    phi = (1.0 - phi0) * np.tanh(2.0 * dl / eps)
+    p = base_params(nx, ny, rho_s=0.9, cp_s=0.5, lambda_l=0.1, eps=eps, theta_deg=theta_deg,
+                    latent=latent_from_stefan(ste, 1.0, T_w), T_cold=T_w,
+                    bc=("dirichlet", "adiabatic", "periodic", "periodic", "periodic", "periodic"),
+                    T_wall=(T_w, 0.0, 0.0, 0.0, 0.0, 0.0))
+    p["lambda_s"] = 0.37
+    p["nz"] = int(nz)
+    p["gz"] = 0.0
+    shape = (nz, ny, nx)
+    return p, _arrays(phi0, phi, np.full(shape, T0), np.ones(shape))
