@@ -412,6 +412,76 @@ int lbm_diagnostics_noalloc(const lbm_params* params, const void* pops, const vo
  * LBM_ERR_CUDA. */
 int lbm_probe_fma_rate(int precision, double* flops_per_s, void* stream);
 
+/* ------------------------------------------------------------------------
+ * Three-dimensional contexts: the same coupled step on the D3Q19 lattice of
+ * Sec. 3.1 (Eq. (13): weights 1/3, 1/18 for the six axes, 1/36 for the
+ * twelve edge diagonals), as used for the rough-fracture case of Sec. 4.5.
+ * Every lattice sum of Eqs. (11)-(28) runs over the 19 velocities, vectors
+ * (velocity, forces, phi u, gradients) carry a z component, and the
+ * isotropic stencils use the D3Q19 weights.  A link that leaves through an
+ * edge or a corner of the box is decided by the first wall it crosses in the
+ * order x, y, z.  Grid arrays are [nz][ny][nx] with x fastest.  Precisions:
+ * LBM_FP32 and LBM_FP64 (others: LBM_ERR_UNSUPPORTED); base.diag_every and
+ * the tan_* fields are ignored.  A step is two kernels (the per-node local
+ * state, then stencils, collisions and streaming).  The conventions of the
+ * 2-D calls apply (status codes, `where`, streams, ownership).
+ * ---------------------------------------------------------------------- */
+typedef struct lbm3_ctx lbm3_ctx;
+
+typedef struct {
+  lbm_params base;    /* nx, ny, precision, lattices, physics; base.bc and
+                         base.T_wall give the x and y faces, (gx, gy) the
+                         x and y components of the body force */
+  int32_t nz;         /* >= 2 */
+  int32_t bc_z[2];    /* z-low, z-high (LBM_BC_*; periodic in pairs) */
+  double T_wall_z[2]; /* used where bc_z[k] == LBM_BC_DIRICHLET */
+  double gz;          /* z component of the body force G = rho g */
+} lbm3_params;
+
+/* Fields of lbm3_read_fields: bit k selects out[k], in this order. */
+enum {
+  LBM3_F_PHI = 1u << 0, LBM3_F_FS = 1u << 1, LBM3_F_FL = 1u << 2, LBM3_F_T = 1u << 3,
+  LBM3_F_RHOH = 1u << 4, LBM3_F_P = 1u << 5, LBM3_F_UX = 1u << 6, LBM3_F_UY = 1u << 7,
+  LBM3_F_UZ = 1u << 8, LBM3_F_RHO = 1u << 9, LBM3_F_MU = 1u << 10, LBM3_F_W = 1u << 11,
+  LBM3_F_MDOT = 1u << 12
+};
+#define LBM3_NUM_FIELDS 13
+
+/* Validates *params as lbm_create does (plus nz, bc_z and the size limit:
+ * 57 population planes must fit 31-bit offsets) and allocates the device
+ * state (two population buffers of 57 planes, two lag buffers of 7 planes,
+ * 8 local planes, phi0, the mask, and a 13-plane FP64 read-out buffer).
+ * Errors: LBM_ERR_ARG, LBM_ERR_PARAM, LBM_ERR_UNSUPPORTED (precision),
+ * LBM_ERR_OOM, LBM_ERR_CUDA. */
+int lbm3_create(const lbm3_params* params, lbm3_ctx** out);
+
+/* As lbm_set_geometry, with [nz][ny][nx] arrays. */
+int lbm3_set_geometry(lbm3_ctx* ctx, const double* phi0, const uint8_t* cold_mask,
+                      const double* phi, const double* T, const double* fl, int where,
+                      void* stream);
+
+/* Enqueues nsteps >= 0 steps on `stream` (two kernel launches per step).
+ * Errors: LBM_ERR_STATE before lbm3_set_geometry, LBM_ERR_ARG, LBM_ERR_CUDA. */
+int lbm3_step(lbm3_ctx* ctx, int64_t nsteps, void* stream);
+
+/* The fields selected by field_mask (LBM3_F_*) of the current state, as
+ * [nz][ny][nx] doubles in out[k]; host outputs synchronise `stream`. */
+int lbm3_read_fields(lbm3_ctx* ctx, uint32_t field_mask, double* const* out, int where,
+                     void* stream);
+
+/* The FP64 diagnostic sums of the current state (lbm_diag; the kinetic
+ * energy with all three velocity components).  Synchronises `stream`. */
+int lbm3_diagnostics(lbm3_ctx* ctx, lbm_diag* out, void* stream);
+
+int64_t lbm3_step_count(const lbm3_ctx* ctx);
+const char* lbm3_last_error(const lbm3_ctx* ctx);
+void lbm3_destroy(lbm3_ctx* ctx);
+
+/* The lattice the kernels use: c[3 i + a] = component a of velocity i and
+ * w[i] its weight, i = 0 ... 18 in the order of Eq. (13).  Host only; needs
+ * no device. */
+void lbm3_lattice(int32_t* c, double* w);
+
 #ifdef __cplusplus
 }
 #endif

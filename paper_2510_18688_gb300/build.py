@@ -30,6 +30,7 @@ UNITS = {
     "lbm_adjoint.cu": [],
     "lbm_static.cu": [],
     "lbm_probe.cu": [],
+    "lbm3d.cu": [],
 }
 
 

@@ -61,7 +61,10 @@ EXPORTS = ("lbm_create", "lbm_set_geometry", "lbm_step", "lbm_read_fields",
            "lbm_batch_create", "lbm_batch_step", "lbm_batch_destroy", "lbm_probe_fma_rate",
            "lbm_read_crossings", "lbm_read_tangent_fields", "lbm_read_tangent_diagnostics",
            "lbm_read_crossings_tangent", "lbm_autotune", "lbm_adjoint_frozen_fraction",
-           "lbm_adjoint_crossing")
+           "lbm_adjoint_crossing", "lbm3_create", "lbm3_set_geometry", "lbm3_step",
+           "lbm3_read_fields", "lbm3_diagnostics", "lbm3_step_count", "lbm3_last_error",
+           "lbm3_destroy", "lbm3_lattice")
+FIELDS3 = ("phi", "fs", "fl", "T", "rhoH", "p", "ux", "uy", "uz", "rho", "mu", "w", "mdot")
 
 _lib = None
 
@@ -107,6 +110,22 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     L.lbm_adjoint_frozen_fraction.argtypes = [vp, ctypes.c_int64, ctypes.c_int, dp, dp, vp]
     L.lbm_adjoint_crossing.argtypes = [vp, ctypes.c_int64, ctypes.c_int, ctypes.c_int,
                                        ctypes.c_int, dp, dp, vp]
+    L.lbm3_create.argtypes = [ctypes.POINTER(Lbm3Params), ctypes.POINTER(vp)]
+    L.lbm3_set_geometry.argtypes = [vp, vp, vp, vp, vp, vp, ctypes.c_int, vp]
+    L.lbm3_step.argtypes = [vp, ctypes.c_int64, vp]
+    L.lbm3_read_fields.argtypes = [vp, ctypes.c_uint32, ctypes.POINTER(vp), ctypes.c_int, vp]
+    L.lbm3_diagnostics.argtypes = [vp, ctypes.POINTER(LbmDiag), vp]
+    L.lbm3_step_count.argtypes = [vp]
+    L.lbm3_step_count.restype = ctypes.c_int64
+    L.lbm3_last_error.argtypes = [vp]
+    L.lbm3_last_error.restype = ctypes.c_char_p
+    L.lbm3_destroy.argtypes = [vp]
+    L.lbm3_destroy.restype = None
+    L.lbm3_lattice.argtypes = [ctypes.POINTER(ctypes.c_int32), dp]
+    L.lbm3_lattice.restype = None
+    for fn in ("lbm3_create", "lbm3_set_geometry", "lbm3_step", "lbm3_read_fields",
+               "lbm3_diagnostics"):
+        getattr(L, fn).restype = ctypes.c_int
     for fn in ("lbm_create", "lbm_set_geometry", "lbm_step", "lbm_read_fields",
                "lbm_compute_diagnostics", "lbm_read_diagnostics", "lbm_state_size",
                "lbm_save_state", "lbm_load_state", "lbm_diagnostics_noalloc",
@@ -117,6 +136,11 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         getattr(L, fn).restype = ctypes.c_int
     _lib = L
     return L
+
+
+class Lbm3Params(ctypes.Structure):
+    _fields_ = [("base", LbmParams), ("nz", ctypes.c_int32), ("bc_z", ctypes.c_int32 * 2),
+                ("T_wall_z", ctypes.c_double * 2), ("gz", ctypes.c_double)]
 
 
 class LbmError(RuntimeError):
@@ -470,3 +494,147 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+# --- three-dimensional (D3Q19) contexts ---------------------------------------
+
+def make_params3(cfg: dict, precision: str = "fp32") -> Lbm3Params:
+    """lbm3_params of a 3-D workload dict (six boundary types and wall
+    temperatures: x_lo, x_hi, y_lo, y_hi, z_lo, z_hi; nz; gz)."""
+    base = make_params(dict(cfg, bc=tuple(cfg["bc"][:4]), T_wall=tuple(cfg["T_wall"][:4])),
+                       precision)
+    p = Lbm3Params()
+    p.base = base
+    p.nz = int(cfg["nz"])
+    for k in range(2):
+        p.bc_z[k] = BC[cfg["bc"][4 + k]]
+        p.T_wall_z[k] = float(cfg["T_wall"][4 + k])
+    p.gz = float(cfg.get("gz", 0.0))
+    return p
+
+
+def _check3(ctx, st, what):
+    if st != LBM_OK:
+        msg = load().lbm3_last_error(ctx).decode() if ctx else ""
+        raise LbmError(st, f"{what}: {load().lbm_status_string(st).decode()} {msg}")
+
+
+def lbm3_create(params: Lbm3Params) -> ctypes.c_void_p:
+    h = ctypes.c_void_p()
+    _check3(None, load().lbm3_create(ctypes.byref(params), ctypes.byref(h)), "lbm3_create")
+    return h
+
+
+def lbm3_set_geometry(ctx, phi0, cold_mask, phi, T, fl, where, stream=None):
+    _check3(ctx, load().lbm3_set_geometry(ctx, phi0, cold_mask, phi, T, fl, where, stream),
+            "lbm3_set_geometry")
+
+
+def lbm3_step(ctx, nsteps: int, stream=None):
+    _check3(ctx, load().lbm3_step(ctx, int(nsteps), stream), "lbm3_step")
+
+
+def lbm3_read_fields(ctx, field_mask: int, out_ptrs, where, stream=None):
+    arr = (ctypes.c_void_p * len(FIELDS3))(*[p or None for p in out_ptrs])
+    _check3(ctx, load().lbm3_read_fields(ctx, field_mask, arr, where, stream), "lbm3_read_fields")
+
+
+def lbm3_diagnostics(ctx, stream=None) -> dict:
+    """The diagnostic sums (a non-finite state is reported in 'nonfinite',
+    not raised)."""
+    d = LbmDiag()
+    st = load().lbm3_diagnostics(ctx, ctypes.byref(d), stream)
+    if st not in (LBM_OK, LBM_ERR_NONFINITE):
+        _check3(ctx, st, "lbm3_diagnostics")
+    return {k: getattr(d, k) for k, _ in LbmDiag._fields_}
+
+
+def lbm3_step_count(ctx) -> int:
+    return int(load().lbm3_step_count(ctx))
+
+
+def lbm3_last_error(ctx) -> str:
+    return load().lbm3_last_error(ctx).decode()
+
+
+def lbm3_destroy(ctx):
+    load().lbm3_destroy(ctx)
+
+
+def lbm3_lattice():
+    """(c [19, 3], w [19]) of the library's D3Q19 lattice (host only)."""
+    c = (ctypes.c_int32 * 57)()
+    w = (ctypes.c_double * 19)()
+    load().lbm3_lattice(c, w)
+    return np.array(c[:]).reshape(19, 3), np.array(w[:])
+
+
+class Solver3:
+    """One three-dimensional (D3Q19) GPU context; arrays are [nz, ny, nx]."""
+
+    def __init__(self, cfg: dict, precision: str = "fp32"):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("Solver3 needs a CUDA device (no CPU path)")
+        if precision not in ("fp32", "fp64"):
+            raise ValueError("3-D contexts take fp32 or fp64")
+        load()
+        self.cfg = dict(cfg)
+        self.shape = (int(cfg["nz"]), int(cfg["ny"]), int(cfg["nx"]))
+        self.precision = precision
+        self.params = make_params3(cfg, precision)
+        self.ctx = lbm3_create(self.params)
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            lbm3_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_geometry(self, arrays: dict, on_device: bool = True):
+        import torch
+        keys = ("phi0", "phi", "T", "fl")
+        m = arrays.get("mask")
+        if on_device:
+            t = {k: torch.as_tensor(np.ascontiguousarray(arrays[k], dtype=np.float64),
+                                    device="cuda") for k in keys}
+            tm = None if m is None else torch.as_tensor(np.ascontiguousarray(m, dtype=np.uint8),
+                                                        device="cuda")
+            ptrs = [t[k].data_ptr() for k in keys]
+            mp, where = (None if tm is None else tm.data_ptr()), LBM_DEVICE
+        else:
+            h = {k: np.ascontiguousarray(arrays[k], dtype=np.float64) for k in keys}
+            hm = None if m is None else np.ascontiguousarray(m, dtype=np.uint8)
+            ptrs = [h[k].ctypes.data for k in keys]
+            mp, where = (None if hm is None else hm.ctypes.data), LBM_HOST
+        lbm3_set_geometry(self.ctx, ptrs[0], mp, ptrs[1], ptrs[2], ptrs[3], where, _stream())
+        if on_device:
+            torch.cuda.current_stream().synchronize()
+        return self
+
+    def step(self, n: int = 1):
+        lbm3_step(self.ctx, n, _stream())
+        return self
+
+    @property
+    def steps_done(self) -> int:
+        return lbm3_step_count(self.ctx)
+
+    def fields(self, names=FIELDS3) -> dict:
+        out = {k: np.empty(self.shape, dtype=np.float64) for k in names}
+        mask = 0
+        ptrs = [None] * len(FIELDS3)
+        for k in names:
+            i = FIELDS3.index(k)
+            mask |= 1 << i
+            ptrs[i] = out[k].ctypes.data
+        lbm3_read_fields(self.ctx, mask, ptrs, LBM_HOST, _stream())
+        return out
+
+    def diagnostics(self) -> dict:
+        return lbm3_diagnostics(self.ctx, _stream())

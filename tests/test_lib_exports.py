@@ -19,7 +19,7 @@ def lib():
 def _declared():
     src = open(os.path.join(ROOT, "include", "lbm.h")).read()
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    return sorted(set(re.findall(r"\b(lbm_[a-z_]+)\s*\(", src)))
+    return sorted(set(re.findall(r"\b(lbm3?_[a-z0-9_]+)\s*\(", src)))
 
 
 def test_header_declares_the_boundary():
@@ -64,3 +64,43 @@ def test_null_context_is_an_error_not_a_crash(lib):
     assert lib.lbm_step_count(None) == -1
     lib.lbm_destroy(None)
     assert lbm.LBM_OK == 0
+
+
+def test_3d_lattice_is_the_printed_d3q19(lib):
+    """The kernels' D3Q19 table (a host copy of the same constexpr
+    functions) against the velocity matrix and weights printed in Sec. 3.1."""
+    from fractions import Fraction
+    from paper_2510_18688_gb300 import lbm
+    c, w = lbm.lbm3_lattice()
+    rows = [l.split() for l in open(os.path.join(ROOT, "tests", "golden", "d3q19_lattice.txt"))
+            if l.strip() and not l.startswith("#")]
+    assert len(rows) == 19
+    for r in rows:
+        i = int(r[0])
+        assert tuple(c[i]) == (int(r[1]), int(r[2]), int(r[3]))
+        assert w[i] == float(Fraction(r[4]))
+
+
+def test_3d_create_rejects_invalid_parameters_without_gpu(lib):
+    from paper_2510_18688_gb300 import lbm, workloads as W
+    cfg, _ = W.random_state3(8, 6, 4, seed=2)
+    bad = [dict(nz=1), dict(nx=1), dict(mu_l=0.0),
+           dict(bc=("periodic",) * 4 + ("periodic", "dirichlet")),
+           dict(bc=("periodic",) * 4 + ("periodic", "sticky"))]
+    for b in bad:
+        c = dict(cfg, **b)
+        try:
+            p = lbm.make_params3(c)
+        except KeyError:
+            continue  # an unknown boundary name never reaches the library
+        h = ctypes.c_void_p()
+        st = lib.lbm3_create(ctypes.byref(p), ctypes.byref(h))
+        assert st in (-1, -2), (b, st)
+        assert not h.value
+    p = lbm.make_params3(cfg, "fp32")
+    p.base.precision = 2  # FP16 storage is not offered in 3-D
+    h = ctypes.c_void_p()
+    assert lib.lbm3_create(ctypes.byref(p), ctypes.byref(h)) == -6
+    assert lib.lbm3_step(None, 1, None) == -1
+    assert lib.lbm3_step_count(None) == -1
+    lib.lbm3_destroy(None)
