@@ -81,6 +81,20 @@ WORKLOADS = {
 }
 
 
+# three-dimensional (D3Q19) context lines: run by fracture_line
+WORKLOADS3 = {
+    "fracture256x128x30": "freezing in a rough fracture 256x128x30 (Sec. 4.5 shape: self-affine "
+                          "aperture, liquid column with three bubbles, cold wall at x = 0), "
+                          "D3Q19, 3 lattices",
+}
+
+
+def algorithmic_bytes_per_node3(esize: int) -> int:
+    """D3Q19: 57 populations read and written, 7 lag fields read and
+    written, phi0 read."""
+    return 2 * 57 * esize + 2 * 7 * esize + esize
+
+
 def algorithmic_bytes_per_node(esize: int, has_mask: bool, pop_bytes: int = 0) -> int:
     """27 populations read and written, 6 lag fields read and written, phi0
     read, mask byte read."""
@@ -363,6 +377,102 @@ def adjoint_line(args, rank, world, every: int = 64):
     print(json.dumps(line), flush=True)
 
 
+def fracture_line(args, rank, world):
+    """The D3Q19 step on the 256 x 128 x 30 rough fracture (FP32 or FP64).
+    Each step is two kernels (local state; stencils, collisions and
+    streaming); the state (57 planes, 224 MB in FP32 per buffer) is larger
+    than L2, so no flush is needed between steps.  The roofline is taken
+    over the whole step (both kernels) with the single-pass state traffic."""
+    import torch
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
+    from paper_2510_18688_gb300 import build, lbm, workloads as W
+    build.build()
+    lbm.load()
+    if args.precision not in ("fp32", "fp64"):
+        raise SystemExit("the 3-D workload takes --precision fp32 or fp64")
+    cfg, arr = W.rough_fracture(seed=rank)
+    n = cfg["nx"] * cfg["ny"] * cfg["nz"]
+    stream = torch.cuda.current_stream()
+    sptr = ctypes.c_void_p(stream.cuda_stream)
+    s = lbm.Solver3(cfg, args.precision).set_geometry(arr)
+    s.step(args.warmup)
+    torch.cuda.synchronize()
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    with ClockSampler(int(os.environ.get("LOCAL_RANK", 0))) as clk:
+        for k in range(args.steps):
+            starts[k].record(stream)
+            lbm.lbm3_step(s.ctx, 1, sptr)
+            ends[k].record(stream)
+        torch.cuda.synchronize()
+    times = np.array([a.elapsed_time(b) for a, b in zip(starts, ends)])
+    t_step = float(times.mean())
+    diag = s.diagnostics()
+
+    # end to end through the C ABI with host buffers: geometry upload from
+    # pinned memory, K steps, phi/fl/T download to pinned memory
+    def pinned(a, dtype):
+        t = torch.empty(a.shape, dtype=dtype, pin_memory=True)
+        t.numpy()[...] = a
+        return t
+
+    ht = {k: pinned(arr[k], torch.float64) for k in ("phi0", "phi", "T", "fl")}
+    ot = {k: torch.empty(arr["phi"].shape, dtype=torch.float64, pin_memory=True)
+          for k in ("phi", "fl", "T")}
+    fmask = sum(1 << lbm.FIELDS3.index(k) for k in ot)
+    ptrs = [ot[k].numpy().ctypes.data if k in ot else None for k in lbm.FIELDS3]
+    h = {k: v.numpy() for k, v in ht.items()}
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    lbm.lbm3_set_geometry(s.ctx, h["phi0"].ctypes.data, None, h["phi"].ctypes.data,
+                          h["T"].ctypes.data, h["fl"].ctypes.data, lbm.LBM_HOST, sptr)
+    lbm.lbm3_step(s.ctx, args.steps, sptr)
+    lbm.lbm3_read_fields(s.ctx, fmask, ptrs, lbm.LBM_HOST, sptr)
+    e2e_s = time.perf_counter() - t0
+    s.close()
+    if rank != 0:
+        return
+    esize = 8 if args.precision == "fp64" else 4
+    bpn = algorithmic_bytes_per_node3(esize)
+    peak, peak_src = measured_peak()
+    achieved = bpn * n / (t_step * 1e-3) / 1e9
+    line = {
+        "metric": METRIC, "value": n / (t_step * 1e-3) / 1e6 * world, "unit": "MLUPS",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_step,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": {"fp32": "f32", "fp64": "f64"}[args.precision], "data": "synthetic",
+        "config": {"workload": WORKLOADS3["fracture256x128x30"] + f", seed {rank}",
+                   "grid": [cfg["nx"], cfg["ny"], cfg["nz"]], "precision": args.precision,
+                   "l2": "not flushed: the state (57 population planes) is larger than L2",
+                   "parallelism": f"replicas x{world}"},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": None, "peak_source": peak_src,
+                     "bytes_per_node": bpn,
+                     "scope": "whole step (local-state and collide kernels together)"},
+        "gpu_launches": 2 * args.steps,
+        "e2e": {"value": n * args.steps / e2e_s / 1e6, "unit": "MLUPS",
+                "h2d_bytes_per_step": 4 * n * 8 / args.steps,
+                "d2h_bytes_per_step": 3 * n * 8 / args.steps},
+        "diag_last": {k: diag[k] for k in ("material_mass", "frozen_volume", "nonfinite", "step")},
+        "clocks": clk.summary(),
+    }
+    if not args.no_cpu_baseline:
+        from oracle import oracle3d as O3
+        cores = int(os.cpu_count() or 1)
+        o = O3.from_workload((cfg, arr))
+        o.step(1)
+        t0 = time.perf_counter()
+        k = 0
+        while time.perf_counter() - t0 < 12.0:
+            o.step(1)
+            k += 1
+        dt = time.perf_counter() - t0
+        line["cpu_baseline"] = {"value": n * k / dt / 1e6, "unit": "MLUPS", "cores": cores,
+                                "kind": "oracle",
+                                "sample": f"{k} full steps of the same 3-D workload (about 12 s)"}
+    print(json.dumps(line), flush=True)
+
+
 def cpu_baseline_sample(target_s: float = 12.0):
     """Time the oracle on the same workload for about target_s seconds."""
     from oracle import oracle as O
@@ -401,7 +511,8 @@ def main():
                     help="time a reverse-mode gradient against its forward run (FP64): heat, the "
                          "frozen fraction of the conduction column 2048 x 256 (enthalpy lattice "
                          "alone); phase, the tip height of the 512^2 droplet (phase field alone)")
-    ap.add_argument("--workload", default="droplet512", choices=sorted(WORKLOADS),
+    ap.add_argument("--workload", default="droplet512",
+                    choices=sorted(WORKLOADS) + sorted(WORKLOADS3),
                     help="droplet512 is the headline; the others are context lines")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
@@ -415,6 +526,9 @@ def main():
         return
     if args.back_to_back:
         back_to_back_line(args, rank, world)
+        return
+    if args.workload in WORKLOADS3:
+        fracture_line(args, rank, world)
         return
 
     import torch
