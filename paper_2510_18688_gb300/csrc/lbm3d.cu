@@ -51,7 +51,18 @@ using lbmk::BC_DIRICHLET;
 using lbmk::BC_PERIODIC;
 
 constexpr int Q = 19;
-constexpr int BX = 32, BY = 4, BZ = 2, NT = BX * BY * BZ;
+// thread block (x fastest) and the resident blocks per SM the FP32 collide
+// kernel is compiled for
+#ifndef LBM3_BY
+#define LBM3_BY 4
+#endif
+#ifndef LBM3_BZ
+#define LBM3_BZ 2
+#endif
+#ifndef LBM3_MINB_F32
+#define LBM3_MINB_F32 3
+#endif
+constexpr int BX = 32, BY = LBM3_BY, BZ = LBM3_BZ, NT = BX * BY * BZ;
 enum { L_FL = 0, L_W, L_P, L_PHUX, L_PHUY, L_PHUZ, L_Q, NLAG };
 enum { S_PHI = 0, S_FS, S_RHO, S_T, S_FL, S_MDOT, S_RHOH, S_W, NLOC };
 constexpr int NFIELD3 = 13;  // phi fs fl T rhoH p ux uy uz rho mu w mdot
@@ -338,7 +349,7 @@ __device__ __forceinline__ void collide_heat(const Args3<R>& a, R* out, int P, i
 }
 
 template <typename R, bool READ>
-__global__ void __launch_bounds__(NT) lbm3_collide_kernel(const Args3<R> a) {
+__global__ void __launch_bounds__(NT, (sizeof(R) == 4 ? LBM3_MINB_F32 : 2)) lbm3_collide_kernel(const Args3<R> a) {
   const Geom3& g = a.g;
   const Coef<R>& c = a.c;
   const int x = blockIdx.x * BX + threadIdx.x;
