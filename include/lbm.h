@@ -327,7 +327,8 @@ int lbm_adjoint_frozen_fraction(lbm_ctx* ctx, int64_t nsteps, int every, double*
  * potential, so its gradient is that of the whole run from the initial
  * fields.  One reverse sweep of hand-written adjoint kernels: pull through
  * the push and bounce-back, back through the collision to mu_phi, and the
- * transposed Laplacian stencils (a scatter) back to phi and fs; kinks of
+ * transposed Laplacian stencils (a gather in a fixed order: results are
+ * deterministic) back to phi and fs; kinks of
  * the clamps take the branch the forward step took.  Checkpoints as in
  * lbm_adjoint_frozen_fraction.  *pos is NaN (and the gradient zero) when
  * phi does not cross 0 along the line.  Synchronises `stream`.

@@ -34,8 +34,8 @@ cudaError_t launch_phase_adjoint_seed(const PhaseAdjArgs& a, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-// one reverse step: the scatter of part 1 accumulates into phib and fsb,
-// which the caller has zeroed
+// one reverse step: the node's own terms, then the gather of the stencil
+// transposes and the local chain
 cudaError_t launch_phase_adjoint_step(const PhaseAdjArgs& a, cudaStream_t s) {
   lbm_phase_adjoint1_kernel<<<grid_dims(a.g), block_dims(), 0, s>>>(a);
   lbm_phase_adjoint2_kernel<<<grid_dims(a.g), block_dims(), 0, s>>>(a);

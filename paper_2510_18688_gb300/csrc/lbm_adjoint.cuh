@@ -299,8 +299,9 @@ struct PhaseAdjArgs {
   double* __restrict__ fs;
   const double* __restrict__ lam_in;  // adjoint of the next state's 9 planes
   double* __restrict__ gs;            // 9 planes: adjoint of the post-collision populations
-  double* __restrict__ phib;          // adjoint of phi (accumulated, zeroed per step)
-  double* __restrict__ fsb;           // adjoint of fs (accumulated, zeroed per step)
+  double* __restrict__ phib;          // adjoint of phi: the node's own terms
+  double* __restrict__ fsb;           // adjoint of fs: the node's own terms
+  double* __restrict__ mub;           // adjoint of mu_phi
   double* __restrict__ lam_out;       // adjoint of this state's 9 planes
   double* __restrict__ acc;           // PADJ_NACC accumulator planes (+=)
   double dcos_dtheta;                 // d cos(theta) / d theta_deg
@@ -378,8 +379,10 @@ __device__ __forceinline__ void chem_partials(const Coef<double>& c, double ph, 
   *dcos = c.s3 * q0 * (3.0 * ph * ph + q0 * q0 - 1.0);
 }
 
-// Reverse step, part 1: pull the adjoint through the push, back through the
-// collision to mu_phi, and scatter mu_phi's adjoint over the stencils.
+// Reverse step, part 1: pull the adjoint through the push and back through
+// the collision to mu_phi; store mu_phi's adjoint and the terms of phi's and
+// fs's adjoints that come from the node itself (the collision's phi, the
+// local part of Eq. (6), the centre of the Laplacians).
 static __global__ void __launch_bounds__(NT) lbm_phase_adjoint1_kernel(const PhaseAdjArgs a) {
   const Geom& g = a.g;
   const Coef<double>& c = a.c;
@@ -406,34 +409,56 @@ static __global__ void __launch_bounds__(NT) lbm_phase_adjoint1_kernel(const Pha
   const double lphi = lap6(g, a.phi, x, y, n), lphi0 = lap6(g, a.phi0, x, y, n);
   const double lfs = lap6(g, a.fs, x, y, n);
   const double mu = chem_local(c, ph, q0, fs) - c.klap * (lphi + c.cos_th * lphi0 + c.cos_ps * lfs);
-  // own node: the collision's phi, the local part of mu, the centre of the Laplacians
   const double self = 6.0 * (1.0 - qw<double>(0));  // 6 sum_{i>0} w_i
-  atomicAdd(a.phib + n, itg * gb[0] + mub * dphi + c.klap * self * mub);
-  atomicAdd(a.fsb + n, mub * dfs + c.klap * c.cos_ps * self * mub);
-#pragma unroll
-  for (int i = 1; i < 9; i++) {
-    const int m = stencil_index(g, x, y, i);
-    atomicAdd(a.phib + m, -c.klap * 6.0 * qw<double>(i) * mub);
-    atomicAdd(a.fsb + m, -c.klap * c.cos_ps * 6.0 * qw<double>(i) * mub);
-  }
+  a.mub[n] = mub;
+  a.phib[n] = itg * gb[0] + mub * dphi + c.klap * self * mub;
+  a.fsb[n] = mub * dfs + c.klap * c.cos_ps * self * mub;
   a.acc[n] += mub * (dcos - c.klap * lphi0) * a.dcos_dtheta;
   a.acc[P + n] += mub * mu / c.sigma;
 }
 
-// Reverse step, part 2: fs -> w -> phi (local), phi = sum g.
+// Reverse step, part 2: the transposed Laplacian stencils as a gather (every
+// node p within one node of n, and every direction i whose clamped or
+// wrapped stencil neighbour of p is n, adds -klap 6 w_i mub(p); a fixed
+// order, so the sweep is deterministic), then fs -> w -> phi (local) and
+// phi = sum g.
 static __global__ void __launch_bounds__(NT) lbm_phase_adjoint2_kernel(const PhaseAdjArgs a) {
   const Geom& g = a.g;
+  const Coef<double>& c = a.c;
   const int x = blockIdx.x * TX + threadIdx.x, y = blockIdx.y * TY + threadIdx.y;
   if (x >= g.nx || y >= g.ny) return;
   const int P = (int)g.plane;
   const int n = y * g.pitch + x;
+  double lsum = 0.0;  // sum of 6 w_i mub(p) over the stencil links that reach n
+  for (int dy = -1; dy <= 1; dy++) {
+    int py = y + dy;
+    if (py < 0 || py >= g.ny) {
+      if (g.bc[2] != BC_PERIODIC) continue;
+      py = (py + g.ny) % g.ny;
+    }
+    // on a periodic axis of length 2, y - 1 and y + 1 are the same node
+    if (dy == 1 && py == (y - 1 + g.ny) % g.ny && g.ny > 1 && g.bc[2] == BC_PERIODIC) continue;
+    for (int dx = -1; dx <= 1; dx++) {
+      int px = x + dx;
+      if (px < 0 || px >= g.nx) {
+        if (g.bc[0] != BC_PERIODIC) continue;
+        px = (px + g.nx) % g.nx;
+      }
+      if (dx == 1 && px == (x - 1 + g.nx) % g.nx && g.nx > 1 && g.bc[0] == BC_PERIODIC) continue;
+      const double mp = a.mub[py * g.pitch + px];
+#pragma unroll
+      for (int i = 1; i < 9; i++)
+        if (stencil_index(g, px, py, i) == n) lsum += 6.0 * qw<double>(i) * mp;
+    }
+  }
+  double phib = a.phib[n] - c.klap * lsum;
+  const double fsb = a.fsb[n] - c.klap * c.cos_ps * lsum;
   const double q0 = a.phi0[n], ph = a.phi[n], fl = a.lag[LAG_FL * P + n];
-  double phib = a.phib[n];
   const double wraw = (1.0 - q0 + ph) * 0.5;
   const double w = clamp01(wraw);
   const double fsraw = q0 + w * (1.0 - fl);
-  if (!(fsraw > 1.0) && !(wraw < 0.0) && !(wraw > 1.0)) phib += a.fsb[n] * (1.0 - fl) * 0.5;
-  const double omg = 1.0 - a.c.inv_tau_g;
+  if (!(fsraw > 1.0) && !(wraw < 0.0) && !(wraw > 1.0)) phib += fsb * (1.0 - fl) * 0.5;
+  const double omg = 1.0 - c.inv_tau_g;
 #pragma unroll
   for (int i = 0; i < 9; i++) a.lam_out[i * P + n] = omg * a.gs[i * P + n] + phib;
 }

@@ -853,8 +853,8 @@ extern "C" int lbm_adjoint_crossing(lbm_ctx* c, int64_t nsteps, int every, int a
   const size_t gN = 9 * P, lN = lbmk::NLAG * P, stN = gN + lN;  // doubles per stored state
   const int64_t nck = (nsteps + every - 1) / every;
   const int64_t seglen = std::min<int64_t>(every, nsteps);
-  // work planes: phi, fs, phib, fsb, 9 gs, 2 x 9 adjoint populations
-  const size_t wN = (4 + 9 + 18) * P;
+  // work planes: phi, fs, phib, fsb, mub, 9 gs, 2 x 9 adjoint populations
+  const size_t wN = (5 + 9 + 18) * P;
   double *ck = nullptr, *seg = nullptr, *wk = nullptr, *acc = nullptr, *dout = nullptr,
          *fin = nullptr;
   cudaError_t e = cudaMalloc(&ck, nck * stN * sizeof(double));
@@ -897,7 +897,7 @@ extern "C" int lbm_adjoint_crossing(lbm_ctx* c, int64_t nsteps, int every, int a
   if (e == cudaSuccess) e = cudaMemsetAsync(acc, 0, lbmk::ADJ_NACC * P * sizeof(double), s);
   if (e == cudaSuccess) e = cudaMemsetAsync(wk, 0, wN * sizeof(double), s);
   const double pi = 3.14159265358979323846;
-  double* lb[2] = {wk + 13 * P, wk + 22 * P};
+  double* lb[2] = {wk + 14 * P, wk + 23 * P};
   lbmk::PhaseAdjArgs a;
   std::memset(&a, 0, sizeof(a));
   a.g = c->g;
@@ -907,7 +907,8 @@ extern "C" int lbm_adjoint_crossing(lbm_ctx* c, int64_t nsteps, int every, int a
   a.fs = wk + P;
   a.phib = wk + 2 * P;
   a.fsb = wk + 3 * P;
-  a.gs = wk + 4 * P;
+  a.mub = wk + 4 * P;
+  a.gs = wk + 5 * P;
   a.acc = acc;
   a.dcos_dtheta = -std::sin(c->p.theta_deg * pi / 180.0) * (pi / 180.0);
   a.axis = axis;
@@ -944,7 +945,6 @@ extern "C" int lbm_adjoint_crossing(lbm_ctx* c, int64_t nsteps, int every, int a
       a.lam_in = lb[cur_adj];
       a.lam_out = lb[cur_adj ^ 1];
       e = lbmk::launch_phase_adjoint_fields(a, s);
-      if (e == cudaSuccess) e = cudaMemsetAsync(a.phib, 0, 2 * P * sizeof(double), s);
       if (e == cudaSuccess) e = lbmk::launch_phase_adjoint_step(a, s);
       cur_adj ^= 1;
     }
