@@ -122,3 +122,37 @@ def test_extruded_2d_state_stays_z_uniform(env):
     # summation order
     assert np.abs(f["uz"]).max() <= 1e-10 * max(np.abs(f["ux"]).max(), np.abs(f["uy"]).max())
     s.close()
+
+
+@pytest.mark.parametrize("shape,bc", [
+    ((2, 2, 2), ("periodic",) * 6),
+    ((2, 2, 2), ("dirichlet", "adiabatic", "adiabatic", "dirichlet", "dirichlet", "dirichlet")),
+    ((33, 2, 3), ("periodic", "periodic", "dirichlet", "dirichlet", "periodic", "periodic")),
+    ((3, 5, 2), ("adiabatic", "dirichlet", "periodic", "periodic", "dirichlet", "adiabatic")),
+])
+def test_degenerate_grids_match_oracle(env, shape, bc):
+    """The smallest grids: every node is on a face, edge or corner (links
+    leave through several walls at once; a periodic axis of length 2 wraps
+    both neighbours onto the same node)."""
+    O3, lbm = env
+    nx, ny, nz = shape
+    wl = W.random_state3(nx, ny, nz, seed=5, bc=bc)
+    o = O3.from_workload(wl).step(20)
+    s = lbm.Solver3(wl[0], "fp64").set_geometry(wl[1]).step(20)
+    _compare(o.fields(), s.fields(), "fp64", f"{shape} {bc}")
+    s.close()
+
+
+def test_nonfinite_state_is_reported(env):
+    """A non-finite initial temperature makes the state non-finite; the
+    diagnostics count the nodes instead of failing silently."""
+    O3, lbm = env
+    cfg, arr = W.random_state3(20, 8, 6, seed=2)
+    arr = dict(arr)
+    T = arr["T"].copy()
+    T[3, 4, 5] = np.nan
+    arr["T"] = T
+    s = lbm.Solver3(cfg, "fp32").set_geometry(arr).step(3)
+    d = s.diagnostics()
+    assert d["nonfinite"] >= 1
+    s.close()
