@@ -170,3 +170,77 @@ class FreezingObservables:
 
             cls._fn = _Fn
         return cls._fn.apply(p, cfg, arrays, steps, wall, line)
+
+
+# --- reverse mode: the hand-written adjoints behind torch.autograd ------------
+
+def _adjoint_fn(name, run):
+    """A torch.autograd.Function whose forward runs a reverse-mode library
+    call from the initial fields (value and gradient in one sweep) and whose
+    backward returns grad_output times the stored gradient."""
+    import torch
+
+    class _Fn(torch.autograd.Function):
+        @staticmethod
+        def forward(ctx, q, *args):
+            val, grad = run(q.detach().cpu().numpy().astype(np.float64), *args)
+            ctx.save_for_backward(torch.as_tensor(np.asarray(grad), dtype=torch.float64))
+            ctx.nargs = len(args)
+            return torch.as_tensor(val, dtype=torch.float64)
+
+        @staticmethod
+        def backward(ctx, g):
+            (grad,) = ctx.saved_tensors
+            return ((g.to(grad.dtype) * grad).to(g.device),) + (None,) * ctx.nargs
+
+    _Fn.__name__ = name
+    return _Fn
+
+
+def _run_adjoint_ff(q, cfg, arrays, steps, every):
+    c = dict(cfg, T_wall=tuple(float(v) for v in q[:4]), latent=float(q[4]))
+    s = lbm.Solver(c, precision="fp64").set_geometry(arrays)
+    try:
+        return s.adjoint_frozen_fraction(steps, every)
+    finally:
+        s.close()
+
+
+def _run_adjoint_crossing(q, cfg, arrays, steps, axis, index, every):
+    c = dict(cfg, theta_deg=float(q[0]), sigma=float(q[1]))
+    s = lbm.Solver(c, precision="fp64").set_geometry(arrays)
+    try:
+        return s.adjoint_crossing(steps, axis, index, every)
+    finally:
+        s.close()
+
+
+class AdjointFrozenFraction:
+    """``AdjointFrozenFraction.apply(q, cfg, arrays, steps, every)``: the
+    frozen fraction after `steps` steps of an enthalpy-lattice context (see
+    lbm_adjoint_frozen_fraction) as a differentiable function of
+    q = (T_wall[0..3], latent) (a float64 tensor of 5), from the initial
+    fields; one forward-and-reverse sweep gives the value and the gradient."""
+
+    _fn = None
+
+    @classmethod
+    def apply(cls, q, cfg, arrays, steps, every=64):
+        if cls._fn is None:
+            cls._fn = _adjoint_fn("AdjointFrozenFraction", _run_adjoint_ff)
+        return cls._fn.apply(q, cfg, arrays, steps, every)
+
+
+class AdjointCrossing:
+    """``AdjointCrossing.apply(q, cfg, arrays, steps, axis, index, every)``:
+    the last phi = 0 crossing along a grid line after `steps` steps of a
+    phase-field context (see lbm_adjoint_crossing) as a differentiable
+    function of q = (theta_deg, sigma), from the initial fields."""
+
+    _fn = None
+
+    @classmethod
+    def apply(cls, q, cfg, arrays, steps, axis, index, every=64):
+        if cls._fn is None:
+            cls._fn = _adjoint_fn("AdjointCrossing", _run_adjoint_crossing)
+        return cls._fn.apply(q, cfg, arrays, steps, axis, index, every)

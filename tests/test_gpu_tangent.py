@@ -417,3 +417,31 @@ def test_phase_adjoint_checkpoints_final_state_and_rejections(env):
             s.adjoint_crossing(10, axis, index, 5)
         assert e.value.status == -1
     s.close()
+
+
+def test_adjoints_behind_autograd(env):
+    """The reverse-mode calls behind torch.autograd: backward returns
+    grad_output times the sweep's gradient, and the values are those of plain
+    runs with the same parameters."""
+    O, lbm, S, torch = env
+    cfg, arr = _phase_droplet()
+    q = torch.tensor([cfg["theta_deg"], cfg["sigma"]], dtype=torch.float64, requires_grad=True)
+    y = S.AdjointCrossing.apply(q, cfg, arr, 200, 0, 9, 50)
+    (3.0 * y).backward()
+    s = lbm.Solver(cfg, precision="fp64").set_geometry(arr)
+    pos, grad = s.adjoint_crossing(200, 0, 9, every=50)
+    s.close()
+    assert float(y.detach()) == pos
+    assert q.grad.tolist() == [3.0 * grad[0], 3.0 * grad[1]]
+
+    hc, ha = _heat_column()
+    qh = torch.tensor(list(hc["T_wall"]) + [hc["latent"]], dtype=torch.float64, requires_grad=True)
+    ff = S.AdjointFrozenFraction.apply(qh, hc, ha, 300, 100)
+    ff.backward()
+    t = lbm.Solver(hc, precision="tangent", tangent={"T_wall": [1.0, 0.0, 0.0, 0.0]}).set_geometry(ha).step(300)
+    d, dt = t.diagnostics(), t.tangent_diagnostics(compute=False)
+    fz, mv = d["frozen_volume"], d["material_volume"]
+    tan = (dt["frozen_volume"] * mv - fz * dt["material_volume"]) / mv ** 2
+    t.close()
+    assert abs(float(ff.detach()) - fz / mv) <= 1e-12 * float(ff.detach())
+    assert abs(float(qh.grad[0]) - tan) <= 1e-9 * abs(tan)
