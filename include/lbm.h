@@ -339,6 +339,30 @@ int lbm_adjoint_frozen_fraction(lbm_ctx* ctx, int64_t nsteps, int every, double*
 int lbm_adjoint_crossing(lbm_ctx* ctx, int64_t nsteps, int every, int axis, int index,
                          double* pos, double* grad, void* stream);
 
+/* Reverse mode (adjoint) of the coupled freezing step with the fluid at
+ * rest: for a context with precision LBM_FP64, lattices == LBM_LAT_PHASE |
+ * LBM_LAT_HEAT, no cold mask and sigma > 0, the phase field and the enthalpy
+ * lattice coupled as in the full step (the mass source of Eq. (1) in the
+ * order parameter, Eq. (22), and in the phase source, Eq. (20); w and
+ * fs = phi0 + w (1 - fl) in the properties of Eq. (10) and in Eq. (6); the
+ * lagged w in the inversion of Eq. (8)).  Advances the state by nsteps steps
+ * as lbm_step would and returns in *value the observable of the final
+ * state -- observable 0: the frozen fraction FF = sum w (1 - fl) / sum w;
+ * observable 1: the last phi = 0 crossing along grid line (axis, index), as
+ * out[0] of lbm_read_crossings -- and in grad[0..6] its derivatives with
+ * respect to T_wall[0..3] (zero where bc[k] is not LBM_BC_DIRICHLET), the
+ * latent heat L, the contact angle theta (degrees) and sigma.  The state at
+ * the start of the call is held fixed, except that a call right after
+ * lbm_set_geometry (step 0) includes the initial populations' dependence on
+ * L, theta and sigma.  Checkpoints and kinks as in
+ * lbm_adjoint_frozen_fraction and lbm_adjoint_crossing.  Synchronises
+ * `stream`.  Errors: LBM_ERR_ARG (null output, nsteps < 1, every < 1,
+ * observable not 0 or 1, a bad line), LBM_ERR_STATE before
+ * lbm_set_geometry, LBM_ERR_UNSUPPORTED for other contexts,
+ * LBM_ERR_OOM/LBM_ERR_CUDA (the context's state is then undefined). */
+int lbm_adjoint_freezing(lbm_ctx* ctx, int64_t nsteps, int every, int observable, int axis,
+                         int index, double* value, double* grad, void* stream);
+
 /* Autotuner (the paper gives no implementation; a measuring aid of this
  * library): times the step forms this build has on the context's own grid
  * and state and keeps the fastest for later lbm_step calls.  Variants, in

@@ -47,4 +47,29 @@ cudaError_t launch_phase_adjoint_init(const PhaseAdjArgs& a, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+cudaError_t launch_frz_fields(const FrzArgs& a, cudaStream_t s) {
+  lbm_frz_fields_kernel<<<grid_dims(a.g), block_dims(), 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_frz_mub(const FrzArgs& a, cudaStream_t s) {
+  lbm_frz_mub_kernel<<<grid_dims(a.g), block_dims(), 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_frz_step(const FrzArgs& a, cudaStream_t s) {
+  lbm_frz_step_kernel<<<grid_dims(a.g), block_dims(), 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_frz_seed_ff(const FrzArgs& a, cudaStream_t s) {
+  lbm_frz_seed_ff_kernel<<<grid_dims(a.g), block_dims(), 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_frz_seed_crossing(const FrzArgs& a, double* phib, cudaStream_t s) {
+  lbm_frz_seed_crossing_kernel<<<1, 32, 0, s>>>(a, phib);
+  return cudaGetLastError();
+}
+
 }  // namespace lbmk

@@ -158,7 +158,6 @@ static __global__ void __launch_bounds__(NT) lbm_adjoint_step_kernel(const AdjAr
   const double Qp = a.lag[LAG_Q * P + n], phi0 = a.phi0[n];
   const HeatNode q = heat_forward(c, sum_h(h), flp, wp, Qp, phi0);
   const double rrT = c.rr * q.T;
-  const double Hsrc = q.hcoef * q.CT * q.mdot;
 
   // reverse of the TRT collision (Eqs. (23)-(27), u = 0)
   double hb[9];
@@ -486,6 +485,389 @@ static __global__ void __launch_bounds__(NT) lbm_phase_init_kernel(const PhaseAd
   a.acc[P + n] += mub * mu / c.sigma;
 }
 
+// ---------------------------------------------------------------------------
+// reverse mode of the coupled phase-field and enthalpy step (lattices ==
+// LAT_PHASE | LAT_HEAT: the fluid at rest, no cold mask).  The freezing
+// couples the lattices: the mass source mdot of Eq. (1) enters the order
+// parameter (Eq. (22)) and the phase source (Eq. (20)); the weight w and
+// the solid fraction fs = phi0 + w (1 - fl) set the properties of Eq. (10)
+// (rho Cp and lambda of the enthalpy collision) and the wetting terms of
+// Eq. (6); the lagged w enters the inversion of Eq. (8) and mdot.  Per step
+// in reverse: a fields kernel (phi, fs of the recomputed state), a kernel for
+// the adjoint of mu_phi and its theta and sigma terms, and a kernel that
+// pulls the adjoints of both lattices through the push (anti-bounce-back at
+// Dirichlet walls), reverses the two collisions, gathers the transposed
+// stencils and runs the local chain (fs, w, phi, mdot, the inversion) back
+// to the adjoints of this state's populations and lags (fl, w, Q).
+// Accumulator planes: d/dT_wall[0..3], d/dL, d/dtheta_deg, d/dsigma.
+// ---------------------------------------------------------------------------
+
+constexpr int FRZ_NACC = 7;
+
+struct FrzArgs {
+  Geom g;
+  Coef<double> c;
+  const double* __restrict__ pop;     // 18 planes of the forward state: g (0-8), h (9-17)
+  const double* __restrict__ lag;     // NLAG planes of the forward state
+  const double* __restrict__ phi0;
+  double* __restrict__ phi;           // fields of the forward state
+  double* __restrict__ fs;
+  const double* __restrict__ lam_in;  // 18 planes: adjoints of the next g (0-8), h (9-17)
+  const double* __restrict__ lfl_in;  // adjoints of the next state's lags fl, w, Q
+  const double* __restrict__ lw_in;
+  const double* __restrict__ lq_in;
+  double* __restrict__ mub;           // adjoint of mu_phi
+  const double* __restrict__ phib_seed;  // extra adjoint of phi (observable seed) or null
+  double* __restrict__ lam_out;       // 18 planes: adjoints of this state's g, h
+  double* __restrict__ lfl_out;
+  double* __restrict__ lw_out;
+  double* __restrict__ lq_out;
+  double* __restrict__ acc;           // FRZ_NACC planes (+=)
+  double dcos_dtheta;
+  double inv_sum_w, ff;               // frozen-fraction seed
+  int axis, index;                    // crossing seed
+  double* __restrict__ out;           // crossing value (1 double)
+};
+
+// Forward quantities of one node of the coupled step.
+struct FrzNode {
+  double rhoH, T, fl, mdot, ell, Cm, Cp, fsf;
+  int branch;  // 0 frozen, 1 liquid, 2 mushy
+  bool fsf_clamped;
+  double D, phi, wraw, w, fs_raw, fs, rho, cp, C, lam, taua, ia, is, hcoef, CT;
+};
+
+__device__ __forceinline__ double dinterp_dfs(double w, double zs, double zl, double zg) {
+  return zs - w * zl - (1.0 - w) * zg;
+}
+__device__ __forceinline__ double dinterp_dw(double fs, double zl, double zg) {
+  return (1.0 - fs) * (zl - zg);
+}
+
+__device__ __forceinline__ FrzNode frz_forward(const Coef<double>& c, double sg, double sh,
+                                               double flp, double wp, double Qp, double phi0) {
+  FrzNode q;
+  q.rhoH = sh + 0.5 * Qp;
+  q.ell = wp * c.rho_l * c.latent;
+  q.fsf = phi0 + wp;
+  q.fsf_clamped = q.fsf > 1.0;
+  if (q.fsf_clamped) q.fsf = 1.0;
+  q.Cm = heat_cap(c, q.fsf, wp);
+  q.Cp = heat_cap(c, phi0, wp);
+  if (q.rhoH < 0.0) {
+    q.branch = 0;
+    q.fl = 0.0;
+    q.T = q.rhoH / q.Cm;
+  } else if (q.rhoH > q.ell) {
+    q.branch = 1;
+    q.fl = 1.0;
+    q.T = (q.rhoH - q.ell) / q.Cp;
+  } else {
+    q.branch = 2;
+    q.T = 0.0;
+    q.fl = q.ell > 0.0 ? q.rhoH / q.ell : 1.0;
+  }
+  q.fl = clamp01(q.fl);
+  q.mdot = c.one_m_ratio * wp * (flp - q.fl);
+  q.D = 1.0 - 0.5 * q.mdot;
+  q.phi = q.mdot == 0.0 ? sg : sg / q.D;
+  q.wraw = (1.0 - phi0 + q.phi) * 0.5;
+  q.w = clamp01(q.wraw);
+  q.fs_raw = phi0 + q.w * (1.0 - q.fl);
+  q.fs = q.fs_raw > 1.0 ? 1.0 : q.fs_raw;
+  q.rho = interp(q.fs, q.w, c.rho_s, c.rho_l, c.rho_g);
+  q.cp = interp(q.fs, q.w, c.cp_s, c.cp_l, c.cp_g);
+  q.C = q.rho * q.cp;
+  q.lam = interp(q.fs, q.w, c.lam_s, c.lam_l, c.lam_g);
+  q.taua = 0.5 + q.lam * c.inv_rr3;
+  q.ia = 1.0 / q.taua;
+  q.is = 2.0 - q.ia;
+  q.hcoef = 1.0 - 0.5 * q.ia;
+  q.CT = q.C * q.T;
+  return q;
+}
+
+__device__ __forceinline__ FrzNode frz_node(const FrzArgs& a, int n) {
+  const int P = (int)a.g.plane;
+  double v[9];
+#pragma unroll
+  for (int i = 0; i < 9; i++) v[i] = a.pop[i * P + n];
+  const double sg = sum_g(v);
+#pragma unroll
+  for (int i = 0; i < 9; i++) v[i] = a.pop[(9 + i) * P + n];
+  const double sh = sum_h(v);
+  return frz_forward(a.c, sg, sh, a.lag[LAG_FL * P + n], a.lag[LAG_W * P + n],
+                     a.lag[LAG_Q * P + n], a.phi0[n]);
+}
+
+// d(rho Cp)/dfs and d(rho Cp)/dw at (fs, w)
+__device__ __forceinline__ void dcap(const Coef<double>& c, double fs, double w, double* dfs,
+                                     double* dw) {
+  const double rho = interp(fs, w, c.rho_s, c.rho_l, c.rho_g);
+  const double cp = interp(fs, w, c.cp_s, c.cp_l, c.cp_g);
+  *dfs = dinterp_dfs(w, c.rho_s, c.rho_l, c.rho_g) * cp + rho * dinterp_dfs(w, c.cp_s, c.cp_l, c.cp_g);
+  *dw = dinterp_dw(fs, c.rho_l, c.rho_g) * cp + rho * dinterp_dw(fs, c.cp_l, c.cp_g);
+}
+
+static __global__ void __launch_bounds__(NT) lbm_frz_fields_kernel(const FrzArgs a) {
+  const Geom& g = a.g;
+  const int x = blockIdx.x * TX + threadIdx.x, y = blockIdx.y * TY + threadIdx.y;
+  if (x >= g.nx || y >= g.ny) return;
+  const int n = y * g.pitch + x;
+  const FrzNode q = frz_node(a, n);
+  a.phi[n] = q.phi;
+  a.fs[n] = q.fs;
+}
+
+// Adjoint of mu_phi from the pulled phase adjoints, with its theta and
+// sigma terms (zero for the seed, whose pulled adjoints are zero).
+static __global__ void __launch_bounds__(NT) lbm_frz_mub_kernel(const FrzArgs a) {
+  const Geom& g = a.g;
+  const Coef<double>& c = a.c;
+  const int x = blockIdx.x * TX + threadIdx.x, y = blockIdx.y * TY + threadIdx.y;
+  if (x >= g.nx || y >= g.ny) return;
+  const int P = (int)g.plane;
+  const int n = y * g.pitch + x;
+  double mub = 0.0;
+#pragma unroll
+  for (int i = 0; i < 9; i++) {
+    int wall;
+    const long long t = stream_target(g, x, y, qx(i), qy(i), wall);
+    const double gb = t >= 0 ? a.lam_in[i * P + (int)t] : a.lam_in[qopp(i) * P + n];
+    mub += (qw<double>(i) - (i == 0 ? 1.0 : 0.0)) * gb;
+  }
+  mub *= c.inv_tau_g * c.eta;
+  a.mub[n] = mub;
+  const double ph = a.phi[n], q0 = a.phi0[n], fs = a.fs[n];
+  double dphi, dfs, dcos;
+  chem_partials(c, ph, q0, fs, &dphi, &dfs, &dcos);
+  const double lphi = lap6(g, a.phi, x, y, n), lphi0 = lap6(g, a.phi0, x, y, n);
+  const double lfs = lap6(g, a.fs, x, y, n);
+  const double mu = chem_local(c, ph, q0, fs) - c.klap * (lphi + c.cos_th * lphi0 + c.cos_ps * lfs);
+  a.acc[5 * P + n] += mub * (dcos - c.klap * lphi0) * a.dcos_dtheta;
+  a.acc[6 * P + n] += mub * mu / c.sigma;
+}
+
+// The rest of one reverse step (see the section header).
+static __global__ void __launch_bounds__(NT) lbm_frz_step_kernel(const FrzArgs a) {
+  const Geom& g = a.g;
+  const Coef<double>& c = a.c;
+  const int x = blockIdx.x * TX + threadIdx.x, y = blockIdx.y * TY + threadIdx.y;
+  if (x >= g.nx || y >= g.ny) return;
+  const int P = (int)g.plane;
+  const int n = y * g.pitch + x;
+  // pull the adjoints of both lattices' post-collision populations
+  double gb[9], hb_star[9];
+  double dTw[4] = {0.0, 0.0, 0.0, 0.0};
+#pragma unroll
+  for (int i = 0; i < 9; i++) {
+    int wall;
+    const long long t = stream_target(g, x, y, qx(i), qy(i), wall);
+    if (t >= 0) {
+      gb[i] = a.lam_in[i * P + (int)t];
+      hb_star[i] = a.lam_in[(9 + i) * P + (int)t];
+    } else {
+      gb[i] = a.lam_in[qopp(i) * P + n];
+      const double lb = a.lam_in[(9 + qopp(i)) * P + n];
+      if (g.bc[wall] == BC_DIRICHLET) {
+        hb_star[i] = -lb;
+        dTw[wall] += lb * 2.0 * qw<double>(i) * c.rr;
+      } else {
+        hb_star[i] = lb;
+      }
+    }
+  }
+  const FrzNode q = frz_node(a, n);
+  const double phi0 = a.phi0[n];
+  const double wp = a.lag[LAG_W * P + n], flp = a.lag[LAG_FL * P + n];
+  double h[9];
+#pragma unroll
+  for (int i = 0; i < 9; i++) h[i] = a.pop[(9 + i) * P + n];
+  const double rrT = c.rr * q.T;
+
+  // enthalpy TRT collision in reverse (u = 0)
+  double hb[9];
+  double isb = 0.0, iab = 0.0, Hsrcb = 0.0, rrTb = 0.0, rhoHb = 0.0;
+  {
+    const double A0 = hb_star[0];
+    const double heq0 = q.rhoH - rrT + qw<double>(0) * rrT;
+    hb[0] = A0 * (1.0 - q.is);
+    const double heq0b = A0 * q.is;
+    isb += -A0 * (h[0] - heq0);
+    Hsrcb += qw<double>(0) * A0;
+    rhoHb += heq0b;
+    rrTb += (qw<double>(0) - 1.0) * heq0b;
+  }
+#pragma unroll
+  for (int i = 1; i <= 8; i++) {
+    if (i == 3 || i == 4 || i == 7 || i == 8) continue;
+    const int o = qopp(i);
+    const double wi = qw<double>(i);
+    const double es = wi * rrT;
+    const double hs = 0.5 * (h[i] + h[o]), ha = 0.5 * (h[i] - h[o]);
+    const double A = hb_star[i], B = hb_star[o];
+    const double Dab = -A + B, Dsb = -A - B;
+    const double hab = Dab * q.ia, hsb = Dsb * q.is;
+    iab += Dab * ha;
+    rrTb += -Dsb * q.is * wi;
+    isb += Dsb * (hs - es);
+    Hsrcb += -wi * Dsb;
+    hb[i] = A + 0.5 * hsb + 0.5 * hab;
+    hb[o] = B + 0.5 * hsb - 0.5 * hab;
+  }
+  // enthalpy source Hsrc = hcoef C T mdot and the lag Q = C T mdot
+  const double lqb = a.lq_in[n];
+  const double hcoefb = Hsrcb * q.CT * q.mdot;
+  const double CTb = Hsrcb * q.hcoef * q.mdot;
+  double mdotb = Hsrcb * q.hcoef * q.CT + lqb * q.C * q.T;
+  const double Cb = lqb * q.T * q.mdot + CTb * q.T;
+  double Tb = c.rr * rrTb + lqb * q.C * q.mdot + CTb * q.C;
+  // relaxation rates from lambda(fs, w), capacity rho Cp (fs, w)
+  iab += -0.5 * hcoefb;
+  iab -= isb;
+  const double lamb = -iab / (q.taua * q.taua) * c.inv_rr3;
+  double fsb = lamb * dinterp_dfs(q.w, c.lam_s, c.lam_l, c.lam_g);
+  double wb = lamb * dinterp_dw(q.fs, c.lam_l, c.lam_g);
+  {
+    double cf, cw;
+    dcap(c, q.fs, q.w, &cf, &cw);
+    fsb += Cb * cf;
+    wb += Cb * cw;
+  }
+  // phase collision in reverse: phi and mdot (the mu_phi part is gathered)
+  double S = 0.0;
+#pragma unroll
+  for (int i = 0; i < 9; i++) S += qw<double>(i) * gb[i];
+  const double itg = c.inv_tau_g, gcoef = 1.0 - 0.5 * itg;
+  double phib = itg * gb[0] + gcoef * q.mdot * S;
+  mdotb += gcoef * q.phi * S;
+  if (a.phib_seed) phib += a.phib_seed[n];
+  // mu_phi of this node (local part, centre of the Laplacians) and the
+  // transposed stencils of the neighbours' mu_phi
+  {
+    const double mub = a.mub[n];
+    double dphi, dfs, dcos;
+    chem_partials(c, q.phi, phi0, q.fs, &dphi, &dfs, &dcos);
+    const double self = 6.0 * (1.0 - qw<double>(0));
+    phib += mub * dphi + c.klap * self * mub;
+    fsb += mub * dfs + c.klap * c.cos_ps * self * mub;
+    double lsum = 0.0;
+    for (int dy = -1; dy <= 1; dy++) {
+      int py = y + dy;
+      if (py < 0 || py >= g.ny) {
+        if (g.bc[2] != BC_PERIODIC) continue;
+        py = (py + g.ny) % g.ny;
+      }
+      if (dy == 1 && py == (y - 1 + g.ny) % g.ny && g.bc[2] == BC_PERIODIC) continue;
+      for (int dx = -1; dx <= 1; dx++) {
+        int px = x + dx;
+        if (px < 0 || px >= g.nx) {
+          if (g.bc[0] != BC_PERIODIC) continue;
+          px = (px + g.nx) % g.nx;
+        }
+        if (dx == 1 && px == (x - 1 + g.nx) % g.nx && g.bc[0] == BC_PERIODIC) continue;
+        const double mp = a.mub[py * g.pitch + px];
+#pragma unroll
+        for (int i = 1; i < 9; i++)
+          if (stencil_index(g, px, py, i) == n) lsum += 6.0 * qw<double>(i) * mp;
+      }
+    }
+    phib -= c.klap * lsum;
+    fsb -= c.klap * c.cos_ps * lsum;
+  }
+  // lags written by this step
+  wb += a.lw_in[n];
+  double flb = a.lfl_in[n];
+  // fs = min(phi0 + w (1 - fl), 1)
+  if (!(q.fs_raw > 1.0)) {
+    wb += fsb * (1.0 - q.fl);
+    flb += -q.w * fsb;
+  }
+  // w = clamp((1 - phi0 + phi) / 2)
+  if (!(q.wraw < 0.0) && !(q.wraw > 1.0)) phib += 0.5 * wb;
+  // phi = sum g / (1 - mdot / 2)
+  const double sgb = phib / q.D;
+  mdotb += phib * 0.5 * q.phi / q.D;
+  // mdot = (1 - rho_s / rho_l) w_prev (fl_prev - fl)
+  double wpb = mdotb * c.one_m_ratio * (flp - q.fl);
+  const double flpb = mdotb * c.one_m_ratio * wp;
+  flb += -mdotb * c.one_m_ratio * wp;
+  // the inversion of Eq. (8) with its dependence on w_prev
+  double ellb = 0.0;
+  if (q.branch == 0) {
+    rhoHb += Tb / q.Cm;
+    const double Cmb = -Tb * q.T / q.Cm;
+    double cf, cw;
+    dcap(c, q.fsf, wp, &cf, &cw);
+    wpb += Cmb * ((q.fsf_clamped ? 0.0 : cf) + cw);
+  } else if (q.branch == 1) {
+    rhoHb += Tb / q.Cp;
+    ellb += -Tb / q.Cp;
+    const double Cpb = -Tb * q.T / q.Cp;
+    double cf, cw;
+    dcap(c, phi0, wp, &cf, &cw);
+    wpb += Cpb * cw;
+  } else if (q.ell > 0.0) {
+    rhoHb += flb / q.ell;
+    ellb += -flb * q.rhoH / (q.ell * q.ell);
+  }
+  wpb += ellb * c.rho_l * c.latent;
+  const double dL = ellb * wp * c.rho_l;
+  const double omg = 1.0 - itg;
+#pragma unroll
+  for (int i = 0; i < 9; i++) {
+    a.lam_out[i * P + n] = omg * gb[i] + sgb;
+    a.lam_out[(9 + i) * P + n] = hb[i] + rhoHb;
+  }
+  a.lfl_out[n] = flpb;
+  a.lw_out[n] = wpb;
+  a.lq_out[n] = 0.5 * rhoHb;
+#pragma unroll
+  for (int k = 0; k < 4; k++) a.acc[k * P + n] += dTw[k];
+  a.acc[4 * P + n] += dL;
+}
+
+// Seeds on the final state.  Frozen fraction FF = sum w (1 - fl) / sum w
+// (w and fl of this state): the adjoints of the lags this state's reader
+// would write, with zero population adjoints.
+static __global__ void __launch_bounds__(NT) lbm_frz_seed_ff_kernel(const FrzArgs a) {
+  const Geom& g = a.g;
+  const int x = blockIdx.x * TX + threadIdx.x, y = blockIdx.y * TY + threadIdx.y;
+  if (x >= g.nx || y >= g.ny) return;
+  const int n = y * g.pitch + x;
+  const FrzNode q = frz_node(a, n);
+  a.lfl_out[n] = -q.w * a.inv_sum_w;
+  a.lw_out[n] = ((1.0 - q.fl) - a.ff) * a.inv_sum_w;
+}
+
+// Crossing: the last phi = 0 crossing along the line (one thread), as an
+// adjoint of phi at its two nodes.
+static __global__ void lbm_frz_seed_crossing_kernel(const FrzArgs a, double* __restrict__ phib) {
+  const Geom& g = a.g;
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  const int len = a.axis == 0 ? g.nx : g.ny;
+  const int stride = a.axis == 0 ? 1 : g.pitch;
+  const int base = a.axis == 0 ? a.index * g.pitch : a.index;
+  double J = __longlong_as_double(0x7ff8000000000000ULL);
+  for (int k = len - 2; k >= 0; k--) {
+    const int n0 = base + k * stride, n1 = n0 + stride;
+    const double va = a.phi[n0], vb = a.phi[n1];
+    if ((va <= 0.0) != (vb <= 0.0)) {
+      const double d = va - vb;
+      J = k + va / d;
+      phib[n0] = -vb / (d * d);
+      phib[n1] = va / (d * d);
+      break;
+    }
+  }
+  a.out[0] = J;
+}
+
+cudaError_t launch_frz_fields(const FrzArgs& a, cudaStream_t s);
+cudaError_t launch_frz_mub(const FrzArgs& a, cudaStream_t s);
+cudaError_t launch_frz_step(const FrzArgs& a, cudaStream_t s);
+cudaError_t launch_frz_seed_ff(const FrzArgs& a, cudaStream_t s);
+cudaError_t launch_frz_seed_crossing(const FrzArgs& a, double* phib, cudaStream_t s);
 cudaError_t launch_phase_adjoint_fields(const PhaseAdjArgs& a, cudaStream_t s);
 cudaError_t launch_phase_adjoint_seed(const PhaseAdjArgs& a, cudaStream_t s);
 cudaError_t launch_phase_adjoint_step(const PhaseAdjArgs& a, cudaStream_t s);

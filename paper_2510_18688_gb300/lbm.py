@@ -61,7 +61,7 @@ EXPORTS = ("lbm_create", "lbm_set_geometry", "lbm_step", "lbm_read_fields",
            "lbm_batch_create", "lbm_batch_step", "lbm_batch_destroy", "lbm_probe_fma_rate",
            "lbm_read_crossings", "lbm_read_tangent_fields", "lbm_read_tangent_diagnostics",
            "lbm_read_crossings_tangent", "lbm_autotune", "lbm_adjoint_frozen_fraction",
-           "lbm_adjoint_crossing", "lbm3_create", "lbm3_set_geometry", "lbm3_step",
+           "lbm_adjoint_crossing", "lbm_adjoint_freezing", "lbm3_create", "lbm3_set_geometry", "lbm3_step",
            "lbm3_read_fields", "lbm3_diagnostics", "lbm3_step_count", "lbm3_last_error",
            "lbm3_destroy", "lbm3_lattice")
 FIELDS3 = ("phi", "fs", "fl", "T", "rhoH", "p", "ux", "uy", "uz", "rho", "mu", "w", "mdot")
@@ -110,6 +110,8 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     L.lbm_adjoint_frozen_fraction.argtypes = [vp, ctypes.c_int64, ctypes.c_int, dp, dp, vp]
     L.lbm_adjoint_crossing.argtypes = [vp, ctypes.c_int64, ctypes.c_int, ctypes.c_int,
                                        ctypes.c_int, dp, dp, vp]
+    L.lbm_adjoint_freezing.argtypes = [vp, ctypes.c_int64, ctypes.c_int, ctypes.c_int,
+                                       ctypes.c_int, ctypes.c_int, dp, dp, vp]
     L.lbm3_create.argtypes = [ctypes.POINTER(Lbm3Params), ctypes.POINTER(vp)]
     L.lbm3_set_geometry.argtypes = [vp, vp, vp, vp, vp, vp, ctypes.c_int, vp]
     L.lbm3_step.argtypes = [vp, ctypes.c_int64, vp]
@@ -132,7 +134,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
                "lbm_batch_create", "lbm_batch_step", "lbm_probe_fma_rate",
                "lbm_read_crossings", "lbm_read_crossings_tangent", "lbm_read_tangent_fields",
                "lbm_read_tangent_diagnostics", "lbm_autotune", "lbm_adjoint_frozen_fraction",
-               "lbm_adjoint_crossing"):
+               "lbm_adjoint_crossing", "lbm_adjoint_freezing"):
         getattr(L, fn).restype = ctypes.c_int
     _lib = L
     return L
@@ -243,6 +245,19 @@ def lbm_adjoint_crossing(ctx, nsteps: int, every: int, axis: int, index: int, st
                                             ctypes.byref(pos), grad, stream),
            "lbm_adjoint_crossing")
     return pos.value, list(grad)
+
+
+def lbm_adjoint_freezing(ctx, nsteps: int, every: int, observable: int, axis: int = 0,
+                         index: int = 0, stream=None):
+    """(observable after nsteps steps -- 0: frozen fraction, 1: the phi = 0
+    crossing along (axis, index) -- and its gradient w.r.t. (T_wall[0..3],
+    latent, theta_deg, sigma)); see include/lbm.h."""
+    val = ctypes.c_double()
+    grad = (ctypes.c_double * 7)()
+    _check(ctx, load().lbm_adjoint_freezing(ctx, int(nsteps), int(every), int(observable),
+                                            int(axis), int(index), ctypes.byref(val), grad,
+                                            stream), "lbm_adjoint_freezing")
+    return val.value, list(grad)
 
 
 VARIANTS = ("fused, periods >= 32", "fused, periods >= 256", "split, periods >= 32",
@@ -426,6 +441,13 @@ class Solver:
         gradient with respect to (theta_deg, sigma)) by reverse mode
         (phase-field-only FP64 contexts; see lbm_adjoint_crossing)."""
         return lbm_adjoint_crossing(self.ctx, nsteps, every, axis, index, _stream())
+
+    def adjoint_freezing(self, nsteps: int, observable: int = 0, axis: int = 0, index: int = 0,
+                         every: int = 64):
+        """Advance nsteps and return (observable, gradient w.r.t. (T_wall[0..3],
+        latent, theta_deg, sigma)) by reverse mode of the coupled phase-field
+        and enthalpy step (see lbm_adjoint_freezing)."""
+        return lbm_adjoint_freezing(self.ctx, nsteps, every, observable, axis, index, _stream())
 
     def autotune(self, steps_per_trial: int = 64):
         """Pick the fastest step form for this grid (state unchanged)."""

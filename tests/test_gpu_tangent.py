@@ -445,3 +445,108 @@ def test_adjoints_behind_autograd(env):
     t.close()
     assert abs(float(ff.detach()) - fz / mv) <= 1e-12 * float(ff.detach())
     assert abs(float(qh.grad[0]) - tan) <= 1e-9 * abs(tan)
+
+
+def _frz_state(seed, n=(40, 24)):
+    """A random three-phase state with the phase field and the enthalpy
+    lattice only (fluid at rest), without cold mask: ice, drops, a mushy
+    band and walls of every kind, so freezing couples the two lattices."""
+    cfg, arr = W.random_state(*n, seed=seed, lattices=W.PHASE | W.HEAT)
+    return cfg, {k: v for k, v in arr.items() if k != "mask"}
+
+
+@pytest.mark.parametrize("seed", [1, 3, 4])
+def test_coupled_adjoint_equals_the_tangent(env, seed):
+    """The reverse sweep of the coupled phase-field + enthalpy step gives the
+    derivatives of the frozen fraction and of an interface crossing with
+    respect to the wall temperatures, L, theta (equal to the forward-mode
+    tangent of the same steps) and sigma (central differences)."""
+    O, lbm, S, torch = env
+    cfg, arr = _frz_state(seed)
+    steps = 200
+    plain = lbm.Solver(cfg, precision="fp64").set_geometry(arr).step(steps)
+    col = next(i for i in range(cfg["nx"]) if np.isfinite(plain.crossings(1, i)[0]))
+    plain.close()
+    res = {}
+    for obs in (0, 1):
+        s = lbm.Solver(cfg, precision="fp64").set_geometry(arr)
+        res[obs] = s.adjoint_freezing(steps, obs, 1, col, every=37)
+        s.close()
+    dirs = [("T_wall", k) for k in range(4) if cfg["bc"][k] == "dirichlet"] + [("latent", 4), ("theta_deg", 5)]
+    rows = []
+    for name, k in dirs:
+        t = ({"T_wall": [1.0 if j == k else 0.0 for j in range(4)]} if name == "T_wall" else {name: 1.0})
+        ts = lbm.Solver(cfg, precision="tangent", tangent=t).set_geometry(arr).step(steps)
+        d, dt = ts.diagnostics(), ts.tangent_diagnostics(compute=False)
+        fz, mv = d["frozen_volume"], d["material_volume"]
+        dff = (dt["frozen_volume"] * mv - fz * dt["material_volume"]) / mv ** 2
+        cr = ts.crossings_tangent(1, col)
+        ts.close()
+        assert abs(fz / mv - res[0][0]) <= 1e-12
+        assert abs(cr[0] - res[1][0]) <= 1e-12 * abs(cr[0])
+        rows.append((name, k, res[0][1][k], dff, res[1][1][k], cr[2]))
+
+    def val(c, obs):
+        u = lbm.Solver(c, precision="fp64").set_geometry(arr).step(steps)
+        d = u.diagnostics()
+        v = d["frozen_volume"] / d["material_volume"] if obs == 0 else u.crossings(1, col)[0]
+        u.close()
+        return v
+
+    hs = 1e-5 * cfg["sigma"]
+    for obs in (0, 1):
+        fd = (val(dict(cfg, sigma=cfg["sigma"] + hs), obs) - val(dict(cfg, sigma=cfg["sigma"] - hs), obs)) / (2 * hs)
+        rows.append(("sigma FD", 6, res[obs][1][6], fd, None, None) if obs == 0 else ("sigma FD", 6, None, None, res[obs][1][6], fd))
+    print(f"\nseed {seed}, column {col}: FF {res[0][0]:.10f}, crossing {res[1][0]:.8f}")
+    for r in rows:
+        print("  ", r)
+    scale_ff = max(abs(r[3]) for r in rows if r[3] is not None and r[0] != "sigma FD")
+    scale_cr = max(abs(r[5]) for r in rows if r[5] is not None and r[0] != "sigma FD")
+    for name, k, aff, tff, acr, tcr in rows:
+        if name == "sigma FD":
+            if aff is not None:
+                assert abs(aff - tff) <= 1e-4 * abs(tff) + 1e-9, (name, aff, tff)
+            else:
+                assert abs(acr - tcr) <= 1e-4 * abs(tcr) + 1e-7, (name, acr, tcr)
+            continue
+        assert abs(aff - tff) <= 1e-8 * max(abs(tff), 1e-4 * scale_ff), (name, k, aff, tff)
+        assert abs(acr - tcr) <= 1e-8 * max(abs(tcr), 1e-4 * scale_cr), (name, k, acr, tcr)
+    for k in range(4):
+        if cfg["bc"][k] != "dirichlet":
+            assert res[0][1][k] == 0.0 and res[1][1][k] == 0.0
+
+
+def test_coupled_adjoint_checkpoints_and_rejections(env):
+    """The checkpoint interval does not change the coupled gradient (bit for
+    bit: every reduction and gather runs in a fixed order); the context ends
+    in the state of plain steps; other contexts are refused."""
+    O, lbm, S, torch = env
+    cfg, arr = _frz_state(3)
+    steps = 60
+    out = []
+    for every in (1, 13, 60):
+        s = lbm.Solver(cfg, precision="fp64").set_geometry(arr)
+        out.append(s.adjoint_freezing(steps, 0, every=every))
+        if every == 13:
+            f_adj = s.fields()
+        s.close()
+    assert all(o == out[0] for o in out[1:]), out
+    plain = lbm.Solver(cfg, precision="fp64").set_geometry(arr).step(steps)
+    f_plain = plain.fields()
+    plain.close()
+    for k in FIELDS:
+        assert np.array_equal(f_adj[k], f_plain[k]), k
+    masked = W.random_state(40, 24, seed=3, lattices=W.PHASE | W.HEAT)
+    for c, a, prec in ((cfg, arr, "fp32"), (dict(cfg, lattices=7), arr, "fp64"),
+                       (masked[0], masked[1], "fp64"), (dict(cfg, sigma=0.0), arr, "fp64")):
+        s = lbm.Solver(c, precision=prec).set_geometry(a)
+        with pytest.raises(lbm.LbmError) as e:
+            s.adjoint_freezing(5, 0, every=5)
+        assert e.value.status == -6
+        s.close()
+    s = lbm.Solver(cfg, precision="fp64").set_geometry(arr)
+    for obs, axis, index in ((2, 0, 0), (1, 0, cfg["ny"]), (1, 3, 0)):
+        with pytest.raises(lbm.LbmError) as e:
+            s.adjoint_freezing(5, obs, axis, index, every=5)
+        assert e.value.status == -1
+    s.close()
