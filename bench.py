@@ -319,6 +319,9 @@ def back_to_back_line(args, rank, world):
 
 def adjoint_line(args, rank, world, every: int = 64):
     """Reverse sweep against K forward steps of the same context (FP64).
+    freezing: the frozen fraction of the 512^2 droplet with the phase field
+    and the enthalpy lattice coupled and its gradient w.r.t. (T_wall, L,
+    theta, sigma).
     heat: frozen fraction of a conduction-freezing column (Sec. 4.1 shape,
     2048 x 256, enthalpy lattice alone) and its gradient w.r.t. the wall
     temperatures and L.  phase: the tip height of a 512^2 sessile droplet
@@ -331,6 +334,12 @@ def adjoint_line(args, rank, world, every: int = 64):
     if args.adjoint == "phase":
         cfg, arr = W.sessile_droplet(512, seed=0)
         cfg = dict(cfg, lattices=W.PHASE)
+    elif args.adjoint == "freezing":
+        # the droplet cooled through its solid layer from the cold wall below
+        # (no cold mask), phase field and enthalpy lattices
+        cfg, arr = W.sessile_droplet(512, seed=0)
+        cfg = dict(cfg, lattices=W.PHASE | W.HEAT)
+        arr = {k: v for k, v in arr.items() if k != "mask"}
     else:
         cfg, arr = W.neumann(nx=2048, ny=256)
         cfg = dict(cfg, lattices=W.HEAT)
@@ -350,6 +359,8 @@ def adjoint_line(args, rank, world, every: int = 64):
     t0 = time.perf_counter()
     if args.adjoint == "phase":
         ff, grad = lbm.lbm_adjoint_crossing(s.ctx, K, every, 1, cfg["nx"] // 2, sptr)
+    elif args.adjoint == "freezing":
+        ff, grad = lbm.lbm_adjoint_freezing(s.ctx, K, every, 0, 0, 0, sptr)
     else:
         ff, grad = lbm.lbm_adjoint_frozen_fraction(s.ctx, K, every, sptr)
     t_adj = time.perf_counter() - t0
@@ -364,6 +375,10 @@ def adjoint_line(args, rank, world, every: int = 64):
         "config": {"workload": ("sessile droplet 512x512, phase-field lattice alone, tip height "
                                 "and its gradient w.r.t. contact angle and surface tension"
                                 if args.adjoint == "phase" else
+                                "sessile droplet 512x512 cooled through its solid layer, phase "
+                                "field + enthalpy lattices, frozen fraction and its gradient "
+                                "w.r.t. wall temperatures, latent heat, contact angle and surface "
+                                "tension" if args.adjoint == "freezing" else
                                 "conduction-freezing column 2048x256 (Sec. 4.1 shape), enthalpy "
                                 "lattice alone, frozen fraction and its gradient w.r.t. wall "
                                 "temperatures and latent heat"), "checkpoint_every": every},
@@ -371,6 +386,9 @@ def adjoint_line(args, rank, world, every: int = 64):
         "forward_ms_per_step": t_fwd / K * 1e3,
         **({"tip": ff, "grad": {"theta_deg": grad[0], "sigma": grad[1]}}
            if args.adjoint == "phase" else
+           {"ff": ff, "grad": {"T_wall": grad[:4], "latent": grad[4], "theta_deg": grad[5],
+                               "sigma": grad[6]}}
+           if args.adjoint == "freezing" else
            {"ff": ff, "grad": {"T_wall": grad[:4], "latent": grad[4]}}),
         "note": "host wall-clock around whole calls (synchronised); both include launch overheads",
     }
@@ -507,10 +525,12 @@ def main():
     ap.add_argument("--back-to-back", action="store_true",
                     help="context line for small grids: one call of K steps (captured CUDA "
                          "graphs), no L2 flush, against K single-step calls")
-    ap.add_argument("--adjoint", nargs="?", const="heat", choices=("heat", "phase"),
+    ap.add_argument("--adjoint", nargs="?", const="heat", choices=("heat", "phase", "freezing"),
                     help="time a reverse-mode gradient against its forward run (FP64): heat, the "
                          "frozen fraction of the conduction column 2048 x 256 (enthalpy lattice "
-                         "alone); phase, the tip height of the 512^2 droplet (phase field alone)")
+                         "alone); phase, the tip height of the 512^2 droplet (phase field alone); "
+                         "freezing, the frozen fraction of the 512^2 droplet (phase field and "
+                         "enthalpy coupled)")
     ap.add_argument("--workload", default="droplet512",
                     choices=sorted(WORKLOADS) + sorted(WORKLOADS3),
                     help="droplet512 is the headline; the others are context lines")

@@ -244,3 +244,30 @@ class AdjointCrossing:
         if cls._fn is None:
             cls._fn = _adjoint_fn("AdjointCrossing", _run_adjoint_crossing)
         return cls._fn.apply(q, cfg, arrays, steps, axis, index, every)
+
+
+def _run_adjoint_freezing(q, cfg, arrays, steps, observable, axis, index, every):
+    c = dict(cfg, T_wall=tuple(float(v) for v in q[:4]), latent=float(q[4]),
+             theta_deg=float(q[5]), sigma=float(q[6]))
+    s = lbm.Solver(c, precision="fp64").set_geometry(arrays)
+    try:
+        return s.adjoint_freezing(steps, observable, axis, index, every)
+    finally:
+        s.close()
+
+
+class AdjointFreezing:
+    """``AdjointFreezing.apply(q, cfg, arrays, steps, observable, axis, index,
+    every)``: the frozen fraction (observable 0) or an interface crossing
+    (observable 1, along grid line (axis, index)) after `steps` steps of the
+    coupled phase-field and enthalpy step (see lbm_adjoint_freezing), as a
+    differentiable function of q = (T_wall[0..3], latent, theta_deg, sigma),
+    from the initial fields."""
+
+    _fn = None
+
+    @classmethod
+    def apply(cls, q, cfg, arrays, steps, observable=0, axis=0, index=0, every=64):
+        if cls._fn is None:
+            cls._fn = _adjoint_fn("AdjointFreezing", _run_adjoint_freezing)
+        return cls._fn.apply(q, cfg, arrays, steps, observable, axis, index, every)

@@ -550,3 +550,17 @@ def test_coupled_adjoint_checkpoints_and_rejections(env):
             s.adjoint_freezing(5, obs, axis, index, every=5)
         assert e.value.status == -1
     s.close()
+
+
+def test_coupled_adjoint_behind_autograd(env):
+    O, lbm, S, torch = env
+    cfg, arr = _frz_state(3)
+    q = torch.tensor(list(cfg["T_wall"]) + [cfg["latent"], cfg["theta_deg"], cfg["sigma"]],
+                     dtype=torch.float64, requires_grad=True)
+    y = S.AdjointFreezing.apply(q, cfg, arr, 80, 0, 0, 0, 40)
+    (2.0 * y).backward()
+    s = lbm.Solver(cfg, precision="fp64").set_geometry(arr)
+    ff, grad = s.adjoint_freezing(80, 0, every=40)
+    s.close()
+    assert float(y.detach()) == ff
+    assert q.grad.tolist() == [2.0 * v for v in grad]
