@@ -334,11 +334,11 @@ def adjoint_line(args, rank, world, every: int = 64):
     if args.adjoint == "phase":
         cfg, arr = W.sessile_droplet(512, seed=0)
         cfg = dict(cfg, lattices=W.PHASE)
-    elif args.adjoint == "freezing":
+    elif args.adjoint in ("freezing", "coupled"):
         # the droplet cooled through its solid layer from the cold wall below
-        # (no cold mask), phase field and enthalpy lattices
+        # (no cold mask); phase field and enthalpy lattices, or all three
         cfg, arr = W.sessile_droplet(512, seed=0)
-        cfg = dict(cfg, lattices=W.PHASE | W.HEAT)
+        cfg = dict(cfg, lattices=W.PHASE | W.HEAT if args.adjoint == "freezing" else W.ALL)
         arr = {k: v for k, v in arr.items() if k != "mask"}
     else:
         cfg, arr = W.neumann(nx=2048, ny=256)
@@ -361,6 +361,8 @@ def adjoint_line(args, rank, world, every: int = 64):
         ff, grad = lbm.lbm_adjoint_crossing(s.ctx, K, every, 1, cfg["nx"] // 2, sptr)
     elif args.adjoint == "freezing":
         ff, grad = lbm.lbm_adjoint_freezing(s.ctx, K, every, 0, 0, 0, sptr)
+    elif args.adjoint == "coupled":
+        ff, grad = lbm.lbm_adjoint_coupled(s.ctx, K, every, 0, 0, 0, sptr)
     else:
         ff, grad = lbm.lbm_adjoint_frozen_fraction(s.ctx, K, every, sptr)
     t_adj = time.perf_counter() - t0
@@ -379,6 +381,10 @@ def adjoint_line(args, rank, world, every: int = 64):
                                 "field + enthalpy lattices, frozen fraction and its gradient "
                                 "w.r.t. wall temperatures, latent heat, contact angle and surface "
                                 "tension" if args.adjoint == "freezing" else
+                                "sessile droplet 512x512 cooled through its solid layer, all three "
+                                "lattices (moving fluid), frozen fraction and its gradient w.r.t. "
+                                "wall temperatures, latent heat, contact angle, surface tension "
+                                "and body force" if args.adjoint == "coupled" else
                                 "conduction-freezing column 2048x256 (Sec. 4.1 shape), enthalpy "
                                 "lattice alone, frozen fraction and its gradient w.r.t. wall "
                                 "temperatures and latent heat"), "checkpoint_every": every},
@@ -389,6 +395,9 @@ def adjoint_line(args, rank, world, every: int = 64):
            {"ff": ff, "grad": {"T_wall": grad[:4], "latent": grad[4], "theta_deg": grad[5],
                                "sigma": grad[6]}}
            if args.adjoint == "freezing" else
+           {"ff": ff, "grad": {"T_wall": grad[:4], "latent": grad[4], "theta_deg": grad[5],
+                               "sigma": grad[6], "gx": grad[7], "gy": grad[8]}}
+           if args.adjoint == "coupled" else
            {"ff": ff, "grad": {"T_wall": grad[:4], "latent": grad[4]}}),
         "note": "host wall-clock around whole calls (synchronised); both include launch overheads",
     }
@@ -525,12 +534,12 @@ def main():
     ap.add_argument("--back-to-back", action="store_true",
                     help="context line for small grids: one call of K steps (captured CUDA "
                          "graphs), no L2 flush, against K single-step calls")
-    ap.add_argument("--adjoint", nargs="?", const="heat", choices=("heat", "phase", "freezing"),
+    ap.add_argument("--adjoint", nargs="?", const="heat", choices=("heat", "phase", "freezing", "coupled"),
                     help="time a reverse-mode gradient against its forward run (FP64): heat, the "
                          "frozen fraction of the conduction column 2048 x 256 (enthalpy lattice "
                          "alone); phase, the tip height of the 512^2 droplet (phase field alone); "
                          "freezing, the frozen fraction of the 512^2 droplet (phase field and "
-                         "enthalpy coupled)")
+                         "enthalpy coupled); coupled, the same with all three lattices")
     ap.add_argument("--workload", default="droplet512",
                     choices=sorted(WORKLOADS) + sorted(WORKLOADS3),
                     help="droplet512 is the headline; the others are context lines")

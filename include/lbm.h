@@ -363,6 +363,19 @@ int lbm_adjoint_crossing(lbm_ctx* ctx, int64_t nsteps, int every, int axis, int 
 int lbm_adjoint_freezing(lbm_ctx* ctx, int64_t nsteps, int every, int observable, int axis,
                          int index, double* value, double* grad, void* stream);
 
+/* Reverse mode (adjoint) of the whole coupled step: as lbm_adjoint_freezing
+ * for a context with precision LBM_FP64, all three lattices, no cold mask,
+ * readings == 0 and sigma > 0, with the flow lattice moving -- the velocity
+ * of Eq. (17a,b) with the surface-tension, body and penalty forces, the
+ * source S and the modified force of Eq. (16) (with the lagged pressure
+ * gradient), the pressure of Eq. (17c), the flow collision, and phi u and u
+ * in the phase and enthalpy equilibria all reversed, with the transposed
+ * gradients of phi, rho and the lagged pressure.  grad[0..8]: d/dT_wall[0..3],
+ * d/dL, d/dtheta_deg, d/dsigma, d/dgx, d/dgy.  Errors as
+ * lbm_adjoint_freezing. */
+int lbm_adjoint_coupled(lbm_ctx* ctx, int64_t nsteps, int every, int observable, int axis,
+                        int index, double* value, double* grad, void* stream);
+
 /* Autotuner (the paper gives no implementation; a measuring aid of this
  * library): times the step forms this build has on the context's own grid
  * and state and keeps the fastest for later lbm_step calls.  Variants, in

@@ -1,5 +1,6 @@
 // lbm_adjoint.cu -- launchers of the enthalpy-lattice and phase-field adjoint kernels.
 #include "lbm_adjoint.cuh"
+#include "lbm_adjoint_full.cuh"
 #include "lbm_launch.h"
 
 namespace lbmk {
@@ -69,6 +70,31 @@ cudaError_t launch_frz_seed_ff(const FrzArgs& a, cudaStream_t s) {
 
 cudaError_t launch_frz_seed_crossing(const FrzArgs& a, double* phib, cudaStream_t s) {
   lbm_frz_seed_crossing_kernel<<<1, 32, 0, s>>>(a, phib);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_full_fields(const FullArgs& a, cudaStream_t s) {
+  lbm_full_fields_kernel<<<grid_dims(a.g), block_dims(), 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_full_k1(const FullArgs& a, cudaStream_t s) {
+  lbm_full_k1_kernel<<<grid_dims(a.g), block_dims(), 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_full_k2(const FullArgs& a, cudaStream_t s) {
+  lbm_full_k2_kernel<<<grid_dims(a.g), block_dims(), 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_full_seed_ff(const FullArgs& a, double* llag, cudaStream_t s) {
+  lbm_full_seed_ff_kernel<<<grid_dims(a.g), block_dims(), 0, s>>>(a, llag);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_full_seed_crossing(const FullArgs& a, double* phib, cudaStream_t s) {
+  lbm_full_seed_crossing_kernel<<<1, 32, 0, s>>>(a, phib);
   return cudaGetLastError();
 }
 

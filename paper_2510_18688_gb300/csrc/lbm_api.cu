@@ -20,6 +20,7 @@
 #include "../../include/lbm.h"
 #include "lbm_host.h"
 #include "lbm_adjoint.cuh"
+#include "lbm_adjoint_full.cuh"
 #include "lbm_launch.h"
 
 using lbmk::Args;
@@ -1183,6 +1184,194 @@ extern "C" int lbm_adjoint_freezing(lbm_ctx* c, int64_t nsteps, int every, int o
   if (st != LBM_OK) return st;
   *value_out = observable == 0 ? ffv : hg[10];
   for (int k = 0; k < lbmk::FRZ_NACC; k++) grad[k] = hg[k];
+  c->last_stream = s;
+  return LBM_OK;
+}
+
+// ---------------------------------------------------------------------------
+// reverse mode: the whole coupled step (flow, phase field, enthalpy)
+// ---------------------------------------------------------------------------
+
+extern "C" int lbm_adjoint_coupled(lbm_ctx* c, int64_t nsteps, int every, int observable,
+                                   int axis, int index, double* value_out, double* grad,
+                                   void* stream) {
+  if (!c) return LBM_ERR_ARG;
+  if (!value_out || !grad) return fail(c, LBM_ERR_ARG, "null output%s");
+  if (nsteps < 1 || every < 1) return fail(c, LBM_ERR_ARG, "nsteps and the checkpoint interval must be >= 1%s");
+  if (observable != 0 && observable != 1) return fail(c, LBM_ERR_ARG, "observable must be 0 or 1%s");
+  if (observable == 1 &&
+      ((axis != 0 && axis != 1) || index < 0 || index >= (axis == 0 ? c->p.ny : c->p.nx)))
+    return fail(c, LBM_ERR_ARG, "axis must be 0 or 1 and index a line of the grid%s");
+  if (!c->have_geometry) return fail(c, LBM_ERR_STATE, "adjoint before lbm_set_geometry%s");
+  if (c->p.precision != LBM_FP64 || c->p.lattices != (LBM_LAT_FLOW | LBM_LAT_PHASE | LBM_LAT_HEAT) ||
+      c->g.has_mask || c->p.readings != 0 || !(c->p.sigma > 0.0))
+    return fail(c, LBM_ERR_UNSUPPORTED,
+                "the coupled-step adjoint covers FP64 contexts with all three lattices, no cold "
+                "mask, readings == 0 and sigma > 0%s");
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t P = (size_t)c->g.plane;
+  const size_t pN = 27 * P, lN = lbmk::NLAG * P, stN = pN + lN;
+  const int64_t nck = (nsteps + every - 1) / every;
+  const int64_t seglen = std::min<int64_t>(every, nsteps);
+  // work planes: two adjoint sets of (27 populations, NLAG lags); phi, fs,
+  // rho; 7 stencil adjoints; the seed's phi adjoint and lag adjoints
+  const size_t setN = (27 + lbmk::NLAG) * P;
+  const size_t wN = 2 * setN + (3 + 7 + 1 + lbmk::NLAG) * P;
+  const int nacc = 10;
+  double *ck = nullptr, *seg = nullptr, *wk = nullptr, *acc = nullptr, *dout = nullptr,
+         *fin = nullptr;
+  cudaError_t e = cudaMalloc(&ck, nck * stN * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&seg, seglen * stN * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&wk, wN * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&acc, nacc * P * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&dout, 11 * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&fin, stN * sizeof(double));
+  auto release = [&]() {
+    for (double* p : {ck, seg, wk, acc, dout, fin})
+      if (p) cudaFree(p);
+  };
+  if (e != cudaSuccess) {
+    release();
+    return cuda_fail(c, e, "adjoint allocation");
+  }
+  auto save = [&](double* dst) {
+    cudaError_t r = cudaMemcpyAsync(dst, c->pop[c->cur], pN * sizeof(double), cudaMemcpyDeviceToDevice, s);
+    if (r == cudaSuccess)
+      r = cudaMemcpyAsync(dst + pN, c->lag[c->cur], lN * sizeof(double), cudaMemcpyDeviceToDevice, s);
+    return r;
+  };
+  int st = LBM_OK;
+  const int64_t step0 = c->step;
+  std::vector<int> ckpar((size_t)nck);
+  for (int64_t k = 0; k < nsteps && e == cudaSuccess && st == LBM_OK; k++) {
+    if (k % every == 0) {
+      ckpar[(size_t)(k / every)] = c->cur;
+      e = save(ck + (k / every) * stN);
+    }
+    if (e == cudaSuccess) st = lbm_step(c, 1, s);
+  }
+  double ffv = 0.0, inv_sum_w = 0.0;
+  if (e == cudaSuccess && st == LBM_OK && observable == 0) {
+    st = lbm_compute_diagnostics(c, s);
+    lbm_diag d;
+    if (st == LBM_OK) st = lbm_read_diagnostics(c, &d);
+    if (st == LBM_OK) {
+      ffv = d.frozen_volume / d.material_volume;
+      inv_sum_w = 1.0 / d.material_volume;
+    }
+  }
+  const int parN = c->cur;
+  if (e == cudaSuccess && st == LBM_OK) e = save(fin);
+  if (e == cudaSuccess) e = cudaMemsetAsync(acc, 0, nacc * P * sizeof(double), s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(wk, 0, wN * sizeof(double), s);
+  const double pi = 3.14159265358979323846;
+  double* lb[2] = {wk, wk + setN};
+  double* fld = wk + 2 * setN;
+  double* sbp = fld + 3 * P;
+  double* phib_seed = sbp + 7 * P;
+  double* seed_lag = phib_seed + P;
+  lbmk::FullArgs a;
+  std::memset(&a, 0, sizeof(a));
+  a.g = c->g;
+  a.c = c->cd;
+  a.phi0 = (const double*)c->phi0;
+  a.phi = fld;
+  a.fs = fld + P;
+  a.rho = fld + 2 * P;
+  a.sb = sbp;
+  a.acc = acc;
+  a.dcos_dtheta = -std::sin(c->p.theta_deg * pi / 180.0) * (pi / 180.0);
+  a.inv_sum_w = inv_sum_w;
+  a.ff = ffv;
+  a.axis = axis;
+  a.index = index;
+  a.out = dout + 10;
+  auto set_io = [&](int in, int out) {
+    a.lam_in = lb[in];
+    a.llag_in = lb[in] + pN;
+    a.lam_out = lb[out];
+    a.llag_out = lb[out] + pN;
+  };
+  int cur_adj = 0;
+  if (e == cudaSuccess && st == LBM_OK) {
+    a.pop = (const double*)c->pop[parN];
+    a.lag = (const double*)c->lag[parN];
+    e = lbmk::launch_full_fields(a, s);
+    set_io(1, 0);
+    if (observable == 0) {
+      if (e == cudaSuccess) e = lbmk::launch_full_seed_ff(a, seed_lag, s);
+      a.llag_in = seed_lag;
+    } else {
+      if (e == cudaSuccess) e = lbmk::launch_full_seed_crossing(a, phib_seed, s);
+      a.phib_seed = phib_seed;
+    }
+    if (e == cudaSuccess) e = lbmk::launch_full_k2(a, s);
+    a.phib_seed = nullptr;
+  }
+  for (int64_t sg = nck - 1; sg >= 0 && e == cudaSuccess && st == LBM_OK; sg--) {
+    const int64_t k0 = sg * every, k1 = std::min<int64_t>(k0 + every, nsteps);
+    const int par = ckpar[(size_t)sg];
+    e = cudaMemcpyAsync(c->pop[par], ck + sg * stN, pN * sizeof(double), cudaMemcpyDeviceToDevice, s);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(c->lag[par], ck + sg * stN + pN, lN * sizeof(double),
+                          cudaMemcpyDeviceToDevice, s);
+    c->cur = par;
+    c->step = step0 + k0;
+    c->gen++;
+    for (int64_t j = 0; j < k1 - k0 && e == cudaSuccess && st == LBM_OK; j++) {
+      e = save(seg + j * stN);
+      if (e == cudaSuccess) st = lbm_step(c, 1, s);
+    }
+    for (int64_t j = k1 - k0 - 1; j >= 0 && e == cudaSuccess && st == LBM_OK; j--) {
+      a.pop = seg + j * stN;
+      a.lag = seg + j * stN + pN;
+      set_io(cur_adj, cur_adj ^ 1);
+      e = lbmk::launch_full_fields(a, s);
+      if (e == cudaSuccess) e = lbmk::launch_full_k1(a, s);
+      if (e == cudaSuccess) e = lbmk::launch_full_k2(a, s);
+      cur_adj ^= 1;
+    }
+  }
+  if (e == cudaSuccess && st == LBM_OK && step0 == 0) {
+    lbmk::AdjArgs ha;
+    std::memset(&ha, 0, sizeof(ha));
+    ha.g = c->g;
+    ha.c = c->cd;
+    ha.lam_in = lb[cur_adj] + 18 * P;
+    ha.lag = ck + pN;
+    ha.acc = acc;
+    e = lbmk::launch_adjoint_init(ha, s);
+    lbmk::PhaseAdjArgs pa;
+    std::memset(&pa, 0, sizeof(pa));
+    pa.g = c->g;
+    pa.c = c->cd;
+    pa.lam_in = lb[cur_adj] + 9 * P;
+    pa.phi = fld;
+    pa.fs = fld + P;
+    pa.phi0 = (const double*)c->phi0;
+    pa.acc = acc + 5 * P;
+    pa.dcos_dtheta = a.dcos_dtheta;
+    if (e == cudaSuccess) e = lbmk::launch_phase_adjoint_init(pa, s);
+  }
+  double hg[11] = {0};
+  if (e == cudaSuccess && st == LBM_OK) e = lbmk::launch_adjoint_reduce(acc, c->g, dout, s);
+  if (e == cudaSuccess && st == LBM_OK) e = lbmk::launch_adjoint_reduce(acc + 5 * P, c->g, dout + 5, s);
+  if (e == cudaSuccess && st == LBM_OK)
+    e = cudaMemcpyAsync(hg, dout, sizeof(hg), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess && st == LBM_OK)
+    e = cudaMemcpyAsync(c->pop[parN], fin, pN * sizeof(double), cudaMemcpyDeviceToDevice, s);
+  if (e == cudaSuccess && st == LBM_OK)
+    e = cudaMemcpyAsync(c->lag[parN], fin + pN, lN * sizeof(double), cudaMemcpyDeviceToDevice, s);
+  c->cur = parN;
+  c->step = step0 + nsteps;
+  c->gen++;
+  if (e == cudaSuccess && st == LBM_OK) st = lbm_compute_diagnostics(c, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  release();
+  if (e != cudaSuccess) return cuda_fail(c, e, "adjoint");
+  if (st != LBM_OK) return st;
+  *value_out = observable == 0 ? ffv : hg[10];
+  for (int k = 0; k < lbmk::FULL_NACC; k++) grad[k] = hg[k];
   c->last_stream = s;
   return LBM_OK;
 }

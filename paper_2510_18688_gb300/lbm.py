@@ -61,7 +61,7 @@ EXPORTS = ("lbm_create", "lbm_set_geometry", "lbm_step", "lbm_read_fields",
            "lbm_batch_create", "lbm_batch_step", "lbm_batch_destroy", "lbm_probe_fma_rate",
            "lbm_read_crossings", "lbm_read_tangent_fields", "lbm_read_tangent_diagnostics",
            "lbm_read_crossings_tangent", "lbm_autotune", "lbm_adjoint_frozen_fraction",
-           "lbm_adjoint_crossing", "lbm_adjoint_freezing", "lbm3_create", "lbm3_set_geometry", "lbm3_step",
+           "lbm_adjoint_crossing", "lbm_adjoint_freezing", "lbm_adjoint_coupled", "lbm3_create", "lbm3_set_geometry", "lbm3_step",
            "lbm3_read_fields", "lbm3_diagnostics", "lbm3_step_count", "lbm3_last_error",
            "lbm3_destroy", "lbm3_lattice")
 FIELDS3 = ("phi", "fs", "fl", "T", "rhoH", "p", "ux", "uy", "uz", "rho", "mu", "w", "mdot")
@@ -112,6 +112,8 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
                                        ctypes.c_int, dp, dp, vp]
     L.lbm_adjoint_freezing.argtypes = [vp, ctypes.c_int64, ctypes.c_int, ctypes.c_int,
                                        ctypes.c_int, ctypes.c_int, dp, dp, vp]
+    L.lbm_adjoint_coupled.argtypes = [vp, ctypes.c_int64, ctypes.c_int, ctypes.c_int,
+                                      ctypes.c_int, ctypes.c_int, dp, dp, vp]
     L.lbm3_create.argtypes = [ctypes.POINTER(Lbm3Params), ctypes.POINTER(vp)]
     L.lbm3_set_geometry.argtypes = [vp, vp, vp, vp, vp, vp, ctypes.c_int, vp]
     L.lbm3_step.argtypes = [vp, ctypes.c_int64, vp]
@@ -134,7 +136,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
                "lbm_batch_create", "lbm_batch_step", "lbm_probe_fma_rate",
                "lbm_read_crossings", "lbm_read_crossings_tangent", "lbm_read_tangent_fields",
                "lbm_read_tangent_diagnostics", "lbm_autotune", "lbm_adjoint_frozen_fraction",
-               "lbm_adjoint_crossing", "lbm_adjoint_freezing"):
+               "lbm_adjoint_crossing", "lbm_adjoint_freezing", "lbm_adjoint_coupled"):
         getattr(L, fn).restype = ctypes.c_int
     _lib = L
     return L
@@ -257,6 +259,19 @@ def lbm_adjoint_freezing(ctx, nsteps: int, every: int, observable: int, axis: in
     _check(ctx, load().lbm_adjoint_freezing(ctx, int(nsteps), int(every), int(observable),
                                             int(axis), int(index), ctypes.byref(val), grad,
                                             stream), "lbm_adjoint_freezing")
+    return val.value, list(grad)
+
+
+def lbm_adjoint_coupled(ctx, nsteps: int, every: int, observable: int, axis: int = 0,
+                        index: int = 0, stream=None):
+    """(observable after nsteps steps of the whole coupled step and its
+    gradient w.r.t. (T_wall[0..3], latent, theta_deg, sigma, gx, gy)); see
+    include/lbm.h."""
+    val = ctypes.c_double()
+    grad = (ctypes.c_double * 9)()
+    _check(ctx, load().lbm_adjoint_coupled(ctx, int(nsteps), int(every), int(observable),
+                                           int(axis), int(index), ctypes.byref(val), grad,
+                                           stream), "lbm_adjoint_coupled")
     return val.value, list(grad)
 
 
@@ -448,6 +463,13 @@ class Solver:
         latent, theta_deg, sigma)) by reverse mode of the coupled phase-field
         and enthalpy step (see lbm_adjoint_freezing)."""
         return lbm_adjoint_freezing(self.ctx, nsteps, every, observable, axis, index, _stream())
+
+    def adjoint_coupled(self, nsteps: int, observable: int = 0, axis: int = 0, index: int = 0,
+                        every: int = 64):
+        """Advance nsteps and return (observable, gradient w.r.t. (T_wall[0..3],
+        latent, theta_deg, sigma, gx, gy)) by reverse mode of the whole coupled
+        step (see lbm_adjoint_coupled)."""
+        return lbm_adjoint_coupled(self.ctx, nsteps, every, observable, axis, index, _stream())
 
     def autotune(self, steps_per_trial: int = 64):
         """Pick the fastest step form for this grid (state unchanged)."""

@@ -271,3 +271,30 @@ class AdjointFreezing:
         if cls._fn is None:
             cls._fn = _adjoint_fn("AdjointFreezing", _run_adjoint_freezing)
         return cls._fn.apply(q, cfg, arrays, steps, observable, axis, index, every)
+
+
+def _run_adjoint_coupled(q, cfg, arrays, steps, observable, axis, index, every):
+    c = dict(cfg, T_wall=tuple(float(v) for v in q[:4]), latent=float(q[4]),
+             theta_deg=float(q[5]), sigma=float(q[6]), gx=float(q[7]), gy=float(q[8]))
+    s = lbm.Solver(c, precision="fp64").set_geometry(arrays)
+    try:
+        return s.adjoint_coupled(steps, observable, axis, index, every)
+    finally:
+        s.close()
+
+
+class AdjointCoupled:
+    """``AdjointCoupled.apply(q, cfg, arrays, steps, observable, axis, index,
+    every)``: the frozen fraction (observable 0) or an interface crossing
+    (observable 1) after `steps` steps of the whole coupled step (see
+    lbm_adjoint_coupled) as a differentiable function of
+    q = (T_wall[0..3], latent, theta_deg, sigma, gx, gy), from the initial
+    fields."""
+
+    _fn = None
+
+    @classmethod
+    def apply(cls, q, cfg, arrays, steps, observable=0, axis=0, index=0, every=64):
+        if cls._fn is None:
+            cls._fn = _adjoint_fn("AdjointCoupled", _run_adjoint_coupled)
+        return cls._fn.apply(q, cfg, arrays, steps, observable, axis, index, every)

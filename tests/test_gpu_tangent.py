@@ -564,3 +564,90 @@ def test_coupled_adjoint_behind_autograd(env):
     s.close()
     assert float(y.detach()) == ff
     assert q.grad.tolist() == [2.0 * v for v in grad]
+
+
+def _full_state(seed, n=(40, 24), g=(2e-5, -3e-5)):
+    """A random three-phase state with all three lattices and no cold mask;
+    a body force strong enough that the flow carries the interfaces."""
+    cfg, arr = W.random_state(*n, seed=seed, lattices=W.FLOW | W.PHASE | W.HEAT)
+    return dict(cfg, gx=g[0], gy=g[1]), {k: v for k, v in arr.items() if k != "mask"}
+
+
+@pytest.mark.parametrize("seed", [1, 3])
+def test_full_adjoint_equals_the_tangent(env, seed):
+    """The reverse sweep of the whole coupled step (moving fluid) against
+    the forward-mode tangent (wall temperatures, L, theta) and central
+    differences (sigma, the body force)."""
+    O, lbm, S, torch = env
+    cfg, arr = _full_state(seed)
+    steps = 150
+    plain = lbm.Solver(cfg, precision="fp64").set_geometry(arr).step(steps)
+    assert np.abs(plain.fields(("ux",))["ux"]).max() > 1e-5
+    col = next(i for i in range(cfg["nx"]) if np.isfinite(plain.crossings(1, i)[0]))
+    plain.close()
+    res = {}
+    for obs in (0, 1):
+        s = lbm.Solver(cfg, precision="fp64").set_geometry(arr)
+        res[obs] = s.adjoint_coupled(steps, obs, 1, col, every=37)
+        s.close()
+    rows = []
+    dirs = [("T_wall", k) for k in range(4) if cfg["bc"][k] == "dirichlet"] + [("latent", 4), ("theta_deg", 5)]
+    for name, k in dirs:
+        t = ({"T_wall": [1.0 if j == k else 0.0 for j in range(4)]} if name == "T_wall" else {name: 1.0})
+        ts = lbm.Solver(cfg, precision="tangent", tangent=t).set_geometry(arr).step(steps)
+        d, dt = ts.diagnostics(), ts.tangent_diagnostics(compute=False)
+        fz, mv = d["frozen_volume"], d["material_volume"]
+        dff = (dt["frozen_volume"] * mv - fz * dt["material_volume"]) / mv ** 2
+        cr = ts.crossings_tangent(1, col)
+        ts.close()
+        rows.append((name, k, res[0][1][k], dff, res[1][1][k], cr[2]))
+
+    def val(c, obs):
+        u = lbm.Solver(c, precision="fp64").set_geometry(arr).step(steps)
+        d = u.diagnostics()
+        v = d["frozen_volume"] / d["material_volume"] if obs == 0 else u.crossings(1, col)[0]
+        u.close()
+        return v
+
+    fds = []
+    for name, k, h in (("sigma", 6, 1e-5 * cfg["sigma"]), ("gx", 7, 1e-4 * abs(cfg["gx"])),
+                       ("gy", 8, 1e-4 * abs(cfg["gy"]))):
+        for obs in (0, 1):
+            fd = (val(dict(cfg, **{name: cfg[name] + h}), obs)
+                  - val(dict(cfg, **{name: cfg[name] - h}), obs)) / (2 * h)
+            fds.append((name, obs, res[obs][1][k], fd))
+    print(f"\nseed {seed}, column {col}: FF {res[0][0]:.10f}, crossing {res[1][0]:.8f}")
+    for r in rows + fds:
+        print("  ", r)
+    for name, k, aff, tff, acr, tcr in rows:
+        assert abs(aff - tff) <= 1e-8 * abs(tff) + 1e-13, (name, k, aff, tff)
+        assert abs(acr - tcr) <= 1e-8 * abs(tcr) + 1e-11, (name, k, acr, tcr)
+    for name, obs, adj, fd in fds:
+        assert abs(adj - fd) <= 1e-5 * abs(fd) + (1e-10 if obs == 0 else 1e-8), (name, obs, adj, fd)
+
+
+def test_full_adjoint_checkpoints_and_rejections(env):
+    O, lbm, S, torch = env
+    cfg, arr = _full_state(3)
+    steps = 50
+    out = []
+    for every in (1, 17, 50):
+        s = lbm.Solver(cfg, precision="fp64").set_geometry(arr)
+        out.append(s.adjoint_coupled(steps, 1, 1, 0, every=every))
+        if every == 17:
+            f_adj = s.fields()
+        s.close()
+    assert all(o == out[0] for o in out[1:]), out
+    plain = lbm.Solver(cfg, precision="fp64").set_geometry(arr).step(steps)
+    f_plain = plain.fields()
+    plain.close()
+    for k in FIELDS:
+        assert np.array_equal(f_adj[k], f_plain[k]), k
+    masked = W.random_state(40, 24, seed=3)
+    for c, a, prec in ((cfg, arr, "fp32"), (dict(cfg, lattices=6), arr, "fp64"),
+                       (masked[0], masked[1], "fp64"), (dict(cfg, readings=1), arr, "fp64")):
+        s = lbm.Solver(c, precision=prec).set_geometry(a)
+        with pytest.raises(lbm.LbmError) as e:
+            s.adjoint_coupled(5, 0, every=5)
+        assert e.value.status == -6
+        s.close()
