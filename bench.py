@@ -362,7 +362,7 @@ def adjoint_line(args, rank, world, every: int = 64):
     elif args.adjoint == "freezing":
         ff, grad = lbm.lbm_adjoint_freezing(s.ctx, K, every, 0, 0, 0, sptr)
     elif args.adjoint == "coupled":
-        ff, grad = lbm.lbm_adjoint_coupled(s.ctx, K, every, 0, 0, 0, sptr)
+        ff, grad = lbm.lbm_adjoint_coupled(s.ctx, K, every, 0, 0, 0, None, sptr)
     else:
         ff, grad = lbm.lbm_adjoint_frozen_fraction(s.ctx, K, every, sptr)
     t_adj = time.perf_counter() - t0

@@ -371,10 +371,13 @@ int lbm_adjoint_freezing(lbm_ctx* ctx, int64_t nsteps, int every, int observable
  * gradient), the pressure of Eq. (17c), the flow collision, and phi u and u
  * in the phase and enthalpy equilibria all reversed, with the transposed
  * gradients of phi, rho and the lagged pressure.  grad[0..8]: d/dT_wall[0..3],
- * d/dL, d/dtheta_deg, d/dsigma, d/dgx, d/dgy.  Errors as
+ * d/dL, d/dtheta_deg, d/dsigma, d/dgx, d/dgy.  dT0 (host memory for
+ * [ny][nx] doubles, or NULL): the gradient with respect to the initial
+ * temperature field of lbm_set_geometry, node by node (the call must then
+ * start at step 0, else LBM_ERR_STATE).  Other errors as
  * lbm_adjoint_freezing. */
 int lbm_adjoint_coupled(lbm_ctx* ctx, int64_t nsteps, int every, int observable, int axis,
-                        int index, double* value, double* grad, void* stream);
+                        int index, double* value, double* grad, double* dT0, void* stream);
 
 /* Autotuner (the paper gives no implementation; a measuring aid of this
  * library): times the step forms this build has on the context's own grid

@@ -98,4 +98,9 @@ cudaError_t launch_full_seed_crossing(const FullArgs& a, double* phib, cudaStrea
   return cudaGetLastError();
 }
 
+cudaError_t launch_full_dT0(const FullArgs& a, const double* lam, double* out, cudaStream_t s) {
+  lbm_full_dT0_kernel<<<grid_dims(a.g), block_dims(), 0, s>>>(a, lam, out);
+  return cudaGetLastError();
+}
+
 }  // namespace lbmk

@@ -597,6 +597,39 @@ static __global__ void lbm_full_seed_crossing_kernel(const FullArgs a, double* _
   a.out[0] = J;
 }
 
+// Gradient with respect to the initial temperature field (a run from
+// set_geometry): the initial enthalpy populations are h_eq(rho H, T, u = 0)
+// with rho H = cap T + w rho_l L fl (cap: the frozen capacity below T_m,
+// the liquid one at and above, Eq. (8)), so dh_0/dT = cap - rr + w_0 rr and
+// dh_i/dT = w_i rr; T is recovered from the initial populations (pop, lag)
+// by the inversion.  lam: the adjoints of the initial h (9 planes); out:
+// dense [ny][nx].
+static __global__ void __launch_bounds__(NT) lbm_full_dT0_kernel(const FullArgs a,
+                                                                 const double* __restrict__ lam,
+                                                                 double* __restrict__ out) {
+  const Geom& g = a.g;
+  const Coef<double>& c = a.c;
+  const int x = blockIdx.x * TX + threadIdx.x, y = blockIdx.y * TY + threadIdx.y;
+  if (x >= g.nx || y >= g.ny) return;
+  const int P = (int)g.plane;
+  const int n = y * g.pitch + x;
+  double v[9];
+#pragma unroll
+  for (int i = 0; i < 9; i++) v[i] = a.pop[(9 + i) * P + n];
+  const double sg = sum_g(v);
+#pragma unroll
+  for (int i = 0; i < 9; i++) v[i] = a.pop[(18 + i) * P + n];
+  const double sh = sum_h(v);
+  const FrzNode q = frz_forward(c, sg, sh, a.lag[LAG_FL * P + n], a.lag[LAG_W * P + n],
+                                a.lag[LAG_Q * P + n], a.phi0[n]);
+  const double cap = q.T < 0.0 ? q.Cm : q.Cp;
+  double d = lam[n] * (cap - c.rr + qw<double>(0) * c.rr);
+#pragma unroll
+  for (int i = 1; i < 9; i++) d += lam[i * P + n] * qw<double>(i) * c.rr;
+  out[(long long)y * g.nx + x] = d;
+}
+
+cudaError_t launch_full_dT0(const FullArgs& a, const double* lam, double* out, cudaStream_t s);
 cudaError_t launch_full_fields(const FullArgs& a, cudaStream_t s);
 cudaError_t launch_full_k1(const FullArgs& a, cudaStream_t s);
 cudaError_t launch_full_k2(const FullArgs& a, cudaStream_t s);

@@ -1194,7 +1194,7 @@ extern "C" int lbm_adjoint_freezing(lbm_ctx* c, int64_t nsteps, int every, int o
 
 extern "C" int lbm_adjoint_coupled(lbm_ctx* c, int64_t nsteps, int every, int observable,
                                    int axis, int index, double* value_out, double* grad,
-                                   void* stream) {
+                                   double* dT0, void* stream) {
   if (!c) return LBM_ERR_ARG;
   if (!value_out || !grad) return fail(c, LBM_ERR_ARG, "null output%s");
   if (nsteps < 1 || every < 1) return fail(c, LBM_ERR_ARG, "nsteps and the checkpoint interval must be >= 1%s");
@@ -1203,6 +1203,8 @@ extern "C" int lbm_adjoint_coupled(lbm_ctx* c, int64_t nsteps, int every, int ob
       ((axis != 0 && axis != 1) || index < 0 || index >= (axis == 0 ? c->p.ny : c->p.nx)))
     return fail(c, LBM_ERR_ARG, "axis must be 0 or 1 and index a line of the grid%s");
   if (!c->have_geometry) return fail(c, LBM_ERR_STATE, "adjoint before lbm_set_geometry%s");
+  if (dT0 && c->step != 0)
+    return fail(c, LBM_ERR_STATE, "the initial-temperature gradient needs a run from lbm_set_geometry%s");
   if (c->p.precision != LBM_FP64 || c->p.lattices != (LBM_LAT_FLOW | LBM_LAT_PHASE | LBM_LAT_HEAT) ||
       c->g.has_mask || c->p.readings != 0 || !(c->p.sigma > 0.0))
     return fail(c, LBM_ERR_UNSUPPORTED,
@@ -1352,6 +1354,16 @@ extern "C" int lbm_adjoint_coupled(lbm_ctx* c, int64_t nsteps, int every, int ob
     pa.acc = acc + 5 * P;
     pa.dcos_dtheta = a.dcos_dtheta;
     if (e == cudaSuccess) e = lbmk::launch_phase_adjoint_init(pa, s);
+    if (e == cudaSuccess && dT0) {
+      // the checkpoint-0 state (initial populations and lags) in the
+      // reverse sweep's last recomputed slot; the field planes are reused
+      a.pop = ck;
+      a.lag = ck + pN;
+      e = lbmk::launch_full_dT0(a, lb[cur_adj] + 18 * P, fld, s);
+      if (e == cudaSuccess)
+        e = cudaMemcpyAsync(dT0, fld, (size_t)c->p.nx * c->p.ny * sizeof(double),
+                            cudaMemcpyDeviceToHost, s);
+    }
   }
   double hg[11] = {0};
   if (e == cudaSuccess && st == LBM_OK) e = lbmk::launch_adjoint_reduce(acc, c->g, dout, s);

@@ -113,7 +113,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     L.lbm_adjoint_freezing.argtypes = [vp, ctypes.c_int64, ctypes.c_int, ctypes.c_int,
                                        ctypes.c_int, ctypes.c_int, dp, dp, vp]
     L.lbm_adjoint_coupled.argtypes = [vp, ctypes.c_int64, ctypes.c_int, ctypes.c_int,
-                                      ctypes.c_int, ctypes.c_int, dp, dp, vp]
+                                      ctypes.c_int, ctypes.c_int, dp, dp, dp, vp]
     L.lbm3_create.argtypes = [ctypes.POINTER(Lbm3Params), ctypes.POINTER(vp)]
     L.lbm3_set_geometry.argtypes = [vp, vp, vp, vp, vp, vp, ctypes.c_int, vp]
     L.lbm3_step.argtypes = [vp, ctypes.c_int64, vp]
@@ -263,15 +263,17 @@ def lbm_adjoint_freezing(ctx, nsteps: int, every: int, observable: int, axis: in
 
 
 def lbm_adjoint_coupled(ctx, nsteps: int, every: int, observable: int, axis: int = 0,
-                        index: int = 0, stream=None):
+                        index: int = 0, dT0=None, stream=None):
     """(observable after nsteps steps of the whole coupled step and its
-    gradient w.r.t. (T_wall[0..3], latent, theta_deg, sigma, gx, gy)); see
-    include/lbm.h."""
+    gradient w.r.t. (T_wall[0..3], latent, theta_deg, sigma, gx, gy)); with
+    dT0 (a float64 [ny, nx] numpy array) also the gradient w.r.t. the
+    initial temperature field; see include/lbm.h."""
     val = ctypes.c_double()
     grad = (ctypes.c_double * 9)()
+    dptr = None if dT0 is None else dT0.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
     _check(ctx, load().lbm_adjoint_coupled(ctx, int(nsteps), int(every), int(observable),
                                            int(axis), int(index), ctypes.byref(val), grad,
-                                           stream), "lbm_adjoint_coupled")
+                                           dptr, stream), "lbm_adjoint_coupled")
     return val.value, list(grad)
 
 
@@ -465,11 +467,18 @@ class Solver:
         return lbm_adjoint_freezing(self.ctx, nsteps, every, observable, axis, index, _stream())
 
     def adjoint_coupled(self, nsteps: int, observable: int = 0, axis: int = 0, index: int = 0,
-                        every: int = 64):
+                        every: int = 64, initial_T: bool = False):
         """Advance nsteps and return (observable, gradient w.r.t. (T_wall[0..3],
         latent, theta_deg, sigma, gx, gy)) by reverse mode of the whole coupled
-        step (see lbm_adjoint_coupled)."""
-        return lbm_adjoint_coupled(self.ctx, nsteps, every, observable, axis, index, _stream())
+        step (see lbm_adjoint_coupled); with initial_T also the [ny, nx]
+        gradient w.r.t. the initial temperature field, as a third item."""
+        if not initial_T:
+            return lbm_adjoint_coupled(self.ctx, nsteps, every, observable, axis, index,
+                                       None, _stream())
+        dT0 = np.empty((self.ny, self.nx), dtype=np.float64)
+        v, g = lbm_adjoint_coupled(self.ctx, nsteps, every, observable, axis, index, dT0,
+                                   _stream())
+        return v, g, dT0
 
     def autotune(self, steps_per_trial: int = 64):
         """Pick the fastest step form for this grid (state unchanged)."""

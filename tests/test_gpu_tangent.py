@@ -651,3 +651,41 @@ def test_full_adjoint_checkpoints_and_rejections(env):
             s.adjoint_coupled(5, 0, every=5)
         assert e.value.status == -6
         s.close()
+
+
+def test_full_adjoint_initial_temperature_gradient(env):
+    """The per-node gradient with respect to the initial temperature field
+    (one reverse sweep) against central differences of single-node
+    perturbations, at nodes away from the T = T_m kink of Eq. (8)."""
+    O, lbm, S, torch = env
+    cfg, arr = _full_state(3)
+    steps = 100
+    s = lbm.Solver(cfg, precision="fp64").set_geometry(arr)
+    ff, grad, dT0 = s.adjoint_coupled(steps, 0, every=25, initial_T=True)
+    s.close()
+    T0 = arr["T"]
+    cand = [(j, i) for j in range(3, cfg["ny"] - 3) for i in range(3, cfg["nx"] - 3)
+            if abs(T0[j, i]) > 0.1]
+    nodes = [cand[0], cand[len(cand) // 2], cand[-1]]
+
+    def ff_of(node, delta):
+        a2 = dict(arr)
+        T = T0.copy()
+        T[node] += delta
+        a2["T"] = T
+        u = lbm.Solver(cfg, precision="fp64").set_geometry(a2).step(steps)
+        d = u.diagnostics()
+        u.close()
+        return d["frozen_volume"] / d["material_volume"]
+
+    h = 1e-6
+    for node in nodes:
+        fd = (ff_of(node, h) - ff_of(node, -h)) / (2 * h)
+        print(f"\nnode {node}: T0 {T0[node]:+.3f} adjoint {dT0[node]:.10e} FD {fd:.10e}")
+        assert abs(dT0[node] - fd) <= 1e-5 * abs(fd) + 1e-10, (node, dT0[node], fd)
+    assert np.abs(dT0).max() > 0.0
+    s = lbm.Solver(cfg, precision="fp64").set_geometry(arr).step(3)
+    with pytest.raises(lbm.LbmError) as e:
+        s.adjoint_coupled(5, 0, every=5, initial_T=True)
+    assert e.value.status == -8
+    s.close()
