@@ -514,6 +514,12 @@ int lbm3_read_fields(lbm3_ctx* ctx, uint32_t field_mask, double* const* out, int
  * energy with all three velocity components).  Synchronises `stream`. */
 int lbm3_diagnostics(lbm3_ctx* ctx, lbm_diag* out, void* stream);
 
+/* Checkpoint and resume, as lbm_state_size / lbm_save_state /
+ * lbm_load_state (57 population planes and 7 lag planes after a header). */
+int lbm3_state_size(const lbm3_ctx* ctx, size_t* bytes);
+int lbm3_save_state(lbm3_ctx* ctx, void* host_buf, size_t capacity, void* stream);
+int lbm3_load_state(lbm3_ctx* ctx, const void* host_buf, size_t size, void* stream);
+
 int64_t lbm3_step_count(const lbm3_ctx* ctx);
 const char* lbm3_last_error(const lbm3_ctx* ctx);
 void lbm3_destroy(lbm3_ctx* ctx);

@@ -953,6 +953,72 @@ int lbm3_diagnostics(lbm3_ctx* c, lbm_diag* out, void* stream) {
   return h[8] > 0.0 ? LBM_ERR_NONFINITE : LBM_OK;
 }
 
+namespace {
+// checkpoint header of a 3-D state (the populations and lags follow)
+struct State3Header {
+  uint32_t magic, version;
+  int32_t nx, ny, nz, precision, lattices, pad;
+  int64_t step;
+};
+constexpr uint32_t kMagic3 = 0x4c424d33u;  // "LBM3"
+constexpr uint32_t kVersion3 = 1;
+}  // namespace
+
+int lbm3_state_size(const lbm3_ctx* c, size_t* bytes) {
+  if (!c || !bytes) return LBM_ERR_ARG;
+  const size_t es = c->f64 ? 8 : 4;
+  *bytes = sizeof(State3Header) + (57 + lbm3::NLAG) * es * (size_t)c->g.plane;
+  return LBM_OK;
+}
+
+int lbm3_save_state(lbm3_ctx* c, void* host_buf, size_t capacity, void* stream) {
+  if (!c || !host_buf) return LBM_ERR_ARG;
+  if (!c->have_geometry) return fail3(c, LBM_ERR_STATE, "save before lbm3_set_geometry");
+  size_t need;
+  lbm3_state_size(c, &need);
+  if (capacity < need) return fail3(c, LBM_ERR_ARG, "state buffer too small");
+  cudaStream_t s = (cudaStream_t)stream;
+  const State3Header h = {kMagic3, kVersion3, c->g.nx, c->g.ny, c->g.nz,
+                          c->p.base.precision, (int32_t)c->p.base.lattices, 0, c->step};
+  std::memcpy(host_buf, &h, sizeof(h));
+  char* dst = (char*)host_buf + sizeof(h);
+  const size_t es = c->f64 ? 8 : 4;
+  const size_t pb = 57 * es * (size_t)c->g.plane;
+  cudaError_t e = cudaMemcpyAsync(dst, c->pop[c->cur], pb, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(dst + pb, c->lag[c->cur], lbm3::NLAG * es * (size_t)c->g.plane,
+                        cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_fail3(c, e, "state download");
+  return LBM_OK;
+}
+
+int lbm3_load_state(lbm3_ctx* c, const void* host_buf, size_t size, void* stream) {
+  if (!c || !host_buf) return LBM_ERR_ARG;
+  if (!c->have_geometry) return fail3(c, LBM_ERR_STATE, "load before lbm3_set_geometry");
+  size_t need;
+  lbm3_state_size(c, &need);
+  if (size < need) return fail3(c, LBM_ERR_ARG, "state buffer too small");
+  State3Header h;
+  std::memcpy(&h, host_buf, sizeof(h));
+  if (h.magic != kMagic3 || h.version != kVersion3 || h.nx != c->g.nx || h.ny != c->g.ny ||
+      h.nz != c->g.nz || h.precision != c->p.base.precision ||
+      h.lattices != (int32_t)c->p.base.lattices)
+    return fail3(c, LBM_ERR_ARG, "state does not match this context");
+  cudaStream_t s = (cudaStream_t)stream;
+  const char* src = (const char*)host_buf + sizeof(h);
+  const size_t es = c->f64 ? 8 : 4;
+  const size_t pb = 57 * es * (size_t)c->g.plane;
+  cudaError_t e = cudaMemcpyAsync(c->pop[c->cur], src, pb, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(c->lag[c->cur], src + pb, lbm3::NLAG * es * (size_t)c->g.plane,
+                        cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_fail3(c, e, "state upload");
+  c->step = h.step;
+  return LBM_OK;
+}
+
 int64_t lbm3_step_count(const lbm3_ctx* c) { return c ? c->step : -1; }
 
 const char* lbm3_last_error(const lbm3_ctx* c) { return c ? c->err : "null context"; }

@@ -63,7 +63,8 @@ EXPORTS = ("lbm_create", "lbm_set_geometry", "lbm_step", "lbm_read_fields",
            "lbm_read_crossings_tangent", "lbm_autotune", "lbm_adjoint_frozen_fraction",
            "lbm_adjoint_crossing", "lbm_adjoint_freezing", "lbm_adjoint_coupled", "lbm3_create", "lbm3_set_geometry", "lbm3_step",
            "lbm3_read_fields", "lbm3_diagnostics", "lbm3_step_count", "lbm3_last_error",
-           "lbm3_destroy", "lbm3_lattice")
+           "lbm3_destroy", "lbm3_lattice", "lbm3_state_size", "lbm3_save_state",
+           "lbm3_load_state")
 FIELDS3 = ("phi", "fs", "fl", "T", "rhoH", "p", "ux", "uy", "uz", "rho", "mu", "w", "mdot")
 
 _lib = None
@@ -126,9 +127,12 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     L.lbm3_destroy.argtypes = [vp]
     L.lbm3_destroy.restype = None
     L.lbm3_lattice.argtypes = [ctypes.POINTER(ctypes.c_int32), dp]
+    L.lbm3_state_size.argtypes = [vp, ctypes.POINTER(ctypes.c_size_t)]
+    L.lbm3_save_state.argtypes = [vp, vp, ctypes.c_size_t, vp]
+    L.lbm3_load_state.argtypes = [vp, vp, ctypes.c_size_t, vp]
     L.lbm3_lattice.restype = None
     for fn in ("lbm3_create", "lbm3_set_geometry", "lbm3_step", "lbm3_read_fields",
-               "lbm3_diagnostics"):
+               "lbm3_diagnostics", "lbm3_state_size", "lbm3_save_state", "lbm3_load_state"):
         getattr(L, fn).restype = ctypes.c_int
     for fn in ("lbm_create", "lbm_set_geometry", "lbm_step", "lbm_read_fields",
                "lbm_compute_diagnostics", "lbm_read_diagnostics", "lbm_state_size",
@@ -614,6 +618,23 @@ def lbm3_destroy(ctx):
     load().lbm3_destroy(ctx)
 
 
+def lbm3_state_size(ctx) -> int:
+    n = ctypes.c_size_t()
+    _check3(ctx, load().lbm3_state_size(ctx, ctypes.byref(n)), "lbm3_state_size")
+    return int(n.value)
+
+
+def lbm3_save_state(ctx, stream=None) -> bytes:
+    buf = ctypes.create_string_buffer(lbm3_state_size(ctx))
+    _check3(ctx, load().lbm3_save_state(ctx, buf, len(buf), stream), "lbm3_save_state")
+    return buf.raw
+
+
+def lbm3_load_state(ctx, data: bytes, stream=None):
+    buf = ctypes.create_string_buffer(data, len(data))
+    _check3(ctx, load().lbm3_load_state(ctx, buf, len(data), stream), "lbm3_load_state")
+
+
 def lbm3_lattice():
     """(c [19, 3], w [19]) of the library's D3Q19 lattice (host only)."""
     c = (ctypes.c_int32 * 57)()
@@ -691,3 +712,10 @@ class Solver3:
 
     def diagnostics(self) -> dict:
         return lbm3_diagnostics(self.ctx, _stream())
+
+    def save_state(self) -> bytes:
+        return lbm3_save_state(self.ctx, _stream())
+
+    def load_state(self, data: bytes):
+        lbm3_load_state(self.ctx, data, _stream())
+        return self

@@ -156,3 +156,25 @@ def test_nonfinite_state_is_reported(env):
     d = s.diagnostics()
     assert d["nonfinite"] >= 1
     s.close()
+
+
+def test_checkpoint_resume_is_bit_exact(env):
+    """Run 2N steps, or run N, save, load into a fresh context, run N: the
+    same state bit for bit (FP32 and FP64)."""
+    O3, lbm = env
+    wl = W.random_state3(30, 10, 7, seed=1)
+    for prec in ("fp32", "fp64"):
+        a = lbm.Solver3(wl[0], prec).set_geometry(wl[1]).step(24)
+        b = lbm.Solver3(wl[0], prec).set_geometry(wl[1]).step(12)
+        blob = b.save_state()
+        b.close()
+        c = lbm.Solver3(wl[0], prec).set_geometry(wl[1]).load_state(blob).step(12)
+        assert c.steps_done == 24
+        fa, fc = a.fields(), c.fields()
+        for k in F3:
+            assert np.array_equal(fa[k], fc[k]), (prec, k)
+        other = lbm.Solver3(dict(wl[0], nz=8), prec).set_geometry(W.random_state3(30, 10, 8, seed=1)[1])
+        with pytest.raises(lbm.LbmError):
+            other.load_state(blob)
+        for s in (a, c, other):
+            s.close()
