@@ -283,6 +283,14 @@ int lbm_batch_step(lbm_batch* batch, int64_t nsteps, void* stream);
 /* Frees the batch (not the contexts; NULL is allowed). */
 void lbm_batch_destroy(lbm_batch* batch);
 
+/* Testing hook for the failure paths (host-side fault injection): with
+ * after >= 0, the (after + 1)-th device or pinned-host allocation that
+ * lbm_create makes from now on fails as if the device were out of memory
+ * (lbm_create then returns LBM_ERR_OOM and frees what it had allocated);
+ * the hook disarms itself after firing.  after < 0 disarms it.  Process
+ * wide; not for concurrent use with other lbm_create calls. */
+void lbm_debug_fail_allocation(int after);
+
 /* Reverse mode (adjoint) of the enthalpy-lattice step, Eqs. (8), (23)-(28)
  * with the fluid at rest: for a context with precision LBM_FP64, no cold
  * mask, and lattices == LBM_LAT_HEAT, or LBM_LAT_FLOW | LBM_LAT_HEAT with

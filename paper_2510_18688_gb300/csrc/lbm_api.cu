@@ -19,6 +19,9 @@
 
 #include "../../include/lbm.h"
 #include "lbm_host.h"
+#include <nvtx3/nvToolsExt.h>
+#include <atomic>
+
 #include "lbm_adjoint.cuh"
 #include "lbm_adjoint_full.cuh"
 #include "lbm_launch.h"
@@ -78,6 +81,35 @@ struct StateHeader {
   uint32_t magic, version;
   int32_t nx, ny, precision, lattices;
   int64_t step;
+};
+
+// Testing hook for the failure paths of lbm_create: when armed with n >= 0,
+// the (n + 1)-th device or pinned allocation made by lbm_create fails as if
+// the device were out of memory (then the hook disarms itself).
+std::atomic<int> g_alloc_countdown{-1};
+
+bool injected_alloc_failure() {
+  int n = g_alloc_countdown.load();
+  while (n >= 0) {
+    if (g_alloc_countdown.compare_exchange_weak(n, n - 1)) return n == 0;
+  }
+  return false;
+}
+
+cudaError_t dev_malloc(void** p, size_t bytes) {
+  if (injected_alloc_failure()) return cudaErrorMemoryAllocation;
+  return cudaMalloc(p, bytes);
+}
+
+cudaError_t host_alloc(void** p, size_t bytes) {
+  if (injected_alloc_failure()) return cudaErrorMemoryAllocation;
+  return cudaHostAlloc(p, bytes, 0);
+}
+
+// NVTX range for the duration of a scope (a no-op unless a tool listens)
+struct Range {
+  explicit Range(const char* name) { nvtxRangePushA(name); }
+  ~Range() { nvtxRangePop(); }
 };
 
 int fail(lbm_ctx* c, int code, const char* fmt, const char* detail = "") {
@@ -308,18 +340,18 @@ int lbm_create(const lbm_params* params, lbm_ctx** out) {
   const size_t P = (size_t)c->g.plane;
   cudaError_t e = cudaSuccess;
   for (int b = 0; b < 2 && e == cudaSuccess; b++) {
-    e = cudaMalloc(&c->pop[b], 27 * P * c->pop_esize);
-    if (e == cudaSuccess) e = cudaMalloc(&c->lag[b], lbmk::NLAG * P * c->esize);
+    e = dev_malloc(&c->pop[b], 27 * P * c->pop_esize);
+    if (e == cudaSuccess) e = dev_malloc(&c->lag[b], lbmk::NLAG * P * c->esize);
   }
-  if (e == cudaSuccess) e = cudaMalloc(&c->phi0, P * c->esize);
-  if (e == cudaSuccess) e = cudaMalloc(&c->scratch, lbmk::NSCRATCH * P * c->esize);
-  if (e == cudaSuccess) e = cudaMalloc(&c->mask, P);
+  if (e == cudaSuccess) e = dev_malloc(&c->phi0, P * c->esize);
+  if (e == cudaSuccess) e = dev_malloc(&c->scratch, lbmk::NSCRATCH * P * c->esize);
+  if (e == cudaSuccess) e = dev_malloc((void**)&c->mask, P);
   if (e == cudaSuccess)
-    e = cudaMalloc(&c->diag_partial, dmul * lbmk::NDIAG * c->nblocks * sizeof(double));
-  if (e == cudaSuccess) e = cudaMalloc(&c->diag_out, dmul * (lbmk::NDIAG + 1) * sizeof(double));
+    e = dev_malloc((void**)&c->diag_partial, dmul * lbmk::NDIAG * c->nblocks * sizeof(double));
+  if (e == cudaSuccess) e = dev_malloc((void**)&c->diag_out, dmul * (lbmk::NDIAG + 1) * sizeof(double));
   if (e == cudaSuccess) e = cudaMemset(c->mask, 0, P);
   if (e == cudaSuccess)
-    e = cudaHostAlloc(&c->h_diag, dmul * (lbmk::NDIAG + 1) * sizeof(double), 0);
+    e = host_alloc((void**)&c->h_diag, dmul * (lbmk::NDIAG + 1) * sizeof(double));
   if (e == cudaSuccess) e = cudaDeviceSynchronize();
   if (e != cudaSuccess) {
     int code = cuda_fail(c, e, "lbm_create allocation");
@@ -421,6 +453,7 @@ int lbm_set_geometry(lbm_ctx* c, const double* phi0, const uint8_t* cold_mask,
 }
 
 int lbm_step(lbm_ctx* c, int64_t nsteps, void* stream) {
+  Range nvtx_range("lbm_step");
   if (!c) return LBM_ERR_ARG;
   if (nsteps < 0) return fail(c, LBM_ERR_ARG, "nsteps must be >= 0%s");
   if (!c->have_geometry) return fail(c, LBM_ERR_STATE, "lbm_step before lbm_set_geometry%s");
@@ -687,8 +720,13 @@ int lbm_load_state(lbm_ctx* c, const void* host_buf, size_t size, void* stream) 
 // reverse mode: frozen fraction of an enthalpy-lattice run and its gradient
 // ---------------------------------------------------------------------------
 
+extern "C" void lbm_debug_fail_allocation(int after) {
+  g_alloc_countdown.store(after < 0 ? -1 : after);
+}
+
 extern "C" int lbm_adjoint_frozen_fraction(lbm_ctx* c, int64_t nsteps, int every, double* ff_out,
                                            double* grad, void* stream) {
+  Range nvtx_range("lbm_adjoint_frozen_fraction");
   if (!c) return LBM_ERR_ARG;
   if (!ff_out || !grad) return fail(c, LBM_ERR_ARG, "null output%s");
   if (nsteps < 1 || every < 1) return fail(c, LBM_ERR_ARG, "nsteps and the checkpoint interval must be >= 1%s");
@@ -839,6 +877,7 @@ extern "C" int lbm_adjoint_frozen_fraction(lbm_ctx* c, int64_t nsteps, int every
 
 extern "C" int lbm_adjoint_crossing(lbm_ctx* c, int64_t nsteps, int every, int axis, int index,
                                     double* pos_out, double* grad, void* stream) {
+  Range nvtx_range("lbm_adjoint_crossing");
   if (!c) return LBM_ERR_ARG;
   if (!pos_out || !grad) return fail(c, LBM_ERR_ARG, "null output%s");
   if (nsteps < 1 || every < 1) return fail(c, LBM_ERR_ARG, "nsteps and the checkpoint interval must be >= 1%s");
@@ -988,6 +1027,7 @@ extern "C" int lbm_adjoint_crossing(lbm_ctx* c, int64_t nsteps, int every, int a
 extern "C" int lbm_adjoint_freezing(lbm_ctx* c, int64_t nsteps, int every, int observable,
                                     int axis, int index, double* value_out, double* grad,
                                     void* stream) {
+  Range nvtx_range("lbm_adjoint_freezing");
   if (!c) return LBM_ERR_ARG;
   if (!value_out || !grad) return fail(c, LBM_ERR_ARG, "null output%s");
   if (nsteps < 1 || every < 1) return fail(c, LBM_ERR_ARG, "nsteps and the checkpoint interval must be >= 1%s");
@@ -1195,6 +1235,7 @@ extern "C" int lbm_adjoint_freezing(lbm_ctx* c, int64_t nsteps, int every, int o
 extern "C" int lbm_adjoint_coupled(lbm_ctx* c, int64_t nsteps, int every, int observable,
                                    int axis, int index, double* value_out, double* grad,
                                    double* dT0, void* stream) {
+  Range nvtx_range("lbm_adjoint_coupled");
   if (!c) return LBM_ERR_ARG;
   if (!value_out || !grad) return fail(c, LBM_ERR_ARG, "null output%s");
   if (nsteps < 1 || every < 1) return fail(c, LBM_ERR_ARG, "nsteps and the checkpoint interval must be >= 1%s");
@@ -1394,6 +1435,7 @@ extern "C" int lbm_adjoint_coupled(lbm_ctx* c, int64_t nsteps, int every, int ob
 
 extern "C" int lbm_autotune(lbm_ctx* c, int steps_per_trial, void* stream, double* out_us,
                             int* chosen) {
+  Range nvtx_range("lbm_autotune");
   if (!c) return LBM_ERR_ARG;
   if (steps_per_trial < 2) return fail(c, LBM_ERR_ARG, "steps_per_trial must be >= 2%s");
   if (!c->have_geometry) return fail(c, LBM_ERR_STATE, "autotune before lbm_set_geometry%s");
@@ -1679,6 +1721,7 @@ int lbm_batch_create(lbm_ctx* const* ctxs, int count, lbm_batch** out) {
 }
 
 int lbm_batch_step(lbm_batch* b, int64_t nsteps, void* stream) {
+  Range nvtx_range("lbm_batch_step");
   if (!b) return LBM_ERR_ARG;
   if (nsteps < 0) return LBM_ERR_ARG;
   for (lbm_ctx* c : b->ctx) {

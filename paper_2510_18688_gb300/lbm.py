@@ -61,7 +61,8 @@ EXPORTS = ("lbm_create", "lbm_set_geometry", "lbm_step", "lbm_read_fields",
            "lbm_batch_create", "lbm_batch_step", "lbm_batch_destroy", "lbm_probe_fma_rate",
            "lbm_read_crossings", "lbm_read_tangent_fields", "lbm_read_tangent_diagnostics",
            "lbm_read_crossings_tangent", "lbm_autotune", "lbm_adjoint_frozen_fraction",
-           "lbm_adjoint_crossing", "lbm_adjoint_freezing", "lbm_adjoint_coupled", "lbm3_create", "lbm3_set_geometry", "lbm3_step",
+           "lbm_adjoint_crossing", "lbm_adjoint_freezing", "lbm_adjoint_coupled",
+           "lbm_debug_fail_allocation", "lbm3_create", "lbm3_set_geometry", "lbm3_step",
            "lbm3_read_fields", "lbm3_diagnostics", "lbm3_step_count", "lbm3_last_error",
            "lbm3_destroy", "lbm3_lattice", "lbm3_state_size", "lbm3_save_state",
            "lbm3_load_state")
@@ -115,6 +116,8 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
                                        ctypes.c_int, ctypes.c_int, dp, dp, vp]
     L.lbm_adjoint_coupled.argtypes = [vp, ctypes.c_int64, ctypes.c_int, ctypes.c_int,
                                       ctypes.c_int, ctypes.c_int, dp, dp, dp, vp]
+    L.lbm_debug_fail_allocation.argtypes = [ctypes.c_int]
+    L.lbm_debug_fail_allocation.restype = None
     L.lbm3_create.argtypes = [ctypes.POINTER(Lbm3Params), ctypes.POINTER(vp)]
     L.lbm3_set_geometry.argtypes = [vp, vp, vp, vp, vp, vp, ctypes.c_int, vp]
     L.lbm3_step.argtypes = [vp, ctypes.c_int64, vp]
@@ -574,6 +577,12 @@ def _check3(ctx, st, what):
     if st != LBM_OK:
         msg = load().lbm3_last_error(ctx).decode() if ctx else ""
         raise LbmError(st, f"{what}: {load().lbm_status_string(st).decode()} {msg}")
+
+
+def lbm_debug_fail_allocation(after: int):
+    """Testing hook: the (after + 1)-th allocation of the next lbm_create
+    calls fails as out of memory (after < 0 disarms); see include/lbm.h."""
+    load().lbm_debug_fail_allocation(int(after))
 
 
 def lbm3_create(params: Lbm3Params) -> ctypes.c_void_p:

@@ -1,0 +1,46 @@
+"""Failure paths without a GPU fault (host-side fault injection): every
+device or pinned allocation of lbm_create is made to fail in turn; each
+attempt must return LBM_ERR_OOM, hand back no context, free what it had
+allocated, and leave the library usable."""
+import ctypes
+
+import numpy as np
+import pytest
+
+from paper_2510_18688_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+def test_every_allocation_failure_of_lbm_create_is_clean():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2510_18688_gb300 import build, lbm
+    build.build()
+    L = lbm.load()
+    cfg, arr = W.random_state(64, 48, seed=2)
+    p = lbm.make_params(cfg, "fp32")
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    failures = 0
+    for k in range(32):
+        lbm.lbm_debug_fail_allocation(k)
+        h = ctypes.c_void_p()
+        st = L.lbm_create(ctypes.byref(p), ctypes.byref(h))
+        if st == 0:
+            # k is past the last allocation: the create succeeded
+            lbm.lbm_debug_fail_allocation(-1)
+            L.lbm_destroy(h)
+            break
+        assert st == -4, (k, st)
+        assert not h.value
+        failures += 1
+    lbm.lbm_debug_fail_allocation(-1)
+    assert failures >= 8  # populations, lags, phi0, scratch, mask, diagnostics
+    torch.cuda.synchronize()
+    free1 = torch.cuda.mem_get_info()[0]
+    assert abs(free1 - free0) < 64 << 20, (free0, free1)
+    s = lbm.Solver(cfg, precision="fp32").set_geometry(arr).step(10)
+    assert s.diagnostics()["nonfinite"] == 0
+    s.close()
