@@ -47,7 +47,7 @@ typedef enum {
   LBM_ERR_CUDA = -3,        /* a CUDA runtime call failed                     */
   LBM_ERR_OOM = -4,         /* device or pinned host allocation failed        */
   LBM_ERR_NONFINITE = -5,   /* diagnostics found non-finite populations       */
-  LBM_ERR_UNSUPPORTED = -6, /* valid request this build does not implement    */
+  LBM_ERR_UNSUPPORTED = -6, /* valid request the library does not implement  */
   LBM_ERR_STATE = -8        /* call out of order (e.g. step before geometry)  */
 } lbm_status;
 
@@ -388,7 +388,7 @@ int lbm_adjoint_coupled(lbm_ctx* ctx, int64_t nsteps, int every, int observable,
                         int index, double* value, double* grad, double* dT0, void* stream);
 
 /* Autotuner (the paper gives no implementation; a measuring aid of this
- * library): times the step forms this build has on the context's own grid
+ * library): times the step forms the library has on the context's own grid
  * and state and keeps the fastest for later lbm_step calls.  Variants, in
  * this order: the fused one-kernel step with captured periods of at least
  * 32 steps, the same with at least 256, and (LBM_FP32 and LBM_FP64 only)
@@ -468,7 +468,7 @@ int lbm_probe_fma_rate(int precision, double* flops_per_s, void* stream);
  * Every lattice sum of Eqs. (11)-(28) runs over the 19 velocities, vectors
  * (velocity, forces, phi u, gradients) carry a z component, and the
  * isotropic stencils use the D3Q19 weights.  A link that leaves through an
- * edge or a corner of the box is decided by the first wall it crosses in the
+ * edge or a corner of the grid is decided by the first wall it crosses in the
  * order x, y, z.  Grid arrays are [nz][ny][nx] with x fastest.  Precisions:
  * LBM_FP32 and LBM_FP64 (others: LBM_ERR_UNSUPPORTED); base.diag_every and
  * the tan_* fields are ignored.  A step is two kernels (the per-node local
