@@ -1,4 +1,7 @@
-// lbm_adjoint.cu -- launchers of the enthalpy-lattice and phase-field adjoint kernels.
+// lbm_adjoint.cu -- the reverse-mode (adjoint) kernels and their launchers: enthalpy lattice,
+// phase field, the two coupled, and the whole step (lbm_adjoint.cuh, lbm_adjoint_full.cuh).
+// the kernels of the adjoint headers are compiled in this unit only
+#define LBM_ADJOINT_KERNELS
 #include "lbm_adjoint.cuh"
 #include "lbm_adjoint_full.cuh"
 #include "lbm_launch.h"

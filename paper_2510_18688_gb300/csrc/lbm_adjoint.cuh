@@ -102,6 +102,7 @@ __device__ __forceinline__ double heat_inversion_reverse(const Coef<double>& c, 
 
 // Seed: adjoint of the frozen fraction FF = sum w (1 - fl) / sum w of a
 // state with respect to its populations, lag Q and L (lag fl: zero).
+#ifdef LBM_ADJOINT_KERNELS
 static __global__ void __launch_bounds__(NT) lbm_adjoint_seed_kernel(const AdjArgs a) {
   const Geom& g = a.g;
   const int x = blockIdx.x * TX + threadIdx.x, y = blockIdx.y * TY + threadIdx.y;
@@ -122,8 +123,10 @@ static __global__ void __launch_bounds__(NT) lbm_adjoint_seed_kernel(const AdjAr
   a.lfl_out[n] = 0.0;
   a.acc[(ADJ_NACC - 1) * P + n] += dL;
 }
+#endif  // LBM_ADJOINT_KERNELS
 
 // One step in reverse (see the header).
+#ifdef LBM_ADJOINT_KERNELS
 static __global__ void __launch_bounds__(NT) lbm_adjoint_step_kernel(const AdjArgs a) {
   const Geom& g = a.g;
   const Coef<double>& c = a.c;
@@ -231,11 +234,13 @@ static __global__ void __launch_bounds__(NT) lbm_adjoint_step_kernel(const AdjAr
   for (int k = 0; k < 4; k++) a.acc[k * P + n] += dTw[k];
   a.acc[(ADJ_NACC - 1) * P + n] += dL;
 }
+#endif  // LBM_ADJOINT_KERNELS
 
 // Initial-state term: set_geometry builds the rest enthalpy population
 // from rho H = C T + w rho_l L fl (Eq. (8)), the other populations from T
 // alone (Eq. (25), u = 0), so dh0/dL = w rho_l fl; with lam_in the adjoint
 // of the initial populations and lag the initial lag planes.
+#ifdef LBM_ADJOINT_KERNELS
 static __global__ void __launch_bounds__(NT) lbm_adjoint_init_kernel(const AdjArgs a) {
   const Geom& g = a.g;
   const int x = blockIdx.x * TX + threadIdx.x, y = blockIdx.y * TY + threadIdx.y;
@@ -245,8 +250,10 @@ static __global__ void __launch_bounds__(NT) lbm_adjoint_init_kernel(const AdjAr
   const double w = a.lag[LAG_W * P + n], fl = a.lag[LAG_FL * P + n];
   a.acc[(ADJ_NACC - 1) * P + n] += a.lam_in[n] * w * a.c.rho_l * fl;
 }
+#endif  // LBM_ADJOINT_KERNELS
 
 // Fixed-order sum of the accumulator planes over the grid (one CTA).
+#ifdef LBM_ADJOINT_KERNELS
 static __global__ void __launch_bounds__(NT) lbm_adjoint_reduce_kernel(const double* __restrict__ acc,
                                                                 Geom g, double* __restrict__ out) {
   __shared__ double s[ADJ_NACC][NT / 32];
@@ -274,6 +281,7 @@ static __global__ void __launch_bounds__(NT) lbm_adjoint_reduce_kernel(const dou
     out[tid] = t;
   }
 }
+#endif  // LBM_ADJOINT_KERNELS
 
 // ---------------------------------------------------------------------------
 // reverse mode of the phase-field step (lattices == LAT_PHASE: the fluid at
@@ -309,6 +317,7 @@ struct PhaseAdjArgs {
 };
 
 // phi = sum g and fs = min(phi0 + w (1 - fl), 1), w = clamp((1 - phi0 + phi) / 2)
+#ifdef LBM_ADJOINT_KERNELS
 static __global__ void __launch_bounds__(NT) lbm_phase_fields_kernel(const PhaseAdjArgs a) {
   const Geom& g = a.g;
   const int x = blockIdx.x * TX + threadIdx.x, y = blockIdx.y * TY + threadIdx.y;
@@ -325,6 +334,7 @@ static __global__ void __launch_bounds__(NT) lbm_phase_fields_kernel(const Phase
   a.phi[n] = ph;
   a.fs[n] = fs > 1.0 ? 1.0 : fs;
 }
+#endif  // LBM_ADJOINT_KERNELS
 
 __device__ __forceinline__ int stencil_index(const Geom& g, int x, int y, int i) {
   const int xx = wrap_or_clamp(x + qx(i), g.nx, g.bc[0], g.bc[1]);
@@ -342,6 +352,7 @@ __device__ __forceinline__ double lap6(const Geom& g, const double* chi, int x, 
 
 // Seed: the position J = k + a / (a - b) of the last crossing of phi
 // through 0 along the line (one thread), dJ/dphi at the two nodes.
+#ifdef LBM_ADJOINT_KERNELS
 static __global__ void lbm_phase_seed_kernel(const PhaseAdjArgs a) {
   const Geom& g = a.g;
   const int P = (int)g.plane;
@@ -367,6 +378,7 @@ static __global__ void lbm_phase_seed_kernel(const PhaseAdjArgs a) {
   }
   a.out[0] = J;
 }
+#endif  // LBM_ADJOINT_KERNELS
 
 // Shared pieces of Eq. (6): d chem / d phi, d chem / d fs, d chem / d cos(theta).
 __device__ __forceinline__ void chem_partials(const Coef<double>& c, double ph, double q0,
@@ -382,6 +394,7 @@ __device__ __forceinline__ void chem_partials(const Coef<double>& c, double ph, 
 // the collision to mu_phi; store mu_phi's adjoint and the terms of phi's and
 // fs's adjoints that come from the node itself (the collision's phi, the
 // local part of Eq. (6), the centre of the Laplacians).
+#ifdef LBM_ADJOINT_KERNELS
 static __global__ void __launch_bounds__(NT) lbm_phase_adjoint1_kernel(const PhaseAdjArgs a) {
   const Geom& g = a.g;
   const Coef<double>& c = a.c;
@@ -415,12 +428,14 @@ static __global__ void __launch_bounds__(NT) lbm_phase_adjoint1_kernel(const Pha
   a.acc[n] += mub * (dcos - c.klap * lphi0) * a.dcos_dtheta;
   a.acc[P + n] += mub * mu / c.sigma;
 }
+#endif  // LBM_ADJOINT_KERNELS
 
 // Reverse step, part 2: the transposed Laplacian stencils as a gather (every
 // node p within one node of n, and every direction i whose clamped or
 // wrapped stencil neighbour of p is n, adds -klap 6 w_i mub(p); a fixed
 // order, so the sweep is deterministic), then fs -> w -> phi (local) and
 // phi = sum g.
+#ifdef LBM_ADJOINT_KERNELS
 static __global__ void __launch_bounds__(NT) lbm_phase_adjoint2_kernel(const PhaseAdjArgs a) {
   const Geom& g = a.g;
   const Coef<double>& c = a.c;
@@ -461,9 +476,11 @@ static __global__ void __launch_bounds__(NT) lbm_phase_adjoint2_kernel(const Pha
 #pragma unroll
   for (int i = 0; i < 9; i++) a.lam_out[i * P + n] = omg * a.gs[i * P + n] + phib;
 }
+#endif  // LBM_ADJOINT_KERNELS
 
 // Initial state (a run from set_geometry): g0 = g_eq(phi0_init, mu_phi0)
 // depends on theta and sigma through mu_phi0.
+#ifdef LBM_ADJOINT_KERNELS
 static __global__ void __launch_bounds__(NT) lbm_phase_init_kernel(const PhaseAdjArgs a) {
   const Geom& g = a.g;
   const Coef<double>& c = a.c;
@@ -484,6 +501,7 @@ static __global__ void __launch_bounds__(NT) lbm_phase_init_kernel(const PhaseAd
   a.acc[n] += mub * (dcos - c.klap * lphi0) * a.dcos_dtheta;
   a.acc[P + n] += mub * mu / c.sigma;
 }
+#endif  // LBM_ADJOINT_KERNELS
 
 // ---------------------------------------------------------------------------
 // reverse mode of the coupled phase-field and enthalpy step (lattices ==
@@ -609,6 +627,7 @@ __device__ __forceinline__ void dcap(const Coef<double>& c, double fs, double w,
   *dw = dinterp_dw(fs, c.rho_l, c.rho_g) * cp + rho * dinterp_dw(fs, c.cp_l, c.cp_g);
 }
 
+#ifdef LBM_ADJOINT_KERNELS
 static __global__ void __launch_bounds__(NT) lbm_frz_fields_kernel(const FrzArgs a) {
   const Geom& g = a.g;
   const int x = blockIdx.x * TX + threadIdx.x, y = blockIdx.y * TY + threadIdx.y;
@@ -618,9 +637,11 @@ static __global__ void __launch_bounds__(NT) lbm_frz_fields_kernel(const FrzArgs
   a.phi[n] = q.phi;
   a.fs[n] = q.fs;
 }
+#endif  // LBM_ADJOINT_KERNELS
 
 // Adjoint of mu_phi from the pulled phase adjoints, with its theta and
 // sigma terms (zero for the seed, whose pulled adjoints are zero).
+#ifdef LBM_ADJOINT_KERNELS
 static __global__ void __launch_bounds__(NT) lbm_frz_mub_kernel(const FrzArgs a) {
   const Geom& g = a.g;
   const Coef<double>& c = a.c;
@@ -647,8 +668,10 @@ static __global__ void __launch_bounds__(NT) lbm_frz_mub_kernel(const FrzArgs a)
   a.acc[5 * P + n] += mub * (dcos - c.klap * lphi0) * a.dcos_dtheta;
   a.acc[6 * P + n] += mub * mu / c.sigma;
 }
+#endif  // LBM_ADJOINT_KERNELS
 
 // The rest of one reverse step (see the section header).
+#ifdef LBM_ADJOINT_KERNELS
 static __global__ void __launch_bounds__(NT) lbm_frz_step_kernel(const FrzArgs a) {
   const Geom& g = a.g;
   const Coef<double>& c = a.c;
@@ -826,10 +849,12 @@ static __global__ void __launch_bounds__(NT) lbm_frz_step_kernel(const FrzArgs a
   for (int k = 0; k < 4; k++) a.acc[k * P + n] += dTw[k];
   a.acc[4 * P + n] += dL;
 }
+#endif  // LBM_ADJOINT_KERNELS
 
 // Seeds on the final state.  Frozen fraction FF = sum w (1 - fl) / sum w
 // (w and fl of this state): the adjoints of the lags this state's reader
 // would write, with zero population adjoints.
+#ifdef LBM_ADJOINT_KERNELS
 static __global__ void __launch_bounds__(NT) lbm_frz_seed_ff_kernel(const FrzArgs a) {
   const Geom& g = a.g;
   const int x = blockIdx.x * TX + threadIdx.x, y = blockIdx.y * TY + threadIdx.y;
@@ -839,9 +864,11 @@ static __global__ void __launch_bounds__(NT) lbm_frz_seed_ff_kernel(const FrzArg
   a.lfl_out[n] = -q.w * a.inv_sum_w;
   a.lw_out[n] = ((1.0 - q.fl) - a.ff) * a.inv_sum_w;
 }
+#endif  // LBM_ADJOINT_KERNELS
 
 // Crossing: the last phi = 0 crossing along the line (one thread), as an
 // adjoint of phi at its two nodes.
+#ifdef LBM_ADJOINT_KERNELS
 static __global__ void lbm_frz_seed_crossing_kernel(const FrzArgs a, double* __restrict__ phib) {
   const Geom& g = a.g;
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
@@ -862,6 +889,7 @@ static __global__ void lbm_frz_seed_crossing_kernel(const FrzArgs a, double* __r
   }
   a.out[0] = J;
 }
+#endif  // LBM_ADJOINT_KERNELS
 
 cudaError_t launch_frz_fields(const FrzArgs& a, cudaStream_t s);
 cudaError_t launch_frz_mub(const FrzArgs& a, cudaStream_t s);

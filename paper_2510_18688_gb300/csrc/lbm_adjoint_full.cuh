@@ -389,6 +389,7 @@ __device__ __forceinline__ void full_local_reverse(const FullArgs& a, const Full
   d.flb = ll[LAG_FL * P + n];
 }
 
+#ifdef LBM_ADJOINT_KERNELS
 static __global__ void __launch_bounds__(NT) lbm_full_fields_kernel(const FullArgs a) {
   const Geom& g = a.g;
   const int x = blockIdx.x * TX + threadIdx.x, y = blockIdx.y * TY + threadIdx.y;
@@ -408,9 +409,11 @@ static __global__ void __launch_bounds__(NT) lbm_full_fields_kernel(const FullAr
   a.fs[n] = q.fs;
   a.rho[n] = q.rho;
 }
+#endif  // LBM_ADJOINT_KERNELS
 
 // Kernel 1: the adjoints the neighbours' stencils need, and the theta and
 // sigma terms of mu_phi's adjoint.
+#ifdef LBM_ADJOINT_KERNELS
 static __global__ void __launch_bounds__(NT) lbm_full_k1_kernel(const FullArgs a) {
   const Geom& g = a.g;
   const Coef<double>& c = a.c;
@@ -433,9 +436,11 @@ static __global__ void __launch_bounds__(NT) lbm_full_k1_kernel(const FullArgs a
   a.acc[5 * P + n] += d.mub * (dcos - c.klap * r.lphi0) * a.dcos_dtheta;
   a.acc[6 * P + n] += d.mub * r.mu / c.sigma;
 }
+#endif  // LBM_ADJOINT_KERNELS
 
 // Kernel 2: the local reverse again, the gathered stencil transposes and the
 // local chain to this state's populations and lags.
+#ifdef LBM_ADJOINT_KERNELS
 static __global__ void __launch_bounds__(NT) lbm_full_k2_kernel(const FullArgs a) {
   const Geom& g = a.g;
   const Coef<double>& c = a.c;
@@ -552,9 +557,11 @@ static __global__ void __launch_bounds__(NT) lbm_full_k2_kernel(const FullArgs a
   a.acc[7 * P + n] += d.dg[0];
   a.acc[8 * P + n] += d.dg[1];
 }
+#endif  // LBM_ADJOINT_KERNELS
 
 // Frozen-fraction seed: the adjoints of the lags fl and w the final state's
 // reader writes (other lag and population adjoints zero).
+#ifdef LBM_ADJOINT_KERNELS
 static __global__ void __launch_bounds__(NT) lbm_full_seed_ff_kernel(const FullArgs a,
                                                                      double* __restrict__ llag) {
   const Geom& g = a.g;
@@ -574,8 +581,10 @@ static __global__ void __launch_bounds__(NT) lbm_full_seed_ff_kernel(const FullA
   llag[LAG_FL * P + n] = -q.w * a.inv_sum_w;
   llag[LAG_W * P + n] = ((1.0 - q.fl) - a.ff) * a.inv_sum_w;
 }
+#endif  // LBM_ADJOINT_KERNELS
 
 // Crossing seed (one thread), as lbm_frz_seed_crossing_kernel.
+#ifdef LBM_ADJOINT_KERNELS
 static __global__ void lbm_full_seed_crossing_kernel(const FullArgs a, double* __restrict__ phib) {
   const Geom& g = a.g;
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
@@ -596,6 +605,7 @@ static __global__ void lbm_full_seed_crossing_kernel(const FullArgs a, double* _
   }
   a.out[0] = J;
 }
+#endif  // LBM_ADJOINT_KERNELS
 
 // Gradient with respect to the initial temperature field (a run from
 // set_geometry): the initial enthalpy populations are h_eq(rho H, T, u = 0)
@@ -604,6 +614,7 @@ static __global__ void lbm_full_seed_crossing_kernel(const FullArgs a, double* _
 // dh_i/dT = w_i rr; T is recovered from the initial populations (pop, lag)
 // by the inversion.  lam: the adjoints of the initial h (9 planes); out:
 // dense [ny][nx].
+#ifdef LBM_ADJOINT_KERNELS
 static __global__ void __launch_bounds__(NT) lbm_full_dT0_kernel(const FullArgs a,
                                                                  const double* __restrict__ lam,
                                                                  double* __restrict__ out) {
@@ -628,6 +639,7 @@ static __global__ void __launch_bounds__(NT) lbm_full_dT0_kernel(const FullArgs 
   for (int i = 1; i < 9; i++) d += lam[i * P + n] * qw<double>(i) * c.rr;
   out[(long long)y * g.nx + x] = d;
 }
+#endif  // LBM_ADJOINT_KERNELS
 
 cudaError_t launch_full_dT0(const FullArgs& a, const double* lam, double* out, cudaStream_t s);
 cudaError_t launch_full_fields(const FullArgs& a, cudaStream_t s);
