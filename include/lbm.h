@@ -470,8 +470,10 @@ int lbm_probe_fma_rate(int precision, double* flops_per_s, void* stream);
  * isotropic stencils use the D3Q19 weights.  A link that leaves through an
  * edge or a corner of the grid is decided by the first wall it crosses in the
  * order x, y, z.  Grid arrays are [nz][ny][nx] with x fastest.  Precisions:
- * LBM_FP32 and LBM_FP64 (others: LBM_ERR_UNSUPPORTED); base.diag_every and
- * the tan_* fields are ignored.  A step is two kernels (the per-node local
+ * LBM_FP32, LBM_FP64 and LBM_FP64_TANGENT (FP64 values with their
+ * derivatives along the direction of base.tan_* and tan_T_wall_z, read with
+ * lbm3_read_tangent_fields and lbm3_read_tangent_diagnostics); LBM_FP16S:
+ * LBM_ERR_UNSUPPORTED.  base.diag_every is ignored.  A step is two kernels (the per-node local
  * state, then stencils, collisions and streaming).  The conventions of the
  * 2-D calls apply (status codes, `where`, streams, ownership).
  * ---------------------------------------------------------------------- */
@@ -485,6 +487,8 @@ typedef struct {
   int32_t bc_z[2];    /* z-low, z-high (LBM_BC_*; periodic in pairs) */
   double T_wall_z[2]; /* used where bc_z[k] == LBM_BC_DIRICHLET */
   double gz;          /* z component of the body force G = rho g */
+  double tan_T_wall_z[2]; /* LBM_FP64_TANGENT: dT_wall_z[k]/ds (the x and y
+                             faces' rates are base.tan_T_wall) */
 } lbm3_params;
 
 /* Fields of lbm3_read_fields: bit k selects out[k], in this order. */
@@ -521,6 +525,14 @@ int lbm3_read_fields(lbm3_ctx* ctx, uint32_t field_mask, double* const* out, int
 /* The FP64 diagnostic sums of the current state (lbm_diag; the kinetic
  * energy with all three velocity components).  Synchronises `stream`. */
 int lbm3_diagnostics(lbm3_ctx* ctx, lbm_diag* out, void* stream);
+
+/* LBM_FP64_TANGENT contexts: the derivatives of the selected fields of the
+ * current state (as lbm3_read_fields), and of the sums of the most recent
+ * lbm3_diagnostics call (nonfinite: 0).  LBM_ERR_UNSUPPORTED for other
+ * precisions, LBM_ERR_STATE before any diagnostics. */
+int lbm3_read_tangent_fields(lbm3_ctx* ctx, uint32_t field_mask, double* const* out, int where,
+                             void* stream);
+int lbm3_read_tangent_diagnostics(lbm3_ctx* ctx, lbm_diag* out);
 
 /* Checkpoint and resume, as lbm_state_size / lbm_save_state /
  * lbm_load_state (57 population planes and 7 lag planes after a header). */

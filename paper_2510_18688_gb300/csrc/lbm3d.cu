@@ -349,7 +349,8 @@ __device__ __forceinline__ void collide_heat(const Args3<R>& a, R* out, int P, i
 }
 
 template <typename R, bool READ>
-__global__ void __launch_bounds__(NT, (sizeof(R) == 4 ? LBM3_MINB_F32 : 2)) lbm3_collide_kernel(const Args3<R> a) {
+__global__ void __launch_bounds__(NT, (sizeof(R) == 4 ? LBM3_MINB_F32 : (sizeof(R) == 8 ? 2 : 1)))
+    lbm3_collide_kernel(const Args3<R> a) {
   const Geom3& g = a.g;
   const Coef<R>& c = a.c;
   const int x = blockIdx.x * BX + threadIdx.x;
@@ -471,7 +472,7 @@ __global__ void __launch_bounds__(NT, (sizeof(R) == 4 ? LBM3_MINB_F32 : 2)) lbm3
     const R vals[NFIELD3] = {phi, fs, fl, T, rhoH, M.pr, M.u[0], M.u[1], M.u[2],
                              rho, M.muphi, w, mdot};
 #pragma unroll
-    for (int k = 0; k < NFIELD3; k++) a.fld[k * N + d] = (double)vals[k];
+    for (int k = 0; k < NFIELD3; k++) lbmk::put_out(a.fld + k * N, d, NFIELD3 * N, vals[k]);
     return;
   }
 
@@ -606,28 +607,42 @@ __global__ void __launch_bounds__(NT) lbm3_init_pops_kernel(const Args3<R> a) {
   }
 }
 
+__device__ __forceinline__ double vv(float x) { return x; }
+__device__ __forceinline__ double vv(double x) { return x; }
+__device__ __forceinline__ double vv(const lbmk::Dual& x) { return x.v; }
+
 // Per-block FP64 partial sums of the diagnostics of the state whose fields
 // the read-out pass left in a.fld (dense order; block b covers nodes
-// b NT ... (b + 1) NT - 1), summed in a fixed tree order.
+// b NT ... (b + 1) NT - 1), summed in a fixed tree order.  For a tangent
+// state (R = Dual) the derivative sums follow as rows NDIAG3 ... 2 NDIAG3 - 1,
+// from the derivative planes the read-out wrote NFIELD3 planes further on.
 template <typename R>
 __global__ void __launch_bounds__(NT) lbm3_diag_partial_kernel(const Args3<R> a,
                                                                double* __restrict__ partial) {
-  __shared__ double s[NDIAG3][NT];
+  constexpr bool TAN = lbmk::is_dual<R>::value;
+  using V = typename std::conditional<TAN, lbmk::Dual, double>::type;
+  constexpr int ND = TAN ? 2 * NDIAG3 : NDIAG3;
+  __shared__ double s[ND][NT];
   const Geom3& g = a.g;
   const Coef<R>& c = a.c;
   const int tid = threadIdx.x;
   const long long N = (long long)g.nx * g.ny * g.nz;
   const long long d = (long long)blockIdx.x * NT + tid;
-  double v[NDIAG3];
+  V v[NDIAG3];
 #pragma unroll
-  for (int k = 0; k < NDIAG3; k++) v[k] = 0.0;
+  for (int k = 0; k < NDIAG3; k++) v[k] = V(0.0);
   if (d < N) {
     const double* F = a.fld;
-    const double phi = F[0 * N + d], fl = F[2 * N + d], rhoH = F[4 * N + d];
-    const double ux = F[6 * N + d], uy = F[7 * N + d], uz = F[8 * N + d];
-    const double rho = F[9 * N + d], w = F[11 * N + d];
+    auto get = [&](int k) -> V {
+      if constexpr (TAN) return V(F[k * N + d], F[(NFIELD3 + k) * N + d]);
+      else return V(F[k * N + d]);
+    };
+    const V phi = get(0), fl = get(2), rhoH = get(4);
+    const V ux = get(6), uy = get(7), uz = get(8);
+    const V rho = get(9), w = get(11);
+    const double rs = vv(c.rho_s), rl = vv(c.rho_l);
     v[0] = rho;
-    v[1] = w * ((double)c.rho_s * (1.0 - fl) + (double)c.rho_l * fl);
+    v[1] = w * (rs * (1.0 - fl) + rl * fl);
     v[2] = rhoH;
     v[3] = w * fl;
     v[4] = w;
@@ -650,26 +665,34 @@ __global__ void __launch_bounds__(NT) lbm3_diag_partial_kernel(const Args3<R> a,
         for (int i = 0; i < Q; i++) tot += a.pin[(2 * Q + i) * P + n];
       }
     }
-    v[8] = isfinite((double)tot) ? 0.0 : 1.0;
+    v[8] = V(lbmk::finite(tot) ? 0.0 : 1.0);
   }
 #pragma unroll
-  for (int k = 0; k < NDIAG3; k++) s[k][tid] = v[k];
+  for (int k = 0; k < NDIAG3; k++) {
+    if constexpr (TAN) {
+      s[k][tid] = v[k].v;
+      s[NDIAG3 + k][tid] = v[k].d;
+    } else {
+      s[k][tid] = v[k];
+    }
+  }
   __syncthreads();
   for (int h = NT / 2; h > 0; h >>= 1) {
     if (tid < h) {
 #pragma unroll
-      for (int k = 0; k < NDIAG3; k++) s[k][tid] += s[k][tid + h];
+      for (int k = 0; k < ND; k++) s[k][tid] += s[k][tid + h];
     }
     __syncthreads();
   }
-  if (tid < NDIAG3) partial[(long long)tid * gridDim.x + blockIdx.x] = s[tid][0];
+  if (tid < ND) partial[(long long)tid * gridDim.x + blockIdx.x] = s[tid][0];
 }
 
 __global__ void __launch_bounds__(NT) lbm3_diag_final_kernel(const double* __restrict__ partial,
-                                                             int nb, double* __restrict__ out) {
+                                                             int nb, int nrows,
+                                                             double* __restrict__ out) {
   __shared__ double s[NT];
   const int tid = threadIdx.x;
-  for (int k = 0; k < NDIAG3; k++) {
+  for (int k = 0; k < nrows; k++) {
     double v = 0.0;
     for (int j = tid; j < nb; j += NT) v += partial[(long long)k * nb + j];
     s[tid] = v;
@@ -693,8 +716,12 @@ struct lbm3_ctx {
   lbm3_params p;
   lbm3::Geom3 g;
   bool f64;
+  bool tangent;  // FP64 values with their derivatives (lbmk::Dual)
   lbmk::Coef<float> cf;
   lbmk::Coef<double> cd;
+  lbmk::Coef<lbmk::Dual> ct;
+  double h_tan[lbm3::NDIAG3];  // derivative sums of the last diagnostics
+  int64_t tan_step;
   void* pop[2];
   void* lag[2];
   void* loc;
@@ -728,6 +755,13 @@ dim3 grid3(const lbm3::Geom3& g) {
 }
 dim3 block3() { return dim3(lbm3::BX, lbm3::BY, lbm3::BZ); }
 
+// a wall temperature with (tangent) or without its derivative
+template <typename R>
+R wall_value(double v, double d) {
+  if constexpr (lbmk::is_dual<R>::value) return R(v, d);
+  else { (void)d; return (R)v; }
+}
+
 template <typename R>
 lbm3::Args3<R> args3(lbm3_ctx* c, const lbmk::Coef<R>& coef) {
   lbm3::Args3<R> a;
@@ -735,9 +769,9 @@ lbm3::Args3<R> args3(lbm3_ctx* c, const lbmk::Coef<R>& coef) {
   a.g = c->g;
   a.c = coef;
   a.gz = (R)c->p.gz;
-  for (int k = 0; k < 4; k++) a.T_wall[k] = (R)c->p.base.T_wall[k];
-  a.T_wall[4] = (R)c->p.T_wall_z[0];
-  a.T_wall[5] = (R)c->p.T_wall_z[1];
+  for (int k = 0; k < 4; k++) a.T_wall[k] = wall_value<R>(c->p.base.T_wall[k], c->p.base.tan_T_wall[k]);
+  a.T_wall[4] = wall_value<R>(c->p.T_wall_z[0], c->p.tan_T_wall_z[0]);
+  a.T_wall[5] = wall_value<R>(c->p.T_wall_z[1], c->p.tan_T_wall_z[1]);
   a.phi0 = (const R*)c->phi0;
   a.mask = c->mask;
   a.loc = (R*)c->loc;
@@ -761,6 +795,7 @@ cudaError_t launch3(lbm3_ctx* c, const lbmk::Coef<R>& coef, bool read, cudaStrea
 }
 
 cudaError_t launch3(lbm3_ctx* c, bool read, cudaStream_t s) {
+  if (c->tangent) return launch3<lbmk::Dual>(c, c->ct, read, s);
   return c->f64 ? launch3<double>(c, c->cd, read, s) : launch3<float>(c, c->cf, read, s);
 }
 
@@ -768,7 +803,8 @@ template <typename R>
 cudaError_t launch_diag3(lbm3_ctx* c, const lbmk::Coef<R>& coef, cudaStream_t s) {
   const lbm3::Args3<R> a = args3<R>(c, coef);
   lbm3::lbm3_diag_partial_kernel<R><<<c->nb, lbm3::NT, 0, s>>>(a, c->partial);
-  lbm3::lbm3_diag_final_kernel<<<1, lbm3::NT, 0, s>>>(c->partial, c->nb, c->dout);
+  const int rows = lbmk::is_dual<R>::value ? 2 * lbm3::NDIAG3 : lbm3::NDIAG3;
+  lbm3::lbm3_diag_final_kernel<<<1, lbm3::NT, 0, s>>>(c->partial, c->nb, rows, c->dout);
   return cudaGetLastError();
 }
 
@@ -794,7 +830,8 @@ int lbm3_create(const lbm3_params* p, lbm3_ctx** out) {
   *out = nullptr;
   char err[256] = {0};
   lbm_params b = p->base;
-  if (b.precision != LBM_FP32 && b.precision != LBM_FP64) return LBM_ERR_UNSUPPORTED;
+  if (b.precision != LBM_FP32 && b.precision != LBM_FP64 && b.precision != LBM_FP64_TANGENT)
+    return LBM_ERR_UNSUPPORTED;
   // the 2-D checks on the x and y extents and the physics (sizes are
   // checked here for the 3-D grid)
   b.ny = 2;
@@ -805,7 +842,8 @@ int lbm3_create(const lbm3_params* p, lbm3_ctx** out) {
   for (int k = 0; k < 2; k++)
     if (p->bc_z[k] < LBM_BC_PERIODIC || p->bc_z[k] > LBM_BC_ADIABATIC) return LBM_ERR_ARG;
   if ((p->bc_z[0] == LBM_BC_PERIODIC) != (p->bc_z[1] == LBM_BC_PERIODIC)) return LBM_ERR_ARG;
-  if (!std::isfinite(p->gz) || !std::isfinite(p->T_wall_z[0]) || !std::isfinite(p->T_wall_z[1]))
+  if (!std::isfinite(p->gz) || !std::isfinite(p->T_wall_z[0]) || !std::isfinite(p->T_wall_z[1]) ||
+      !std::isfinite(p->tan_T_wall_z[0]) || !std::isfinite(p->tan_T_wall_z[1]))
     return LBM_ERR_PARAM;
   const long long pitch = (p->base.nx + 31) / 32 * 32;
   const long long plane = (pitch * p->base.ny * p->nz + 63) / 64 * 64;
@@ -824,20 +862,25 @@ int lbm3_create(const lbm3_params* p, lbm3_ctx** out) {
   c->g.lattices = (int)p->base.lattices;
   c->g.has_mask = 0;
   c->f64 = p->base.precision == LBM_FP64;
+  c->tangent = p->base.precision == LBM_FP64_TANGENT;
   c->cf = lbmh::make_coef<float>(p->base);
   c->cd = lbmh::make_coef<double>(p->base);
-  const size_t es = c->f64 ? 8 : 4;
+  if (c->tangent) c->ct = lbmh::make_coef_tangent(p->base);
+  const size_t es = c->tangent ? 16 : (c->f64 ? 8 : 4);
+  const size_t fmul = c->tangent ? 2 : 1;  // read-out and diagnostics: values, then derivatives
   const long long N = (long long)p->base.nx * p->base.ny * p->nz;
   c->nb = (int)((N + lbm3::NT - 1) / lbm3::NT);
+  c->tan_step = -1;
   cudaError_t e = cudaSuccess;
   for (int k = 0; k < 2 && e == cudaSuccess; k++) e = cudaMalloc(&c->pop[k], 57 * plane * es);
   for (int k = 0; k < 2 && e == cudaSuccess; k++) e = cudaMalloc(&c->lag[k], lbm3::NLAG * plane * es);
   if (e == cudaSuccess) e = cudaMalloc(&c->loc, lbm3::NLOC * plane * es);
   if (e == cudaSuccess) e = cudaMalloc(&c->phi0, plane * es);
   if (e == cudaSuccess) e = cudaMalloc((void**)&c->mask, plane);
-  if (e == cudaSuccess) e = cudaMalloc((void**)&c->fld, lbm3::NFIELD3 * N * sizeof(double));
-  if (e == cudaSuccess) e = cudaMalloc((void**)&c->partial, lbm3::NDIAG3 * (size_t)c->nb * sizeof(double));
-  if (e == cudaSuccess) e = cudaMalloc((void**)&c->dout, lbm3::NDIAG3 * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc((void**)&c->fld, fmul * lbm3::NFIELD3 * N * sizeof(double));
+  if (e == cudaSuccess)
+    e = cudaMalloc((void**)&c->partial, fmul * lbm3::NDIAG3 * (size_t)c->nb * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc((void**)&c->dout, fmul * lbm3::NDIAG3 * sizeof(double));
   // padding nodes are never read; zero them once so that no buffer holds
   // uninitialised values
   for (int k = 0; k < 2 && e == cudaSuccess; k++) e = cudaMemset(c->pop[k], 0, 57 * plane * es);
@@ -882,8 +925,9 @@ int lbm3_set_geometry(lbm3_ctx* c, const double* phi0, const uint8_t* mask, cons
   c->g.has_mask = mask ? 1 : 0;
   c->cur = 0;
   if (e == cudaSuccess)
-    e = c->f64 ? launch_init3<double>(c, c->cd, dsrc[0], dmask, dsrc[1], dsrc[2], dsrc[3], s)
-               : launch_init3<float>(c, c->cf, dsrc[0], dmask, dsrc[1], dsrc[2], dsrc[3], s);
+    e = c->tangent ? launch_init3<lbmk::Dual>(c, c->ct, dsrc[0], dmask, dsrc[1], dsrc[2], dsrc[3], s)
+        : c->f64   ? launch_init3<double>(c, c->cd, dsrc[0], dmask, dsrc[1], dsrc[2], dsrc[3], s)
+                   : launch_init3<float>(c, c->cf, dsrc[0], dmask, dsrc[1], dsrc[2], dsrc[3], s);
   if (where == LBM_HOST) {
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (stage) cudaFree(stage);
@@ -929,15 +973,57 @@ int lbm3_read_fields(lbm3_ctx* c, uint32_t field_mask, double* const* out, int w
   return LBM_OK;
 }
 
+int lbm3_read_tangent_fields(lbm3_ctx* c, uint32_t field_mask, double* const* out, int where,
+                             void* stream) {
+  if (!c) return LBM_ERR_ARG;
+  if (!c->tangent) return fail3(c, LBM_ERR_UNSUPPORTED, "not a tangent context");
+  if (!out || (field_mask >> lbm3::NFIELD3)) return fail3(c, LBM_ERR_ARG, "bad field mask or output");
+  if (where != LBM_HOST && where != LBM_DEVICE) return fail3(c, LBM_ERR_ARG, "bad `where`");
+  if (!c->have_geometry) return fail3(c, LBM_ERR_STATE, "read before lbm3_set_geometry");
+  for (int k = 0; k < lbm3::NFIELD3; k++)
+    if ((field_mask >> k & 1u) && !out[k]) return fail3(c, LBM_ERR_ARG, "null output for a selected field");
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t N = (size_t)c->g.nx * c->g.ny * c->g.nz;
+  cudaError_t e = launch3(c, true, s);
+  for (int k = 0; k < lbm3::NFIELD3 && e == cudaSuccess; k++)
+    if (field_mask >> k & 1u)
+      e = cudaMemcpyAsync(out[k], c->fld + (lbm3::NFIELD3 + k) * N, N * sizeof(double),
+                          where == LBM_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, s);
+  if (e == cudaSuccess && where == LBM_HOST) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_fail3(c, e, "lbm3_read_tangent_fields");
+  return LBM_OK;
+}
+
+int lbm3_read_tangent_diagnostics(lbm3_ctx* c, lbm_diag* out) {
+  if (!c || !out) return LBM_ERR_ARG;
+  if (!c->tangent) return fail3(c, LBM_ERR_UNSUPPORTED, "not a tangent context");
+  if (c->tan_step < 0) return fail3(c, LBM_ERR_STATE, "no diagnostics computed yet");
+  const double* h = c->h_tan;
+  out->mass = h[0];
+  out->material_mass = h[1];
+  out->rhoH = h[2];
+  out->liquid_volume = h[3];
+  out->material_volume = h[4];
+  out->frozen_volume = h[5];
+  out->phi_sum = h[6];
+  out->kinetic = h[7];
+  out->nonfinite = 0.0;
+  out->step = c->tan_step;
+  return LBM_OK;
+}
+
 int lbm3_diagnostics(lbm3_ctx* c, lbm_diag* out, void* stream) {
   if (!c || !out) return LBM_ERR_ARG;
   if (!c->have_geometry) return fail3(c, LBM_ERR_STATE, "diagnostics before lbm3_set_geometry");
   cudaStream_t s = (cudaStream_t)stream;
-  double h[lbm3::NDIAG3];
+  double h[2 * lbm3::NDIAG3];
+  const size_t rows = c->tangent ? 2 * lbm3::NDIAG3 : lbm3::NDIAG3;
   cudaError_t e = launch3(c, true, s);
   if (e == cudaSuccess)
-    e = c->f64 ? launch_diag3<double>(c, c->cd, s) : launch_diag3<float>(c, c->cf, s);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(h, c->dout, sizeof(h), cudaMemcpyDeviceToHost, s);
+    e = c->tangent ? launch_diag3<lbmk::Dual>(c, c->ct, s)
+        : c->f64   ? launch_diag3<double>(c, c->cd, s)
+                   : launch_diag3<float>(c, c->cf, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(h, c->dout, rows * sizeof(double), cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return cuda_fail3(c, e, "lbm3_diagnostics");
   out->mass = h[0];
@@ -950,6 +1036,10 @@ int lbm3_diagnostics(lbm3_ctx* c, lbm_diag* out, void* stream) {
   out->kinetic = h[7];
   out->nonfinite = h[8];
   out->step = c->step;
+  if (c->tangent) {
+    for (int k = 0; k < lbm3::NDIAG3; k++) c->h_tan[k] = k == 8 ? 0.0 : h[lbm3::NDIAG3 + k];
+    c->tan_step = c->step;
+  }
   return h[8] > 0.0 ? LBM_ERR_NONFINITE : LBM_OK;
 }
 
@@ -966,7 +1056,7 @@ constexpr uint32_t kVersion3 = 1;
 
 int lbm3_state_size(const lbm3_ctx* c, size_t* bytes) {
   if (!c || !bytes) return LBM_ERR_ARG;
-  const size_t es = c->f64 ? 8 : 4;
+  const size_t es = c->tangent ? 16 : (c->f64 ? 8 : 4);
   *bytes = sizeof(State3Header) + (57 + lbm3::NLAG) * es * (size_t)c->g.plane;
   return LBM_OK;
 }
@@ -982,7 +1072,7 @@ int lbm3_save_state(lbm3_ctx* c, void* host_buf, size_t capacity, void* stream) 
                           c->p.base.precision, (int32_t)c->p.base.lattices, 0, c->step};
   std::memcpy(host_buf, &h, sizeof(h));
   char* dst = (char*)host_buf + sizeof(h);
-  const size_t es = c->f64 ? 8 : 4;
+  const size_t es = c->tangent ? 16 : (c->f64 ? 8 : 4);
   const size_t pb = 57 * es * (size_t)c->g.plane;
   cudaError_t e = cudaMemcpyAsync(dst, c->pop[c->cur], pb, cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess)
@@ -1007,7 +1097,7 @@ int lbm3_load_state(lbm3_ctx* c, const void* host_buf, size_t size, void* stream
     return fail3(c, LBM_ERR_ARG, "state does not match this context");
   cudaStream_t s = (cudaStream_t)stream;
   const char* src = (const char*)host_buf + sizeof(h);
-  const size_t es = c->f64 ? 8 : 4;
+  const size_t es = c->tangent ? 16 : (c->f64 ? 8 : 4);
   const size_t pb = 57 * es * (size_t)c->g.plane;
   cudaError_t e = cudaMemcpyAsync(c->pop[c->cur], src, pb, cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess)

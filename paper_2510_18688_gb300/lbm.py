@@ -65,7 +65,7 @@ EXPORTS = ("lbm_create", "lbm_set_geometry", "lbm_step", "lbm_read_fields",
            "lbm_debug_fail_allocation", "lbm3_create", "lbm3_set_geometry", "lbm3_step",
            "lbm3_read_fields", "lbm3_diagnostics", "lbm3_step_count", "lbm3_last_error",
            "lbm3_destroy", "lbm3_lattice", "lbm3_state_size", "lbm3_save_state",
-           "lbm3_load_state")
+           "lbm3_load_state", "lbm3_read_tangent_fields", "lbm3_read_tangent_diagnostics")
 FIELDS3 = ("phi", "fs", "fl", "T", "rhoH", "p", "ux", "uy", "uz", "rho", "mu", "w", "mdot")
 
 _lib = None
@@ -131,11 +131,14 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     L.lbm3_destroy.restype = None
     L.lbm3_lattice.argtypes = [ctypes.POINTER(ctypes.c_int32), dp]
     L.lbm3_state_size.argtypes = [vp, ctypes.POINTER(ctypes.c_size_t)]
+    L.lbm3_read_tangent_fields.argtypes = [vp, ctypes.c_uint32, ctypes.POINTER(vp), ctypes.c_int, vp]
+    L.lbm3_read_tangent_diagnostics.argtypes = [vp, ctypes.POINTER(LbmDiag)]
     L.lbm3_save_state.argtypes = [vp, vp, ctypes.c_size_t, vp]
     L.lbm3_load_state.argtypes = [vp, vp, ctypes.c_size_t, vp]
     L.lbm3_lattice.restype = None
     for fn in ("lbm3_create", "lbm3_set_geometry", "lbm3_step", "lbm3_read_fields",
-               "lbm3_diagnostics", "lbm3_state_size", "lbm3_save_state", "lbm3_load_state"):
+               "lbm3_diagnostics", "lbm3_state_size", "lbm3_save_state", "lbm3_load_state",
+               "lbm3_read_tangent_fields", "lbm3_read_tangent_diagnostics"):
         getattr(L, fn).restype = ctypes.c_int
     for fn in ("lbm_create", "lbm_set_geometry", "lbm_step", "lbm_read_fields",
                "lbm_compute_diagnostics", "lbm_read_diagnostics", "lbm_state_size",
@@ -151,7 +154,8 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
 
 class Lbm3Params(ctypes.Structure):
     _fields_ = [("base", LbmParams), ("nz", ctypes.c_int32), ("bc_z", ctypes.c_int32 * 2),
-                ("T_wall_z", ctypes.c_double * 2), ("gz", ctypes.c_double)]
+                ("T_wall_z", ctypes.c_double * 2), ("gz", ctypes.c_double),
+                ("tan_T_wall_z", ctypes.c_double * 2)]
 
 
 class LbmError(RuntimeError):
@@ -558,11 +562,16 @@ class Batch:
 
 # --- three-dimensional (D3Q19) contexts ---------------------------------------
 
-def make_params3(cfg: dict, precision: str = "fp32") -> Lbm3Params:
+def make_params3(cfg: dict, precision: str = "fp32", tangent: dict = None) -> Lbm3Params:
     """lbm3_params of a 3-D workload dict (six boundary types and wall
-    temperatures: x_lo, x_hi, y_lo, y_hi, z_lo, z_hi; nz; gz)."""
+    temperatures: x_lo, x_hi, y_lo, y_hi, z_lo, z_hi; nz; gz).  tangent
+    (precision "tangent"): {"T_wall": [6 rates], "T_cold", "theta_deg",
+    "latent"} (missing entries: 0)."""
+    t = dict(tangent or {})
+    tw = list(t.get("T_wall", [0.0] * 6)) + [0.0] * 6
+    t2 = dict(t, T_wall=tw[:4])
     base = make_params(dict(cfg, bc=tuple(cfg["bc"][:4]), T_wall=tuple(cfg["T_wall"][:4])),
-                       precision)
+                       precision, 0, t2)
     p = Lbm3Params()
     p.base = base
     p.nz = int(cfg["nz"])
@@ -570,6 +579,7 @@ def make_params3(cfg: dict, precision: str = "fp32") -> Lbm3Params:
         p.bc_z[k] = BC[cfg["bc"][4 + k]]
         p.T_wall_z[k] = float(cfg["T_wall"][4 + k])
     p.gz = float(cfg.get("gz", 0.0))
+    p.tan_T_wall_z[0], p.tan_T_wall_z[1] = float(tw[4]), float(tw[5])
     return p
 
 
@@ -644,6 +654,19 @@ def lbm3_load_state(ctx, data: bytes, stream=None):
     _check3(ctx, load().lbm3_load_state(ctx, buf, len(data), stream), "lbm3_load_state")
 
 
+def lbm3_read_tangent_fields(ctx, field_mask: int, out_ptrs, where, stream=None):
+    arr = (ctypes.c_void_p * len(FIELDS3))(*[p or None for p in out_ptrs])
+    _check3(ctx, load().lbm3_read_tangent_fields(ctx, field_mask, arr, where, stream),
+            "lbm3_read_tangent_fields")
+
+
+def lbm3_read_tangent_diagnostics(ctx) -> dict:
+    d = LbmDiag()
+    _check3(ctx, load().lbm3_read_tangent_diagnostics(ctx, ctypes.byref(d)),
+            "lbm3_read_tangent_diagnostics")
+    return {k: getattr(d, k) for k, _ in LbmDiag._fields_}
+
+
 def lbm3_lattice():
     """(c [19, 3], w [19]) of the library's D3Q19 lattice (host only)."""
     c = (ctypes.c_int32 * 57)()
@@ -655,17 +678,17 @@ def lbm3_lattice():
 class Solver3:
     """One three-dimensional (D3Q19) GPU context; arrays are [nz, ny, nx]."""
 
-    def __init__(self, cfg: dict, precision: str = "fp32"):
+    def __init__(self, cfg: dict, precision: str = "fp32", tangent: dict = None):
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("Solver3 needs a CUDA device (no CPU path)")
-        if precision not in ("fp32", "fp64"):
-            raise ValueError("3-D contexts take fp32 or fp64")
+        if precision not in ("fp32", "fp64", "tangent"):
+            raise ValueError("3-D contexts take fp32, fp64 or tangent")
         load()
         self.cfg = dict(cfg)
         self.shape = (int(cfg["nz"]), int(cfg["ny"]), int(cfg["nx"]))
         self.precision = precision
-        self.params = make_params3(cfg, precision)
+        self.params = make_params3(cfg, precision, tangent)
         self.ctx = lbm3_create(self.params)
 
     def close(self):
@@ -721,6 +744,22 @@ class Solver3:
 
     def diagnostics(self) -> dict:
         return lbm3_diagnostics(self.ctx, _stream())
+
+    def tangent_fields(self, names=FIELDS3) -> dict:
+        """Derivatives of the fields along the parameter direction (host)."""
+        out = {k: np.empty(self.shape, dtype=np.float64) for k in names}
+        mask = 0
+        ptrs = [None] * len(FIELDS3)
+        for k in names:
+            i = FIELDS3.index(k)
+            mask |= 1 << i
+            ptrs[i] = out[k].ctypes.data
+        lbm3_read_tangent_fields(self.ctx, mask, ptrs, LBM_HOST, _stream())
+        return out
+
+    def tangent_diagnostics(self) -> dict:
+        """Derivatives of the sums of the most recent diagnostics() call."""
+        return lbm3_read_tangent_diagnostics(self.ctx)
 
     def save_state(self) -> bytes:
         return lbm3_save_state(self.ctx, _stream())

@@ -178,3 +178,50 @@ def test_checkpoint_resume_is_bit_exact(env):
             other.load_state(blob)
         for s in (a, c, other):
             s.close()
+
+
+def test_tangent_3d_matches_fp64_and_differences(env):
+    """Forward mode on D3Q19: the tangent context's values are the FP64
+    step's, and its derivatives of the frozen fraction and of the
+    temperature field along a wall temperature, the cold-mask temperature,
+    the contact angle and L agree with central differences of the FP64 3-D
+    step."""
+    O3, lbm = env
+    cfg, arr = W.random_state3(20, 12, 8, seed=3)
+    steps = 40
+
+    def ff_fields(c):
+        u = lbm.Solver3(c, "fp64").set_geometry(arr).step(steps)
+        d = u.diagnostics()
+        f = u.fields(("T", "phi"))
+        u.close()
+        return d["frozen_volume"] / d["material_volume"], f
+
+    ff0, f0 = ff_fields(cfg)
+    dirs = [("T_wall", {"T_wall": [1.0, 0, 0, 0, 0, 0]}, 1e-6),
+            ("T_cold", {"T_cold": 1.0}, 1e-6),
+            ("theta_deg", {"theta_deg": 1.0}, 1e-4),
+            ("latent", {"latent": 1.0}, 1e-6 * cfg["latent"])]
+    for name, t, h in dirs:
+        s = lbm.Solver3(cfg, "tangent", tangent=t).set_geometry(arr).step(steps)
+        d = s.diagnostics()
+        dt = s.tangent_diagnostics()
+        f = s.fields(("T", "phi"))
+        df = s.tangent_fields(("T",))
+        s.close()
+        fz, mv = d["frozen_volume"], d["material_volume"]
+        assert abs(fz / mv - ff0) <= 1e-12
+        assert np.abs(f["T"] - f0["T"]).max() <= 1e-12 * max(1.0, np.abs(f0["T"]).max())
+        dff = (dt["frozen_volume"] * mv - fz * dt["material_volume"]) / mv ** 2
+        if name == "T_wall":
+            cp, cm = dict(cfg, T_wall=(cfg["T_wall"][0] + h,) + tuple(cfg["T_wall"][1:])), \
+                dict(cfg, T_wall=(cfg["T_wall"][0] - h,) + tuple(cfg["T_wall"][1:]))
+        else:
+            cp, cm = dict(cfg, **{name: cfg[name] + h}), dict(cfg, **{name: cfg[name] - h})
+        (fp, Fp), (fm, Fm) = ff_fields(cp), ff_fields(cm)
+        fd = (fp - fm) / (2 * h)
+        fdT = (Fp["T"] - Fm["T"]) / (2 * h)
+        print(f"\n{name}: dFF tangent {dff:.10e} FD {fd:.10e}; dT max {np.abs(df['T']).max():.4e} "
+              f"err {np.abs(df['T'] - fdT).max():.3e}")
+        assert abs(dff - fd) <= 1e-4 * abs(fd) + 1e-9, (name, dff, fd)
+        assert np.abs(df["T"] - fdT).max() <= 1e-4 * max(np.abs(fdT).max(), 1e-6), name
