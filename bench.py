@@ -115,9 +115,13 @@ KERNEL_SOURCES = ("lbm_kernels.cuh", "lbm_dual.cuh", "lbm_step.cuh", "lbm_split.
                   "lbm_launch.h", "lbm_f32.cu", "lbm_f64.cu", "lbm_f16.cu", "lbm_tan.cu")
 
 
-def kernel_source_hash() -> str:
+# the sources of the 3-D step kernels
+KERNEL_SOURCES3 = ("lbm3d.cu", "lbm_kernels.cuh", "lbm_dual.cuh", "lbm_host.h")
+
+
+def kernel_source_hash(sources=KERNEL_SOURCES) -> str:
     h = hashlib.sha256()
-    for f in KERNEL_SOURCES:
+    for f in sources:
         with open(os.path.join(ROOT, "paper_2510_18688_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -133,6 +137,16 @@ def profiled_value(workload: str, precision: str, key: str):
     """A per-launch figure (e.g. "dram bytes per launch") from the committed
     ncu summary of this workload, if it was taken on the current kernel
     source; else None."""
+    if workload in WORKLOADS3:
+        path = os.path.join(ROOT, "profiles", f"lbm3_collide_{ {'fp32': 'f32', 'fp64': 'f64'}[precision] }_{workload}.md")
+        if not os.path.exists(path):
+            return None
+        txt = open(path).read()
+        m = re.search(r"kernel source hash:\s*([0-9a-f]+)", txt)
+        t = re.search(re.escape(key) + r":\s*([0-9.eE+]+)", txt)
+        if not m or not t or m.group(1) != kernel_source_hash(KERNEL_SOURCES3):
+            return None
+        return float(t.group(1))
     path = os.path.join(ROOT, "profiles", profile_name(workload, precision))
     if not os.path.exists(path):
         return None
@@ -473,8 +487,9 @@ def fracture_line(args, rank, world):
                    "l2": "not flushed: the state (57 population planes) is larger than L2",
                    "parallelism": f"replicas x{world}"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": None, "peak_source": peak_src,
-                     "bytes_per_node": bpn,
+                     "frac": achieved / peak,
+                     "traffic": profiled_value(args.workload, args.precision, "dram bytes per step"),
+                     "peak_source": peak_src, "bytes_per_node": bpn,
                      "scope": "whole step (local-state and collide kernels together)"},
         "gpu_launches": 2 * args.steps,
         "e2e": {"value": n * args.steps / e2e_s / 1e6, "unit": "MLUPS",
