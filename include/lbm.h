@@ -501,7 +501,9 @@ enum {
 #define LBM3_NUM_FIELDS 13
 
 /* Validates *params as lbm_create does (plus nz, bc_z and the size limit:
- * 57 population planes must fit 31-bit offsets) and allocates the device
+ * a plane of nx rounded up to 32 times ny times nz nodes must stay below
+ * 2^31; the device memory, about 550 B per node in FP32, is the practical
+ * limit: some 500 million nodes on 280 GB) and allocates the device
  * state (two population buffers of 57 planes, two lag buffers of 7 planes,
  * 8 local planes, phi0, the mask, and a 13-plane FP64 read-out buffer).
  * Errors: LBM_ERR_ARG, LBM_ERR_PARAM, LBM_ERR_UNSUPPORTED (precision),

@@ -94,7 +94,7 @@ __device__ __forceinline__ R wq(int i) {
 
 struct Geom3 {
   int nx, ny, nz, pitch;
-  int plane;  // elements per plane (57 population planes fit 31 bits)
+  long long plane;  // elements per plane (node offsets within a plane fit 31 bits)
   int bc[6];
   int lattices;
   int has_mask;
@@ -150,8 +150,8 @@ __device__ __forceinline__ int stream_target(const Geom3& g, int x, int y, int z
 // Store of one post-collision population of direction i from node n; for
 // the enthalpy lattice (HEAT) a link leaving through a Dirichlet wall
 // returns by anti-bounce-back, through an adiabatic wall by bounce-back.
-template <typename R, bool HEAT>
-__device__ __forceinline__ void push(const Args3<R>& a, R* __restrict__ plane0, int P, int i,
+template <typename R, bool HEAT, typename I>
+__device__ __forceinline__ void push(const Args3<R>& a, R* __restrict__ plane0, I P, int i,
                                      int x, int y, int z, int n, bool inner, R v) {
   const Geom3& g = a.g;
   if (inner) {
@@ -198,7 +198,10 @@ __device__ __forceinline__ R sum19(const R* v) {
 // kernel 1: local state of every node
 // ---------------------------------------------------------------------------
 
-template <typename R>
+// I: the type of plane offsets (int while 57 population planes fit 31
+// bits, which keeps the index arithmetic in 32-bit registers; long long for
+// larger grids)
+template <typename R, typename I>
 __global__ void __launch_bounds__(NT) lbm3_local_kernel(const Args3<R> a) {
   const Geom3& g = a.g;
   const Coef<R>& c = a.c;
@@ -206,7 +209,7 @@ __global__ void __launch_bounds__(NT) lbm3_local_kernel(const Args3<R> a) {
   const int y = blockIdx.y * BY + threadIdx.y;
   const int z = blockIdx.z * BZ + threadIdx.z;
   if (x >= g.nx || y >= g.ny || z >= g.nz) return;
-  const int P = g.plane;
+  const I P = (I)g.plane;
   const int n = node(g, x, y, z);
   const int lat = g.lattices;
   const R phi0 = a.phi0[n];
@@ -251,8 +254,8 @@ struct Macro3 {
 
 // Flow collision Eqs. (11), (14)-(16) over the opposite pairs (i, i + 1):
 // the terms even in c_i are shared by the pair, the odd ones change sign.
-template <typename R>
-__device__ __forceinline__ void collide_flow(const Args3<R>& a, R* out, int P, int x, int y,
+template <typename R, typename I>
+__device__ __forceinline__ void collide_flow(const Args3<R>& a, R* out, I P, int x, int y,
                                              int z, int n, bool inner, const R* f, R rho,
                                              const Macro3<R>& M) {
   const R itau = lbmk::qdiv(R(1), M.tauf);
@@ -265,7 +268,7 @@ __device__ __forceinline__ void collide_flow(const Args3<R>& a, R* out, int P, i
     R F0 = fsym0;
     if (iso) F0 += M.S * (R(0) - R(1)) * R(1.5);
     const R feq0 = M.pr * R(3) * (wq<R>(0) - R(1)) + rho * wq<R>(0) * (-R(1.5) * M.uu);
-    push<R, false>(a, out, P, 0, x, y, z, n, inner, f[0] * omi + itau * feq0 + fcoef * wq<R>(0) * F0);
+    push<R, false, I>(a, out, P, 0, x, y, z, n, inner, f[0] * omi + itau * feq0 + fcoef * wq<R>(0) * F0);
   }
 #pragma unroll
   for (int i = 1; i < Q; i += 2) {
@@ -281,14 +284,14 @@ __device__ __forceinline__ void collide_flow(const Args3<R>& a, R* out, int P, i
     const R srcA = R(3) * cG;
     const R Ps = wi * (itau * eqS + fcoef * srcS);
     const R Pa = wi * (itau * eqA + fcoef * srcA);
-    push<R, false>(a, out, P, i, x, y, z, n, inner, f[i] * omi + Ps + Pa);
-    push<R, false>(a, out, P, o, x, y, z, n, inner, f[o] * omi + Ps - Pa);
+    push<R, false, I>(a, out, P, i, x, y, z, n, inner, f[i] * omi + Ps + Pa);
+    push<R, false, I>(a, out, P, o, x, y, z, n, inner, f[o] * omi + Ps - Pa);
   }
 }
 
 // Phase-field collision Eqs. (18)-(20).
-template <typename R>
-__device__ __forceinline__ void collide_phase(const Args3<R>& a, R* out, int P, int x, int y,
+template <typename R, typename I>
+__device__ __forceinline__ void collide_phase(const Args3<R>& a, R* out, I P, int x, int y,
                                               int z, int n, bool inner, const R* gq, R phi,
                                               R mdot, const R* phup, const Macro3<R>& M) {
   const Coef<R>& c = a.c;
@@ -302,7 +305,7 @@ __device__ __forceinline__ void collide_phase(const Args3<R>& a, R* out, int P, 
   for (int k = 0; k < 3; k++) V[k] = R(3) * (itg * M.phu[k] + gcoef * (M.phu[k] - phup[k]));
   {
     const R geq0 = phi + (wq<R>(0) - R(1)) * emu;
-    push<R, false>(a, out, P, 0, x, y, z, n, inner,
+    push<R, false, I>(a, out, P, 0, x, y, z, n, inner,
                    gq[0] * omg + itg * geq0 + gcoef * wq<R>(0) * phi * mdot);
   }
 #pragma unroll
@@ -311,14 +314,14 @@ __device__ __forceinline__ void collide_phase(const Args3<R>& a, R* out, int P, 
     const R wi = wq<R>(i);
     const R Ps = wi * Zs;
     const R Pa = wi * (R(cx(i)) * V[0] + R(cy(i)) * V[1] + R(cz(i)) * V[2]);
-    push<R, false>(a, out, P, i, x, y, z, n, inner, gq[i] * omg + Ps + Pa);
-    push<R, false>(a, out, P, o, x, y, z, n, inner, gq[o] * omg + Ps - Pa);
+    push<R, false, I>(a, out, P, i, x, y, z, n, inner, gq[i] * omg + Ps + Pa);
+    push<R, false, I>(a, out, P, o, x, y, z, n, inner, gq[o] * omg + Ps - Pa);
   }
 }
 
 // Enthalpy TRT collision Eqs. (23)-(27) with the magic relation.
-template <typename R>
-__device__ __forceinline__ void collide_heat(const Args3<R>& a, R* out, int P, int x, int y,
+template <typename R, typename I>
+__device__ __forceinline__ void collide_heat(const Args3<R>& a, R* out, I P, int x, int y,
                                              int z, int n, bool inner, const R* h, R fs, R w,
                                              R T, R rhoH, R mdot, const Macro3<R>& M) {
   const Coef<R>& c = a.c;
@@ -331,7 +334,7 @@ __device__ __forceinline__ void collide_heat(const Args3<R>& a, R* out, int P, i
   const R rrT = c.rr * T;
   {
     const R heq0 = rhoH - rrT + wq<R>(0) * (rrT - CT * M.uu * R(1.5));
-    push<R, true>(a, out, P, 0, x, y, z, n, inner, h[0] - (h[0] - heq0) * is + wq<R>(0) * Hsrc);
+    push<R, true, I>(a, out, P, 0, x, y, z, n, inner, h[0] - (h[0] - heq0) * is + wq<R>(0) * Hsrc);
   }
 #pragma unroll
   for (int i = 1; i < Q; i += 2) {
@@ -343,12 +346,12 @@ __device__ __forceinline__ void collide_heat(const Args3<R>& a, R* out, int P, i
     const R hs = R(0.5) * (h[i] + h[o]), ha = R(0.5) * (h[i] - h[o]);
     const R Da = (ha - ea) * ia;
     const R Ds = (hs - es) * is - wi * Hsrc;
-    push<R, true>(a, out, P, i, x, y, z, n, inner, h[i] - Da - Ds);
-    push<R, true>(a, out, P, o, x, y, z, n, inner, h[o] + Da - Ds);
+    push<R, true, I>(a, out, P, i, x, y, z, n, inner, h[i] - Da - Ds);
+    push<R, true, I>(a, out, P, o, x, y, z, n, inner, h[o] + Da - Ds);
   }
 }
 
-template <typename R, bool READ>
+template <typename R, bool READ, typename I>
 __global__ void __launch_bounds__(NT, (sizeof(R) == 4 ? LBM3_MINB_F32 : (sizeof(R) == 8 ? 2 : 1)))
     lbm3_collide_kernel(const Args3<R> a) {
   const Geom3& g = a.g;
@@ -357,7 +360,7 @@ __global__ void __launch_bounds__(NT, (sizeof(R) == 4 ? LBM3_MINB_F32 : (sizeof(
   const int y = blockIdx.y * BY + threadIdx.y;
   const int z = blockIdx.z * BZ + threadIdx.z;
   if (x >= g.nx || y >= g.ny || z >= g.nz) return;
-  const int P = g.plane;
+  const I P = (I)g.plane;
   const int n = node(g, x, y, z);
   const int lat = g.lattices;
   const R* loc = a.loc;
@@ -522,7 +525,7 @@ __global__ void __launch_bounds__(NT) lbm3_init_local_kernel(
   const int y = blockIdx.y * BY + threadIdx.y;
   const int z = blockIdx.z * BZ + threadIdx.z;
   if (x >= g.nx || y >= g.ny || z >= g.nz) return;
-  const int P = g.plane;
+  const long long P = g.plane;
   const int n = node(g, x, y, z);
   const long long d = ((long long)z * g.ny + y) * g.nx + x;
   const R q0 = (R)phi0d[d], ph = (R)phid[d];
@@ -563,7 +566,7 @@ __global__ void __launch_bounds__(NT) lbm3_init_pops_kernel(const Args3<R> a) {
   const int y = blockIdx.y * BY + threadIdx.y;
   const int z = blockIdx.z * BZ + threadIdx.z;
   if (x >= g.nx || y >= g.ny || z >= g.nz) return;
-  const int P = g.plane;
+  const long long P = g.plane;
   const int n = node(g, x, y, z);
   const R* loc = a.loc;
   const R phi = loc[S_PHI * P + n], fs = loc[S_FS * P + n], T = loc[S_T * P + n];
@@ -650,7 +653,8 @@ __global__ void __launch_bounds__(NT) lbm3_diag_partial_kernel(const Args3<R> a,
     v[6] = phi;
     v[7] = 0.5 * rho * (ux * ux + uy * uy + uz * uz);
     const int x = (int)(d % g.nx), y = (int)((d / g.nx) % g.ny), z = (int)(d / ((long long)g.nx * g.ny));
-    const int P = g.plane, n = node(g, x, y, z);
+    const long long P = g.plane;
+    const int n = node(g, x, y, z);
     R tot = R(0);
     if (g.lattices & LAT_FLOW)
       for (int i = 0; i < Q; i++) tot += a.pin[i * P + n];
@@ -788,9 +792,15 @@ lbm3::Args3<R> args3(lbm3_ctx* c, const lbmk::Coef<R>& coef) {
 template <typename R>
 cudaError_t launch3(lbm3_ctx* c, const lbmk::Coef<R>& coef, bool read, cudaStream_t s) {
   const lbm3::Args3<R> a = args3<R>(c, coef);
-  lbm3::lbm3_local_kernel<R><<<grid3(c->g), block3(), 0, s>>>(a);
-  if (read) lbm3::lbm3_collide_kernel<R, true><<<grid3(c->g), block3(), 0, s>>>(a);
-  else lbm3::lbm3_collide_kernel<R, false><<<grid3(c->g), block3(), 0, s>>>(a);
+  if (c->g.plane * 57 < (1LL << 31)) {
+    lbm3::lbm3_local_kernel<R, int><<<grid3(c->g), block3(), 0, s>>>(a);
+    if (read) lbm3::lbm3_collide_kernel<R, true, int><<<grid3(c->g), block3(), 0, s>>>(a);
+    else lbm3::lbm3_collide_kernel<R, false, int><<<grid3(c->g), block3(), 0, s>>>(a);
+  } else {
+    lbm3::lbm3_local_kernel<R, long long><<<grid3(c->g), block3(), 0, s>>>(a);
+    if (read) lbm3::lbm3_collide_kernel<R, true, long long><<<grid3(c->g), block3(), 0, s>>>(a);
+    else lbm3::lbm3_collide_kernel<R, false, long long><<<grid3(c->g), block3(), 0, s>>>(a);
+  }
   return cudaGetLastError();
 }
 
@@ -847,7 +857,7 @@ int lbm3_create(const lbm3_params* p, lbm3_ctx** out) {
     return LBM_ERR_PARAM;
   const long long pitch = (p->base.nx + 31) / 32 * 32;
   const long long plane = (pitch * p->base.ny * p->nz + 63) / 64 * 64;
-  if (plane * 57 >= (1LL << 31)) return LBM_ERR_ARG;
+  if (plane >= (1LL << 31)) return LBM_ERR_ARG;  // node offsets within a plane are 32-bit
   lbm3_ctx* c = new (std::nothrow) lbm3_ctx();
   if (!c) return LBM_ERR_OOM;
   c->p = *p;
@@ -855,7 +865,7 @@ int lbm3_create(const lbm3_params* p, lbm3_ctx** out) {
   c->g.ny = p->base.ny;
   c->g.nz = p->nz;
   c->g.pitch = (int)pitch;
-  c->g.plane = (int)plane;
+  c->g.plane = plane;
   for (int k = 0; k < 4; k++) c->g.bc[k] = p->base.bc[k];
   c->g.bc[4] = p->bc_z[0];
   c->g.bc[5] = p->bc_z[1];

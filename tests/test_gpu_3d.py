@@ -225,3 +225,31 @@ def test_tangent_3d_matches_fp64_and_differences(env):
               f"err {np.abs(df['T'] - fdT).max():.3e}")
         assert abs(dff - fd) <= 1e-4 * abs(fd) + 1e-9, (name, dff, fd)
         assert np.abs(df["T"] - fdT).max() <= 1e-4 * max(np.abs(fdT).max(), 1e-6), name
+
+
+@pytest.mark.slow
+def test_grid_beyond_31_bit_population_offsets(env):
+    """A grid whose 57 population planes span more than 2^31 elements (39.3M
+    nodes, 64-bit plane offsets): a small periodic state repeated 200 times
+    along x must step into exactly the repeated result of the small grid
+    (translation symmetry; the small grid itself is checked against the
+    oracle above)."""
+    O3, lbm = env
+    import torch
+    reps = 200
+    cfg, arr = W.random_state3(48, 64, 64, seed=2)  # periodic on all six faces
+    assert all(b == "periodic" for b in cfg["bc"])
+    small = lbm.Solver3(cfg, "fp32").set_geometry(arr).step(4)
+    fs = small.fields(("phi", "T"))
+    small.close()
+    big_cfg = dict(cfg, nx=cfg["nx"] * reps)
+    big_arr = {k: np.ascontiguousarray(np.tile(v, (1, 1, reps))) for k, v in arr.items()}
+    assert 57 * big_cfg["nx"] * cfg["ny"] * cfg["nz"] > 2 ** 31
+    big = lbm.Solver3(big_cfg, "fp32").set_geometry(big_arr).step(4)
+    fb = big.fields(("phi", "T"))
+    d = big.diagnostics()
+    big.close()
+    torch.cuda.empty_cache()
+    for k in ("phi", "T"):
+        assert np.array_equal(fb[k], np.tile(fs[k], (1, 1, reps))), k
+    assert d["nonfinite"] == 0
