@@ -148,7 +148,8 @@ typedef struct {
 /* Validates *params, derives the relaxation times (Sec. 3: tau_f = nu/cs^2
  * + 1/2 per node, tau_g from Eq. (21), tau_a from Eq. (26), tau_s from
  * Eq. (27)) and allocates the device state on the current CUDA device.
- * Errors: LBM_ERR_ARG (null, grid < 2, unpaired periodic axis),
+ * Errors: LBM_ERR_ARG (null, grid < 2, unpaired periodic axis, a grid whose 27
+ * population planes would pass 2^31 elements: about 79 million nodes),
  * LBM_ERR_PARAM (non-positive property, relaxation time <= 1/2 for any
  * phase), LBM_ERR_OOM, LBM_ERR_CUDA.  On success *out owns the memory until
  * lbm_destroy. */
