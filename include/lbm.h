@@ -373,14 +373,15 @@ int lbm_adjoint_freezing(lbm_ctx* ctx, int64_t nsteps, int every, int observable
                          int index, double* value, double* grad, void* stream);
 
 /* Reverse mode (adjoint) of the whole coupled step: as lbm_adjoint_freezing
- * for a context with precision LBM_FP64, all three lattices, no cold mask,
- * readings == 0 and sigma > 0, with the flow lattice moving -- the velocity
+ * for a context with precision LBM_FP64, all three lattices, readings == 0
+ * and sigma > 0 (a cold mask allowed), with the flow lattice moving -- the velocity
  * of Eq. (17a,b) with the surface-tension, body and penalty forces, the
  * source S and the modified force of Eq. (16) (with the lagged pressure
  * gradient), the pressure of Eq. (17c), the flow collision, and phi u and u
  * in the phase and enthalpy equilibria all reversed, with the transposed
- * gradients of phi, rho and the lagged pressure.  grad[0..8]: d/dT_wall[0..3],
- * d/dL, d/dtheta_deg, d/dsigma, d/dgx, d/dgy.  dT0 (host memory for
+ * gradients of phi, rho and the lagged pressure.  grad[0..9]: d/dT_wall[0..3],
+ * d/dL, d/dtheta_deg, d/dsigma, d/dgx, d/dgy, d/dT_cold (the cold-mask
+ * temperature; zero without a mask).  dT0 (host memory for
  * [ny][nx] doubles, or NULL): the gradient with respect to the initial
  * temperature field of lbm_set_geometry, node by node (the call must then
  * start at step 0, else LBM_ERR_STATE).  Other errors as

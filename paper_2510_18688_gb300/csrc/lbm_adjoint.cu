@@ -106,4 +106,11 @@ cudaError_t launch_full_dT0(const FullArgs& a, const double* lam, double* out, c
   return cudaGetLastError();
 }
 
+cudaError_t launch_adjoint_init_fields(const Geom& g, const double* gpop, const double* lag,
+                                       const double* phi0, double* phi, double* fs,
+                                       cudaStream_t s) {
+  lbm_adjoint_init_fields_kernel<<<grid_dims(g), block_dims(), 0, s>>>(g, gpop, lag, phi0, phi, fs);
+  return cudaGetLastError();
+}
+
 }  // namespace lbmk

@@ -896,6 +896,31 @@ cudaError_t launch_frz_mub(const FrzArgs& a, cudaStream_t s);
 cudaError_t launch_frz_step(const FrzArgs& a, cudaStream_t s);
 cudaError_t launch_frz_seed_ff(const FrzArgs& a, cudaStream_t s);
 cudaError_t launch_frz_seed_crossing(const FrzArgs& a, double* phib, cudaStream_t s);
+// phi and fs of a state as lbm_set_geometry built it (for the initial-state
+// terms): phi = sum g (the initial phase equilibrium sums to the input phi)
+// and fs = min(phi0 + w (1 - fl), 1) from the initial lags -- not from the
+// enthalpy inversion, which at a cold-mask node need not give back the input
+// fl.  gpop: the 9 phase planes; out: two planes.
+#ifdef LBM_ADJOINT_KERNELS
+static __global__ void __launch_bounds__(NT) lbm_adjoint_init_fields_kernel(
+    Geom g, const double* __restrict__ gpop, const double* __restrict__ lag,
+    const double* __restrict__ phi0, double* __restrict__ phi, double* __restrict__ fs) {
+  const int x = blockIdx.x * TX + threadIdx.x, y = blockIdx.y * TY + threadIdx.y;
+  if (x >= g.nx || y >= g.ny) return;
+  const int P = (int)g.plane;
+  const int n = y * g.pitch + x;
+  double v[9];
+#pragma unroll
+  for (int i = 0; i < 9; i++) v[i] = gpop[i * P + n];
+  phi[n] = sum_g(v);
+  const double f = phi0[n] + lag[LAG_W * P + n] * (1.0 - lag[LAG_FL * P + n]);
+  fs[n] = f > 1.0 ? 1.0 : f;
+}
+#endif  // LBM_ADJOINT_KERNELS
+
+cudaError_t launch_adjoint_init_fields(const Geom& g, const double* gpop, const double* lag,
+                                       const double* phi0, double* phi, double* fs,
+                                       cudaStream_t s);
 cudaError_t launch_phase_adjoint_fields(const PhaseAdjArgs& a, cudaStream_t s);
 cudaError_t launch_phase_adjoint_seed(const PhaseAdjArgs& a, cudaStream_t s);
 cudaError_t launch_phase_adjoint_step(const PhaseAdjArgs& a, cudaStream_t s);

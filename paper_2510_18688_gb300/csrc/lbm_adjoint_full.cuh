@@ -1,5 +1,5 @@
 // lbm_adjoint_full.cuh -- reverse mode of the whole coupled step (flow,
-// phase field and enthalpy lattices; FP64; no cold mask; readings == 0).
+// phase field and enthalpy lattices; FP64; readings == 0).
 //
 // On top of the freezing coupling of the phase-field and enthalpy adjoint
 // (lbm_adjoint.cuh), the flow lattice moves: the velocity of Eq. (17a,b)
@@ -18,15 +18,18 @@
 // theta and sigma terms; kernel 2 runs the same local reverse again, gathers
 // the neighbours' stencil adjoints in a fixed order and finishes the local
 // chain to this state's populations and lags (fl, w, p, phi u, Q).
+// A cold-mask node reads its enthalpy populations as the equilibrium at
+// T_cold (R-BC) built from its lagged w, so their adjoint goes to the lagged
+// w, to T_cold and to L instead of to the stored populations.
 // Accumulator planes: d/dT_wall[0..3], d/dL, d/dtheta_deg, d/dsigma, d/dgx,
-// d/dgy.
+// d/dgy, d/dT_cold.
 #pragma once
 
 #include "lbm_adjoint.cuh"
 
 namespace lbmk {
 
-constexpr int FULL_NACC = 9;
+constexpr int FULL_NACC = 10;
 
 struct FullArgs {
   Geom g;
@@ -34,6 +37,8 @@ struct FullArgs {
   const double* __restrict__ pop;     // 27 planes of the forward state: f, g, h
   const double* __restrict__ lag;     // NLAG planes of the forward state
   const double* __restrict__ phi0;
+  const unsigned char* __restrict__ mask;  // cold mask (has_mask) or null
+  int has_mask;
   double* __restrict__ phi;           // fields of the forward state
   double* __restrict__ fs;
   double* __restrict__ rho;
@@ -50,6 +55,29 @@ struct FullArgs {
   double* __restrict__ out;
 };
 
+// The phase and enthalpy population sums of node n as the step reads them
+// (the enthalpy populations of a cold-mask node: the mask equilibrium); h
+// (or null) receives the enthalpy populations.
+__device__ __forceinline__ void full_sums(const FullArgs& a, int n, double* sg, double* sh,
+                                          double* h) {
+  const int P = (int)a.g.plane;
+  double v[9];
+#pragma unroll
+  for (int i = 0; i < 9; i++) v[i] = a.pop[(9 + i) * P + n];
+  *sg = sum_g(v);
+  if (a.has_mask && a.mask[n]) {
+    cold_mask_h(a.c, a.lag[LAG_W * P + n], a.phi0[n], v);
+  } else {
+#pragma unroll
+    for (int i = 0; i < 9; i++) v[i] = a.pop[(18 + i) * P + n];
+  }
+  *sh = sum_h(v);
+  if (h) {
+#pragma unroll
+    for (int i = 0; i < 9; i++) h[i] = v[i];
+  }
+}
+
 // Forward values of one node that its reverse needs.
 struct FullNode {
   FrzNode q;
@@ -64,13 +92,8 @@ __device__ __forceinline__ FullNode full_forward(const FullArgs& a, int x, int y
   const Coef<double>& c = a.c;
   const int P = (int)g.plane;
   FullNode r;
-  double v[9];
-#pragma unroll
-  for (int i = 0; i < 9; i++) v[i] = a.pop[(9 + i) * P + n];
-  const double sg = sum_g(v);
-#pragma unroll
-  for (int i = 0; i < 9; i++) r.h[i] = a.pop[(18 + i) * P + n];
-  const double sh = sum_h(r.h);
+  double sg, sh;
+  full_sums(a, n, &sg, &sh, r.h);
 #pragma unroll
   for (int i = 0; i < 9; i++) r.f[i] = a.pop[i * P + n];
   const double phi0 = a.phi0[n];
@@ -396,13 +419,8 @@ static __global__ void __launch_bounds__(NT) lbm_full_fields_kernel(const FullAr
   if (x >= g.nx || y >= g.ny) return;
   const int P = (int)g.plane;
   const int n = y * g.pitch + x;
-  double v[9];
-#pragma unroll
-  for (int i = 0; i < 9; i++) v[i] = a.pop[(9 + i) * P + n];
-  const double sg = sum_g(v);
-#pragma unroll
-  for (int i = 0; i < 9; i++) v[i] = a.pop[(18 + i) * P + n];
-  const double sh = sum_h(v);
+  double sg, sh;
+  full_sums(a, n, &sg, &sh, nullptr);
   const FrzNode q = frz_forward(a.c, sg, sh, a.lag[LAG_FL * P + n], a.lag[LAG_W * P + n],
                                 a.lag[LAG_Q * P + n], a.phi0[n]);
   a.phi[n] = q.phi;
@@ -538,12 +556,40 @@ static __global__ void __launch_bounds__(NT) lbm_full_k2_kernel(const FullArgs a
     ellb += -flb * q.rhoH / (q.ell * q.ell);
   }
   wpb += ellb * c.rho_l * c.latent;
-  const double dL = ellb * wp * c.rho_l;
+  double dL = ellb * wp * c.rho_l, dTc = 0.0;
+  const bool masked = a.has_mask && a.mask[n];
+  if (masked) {
+    // the enthalpy populations read here are h_eq(T_cold, u = 0) at w_prev:
+    // h_0 = rho H - rr T + w_0 rr T, h_i = w_i rr T with
+    // rho H = cap(w_prev) T + w_prev rho_l L fl_c
+    const double Tc = c.T_cold;
+    const double flc = Tc < 0.0 ? 0.0 : 1.0;
+    double fsf = phi0 + wp;
+    const bool fsf_cl = fsf > 1.0;
+    if (fsf_cl) fsf = 1.0;
+    double cf, cw, cap, dcapw;
+    if (Tc < 0.0) {
+      cap = heat_cap(c, fsf, wp);
+      dcap(c, fsf, wp, &cf, &cw);
+      dcapw = (fsf_cl ? 0.0 : cf) + cw;
+    } else {
+      cap = heat_cap(c, phi0, wp);
+      dcap(c, phi0, wp, &cf, &cw);
+      dcapw = cw;
+    }
+    double sb = 0.0;  // sum over i>0 of the adjoints times w_i
+#pragma unroll
+    for (int i = 1; i < 9; i++) sb += (d.hb[i] + rhoHb) * qw<double>(i);
+    const double h0b = d.hb[0] + rhoHb;
+    wpb += h0b * (dcapw * Tc + c.rho_l * c.latent * flc);
+    dTc = h0b * (cap - c.rr + qw<double>(0) * c.rr) + sb * c.rr;
+    dL += h0b * wp * c.rho_l * flc;
+  }
 #pragma unroll
   for (int i = 0; i < 9; i++) {
     a.lam_out[i * P + n] = d.fb[i];
     a.lam_out[(9 + i) * P + n] = d.gbd[i] + sgb;
-    a.lam_out[(18 + i) * P + n] = d.hb[i] + rhoHb;
+    a.lam_out[(18 + i) * P + n] = masked ? 0.0 : d.hb[i] + rhoHb;
   }
   a.llag_out[LAG_FL * P + n] = flpb;
   a.llag_out[LAG_W * P + n] = wpb;
@@ -556,6 +602,7 @@ static __global__ void __launch_bounds__(NT) lbm_full_k2_kernel(const FullArgs a
   a.acc[4 * P + n] += dL;
   a.acc[7 * P + n] += d.dg[0];
   a.acc[8 * P + n] += d.dg[1];
+  a.acc[9 * P + n] += dTc;
 }
 #endif  // LBM_ADJOINT_KERNELS
 
@@ -569,13 +616,8 @@ static __global__ void __launch_bounds__(NT) lbm_full_seed_ff_kernel(const FullA
   if (x >= g.nx || y >= g.ny) return;
   const int P = (int)g.plane;
   const int n = y * g.pitch + x;
-  double v[9];
-#pragma unroll
-  for (int i = 0; i < 9; i++) v[i] = a.pop[(9 + i) * P + n];
-  const double sg = sum_g(v);
-#pragma unroll
-  for (int i = 0; i < 9; i++) v[i] = a.pop[(18 + i) * P + n];
-  const double sh = sum_h(v);
+  double sg, sh;
+  full_sums(a, n, &sg, &sh, nullptr);
   const FrzNode q = frz_forward(a.c, sg, sh, a.lag[LAG_FL * P + n], a.lag[LAG_W * P + n],
                                 a.lag[LAG_Q * P + n], a.phi0[n]);
   llag[LAG_FL * P + n] = -q.w * a.inv_sum_w;
@@ -624,13 +666,8 @@ static __global__ void __launch_bounds__(NT) lbm_full_dT0_kernel(const FullArgs 
   if (x >= g.nx || y >= g.ny) return;
   const int P = (int)g.plane;
   const int n = y * g.pitch + x;
-  double v[9];
-#pragma unroll
-  for (int i = 0; i < 9; i++) v[i] = a.pop[(9 + i) * P + n];
-  const double sg = sum_g(v);
-#pragma unroll
-  for (int i = 0; i < 9; i++) v[i] = a.pop[(18 + i) * P + n];
-  const double sh = sum_h(v);
+  double sg, sh;
+  full_sums(a, n, &sg, &sh, nullptr);
   const FrzNode q = frz_forward(c, sg, sh, a.lag[LAG_FL * P + n], a.lag[LAG_W * P + n],
                                 a.lag[LAG_Q * P + n], a.phi0[n]);
   const double cap = q.T < 0.0 ? q.Cm : q.Cp;

@@ -1182,8 +1182,8 @@ extern "C" int lbm_adjoint_freezing(lbm_ctx* c, int64_t nsteps, int every, int o
     }
   }
   // a run from set_geometry's state: the initial populations' dependence on
-  // L (rest enthalpy population) and on theta and sigma (phase equilibrium);
-  // phi and fs of that state are still in the field planes
+  // L (rest enthalpy population) and on theta and sigma (phase equilibrium,
+  // with the phi and fs set_geometry used, rebuilt from checkpoint 0)
   if (e == cudaSuccess && st == LBM_OK && step0 == 0) {
     lbmk::AdjArgs ha;
     std::memset(&ha, 0, sizeof(ha));
@@ -1193,6 +1193,8 @@ extern "C" int lbm_adjoint_freezing(lbm_ctx* c, int64_t nsteps, int every, int o
     ha.lag = ck + pN;
     ha.acc = acc;
     e = lbmk::launch_adjoint_init(ha, s);
+    if (e == cudaSuccess)
+      e = lbmk::launch_adjoint_init_fields(c->g, ck, ck + pN, (const double*)c->phi0, phi, fsp, s);
     lbmk::PhaseAdjArgs pa;
     std::memset(&pa, 0, sizeof(pa));
     pa.g = c->g;
@@ -1247,10 +1249,10 @@ extern "C" int lbm_adjoint_coupled(lbm_ctx* c, int64_t nsteps, int every, int ob
   if (dT0 && c->step != 0)
     return fail(c, LBM_ERR_STATE, "the initial-temperature gradient needs a run from lbm_set_geometry%s");
   if (c->p.precision != LBM_FP64 || c->p.lattices != (LBM_LAT_FLOW | LBM_LAT_PHASE | LBM_LAT_HEAT) ||
-      c->g.has_mask || c->p.readings != 0 || !(c->p.sigma > 0.0))
+      c->p.readings != 0 || !(c->p.sigma > 0.0))
     return fail(c, LBM_ERR_UNSUPPORTED,
-                "the coupled-step adjoint covers FP64 contexts with all three lattices, no cold "
-                "mask, readings == 0 and sigma > 0%s");
+                "the coupled-step adjoint covers FP64 contexts with all three lattices, "
+                "readings == 0 and sigma > 0%s");
   cudaStream_t s = (cudaStream_t)stream;
   const size_t P = (size_t)c->g.plane;
   const size_t pN = 27 * P, lN = lbmk::NLAG * P, stN = pN + lN;
@@ -1318,6 +1320,8 @@ extern "C" int lbm_adjoint_coupled(lbm_ctx* c, int64_t nsteps, int every, int ob
   a.g = c->g;
   a.c = c->cd;
   a.phi0 = (const double*)c->phi0;
+  a.mask = (const unsigned char*)c->mask;
+  a.has_mask = c->g.has_mask;
   a.phi = fld;
   a.fs = fld + P;
   a.rho = fld + 2 * P;
@@ -1384,6 +1388,9 @@ extern "C" int lbm_adjoint_coupled(lbm_ctx* c, int64_t nsteps, int every, int ob
     ha.lag = ck + pN;
     ha.acc = acc;
     e = lbmk::launch_adjoint_init(ha, s);
+    if (e == cudaSuccess)
+      e = lbmk::launch_adjoint_init_fields(c->g, ck + 9 * P, ck + pN, (const double*)c->phi0, fld,
+                                           fld + P, s);
     lbmk::PhaseAdjArgs pa;
     std::memset(&pa, 0, sizeof(pa));
     pa.g = c->g;

@@ -276,11 +276,11 @@ def lbm_adjoint_freezing(ctx, nsteps: int, every: int, observable: int, axis: in
 def lbm_adjoint_coupled(ctx, nsteps: int, every: int, observable: int, axis: int = 0,
                         index: int = 0, dT0=None, stream=None):
     """(observable after nsteps steps of the whole coupled step and its
-    gradient w.r.t. (T_wall[0..3], latent, theta_deg, sigma, gx, gy)); with
-    dT0 (a float64 [ny, nx] numpy array) also the gradient w.r.t. the
-    initial temperature field; see include/lbm.h."""
+    gradient w.r.t. (T_wall[0..3], latent, theta_deg, sigma, gx, gy,
+    T_cold)); with dT0 (a float64 [ny, nx] numpy array) also the gradient
+    w.r.t. the initial temperature field; see include/lbm.h."""
     val = ctypes.c_double()
-    grad = (ctypes.c_double * 9)()
+    grad = (ctypes.c_double * 10)()
     dptr = None if dT0 is None else dT0.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
     _check(ctx, load().lbm_adjoint_coupled(ctx, int(nsteps), int(every), int(observable),
                                            int(axis), int(index), ctypes.byref(val), grad,
@@ -480,7 +480,7 @@ class Solver:
     def adjoint_coupled(self, nsteps: int, observable: int = 0, axis: int = 0, index: int = 0,
                         every: int = 64, initial_T: bool = False):
         """Advance nsteps and return (observable, gradient w.r.t. (T_wall[0..3],
-        latent, theta_deg, sigma, gx, gy)) by reverse mode of the whole coupled
+        latent, theta_deg, sigma, gx, gy, T_cold)) by reverse mode of the whole coupled
         step (see lbm_adjoint_coupled); with initial_T also the [ny, nx]
         gradient w.r.t. the initial temperature field, as a third item."""
         if not initial_T:

@@ -275,7 +275,8 @@ class AdjointFreezing:
 
 def _run_adjoint_coupled(q, cfg, arrays, steps, observable, axis, index, every):
     c = dict(cfg, T_wall=tuple(float(v) for v in q[:4]), latent=float(q[4]),
-             theta_deg=float(q[5]), sigma=float(q[6]), gx=float(q[7]), gy=float(q[8]))
+             theta_deg=float(q[5]), sigma=float(q[6]), gx=float(q[7]), gy=float(q[8]),
+             T_cold=float(q[9]))
     s = lbm.Solver(c, precision="fp64").set_geometry(arrays)
     try:
         return s.adjoint_coupled(steps, observable, axis, index, every)
@@ -288,8 +289,8 @@ class AdjointCoupled:
     every)``: the frozen fraction (observable 0) or an interface crossing
     (observable 1) after `steps` steps of the whole coupled step (see
     lbm_adjoint_coupled) as a differentiable function of
-    q = (T_wall[0..3], latent, theta_deg, sigma, gx, gy), from the initial
-    fields."""
+    q = (T_wall[0..3], latent, theta_deg, sigma, gx, gy, T_cold), from the
+    initial fields."""
 
     _fn = None
 

@@ -566,20 +566,22 @@ def test_coupled_adjoint_behind_autograd(env):
     assert q.grad.tolist() == [2.0 * v for v in grad]
 
 
-def _full_state(seed, n=(40, 24), g=(2e-5, -3e-5)):
-    """A random three-phase state with all three lattices and no cold mask;
-    a body force strong enough that the flow carries the interfaces."""
+def _full_state(seed, n=(40, 24), g=(2e-5, -3e-5), mask=False):
+    """A random three-phase state with all three lattices (with or without
+    its cold mask); a body force strong enough that the flow carries the
+    interfaces."""
     cfg, arr = W.random_state(*n, seed=seed, lattices=W.FLOW | W.PHASE | W.HEAT)
-    return dict(cfg, gx=g[0], gy=g[1]), {k: v for k, v in arr.items() if k != "mask"}
+    return dict(cfg, gx=g[0], gy=g[1]), {k: v for k, v in arr.items() if mask or k != "mask"}
 
 
-@pytest.mark.parametrize("seed", [1, 3])
-def test_full_adjoint_equals_the_tangent(env, seed):
-    """The reverse sweep of the whole coupled step (moving fluid) against
-    the forward-mode tangent (wall temperatures, L, theta) and central
+@pytest.mark.parametrize("seed,mask", [(1, False), (3, False), (3, True), (0, True)])
+def test_full_adjoint_equals_the_tangent(env, seed, mask):
+    """The reverse sweep of the whole coupled step (moving fluid; with and
+    without a cold mask) against the forward-mode tangent (wall
+    temperatures, L, theta, the cold-mask temperature) and central
     differences (sigma, the body force)."""
     O, lbm, S, torch = env
-    cfg, arr = _full_state(seed)
+    cfg, arr = _full_state(seed, mask=mask)
     steps = 150
     plain = lbm.Solver(cfg, precision="fp64").set_geometry(arr).step(steps)
     assert np.abs(plain.fields(("ux",))["ux"]).max() > 1e-5
@@ -592,6 +594,8 @@ def test_full_adjoint_equals_the_tangent(env, seed):
         s.close()
     rows = []
     dirs = [("T_wall", k) for k in range(4) if cfg["bc"][k] == "dirichlet"] + [("latent", 4), ("theta_deg", 5)]
+    if mask:
+        dirs.append(("T_cold", 9))
     for name, k in dirs:
         t = ({"T_wall": [1.0 if j == k else 0.0 for j in range(4)]} if name == "T_wall" else {name: 1.0})
         ts = lbm.Solver(cfg, precision="tangent", tangent=t).set_geometry(arr).step(steps)
@@ -643,9 +647,8 @@ def test_full_adjoint_checkpoints_and_rejections(env):
     plain.close()
     for k in FIELDS:
         assert np.array_equal(f_adj[k], f_plain[k]), k
-    masked = W.random_state(40, 24, seed=3)
     for c, a, prec in ((cfg, arr, "fp32"), (dict(cfg, lattices=6), arr, "fp64"),
-                       (masked[0], masked[1], "fp64"), (dict(cfg, readings=1), arr, "fp64")):
+                       (dict(cfg, readings=1), arr, "fp64")):
         s = lbm.Solver(c, precision=prec).set_geometry(a)
         with pytest.raises(lbm.LbmError) as e:
             s.adjoint_coupled(5, 0, every=5)
