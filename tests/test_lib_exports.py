@@ -107,11 +107,13 @@ def test_3d_create_rejects_invalid_parameters_without_gpu(lib):
 
 
 def test_3d_create_rejects_grids_beyond_31_bit_offsets(lib):
-    """57 population planes must fit 31-bit offsets; the check runs before any
-    device allocation."""
+    """Node offsets within one plane are 32-bit (planes of up to 2^31
+    elements; the population planes themselves are addressed with 64-bit
+    offsets once they pass 2^31 together); the check runs before any device
+    allocation."""
     from paper_2510_18688_gb300 import lbm, workloads as W
     cfg, _ = W.random_state3(8, 6, 4, seed=2)
-    p = lbm.make_params3(dict(cfg, nx=1024, ny=1024, nz=40))  # 57 x 41.9 M > 2^31
+    p = lbm.make_params3(dict(cfg, nx=2048, ny=1024, nz=1025))  # 2.15 G nodes per plane
     h = ctypes.c_void_p()
     assert lib.lbm3_create(ctypes.byref(p), ctypes.byref(h)) == -1
     assert not h.value
