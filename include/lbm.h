@@ -350,7 +350,7 @@ int lbm_adjoint_crossing(lbm_ctx* ctx, int64_t nsteps, int every, int axis, int 
 
 /* Reverse mode (adjoint) of the coupled freezing step with the fluid at
  * rest: for a context with precision LBM_FP64, lattices == LBM_LAT_PHASE |
- * LBM_LAT_HEAT, no cold mask and sigma > 0, the phase field and the enthalpy
+ * LBM_LAT_HEAT and sigma > 0 (a cold mask allowed), the phase field and the enthalpy
  * lattice coupled as in the full step (the mass source of Eq. (1) in the
  * order parameter, Eq. (22), and in the phase source, Eq. (20); w and
  * fs = phi0 + w (1 - fl) in the properties of Eq. (10) and in Eq. (6); the
@@ -358,9 +358,10 @@ int lbm_adjoint_crossing(lbm_ctx* ctx, int64_t nsteps, int every, int axis, int 
  * as lbm_step would and returns in *value the observable of the final
  * state -- observable 0: the frozen fraction FF = sum w (1 - fl) / sum w;
  * observable 1: the last phi = 0 crossing along grid line (axis, index), as
- * out[0] of lbm_read_crossings -- and in grad[0..6] its derivatives with
+ * out[0] of lbm_read_crossings -- and in grad[0..7] its derivatives with
  * respect to T_wall[0..3] (zero where bc[k] is not LBM_BC_DIRICHLET), the
- * latent heat L, the contact angle theta (degrees) and sigma.  The state at
+ * latent heat L, the contact angle theta (degrees), sigma and the cold-mask
+ * temperature T_cold (zero without a mask).  The state at
  * the start of the call is held fixed, except that a call right after
  * lbm_set_geometry (step 0) includes the initial populations' dependence on
  * L, theta and sigma.  Checkpoints and kinks as in

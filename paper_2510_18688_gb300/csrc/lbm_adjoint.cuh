@@ -520,11 +520,13 @@ static __global__ void __launch_bounds__(NT) lbm_phase_init_kernel(const PhaseAd
 // Accumulator planes: d/dT_wall[0..3], d/dL, d/dtheta_deg, d/dsigma.
 // ---------------------------------------------------------------------------
 
-constexpr int FRZ_NACC = 7;
+constexpr int FRZ_NACC = 8;  // ... and d/dT_cold (cold mask)
 
 struct FrzArgs {
   Geom g;
   Coef<double> c;
+  const unsigned char* __restrict__ mask;  // cold mask (has_mask) or null
+  int has_mask;
   const double* __restrict__ pop;     // 18 planes of the forward state: g (0-8), h (9-17)
   const double* __restrict__ lag;     // NLAG planes of the forward state
   const double* __restrict__ phi0;
@@ -611,8 +613,13 @@ __device__ __forceinline__ FrzNode frz_node(const FrzArgs& a, int n) {
 #pragma unroll
   for (int i = 0; i < 9; i++) v[i] = a.pop[i * P + n];
   const double sg = sum_g(v);
+  if (a.has_mask && a.mask[n]) {
+    // a cold-mask node reads h_eq(T_cold, u = 0) at its lagged w
+    cold_mask_h(a.c, a.lag[LAG_W * P + n], a.phi0[n], v);
+  } else {
 #pragma unroll
-  for (int i = 0; i < 9; i++) v[i] = a.pop[(9 + i) * P + n];
+    for (int i = 0; i < 9; i++) v[i] = a.pop[(9 + i) * P + n];
+  }
   const double sh = sum_h(v);
   return frz_forward(a.c, sg, sh, a.lag[LAG_FL * P + n], a.lag[LAG_W * P + n],
                      a.lag[LAG_Q * P + n], a.phi0[n]);
@@ -703,9 +710,14 @@ static __global__ void __launch_bounds__(NT) lbm_frz_step_kernel(const FrzArgs a
   const FrzNode q = frz_node(a, n);
   const double phi0 = a.phi0[n];
   const double wp = a.lag[LAG_W * P + n], flp = a.lag[LAG_FL * P + n];
+  const bool masked = a.has_mask && a.mask[n];
   double h[9];
+  if (masked) {
+    cold_mask_h(c, wp, phi0, h);
+  } else {
 #pragma unroll
-  for (int i = 0; i < 9; i++) h[i] = a.pop[(9 + i) * P + n];
+    for (int i = 0; i < 9; i++) h[i] = a.pop[(9 + i) * P + n];
+  }
   const double rrT = c.rr * q.T;
 
   // enthalpy TRT collision in reverse (u = 0)
@@ -835,12 +847,38 @@ static __global__ void __launch_bounds__(NT) lbm_frz_step_kernel(const FrzArgs a
     ellb += -flb * q.rhoH / (q.ell * q.ell);
   }
   wpb += ellb * c.rho_l * c.latent;
-  const double dL = ellb * wp * c.rho_l;
+  double dL = ellb * wp * c.rho_l, dTc = 0.0;
+  if (masked) {
+    // the populations read here are h_eq(T_cold, u = 0) at w_prev: their
+    // adjoint goes to w_prev, T_cold and L instead of the stored ones
+    const double Tc = c.T_cold;
+    const double flc = Tc < 0.0 ? 0.0 : 1.0;
+    double fsf = phi0 + wp;
+    const bool fsf_cl = fsf > 1.0;
+    if (fsf_cl) fsf = 1.0;
+    double cf, cw, cap, dcapw;
+    if (Tc < 0.0) {
+      cap = heat_cap(c, fsf, wp);
+      dcap(c, fsf, wp, &cf, &cw);
+      dcapw = (fsf_cl ? 0.0 : cf) + cw;
+    } else {
+      cap = heat_cap(c, phi0, wp);
+      dcap(c, phi0, wp, &cf, &cw);
+      dcapw = cw;
+    }
+    double sb = 0.0;
+#pragma unroll
+    for (int i = 1; i < 9; i++) sb += (hb[i] + rhoHb) * qw<double>(i);
+    const double h0b = hb[0] + rhoHb;
+    wpb += h0b * (dcapw * Tc + c.rho_l * c.latent * flc);
+    dTc = h0b * (cap - c.rr + qw<double>(0) * c.rr) + sb * c.rr;
+    dL += h0b * wp * c.rho_l * flc;
+  }
   const double omg = 1.0 - itg;
 #pragma unroll
   for (int i = 0; i < 9; i++) {
     a.lam_out[i * P + n] = omg * gb[i] + sgb;
-    a.lam_out[(9 + i) * P + n] = hb[i] + rhoHb;
+    a.lam_out[(9 + i) * P + n] = masked ? 0.0 : hb[i] + rhoHb;
   }
   a.lfl_out[n] = flpb;
   a.lw_out[n] = wpb;
@@ -848,6 +886,7 @@ static __global__ void __launch_bounds__(NT) lbm_frz_step_kernel(const FrzArgs a
 #pragma unroll
   for (int k = 0; k < 4; k++) a.acc[k * P + n] += dTw[k];
   a.acc[4 * P + n] += dL;
+  a.acc[7 * P + n] += dTc;
 }
 #endif  // LBM_ADJOINT_KERNELS
 

@@ -1037,10 +1037,10 @@ extern "C" int lbm_adjoint_freezing(lbm_ctx* c, int64_t nsteps, int every, int o
     return fail(c, LBM_ERR_ARG, "axis must be 0 or 1 and index a line of the grid%s");
   if (!c->have_geometry) return fail(c, LBM_ERR_STATE, "adjoint before lbm_set_geometry%s");
   if (c->p.precision != LBM_FP64 || c->p.lattices != (LBM_LAT_PHASE | LBM_LAT_HEAT) ||
-      c->g.has_mask || !(c->p.sigma > 0.0))
+      !(c->p.sigma > 0.0))
     return fail(c, LBM_ERR_UNSUPPORTED,
                 "the coupled adjoint covers FP64 contexts with the phase-field and enthalpy "
-                "lattices (no flow lattice), no cold mask and sigma > 0%s");
+                "lattices (no flow lattice) and sigma > 0%s");
   cudaStream_t s = (cudaStream_t)stream;
   const size_t P = (size_t)c->g.plane;
   const size_t pN = 18 * P, lN = lbmk::NLAG * P, stN = pN + lN;
@@ -1113,6 +1113,8 @@ extern "C" int lbm_adjoint_freezing(lbm_ctx* c, int64_t nsteps, int every, int o
   std::memset(&a, 0, sizeof(a));
   a.g = c->g;
   a.c = c->cd;
+  a.mask = (const unsigned char*)c->mask;
+  a.has_mask = c->g.has_mask;
   a.phi0 = (const double*)c->phi0;
   a.phi = phi;
   a.fs = fsp;

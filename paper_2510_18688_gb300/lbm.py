@@ -264,9 +264,9 @@ def lbm_adjoint_freezing(ctx, nsteps: int, every: int, observable: int, axis: in
                          index: int = 0, stream=None):
     """(observable after nsteps steps -- 0: frozen fraction, 1: the phi = 0
     crossing along (axis, index) -- and its gradient w.r.t. (T_wall[0..3],
-    latent, theta_deg, sigma)); see include/lbm.h."""
+    latent, theta_deg, sigma, T_cold)); see include/lbm.h."""
     val = ctypes.c_double()
-    grad = (ctypes.c_double * 7)()
+    grad = (ctypes.c_double * 8)()
     _check(ctx, load().lbm_adjoint_freezing(ctx, int(nsteps), int(every), int(observable),
                                             int(axis), int(index), ctypes.byref(val), grad,
                                             stream), "lbm_adjoint_freezing")
@@ -473,7 +473,7 @@ class Solver:
     def adjoint_freezing(self, nsteps: int, observable: int = 0, axis: int = 0, index: int = 0,
                          every: int = 64):
         """Advance nsteps and return (observable, gradient w.r.t. (T_wall[0..3],
-        latent, theta_deg, sigma)) by reverse mode of the coupled phase-field
+        latent, theta_deg, sigma, T_cold)) by reverse mode of the coupled phase-field
         and enthalpy step (see lbm_adjoint_freezing)."""
         return lbm_adjoint_freezing(self.ctx, nsteps, every, observable, axis, index, _stream())
 

@@ -248,7 +248,7 @@ class AdjointCrossing:
 
 def _run_adjoint_freezing(q, cfg, arrays, steps, observable, axis, index, every):
     c = dict(cfg, T_wall=tuple(float(v) for v in q[:4]), latent=float(q[4]),
-             theta_deg=float(q[5]), sigma=float(q[6]))
+             theta_deg=float(q[5]), sigma=float(q[6]), T_cold=float(q[7]))
     s = lbm.Solver(c, precision="fp64").set_geometry(arrays)
     try:
         return s.adjoint_freezing(steps, observable, axis, index, every)
@@ -261,8 +261,8 @@ class AdjointFreezing:
     every)``: the frozen fraction (observable 0) or an interface crossing
     (observable 1, along grid line (axis, index)) after `steps` steps of the
     coupled phase-field and enthalpy step (see lbm_adjoint_freezing), as a
-    differentiable function of q = (T_wall[0..3], latent, theta_deg, sigma),
-    from the initial fields."""
+    differentiable function of q = (T_wall[0..3], latent, theta_deg, sigma,
+    T_cold), from the initial fields."""
 
     _fn = None
 

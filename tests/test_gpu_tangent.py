@@ -447,22 +447,23 @@ def test_adjoints_behind_autograd(env):
     assert abs(float(qh.grad[0]) - tan) <= 1e-9 * abs(tan)
 
 
-def _frz_state(seed, n=(40, 24)):
+def _frz_state(seed, n=(40, 24), mask=False):
     """A random three-phase state with the phase field and the enthalpy
-    lattice only (fluid at rest), without cold mask: ice, drops, a mushy
-    band and walls of every kind, so freezing couples the two lattices."""
+    lattice only (fluid at rest), with or without its cold mask: ice, drops,
+    a mushy band and walls of every kind, so freezing couples the two
+    lattices."""
     cfg, arr = W.random_state(*n, seed=seed, lattices=W.PHASE | W.HEAT)
-    return cfg, {k: v for k, v in arr.items() if k != "mask"}
+    return cfg, {k: v for k, v in arr.items() if mask or k != "mask"}
 
 
-@pytest.mark.parametrize("seed", [1, 3, 4])
-def test_coupled_adjoint_equals_the_tangent(env, seed):
+@pytest.mark.parametrize("seed,mask", [(1, False), (3, False), (4, False), (3, True)])
+def test_coupled_adjoint_equals_the_tangent(env, seed, mask):
     """The reverse sweep of the coupled phase-field + enthalpy step gives the
     derivatives of the frozen fraction and of an interface crossing with
     respect to the wall temperatures, L, theta (equal to the forward-mode
     tangent of the same steps) and sigma (central differences)."""
     O, lbm, S, torch = env
-    cfg, arr = _frz_state(seed)
+    cfg, arr = _frz_state(seed, mask=mask)
     steps = 200
     plain = lbm.Solver(cfg, precision="fp64").set_geometry(arr).step(steps)
     col = next(i for i in range(cfg["nx"]) if np.isfinite(plain.crossings(1, i)[0]))
@@ -473,6 +474,8 @@ def test_coupled_adjoint_equals_the_tangent(env, seed):
         res[obs] = s.adjoint_freezing(steps, obs, 1, col, every=37)
         s.close()
     dirs = [("T_wall", k) for k in range(4) if cfg["bc"][k] == "dirichlet"] + [("latent", 4), ("theta_deg", 5)]
+    if mask:
+        dirs.append(("T_cold", 7))
     rows = []
     for name, k in dirs:
         t = ({"T_wall": [1.0 if j == k else 0.0 for j in range(4)]} if name == "T_wall" else {name: 1.0})
@@ -536,9 +539,8 @@ def test_coupled_adjoint_checkpoints_and_rejections(env):
     plain.close()
     for k in FIELDS:
         assert np.array_equal(f_adj[k], f_plain[k]), k
-    masked = W.random_state(40, 24, seed=3, lattices=W.PHASE | W.HEAT)
     for c, a, prec in ((cfg, arr, "fp32"), (dict(cfg, lattices=7), arr, "fp64"),
-                       (masked[0], masked[1], "fp64"), (dict(cfg, sigma=0.0), arr, "fp64")):
+                       (dict(cfg, sigma=0.0), arr, "fp64")):
         s = lbm.Solver(c, precision=prec).set_geometry(a)
         with pytest.raises(lbm.LbmError) as e:
             s.adjoint_freezing(5, 0, every=5)
@@ -555,8 +557,8 @@ def test_coupled_adjoint_checkpoints_and_rejections(env):
 def test_coupled_adjoint_behind_autograd(env):
     O, lbm, S, torch = env
     cfg, arr = _frz_state(3)
-    q = torch.tensor(list(cfg["T_wall"]) + [cfg["latent"], cfg["theta_deg"], cfg["sigma"]],
-                     dtype=torch.float64, requires_grad=True)
+    q = torch.tensor(list(cfg["T_wall"]) + [cfg["latent"], cfg["theta_deg"], cfg["sigma"],
+                                            cfg["T_cold"]], dtype=torch.float64, requires_grad=True)
     y = S.AdjointFreezing.apply(q, cfg, arr, 80, 0, 0, 0, 40)
     (2.0 * y).backward()
     s = lbm.Solver(cfg, precision="fp64").set_geometry(arr)
