@@ -293,15 +293,16 @@ void lbm_batch_destroy(lbm_batch* batch);
 void lbm_debug_fail_allocation(int after);
 
 /* Reverse mode (adjoint) of the enthalpy-lattice step, Eqs. (8), (23)-(28)
- * with the fluid at rest: for a context with precision LBM_FP64, no cold
- * mask, and lattices == LBM_LAT_HEAT, or LBM_LAT_FLOW | LBM_LAT_HEAT with
+ * with the fluid at rest: for a context with precision LBM_FP64 (a cold mask
+ * allowed) and lattices == LBM_LAT_HEAT, or LBM_LAT_FLOW | LBM_LAT_HEAT with
  * rho_s == rho_l and no body force (then no mass source and no force ever
  * set the flow in motion, so its populations stay exactly zero: the
  * conduction-freezing column of Sec. 4.1), advances the state by nsteps
  * steps, as lbm_step
  * would, and returns the frozen fraction FF = sum w (1 - fl) / sum w of the
- * final state in *ff and its gradient in grad[0..4]: dFF/dT_wall[k] for the
- * four walls (zero where bc[k] is not LBM_BC_DIRICHLET) and dFF/dlatent,
+ * final state in *ff and its gradient in grad[0..5]: dFF/dT_wall[k] for the
+ * four walls (zero where bc[k] is not LBM_BC_DIRICHLET), dFF/dlatent and
+ * dFF/dT_cold (the cold-mask temperature; zero without a mask),
  * with the state at the start of the call held fixed, except that a call
  * right after lbm_set_geometry (step 0) includes the dependence of the
  * initial enthalpy populations on the latent heat (rho H = C T + w rho_l L

@@ -27,6 +27,8 @@ constexpr int ADJ_NACC = 5;
 struct AdjArgs {
   Geom g;
   Coef<double> c;
+  const unsigned char* __restrict__ mask;  // cold mask (has_mask) or null
+  int has_mask;
   const double* __restrict__ h;      // 9 enthalpy planes of the forward state
   const double* __restrict__ lag;    // NLAG lag planes of the forward state
   const double* __restrict__ phi0;
@@ -110,10 +112,14 @@ static __global__ void __launch_bounds__(NT) lbm_adjoint_seed_kernel(const AdjAr
   const int P = (int)g.plane;
   const int n = y * g.pitch + x;
   double h[9];
-#pragma unroll
-  for (int i = 0; i < 9; i++) h[i] = a.h[i * P + n];
   const double wp = a.lag[LAG_W * P + n], flp = a.lag[LAG_FL * P + n];
   const double Qp = a.lag[LAG_Q * P + n], phi0 = a.phi0[n];
+  if (a.has_mask && a.mask[n]) {
+    cold_mask_h(a.c, wp, phi0, h);
+  } else {
+#pragma unroll
+    for (int i = 0; i < 9; i++) h[i] = a.h[i * P + n];
+  }
   const HeatNode q = heat_forward(a.c, sum_h(h), flp, wp, Qp, phi0);
   double dL = 0.0;
   const double rhoHb = heat_inversion_reverse(a.c, q, wp, 0.0, -wp * a.inv_sum_w, &dL);
@@ -153,12 +159,17 @@ static __global__ void __launch_bounds__(NT) lbm_adjoint_step_kernel(const AdjAr
       }
     }
   }
-  // forward recompute of this node
+  // forward recompute of this node (a cold-mask node reads h_eq(T_cold))
   double h[9];
-#pragma unroll
-  for (int i = 0; i < 9; i++) h[i] = a.h[i * P + n];
   const double wp = a.lag[LAG_W * P + n], flp = a.lag[LAG_FL * P + n];
   const double Qp = a.lag[LAG_Q * P + n], phi0 = a.phi0[n];
+  const bool masked = a.has_mask && a.mask[n];
+  if (masked) {
+    cold_mask_h(c, wp, phi0, h);
+  } else {
+#pragma unroll
+    for (int i = 0; i < 9; i++) h[i] = a.h[i * P + n];
+  }
   const HeatNode q = heat_forward(c, sum_h(h), flp, wp, Qp, phi0);
   const double rrT = c.rr * q.T;
 
@@ -226,13 +237,30 @@ static __global__ void __launch_bounds__(NT) lbm_adjoint_step_kernel(const AdjAr
   flb += -c.one_m_ratio * wp * mdotb;
   double dL = 0.0;
   rhoHb += heat_inversion_reverse(c, q, wp, Tb, flb, &dL);
+  double dTc = 0.0;
+  if (masked) {
+    // h_eq(T_cold, u = 0) at the (static) weight w: h_0 = rho H - rr T +
+    // w_0 rr T, h_i = w_i rr T, rho H = cap T + w rho_l L fl_c
+    const double Tc = c.T_cold;
+    const double flc = Tc < 0.0 ? 0.0 : 1.0;
+    double fsf = phi0 + wp;
+    fsf = fsf > 1.0 ? 1.0 : fsf;
+    const double cap = Tc < 0.0 ? heat_cap(c, fsf, wp) : heat_cap(c, phi0, wp);
+    double sb = 0.0;
 #pragma unroll
-  for (int i = 0; i < 9; i++) a.lam_out[i * P + n] = hb[i] + rhoHb;
+    for (int i = 1; i < 9; i++) sb += (hb[i] + rhoHb) * qw<double>(i);
+    const double h0b = hb[0] + rhoHb;
+    dTc = h0b * (cap - c.rr + qw<double>(0) * c.rr) + sb * c.rr;
+    dL += h0b * wp * c.rho_l * flc;
+  }
+#pragma unroll
+  for (int i = 0; i < 9; i++) a.lam_out[i * P + n] = masked ? 0.0 : hb[i] + rhoHb;
   a.lq_out[n] = 0.5 * rhoHb;
   a.lfl_out[n] = flpb;
 #pragma unroll
   for (int k = 0; k < 4; k++) a.acc[k * P + n] += dTw[k];
   a.acc[(ADJ_NACC - 1) * P + n] += dL;
+  a.acc[ADJ_NACC * P + n] += dTc;  // the caller's accumulator has a plane for T_cold
 }
 #endif  // LBM_ADJOINT_KERNELS
 

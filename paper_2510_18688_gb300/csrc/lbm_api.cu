@@ -735,11 +735,10 @@ extern "C" int lbm_adjoint_frozen_fraction(lbm_ctx* c, int64_t nsteps, int every
   // rest (no mass source: rho_s = rho_l; no body force)
   const bool resting_flow = c->p.lattices == (LBM_LAT_FLOW | LBM_LAT_HEAT) &&
                             c->p.rho_s == c->p.rho_l && c->p.gx == 0.0 && c->p.gy == 0.0;
-  if (c->p.precision != LBM_FP64 || !(c->p.lattices == LBM_LAT_HEAT || resting_flow) ||
-      c->g.has_mask)
+  if (c->p.precision != LBM_FP64 || !(c->p.lattices == LBM_LAT_HEAT || resting_flow))
     return fail(c, LBM_ERR_UNSUPPORTED,
                 "the adjoint covers FP64 contexts with the enthalpy lattice (alone, or with a flow "
-                "lattice that stays at rest: rho_s = rho_l, no body force) and no cold mask%s");
+                "lattice that stays at rest: rho_s = rho_l, no body force)%s");
   cudaStream_t s = (cudaStream_t)stream;
   const size_t P = (size_t)c->g.plane;
   const size_t hN = 9 * P, lN = lbmk::NLAG * P, stN = hN + lN;  // doubles per stored state
@@ -749,8 +748,10 @@ extern "C" int lbm_adjoint_frozen_fraction(lbm_ctx* c, int64_t nsteps, int every
   cudaError_t e = cudaMalloc(&ck, nck * stN * sizeof(double));
   if (e == cudaSuccess) e = cudaMalloc(&seg, seglen * stN * sizeof(double));
   if (e == cudaSuccess) e = cudaMalloc(&lam, 2 * (9 + 2) * P * sizeof(double));
-  if (e == cudaSuccess) e = cudaMalloc(&acc, lbmk::ADJ_NACC * P * sizeof(double));
-  if (e == cudaSuccess) e = cudaMalloc(&dout, lbmk::ADJ_NACC * sizeof(double));
+  // accumulators: T_wall[0..3], L, T_cold, padded for two 5-plane reductions
+  const int nacc = 10;
+  if (e == cudaSuccess) e = cudaMalloc(&acc, nacc * P * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&dout, nacc * sizeof(double));
   if (e == cudaSuccess) e = cudaMalloc(&fin, (27 + lbmk::NLAG) * P * sizeof(double));
   auto release = [&]() {
     for (double* p : {ck, seg, lam, acc, dout, fin})
@@ -794,13 +795,15 @@ extern "C" int lbm_adjoint_frozen_fraction(lbm_ctx* c, int64_t nsteps, int every
     e = cudaMemcpyAsync(fin, c->pop[parN], 27 * P * sizeof(double), cudaMemcpyDeviceToDevice, s);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(fin + 27 * P, c->lag[parN], lN * sizeof(double), cudaMemcpyDeviceToDevice, s);
-  if (e == cudaSuccess) e = cudaMemsetAsync(acc, 0, lbmk::ADJ_NACC * P * sizeof(double), s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(acc, 0, nacc * P * sizeof(double), s);
   // adjoint buffers: two sets of (9 population planes, lag fl, lag Q)
   double* lb[2] = {lam, lam + (9 + 2) * P};
   lbmk::AdjArgs a;
   std::memset(&a, 0, sizeof(a));
   a.g = c->g;
   a.c = c->cd;
+  a.mask = (const unsigned char*)c->mask;
+  a.has_mask = c->g.has_mask;
   a.phi0 = (const double*)c->phi0;
   a.acc = acc;
   a.inv_sum_w = inv_sum_w;
@@ -848,8 +851,10 @@ extern "C" int lbm_adjoint_frozen_fraction(lbm_ctx* c, int64_t nsteps, int every
     a.lag = ck + hN;  // checkpoint 0 holds the initial lags
     e = lbmk::launch_adjoint_init(a, s);
   }
-  double hg[lbmk::ADJ_NACC] = {0};
+  double hg[10] = {0};
   if (e == cudaSuccess && st == LBM_OK) e = lbmk::launch_adjoint_reduce(acc, c->g, dout, s);
+  if (e == cudaSuccess && st == LBM_OK)
+    e = lbmk::launch_adjoint_reduce(acc + 5 * P, c->g, dout + 5, s);
   if (e == cudaSuccess && st == LBM_OK)
     e = cudaMemcpyAsync(hg, dout, sizeof(hg), cudaMemcpyDeviceToHost, s);
   // the context ends at the final state, as after lbm_step(nsteps)
@@ -866,7 +871,7 @@ extern "C" int lbm_adjoint_frozen_fraction(lbm_ctx* c, int64_t nsteps, int every
   if (e != cudaSuccess) return cuda_fail(c, e, "adjoint");
   if (st != LBM_OK) return st;
   *ff_out = ffv;
-  for (int k = 0; k < lbmk::ADJ_NACC; k++) grad[k] = hg[k];
+  for (int k = 0; k < 6; k++) grad[k] = hg[k];
   c->last_stream = s;
   return LBM_OK;
 }

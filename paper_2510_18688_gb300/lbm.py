@@ -241,9 +241,10 @@ def lbm_read_crossings_tangent(ctx, axis: int, index: int, stream=None):
 
 
 def lbm_adjoint_frozen_fraction(ctx, nsteps: int, every: int, stream=None):
-    """(FF after nsteps steps, [dFF/dT_wall[0..3], dFF/dlatent]); see include/lbm.h."""
+    """(FF after nsteps steps, [dFF/dT_wall[0..3], dFF/dlatent, dFF/dT_cold]);
+    see include/lbm.h."""
     ff = ctypes.c_double()
-    grad = (ctypes.c_double * 5)()
+    grad = (ctypes.c_double * 6)()
     _check(ctx, load().lbm_adjoint_frozen_fraction(ctx, int(nsteps), int(every), ctypes.byref(ff),
                                                    grad, stream), "lbm_adjoint_frozen_fraction")
     return ff.value, list(grad)

@@ -198,7 +198,7 @@ def _adjoint_fn(name, run):
 
 
 def _run_adjoint_ff(q, cfg, arrays, steps, every):
-    c = dict(cfg, T_wall=tuple(float(v) for v in q[:4]), latent=float(q[4]))
+    c = dict(cfg, T_wall=tuple(float(v) for v in q[:4]), latent=float(q[4]), T_cold=float(q[5]))
     s = lbm.Solver(c, precision="fp64").set_geometry(arrays)
     try:
         return s.adjoint_frozen_fraction(steps, every)
@@ -219,8 +219,9 @@ class AdjointFrozenFraction:
     """``AdjointFrozenFraction.apply(q, cfg, arrays, steps, every)``: the
     frozen fraction after `steps` steps of an enthalpy-lattice context (see
     lbm_adjoint_frozen_fraction) as a differentiable function of
-    q = (T_wall[0..3], latent) (a float64 tensor of 5), from the initial
-    fields; one forward-and-reverse sweep gives the value and the gradient."""
+    q = (T_wall[0..3], latent, T_cold) (a float64 tensor of 6), from the
+    initial fields; one forward-and-reverse sweep gives the value and the
+    gradient."""
 
     _fn = None
 

@@ -435,7 +435,8 @@ def test_adjoints_behind_autograd(env):
     assert q.grad.tolist() == [3.0 * grad[0], 3.0 * grad[1]]
 
     hc, ha = _heat_column()
-    qh = torch.tensor(list(hc["T_wall"]) + [hc["latent"]], dtype=torch.float64, requires_grad=True)
+    qh = torch.tensor(list(hc["T_wall"]) + [hc["latent"], hc["T_cold"]], dtype=torch.float64,
+                      requires_grad=True)
     ff = S.AdjointFrozenFraction.apply(qh, hc, ha, 300, 100)
     ff.backward()
     t = lbm.Solver(hc, precision="tangent", tangent={"T_wall": [1.0, 0.0, 0.0, 0.0]}).set_geometry(ha).step(300)
@@ -694,3 +695,27 @@ def test_full_adjoint_initial_temperature_gradient(env):
         s.adjoint_coupled(5, 0, every=5, initial_T=True)
     assert e.value.status == -8
     s.close()
+
+
+def test_heat_adjoint_with_cold_mask_equals_the_tangent(env):
+    """The enthalpy-lattice sweep on a random state with a cold mask: the
+    gradient w.r.t. the wall temperatures, L and the mask temperature T_cold
+    equals the forward-mode tangent."""
+    O, lbm, S, torch = env
+    cfg, arr = W.random_state(40, 24, seed=3, lattices=W.HEAT)
+    assert "mask" in arr and arr["mask"].any()
+    steps = 150
+    s = lbm.Solver(cfg, precision="fp64").set_geometry(arr)
+    ff, grad = s.adjoint_frozen_fraction(steps, every=40)
+    s.close()
+    dirs = [("T_wall", k) for k in range(4) if cfg["bc"][k] == "dirichlet"] + [("latent", 4), ("T_cold", 5)]
+    for name, k in dirs:
+        t = ({"T_wall": [1.0 if j == k else 0.0 for j in range(4)]} if name == "T_wall" else {name: 1.0})
+        ts = lbm.Solver(cfg, precision="tangent", tangent=t).set_geometry(arr).step(steps)
+        d, dt = ts.diagnostics(), ts.tangent_diagnostics(compute=False)
+        ts.close()
+        fz, mv = d["frozen_volume"], d["material_volume"]
+        tan = (dt["frozen_volume"] * mv - fz * dt["material_volume"]) / mv ** 2
+        print(f"\n{name}: adjoint {grad[k]:.12e} tangent {tan:.12e}")
+        assert abs(fz / mv - ff) <= 1e-12
+        assert abs(grad[k] - tan) <= 1e-9 * abs(tan) + 1e-14, (name, grad[k], tan)
