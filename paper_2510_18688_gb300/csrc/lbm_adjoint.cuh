@@ -1,6 +1,9 @@
 // lbm_adjoint.cuh -- hand-written reverse-mode (adjoint) kernels of the
-// enthalpy-lattice step (contexts whose only lattice is LAT_HEAT, FP64, no
-// cold mask).
+// enthalpy-lattice step (contexts whose only lattice is LAT_HEAT, or whose
+// flow lattice stays at rest; FP64), of the phase-field step and of the two
+// coupled.  A cold-mask node reads its enthalpy populations as the
+// equilibrium at T_cold, so their adjoint goes to T_cold (and L, and the
+// lagged w where it varies) instead of to the stored populations.
 //
 // With the enthalpy lattice alone the fluid is at rest (u = 0) and the step
 // at one node is local: rho H = sum h + Q_prev / 2 (Eq. (28)), the
@@ -533,7 +536,7 @@ static __global__ void __launch_bounds__(NT) lbm_phase_init_kernel(const PhaseAd
 
 // ---------------------------------------------------------------------------
 // reverse mode of the coupled phase-field and enthalpy step (lattices ==
-// LAT_PHASE | LAT_HEAT: the fluid at rest, no cold mask).  The freezing
+// LAT_PHASE | LAT_HEAT: the fluid at rest).  The freezing
 // couples the lattices: the mass source mdot of Eq. (1) enters the order
 // parameter (Eq. (22)) and the phase source (Eq. (20)); the weight w and
 // the solid fraction fs = phi0 + w (1 - fl) set the properties of Eq. (10)
