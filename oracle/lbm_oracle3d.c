@@ -711,3 +711,27 @@ void oracle3_lattice(int* cx, int* cy, int* cz, double* w, int* opp) {
     opp[i] = OPP[i];
   }
 }
+
+/* --- single-node entry points for the moment pins --- */
+
+void oracle3_node_flow(double pr, double rho, const double* u, double S, const double* F,
+                       const double* fp, const double* Ft, uint32_t readings, double* feq,
+                       double* Fi) {
+  lattice_setup();
+  flow_equilibrium(pr, rho, u, feq);
+  flow_forcing(S, F, rho, fp, u, Ft, readings, Fi);
+}
+
+void oracle3_node_phase(double phi, double muphi, double eta, const double* phu,
+                        const double* dphu, double mdot, double* geq, double* Gi) {
+  lattice_setup();
+  phase_equilibrium(phi, muphi, eta, phu, geq);
+  phase_source(dphu, phi, mdot, Gi);
+}
+
+void oracle3_node_heat(double rhoH, double C, double T, double rr, const double* u, double mdot,
+                       double* heq, double* Hi) {
+  lattice_setup();
+  heat_equilibrium(rhoH, C, T, rr, u, heq);
+  heat_source(C, T, mdot, Hi);
+}

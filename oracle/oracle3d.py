@@ -105,6 +105,11 @@ def lib():
         L.oracle3_step_count.restype = ctypes.c_int64
         L.oracle3_step_count.argtypes = [ctypes.c_void_p]
         L.oracle3_lattice.argtypes = [_ip, _ip, _ip, _dp, _ip]
+        L.oracle3_node_flow.argtypes = [ctypes.c_double, ctypes.c_double, _dp, ctypes.c_double,
+                                        _dp, _dp, _dp, ctypes.c_uint32, _dp, _dp]
+        L.oracle3_node_phase.argtypes = [ctypes.c_double] * 3 + [_dp, _dp, ctypes.c_double,
+                                                                 _dp, _dp]
+        L.oracle3_node_heat.argtypes = [ctypes.c_double] * 4 + [_dp, ctypes.c_double, _dp, _dp]
         _lib = L
     return _lib
 
@@ -193,3 +198,27 @@ def lattice():
     w = (ctypes.c_double * NQ)()
     lib().oracle3_lattice(cx, cy, cz, w, opp)
     return (np.array(cx[:]), np.array(cy[:]), np.array(cz[:]), np.array(w[:]), np.array(opp[:]))
+
+
+# --- single-node entry points, used by the moment pins -----------------------
+
+def node_flow(pr, rho, u, S, F, fp, Ft, readings=0):
+    feq, Fi = np.empty(NQ), np.empty(NQ)
+    u, F, fp, Ft = (_f64(v) for v in (u, F, fp, Ft))
+    lib().oracle3_node_flow(pr, rho, _ptr(u), S, _ptr(F), _ptr(fp), _ptr(Ft), readings,
+                            _ptr(feq), _ptr(Fi))
+    return feq, Fi
+
+
+def node_phase(phi, muphi, eta, phu, dphu, mdot):
+    geq, Gi = np.empty(NQ), np.empty(NQ)
+    phu, dphu = _f64(phu), _f64(dphu)
+    lib().oracle3_node_phase(phi, muphi, eta, _ptr(phu), _ptr(dphu), mdot, _ptr(geq), _ptr(Gi))
+    return geq, Gi
+
+
+def node_heat(rhoH, C, T, rr, u, mdot):
+    heq, Hi = np.empty(NQ), np.empty(NQ)
+    u = _f64(u)
+    lib().oracle3_node_heat(rhoH, C, T, rr, _ptr(u), mdot, _ptr(heq), _ptr(Hi))
+    return heq, Hi

@@ -198,3 +198,54 @@ def test_axis_permutation_symmetry(O3, bc):
         back = np.transpose(fp[new], (1, 2, 0))
         scale = max(1e-30, np.abs(f[old]).max())
         assert np.abs(back - f[old]).max() <= 1e-9 * scale, (new, old)
+
+
+def _m3(O3, v):
+    cx, cy, cz, _, _ = O3.lattice()
+    c = np.stack([cx, cy, cz], 1).astype(float)
+    return v.sum(), c.T @ v, np.einsum("ia,ib,i->ab", c, c, v)
+
+
+@pytest.mark.parametrize("seed", range(3))
+def test_equilibrium_and_source_moments_3d(O3, seed):
+    """The moments Eqs. (14), (16), (19), (20), (25) must have on D3Q19 for
+    the model to recover its macroscopic equations (the 3-D form of the 2-D
+    moment pins), including the R-FT variant: its trace term c.c - 3 cs^2
+    adds cs^2 S I to the second moment of F_i and nothing to the zeroth (a
+    2-D trace c.c - 2 cs^2 would shift the zeroth moment by cs^2 S)."""
+    cs2 = 1.0 / 3.0
+    r = np.random.default_rng(40 + seed)
+    p, rho = r.uniform(-1e-3, 1e-3), r.uniform(0.1, 1.0)
+    u = r.uniform(-0.05, 0.05, 3)
+    S, F, fp, Ft = r.normal() * 1e-3, r.normal(size=3) * 1e-3, r.normal(size=3) * 1e-3, r.normal(size=3) * 1e-3
+    feq, Fi = O3.node_flow(p, rho, u, S, F, fp, Ft)
+    m0, m1, m2 = _m3(O3, feq)
+    assert abs(m0) < 1e-15
+    assert np.allclose(m1, rho * u, rtol=1e-13, atol=1e-17)
+    assert np.allclose(m2, p * np.eye(3) + rho * np.outer(u, u), rtol=1e-12, atol=1e-17)
+    m0, m1, m2 = _m3(O3, Fi)
+    assert abs(m0 - S) < 1e-15
+    assert np.allclose(m1, F + rho * fp, rtol=1e-13, atol=1e-18)
+    assert np.allclose(m2, cs2 * S * np.eye(3) + np.outer(u, Ft) + np.outer(Ft, u), rtol=1e-12,
+                       atol=1e-18)
+    _, Fv = O3.node_flow(p, rho, u, S, F, fp, Ft, readings=1)
+    v0, v1, v2 = _m3(O3, Fv)
+    assert abs(v0 - S) < 1e-15 and np.allclose(v1, m1, atol=1e-18)
+    assert np.allclose(v2 - m2, cs2 * S * np.eye(3), atol=1e-17)
+    phi, mu, eta = r.uniform(-1, 1), r.normal() * 1e-3, r.uniform(0.5, 2)
+    phu, dphu, md = r.normal(size=3) * 1e-2, r.normal(size=3) * 1e-4, r.normal() * 1e-4
+    geq, G = O3.node_phase(phi, mu, eta, phu, dphu, md)
+    m0, m1, m2 = _m3(O3, geq)
+    assert abs(m0 - phi) < 1e-15
+    assert np.allclose(m1, phu, atol=1e-16)
+    assert np.allclose(m2, cs2 * eta * mu * np.eye(3), atol=1e-17)
+    m0, m1, _ = _m3(O3, G)
+    assert abs(m0 - phi * md) < 1e-18
+    assert np.allclose(m1, dphu, atol=1e-18)
+    rhoH, C, T, rr = r.uniform(-2, 12), r.uniform(0.5, 2), r.uniform(-1, 1), r.uniform(0.5, 1.5)
+    heq, H = O3.node_heat(rhoH, C, T, rr, u, md)
+    m0, m1, m2 = _m3(O3, heq)
+    assert abs(m0 - rhoH) < 1e-13
+    assert np.allclose(m1, C * T * u, rtol=1e-12, atol=1e-16)
+    assert np.allclose(m2, rr * T * cs2 * np.eye(3) + C * T * np.outer(u, u), rtol=1e-12, atol=1e-15)
+    assert abs(H.sum() - C * T * md) < 1e-16
