@@ -361,26 +361,35 @@ def random_state3(nx, ny, nz, seed=0, lattices=ALL, bc=None, n_blobs=3, mushy=Tr
         return np.sqrt(d[0] ** 2 + d[1] ** 2 + d[2] ** 2)
 
     shape = (nz, ny, nx)
-    phi0 = np.zeros(shape)
-    dl = np.full(shape, -1e30)
     m = min(nx, ny, nz)
-    for _ in range(n_blobs):
-        c = (r.uniform(0, nx), r.uniform(0, ny), r.uniform(0, nz))
-        rad = r.uniform(2.0, max(3.0, m / 3.0))
-        phi0 = np.maximum(phi0, 0.5 + 0.5 * np.tanh(2.0 * (rad - dist(*c)) / eps))
-        c = (r.uniform(0, nx), r.uniform(0, ny), r.uniform(0, nz))
-        rad = r.uniform(3.0, max(4.0, m / 2.0))
-        dl = np.maximum(dl, rad - dist(*c))
-    phi = (1.0 - phi0) * np.tanh(2.0 * dl / eps)
-    T = (0.3 * np.sin(2 * np.pi * X / nx * r.integers(1, 3)) + 0.2 * r.standard_normal()
-         + 0.05 * np.cos(2 * np.pi * Y / ny) + 0.05 * np.sin(2 * np.pi * Z / nz))
-    T = np.where(phi < 0.9, np.maximum(T, 0.1), T)
-    fl = np.where(T < 0.0, 0.0, 1.0)
-    if mushy:
+    # draw until the state has every branch (solid, liquid and gas; liquid
+    # below and above T_m; a mushy band when asked for; masked nodes), at
+    # most 64 times (the smallest grids cannot hold them all)
+    for _attempt in range(64):
+        phi0 = np.zeros(shape)
+        dl = np.full(shape, -1e30)
+        for _ in range(n_blobs):
+            c = (r.uniform(0, nx), r.uniform(0, ny), r.uniform(0, nz))
+            rad = r.uniform(2.0, max(3.0, m / 3.0))
+            phi0 = np.maximum(phi0, 0.5 + 0.5 * np.tanh(2.0 * (rad - dist(*c)) / eps))
+            c = (r.uniform(0, nx), r.uniform(0, ny), r.uniform(0, nz))
+            rad = r.uniform(3.0, max(4.0, m / 2.0))
+            dl = np.maximum(dl, rad - dist(*c))
+        phi = (1.0 - phi0) * np.tanh(2.0 * dl / eps)
+        T = (0.3 * np.sin(2 * np.pi * X / nx * r.integers(1, 3)) + 0.2 * r.standard_normal()
+             + 0.05 * np.cos(2 * np.pi * Y / ny) + 0.05 * np.sin(2 * np.pi * Z / nz))
+        T = np.where(phi < 0.9, np.maximum(T, 0.1), T)
+        fl = np.where(T < 0.0, 0.0, 1.0)
         band = np.abs(T) < 0.05
-        fl = np.where(band, 0.5 + T / 0.1, fl)
-        T = np.where(band, 0.0, T)
-    mask = (phi0 > 0.7) & (r.uniform(size=shape) < 0.5)
+        if mushy:
+            fl = np.where(band, 0.5 + T / 0.1, fl)
+            T = np.where(band, 0.0, T)
+        mask = (phi0 > 0.7) & (r.uniform(size=shape) < 0.5)
+        complete = ((phi0 > 0.5).any() and (phi > 0.5).any() and (phi < -0.5).any()
+                    and (T < 0.0).any() and (T > 0.0).any() and mask.any()
+                    and (band.any() or not mushy))
+        if complete:
+            break
     p = base_params(nx, ny, rho_s=float(r.uniform(0.85, 1.1)), cp_s=0.8, lambda_l=0.12,
                     latent=latent_from_stefan(float(r.uniform(0.1, 0.5))),
                     theta_deg=float(r.uniform(40.0, 140.0)),
