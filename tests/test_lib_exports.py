@@ -117,3 +117,22 @@ def test_3d_create_rejects_grids_beyond_31_bit_offsets(lib):
     h = ctypes.c_void_p()
     assert lib.lbm3_create(ctypes.byref(p), ctypes.byref(h)) == -1
     assert not h.value
+
+
+def test_3d_params_marshalling():
+    """make_params3 maps a 3-D workload dict onto lbm3_params: the x and y
+    faces into the base parameters, the z faces, g_z and the tangent rates of
+    all six walls into the 3-D fields."""
+    from paper_2510_18688_gb300 import lbm, workloads as W
+    cfg, _ = W.random_state3(12, 8, 6, seed=3)
+    tw = [0.1, 0.2, 0.3, 0.4, 0.5, 0.6]
+    p = lbm.make_params3(cfg, "tangent", {"T_wall": tw, "theta_deg": 1.0})
+    assert (p.base.nx, p.base.ny, p.nz) == (12, 8, 6)
+    assert p.base.precision == lbm.PRECISION["tangent"]
+    assert [p.base.bc[k] for k in range(4)] == [lbm.BC[b] for b in cfg["bc"][:4]]
+    assert [p.bc_z[k] for k in range(2)] == [lbm.BC[b] for b in cfg["bc"][4:]]
+    assert list(p.base.T_wall) == list(cfg["T_wall"][:4])
+    assert list(p.T_wall_z) == list(cfg["T_wall"][4:])
+    assert p.gz == cfg["gz"]
+    assert list(p.base.tan_T_wall) == tw[:4] and list(p.tan_T_wall_z) == tw[4:]
+    assert p.base.tan_theta_deg == 1.0 and p.base.tan_latent == 0.0
