@@ -95,10 +95,16 @@ def algorithmic_bytes_per_node3(esize: int) -> int:
     return 2 * 57 * esize + 2 * 7 * esize + esize
 
 
-def algorithmic_bytes_per_node(esize: int, has_mask: bool, pop_bytes: int = 0) -> int:
-    """27 populations read and written, 6 lag fields read and written, phi0
-    read, mask byte read."""
-    return 2 * 27 * (pop_bytes or esize) + 2 * 6 * esize + esize + (1 if has_mask else 0)
+def algorithmic_bytes_per_node(esize: int, has_mask: bool, pop_bytes: int = 0,
+                               nlag: int = 6) -> int:
+    """27 populations read and written, the lag fields read and written (6;
+    7 for float arithmetic, whose well-balanced storage also keeps the
+    previous temperature), phi0 read, mask byte read."""
+    return 2 * 27 * (pop_bytes or esize) + 2 * nlag * esize + esize + (1 if has_mask else 0)
+
+
+def lag_planes(precision: str) -> int:
+    return 7 if precision in ("fp32", "fp16s") else 6
 
 
 def measured_peak():
@@ -174,13 +180,22 @@ class ClockSampler:
         try:
             self._proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.index), f"--query-gpu={q}",
-                 "--format=csv,noheader,nounits", "-lms", "50"],
+                 "--format=csv,noheader,nounits", "-lms", "20"],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self._t = threading.Thread(target=self._read, daemon=True)
             self._t.start()
+            # nvidia-smi takes a moment to start: wait for its first sample so
+            # that the window covers what follows
+            t0 = time.perf_counter()
+            while not self.samples and time.perf_counter() - t0 < 3.0:
+                time.sleep(0.01)
         except (FileNotFoundError, OSError):
             self._proc = None
         return self
+
+    def mark(self):
+        """Index of the next sample (to split warm-up from the timed region)."""
+        return len(self.samples)
 
     def _read(self):
         for line in self._proc.stdout:
@@ -196,17 +211,23 @@ class ClockSampler:
             except subprocess.TimeoutExpired:
                 self._proc.kill()
 
-    def summary(self):
-        if not self.samples:
+    def summary(self, start: int = 0, window: str = ""):
+        """Median SM clock, maximum clock and throttle reasons of the samples
+        from index `start` on."""
+        samples = self.samples[start:]
+        if not samples:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
-        sm = [float(s[0]) for s in self.samples if s[0].replace(".", "").isdigit()]
-        mx = [float(s[1]) for s in self.samples if s[1].replace(".", "").isdigit()]
+        sm = [float(s[0]) for s in samples if s[0].replace(".", "").isdigit()]
+        mx = [float(s[1]) for s in samples if s[1].replace(".", "").isdigit()]
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        reasons = sorted({names[k] for s in self.samples for k in range(4)
+        reasons = sorted({names[k] for s in samples for k in range(4)
                           if s[3 + k].lower() == "active"})
-        return {"sm_mhz": float(np.median(sm)) if sm else None,
-                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
-                "samples": len(self.samples)}
+        out = {"sm_mhz": float(np.median(sm)) if sm else None,
+               "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+               "samples": len(samples)}
+        if window:
+            out["window"] = window
+        return out
 
 
 def dist_env():
@@ -519,6 +540,79 @@ def fracture_line(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def fp64_record(lbm, wl, flush, stream, sptr, args, t32_ms):
+    """The FP64 step on the same workload: MLUPS, its HBM fraction and its
+    fraction of the FP64 FMA rate measured now (the FP64 pipe, not HBM,
+    bounds this step on GB300), each step timed alone after an L2 flush."""
+    import torch
+    cfg, arr = wl
+    n = cfg["nx"] * cfg["ny"]
+    s = lbm.Solver(cfg, precision="fp64", diag_every=args.diag_every).set_geometry(arr)
+    k = max(10, min(args.steps, 40))
+    for _ in range(3):
+        flush.zero_()
+        lbm.lbm_step(s.ctx, 1, sptr)
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(k)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(k)]
+    for j in range(k):
+        flush.zero_()
+        starts[j].record(stream)
+        lbm.lbm_step(s.ctx, 1, sptr)
+        ends[j].record(stream)
+    torch.cuda.synchronize()
+    t = float(np.mean([a.elapsed_time(b) for a, b in zip(starts, ends)]))
+    s.close()
+    fma = lbm.lbm_probe_fma_rate("fp64", sptr) / 1e12
+    bpn = algorithmic_bytes_per_node(8, "mask" in arr)
+    peak, peak_src = measured_peak()
+    hbm = bpn * n / (t * 1e-3) / 1e9
+    fpn = profiled_value(args.workload, "fp64", "fp64 flops per node")
+    ach = fpn * n / (t * 1e-3) / 1e12 if fpn else None
+    return {"value": n / (t * 1e-3) / 1e6, "unit": "MLUPS", "ms_per_step": t, "steps": k,
+            "fp32_over_fp64": t / t32_ms,
+            "fp64_pipe": {"achieved": ach, "peak": fma, "unit": "TFLOP/s",
+                          "frac": ach / fma if ach else None, "flops_per_node": fpn,
+                          "peak_source": "FP64 FMA rate measured in this run"},
+            "hbm": {"achieved": hbm, "peak": peak, "unit": "GB/s", "frac": hbm / peak,
+                    "bytes_per_node": bpn, "peak_source": peak_src}}
+
+
+def adjoint_record(lbm, wl, sptr, t32_ms, steps: int = 256, every: int = 16):
+    """Reverse sweep of the whole coupled step (FP64, checkpointed recompute):
+    the frozen fraction of the same workload after `steps` steps and its
+    gradient w.r.t. (T_wall, L, theta, sigma, g, T_cold), timed against the
+    FP64 forward run of the same steps (host clock around synchronised
+    calls)."""
+    import torch
+    cfg, arr = wl
+    s = lbm.Solver(cfg, precision="fp64").set_geometry(arr)
+    lbm.lbm_step(s.ctx, 3, sptr)
+    s.set_geometry(arr)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    lbm.lbm_step(s.ctx, steps, sptr)
+    torch.cuda.synchronize()
+    t_fwd = time.perf_counter() - t0
+    s.set_geometry(arr)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    ff, grad = lbm.lbm_adjoint_coupled(s.ctx, steps, every, 0, 0, 0, None, sptr)
+    torch.cuda.synchronize()
+    t_adj = time.perf_counter() - t0
+    s.close()
+    return {"adjoint_forward_ratio": t_adj / t_fwd,
+            "adjoint_over_fp32_forward": (t_adj / steps * 1e3) / t32_ms,
+            "steps": steps, "checkpoint_every": every,
+            "forward_ms_per_step": t_fwd / steps * 1e3,
+            "adjoint_ms_per_step": t_adj / steps * 1e3,
+            "observable": "frozen fraction", "ff": ff,
+            "grad": {"T_wall": grad[:4], "latent": grad[4], "theta_deg": grad[5],
+                     "sigma": grad[6], "gx": grad[7], "gy": grad[8], "T_cold": grad[9]},
+            "note": "forward + reverse sweep over the FP64 forward run of the same steps "
+                    "(adjoint_forward_ratio); adjoint_over_fp32_forward divides by the timed "
+                    "FP32 step of this line"}
+
+
 def cpu_baseline_sample(target_s: float = 12.0):
     """Time the oracle on the same workload for about target_s seconds."""
     from oracle import oracle as O
@@ -548,6 +642,8 @@ def main():
                     help="fp16s: FP16 population storage, FP32 arithmetic; tangent: FP64 "
                          "step with its derivative along the wall temperature")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-sub-records", action="store_true",
+                    help="skip the FP64 and adjoint sub-records of the default FP32 line")
     ap.add_argument("--diag-every", type=int, default=1,
                     help="steps between fused FP64 diagnostic reductions (0: none)")
     ap.add_argument("--back-to-back", action="store_true",
@@ -609,17 +705,29 @@ def main():
 
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
 
-    for _ in range(args.warmup):
-        flush.zero_()
-        step(1)
-    torch.cuda.synchronize()
-
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    if pg:
-        pg.barrier()
-    torch.cuda.synchronize()
+    # the clock sampler runs from before the warm-up to after the timed
+    # region; a short timed region (tens of steps, about a millisecond) falls
+    # between two nvidia-smi samples, so the warm-up ends with a sustained
+    # untimed load of the same kernel (at least 0.3 s) whose clocks are
+    # recorded with it
     with ClockSampler(local) as clk:
+        for _ in range(args.warmup):
+            flush.zero_()
+            step(1)
+        torch.cuda.synchronize()
+        t_load = time.perf_counter()
+        while time.perf_counter() - t_load < 0.3:
+            step(64)
+            torch.cuda.synchronize()
+        for _ in range(3):
+            flush.zero_()
+            step(1)
+        if pg:
+            pg.barrier()
+        torch.cuda.synchronize()
+        timed_mark = clk.mark()
         wall0 = time.perf_counter()
         for k in range(args.steps):
             flush.zero_()
@@ -628,6 +736,7 @@ def main():
             ends[k].record(stream)
         torch.cuda.synchronize()
         wall = time.perf_counter() - wall0
+        time.sleep(0.05)  # one more sample after the timed region
     if pg:
         pg.barrier()
     times = np.array([s.elapsed_time(e) for s, e in zip(starts, ends)])  # ms
@@ -660,19 +769,22 @@ def main():
         downloads.append((sv.ctx, ptrs))
         h2d += 4 * c["nx"] * c["ny"] * 8 + (c["nx"] * c["ny"] if hm is not None else 0)
         d2h += 3 * c["nx"] * c["ny"] * 8
+    # a job of at least 2000 steps, so that the upload does not dominate
+    k_e2e = max(args.steps, 2000)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for u in uploads:
         lbm.lbm_set_geometry(*u, lbm.LBM_HOST, sptr)
-    step(args.steps)
+    step(k_e2e)
     for ctx, ptrs in downloads:
         lbm.lbm_read_fields(ctx, fmask, ptrs, lbm.LBM_HOST, sptr)
     e2e_s = time.perf_counter() - t0
-    e2e = {"value": n * args.steps / e2e_s / 1e6, "unit": "MLUPS",
-           "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": d2h / args.steps,
-           "note": ("one job through the C ABI: pinned-host geometry upload, K steps back to "
-                    "back (no L2 flush between them, unlike the per-step timing of value), "
-                    "phi/fl/T download to pinned host memory")}
+    e2e = {"value": n * k_e2e / e2e_s / 1e6, "unit": "MLUPS", "steps": k_e2e,
+           "h2d_bytes_per_step": h2d / k_e2e, "d2h_bytes_per_step": d2h / k_e2e,
+           "note": (f"one job of {k_e2e} steps through the C ABI: pinned-host geometry upload, "
+                    "the steps back to back (no L2 flush between them, unlike the per-step "
+                    "timing of value), phi/fl/T download to pinned host memory; host clock "
+                    "around the synchronised job")}
 
     # steady state without flushes (context only, not the value)
     g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -689,7 +801,8 @@ def main():
     esize = {"fp64": 8, "tangent": 16}.get(args.precision, 4)
     pop_bytes = 2 if args.precision == "fp16s" else esize
     # node-weighted bytes per node (grids with a cold mask read one more byte)
-    bpn = sum(algorithmic_bytes_per_node(esize, "mask" in a, pop_bytes) * c["nx"] * c["ny"]
+    bpn = sum(algorithmic_bytes_per_node(esize, "mask" in a, pop_bytes,
+                                         lag_planes(args.precision)) * c["nx"] * c["ny"]
               for c, a in wls) / n
     peak, peak_src = measured_peak()
     achieved = bpn * n / (t_step * 1e-3) / 1e9
@@ -729,9 +842,17 @@ def main():
         "e2e": e2e,
         "l2_resident_mlups": n / (l2_ms * 1e-3) / 1e6,
         "diag_last": {k: diag[k] for k in ("material_mass", "frozen_volume", "nonfinite", "step")},
-        "clocks": clk.summary(),
+        "clocks": clk.summary(timed_mark, "timed region"),
+        "clocks_window": clk.summary(0, "warm-up (with at least 0.3 s of sustained untimed steps) "
+                                        "through the timed region"),
         "wall_s_timed_region": wall,
     }
+    if args.precision == "fp32" and len(wls) == 1 and not args.no_sub_records:
+        # the other two parts of the metric on the same workload: the FP64
+        # step, and the reverse sweep of the coupled step against its forward
+        line["fp64"] = fp64_record(lbm, wls[0], flush, stream, sptr, args, t_step)
+        line["adjoint"] = adjoint_record(lbm, wls[0], sptr, t_step)
+    line["build"] = {"source_hash": lbm.lbm_source_hash()}
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline_sample()
     print(json.dumps(line), flush=True)

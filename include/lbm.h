@@ -51,14 +51,22 @@ typedef enum {
   LBM_ERR_STATE = -8        /* call out of order (e.g. step before geometry)  */
 } lbm_status;
 
-/* Arithmetic and storage of the populations.  LBM_FP16S stores the 27
- * populations in IEEE binary16 and does all arithmetic, the lag fields and
- * phi0 in FP32; the rest populations g0 and h0 are stored as differences
- * from FP32 references the same node holds (2 w - 1 + phi0 and
- * w rho_l L fl, from its lag fields), so FP16 keeps only small remainders.
- * This is not in the paper (which gives no precision); it trades accuracy
- * for 161 instead of 269 bytes of state traffic per node update.  Batches
- * and lbm_diagnostics_noalloc do not take it (LBM_ERR_UNSUPPORTED). */
+/* Arithmetic and storage of the populations.  LBM_FP64: everything in
+ * double.  LBM_FP32: populations, lag fields and arithmetic in float, with
+ * well-balanced storage: every population that carries a large, slowly
+ * varying part is stored as its difference from a reference that writer and
+ * reader form identically from the lag fields (g0 from 2 w - 1 + phi0; h0
+ * from the node's previous enthalpy state ell fl + (C - 5/9 rho_ref Cp_ref)
+ * T; h_i, i > 0, from w_i rho_ref Cp_ref T of the node it is streamed to;
+ * f_i from 3 (w_i - delta_i0) p of the node it is streamed from), so that
+ * float rounds only the small remainders; the inversion of Eq. (8) near the
+ * melting point (branch test, liquid fraction and its clamp) runs in FP64.
+ * Float states carry one more lag plane, the temperature T of the previous
+ * step.  LBM_FP16S: the same with the 27 populations in IEEE binary16.
+ * Neither storage format is in the paper (which gives no precision);
+ * LBM_FP16S trades accuracy for 165 instead of 277 bytes of state traffic
+ * per node update.  Batches and lbm_diagnostics_noalloc do not take
+ * LBM_FP16S (LBM_ERR_UNSUPPORTED). */
 /* LBM_FP64_TANGENT: the FP64 step in forward-mode (dual-number)
  * arithmetic: every value carries its derivative with respect to the
  * parameter direction given by the tan_* fields of lbm_params (16 bytes per
@@ -252,6 +260,13 @@ int64_t lbm_step_count(const lbm_ctx* ctx);
 const char* lbm_last_error(const lbm_ctx* ctx);
 const char* lbm_status_string(int status);
 
+/* The source hash the library was built from: the first 16 hex digits of
+ * the SHA-256 of every kernel and host source file, this header and the
+ * compile flags (a static string, never NULL; "unknown" for a build that
+ * did not define it).  No counterpart in the paper: it ties a loaded binary
+ * to its sources. */
+const char* lbm_source_hash(void);
+
 /* Frees the context and all memory it owns (NULL is allowed). */
 void lbm_destroy(lbm_ctx* ctx);
 
@@ -395,8 +410,8 @@ int lbm_adjoint_coupled(lbm_ctx* ctx, int64_t nsteps, int every, int observable,
  * library): times the step forms the library has on the context's own grid
  * and state and keeps the fastest for later lbm_step calls.  Variants, in
  * this order: the fused one-kernel step with captured periods of at least
- * 32 steps, the same with at least 256, and (LBM_FP32 and LBM_FP64 only)
- * the two-kernel split with 32 and with 256.  Each variant runs
+ * 32 steps, the same with at least 256, and (LBM_FP64 only) the two-kernel
+ * split with 32 and with 256.  Each variant runs
  * steps_per_trial steps twice from the same saved state (the first run
  * warms up and captures; the second is timed with CUDA events on `stream`).
  * The state, step counter and diagnostics (including partial sums not yet
@@ -426,7 +441,9 @@ int lbm_autotune(lbm_ctx* ctx, int steps_per_trial, void* stream, double* out_us
  * Inputs (device memory of the current device, element type float for
  * LBM_FP32 and double for LBM_FP64 in params->precision): `pops`, 27 planes
  * in the order f0..f8, g0..g8, h0..h8; `lags`, 6 planes in the order fl, w,
- * p, phi ux, phi uy, Q; `phi0`, one plane; `cold_mask`, one plane of bytes or
+ * p, phi ux, phi uy, Q (LBM_FP64) or 7 planes, the same and T (LBM_FP32,
+ * whose populations are stored in the well-balanced form of LBM_FP32);
+ * `phi0`, one plane; `cold_mask`, one plane of bytes or
  * NULL.  A plane holds ny rows of pitch elements, pitch = nx rounded up to a
  * multiple of 32, and planes start every `plane` elements, plane =
  * pitch * ny rounded up to a multiple of 64.  This is the layout that

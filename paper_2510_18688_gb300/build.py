@@ -1,5 +1,12 @@
 """Build the sm_103a shared library ``_lib/liblbm_gb300.so`` with nvcc.
 
+The library is rebuilt whenever the SHA-256 of its sources (every file of
+``csrc/``, ``include/lbm.h``) and of the compile command differs from the
+stamp written beside it at the last build -- file times are not trusted, so
+a library copied in with a newer time than its sources is still rebuilt.
+The hash is compiled into the library (``lbm_source_hash``), which ties a
+loaded binary to the sources it was built from.
+
 The translation units (host API, FP32, FP64, FP16-storage, tangent and adjoint kernels, the
 allocation-free diagnostics, the FMA-rate probe) compile
 in parallel and link into one C-ABI library.  Both precisions keep fused
@@ -11,6 +18,7 @@ from __future__ import annotations
 
 import argparse
 import concurrent.futures as cf
+import hashlib
 import os
 import shutil
 import subprocess
@@ -20,6 +28,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 SRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(OUT_DIR, "liblbm_gb300.so")
+STAMP = LIB + ".srchash"
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 UNITS = {
     "lbm_api.cu": [],
@@ -42,15 +51,38 @@ def nvcc() -> str:
 
 
 def _sources():
-    return [os.path.join(SRC, f) for f in os.listdir(SRC)] + [
+    return sorted(os.path.join(SRC, f) for f in os.listdir(SRC)) + [
         os.path.join(os.path.dirname(HERE), "include", "lbm.h")]
 
 
+def _flags(verbose: bool = False):
+    base = [ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC"]
+    base += os.environ.get("LBM_NVCC_EXTRA", "").split()
+    if verbose:
+        base += ["-Xptxas", "-v"]
+    return base
+
+
+def source_hash() -> str:
+    """SHA-256 (first 16 hex digits) of the library's sources and compile
+    flags; the file names are hashed with their contents."""
+    h = hashlib.sha256()
+    for path in _sources():
+        h.update(os.path.basename(path).encode() + b"\0")
+        with open(path, "rb") as fh:
+            h.update(fh.read())
+        h.update(b"\0")
+    h.update(" ".join(_flags()).encode())
+    return h.hexdigest()[:16]
+
+
 def up_to_date() -> bool:
-    if not os.path.exists(LIB):
+    """True when the library exists and its stamp holds the current source
+    hash (not a comparison of file times)."""
+    if not (os.path.exists(LIB) and os.path.exists(STAMP)):
         return False
-    t = os.path.getmtime(LIB)
-    return all(os.path.getmtime(s) <= t for s in _sources())
+    with open(STAMP) as fh:
+        return fh.read().strip() == source_hash()
 
 
 def build(force: bool = False, verbose: bool = False) -> str:
@@ -58,14 +90,13 @@ def build(force: bool = False, verbose: bool = False) -> str:
         return LIB
     os.makedirs(OUT_DIR, exist_ok=True)
     tool = nvcc()
-    base = [tool, ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC"]
-    base += os.environ.get("LBM_NVCC_EXTRA", "").split()
-    if verbose:
-        base += ["-Xptxas", "-v"]
+    digest = source_hash()
+    base = [tool] + _flags(verbose)
 
     def compile_one(unit):
         obj = os.path.join(OUT_DIR, unit.replace(".cu", ".o"))
-        cmd = base + UNITS[unit] + ["-c", os.path.join(SRC, unit), "-o", obj]
+        extra = [f'-DLBM_SOURCE_HASH="{digest}"'] if unit == "lbm_api.cu" else []
+        cmd = base + UNITS[unit] + extra + ["-c", os.path.join(SRC, unit), "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"nvcc failed on {unit}:\n{r.stdout}\n{r.stderr}")
@@ -82,6 +113,9 @@ def build(force: bool = False, verbose: bool = False) -> str:
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
     os.replace(tmp, LIB)
+    with open(STAMP + f".tmp{os.getpid()}", "w") as fh:
+        fh.write(digest + "\n")
+    os.replace(STAMP + f".tmp{os.getpid()}", STAMP)
     return LIB
 
 

@@ -51,6 +51,7 @@ struct lbm_ctx {
   double* h_diag;        // pinned, NDIAG + 1
   void* scratch;         // NSCRATCH planes (phi, fs, rho) of the two-kernel step
   bool split;            // step as macro + collide kernels, or fused (default)
+  int nlag;              // lag planes per buffer: NLAG, plus T for float arithmetic
   int cur;
   int64_t step;
   bool have_geometry;
@@ -75,7 +76,7 @@ struct lbm_ctx {
 namespace {
 
 const uint32_t kMagic = 0x4c424d46u;  // "LBMF"
-const uint32_t kVersion = 1u;
+const uint32_t kVersion = 2u;  // 2: float states keep g0, h0 relative to references
 
 struct StateHeader {
   uint32_t magic, version;
@@ -139,13 +140,7 @@ Args<R, S> step_args(lbm_ctx* c, const Coef<R>& coef) {
 }
 
 cudaError_t launch(lbm_ctx* c, int mode, bool diag, double* const* outs, cudaStream_t s) {
-  if (mode == lbmk::MODE_STEP && c->split) {
-    if (c->p.precision == LBM_FP32) {
-      lbmk::SplitArgs<float> a;
-      a.a = step_args<float>(c, c->cf);
-      a.sc = (float*)c->scratch;
-      return lbmk::launch_split_f32(a, diag, s);
-    }
+  if (mode == lbmk::MODE_STEP && c->split) {  // FP64 only
     lbmk::SplitArgs<double> a;
     a.a = step_args<double>(c, c->cd);
     a.sc = (double*)c->scratch;
@@ -299,6 +294,11 @@ const char* lbm_status_string(int status) {
 
 const char* lbm_last_error(const lbm_ctx* c) { return c ? c->err : "null context"; }
 
+#ifndef LBM_SOURCE_HASH
+#define LBM_SOURCE_HASH "unknown"
+#endif
+const char* lbm_source_hash(void) { return LBM_SOURCE_HASH; }
+
 int64_t lbm_step_count(const lbm_ctx* c) { return c ? c->step : -1; }
 
 int lbm_create(const lbm_params* params, lbm_ctx** out) {
@@ -318,13 +318,14 @@ int lbm_create(const lbm_params* params, lbm_ctx** out) {
   c->esize = c->tangent ? sizeof(lbmk::Dual)
                         : (params->precision == LBM_FP64 ? sizeof(double) : sizeof(float));
   c->pop_esize = params->precision == LBM_FP16S ? sizeof(__half) : c->esize;
+  c->nlag = (params->precision == LBM_FP32 || params->precision == LBM_FP16S) ? lbmk::NLAG + 1
+                                                                              : lbmk::NLAG;
   c->g = lbmh::make_geom(*params);
   {
     // LBM_STEP_KERNEL=split selects the two-kernel step (macro pass +
     // collide pass); the default is the fused one-kernel step
     const char* k = std::getenv("LBM_STEP_KERNEL");
-    c->split = k && std::strcmp(k, "split") == 0 && params->precision != LBM_FP16S &&
-               !c->tangent;
+    c->split = k && std::strcmp(k, "split") == 0 && params->precision == LBM_FP64;
     // LBM_STEP_GRAPHS=0 launches every step on its own instead of
     // replaying captured periods
     const char* gr = std::getenv("LBM_STEP_GRAPHS");
@@ -341,7 +342,7 @@ int lbm_create(const lbm_params* params, lbm_ctx** out) {
   cudaError_t e = cudaSuccess;
   for (int b = 0; b < 2 && e == cudaSuccess; b++) {
     e = dev_malloc(&c->pop[b], 27 * P * c->pop_esize);
-    if (e == cudaSuccess) e = dev_malloc(&c->lag[b], lbmk::NLAG * P * c->esize);
+    if (e == cudaSuccess) e = dev_malloc(&c->lag[b], c->nlag * P * c->esize);
   }
   if (e == cudaSuccess) e = dev_malloc(&c->phi0, P * c->esize);
   if (e == cudaSuccess) e = dev_malloc(&c->scratch, lbmk::NSCRATCH * P * c->esize);
@@ -661,7 +662,7 @@ int lbm_read_tangent_diagnostics(lbm_ctx* c, lbm_diag* out) {
 
 int lbm_state_size(const lbm_ctx* c, size_t* bytes) {
   if (!c || !bytes) return LBM_ERR_ARG;
-  *bytes = sizeof(StateHeader) + (27 * c->pop_esize + lbmk::NLAG * c->esize) * (size_t)c->g.plane;
+  *bytes = sizeof(StateHeader) + (27 * c->pop_esize + c->nlag * c->esize) * (size_t)c->g.plane;
   return LBM_OK;
 }
 
@@ -679,7 +680,7 @@ int lbm_save_state(lbm_ctx* c, void* host_buf, size_t capacity, void* stream) {
   const size_t pb = 27 * (size_t)c->g.plane * c->pop_esize;
   cudaError_t e = cudaMemcpyAsync(dst, c->pop[c->cur], pb, cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess)
-    e = cudaMemcpyAsync(dst + pb, c->lag[c->cur], lbmk::NLAG * (size_t)c->g.plane * c->esize,
+    e = cudaMemcpyAsync(dst + pb, c->lag[c->cur], c->nlag * (size_t)c->g.plane * c->esize,
                         cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return cuda_fail(c, e, "state download");
@@ -702,7 +703,7 @@ int lbm_load_state(lbm_ctx* c, const void* host_buf, size_t size, void* stream) 
   const size_t pb = 27 * (size_t)c->g.plane * c->pop_esize;
   cudaError_t e = cudaMemcpyAsync(c->pop[c->cur], src, pb, cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess)
-    e = cudaMemcpyAsync(c->lag[c->cur], src + pb, lbmk::NLAG * (size_t)c->g.plane * c->esize,
+    e = cudaMemcpyAsync(c->lag[c->cur], src + pb, c->nlag * (size_t)c->g.plane * c->esize,
                         cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return cuda_fail(c, e, "state upload");
@@ -1455,7 +1456,7 @@ extern "C" int lbm_autotune(lbm_ctx* c, int steps_per_trial, void* stream, doubl
   if (!c->have_geometry) return fail(c, LBM_ERR_STATE, "autotune before lbm_set_geometry%s");
   cudaStream_t s = (cudaStream_t)stream;
   const size_t P = (size_t)c->g.plane;
-  const size_t pb = 27 * P * c->pop_esize, lb = lbmk::NLAG * P * c->esize;
+  const size_t pb = 27 * P * c->pop_esize, lb = c->nlag * P * c->esize;
   // the diagnostic partials too: trial steps overwrite them
   const size_t db = (c->tangent ? 2 : 1) * (size_t)lbmk::NDIAG * c->nblocks * sizeof(double);
   void* backup = nullptr;
@@ -1474,7 +1475,7 @@ extern "C" int lbm_autotune(lbm_ctx* c, int steps_per_trial, void* stream, doubl
     e = cudaMemcpyAsync((char*)backup + pb + lb, c->diag_partial, db, cudaMemcpyDeviceToDevice, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   // variants: kernel form (fused, split) x shortest captured period (32, 256)
-  const bool split_ok = c->p.precision == LBM_FP32 || c->p.precision == LBM_FP64;
+  const bool split_ok = c->p.precision == LBM_FP64;
   double us[4] = {-1.0, -1.0, -1.0, -1.0};
   cudaEvent_t t0 = nullptr, t1 = nullptr;
   if (e == cudaSuccess) e = cudaEventCreate(&t0);

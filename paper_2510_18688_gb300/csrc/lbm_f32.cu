@@ -25,21 +25,6 @@ cudaError_t launch_step_f32(const Args<float>& a, int mode, bool diag, cudaStrea
   return cudaGetLastError();
 }
 
-cudaError_t launch_split_f32(const SplitArgs<float>& a, bool diag, cudaStream_t s) {
-  const dim3 grid = grid_dims(a.a.g), block = block_dims();
-  const bool all = a.a.g.lattices == (LAT_FLOW | LAT_PHASE | LAT_HEAT);
-  if (all) lbm_macro_kernel<float, 7><<<grid, block, 0, s>>>(a);
-  else lbm_macro_kernel<float, 0><<<grid, block, 0, s>>>(a);
-  if (all) {
-    if (diag) lbm_collide_kernel<float, true, 7><<<grid, block, 0, s>>>(a);
-    else lbm_collide_kernel<float, false, 7><<<grid, block, 0, s>>>(a);
-  } else {
-    if (diag) lbm_collide_kernel<float, true, 0><<<grid, block, 0, s>>>(a);
-    else lbm_collide_kernel<float, false, 0><<<grid, block, 0, s>>>(a);
-  }
-  return cudaGetLastError();
-}
-
 cudaError_t launch_batch_f32(const BatchTable<float>& b, bool diag, bool all, cudaStream_t s) {
   const dim3 block = block_dims();
   const int ctas = b.tile_base[b.ngrids];

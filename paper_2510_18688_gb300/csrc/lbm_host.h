@@ -44,6 +44,12 @@ inline Coef<R> make_coef(const lbm_params& p) {
   c.rr3 = (R)(p.rho_ref * (2.0 * p.cp_s * p.cp_l / (p.cp_s + p.cp_l)) / 3.0);
   c.inv_rr3 = (R)(3.0 / (p.rho_ref * (2.0 * p.cp_s * p.cp_l / (p.cp_s + p.cp_l))));
   c.inv_tau_g = (R)(1.0 / (0.5 + p.mobility / (p.eta / 3.0)));
+  {
+    const double rr = p.rho_ref * (2.0 * p.cp_s * p.cp_l / (p.cp_s + p.cp_l));
+    c.wrr1 = (R)(rr / 9.0);
+    c.wrr5 = (R)(rr / 36.0);
+    c.rr_rest = (R)(rr * 5.0 / 9.0);
+  }
   c.readings = p.readings;
   return c;
 }

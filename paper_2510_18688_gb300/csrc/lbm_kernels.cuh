@@ -47,6 +47,10 @@ static_assert(RING * NPART <= NT, "ring loads must fit one pass of the CTA");
 enum { BC_PERIODIC = 0, BC_DIRICHLET = 1, BC_ADIABATIC = 2 };
 enum { LAT_FLOW = 1, LAT_PHASE = 2, LAT_HEAT = 4 };
 enum { LAG_FL = 0, LAG_W, LAG_P, LAG_PHUX, LAG_PHUY, LAG_Q, NLAG };
+// Contexts with float arithmetic (FP32, FP16 storage) keep one more lag plane
+// after these: the temperature of the previous step, the reference of their
+// well-balanced enthalpy storage (see kShift).
+constexpr int LAG_T = NLAG;
 enum { F_PHI = 0, F_FS, F_FL, F_T, F_RHOH, F_P, F_UX, F_UY, F_RHO, F_MU, F_W, F_MDOT };
 enum { MODE_STEP = 0, MODE_READ = 1 };
 
@@ -86,7 +90,9 @@ struct Coef {
   R rr3;         // rho_ref Cp_ref cs^2 (Eq. (26))
   R inv_rr3;     // 1 / rr3
   R inv_tau_g;   // 1 / tau_g
-  uint32_t readings;
+  R wrr1, wrr5;  // w_i rho_ref Cp_ref of the axes and of the diagonals
+  R rr_rest;     // (1 - w_0) rho_ref Cp_ref
+  uint32_t readings;  // must stay the last member
 };
 
 struct Geom {
@@ -221,23 +227,81 @@ __device__ __forceinline__ void stp(float* p, float v) { *p = v; }
 __device__ __forceinline__ void stp(double* p, double v) { *p = v; }
 __device__ __forceinline__ void stp(__half* p, float v) { *p = __float2half_rn(v); }
 
-// With FP16 storage the rest populations g0 and h0, which carry the order
-// parameter and the enthalpy (values of order 1 to 10), are stored as
-// differences from references that the writer and the next reader of the
-// same node both hold in FP32: 2 w - 1 + phi0 (= phi where w is not
-// clamped) for g0 and w rho_l L fl (the latent part of rho H, Eq. (8)) for
-// h0, from the lag fields w, fl written with them.  FP16 then holds only the
-// small remainders.  Other populations and other storage types: no shift.
-template <typename S>
-constexpr bool kShiftRest = std::is_same<S, __half>::value;
+// Well-balanced storage of float states (FP32 and FP16 storage).  Every
+// population that carries a large, slowly varying part is stored -- and
+// handled in the arithmetic of the step -- as its difference from a
+// reference that the writer and the next reader compute identically from
+// the lag fields:
+//
+//   g0       2 w - 1 + phi0 (= phi where w is not clamped), the bulk of the
+//            rest population phi + (w_0 - 1) eta mu of Eq. (19);
+//   h_i      w_i rho_ref Cp_ref T' (i > 0), h0 ell fl' + (C' - (1 - w_0)
+//            rho_ref Cp_ref) T': the equilibrium of Eq. (25) at rest at the
+//            node's own previous state (T', fl', w', C' = rho Cp of
+//            Eq. (10) there, ell = w' rho_l L); the h_i are referred to
+//            the node they are streamed TO, whose new temperature the
+//            writer holds in shared memory, the reader its own lag T;
+//   f_i      3 (w_i - delta_i0) p' of the node they are streamed FROM
+//            (the node itself for a population returned by a wall), the
+//            pressure part of Eq. (14); the reader has that lagged
+//            pressure for its stencil of Eq. (17).
+//
+// Stored as they are, a step's small change of h0 ~ rho H ~ 10, of h_i ~
+// w_i T or of f_i ~ w_i p falls below half an ulp of float and is lost, so a
+// slowly freezing or warming region drifts and the small velocity of the
+// volume change is buried under the pressure.  Relative to the references
+// only the small remainders are rounded; a change of reference enters as a
+// difference of two references (exact in float when they are close).  The
+// FP64 and tangent steps keep the populations as they are.
+template <typename R>
+constexpr bool kShift = std::is_same<R, float>::value;
 
+// The references are formed with explicitly rounded operations
+// (__fmul_rn, __fadd_rn, which the compiler never contracts into a fused
+// multiply-add), so that every evaluation -- by the writer, by the next
+// reader, in any kernel variant -- gives the same float.
 template <typename R>
 __device__ __forceinline__ R rest_ref_g(R w, R phi0) {
   return R(2) * w - R(1) + phi0;
 }
+__device__ __forceinline__ float rest_ref_g(float w, float phi0) {
+  return __fadd_rn(__fadd_rn(__fmul_rn(2.f, w), -1.f), phi0);
+}
+// latent capacity ell = w rho_l L (Eq. (8) with reading R-T1)
 template <typename R>
-__device__ __forceinline__ R rest_ref_h(const Coef<R>& c, R w, R fl) {
-  return w * c.rho_l * c.latent * fl;
+__device__ __forceinline__ R latent_cap(const Coef<R>& c, R w) {
+  return w * c.rho_l * c.latent;
+}
+__device__ __forceinline__ float latent_cap(const Coef<float>& c, float w) {
+  return __fmul_rn(__fmul_rn(w, c.rho_l), c.latent);
+}
+// Eq. (10), explicitly rounded
+__device__ __forceinline__ float interp_rn(float fs, float w, float zs, float zl, float zg) {
+  const float a = __fsub_rn(1.f, fs);
+  return __fadd_rn(__fadd_rn(__fmul_rn(fs, zs), __fmul_rn(__fmul_rn(a, w), zl)),
+                   __fmul_rn(__fmul_rn(a, __fsub_rn(1.f, w)), zg));
+}
+// solid fraction min(phi0 + w (1 - fl), 1) and heat capacity rho Cp of a
+// state given by its weight and liquid fraction: fl = 1 gives the fully
+// liquid capacity C+ (fs = phi0), fl = 0 the fully frozen C- (fs = min(phi0
+// + w, 1)) of the inversion, bit for bit
+__device__ __forceinline__ float fs_rn(float w, float fl, float phi0) {
+  return fminf(__fadd_rn(phi0, __fmul_rn(w, __fsub_rn(1.f, fl))), 1.f);
+}
+__device__ __forceinline__ float cap_rn(const Coef<float>& c, float fs, float w) {
+  return __fmul_rn(interp_rn(fs, w, c.rho_s, c.rho_l, c.rho_g),
+                   interp_rn(fs, w, c.cp_s, c.cp_l, c.cp_g));
+}
+// reference of h0: ell fl + (C - (1 - w_0) rho_ref Cp_ref) T
+__device__ __forceinline__ float ref_h0(const Coef<float>& c, float w, float fl, float T,
+                                        float C) {
+  return __fadd_rn(__fmul_rn(latent_cap(c, w), fl), __fmul_rn(__fsub_rn(C, c.rr_rest), T));
+}
+// reference of h_i, i > 0: w_i rho_ref Cp_ref T (wrr = c.wrr1 or c.wrr5)
+__device__ __forceinline__ float ref_hi(float wrr, float T) { return __fmul_rn(wrr, T); }
+// new reference - old reference
+__device__ __forceinline__ float ref_delta(float r_new, float r_old) {
+  return __fsub_rn(r_new, r_old);
 }
 
 template <typename R>
@@ -252,9 +316,12 @@ __device__ __forceinline__ R sum_h(const R* v) {
 template <typename R>
 struct Local {
   R T, fl, mdot, rhoH, phi, w, fs, rho;
+  R rhoHr;  // rho H minus its reference (float storage), else rho H
+  R phir;   // phi minus the reference of g0 (float storage), else phi
 };
 
-// Rows a1-a2 for one node from its population sums and lag fields.
+// Rows a1-a2 for one node from its population sums and lag fields (plain
+// populations: FP64, tangent and the 3-D step).
 template <typename R>
 __device__ __forceinline__ Local<R> local_state(const Coef<R>& c, int lat, R sg, R sh, R flp,
                                                 R wp, R Qp, R phi0) {
@@ -268,11 +335,12 @@ __device__ __forceinline__ Local<R> local_state(const Coef<R>& c, int lat, R sg,
     invert_enthalpy(c, L.rhoH, wp, phi0, L.T, L.fl);
     L.mdot = c.one_m_ratio * wp * (flp - L.fl);  // Eq. (1), phase-change part
   }
+  L.rhoHr = L.rhoH;
   if (lat & LAT_PHASE) {
     // Eq. (22) solved for phi.  Without phase change the divisor is exactly
     // 1, and the FP64 step (bound by its FP64 pipe, where a division costs
     // about ten operations) skips it; a tangent still divides (the
-    // derivative of mdot need not vanish), and float division is cheap.
+    // derivative of mdot need not vanish).
     if constexpr (std::is_same<R, double>::value)
       L.phi = L.mdot == R(0) ? sg : qdiv(sg, R(1) - R(0.5) * L.mdot);
     else
@@ -282,8 +350,87 @@ __device__ __forceinline__ Local<R> local_state(const Coef<R>& c, int lat, R sg,
     L.w = wp;
     L.phi = R(2) * wp - R(1) + phi0;
   }
+  L.phir = L.phi;
   R fs = phi0 + L.w * (R(1) - L.fl);
   L.fs = fs > R(1) ? R(1) : fs;
+  L.rho = interp(L.fs, L.w, c.rho_s, c.rho_l, c.rho_g);
+  return L;
+}
+
+// Rows a1-a2 of a well-balanced float state: sg, sh are sums of the stored
+// remainders; Tp, flp, wp the node's lags, Cp its heat capacity at the lags
+// (cap_rn(fs_rn(wp, flp, phi0), wp)), so that rho H = e + ell flp + Cp Tp
+// with e = sh + Q/2 (Eq. (28)).
+//
+// Eq. (8) for such a state.  A node that was fully liquid (flp = 1) has
+// rho H - ell = e + C+ Tp; if the new temperature Tp + e / C+ stays above
+// the liquidus it is the answer, exact in float as an increment of Tp.
+// Likewise a fully frozen node (flp = 0, rho H = e + C- Tp) below the
+// solidus.  Every other node -- the ones near the melting point -- takes the
+// branch test, the liquid fraction and its clamp to [0, 1] in FP64 and
+// rounds once.
+__device__ __forceinline__ Local<float> local_state_wb(const Coef<float>& c, int lat, float sg,
+                                                       float sh, float flp, float wp, float Qp,
+                                                       float Tp, float Cp, float phi0) {
+  Local<float> L;
+  L.T = 0.f;
+  L.fl = flp;
+  L.rhoH = 0.f;
+  L.rhoHr = 0.f;
+  L.mdot = 0.f;
+  if (lat & LAT_HEAT) {
+    const float e = sh + 0.5f * Qp;
+    const float ell = latent_cap(c, wp);
+    L.rhoHr = e;
+    bool done = false;
+    if (flp == 1.f) {  // Cp is C+ here
+      const float T1 = Tp + qdiv(e, Cp);
+      if (T1 > 0.f) {
+        L.T = T1;
+        L.fl = 1.f;
+        done = true;
+      }
+    } else if (flp == 0.f) {  // Cp is C- here
+      const float T1 = Tp + qdiv(e, Cp);
+      if (T1 < 0.f) {
+        L.T = T1;
+        L.fl = 0.f;
+        done = true;
+      }
+    }
+    if (!done) {
+      const double rH = (double)e + (double)ell * (double)flp + (double)Cp * (double)Tp;
+      const double ld = (double)ell;
+      if (rH < 0.0) {
+        L.fl = 0.f;
+        L.T = (float)(rH / (double)cap_rn(c, fs_rn(wp, 0.f, phi0), wp));
+      } else if (rH > ld) {
+        L.fl = 1.f;
+        L.T = (float)((rH - ld) / (double)cap_rn(c, phi0, wp));
+      } else {
+        double f = ld > 0.0 ? rH / ld : 1.0;
+        f = f < 0.0 ? 0.0 : (f > 1.0 ? 1.0 : f);
+        L.fl = (float)f;
+        L.T = 0.f;
+      }
+    }
+    L.rhoH = e + (ell * flp + Cp * Tp);
+    L.mdot = c.one_m_ratio * wp * (flp - L.fl);  // Eq. (1), phase-change part
+  }
+  if (lat & LAT_PHASE) {
+    // Eq. (22) solved for phi, relative to r0 = 2 wp - 1 + phi0:
+    // phi - r0 = (sum g' + mdot r0 / 2) / (1 - mdot / 2), and the weight
+    // (1 - phi0 + phi) / 2 = wp + (phi - r0) / 2
+    const float r0 = rest_ref_g(wp, phi0);
+    L.phir = qdiv(sg + 0.5f * L.mdot * r0, 1.f - 0.5f * L.mdot);
+    L.phi = r0 + L.phir;
+    L.w = clamp01(wp + 0.5f * L.phir);
+  } else {
+    L.w = wp;
+    L.phi = 2.f * wp - 1.f + phi0;
+    L.phir = 0.f;
+  }
+  L.fs = fs_rn(L.w, L.fl, phi0);
   L.rho = interp(L.fs, L.w, c.rho_s, c.rho_l, c.rho_g);
   return L;
 }
@@ -557,15 +704,23 @@ __global__ void __launch_bounds__(NT) lbm_init_kernel(const InitArgs<R, S> a) {
   const R C = heat_cap(c, fs, w);
   const R rrC = qdiv(c.rr, C);
   const R emu = c.eta * muphi;
-  const R sg0 = kShiftRest<S> ? rest_ref_g(w, q0) : R(0);
-  const R sh0 = kShiftRest<S> ? rest_ref_h(c, w, fl) : R(0);
+  // float states: the remainders of the well-balanced storage (kShift),
+  // referred to this node's own state (streaming has not happened yet)
+  R sg0 = R(0), sh0 = R(0), sha = R(0), shd = R(0);
+  if constexpr (kShift<R>) {
+    sg0 = rest_ref_g(w, q0);
+    sh0 = ref_h0(c, w, fl, T, cap_rn(c, fs_rn(w, fl, q0), w));
+    sha = ref_hi(c.wrr1, T);
+    shd = ref_hi(c.wrr5, T);
+  }
 #pragma unroll
   for (int i = 0; i < 9; i++) {
     stp(a.pout + i * P + n, R(0));
     stp(a.pout + (9 + i) * P + n,
         (i == 0) ? phi + (qw<R>(0) - R(1)) * emu - sg0 : qw<R>(i) * emu);
     stp(a.pout + (18 + i) * P + n,
-        heq_i<R>(i, rhoH, C, T, c.rr, rrC, R(0), R(0), R(0)) - (i == 0 ? sh0 : R(0)));
+        heq_i<R>(i, rhoH, C, T, c.rr, rrC, R(0), R(0), R(0)) -
+            (i == 0 ? sh0 : (i <= 4 ? sha : shd)));
   }
   a.lout[LAG_FL * P + n] = fl;
   a.lout[LAG_W * P + n] = w;
@@ -573,6 +728,7 @@ __global__ void __launch_bounds__(NT) lbm_init_kernel(const InitArgs<R, S> a) {
   a.lout[LAG_PHUX * P + n] = R(0);
   a.lout[LAG_PHUY * P + n] = R(0);
   a.lout[LAG_Q * P + n] = R(0);
+  if constexpr (kShift<R>) a.lout[LAG_T * P + n] = T;
   a.phi0_out[n] = q0;
   if (a.mask_out) a.mask_out[n] = a.mask ? (a.mask[d] != 0) : 0;
 }

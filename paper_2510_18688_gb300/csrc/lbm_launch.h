@@ -19,7 +19,6 @@ inline dim3 grid_dims(const Geom& g) {
 cudaError_t launch_step_f32(const Args<float>& a, int mode, bool diag, cudaStream_t s);
 cudaError_t launch_step_f64(const Args<double>& a, int mode, bool diag, cudaStream_t s);
 // Two-kernel form of MODE_STEP (macro pass, then collide pass).
-cudaError_t launch_split_f32(const SplitArgs<float>& a, bool diag, cudaStream_t s);
 cudaError_t launch_split_f64(const SplitArgs<double>& a, bool diag, cudaStream_t s);
 cudaError_t launch_init_f32(const InitArgs<float>& a, cudaStream_t s);
 // FP16 population storage, FP32 arithmetic.

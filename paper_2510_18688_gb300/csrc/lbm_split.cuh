@@ -13,7 +13,10 @@
 //
 // Neither kernel uses shared memory for the stencil nor a CTA barrier on its
 // main path, and the halo is not recomputed: each node's macros are computed
-// once.  One thread per node; CTA = 32 x 8 nodes.
+// once.  One thread per node; CTA = 32 x 8 nodes.  Plain (FP64) populations
+// only: the well-balanced float storage refers the pushed enthalpy
+// populations to their destinations' new temperatures, which this form
+// would have to write out and read back.
 #pragma once
 
 #include "lbm_kernels.cuh"
@@ -31,6 +34,7 @@ struct SplitArgs {
 
 template <typename R, int LATC>
 __global__ void __launch_bounds__(NT) lbm_macro_kernel(const SplitArgs<R> s) {
+  static_assert(!kShift<R>, "the two-kernel step takes plain populations only");
   const Args<R>& a = s.a;
   const Geom& g = a.g;
   const Coef<R>& c = a.c;
@@ -218,8 +222,8 @@ __global__ void __launch_bounds__(NT, sizeof(R) == 4 ? LBM_MIN_BLOCKS_F32 : 1)
       for (int i = 0; i < 9; i++) gq[i] = pn[(9 + i) * P];
       const R phuxp = a.lin[LAG_PHUX * P + n];
       const R phuyp = a.lin[LAG_PHUY * P + n];
-      if (inner) collide_phase<R, true>(g, c, out + 9 * P, P, gx, gy, n, gq, phi, mdot, phuxp, phuyp, M, R(0));
-      else collide_phase<R, false>(g, c, out + 9 * P, P, gx, gy, n, gq, phi, mdot, phuxp, phuyp, M, R(0));
+      if (inner) collide_phase<R, true>(g, c, out + 9 * P, P, gx, gy, n, gq, phi, phi, mdot, phuxp, phuyp, M, R(0));
+      else collide_phase<R, false>(g, c, out + 9 * P, P, gx, gy, n, gq, phi, phi, mdot, phuxp, phuyp, M, R(0));
     }
     if (lat & LAT_HEAT) {
       R hq[9];

@@ -121,13 +121,15 @@ __device__ __forceinline__ void collide_flow(const Geom& g, const Coef<R>& c, S*
   }
 }
 
-// Phase-field collision Eqs. (18)-(20) and push.
-// rest0: subtracted from the stored rest population (FP16 storage shift).
+// Phase-field collision Eqs. (18)-(20) and push.  gq[0] and phir are the
+// rest population and phi relative to the reader's reference (kShift), and
+// dref = new reference - old reference is taken off the stored rest
+// population (all three are the plain values, and dref = 0, otherwise).
 template <typename R, bool INNER, typename S>
 __device__ __forceinline__ void collide_phase(const Geom& g, const Coef<R>& c,
                                               S* __restrict__ out, int P, int x, int y, int n,
-                                              const R* gq, R phi, R mdot, R phuxp, R phuyp,
-                                              const Macro<R>& M, R rest0) {
+                                              const R* gq, R phi, R phir, R mdot, R phuxp,
+                                              R phuyp, const Macro<R>& M, R dref) {
   const R itg = c.inv_tau_g;
   const R omg = R(1) - itg;
   const R gcoef = R(1) - R(0.5) * itg;
@@ -138,9 +140,9 @@ __device__ __forceinline__ void collide_phase(const Geom& g, const Coef<R>& c,
   const R Vx = R(3) * (itg * M.phux + gcoef * (M.phux - phuxp));
   const R Vy = R(3) * (itg * M.phuy + gcoef * (M.phuy - phuyp));
   {
-    const R geq0 = phi + (qw<R>(0) - R(1)) * emu;
+    const R geq0 = phir + (qw<R>(0) - R(1)) * emu;
     push<R, INNER, false>(g, c, out, P, 0, x, y, n,
-                          gq[0] * omg + itg * geq0 + gcoef * qw<R>(0) * phi * mdot - rest0);
+                          gq[0] * omg + itg * geq0 + gcoef * qw<R>(0) * phi * mdot - dref);
   }
 #pragma unroll
   for (int i = 1; i <= 8; i++) {
@@ -154,11 +156,13 @@ __device__ __forceinline__ void collide_phase(const Geom& g, const Coef<R>& c,
   }
 }
 
-// Enthalpy TRT collision Eqs. (23)-(27) and push.
+// Enthalpy TRT collision Eqs. (23)-(27) and push.  h[0] and rhoHr are the
+// rest population and rho H relative to the reader's reference (kShift);
+// dref as in collide_phase.
 template <typename R, bool INNER, typename S>
 __device__ __forceinline__ void collide_heat(const Geom& g, const Coef<R>& c, S* __restrict__ out,
                                              int P, int x, int y, int n, const R* h, R fs, R w,
-                                             R T, R rhoH, R mdot, const Macro<R>& M, R rest0) {
+                                             R T, R rhoHr, R mdot, const Macro<R>& M, R dref) {
   const R lam = interp(fs, w, c.lam_s, c.lam_l, c.lam_g);
   const R taua = R(0.5) + lam * c.inv_rr3;
   // magic relation of the TRT (Eq. (27)): 1/tau_s + 1/tau_a = 2
@@ -169,9 +173,9 @@ __device__ __forceinline__ void collide_heat(const Geom& g, const Coef<R>& c, S*
   const R rrT = c.rr * T;
   {
     // rest population: purely symmetric
-    const R heq0 = rhoH - rrT + qw<R>(0) * (rrT - CT * M.uu * R(1.5));
+    const R heq0 = rhoHr - rrT + qw<R>(0) * (rrT - CT * M.uu * R(1.5));
     push<R, INNER, true>(g, c, out, P, 0, x, y, n,
-                         h[0] - (h[0] - heq0) * is + qw<R>(0) * Hsrc - rest0);
+                         h[0] - (h[0] - heq0) * is + qw<R>(0) * Hsrc - dref);
   }
 #pragma unroll
   for (int i = 1; i <= 8; i++) {
@@ -186,6 +190,145 @@ __device__ __forceinline__ void collide_heat(const Geom& g, const Coef<R>& c, S*
     const R Ds = (hs - es) * is - wi * Hsrc;
     push<R, INNER, true>(g, c, out, P, i, x, y, n, h[i] - Da - Ds);
     push<R, INNER, true>(g, c, out, P, o, x, y, n, h[o] + Da - Ds);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// well-balanced float storage (kShift; see lbm_kernels.cuh)
+// ---------------------------------------------------------------------------
+
+// True when the node upstream of (x, y) in direction i, (x, y) - c_i, lies
+// beyond a wall: population i of (x, y) then came back from (x, y) itself.
+__device__ __forceinline__ bool upstream_wall(const Geom& g, int x, int y, int i) {
+  const int tx = x - qx(i), ty = y - qy(i);
+  return (tx < 0 && g.bc[0] != BC_PERIODIC) || (tx >= g.nx && g.bc[1] != BC_PERIODIC) ||
+         (ty < 0 && g.bc[2] != BC_PERIODIC) || (ty >= g.ny && g.bc[3] != BC_PERIODIC);
+}
+
+// Flow collision Eqs. (11), (14)-(16) and push for remainders: fr[i] = f_i -
+// 3 (w_i - delta_i0) p_src(i), dps[i] = p_src(i) - p (p = M.pr, the node's new
+// pressure, which the stored remainders are referred to).  The pressure
+// part of the equilibrium and the references then meet as 3 (w_i -
+// delta_i0) (p_src(i) - p) (1 - 1/tau): f*_i - 3 (w_i - delta_i0) p =
+// (1 - 1/tau) (fr_i + 3 (w_i - delta_i0) dps_i) + rho s_i / tau + (1 -
+// 1/2tau) F_i.
+template <bool INNER, typename S>
+__device__ __forceinline__ void collide_flow_wb(const Geom& g, const Coef<float>& c,
+                                                S* __restrict__ out, int P, int x, int y, int n,
+                                                const float* fr, const float* dps, float rho,
+                                                const Macro<float>& M) {
+  const float itau = qdiv(1.f, M.tauf);
+  const float omi = 1.f - itau;
+  const float fcoef = 1.f - 0.5f * itau;
+  const bool iso = (c.readings & 1u) != 0;
+  const float sym0 = rho * (-1.5f * M.uu);
+  const float fsym0 = M.S - 3.f * M.uFt;
+  {
+    float F0 = fsym0;
+    if (iso) F0 += M.S * (0.f - 2.f / 3.f) * 1.5f;
+    const float base = fr[0] + 3.f * (qw<float>(0) - 1.f) * dps[0];
+    push<float, INNER, false>(g, c, out, P, 0, x, y, n,
+                              base * omi + itau * (qw<float>(0) * sym0) +
+                                  fcoef * qw<float>(0) * F0);
+  }
+#pragma unroll
+  for (int i = 1; i <= 8; i++) {
+    if (i == 3 || i == 4 || i == 7 || i == 8) continue;  // handled with its pair
+    const int o = qopp(i);
+    const float wi = qw<float>(i);
+    const float cu = float(qx(i)) * M.ux + float(qy(i)) * M.uy;
+    const float cF = float(qx(i)) * M.Gx + float(qy(i)) * M.Gy;
+    const float cFt = float(qx(i)) * M.Ftx + float(qy(i)) * M.Fty;
+    const float eqS = rho * (4.5f * cu * cu) + sym0;
+    const float eqA = rho * (3.f * cu);
+    float srcS = fsym0 + 9.f * cu * cFt;
+    if (iso) srcS += M.S * (float(qx(i) * qx(i) + qy(i) * qy(i)) - 2.f / 3.f) * 1.5f;
+    const float srcA = 3.f * cF;
+    const float Ps = wi * (itau * eqS + fcoef * srcS);
+    const float Pa = wi * (itau * eqA + fcoef * srcA);
+    const float bi = fr[i] + 3.f * wi * dps[i], bo = fr[o] + 3.f * wi * dps[o];
+    push<float, INNER, false>(g, c, out, P, i, x, y, n, bi * omi + Ps + Pa);
+    push<float, INNER, false>(g, c, out, P, o, x, y, n, bo * omi + Ps - Pa);
+  }
+}
+
+// Store of an enthalpy remainder X (the post-collision population minus the
+// writer's old reference ref_old = w_i rho_ref Cp_ref T') referred to the
+// destination's new reference w_i rho_ref Cp_ref T_dest (T_self for a
+// population a wall returns).  Anti-bounce-back at a Dirichlet wall:
+// -h* + 2 w_i rho_ref Cp_ref T_w, as remainder -X + (wTw - ref_old) + (wTw
+// - ref_new).
+template <bool INNER, typename S>
+__device__ __forceinline__ void push_h(const Geom& g, const Coef<float>& c, S* __restrict__ plane0,
+                                       int P, int i, int x, int y, int n, float X, float ref_old,
+                                       float wrr, float T_self, float T_dest) {
+  if (INNER) {
+    stp(plane0 + i * P + n + qy(i) * g.pitch + qx(i),
+        X - ref_delta(ref_hi(wrr, T_dest), ref_old));
+  } else {
+    int wall;
+    const long long t = stream_target(g, x, y, qx(i), qy(i), wall);
+    if (t >= 0) {
+      stp(plane0 + i * P + (int)t, X - ref_delta(ref_hi(wrr, T_dest), ref_old));
+    } else {
+      const float rn = ref_hi(wrr, T_self);
+      float v;
+      if (g.bc[wall] == BC_DIRICHLET) {
+        const float wTw = ref_hi(wrr, c.T_wall[wall]);
+        v = -X + (ref_delta(wTw, ref_old) + ref_delta(wTw, rn));
+      } else {
+        v = X - ref_delta(rn, ref_old);
+      }
+      stp(plane0 + qopp(i) * P + n, v);
+    }
+  }
+}
+
+// Enthalpy TRT collision Eqs. (23)-(27) and push for remainders: hr[i] = h_i
+// minus the node's old references (ref_h0 for i = 0, aold = w_1 rho_ref
+// Cp_ref T' on the axes, dold = w_5 rho_ref Cp_ref T' on the diagonals),
+// e = rho H minus the sum of those references, dT = T - T'.  With these the
+// non-equilibrium parts are h0 - heq0 = hr0 - e + (1 - w_0) rho_ref Cp_ref
+// dT + 3/2 w_0 C T u.u and, for a pair, hs - es = hs' - w_i (rho_ref Cp_ref
+// dT + C T (9/2 (c.u)^2 - 3/2 u.u)); the rest remainder takes off dref0 =
+// new ref_h0 - old ref_h0, the others are referred to their destinations
+// (push_h).  sT: new temperatures of the tile and its ring, hc: own index.
+template <bool INNER, typename S>
+__device__ __forceinline__ void collide_heat_wb(const Geom& g, const Coef<float>& c,
+                                                S* __restrict__ out, int P, int x, int y, int n,
+                                                const float* hr, float fs, float w, float T,
+                                                float dT, float e, float mdot,
+                                                const Macro<float>& M, float aold, float dold,
+                                                float dref0, const float* sT, int hc) {
+  const float lam = interp(fs, w, c.lam_s, c.lam_l, c.lam_g);
+  const float taua = 0.5f + lam * c.inv_rr3;
+  // magic relation of the TRT (Eq. (27)): 1/tau_s + 1/tau_a = 2
+  const float ia = qdiv(1.f, taua), is = 2.f - ia;
+  const float hcoef = 1.f - 0.5f * ia;
+  const float CT = M.cap * T;
+  const float Hsrc = hcoef * CT * mdot;
+  const float rrdT = c.rr * dT;
+  {
+    const float d0 = hr[0] - e + c.rr_rest * dT + 1.5f * qw<float>(0) * CT * M.uu;
+    stp(out + n, hr[0] - d0 * is + qw<float>(0) * Hsrc - dref0);
+  }
+#pragma unroll
+  for (int i = 1; i <= 8; i++) {
+    if (i == 3 || i == 4 || i == 7 || i == 8) continue;
+    const int o = qopp(i);
+    const float wi = qw<float>(i);
+    const float cu = float(qx(i)) * M.ux + float(qy(i)) * M.uy;
+    const float es = wi * (rrdT + CT * (4.5f * cu * cu - 1.5f * M.uu));
+    const float ea = wi * (CT * (3.f * cu));
+    const float hs = 0.5f * (hr[i] + hr[o]), ha = 0.5f * (hr[i] - hr[o]);
+    const float Da = (ha - ea) * ia;
+    const float Ds = (hs - es) * is - wi * Hsrc;
+    const float ro = i <= 4 ? aold : dold;
+    const float wrr = i <= 4 ? c.wrr1 : c.wrr5;
+    push_h<INNER>(g, c, out, P, i, x, y, n, hr[i] - Da - Ds, ro, wrr, T,
+                  sT[hc + qy(i) * HX + qx(i)]);
+    push_h<INNER>(g, c, out, P, o, x, y, n, hr[o] + Da - Ds, ro, wrr, T,
+                  sT[hc + qy(o) * HX + qx(o)]);
   }
 }
 
@@ -211,6 +354,12 @@ __device__ __forceinline__ void step_tile(const Args<R, S>& a, int bx, int by, i
   __shared__ R s_phi[HN], s_fs[HN], s_rho[HN], s_p[HN], s_phi0[HN];
   __shared__ R s_rsg[RING][NPART], s_rsh[RING][NPART];
   __shared__ R s_rfl[RING], s_rw[RING], s_rQ[RING];
+  // well-balanced float storage: new temperatures of the tile and its ring
+  // (references of the pushed enthalpy populations), lagged temperatures of
+  // the ring and the own node's old temperature and heat capacity
+  constexpr bool WB = kShift<R>;
+  __shared__ R s_T[WB ? HN : 1], s_rT[WB ? RING : 1];
+  __shared__ R s_Tp[WB && STASH ? 2 : 1][NT];
   __shared__ int s_rmask[RING];
   __shared__ R s_red[NT / 32][NDIAG];
 
@@ -248,6 +397,7 @@ __device__ __forceinline__ void step_tile(const Args<R, S>& a, int bx, int by, i
       s_rfl[k] = a.lin[LAG_FL * P + m];
       s_rw[k] = a.lin[LAG_W * P + m];
       s_rQ[k] = a.lin[LAG_Q * P + m];
+      if constexpr (WB) s_rT[k] = a.lin[LAG_T * P + m];
       s_rmask[k] = masked ? 1 : 0;
     } else if (part == 1) {
       if (lat & LAT_PHASE) sgp = ldp(pm + 15 * P) + ldp(pm + 16 * P) + ldp(pm + 17 * P);
@@ -298,36 +448,46 @@ __device__ __forceinline__ void step_tile(const Args<R, S>& a, int bx, int by, i
 #pragma unroll
     for (int i = 0; i < 9; i++) v[i] = ld_pop<STASH>(pn + (9 + i) * P);
     sg = sum_g(v);
-    if (kShiftRest<S>) {
-      const R r0 = rest_ref_g(wp, phi0);
-      sg += r0;
-      v[0] += r0;
-    }
     if (STASH) {
 #pragma unroll
       for (int i = 0; i < 9; i++) s_pop[i][tid] = v[i];
+    }
+  }
+  // well-balanced float storage: the node's lagged temperature and its heat
+  // capacity at the lags (the reference state of its enthalpy populations)
+  R Tp = R(0), Cp = R(0);
+  if constexpr (WB) {
+    if (lat & LAT_HEAT) {
+      Tp = a.lin[LAG_T * P + n];
+      Cp = cap_rn(c, fs_rn(wp, flp, phi0), wp);
+      if (STASH) {
+        s_Tp[0][tid] = Tp;
+        s_Tp[STASH ? 1 : 0][tid] = Cp;
+      }
     }
   }
   if (lat & LAT_HEAT) {
     R v[9];
     if (masked) {
       cold_mask_h(c, wp, phi0, v);
+      if constexpr (WB) {
+        v[0] -= ref_h0(c, wp, flp, Tp, Cp);
+#pragma unroll
+        for (int i = 1; i < 9; i++) v[i] -= ref_hi(i <= 4 ? c.wrr1 : c.wrr5, Tp);
+      }
     } else {
 #pragma unroll
       for (int i = 0; i < 9; i++) v[i] = ld_pop<STASH>(pn + (18 + i) * P);
     }
     sh = sum_h(v);
-    if (kShiftRest<S> && !masked) {
-      const R r0 = rest_ref_h(c, wp, flp);
-      sh += r0;
-      v[0] += r0;
-    }
     if (STASH) {
 #pragma unroll
       for (int i = 0; i < 9; i++) s_pop[STASH ? 9 + i : 0][tid] = v[i];
     }
   }
-  const Local<R> L = local_state(c, lat, sg, sh, flp, wp, Qp, phi0);
+  Local<R> L;
+  if constexpr (WB) L = local_state_wb(c, lat, sg, sh, flp, wp, Qp, Tp, Cp, phi0);
+  else L = local_state(c, lat, sg, sh, flp, wp, Qp, phi0);
   {
     const int hi = (ty + 1) * HX + (tx + 1);
     s_phi[hi] = L.phi;
@@ -335,6 +495,7 @@ __device__ __forceinline__ void step_tile(const Args<R, S>& a, int bx, int by, i
     s_rho[hi] = L.rho;
     s_p[hi] = pp;
     s_phi0[hi] = phi0;
+    if constexpr (WB) s_T[hi] = L.T;
   }
   __syncthreads();
 
@@ -346,27 +507,43 @@ __device__ __forceinline__ void step_tile(const Args<R, S>& a, int bx, int by, i
     const int hi = hy * HX + hx;
     const R q0 = s_phi0[hi];
     const R wq = s_rw[k];
-    R sgq = s_rsg[k][0] + s_rsg[k][1];
-    if (kShiftRest<S>) sgq += rest_ref_g(wq, q0);
+    const R sgq = s_rsg[k][0] + s_rsg[k][1];
+    R Tq = R(0), Cq = R(0);
+    if constexpr (WB) {
+      if (lat & LAT_HEAT) {
+        Tq = s_rT[k];
+        Cq = cap_rn(c, fs_rn(wq, s_rfl[k], q0), wq);
+      }
+    }
     R shq;
     if ((lat & LAT_HEAT) && s_rmask[k]) {
       R hq[9];
       cold_mask_h(c, wq, q0, hq);
+      if constexpr (WB) {
+        hq[0] -= ref_h0(c, wq, s_rfl[k], Tq, Cq);
+#pragma unroll
+        for (int i = 1; i < 9; i++) hq[i] -= ref_hi(i <= 4 ? c.wrr1 : c.wrr5, Tq);
+      }
       shq = sum_h(hq);
     } else {
       shq = s_rsh[k][1] + s_rsh[k][2];
-      if (kShiftRest<S>) shq += rest_ref_h(c, wq, s_rfl[k]);
     }
-    const Local<R> Lq = local_state(c, lat, sgq, shq, s_rfl[k], wq, s_rQ[k], q0);
+    Local<R> Lq;
+    if constexpr (WB) Lq = local_state_wb(c, lat, sgq, shq, s_rfl[k], wq, s_rQ[k], Tq, Cq, q0);
+    else Lq = local_state(c, lat, sgq, shq, s_rfl[k], wq, s_rQ[k], q0);
     s_phi[hi] = Lq.phi;
     s_fs[hi] = Lq.fs;
     s_rho[hi] = Lq.rho;
+    if constexpr (WB) s_T[hi] = Lq.T;
   }
   __syncthreads();
 
   // ---- phase B: stencils, macros, collisions, streaming -------------------
   R dvals[NDIAG];
   Macro<R> M;
+  // links that stay inside the grid need no boundary logic
+  const bool inner = gx > 0 && gx < g.nx - 1 && gy > 0 && gy < g.ny - 1;
+  R dps[WB ? 9 : 1];  // well-balanced flow storage: p_src(i) - p
   if (valid) {
     const int hc = (ty + 1) * HX + (tx + 1);
     // isotropic stencils (reading R-FD): grad = 3 sum w_i c_i chi(x + c_i),
@@ -418,9 +595,24 @@ __device__ __forceinline__ void step_tile(const Args<R, S>& a, int bx, int by, i
     }
     if (lat & LAT_FLOW) {
       const R mu = interp(fs, L.w, c.mu_s, c.mu_l, c.mu_g);
-      const R jx = (f[1] - f[3]) + (f[5] - f[6]) + (f[8] - f[7]);
-      const R jy = (f[2] - f[4]) + (f[5] + f[6]) - (f[7] + f[8]);
-      const R snz = (f[1] + f[2] + f[3] + f[4]) + (f[5] + f[6] + f[7] + f[8]);
+      R jx = (f[1] - f[3]) + (f[5] - f[6]) + (f[8] - f[7]);
+      R jy = (f[2] - f[4]) + (f[5] + f[6]) - (f[7] + f[8]);
+      R snz = (f[1] + f[2] + f[3] + f[4]) + (f[5] + f[6] + f[7] + f[8]);
+      if constexpr (WB) {
+        // the stored f are remainders over 3 (w_i - delta_i0) p_src(i), the
+        // lagged pressure of the node each came from (the node itself for a
+        // population a wall returned): add the references' moments
+        dps[0] = pp;
+#pragma unroll
+        for (int i = 1; i < 9; i++)
+          dps[i] = (!inner && upstream_wall(g, gx, gy, i)) ? pp
+                                                           : s_p[hc - qy(i) * HX - qx(i)];
+        const R w1 = qw<R>(1), w5 = qw<R>(5);
+        jx += R(3) * (w1 * (dps[1] - dps[3]) + w5 * ((dps[5] - dps[6]) + (dps[8] - dps[7])));
+        jy += R(3) * (w1 * (dps[2] - dps[4]) + w5 * ((dps[5] + dps[6]) - (dps[7] + dps[8])));
+        snz += R(3) * (w1 * ((dps[1] + dps[2]) + (dps[3] + dps[4])) +
+                       w5 * ((dps[5] + dps[6]) + (dps[7] + dps[8])));
+      }
       // Eq. (17a,b) with the penalty force f = fs (u_s - u*), u_s = 0
       const R irho = qdiv(R(1), rho);
       const R usx = (jx + R(0.5) * Fx) * irho, usy = (jy + R(0.5) * Fy) * irho;
@@ -442,10 +634,17 @@ __device__ __forceinline__ void step_tile(const Args<R, S>& a, int bx, int by, i
       const R s0 = qw<R>(0) * (-M.uu * R(1.5));
       M.pr = (R(1) / R(3)) / (R(1) - qw<R>(0)) *
              (snz + R(0.5) * M.S + (M.tauf - R(0.5)) * F0 + rho * s0);  // Eq. (17c)
+      if constexpr (WB) {
+#pragma unroll
+        for (int i = 0; i < 9; i++) dps[i] -= M.pr;
+      }
     }
     M.phux = phi * M.ux;
     M.phuy = phi * M.uy;
-    M.cap = rho * interp(fs, L.w, c.cp_s, c.cp_l, c.cp_g);
+    // heat capacity rho Cp (Eq. (10)); float storage forms it as the next
+    // step's reader of this node will (its reference state)
+    if constexpr (WB) M.cap = cap_rn(c, fs, L.w);
+    else M.cap = rho * interp(fs, L.w, c.cp_s, c.cp_l, c.cp_g);
     // diagnostics of this state, reduced over the warp before the
     // collisions so that none of their inputs stays live through them
     if (DIAG) {
@@ -475,12 +674,15 @@ __device__ __forceinline__ void step_tile(const Args<R, S>& a, int bx, int by, i
     const R phi = L.phi, fs = L.fs, rho = L.rho, T = L.T, mdot = L.mdot;
 
     if (MODE == MODE_STEP) {
-      // links that stay inside the grid need no boundary logic
-      const bool inner = gx > 0 && gx < g.nx - 1 && gy > 0 && gy < g.ny - 1;
       S* out = a.pout;
       if (lat & LAT_FLOW) {
-        if (inner) collide_flow<R, true>(g, c, out, P, gx, gy, n, f, rho, M);
-        else collide_flow<R, false>(g, c, out, P, gx, gy, n, f, rho, M);
+        if constexpr (WB) {
+          if (inner) collide_flow_wb<true>(g, c, out, P, gx, gy, n, f, dps, rho, M);
+          else collide_flow_wb<false>(g, c, out, P, gx, gy, n, f, dps, rho, M);
+        } else {
+          if (inner) collide_flow<R, true>(g, c, out, P, gx, gy, n, f, rho, M);
+          else collide_flow<R, false>(g, c, out, P, gx, gy, n, f, rho, M);
+        }
       }
       if (lat & LAT_PHASE) {
         R gq[9];
@@ -490,10 +692,11 @@ __device__ __forceinline__ void step_tile(const Args<R, S>& a, int bx, int by, i
           phuxp = s_phu[0][tid];
           phuyp = s_phu[STASH ? 1 : 0][tid];
         }
-        // the reference the next step's reader of this node will add back
-        const R r0 = kShiftRest<S> ? rest_ref_g(L.w, phi0) : R(0);
-        if (inner) collide_phase<R, true>(g, c, out + 9 * P, P, gx, gy, n, gq, phi, mdot, phuxp, phuyp, M, r0);
-        else collide_phase<R, false>(g, c, out + 9 * P, P, gx, gy, n, gq, phi, mdot, phuxp, phuyp, M, r0);
+        // change of reference between this step's reader and the next one
+        R dref = R(0);
+        if constexpr (WB) dref = ref_delta(rest_ref_g(L.w, phi0), rest_ref_g(wp, phi0));
+        if (inner) collide_phase<R, true>(g, c, out + 9 * P, P, gx, gy, n, gq, phi, L.phir, mdot, phuxp, phuyp, M, dref);
+        else collide_phase<R, false>(g, c, out + 9 * P, P, gx, gy, n, gq, phi, L.phir, mdot, phuxp, phuyp, M, dref);
       }
       if (lat & LAT_HEAT) {
         R hq[9];
@@ -506,9 +709,23 @@ __device__ __forceinline__ void step_tile(const Args<R, S>& a, int bx, int by, i
 #pragma unroll
           for (int i = 0; i < 9; i++) hq[i] = ldp(pn + (18 + i) * P);
         }
-        const R r0 = kShiftRest<S> ? rest_ref_h(c, L.w, L.fl) : R(0);
-        if (inner) collide_heat<R, true>(g, c, out + 18 * P, P, gx, gy, n, hq, fs, L.w, T, L.rhoH, mdot, M, r0);
-        else collide_heat<R, false>(g, c, out + 18 * P, P, gx, gy, n, hq, fs, L.w, T, L.rhoH, mdot, M, r0);
+        if constexpr (WB) {
+          // references: this node's old state, and the new one its rest
+          // population is stored against
+          const R Tq = s_Tp[0][tid], Cq = s_Tp[STASH ? 1 : 0][tid];
+          const R dref0 = ref_delta(ref_h0(c, L.w, L.fl, T, M.cap), ref_h0(c, wp, flp, Tq, Cq));
+          const R aold = ref_hi(c.wrr1, Tq), dold = ref_hi(c.wrr5, Tq);
+          const int hc = (ty + 1) * HX + (tx + 1);
+          if (inner)
+            collide_heat_wb<true>(g, c, out + 18 * P, P, gx, gy, n, hq, fs, L.w, T, T - Tq,
+                                  L.rhoHr, mdot, M, aold, dold, dref0, s_T, hc);
+          else
+            collide_heat_wb<false>(g, c, out + 18 * P, P, gx, gy, n, hq, fs, L.w, T, T - Tq,
+                                   L.rhoHr, mdot, M, aold, dold, dref0, s_T, hc);
+        } else {
+          if (inner) collide_heat<R, true>(g, c, out + 18 * P, P, gx, gy, n, hq, fs, L.w, T, L.rhoHr, mdot, M, R(0));
+          else collide_heat<R, false>(g, c, out + 18 * P, P, gx, gy, n, hq, fs, L.w, T, L.rhoHr, mdot, M, R(0));
+        }
       }
       a.lout[LAG_FL * P + n] = L.fl;
       a.lout[LAG_W * P + n] = L.w;
@@ -516,6 +733,7 @@ __device__ __forceinline__ void step_tile(const Args<R, S>& a, int bx, int by, i
       a.lout[LAG_PHUX * P + n] = (lat & LAT_PHASE) ? M.phux : R(0);
       a.lout[LAG_PHUY * P + n] = (lat & LAT_PHASE) ? M.phuy : R(0);
       a.lout[LAG_Q * P + n] = (lat & LAT_HEAT) ? M.cap * T * mdot : R(0);
+      if constexpr (WB) a.lout[LAG_T * P + n] = T;
     } else {
       const long long d = (long long)gy * g.nx + gx;
       const R vals[NFIELD] = {phi, fs, L.fl, T, L.rhoH, M.pr, M.ux, M.uy, rho, M.muphi, L.w, mdot};

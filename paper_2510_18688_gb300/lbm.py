@@ -57,7 +57,7 @@ class LbmDiag(ctypes.Structure):
 EXPORTS = ("lbm_create", "lbm_set_geometry", "lbm_step", "lbm_read_fields",
            "lbm_compute_diagnostics", "lbm_read_diagnostics", "lbm_state_size",
            "lbm_save_state", "lbm_load_state", "lbm_step_count", "lbm_last_error",
-           "lbm_status_string", "lbm_destroy", "lbm_diagnostics_noalloc",
+           "lbm_status_string", "lbm_source_hash", "lbm_destroy", "lbm_diagnostics_noalloc",
            "lbm_batch_create", "lbm_batch_step", "lbm_batch_destroy", "lbm_probe_fma_rate",
            "lbm_read_crossings", "lbm_read_tangent_fields", "lbm_read_tangent_diagnostics",
            "lbm_read_crossings_tangent", "lbm_autotune", "lbm_adjoint_frozen_fraction",
@@ -96,6 +96,8 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     L.lbm_last_error.restype = ctypes.c_char_p
     L.lbm_status_string.argtypes = [ctypes.c_int]
     L.lbm_status_string.restype = ctypes.c_char_p
+    L.lbm_source_hash.argtypes = []
+    L.lbm_source_hash.restype = ctypes.c_char_p
     L.lbm_destroy.argtypes = [vp]
     L.lbm_destroy.restype = None
     L.lbm_diagnostics_noalloc.argtypes = [ctypes.POINTER(LbmParams), vp, vp, vp, vp, vp, vp]
@@ -384,6 +386,10 @@ def lbm_last_error(ctx) -> str:
 
 def lbm_status_string(status: int) -> str:
     return load().lbm_status_string(int(status)).decode()
+
+
+def lbm_source_hash() -> str:
+    return load().lbm_source_hash().decode()
 
 
 def lbm_destroy(ctx):

@@ -47,6 +47,15 @@ def _l2_rel(a, b):
     return np.linalg.norm(a - b) / nb if nb > 0 else np.linalg.norm(a)
 
 
+def _vel_l2_rel(got, ref):
+    """Relative L2 error of the velocity as one vector field (a component
+    that is zero up to round-off in the oracle, e.g. u_y of a column, has no
+    relative error of its own)."""
+    d = np.hypot(got["ux"] - ref["ux"], got["uy"] - ref["uy"])
+    n = np.linalg.norm(np.hypot(ref["ux"], ref["uy"]))
+    return np.linalg.norm(d) / n if n > 0 else np.linalg.norm(d)
+
+
 def _compare(got, ref, prec, tol=None, fields=FIELDS):
     bad = {}
     for k in fields:
@@ -54,7 +63,7 @@ def _compare(got, ref, prec, tol=None, fields=FIELDS):
             e = _max_rel(got[k], ref[k])
             t = 1e-10 if tol is None else tol
         else:
-            e = _l2_rel(got[k], ref[k])
+            e = _vel_l2_rel(got, ref) if k in ("ux", "uy") else _l2_rel(got[k], ref[k])
             t = (1e-3 if k == "mdot" else 1e-4) if tol is None else tol
         if not e <= t:
             bad[k] = e
@@ -81,11 +90,12 @@ def test_random_states(env, prec, seed, nx, ny):
     _compare(got, ref, prec)
 
 
-@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("prec", ["fp64"])
 @pytest.mark.parametrize("seed", [0, 3])
 def test_two_kernel_step(env, prec, seed, monkeypatch):
     """The two-kernel form of the step (macro pass, then collide pass),
-    selected with LBM_STEP_KERNEL=split when a context is created."""
+    selected with LBM_STEP_KERNEL=split when an FP64 context is created
+    (float contexts always take the fused step)."""
     monkeypatch.setenv("LBM_STEP_KERNEL", "split")
     got, ref = _run_pair(env, W.random_state(53, 29, seed=seed), 90, prec)
     _compare(got, ref, prec)
@@ -129,10 +139,32 @@ def test_neumann_column_full_run(env):
     _compare(got, ref, "fp64")
 
 
+def _front_and_frozen(O, f):
+    """Ice front along row 0 (crossing of w (1 - fl) through 1/2) and the
+    frozen volume sum w (1 - fl) of a field set."""
+    x_ice = O.crossings(f["phi"], f["w"], f["fl"], 0, 0)[1]
+    return x_ice, float(np.sum(f["w"] * (1.0 - f["fl"])))
+
+
+def test_neumann_column_fp32_full_run(env):
+    """400 x 4 conduction-induced freezing (Sec. 4.1), FP32 against the FP64
+    oracle for the full 20k steps: every field within 1e-4 relative L2 (the
+    velocity and pressure are zero in the oracle and must stay zero up to
+    round-off), the ice front and the frozen volume within 0.5 %."""
+    O, lbm = env
+    got, ref = _run_pair(env, W.neumann(), 20000, "fp32")
+    _compare(got, ref, "fp32", tol=1e-4)
+    (xg, vg), (xr, vr) = _front_and_frozen(O, got), _front_and_frozen(O, ref)
+    assert abs(xg - xr) <= 0.005 * xr, (xg, xr)
+    assert abs(vg - vr) <= 0.005 * vr, (vg, vr)
+
+
 def test_stefan_column_fp32(env):
-    """512 x 8 three-phase Stefan problem, FP32 against FP64, 5000 steps."""
+    """512 x 8 three-phase Stefan problem, FP32 against FP64, 5000 steps:
+    every field (the velocity as a vector: u_y is zero up to round-off in
+    the oracle)."""
     got, ref = _run_pair(env, W.stefan(), 5000, "fp32")
-    _compare(got, ref, "fp32", tol=1e-4, fields=("phi", "fs", "fl", "T", "rhoH", "rho", "w"))
+    _compare(got, ref, "fp32", tol=1e-4)
 
 
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
@@ -395,7 +427,7 @@ def test_batch_captured_periods_match_single_launches(env):
     bb.close()
 
 
-@pytest.mark.parametrize("prec", ["fp32", "fp16s"])
+@pytest.mark.parametrize("prec", ["fp32", "fp16s", "fp64"])
 def test_autotune_keeps_the_state_and_picks_a_variant(env, prec):
     """lbm_autotune times the step forms on the context's own state, restores
     that state bit for bit, and the context then steps on as before (FP32:
@@ -413,11 +445,11 @@ def test_autotune_keeps_the_state_and_picks_a_variant(env, prec):
     for k in FIELDS:
         assert np.array_equal(before[k], after[k]), k
     assert s.steps_done == 5
-    n_variants = 4 if prec == "fp32" else 2
+    n_variants = 4 if prec == "fp64" else 2  # the two-kernel form is FP64 only
     assert all(u > 0 for u in us[:n_variants]) and all(u == -1.0 for u in us[n_variants:])
     assert 0 <= chosen < n_variants and us[chosen] == min(us[:n_variants])
     s.step(40)
-    if prec == "fp32":
+    if prec != "fp16s":
         _compare(s.fields(), O.from_workload((cfg, arr)).step(45).fields(), prec)
     s.close()
 
@@ -456,24 +488,36 @@ def test_droplet_on_a_cylinder_reaches_the_closed_form_height(env):
 @pytest.mark.slow
 def test_stefan_column_fp32_full_run(env):
     """The three-phase Stefan column (512 x 8) for the full 50,000 steps, FP32
-    against the FP64 oracle: the gas-liquid interface and the ice front
-    (crossings along a row) within 0.5 % of the column's liquid height, the
-    state fields within 1e-3 relative L2."""
+    against the FP64 oracle: every field within 1e-4 relative L2, the
+    gas-liquid interface and the ice front (crossings along a row) within
+    0.5 % of the column's liquid height, the frozen volume within 0.5 %."""
     O, lbm = env
     cfg, arr = W.stefan()
     steps = 50000
     ref = O.from_workload((cfg, arr)).step(steps).fields()
     s = lbm.Solver(cfg, precision="fp32").set_geometry(arr).step(steps)
     got = s.fields()
-    errs = {k: _l2_rel(got[k], ref[k]) for k in ("phi", "fs", "fl", "T", "rhoH", "rho", "w")}
+    errs = {k: _l2_rel(got[k], ref[k]) for k in FIELDS}
+    errs["u"] = _vel_l2_rel(got, ref)
     want = O.crossings(ref["phi"], ref["w"], ref["fl"], 0, 4)
     have = s.crossings(0, 4)
     print("\nfield errors", {k: f"{v:.1e}" for k, v in errs.items()}, "crossings", have, want)
     column = 80.0 - 16.0  # liquid height h0 - hs of the workload
     for g, w in zip(have, want):
         assert abs(g - w) <= 0.005 * column, (have, want)
-    assert all(v <= 1e-3 for v in errs.values()), errs
+    vg, vr = _front_and_frozen(O, got)[1], _front_and_frozen(O, ref)[1]
+    assert abs(vg - vr) <= 0.005 * vr, (vg, vr)
+    _compare(got, ref, "fp32", tol=1e-4)
     s.close()
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_sessile_droplet_512_long_run(env, prec):
+    """The benchmark workload itself (512^2 droplet, three lattices, cold
+    substrate) for 2,000 steps, every node against the oracle."""
+    got, ref = _run_pair(env, W.sessile_droplet(512, seed=0), 2000, prec)
+    _compare(got, ref, prec)
 
 
 def test_batch64_full_size_sampled_grids(env):

@@ -2,9 +2,8 @@
 field and per observable, on the paper's workload shapes.
 
 FP32 is held to the parity bar (relative L2 per field <= 1e-4; mdot, a
-difference of two float liquid fractions, 1e-3) on the state fields; over
-these long runs the small, slowly growing velocity and pressure fields are
-held to 3e-4.  FP16 storage (populations
+difference of two float liquid fractions, 1e-3; observables 1e-4).  FP16
+storage (populations
 in binary16, arithmetic in FP32) is an accuracy experiment: its errors are
 printed as a table (run with -s) and held to bounds a few times above the
 values measured on GB300, so that a regression shows.  Relative L2 of a
@@ -44,6 +43,11 @@ def _errors(O, lbm, wl, steps, prec, line):
     s = lbm.Solver(cfg, precision=prec).set_geometry(arr).step(steps)
     got, d = s.fields(), s.diagnostics(compute=True)
     err = {k: _rel_l2(got[k], ref[k]) for k in FIELDS}
+    # the velocity as one vector field (a component that is zero up to
+    # round-off in the oracle has no relative error of its own)
+    du = np.hypot(got["ux"] - ref["ux"], got["uy"] - ref["uy"])
+    nu = np.linalg.norm(np.hypot(ref["ux"], ref["uy"]))
+    err["ux"] = err["uy"] = float(np.linalg.norm(du) / nu) if nu > 0 else float(np.linalg.norm(du))
     obs = {k: abs(d[k] - rd[k]) / max(abs(rd[k]), 1e-300)
            for k in ("material_mass", "frozen_volume")}
     if line is not None:
@@ -62,14 +66,7 @@ CASES = [
     ("stefan 512x8, 5000 steps", lambda: W.stefan(), 5000, (0, 4)),
 ]
 
-# FP32 bounds other than the parity bar, per case: the one-dimensional
-# columns run 5000 steps with a sharp freezing front, where the temperature
-# of the node being frozen is the most sensitive value of the state
-F32_OVERRIDE = {"neumann": dict(T=5e-3, fs=1e-3, fl=2e-4, rhoH=2e-4),
-                "stefan": dict(ux=6e-3, p=5e-4, mu=1e-3)}
-F32_OBS_OVERRIDE = {"neumann": dict(frozen_volume=3e-4)}
-# fields that are zero up to round-off in the oracle (no relative error)
-SKIP = {"stefan": ("uy",)}
+SKIP = {}
 
 # FP16-storage bounds: about 3x the GB300 measurement of each entry
 F16_FIELD = {"droplet": dict(phi=3e-4, fs=5e-3, fl=0.1, T=0.05, rhoH=0.03, p=0.02, ux=0.06,
@@ -81,7 +78,7 @@ F16_FIELD = {"droplet": dict(phi=3e-4, fs=5e-3, fl=0.1, T=0.05, rhoH=0.03, p=0.0
              "neumann": dict(phi=1e-6, fs=0.08, fl=0.015, T=0.15, rhoH=0.015, p=1e-6, ux=1e-6,
                              uy=1e-6, rho=1e-6, mu=1e-6, w=1e-6, mdot=1e-6),
              "stefan": dict(phi=8e-3, fs=0.14, fl=0.03, T=0.15, rhoH=0.09, p=0.24, ux=1.7,
-                            uy=None, rho=8e-3, mu=0.38, w=5e-3, mdot=0.25)}
+                            uy=1.7, rho=8e-3, mu=0.38, w=5e-3, mdot=0.25)}
 F16_OBS = {"droplet": dict(material_mass=4e-5, frozen_volume=1e-3, interface_lu=1.5e-3),
            "cylinder": dict(material_mass=1e-4, frozen_volume=1.5e-3, interface_lu=1.5e-3),
            "random": dict(material_mass=1e-6, frozen_volume=1e-4),
@@ -106,13 +103,11 @@ def test_precision_error_table(env, case):
     skip = SKIP.get(key, ())
     err32, obs32 = rows["fp32"]
     bound32 = dict.fromkeys(FIELDS, 1e-4)
-    bound32.update(mdot=1e-3, ux=3e-4, uy=3e-4, p=3e-4)
-    bound32.update(F32_OVERRIDE.get(key, {}))
+    bound32.update(mdot=1e-3)
     for k in FIELDS:
         if k not in skip:
             assert err32[k] <= bound32[k], ("fp32", k, err32[k])
     obs_bound32 = dict.fromkeys(obs32, 1e-4)
-    obs_bound32.update(F32_OBS_OVERRIDE.get(key, {}))
     for k, v in obs32.items():
         assert v <= obs_bound32[k], ("fp32", k, v)
     err16, obs16 = rows["fp16s"]
@@ -181,7 +176,7 @@ def test_fp16_storage_checkpoint_and_captured_steps(env):
     blob = a.save()
     a.step(10)
     after = a.fields()
-    c = lbm.Solver(cfg, precision="fp16s").set_geometry(arr)
+    c = lbm.Solver(cfg, precision="fp16s", diag_every=3).set_geometry(arr)
     c.load(blob)
     c.step(10)
     fc = c.fields()

@@ -54,7 +54,9 @@ def test_noalloc_matches_context_diagnostics(env, prec):
     plane = (pitch * ny + 63) // 64 * 64
     body = np.frombuffer(blob, dtype=np.uint8, offset=HEADER_BYTES)
     pops = np.frombuffer(body[:27 * plane * esize].tobytes(), dtype=dtype)
-    lags = np.frombuffer(body[27 * plane * esize:33 * plane * esize].tobytes(), dtype=dtype)
+    nlag = 7 if prec == "fp32" else 6  # FP32 states carry the lagged temperature too
+    lags = np.frombuffer(body[27 * plane * esize:(27 + nlag) * plane * esize].tobytes(),
+                         dtype=dtype)
     phi0 = _planes(arr["phi0"], nx, ny, pitch, plane, dtype)
     mask = _planes(arr["mask"], nx, ny, pitch, plane, np.uint8)
     d_pops = torch.from_numpy(pops.copy()).cuda()
