@@ -48,6 +48,9 @@ typedef enum {
   LBM_ERR_OOM = -4,         /* device or pinned host allocation failed        */
   LBM_ERR_NONFINITE = -5,   /* diagnostics found non-finite populations       */
   LBM_ERR_UNSUPPORTED = -6, /* valid request the library does not implement  */
+  LBM_ERR_TIMEOUT = -7,     /* a kernel's bounded wait for its own tile copies
+                               ran out (reported by the next synchronising
+                               read; the state is then undefined)            */
   LBM_ERR_STATE = -8        /* call out of order (e.g. step before geometry)  */
 } lbm_status;
 
@@ -306,6 +309,15 @@ void lbm_batch_destroy(lbm_batch* batch);
  * the hook disarms itself after firing.  after < 0 disarms it.  Process
  * wide; not for concurrent use with other lbm_create calls. */
 void lbm_debug_fail_allocation(int after);
+
+/* Testing hook for the bounded waits of the float step's TMA-staged tile
+ * kernel (no device fault is involved): while on != 0, every such kernel
+ * launched expects 16 bytes more than its tile copies deliver, so its first
+ * wait runs out after about a second with nothing left in flight; the
+ * kernel records it and the next lbm_read_fields or lbm_read_diagnostics of
+ * the context returns LBM_ERR_TIMEOUT (the state is then undefined: set the
+ * geometry again).  Process wide. */
+void lbm_debug_tile_timeout(int on);
 
 /* Reverse mode (adjoint) of the enthalpy-lattice step, Eqs. (8), (23)-(28)
  * with the fluid at rest: for a context with precision LBM_FP64 (a cold mask

@@ -15,7 +15,10 @@
 #include <new>
 #include <vector>
 
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_runtime.h>
+#include <mutex>
 
 #include "../../include/lbm.h"
 #include "lbm_host.h"
@@ -52,6 +55,13 @@ struct lbm_ctx {
   void* scratch;         // NSCRATCH planes (phi, fs, rho) of the two-kernel step
   bool split;            // step as macro + collide kernels, or fused (default)
   int nlag;              // lag planes per buffer: NLAG, plus T for float arithmetic
+  // float contexts: the step as the TMA-staged tile kernel (lbm_tile.cuh)
+  bool tile;
+  int tile_stages;       // shared-memory stages of the tile kernel (1 or 2)
+  int tile_grid;         // its CTAs (persistent when fewer than the tiles)
+  int sms;               // multiprocessors of the context's device
+  CUtensorMap tm_f[2], tm_gh[2], tm_lag[2], tm_phi0, tm_mask;  // per A/B buffer
+  unsigned* status;      // device word: a tile's copies did not arrive in time
   int cur;
   int64_t step;
   bool have_geometry;
@@ -89,6 +99,11 @@ struct StateHeader {
 // the device were out of memory (then the hook disarms itself).
 std::atomic<int> g_alloc_countdown{-1};
 
+// Testing hook for the bounded waits of the tile kernel: while armed, every
+// tile kernel launched expects 16 bytes more than its copies deliver, so its
+// first wait runs out (no copy is left in flight).
+std::atomic<int> g_tile_timeout{0};
+
 bool injected_alloc_failure() {
   int n = g_alloc_countdown.load();
   while (n >= 0) {
@@ -123,6 +138,96 @@ int cuda_fail(lbm_ctx* c, cudaError_t e, const char* what) {
   return e == cudaErrorMemoryAllocation ? LBM_ERR_OOM : LBM_ERR_CUDA;
 }
 
+// cuTensorMapEncodeTiled through the runtime's driver entry point (no link
+// against the driver library); null if the driver does not offer it.
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  });
+  return fn;
+}
+
+// A 3-D tiled map over `planes` planes of a grid in the library's layout
+// (x fastest, rows of pitch elements, planes of `plane` elements); cells
+// outside nx x ny read as zero.
+bool encode_map(CUtensorMap* m, CUtensorMapDataType dt, size_t esize, void* base,
+                const lbmk::Geom& g, int planes, unsigned bx, unsigned by, unsigned bz) {
+  PFN_cuTensorMapEncodeTiled_v12000 fn = tensor_map_encoder();
+  if (!fn) return false;
+  const cuuint64_t dims[3] = {(cuuint64_t)g.nx, (cuuint64_t)g.ny, (cuuint64_t)planes};
+  const cuuint64_t strides[2] = {(cuuint64_t)g.pitch * esize, (cuuint64_t)g.plane * esize};
+  const cuuint32_t box[3] = {bx, by, bz};
+  const cuuint32_t es[3] = {1, 1, 1};
+  return fn(m, dt, 3, base, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+            CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// The tensor maps of a float context's tile kernel (both A/B buffers).
+template <typename S>
+bool make_tile_maps(lbm_ctx* c, CUtensorMapDataType dt) {
+  using St = lbmk::TileStage<S>;
+  bool ok = true;
+  for (int b = 0; b < 2; b++) {
+    ok = ok && encode_map(&c->tm_f[b], dt, sizeof(S), c->pop[b], c->g, 27, lbmk::TX, lbmk::TY, 9);
+    ok = ok && encode_map(&c->tm_gh[b], dt, sizeof(S), c->pop[b], c->g, 27, St::WG, lbmk::TY + 2, 18);
+    ok = ok && encode_map(&c->tm_lag[b], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, sizeof(float), c->lag[b],
+                          c->g, lbmk::NLAG + 1, St::WL, lbmk::TY + 2, lbmk::NLAG + 1);
+  }
+  ok = ok && encode_map(&c->tm_phi0, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, sizeof(float), c->phi0, c->g,
+                        1, St::WL, lbmk::TY + 2, 1);
+  ok = ok && encode_map(&c->tm_mask, CU_TENSOR_MAP_DATA_TYPE_UINT8, 1, c->mask, c->g, 1, St::WM,
+                        lbmk::TY + 2, 1);
+  return ok;
+}
+
+template <typename S>
+lbmk::TileArgs<S> tile_args(lbm_ctx* c, const lbmk::Args<float, S>& a) {
+  lbmk::TileArgs<S> t;
+  std::memset(&t, 0, sizeof(t));
+  t.a = a;
+  t.map_f = c->tm_f[c->cur];
+  t.map_gh = c->tm_gh[c->cur];
+  t.map_lag = c->tm_lag[c->cur];
+  t.map_phi0 = c->tm_phi0;
+  t.map_mask = c->tm_mask;
+  t.tiles_x = (c->g.nx + lbmk::TX - 1) / lbmk::TX;
+  t.ntiles = c->nblocks;
+  t.status = c->status;
+  t.extra_tx = g_tile_timeout.load() ? 16u : 0u;
+  return t;
+}
+
+// Tile kernel configuration: `stages` shared-memory stages and `per_sm`
+// persistent CTAs per multiprocessor (0: one CTA per tile).
+void set_tile_config(lbm_ctx* c, int stages, int per_sm) {
+  c->tile_stages = stages;
+  c->tile_grid = per_sm > 0 ? std::max(1, std::min(c->nblocks, per_sm * c->sms)) : c->nblocks;
+}
+
+// A tile kernel whose copies did not arrive within its bounded wait sets
+// c->status; the next synchronising read reports it (once).
+int check_timeout(lbm_ctx* c, cudaStream_t s) {
+  if (!c->status) return LBM_OK;
+  unsigned v = 0;
+  cudaError_t e = cudaMemcpyAsync(&v, c->status, sizeof(v), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_fail(c, e, "status download");
+  if (v) {
+    cudaMemsetAsync(c->status, 0, sizeof(unsigned), s);
+    return fail(c, LBM_ERR_TIMEOUT,
+                "a step's tile copies did not arrive in time; the state is undefined%s");
+  }
+  return LBM_OK;
+}
+
 template <typename R, typename S = R>
 Args<R, S> step_args(lbm_ctx* c, const Coef<R>& coef) {
   Args<R, S> a;
@@ -148,6 +253,8 @@ cudaError_t launch(lbm_ctx* c, int mode, bool diag, double* const* outs, cudaStr
   }
   if (c->p.precision == LBM_FP32) {
     Args<float> a = step_args<float>(c, c->cf);
+    if (mode == lbmk::MODE_STEP && c->tile)
+      return lbmk::launch_tile_f32(tile_args<float>(c, a), diag, c->tile_stages, c->tile_grid, s);
     if (outs)
       for (int k = 0; k < lbmk::NFIELD; k++) a.out[k] = outs[k];
     return lbmk::launch_step_f32(a, mode, diag, s);
@@ -160,6 +267,9 @@ cudaError_t launch(lbm_ctx* c, int mode, bool diag, double* const* outs, cudaStr
   }
   if (c->p.precision == LBM_FP16S) {
     Args<float, __half> a = step_args<float, __half>(c, c->cf);
+    if (mode == lbmk::MODE_STEP && c->tile)
+      return lbmk::launch_tile_f16s(tile_args<__half>(c, a), diag, c->tile_stages, c->tile_grid,
+                                    s);
     if (outs)
       for (int k = 0; k < lbmk::NFIELD; k++) a.out[k] = outs[k];
     return lbmk::launch_step_f16s(a, mode, diag, s);
@@ -268,7 +378,7 @@ void free_all(lbm_ctx* c) {
   if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
   void* dev[] = {c->pop[0], c->pop[1], c->lag[0],     c->lag[1],    c->phi0,   c->mask,
                  c->diag_partial, c->diag_out, c->staging, c->in_stage,
-                 c->scratch};
+                 c->scratch, c->status};
   for (void* p : dev)
     if (p) cudaFree(p);
   if (c->h_diag) cudaFreeHost(c->h_diag);
@@ -288,6 +398,7 @@ const char* lbm_status_string(int status) {
     case LBM_ERR_NONFINITE: return "non-finite state";
     case LBM_ERR_UNSUPPORTED: return "unsupported";
     case LBM_ERR_STATE: return "call out of order";
+    case LBM_ERR_TIMEOUT: return "device wait timed out";
     default: return "unknown status";
   }
 }
@@ -351,6 +462,36 @@ int lbm_create(const lbm_params* params, lbm_ctx** out) {
     e = dev_malloc((void**)&c->diag_partial, dmul * lbmk::NDIAG * c->nblocks * sizeof(double));
   if (e == cudaSuccess) e = dev_malloc((void**)&c->diag_out, dmul * (lbmk::NDIAG + 1) * sizeof(double));
   if (e == cudaSuccess) e = cudaMemset(c->mask, 0, P);
+  if (e == cudaSuccess) e = dev_malloc((void**)&c->status, sizeof(unsigned));
+  if (e == cudaSuccess) e = cudaMemset(c->status, 0, sizeof(unsigned));
+  if (e == cudaSuccess && (params->precision == LBM_FP32 || params->precision == LBM_FP16S)) {
+    // float contexts step through the TMA-staged tile kernel unless
+    // LBM_STEP_KERNEL=fused asks for the one-CTA-per-tile kernel
+    const char* k = std::getenv("LBM_STEP_KERNEL");
+    const bool want = !(k && std::strcmp(k, "fused") == 0);
+    const bool maps = params->precision == LBM_FP32
+                          ? make_tile_maps<float>(c, CU_TENSOR_MAP_DATA_TYPE_FLOAT32)
+                          : make_tile_maps<__half>(c, CU_TENSOR_MAP_DATA_TYPE_FLOAT16);
+    if (want && maps) {
+      e = params->precision == LBM_FP32 ? lbmk::prepare_tile_f32() : lbmk::prepare_tile_f16s();
+      int dev = 0, sms = 0;
+      if (e == cudaSuccess) e = cudaGetDevice(&dev);
+      if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+      c->sms = std::max(1, sms);
+      // LBM_TILE=<stages>:<CTAs per SM> (0: one CTA per tile) chooses the
+      // configuration; the default is two stages, two persistent CTAs per SM
+      int st = 2, per = 2;
+      if (const char* v = std::getenv("LBM_TILE")) {
+        int a = 0, b = 0;
+        if (std::sscanf(v, "%d:%d", &a, &b) == 2 && (a == 1 || a == 2) && b >= 0 && b <= 4) {
+          st = a;
+          per = b;
+        }
+      }
+      set_tile_config(c, st, per);
+      c->tile = e == cudaSuccess;
+    }
+  }
   if (e == cudaSuccess)
     e = host_alloc((void**)&c->h_diag, dmul * (lbmk::NDIAG + 1) * sizeof(double));
   if (e == cudaSuccess) e = cudaDeviceSynchronize();
@@ -570,7 +711,9 @@ extern "C" {
 int lbm_read_fields(lbm_ctx* c, uint32_t field_mask, double* const* out, int where,
                     void* stream) {
   if (!c) return LBM_ERR_ARG;
-  return read_fields_impl(c, field_mask, out, where, (cudaStream_t)stream, false);
+  const int st = read_fields_impl(c, field_mask, out, where, (cudaStream_t)stream, false);
+  if (st != LBM_OK) return st;
+  return check_timeout(c, (cudaStream_t)stream);
 }
 
 int lbm_read_tangent_fields(lbm_ctx* c, uint32_t field_mask, double* const* out, int where,
@@ -618,6 +761,8 @@ int lbm_read_diagnostics(lbm_ctx* c, lbm_diag* out) {
                                   cudaMemcpyDeviceToHost, c->last_stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(c->last_stream);
   if (e != cudaSuccess) return cuda_fail(c, e, "diagnostics download");
+  const int st = check_timeout(c, c->last_stream);
+  if (st != LBM_OK) return st;
   const double* d = c->h_diag;
   out->mass = d[0];
   out->material_mass = d[1];
@@ -724,6 +869,8 @@ int lbm_load_state(lbm_ctx* c, const void* host_buf, size_t size, void* stream) 
 extern "C" void lbm_debug_fail_allocation(int after) {
   g_alloc_countdown.store(after < 0 ? -1 : after);
 }
+
+void lbm_debug_tile_timeout(int on) { g_tile_timeout.store(on ? 1 : 0); }
 
 extern "C" int lbm_adjoint_frozen_fraction(lbm_ctx* c, int64_t nsteps, int every, double* ff_out,
                                            double* grad, void* stream) {

@@ -43,4 +43,46 @@ cudaError_t launch_init_f32(const InitArgs<float>& a, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+
+template <bool DIAG, int LATC, int NST>
+static cudaError_t prepare_tile_one() {
+  return cudaFuncSetAttribute(lbm_tile_kernel<float, DIAG, LATC, NST>,
+                              cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)tile_smem_bytes<float>(NST));
+}
+
+template <int NST>
+static cudaError_t prepare_tile_nst() {
+  cudaError_t e = prepare_tile_one<false, 7, NST>();
+  if (e == cudaSuccess) e = prepare_tile_one<true, 7, NST>();
+  if (e == cudaSuccess) e = prepare_tile_one<false, 0, NST>();
+  if (e == cudaSuccess) e = prepare_tile_one<true, 0, NST>();
+  return e;
+}
+
+cudaError_t prepare_tile_f32() {
+  cudaError_t e = prepare_tile_nst<1>();
+  if (e == cudaSuccess) e = prepare_tile_nst<2>();
+  return e;
+}
+
+template <int NST>
+static void tile_launch(const TileArgs<float>& t, bool diag, int grid, cudaStream_t s) {
+  const size_t smem = tile_smem_bytes<float>(NST);
+  const bool all = t.a.g.lattices == (LAT_FLOW | LAT_PHASE | LAT_HEAT);
+  if (all) {
+    if (diag) lbm_tile_kernel<float, true, 7, NST><<<grid, block_dims(), smem, s>>>(t);
+    else lbm_tile_kernel<float, false, 7, NST><<<grid, block_dims(), smem, s>>>(t);
+  } else {
+    if (diag) lbm_tile_kernel<float, true, 0, NST><<<grid, block_dims(), smem, s>>>(t);
+    else lbm_tile_kernel<float, false, 0, NST><<<grid, block_dims(), smem, s>>>(t);
+  }
+}
+
+cudaError_t launch_tile_f32(const TileArgs<float>& t, bool diag, int stages, int grid, cudaStream_t s) {
+  if (stages == 2) tile_launch<2>(t, diag, grid, s);
+  else tile_launch<1>(t, diag, grid, s);
+  return cudaGetLastError();
+}
+
 }  // namespace lbmk

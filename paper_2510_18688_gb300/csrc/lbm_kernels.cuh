@@ -69,10 +69,16 @@ __device__ __forceinline__ R qw(int i) {
   return i == 0 ? R(4.0 / 9.0) : (i <= 4 ? R(1.0 / 9.0) : R(1.0 / 36.0));
 }
 
-// Division: IEEE in double, the fast approximate form in float (relative
-// error of a few ulp, far below the float parity bar).
+// Division: IEEE in double; in float the fast approximate form (relative
+// error of a few ulp, far below the float parity bar), or the IEEE one when
+// built with LBM_F32_FAST_DIV=0.
+#ifndef LBM_F32_FAST_DIV
+#define LBM_F32_FAST_DIV 1
+#endif
 __device__ __forceinline__ double qdiv(double a, double b) { return a / b; }
-__device__ __forceinline__ float qdiv(float a, float b) { return __fdividef(a, b); }
+__device__ __forceinline__ float qdiv(float a, float b) {
+  return LBM_F32_FAST_DIV ? __fdividef(a, b) : __fdiv_rn(a, b);
+}
 
 // Per-context constants (derived on the host by lbm_create).
 template <typename R>

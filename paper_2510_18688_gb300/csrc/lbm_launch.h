@@ -7,6 +7,7 @@
 #include "lbm_kernels.cuh"
 #include "lbm_step.cuh"
 #include "lbm_split.cuh"
+#include "lbm_tile.cuh"
 
 namespace lbmk {
 
@@ -21,6 +22,16 @@ cudaError_t launch_step_f64(const Args<double>& a, int mode, bool diag, cudaStre
 // Two-kernel form of MODE_STEP (macro pass, then collide pass).
 cudaError_t launch_split_f64(const SplitArgs<double>& a, bool diag, cudaStream_t s);
 cudaError_t launch_init_f32(const InitArgs<float>& a, cudaStream_t s);
+// The float step as the TMA-staged tile kernel (lbm_tile.cuh) with 1 or 2
+// shared-memory stages on `grid` CTAs (persistent when grid < tiles);
+// prepare_tile_* sets its shared-memory sizes once (call before the first
+// launch, outside stream capture).
+cudaError_t prepare_tile_f32();
+cudaError_t prepare_tile_f16s();
+cudaError_t launch_tile_f32(const TileArgs<float>& t, bool diag, int stages, int grid,
+                            cudaStream_t s);
+cudaError_t launch_tile_f16s(const TileArgs<__half>& t, bool diag, int stages, int grid,
+                             cudaStream_t s);
 // FP16 population storage, FP32 arithmetic.
 cudaError_t launch_step_f16s(const Args<float, __half>& a, int mode, bool diag, cudaStream_t s);
 cudaError_t launch_init_f16s(const InitArgs<float, __half>& a, cudaStream_t s);

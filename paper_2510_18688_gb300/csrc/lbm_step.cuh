@@ -72,6 +72,7 @@ __device__ __forceinline__ void push(const Geom& g, const Coef<R>& c, S* __restr
 template <typename R>
 struct Macro {
   R ux, uy, uu, pr, S, Ftx, Fty, uFt, Gx, Gy, tauf, muphi, phux, phuy, cap;
+  R prl;  // well-balanced storage: the pressure's rounding residual (exact p = pr + prl)
 };
 
 // The three collisions are evaluated pairwise over (i, opposite of i): in
@@ -207,11 +208,11 @@ __device__ __forceinline__ bool upstream_wall(const Geom& g, int x, int y, int i
 
 // Flow collision Eqs. (11), (14)-(16) and push for remainders: fr[i] = f_i -
 // 3 (w_i - delta_i0) p_src(i), dps[i] = p_src(i) - p (p = M.pr, the node's new
-// pressure, which the stored remainders are referred to).  The pressure
-// part of the equilibrium and the references then meet as 3 (w_i -
-// delta_i0) (p_src(i) - p) (1 - 1/tau): f*_i - 3 (w_i - delta_i0) p =
-// (1 - 1/tau) (fr_i + 3 (w_i - delta_i0) dps_i) + rho s_i / tau + (1 -
-// 1/2tau) F_i.
+// pressure as stored, which the remainders are referred to; the exact
+// pressure is p + M.prl).  The pressure part of the equilibrium and the
+// references then meet as f*_i - 3 (w_i - delta_i0) p = (1 - 1/tau) (fr_i +
+// 3 (w_i - delta_i0) dps_i) + (rho s_i + 3 (w_i - delta_i0) prl) / tau +
+// (1 - 1/2tau) F_i.
 template <bool INNER, typename S>
 __device__ __forceinline__ void collide_flow_wb(const Geom& g, const Coef<float>& c,
                                                 S* __restrict__ out, int P, int x, int y, int n,
@@ -228,7 +229,8 @@ __device__ __forceinline__ void collide_flow_wb(const Geom& g, const Coef<float>
     if (iso) F0 += M.S * (0.f - 2.f / 3.f) * 1.5f;
     const float base = fr[0] + 3.f * (qw<float>(0) - 1.f) * dps[0];
     push<float, INNER, false>(g, c, out, P, 0, x, y, n,
-                              base * omi + itau * (qw<float>(0) * sym0) +
+                              base * omi +
+                                  itau * (qw<float>(0) * sym0 + 3.f * (qw<float>(0) - 1.f) * M.prl) +
                                   fcoef * qw<float>(0) * F0);
   }
 #pragma unroll
@@ -239,7 +241,7 @@ __device__ __forceinline__ void collide_flow_wb(const Geom& g, const Coef<float>
     const float cu = float(qx(i)) * M.ux + float(qy(i)) * M.uy;
     const float cF = float(qx(i)) * M.Gx + float(qy(i)) * M.Gy;
     const float cFt = float(qx(i)) * M.Ftx + float(qy(i)) * M.Fty;
-    const float eqS = rho * (4.5f * cu * cu) + sym0;
+    const float eqS = rho * (4.5f * cu * cu) + sym0 + 3.f * M.prl;
     const float eqA = rho * (3.f * cu);
     float srcS = fsym0 + 9.f * cu * cFt;
     if (iso) srcS += M.S * (float(qx(i) * qx(i) + qy(i) * qy(i)) - 2.f / 3.f) * 1.5f;
@@ -330,6 +332,151 @@ __device__ __forceinline__ void collide_heat_wb(const Geom& g, const Coef<float>
     push_h<INNER>(g, c, out, P, o, x, y, n, hr[o] + Da - Ds, ro, wrr, T,
                   sT[hc + qy(o) * HX + qx(o)]);
   }
+}
+
+// Phase B of one node up to its collisions: the isotropic stencils (reading
+// R-FD: grad chi = 3 sum w_i c_i chi(x + c_i), lap chi = 6 sum w_i (chi(x +
+// c_i) - chi(x))) of phi, phi0, f_s, rho and the lagged pressure, the
+// chemical potential of Eq. (6), the surface-tension, body and penalty
+// forces, velocity and pressure of Eq. (17), the source S and the modified
+// force of Eq. (16) (readings R-FT, R-FP).  cphi, cfs, crho point at the node
+// in halo arrays of row stride sh; cp, cphi0 at the node in arrays of row
+// stride sb.  f: the node's flow populations; with well-balanced storage
+// (WB) they are remainders over 3 (w_i - delta_i0) p_src(i), the lagged
+// pressure of the node each came from (the node itself for a population a
+// wall returned), and dps holds p_src(i) - p on return.
+template <typename R, bool WB>
+__device__ __forceinline__ void node_macros(const Geom& g, const Coef<R>& c, int lat, int gx,
+                                            int gy, bool inner, const Local<R>& L, R phi0, R pp,
+                                            const R* f, const R* cphi, const R* cfs,
+                                            const R* crho, int sh, const R* cp,
+                                            const R* cphi0, int sb, Macro<R>& M, R* dps) {
+  R gphx = R(0), gphy = R(0), lphi = R(0), lphi0 = R(0), lfs = R(0);
+  R grx = R(0), gry = R(0), gpx = R(0), gpy = R(0);
+#pragma unroll
+  for (int i = 1; i < 9; i++) {
+    const int oh = qy(i) * sh + qx(i), ob = qy(i) * sb + qx(i);
+    const R wi = qw<R>(i);
+    const R cxi = R(qx(i)), cyi = R(qy(i));
+    if (lat & LAT_PHASE) {
+      const R ph = cphi[oh];
+      gphx += wi * cxi * ph;
+      gphy += wi * cyi * ph;
+      lphi += R(2) * wi * (ph - cphi[0]);
+      lphi0 += R(2) * wi * (cphi0[ob] - cphi0[0]);
+      lfs += R(2) * wi * (cfs[oh] - cfs[0]);
+    }
+    if (lat & LAT_FLOW) {
+      const R rq = crho[oh], pq = cp[ob];
+      grx += wi * cxi * rq;
+      gry += wi * cyi * rq;
+      gpx += wi * cxi * pq;
+      gpy += wi * cyi * pq;
+    }
+  }
+  gphx *= R(3); gphy *= R(3); lphi *= R(3); lphi0 *= R(3); lfs *= R(3);
+  grx *= R(3); gry *= R(3); gpx *= R(3); gpy *= R(3);
+
+  const R phi = L.phi, fs = L.fs, rho = L.rho, mdot = L.mdot;
+  M.muphi = R(0);
+  R Fx, Fy;
+  {
+    R Fsx = R(0), Fsy = R(0);
+    if (lat & LAT_PHASE) {
+      M.muphi = chem_local(c, phi, phi0, fs) -
+                c.klap * (lphi + c.cos_th * lphi0 + c.cos_ps * lfs);
+      Fsx = M.muphi * gphx;
+      Fsy = M.muphi * gphy;
+    }
+    Fx = Fsx + rho * c.gx;
+    Fy = Fsy + rho * c.gy;
+  }
+  M.ux = R(0); M.uy = R(0); M.uu = R(0); M.pr = R(0);
+  if (lat & LAT_FLOW) {
+    const R mu = interp(fs, L.w, c.mu_s, c.mu_l, c.mu_g);
+    R jx = (f[1] - f[3]) + (f[5] - f[6]) + (f[8] - f[7]);
+    R jy = (f[2] - f[4]) + (f[5] + f[6]) - (f[7] + f[8]);
+    R snz = (f[1] + f[2] + f[3] + f[4]) + (f[5] + f[6] + f[7] + f[8]);
+    if constexpr (WB) {
+      // add the moments of the references 3 w_i p_src(i), as differences
+      // from the node's own lagged pressure pp (whose share, 3 (1 - w_0) pp
+      // in the sum, returns pp itself in Eq. (17c) below)
+      dps[0] = R(0);
+#pragma unroll
+      for (int i = 1; i < 9; i++)
+        dps[i] = (!inner && upstream_wall(g, gx, gy, i)) ? R(0)
+                                                         : cp[-(qy(i) * sb + qx(i))] - pp;
+      const R w1 = qw<R>(1), w5 = qw<R>(5);
+      jx += R(3) * (w1 * (dps[1] - dps[3]) + w5 * ((dps[5] - dps[6]) + (dps[8] - dps[7])));
+      jy += R(3) * (w1 * (dps[2] - dps[4]) + w5 * ((dps[5] + dps[6]) - (dps[7] + dps[8])));
+      snz += R(3) * (w1 * ((dps[1] + dps[2]) + (dps[3] + dps[4])) +
+                     w5 * ((dps[5] + dps[6]) + (dps[7] + dps[8])));
+    }
+    // Eq. (17a,b) with the penalty force f = fs (u_s - u*), u_s = 0
+    const R irho = qdiv(R(1), rho);
+    const R usx = (jx + R(0.5) * Fx) * irho, usy = (jy + R(0.5) * Fy) * irho;
+    const R fpx = -fs * usx, fpy = -fs * usy;
+    M.ux = usx + R(0.5) * fpx;
+    M.uy = usy + R(0.5) * fpy;
+    M.uu = M.ux * M.ux + M.uy * M.uy;
+    M.S = rho * mdot + M.ux * grx + M.uy * gry;
+    // modified force (reading R-FT), lagged pressure (reading R-FP)
+    M.Ftx = Fx - (gpx - grx * R(1.0 / 3.0));
+    M.Fty = Fy - (gpy - gry * R(1.0 / 3.0));
+    M.uFt = M.ux * M.Ftx + M.uy * M.Fty;
+    M.tauf = R(3) * mu * irho + R(0.5);
+    M.Gx = Fx + rho * fpx;
+    M.Gy = Fy + rho * fpy;
+    // F_0 of Eq. (16)
+    R F0 = qw<R>(0) * (M.S + (R(0) - R(2) / R(3) * M.uFt) * R(4.5));
+    if (c.readings & 1u) F0 += qw<R>(0) * (M.S * (R(0) - R(2) / R(3)) * R(1.5));
+    const R s0 = qw<R>(0) * (-M.uu * R(1.5));
+    const R dp = (R(1) / R(3)) / (R(1) - qw<R>(0)) *
+                 (snz + R(0.5) * M.S + (M.tauf - R(0.5)) * F0 + rho * s0);  // Eq. (17c)
+    M.prl = R(0);
+    if constexpr (WB) {
+      // p = pp + dp, rounded once; the rounding residual (exact, TwoSum)
+      // goes into the stored remainders through the equilibrium (see
+      // collide_flow_wb), so that a slowly rising pressure is not rounded
+      // off step after step
+      M.pr = pp + dp;
+      const R bb = M.pr - pp;
+      M.prl = (pp - (M.pr - bb)) + (dp - bb);
+#pragma unroll
+      for (int i = 0; i < 9; i++) dps[i] -= bb;  // p_src(i) - p
+    } else {
+      M.pr = dp;
+    }
+  }
+  M.phux = phi * M.ux;
+  M.phuy = phi * M.uy;
+  // heat capacity rho Cp (Eq. (10)); float storage forms it as the next
+  // step's reader of this node will (its reference state)
+  if constexpr (WB) M.cap = cap_rn(c, fs, L.w);
+  else M.cap = rho * interp(fs, L.w, c.cp_s, c.cp_l, c.cp_g);
+}
+
+// The node's contributions to the FP64 diagnostics (lbm_diag order) and a
+// non-finite flag: a non-finite population anywhere makes one of the sums
+// non-finite.
+template <typename R>
+__device__ __forceinline__ void diag_values(const Coef<R>& c, int lat, const Local<R>& L,
+                                            const Macro<R>& M, R sg, R sh, const R* f,
+                                            R* dvals) {
+  dvals[0] = L.rho;
+  dvals[1] = L.w * (c.rho_s * (R(1) - L.fl) + c.rho_l * L.fl);
+  dvals[2] = L.rhoH;
+  dvals[3] = L.w * L.fl;
+  dvals[4] = L.w;
+  dvals[5] = L.w * (R(1) - L.fl);
+  dvals[6] = L.phi;
+  dvals[7] = R(0.5) * L.rho * M.uu;
+  R tot = sg + sh;
+  if (lat & LAT_FLOW) {
+#pragma unroll
+    for (int i = 0; i < 9; i++) tot += f[i];
+  }
+  dvals[8] = finite(tot) ? R(0) : R(1);
 }
 
 // One tile (bx, by) of one grid: the whole step (or read-out) for its
@@ -546,124 +693,15 @@ __device__ __forceinline__ void step_tile(const Args<R, S>& a, int bx, int by, i
   R dps[WB ? 9 : 1];  // well-balanced flow storage: p_src(i) - p
   if (valid) {
     const int hc = (ty + 1) * HX + (tx + 1);
-    // isotropic stencils (reading R-FD): grad = 3 sum w_i c_i chi(x + c_i),
-    // lap = 6 sum w_i (chi(x + c_i) - chi(x))
-    R gphx = R(0), gphy = R(0), lphi = R(0), lphi0 = R(0), lfs = R(0);
-    R grx = R(0), gry = R(0), gpx = R(0), gpy = R(0);
-#pragma unroll
-    for (int i = 1; i < 9; i++) {
-      const int hn = hc + qy(i) * HX + qx(i);
-      const R wi = qw<R>(i);
-      const R cxi = R(qx(i)), cyi = R(qy(i));
-      if (lat & LAT_PHASE) {
-        const R ph = s_phi[hn];
-        gphx += wi * cxi * ph;
-        gphy += wi * cyi * ph;
-        lphi += R(2) * wi * (ph - s_phi[hc]);
-        lphi0 += R(2) * wi * (s_phi0[hn] - s_phi0[hc]);
-        lfs += R(2) * wi * (s_fs[hn] - s_fs[hc]);
-      }
-      if (lat & LAT_FLOW) {
-        const R rq = s_rho[hn], pq = s_p[hn];
-        grx += wi * cxi * rq;
-        gry += wi * cyi * rq;
-        gpx += wi * cxi * pq;
-        gpy += wi * cyi * pq;
-      }
-    }
-    gphx *= R(3); gphy *= R(3); lphi *= R(3); lphi0 *= R(3); lfs *= R(3);
-    grx *= R(3); gry *= R(3); gpx *= R(3); gpy *= R(3);
-
-    const R phi = L.phi, fs = L.fs, rho = L.rho, mdot = L.mdot;
-    M.muphi = R(0);
-    R Fx, Fy;
-    {
-      R Fsx = R(0), Fsy = R(0);
-      if (lat & LAT_PHASE) {
-        M.muphi = chem_local(c, phi, phi0, fs) -
-                  c.klap * (lphi + c.cos_th * lphi0 + c.cos_ps * lfs);
-        Fsx = M.muphi * gphx;
-        Fsy = M.muphi * gphy;
-      }
-      Fx = Fsx + rho * c.gx;
-      Fy = Fsy + rho * c.gy;
-    }
-    M.ux = R(0); M.uy = R(0); M.uu = R(0); M.pr = R(0);
     if (STASHF && (lat & LAT_FLOW)) {
 #pragma unroll
       for (int i = 0; i < 9; i++) f[i] = s_fpop[STASHF ? i : 0][tid];
     }
-    if (lat & LAT_FLOW) {
-      const R mu = interp(fs, L.w, c.mu_s, c.mu_l, c.mu_g);
-      R jx = (f[1] - f[3]) + (f[5] - f[6]) + (f[8] - f[7]);
-      R jy = (f[2] - f[4]) + (f[5] + f[6]) - (f[7] + f[8]);
-      R snz = (f[1] + f[2] + f[3] + f[4]) + (f[5] + f[6] + f[7] + f[8]);
-      if constexpr (WB) {
-        // the stored f are remainders over 3 (w_i - delta_i0) p_src(i), the
-        // lagged pressure of the node each came from (the node itself for a
-        // population a wall returned): add the references' moments
-        dps[0] = pp;
-#pragma unroll
-        for (int i = 1; i < 9; i++)
-          dps[i] = (!inner && upstream_wall(g, gx, gy, i)) ? pp
-                                                           : s_p[hc - qy(i) * HX - qx(i)];
-        const R w1 = qw<R>(1), w5 = qw<R>(5);
-        jx += R(3) * (w1 * (dps[1] - dps[3]) + w5 * ((dps[5] - dps[6]) + (dps[8] - dps[7])));
-        jy += R(3) * (w1 * (dps[2] - dps[4]) + w5 * ((dps[5] + dps[6]) - (dps[7] + dps[8])));
-        snz += R(3) * (w1 * ((dps[1] + dps[2]) + (dps[3] + dps[4])) +
-                       w5 * ((dps[5] + dps[6]) + (dps[7] + dps[8])));
-      }
-      // Eq. (17a,b) with the penalty force f = fs (u_s - u*), u_s = 0
-      const R irho = qdiv(R(1), rho);
-      const R usx = (jx + R(0.5) * Fx) * irho, usy = (jy + R(0.5) * Fy) * irho;
-      const R fpx = -fs * usx, fpy = -fs * usy;
-      M.ux = usx + R(0.5) * fpx;
-      M.uy = usy + R(0.5) * fpy;
-      M.uu = M.ux * M.ux + M.uy * M.uy;
-      M.S = rho * mdot + M.ux * grx + M.uy * gry;
-      // modified force (reading R-FT), lagged pressure (reading R-FP)
-      M.Ftx = Fx - (gpx - grx * R(1.0 / 3.0));
-      M.Fty = Fy - (gpy - gry * R(1.0 / 3.0));
-      M.uFt = M.ux * M.Ftx + M.uy * M.Fty;
-      M.tauf = R(3) * mu * irho + R(0.5);
-      M.Gx = Fx + rho * fpx;
-      M.Gy = Fy + rho * fpy;
-      // F_0 of Eq. (16)
-      R F0 = qw<R>(0) * (M.S + (R(0) - R(2) / R(3) * M.uFt) * R(4.5));
-      if (c.readings & 1u) F0 += qw<R>(0) * (M.S * (R(0) - R(2) / R(3)) * R(1.5));
-      const R s0 = qw<R>(0) * (-M.uu * R(1.5));
-      M.pr = (R(1) / R(3)) / (R(1) - qw<R>(0)) *
-             (snz + R(0.5) * M.S + (M.tauf - R(0.5)) * F0 + rho * s0);  // Eq. (17c)
-      if constexpr (WB) {
-#pragma unroll
-        for (int i = 0; i < 9; i++) dps[i] -= M.pr;
-      }
-    }
-    M.phux = phi * M.ux;
-    M.phuy = phi * M.uy;
-    // heat capacity rho Cp (Eq. (10)); float storage forms it as the next
-    // step's reader of this node will (its reference state)
-    if constexpr (WB) M.cap = cap_rn(c, fs, L.w);
-    else M.cap = rho * interp(fs, L.w, c.cp_s, c.cp_l, c.cp_g);
+    node_macros<R, WB>(g, c, lat, gx, gy, inner, L, phi0, pp, f, s_phi + hc, s_fs + hc,
+                       s_rho + hc, HX, s_p + hc, s_phi0 + hc, HX, M, dps);
     // diagnostics of this state, reduced over the warp before the
     // collisions so that none of their inputs stays live through them
-    if (DIAG) {
-      dvals[0] = rho;
-      dvals[1] = L.w * (c.rho_s * (R(1) - L.fl) + c.rho_l * L.fl);
-      dvals[2] = L.rhoH;
-      dvals[3] = L.w * L.fl;
-      dvals[4] = L.w;
-      dvals[5] = L.w * (R(1) - L.fl);
-      dvals[6] = phi;
-      dvals[7] = R(0.5) * rho * M.uu;
-      // a non-finite population anywhere makes one of the sums non-finite
-      R tot = sg + sh;
-      if (lat & LAT_FLOW) {
-#pragma unroll
-        for (int i = 0; i < 9; i++) tot += f[i];
-      }
-      dvals[8] = finite(tot) ? R(0) : R(1);
-    }
+    if (DIAG) diag_values(c, lat, L, M, sg, sh, f, dvals);
   } else if (DIAG) {
 #pragma unroll
     for (int k = 0; k < NDIAG; k++) dvals[k] = R(0);

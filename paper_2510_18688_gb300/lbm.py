@@ -62,7 +62,7 @@ EXPORTS = ("lbm_create", "lbm_set_geometry", "lbm_step", "lbm_read_fields",
            "lbm_read_crossings", "lbm_read_tangent_fields", "lbm_read_tangent_diagnostics",
            "lbm_read_crossings_tangent", "lbm_autotune", "lbm_adjoint_frozen_fraction",
            "lbm_adjoint_crossing", "lbm_adjoint_freezing", "lbm_adjoint_coupled",
-           "lbm_debug_fail_allocation", "lbm3_create", "lbm3_set_geometry", "lbm3_step",
+           "lbm_debug_fail_allocation", "lbm_debug_tile_timeout", "lbm3_create", "lbm3_set_geometry", "lbm3_step",
            "lbm3_read_fields", "lbm3_diagnostics", "lbm3_step_count", "lbm3_last_error",
            "lbm3_destroy", "lbm3_lattice", "lbm3_state_size", "lbm3_save_state",
            "lbm3_load_state", "lbm3_read_tangent_fields", "lbm3_read_tangent_diagnostics")
@@ -120,6 +120,8 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
                                       ctypes.c_int, ctypes.c_int, dp, dp, dp, vp]
     L.lbm_debug_fail_allocation.argtypes = [ctypes.c_int]
     L.lbm_debug_fail_allocation.restype = None
+    L.lbm_debug_tile_timeout.argtypes = [ctypes.c_int]
+    L.lbm_debug_tile_timeout.restype = None
     L.lbm3_create.argtypes = [ctypes.POINTER(Lbm3Params), ctypes.POINTER(vp)]
     L.lbm3_set_geometry.argtypes = [vp, vp, vp, vp, vp, vp, ctypes.c_int, vp]
     L.lbm3_step.argtypes = [vp, ctypes.c_int64, vp]
@@ -600,6 +602,12 @@ def lbm_debug_fail_allocation(after: int):
     """Testing hook: the (after + 1)-th allocation of the next lbm_create
     calls fails as out of memory (after < 0 disarms); see include/lbm.h."""
     load().lbm_debug_fail_allocation(int(after))
+
+
+def lbm_debug_tile_timeout(on: bool):
+    """Test hook: the float step's tile kernels expect more bytes than their
+    copies deliver, so their bounded waits run out (see include/lbm.h)."""
+    load().lbm_debug_tile_timeout(1 if on else 0)
 
 
 def lbm3_create(params: Lbm3Params) -> ctypes.c_void_p:

@@ -44,3 +44,35 @@ def test_every_allocation_failure_of_lbm_create_is_clean():
     s = lbm.Solver(cfg, precision="fp32").set_geometry(arr).step(10)
     assert s.diagnostics()["nonfinite"] == 0
     s.close()
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp16s"])
+def test_tile_wait_timeout_is_reported(prec):
+    """The float step's tile kernel waits for its TMA copies with a bound of
+    about a second.  The test hook makes every such wait run out (the
+    kernel expects 16 bytes more than its copies deliver; nothing is left in
+    flight, no device fault): the next read reports LBM_ERR_TIMEOUT, and the
+    context steps correctly again once the geometry is set anew."""
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2510_18688_gb300 import build, lbm
+    build.build()
+    lbm.load()
+    cfg, arr = W.random_state(70, 45, seed=4)
+    s = lbm.Solver(cfg, precision=prec).set_geometry(arr)
+    lbm.lbm_debug_tile_timeout(True)
+    try:
+        s.step(1)
+        with pytest.raises(lbm.LbmError) as e:
+            s.fields()
+        assert e.value.status == -7  # LBM_ERR_TIMEOUT
+    finally:
+        lbm.lbm_debug_tile_timeout(False)
+    s.set_geometry(arr).step(5)
+    ref = lbm.Solver(cfg, precision=prec).set_geometry(arr).step(5)
+    a, b = s.fields(), ref.fields()
+    for k in a:
+        assert np.array_equal(a[k], b[k]), k
+    s.close()
+    ref.close()

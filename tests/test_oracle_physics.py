@@ -240,41 +240,101 @@ def _crossing(phi_row, start):
     return float("nan")
 
 
-@pytest.mark.parametrize("rho_r,tol", [(0.9, 0.015), (1.2, 0.04)])
-def test_stefan_final_height_table1(O, rho_r, tol):
-    """P3: after complete freezing the solid height is rho_l h0 / rho_s
-    (Table 1); the paper's own maximum error over its table is below 1.5 %.
-    The liquid column sits on a solid layer (phi0) above the cold wall, gas
-    above it, liquid initially at T_m so that it freezes completely.  The
-    height is read at the first check after complete freezing: later, the
-    solid-fraction penalty of Eq. (4) keeps pushing phi out of the ice and
-    the phi = 0 crossing creeps (faster under shrinkage, hence the wider
-    tolerance at rho_s/rho_l = 1.2)."""
-    hs, h0 = 8.0, 32.0
-    cfg, arr = W.stefan(nx=128, ny=4, hs=hs, h0=h0, rho_ratio=rho_r, T0=0.0, alpha=0.5)
+def test_stefan_final_height_table1(O):
+    """P3 (Sec. 4.2, Table 1): after complete freezing the solid height is
+    h_f = rho_l h0 / rho_s.  The configuration is the paper's: the whole
+    system initially at T0 = 1, cold wall T_b = -1, T_m = 0, Ste = 0.1,
+    eps = 4, sigma = 0.001, M = 0.1, mu = 0.1, unit Cp and conductivity
+    ratios; a liquid column of 64 lattice units on a solid layer (phi0) of
+    16, gas above.  At rho_s/rho_l = 0.9 the paper reports 1.1108 against
+    1.1111 (0.03 %); the oracle must be within 0.5 %.  h_f is read at the
+    first check after complete freezing (the phi = 0 crossing above the
+    solid layer)."""
+    hs, h0, rho_r = 16.0, 80.0, 0.9
+    cfg, arr = W.stefan(nx=256, ny=4, hs=hs, h0=h0, rho_ratio=rho_r, T0=1.0, alpha=0.5)
     o = _run(O, (cfg, arr))
-    m0 = o.diagnostics()["material_mass"]
-    done = 0
-    for _ in range(20):
-        o.step(1000)
-        done += 1000
+    for _ in range(100):
+        o.step(2000)
         d = o.diagnostics()
         if d["frozen_volume"] / d["material_volume"] > 0.999:
             break
     assert d["frozen_volume"] / d["material_volume"] > 0.999
     hf = (_crossing(o.fields()["phi"][0], int(hs)) - hs) / (h0 - hs)
-    assert hf == pytest.approx(CF.stefan_final_height(1.0, rho_r), rel=tol)
-    # volume change in the right direction and by a comparable amount
+    assert hf == pytest.approx(CF.stefan_final_height(1.0, rho_r), rel=0.005)
+    assert d["nonfinite"] == 0
+
+
+def test_stefan_shrinkage_final_height(O):
+    """Shrinkage (rho_s/rho_l = 1.2, Table 1: h_f/h0 = 0.8333): a short
+    column of liquid initially at T_m on a solid layer.  The height moves in
+    the right direction and within 4 % of rho_l h0 / rho_s (the paper's own
+    errors at 1.2 are 0.5-0.7 %; after complete freezing the f_s penalty of
+    Eq. (4) keeps pushing phi out of the ice, so the phi = 0 crossing creeps
+    and the check is made at the first sample after freezing).  Under
+    shrinkage the weight w of Eq. (10) overcounts the material near the
+    converging interface (about 10 % of the material mass), a limitation of
+    the method as read that this pin records rather than hides."""
+    hs, h0, rho_r = 8.0, 32.0, 1.2
+    cfg, arr = W.stefan(nx=128, ny=4, hs=hs, h0=h0, rho_ratio=rho_r, T0=0.0, alpha=0.5)
+    o = _run(O, (cfg, arr))
+    m0 = o.diagnostics()["material_mass"]
+    for _ in range(20):
+        o.step(1000)
+        d = o.diagnostics()
+        if d["frozen_volume"] / d["material_volume"] > 0.999:
+            break
+    assert d["frozen_volume"] / d["material_volume"] > 0.999
+    hf = (_crossing(o.fields()["phi"][0], int(hs)) - hs) / (h0 - hs)
+    assert hf == pytest.approx(CF.stefan_final_height(1.0, rho_r), rel=0.04)
     assert (hf - 1.0) * (1.0 / rho_r - 1.0) > 0.5 * (1.0 / rho_r - 1.0) ** 2
-    # P4: material mass sum w (rho_s (1 - fl) + rho_l fl) is conserved up to
-    # the diffuse-interface level under expansion; under shrinkage the
-    # converging flow piles phi up in the ice and the weight w of Eq. (10)
-    # overcounts the material (about 10 %), a limitation of the method as
-    # read that this pin records rather than hides
-    if rho_r < 1.0:
-        assert abs(d["material_mass"] / m0 - 1) < 0.02
-    else:
-        assert abs(d["material_mass"] / m0 - 1) < 0.15
+    assert abs(d["material_mass"] / m0 - 1) < 0.15
+
+
+def _front(f, row=0):
+    """Last crossing of the frozen material fraction w (1 - fl) through 1/2,
+    in wall coordinates (node i at i + 1/2; the cold wall at 0)."""
+    s = f["w"][row] * (1.0 - f["fl"][row]) - 0.5
+    out = float("nan")
+    for i in range(len(s) - 1):
+        if s[i] > 0 >= s[i + 1]:
+            out = i + 0.5 + s[i] / (s[i] - s[i + 1])
+    return out
+
+
+def test_stefan_front_and_interface_displacement(O):
+    """P3 (Sec. 4.2, Eq. (35)): the freezing front follows h_s(t) = 2 kappa
+    sqrt(alpha_s t), kappa the root of Eq. (35); and the liquid above it is
+    pushed up by the convection velocity the paper prints, u = (dh_s/dt)(1 -
+    rho_s/rho_l), so that the gas-liquid interface has moved by
+    (1 - rho_s/rho_l) (h_s - h_s0) -- the integral of that velocity, which
+    the standing sound wave of the closed gas column (period ~600 steps)
+    does not blur.  Paper configuration (T0 = 1, Ste = 0.1, rho_s/rho_l =
+    0.9) on a thin solid layer (one interface width, so that the front
+    starts at the wall).  The paper shows the front as a figure only (good
+    agreement); the bounds: front within 3 % (the Neumann pins allow 2 %; the
+    diffuse layer and the moving liquid add to it), interface displacement
+    within 5 % of the front's advance times (1 - rho_s/rho_l), at 10k, 20k
+    and 40k steps.  A mass source with the wrong factor or sign (Eq. (1))
+    fails the second; a wrong latent heat or Stefan number the first."""
+    hs, h0, rho_r = 4.0, 68.0, 0.9
+    cfg, arr = W.stefan(nx=256, ny=4, hs=hs, h0=h0, rho_ratio=rho_r, T0=1.0, alpha=0.5)
+    a_s = cfg["lambda_s"] / (cfg["rho_s"] * cfg["cp_s"])
+    a_l = cfg["lambda_l"] / (cfg["rho_l"] * cfg["cp_l"])
+    kappa = CF.stefan_kappa(0.1, cfg["lambda_l"], cfg["lambda_s"], 1.0, 0.0, -1.0, a_s, a_l,
+                            rho_r)
+    o = _run(O, (cfg, arr))
+    x_gl0 = _crossing(o.fields()["phi"][0], int(hs))
+    done = 0
+    for t in (10000, 20000, 40000):
+        o.step(t - done)
+        done = t
+        f = o.fields()
+        X = _front(f)
+        want = 2.0 * kappa * math.sqrt(a_s * t)
+        assert abs(X - want) <= 0.03 * want, (t, X, want)
+        moved = _crossing(f["phi"][0], int(X) + 2) - x_gl0
+        expect = (1.0 - rho_r) * (X - hs)
+        assert abs(moved - expect) <= 0.05 * expect, (t, moved, expect)
 
 
 def test_flat_interface_stays_stationary(O):
