@@ -6,7 +6,7 @@ number), all three lattices, FP32 populations.  One bench step is one full
 time step of the coupled update (enthalpy inversion, order parameter,
 stencils, three collisions, streaming with walls, lag store and the fused
 FP64 diagnostics) over the whole grid.  The FP32 working set (~70 MB) fits in the
-129 MB L2, so the L2 is flushed (a 256 MB write) before every timed step and
+129 MB L2, so the L2 is flushed (256 MB written, then read) before every timed step and
 each step is timed alone with CUDA events on the launching stream: the
 number is the HBM-bound one.  Under torchrun every rank advances its own
 replica (weak scaling, no collective on the data path).
@@ -36,6 +36,31 @@ sys.path.insert(0, ROOT)
 METRIC = "coupled MLUPS"  # node updates of all enabled lattices per second / 1e6
 WORKLOAD = "sessile droplet freezing 512x512 (R=100, cold solid layer), 3 lattices, seed 0"
 L2_FLUSH_BYTES = 256 << 20
+
+
+class L2Flush:
+    """Evicts the L2 before a timed step: a write of L2_FLUSH_BYTES and, in
+    the "clean" mode, a read of the same buffer after it, so that the lines
+    the timed kernel then evicts are clean (with a write alone the kernel
+    also pays for writing the flush buffer's dirty lines back to HBM)."""
+
+    def __init__(self, mode):
+        import torch
+        self.clean = mode == "clean"
+        self.buf = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+        self.acc = torch.zeros((), dtype=torch.float32, device="cuda")
+
+    def __call__(self):
+        import torch
+        self.buf.zero_()
+        if self.clean:
+            torch.sum(self.buf, 0, out=self.acc)
+
+    @property
+    def describe(self):
+        mb = L2_FLUSH_BYTES >> 20
+        return (f"flushed before every timed step ({mb} MB written, then read: no dirty lines "
+                f"left in L2)" if self.clean else f"flushed before every timed step ({mb} MB write)")
 
 
 def _droplet512(seed):
@@ -550,12 +575,12 @@ def fp64_record(lbm, wl, flush, stream, sptr, args, t32_ms):
     s = lbm.Solver(cfg, precision="fp64", diag_every=args.diag_every).set_geometry(arr)
     k = max(10, min(args.steps, 40))
     for _ in range(3):
-        flush.zero_()
+        flush()
         lbm.lbm_step(s.ctx, 1, sptr)
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(k)]
     ends = [torch.cuda.Event(enable_timing=True) for _ in range(k)]
     for j in range(k):
-        flush.zero_()
+        flush()
         starts[j].record(stream)
         lbm.lbm_step(s.ctx, 1, sptr)
         ends[j].record(stream)
@@ -642,6 +667,12 @@ def main():
                     help="fp16s: FP16 population storage, FP32 arithmetic; tangent: FP64 "
                          "step with its derivative along the wall temperature")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--l2-flush", default="clean", choices=["clean", "write"],
+                    help="L2 eviction before each timed step: clean (write then read a "
+                         "256 MB buffer) or write (the write alone, which leaves dirty lines "
+                         "that the timed kernel must write back)")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="step with the library's default kernel form (no lbm_autotune)")
     ap.add_argument("--no-sub-records", action="store_true",
                     help="skip the FP64 and adjoint sub-records of the default FP32 line")
     ap.add_argument("--diag-every", type=int, default=1,
@@ -696,6 +727,16 @@ def main():
     solvers = [lbm.Solver(c, precision=args.precision, diag_every=args.diag_every,
                           tangent=tan).set_geometry(a) for c, a in wls]
     batch = lbm.Batch(solvers) if len(solvers) > 1 else None
+    # the library's autotuner picks the kernel form and graph period for this
+    # grid (state unchanged); batches use the batch kernel
+    tune = None
+    if batch is None and not args.no_autotune:
+        us, chosen = solvers[0].autotune(64)
+        tune = {"chosen": chosen, "us_per_step": us,
+                "variants": "kernel form v//2 (float: 0 one CTA per tile, 1 TMA-staged one "
+                            "stage, 2 TMA-staged two stages 2 CTAs/SM, 3 TMA-staged one "
+                            "stage 3 CTAs/SM; fp64: 0 fused, 1 split) x captured period "
+                            "(v even 32, odd 256); timed back to back without L2 flush"}
 
     def step(k):
         if batch is not None:
@@ -703,7 +744,7 @@ def main():
         else:
             lbm.lbm_step(solvers[0].ctx, k, sptr)
 
-    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    flush = L2Flush(args.l2_flush)
 
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
@@ -714,7 +755,7 @@ def main():
     # recorded with it
     with ClockSampler(local) as clk:
         for _ in range(args.warmup):
-            flush.zero_()
+            flush()
             step(1)
         torch.cuda.synchronize()
         t_load = time.perf_counter()
@@ -722,7 +763,7 @@ def main():
             step(64)
             torch.cuda.synchronize()
         for _ in range(3):
-            flush.zero_()
+            flush()
             step(1)
         if pg:
             pg.barrier()
@@ -730,7 +771,7 @@ def main():
         timed_mark = clk.mark()
         wall0 = time.perf_counter()
         for k in range(args.steps):
-            flush.zero_()
+            flush()
             starts[k].record(stream)
             step(1)
             ends[k].record(stream)
@@ -834,10 +875,11 @@ def main():
                    "grid": ([wls[0][0]["nx"], wls[0][0]["ny"]] if len(wls) == 1
                             else f"{len(wls)} grids, {n} nodes"),
                    "precision": args.precision,
-                   "l2": "flushed before every timed step (256 MB write)",
+                   "l2": flush.describe,
                    "diag_every": args.diag_every,
                    "parallelism": f"replicas x{world}"},
         "roofline": roofline,
+        "autotune": tune,
         "gpu_launches": args.steps,
         "e2e": e2e,
         "l2_resident_mlups": n / (l2_ms * 1e-3) / 1e6,

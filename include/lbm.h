@@ -420,18 +420,22 @@ int lbm_adjoint_coupled(lbm_ctx* ctx, int64_t nsteps, int every, int observable,
 
 /* Autotuner (the paper gives no implementation; a measuring aid of this
  * library): times the step forms the library has on the context's own grid
- * and state and keeps the fastest for later lbm_step calls.  Variants, in
- * this order: the fused one-kernel step with captured periods of at least
- * 32 steps, the same with at least 256, and (LBM_FP64 only) the two-kernel
- * split with 32 and with 256.  Each variant runs
- * steps_per_trial steps twice from the same saved state (the first run
- * warms up and captures; the second is timed with CUDA events on `stream`).
- * The state, step counter and diagnostics (including partial sums not yet
- * read) are restored afterwards, so the call does not advance the
- * simulation.  out_us (4 doubles, may be NULL):
+ * and state and keeps the fastest for later lbm_step calls.  Variant v is
+ * kernel form v / 2 with captured periods of at least 32 steps (v even) or
+ * 256 (v odd).  Kernel forms: LBM_FP32 and LBM_FP16S 0 one CTA per 32 x 8
+ * tile loading from global memory, 1 the TMA-staged tile kernel with one
+ * shared-memory stage and one CTA per tile, 2 the same with two stages and
+ * two persistent CTAs per multiprocessor (the copies of the next tile
+ * overlap the current one), 3 one stage and three persistent CTAs per
+ * multiprocessor; LBM_FP64 0 fused, 1 the two-kernel split; tangent
+ * contexts 0.  Each variant runs steps_per_trial steps twice from the same
+ * saved state (the first run warms up and captures; the second is timed
+ * with CUDA events on `stream`).  The state, step counter and diagnostics
+ * (including partial sums not yet read) are restored afterwards, so the
+ * call does not advance the simulation.  out_us (8 doubles, may be NULL):
  * microseconds per step of each variant (-1 where not run); chosen (may be
- * NULL): the index kept.  Allocates a backup of the state (27 population
- * and 6 lag planes) for the duration of the call and synchronises `stream`.
+ * NULL): the index kept.  Allocates a backup of the state (its population
+ * and lag planes) for the duration of the call and synchronises `stream`.
  * Errors: LBM_ERR_ARG (steps_per_trial < 2), LBM_ERR_STATE before
  * lbm_set_geometry, LBM_ERR_OOM/LBM_ERR_CUDA. */
 int lbm_autotune(lbm_ctx* ctx, int steps_per_trial, void* stream, double* out_us, int* chosen);
@@ -469,8 +473,11 @@ int lbm_autotune(lbm_ctx* ctx, int steps_per_trial, void* stream, double* out_us
  * clearing, but all calls share the array: calls whose work overlaps on the
  * GPU (different streams without ordering) race and give wrong sums.  The
  * first call on a device looks up the array's device address
- * (cudaGetSymbolAddress), so make that first call before any stream
- * capture.  Enqueues on `stream`; does not synchronise.
+ * (cudaGetSymbolAddress) and keeps it for the life of the process (safe
+ * against concurrent first calls), so make that first call before any
+ * stream capture; after cudaDeviceReset of a device the kept address is
+ * stale, and this entry point must not be called on that device again.
+ * Enqueues on `stream`; does not synchronise.
  *
  * Errors: LBM_ERR_ARG for a null pointer or invalid grid, LBM_ERR_PARAM for
  * invalid parameters (the checks of lbm_create), LBM_ERR_UNSUPPORTED for a

@@ -57,6 +57,8 @@ struct lbm_ctx {
   int nlag;              // lag planes per buffer: NLAG, plus T for float arithmetic
   // float contexts: the step as the TMA-staged tile kernel (lbm_tile.cuh)
   bool tile;
+  bool tile_ok;          // the tile kernel's tensor maps exist (float contexts)
+  int form;              // kernel form (kernel_forms, set_kernel_form)
   int tile_stages;       // shared-memory stages of the tile kernel (1 or 2)
   int tile_grid;         // its CTAs (persistent when fewer than the tiles)
   int sms;               // multiprocessors of the context's device
@@ -86,6 +88,7 @@ struct lbm_ctx {
 namespace {
 
 const uint32_t kMagic = 0x4c424d46u;  // "LBMF"
+constexpr int kAutotuneVariants = 8;   // 4 kernel forms x 2 captured periods
 const uint32_t kVersion = 2u;  // 2: float states keep g0, h0 relative to references
 
 struct StateHeader {
@@ -210,6 +213,29 @@ lbmk::TileArgs<S> tile_args(lbm_ctx* c, const lbmk::Args<float, S>& a) {
 void set_tile_config(lbm_ctx* c, int stages, int per_sm) {
   c->tile_stages = stages;
   c->tile_grid = per_sm > 0 ? std::max(1, std::min(c->nblocks, per_sm * c->sms)) : c->nblocks;
+}
+
+// Kernel forms of the step (lbm_autotune): float contexts 0 one CTA per
+// tile, 1 TMA-staged, one stage, one CTA per tile, 2 TMA-staged, two stages,
+// two persistent CTAs per SM, 3 TMA-staged, one stage, three persistent CTAs
+// per SM; FP64 contexts 0 fused, 1 two-kernel split; tangent contexts 0.
+int kernel_forms(const lbm_ctx* c) {
+  if (c->tangent) return 1;
+  if (c->p.precision == LBM_FP64) return 2;
+  return c->tile_ok ? 4 : 1;
+}
+
+void set_kernel_form(lbm_ctx* c, int form) {
+  c->form = form;
+  if (c->p.precision == LBM_FP64 && !c->tangent) {
+    c->split = form == 1;
+    return;
+  }
+  c->split = false;
+  c->tile = c->tile_ok && form >= 1;
+  if (form == 1) set_tile_config(c, 1, 0);
+  else if (form == 2) set_tile_config(c, 2, 2);
+  else if (form == 3) set_tile_config(c, 1, 3);
 }
 
 // A tile kernel whose copies did not arrive within its bounded wait sets
@@ -465,32 +491,36 @@ int lbm_create(const lbm_params* params, lbm_ctx** out) {
   if (e == cudaSuccess) e = dev_malloc((void**)&c->status, sizeof(unsigned));
   if (e == cudaSuccess) e = cudaMemset(c->status, 0, sizeof(unsigned));
   if (e == cudaSuccess && (params->precision == LBM_FP32 || params->precision == LBM_FP16S)) {
-    // float contexts step through the TMA-staged tile kernel unless
-    // LBM_STEP_KERNEL=fused asks for the one-CTA-per-tile kernel
-    const char* k = std::getenv("LBM_STEP_KERNEL");
-    const bool want = !(k && std::strcmp(k, "fused") == 0);
+    // the TMA-staged tile kernel needs its tensor maps and shared-memory sizes
     const bool maps = params->precision == LBM_FP32
                           ? make_tile_maps<float>(c, CU_TENSOR_MAP_DATA_TYPE_FLOAT32)
                           : make_tile_maps<__half>(c, CU_TENSOR_MAP_DATA_TYPE_FLOAT16);
-    if (want && maps) {
+    int dev = 0, sms = 0;
+    e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    c->sms = std::max(1, sms);
+    if (e == cudaSuccess && maps)
       e = params->precision == LBM_FP32 ? lbmk::prepare_tile_f32() : lbmk::prepare_tile_f16s();
-      int dev = 0, sms = 0;
-      if (e == cudaSuccess) e = cudaGetDevice(&dev);
-      if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-      c->sms = std::max(1, sms);
-      // LBM_TILE=<stages>:<CTAs per SM> (0: one CTA per tile) chooses the
-      // configuration; the default is two stages, two persistent CTAs per SM
-      int st = 2, per = 2;
-      if (const char* v = std::getenv("LBM_TILE")) {
-        int a = 0, b = 0;
-        if (std::sscanf(v, "%d:%d", &a, &b) == 2 && (a == 1 || a == 2) && b >= 0 && b <= 4) {
-          st = a;
-          per = b;
-        }
+    c->tile_ok = e == cudaSuccess && maps;
+    // Default kernel form (lbm_autotune measures them all): one CTA per
+    // tile from global loads on grids of fewer than eight tiles per
+    // multiprocessor, where every tile's loads and compute overlap with
+    // the other resident CTAs'; the TMA-staged form with one CTA per tile on
+    // larger grids.  LBM_STEP_KERNEL=fused forces the first,
+    // LBM_TILE=<stages>:<CTAs per SM> (0: one CTA per tile) a tile kernel.
+    int form = (c->tile_ok && c->nblocks >= 8 * c->sms) ? 1 : 0;
+    if (const char* v = std::getenv("LBM_TILE")) {
+      int a = 0, b = 0;
+      if (c->tile_ok && std::sscanf(v, "%d:%d", &a, &b) == 2 && (a == 1 || a == 2) && b >= 0 &&
+          b <= 4) {
+        set_kernel_form(c, 1);
+        set_tile_config(c, a, b);
+        form = -1;
       }
-      set_tile_config(c, st, per);
-      c->tile = e == cudaSuccess;
     }
+    if (const char* k = std::getenv("LBM_STEP_KERNEL"))
+      if (std::strcmp(k, "fused") == 0) form = 0;
+    if (form >= 0) set_kernel_form(c, form);
   }
   if (e == cudaSuccess)
     e = host_alloc((void**)&c->h_diag, dmul * (lbmk::NDIAG + 1) * sizeof(double));
@@ -1613,23 +1643,23 @@ extern "C" int lbm_autotune(lbm_ctx* c, int steps_per_trial, void* stream, doubl
   const int cur = c->cur;
   const int64_t step = c->step, diag_step = c->diag_step;
   const bool have_diag = c->have_diag, pending = c->diag_pending;
-  const bool split0 = c->split, graphs0 = c->graphs;
-  const int gmin0 = c->graph_min;
+  const bool graphs0 = c->graphs;
+  const int gmin0 = c->graph_min, form0 = c->form;
   e = cudaMemcpyAsync(backup, c->pop[cur], pb, cudaMemcpyDeviceToDevice, s);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync((char*)backup + pb, c->lag[cur], lb, cudaMemcpyDeviceToDevice, s);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync((char*)backup + pb + lb, c->diag_partial, db, cudaMemcpyDeviceToDevice, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-  // variants: kernel form (fused, split) x shortest captured period (32, 256)
-  const bool split_ok = c->p.precision == LBM_FP64;
-  double us[4] = {-1.0, -1.0, -1.0, -1.0};
+  // variants: kernel form (v / 2) x shortest captured period (32, 256)
+  const int nforms = kernel_forms(c);
+  double us[kAutotuneVariants];
+  for (int v = 0; v < kAutotuneVariants; v++) us[v] = -1.0;
   cudaEvent_t t0 = nullptr, t1 = nullptr;
   if (e == cudaSuccess) e = cudaEventCreate(&t0);
   if (e == cudaSuccess) e = cudaEventCreate(&t1);
-  for (int v = 0; v < 4 && e == cudaSuccess; v++) {
-    if (v >= 2 && !split_ok) break;
-    c->split = v >= 2;
+  for (int v = 0; v < 2 * nforms && e == cudaSuccess; v++) {
+    set_kernel_form(c, v / 2);
     c->graphs = graphs0;
     c->graph_min = (v & 1) ? 256 : 32;
     c->gen++;  // another kernel form: nothing captured before applies
@@ -1650,7 +1680,7 @@ extern "C" int lbm_autotune(lbm_ctx* c, int steps_per_trial, void* stream, doubl
     }
   }
   int best = 0;
-  for (int v = 1; v < 4; v++)
+  for (int v = 1; v < kAutotuneVariants; v++)
     if (us[v] > 0.0 && us[v] < us[best]) best = v;
   // restore the state, keep the fastest variant
   cudaError_t er = cudaMemcpyAsync(c->pop[cur], backup, pb, cudaMemcpyDeviceToDevice, s);
@@ -1667,10 +1697,10 @@ extern "C" int lbm_autotune(lbm_ctx* c, int steps_per_trial, void* stream, doubl
   c->gen++;
   c->graphs = graphs0;
   if (e == cudaSuccess && er == cudaSuccess) {
-    c->split = best >= 2;
+    set_kernel_form(c, best / 2);
     c->graph_min = (best & 1) ? 256 : 32;
   } else {
-    c->split = split0;
+    set_kernel_form(c, form0);
     c->graph_min = gmin0;
   }
   if (t0) cudaEventDestroy(t0);
@@ -1679,7 +1709,7 @@ extern "C" int lbm_autotune(lbm_ctx* c, int steps_per_trial, void* stream, doubl
   if (e != cudaSuccess) return cuda_fail(c, e, "autotune trial");
   if (er != cudaSuccess) return cuda_fail(c, er, "autotune restore");
   if (out_us)
-    for (int v = 0; v < 4; v++) out_us[v] = us[v];
+    for (int v = 0; v < kAutotuneVariants; v++) out_us[v] = us[v];
   if (chosen) *chosen = best;
   c->last_stream = s;
   return LBM_OK;

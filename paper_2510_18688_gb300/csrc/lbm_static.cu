@@ -6,8 +6,10 @@
 // partial per diagnostic per CTA) in a file-scope device array instead of
 // context-owned memory.  Nothing here calls cudaMalloc, cudaFree or any
 // allocating routine.
+#include <atomic>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 
 #include <cuda_runtime.h>
 
@@ -26,22 +28,31 @@ constexpr size_t kPartials = (size_t)lbmk::NDIAG * kMaxBlocks;
 static __device__ __align__(256) double g_noalloc_scratch[kPartials];
 
 constexpr int kMaxDevices = 64;
-double* g_scratch_addr[kMaxDevices] = {nullptr};
+// Device address of the scratch, looked up once per device (first call with
+// that device current) under a lock, so that host threads making their first
+// calls at the same time agree on it.  In host code g_noalloc_scratch only
+// names a host-side stand-in, never the device memory itself.
+std::atomic<double*> g_scratch_addr[kMaxDevices];
+std::mutex g_scratch_lock;
 
-// Device address of the scratch on the current device (looked up once per
-// device; in host code g_noalloc_scratch only names a host-side stand-in).
 cudaError_t scratch_on_current_device(double** out) {
   int dev = -1;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
-  if (!g_scratch_addr[dev]) {
-    void* p = nullptr;
-    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-    if (e != cudaSuccess) return e;
-    g_scratch_addr[dev] = (double*)p;
+  double* p = g_scratch_addr[dev].load(std::memory_order_acquire);
+  if (!p) {
+    std::lock_guard<std::mutex> guard(g_scratch_lock);
+    p = g_scratch_addr[dev].load(std::memory_order_relaxed);
+    if (!p) {
+      void* q = nullptr;
+      e = cudaGetSymbolAddress(&q, g_noalloc_scratch);
+      if (e != cudaSuccess) return e;
+      p = (double*)q;
+      g_scratch_addr[dev].store(p, std::memory_order_release);
+    }
   }
-  *out = g_scratch_addr[dev];
+  *out = p;
   return cudaSuccess;
 }
 

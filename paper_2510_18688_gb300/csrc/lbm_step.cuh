@@ -345,6 +345,19 @@ __device__ __forceinline__ void collide_heat_wb(const Geom& g, const Coef<float>
 // (WB) they are remainders over 3 (w_i - delta_i0) p_src(i), the lagged
 // pressure of the node each came from (the node itself for a population a
 // wall returned), and dps holds p_src(i) - p on return.
+// sum_i w_i c_i v(x + c_i) over opposite neighbours taken in pairs: the
+// difference of two close neighbour values is exact in float, so a small
+// gradient of a large field (the pressure of a compressed gas, ~1e-9 per node
+// against p ~ 6e-4) keeps its relative precision instead of being lost in
+// the rounding of the products w_i v.
+template <typename R>
+__device__ __forceinline__ void grad_pairs(const R* v, int s, R& gx, R& gy) {
+  const R d13 = v[1] - v[-1], d24 = v[s] - v[-s];
+  const R d57 = v[s + 1] - v[-s - 1], d86 = v[-s + 1] - v[s - 1];
+  gx = qw<R>(1) * d13 + qw<R>(5) * (d57 + d86);
+  gy = qw<R>(1) * d24 + qw<R>(5) * (d57 - d86);
+}
+
 template <typename R, bool WB>
 __device__ __forceinline__ void node_macros(const Geom& g, const Coef<R>& c, int lat, int gx,
                                             int gy, bool inner, const Local<R>& L, R phi0, R pp,
@@ -353,26 +366,20 @@ __device__ __forceinline__ void node_macros(const Geom& g, const Coef<R>& c, int
                                             const R* cphi0, int sb, Macro<R>& M, R* dps) {
   R gphx = R(0), gphy = R(0), lphi = R(0), lphi0 = R(0), lfs = R(0);
   R grx = R(0), gry = R(0), gpx = R(0), gpy = R(0);
+  if (lat & LAT_PHASE) {
 #pragma unroll
-  for (int i = 1; i < 9; i++) {
-    const int oh = qy(i) * sh + qx(i), ob = qy(i) * sb + qx(i);
-    const R wi = qw<R>(i);
-    const R cxi = R(qx(i)), cyi = R(qy(i));
-    if (lat & LAT_PHASE) {
-      const R ph = cphi[oh];
-      gphx += wi * cxi * ph;
-      gphy += wi * cyi * ph;
-      lphi += R(2) * wi * (ph - cphi[0]);
+    for (int i = 1; i < 9; i++) {
+      const int oh = qy(i) * sh + qx(i), ob = qy(i) * sb + qx(i);
+      const R wi = qw<R>(i);
+      lphi += R(2) * wi * (cphi[oh] - cphi[0]);
       lphi0 += R(2) * wi * (cphi0[ob] - cphi0[0]);
       lfs += R(2) * wi * (cfs[oh] - cfs[0]);
     }
-    if (lat & LAT_FLOW) {
-      const R rq = crho[oh], pq = cp[ob];
-      grx += wi * cxi * rq;
-      gry += wi * cyi * rq;
-      gpx += wi * cxi * pq;
-      gpy += wi * cyi * pq;
-    }
+    grad_pairs(cphi, sh, gphx, gphy);
+  }
+  if (lat & LAT_FLOW) {
+    grad_pairs(crho, sh, grx, gry);
+    grad_pairs(cp, sb, gpx, gpy);
   }
   gphx *= R(3); gphy *= R(3); lphi *= R(3); lphi0 *= R(3); lfs *= R(3);
   grx *= R(3); gry *= R(3); gpx *= R(3); gpy *= R(3);
@@ -686,12 +693,18 @@ __device__ __forceinline__ void step_tile(const Args<R, S>& a, int bx, int by, i
   __syncthreads();
 
   // ---- phase B: stencils, macros, collisions, streaming -------------------
+  // Instantiated twice: for a tile whose nodes and ring are all inside the
+  // grid (block-uniform branch) every node is valid and every link stays in
+  // the grid, so that path carries no boundary logic at all.
+  auto phase_b = [&](auto interior) {
+  constexpr bool IN = decltype(interior)::value;
   R dvals[NDIAG];
   Macro<R> M;
   // links that stay inside the grid need no boundary logic
-  const bool inner = gx > 0 && gx < g.nx - 1 && gy > 0 && gy < g.ny - 1;
+  const bool inner = IN || (gx > 0 && gx < g.nx - 1 && gy > 0 && gy < g.ny - 1);
+  const bool valid_n = IN || valid;
   R dps[WB ? 9 : 1];  // well-balanced flow storage: p_src(i) - p
-  if (valid) {
+  if (valid_n) {
     const int hc = (ty + 1) * HX + (tx + 1);
     if (STASHF && (lat & LAT_FLOW)) {
 #pragma unroll
@@ -708,7 +721,7 @@ __device__ __forceinline__ void step_tile(const Args<R, S>& a, int bx, int by, i
   }
   if (DIAG) block_diag_warps(dvals, s_red, tid);
 
-  if (valid) {
+  if (valid_n) {
     const R phi = L.phi, fs = L.fs, rho = L.rho, T = L.T, mdot = L.mdot;
 
     if (MODE == MODE_STEP) {
@@ -780,6 +793,9 @@ __device__ __forceinline__ void step_tile(const Args<R, S>& a, int bx, int by, i
         if (a.out[k]) put_out(a.out[k], d, (long long)g.nx * g.ny, vals[k]);
     }
   }
+  };
+  if (x0 >= 1 && x0 + TX < g.nx && y0 >= 1 && y0 + TY < g.ny) phase_b(std::true_type{});
+  else phase_b(std::false_type{});
   if (DIAG) {
     if (b < 0) block_diag_finish(s_red, a.diag_partial, tid, blockIdx.y * gridDim.x + blockIdx.x,
                                  gridDim.x * gridDim.y);

@@ -215,11 +215,16 @@ __device__ __forceinline__ void tile_step(const Args<float, S>& a, const TileSta
   __syncthreads();
 
   // ---- phase B: stencils, macros, collisions, streaming -------------------
+  // Instantiated twice: for a tile whose nodes and ring are all inside the
+  // grid (block-uniform branch) no node needs boundary logic.
+  auto phase_b = [&](auto interior) {
+  constexpr bool IN = decltype(interior)::value;
   R dvals[NDIAG];
   Macro<R> M;
-  const bool inner = gx > 0 && gx < g.nx - 1 && gy > 0 && gy < g.ny - 1;
+  const bool inner = IN || (gx > 0 && gx < g.nx - 1 && gy > 0 && gy < g.ny - 1);
+  const bool valid_n = IN || valid;
   R f[9], dps[9];
-  if (valid) {
+  if (valid_n) {
     if (lat & LAT_FLOW) {
 #pragma unroll
       for (int i = 0; i < 9; i++) f[i] = lds(&st.f[i][ty][tx]);
@@ -234,7 +239,7 @@ __device__ __forceinline__ void tile_step(const Args<float, S>& a, const TileSta
   }
   if (DIAG) block_diag_warps(dvals, s_red, tid);
 
-  if (valid) {
+  if (valid_n) {
     S* out = a.pout;
     if (lat & LAT_FLOW) {
       if (inner) collide_flow_wb<true>(g, c, out, P, gx, gy, n, f, dps, L.rho, M);
@@ -281,6 +286,9 @@ __device__ __forceinline__ void tile_step(const Args<float, S>& a, const TileSta
     a.lout[LAG_Q * P + n] = (lat & LAT_HEAT) ? M.cap * L.T * L.mdot : R(0);
     a.lout[LAG_T * P + n] = L.T;
   }
+  };
+  if (x0 >= 1 && x0 + TX < g.nx && y0 >= 1 && y0 + TY < g.ny) phase_b(std::true_type{});
+  else phase_b(std::false_type{});
   if (DIAG) block_diag_finish(s_red, a.diag_partial, tid, b, nb);
 }
 

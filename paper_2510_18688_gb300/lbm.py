@@ -299,7 +299,7 @@ VARIANTS = ("fused, periods >= 32", "fused, periods >= 256", "split, periods >= 
 
 def lbm_autotune(ctx, steps_per_trial: int = 64, stream=None):
     """(microseconds per step of each variant, index kept); see include/lbm.h."""
-    us = (ctypes.c_double * 4)()
+    us = (ctypes.c_double * 8)()
     chosen = ctypes.c_int()
     _check(ctx, load().lbm_autotune(ctx, int(steps_per_trial), stream, us, ctypes.byref(chosen)),
            "lbm_autotune")

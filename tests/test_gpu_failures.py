@@ -47,7 +47,8 @@ def test_every_allocation_failure_of_lbm_create_is_clean():
 
 
 @pytest.mark.parametrize("prec", ["fp32", "fp16s"])
-def test_tile_wait_timeout_is_reported(prec):
+@pytest.mark.parametrize("tile", ["1:0", "2:2"])
+def test_tile_wait_timeout_is_reported(prec, tile, monkeypatch):
     """The float step's tile kernel waits for its TMA copies with a bound of
     about a second.  The test hook makes every such wait run out (the
     kernel expects 16 bytes more than its copies deliver; nothing is left in
@@ -60,6 +61,7 @@ def test_tile_wait_timeout_is_reported(prec):
     build.build()
     lbm.load()
     cfg, arr = W.random_state(70, 45, seed=4)
+    monkeypatch.setenv("LBM_TILE", tile)  # the tile kernel in this configuration
     s = lbm.Solver(cfg, precision=prec).set_geometry(arr)
     lbm.lbm_debug_tile_timeout(True)
     try:

@@ -445,7 +445,9 @@ def test_autotune_keeps_the_state_and_picks_a_variant(env, prec):
     for k in FIELDS:
         assert np.array_equal(before[k], after[k]), k
     assert s.steps_done == 5
-    n_variants = 4 if prec == "fp64" else 2  # the two-kernel form is FP64 only
+    # FP64: fused and two-kernel split; float: four kernel forms (one CTA
+    # per tile, three TMA-staged tile configurations); x two graph periods
+    n_variants = 4 if prec == "fp64" else 8
     assert all(u > 0 for u in us[:n_variants]) and all(u == -1.0 for u in us[n_variants:])
     assert 0 <= chosen < n_variants and us[chosen] == min(us[:n_variants])
     s.step(40)
@@ -564,24 +566,37 @@ def test_batch_of_more_than_64_grids(env):
 
 
 @pytest.mark.parametrize("prec", ["fp32", "fp16s"])
-@pytest.mark.parametrize("wl", ["random", "droplet", "subset"])
+@pytest.mark.parametrize("wl", ["random", "droplet", "subset", "tiles2"])
 def test_tile_kernel_matches_one_cta_per_tile_kernel(env, prec, wl, monkeypatch):
     """The float step runs as the persistent TMA-staged tile kernel; the
     one-CTA-per-tile kernel (LBM_STEP_KERNEL=fused) computes the same
-    arithmetic from global loads.  Same fields up to the last bits of float
-    (the compiler may fuse multiply-adds differently), and the same state
-    after a checkpoint round trip between them."""
+    arithmetic from global loads.  FP32: the same fields up to the last bits
+    of float (the compiler may contract multiply-adds differently in the
+    two kernels).  FP16 storage: such a last-bit difference now and then
+    flips the binary16 rounding of a stored population, and the two runs
+    then drift apart by up to the format's own error, so each field of the
+    two is held within twice its distance from the FP64 state (the triangle
+    bound for two runs each that far from it)."""
     O, lbm = env
     cfg, arr = {"random": lambda: W.random_state(101, 37, seed=21),
                 "droplet": lambda: W.sessile_droplet(160, seed=2, radius=40),
-                "subset": lambda: W.random_state(67, 29, seed=22, lattices=5)}[wl]()
+                "subset": lambda: W.random_state(67, 29, seed=22, lattices=5),
+                "tiles2": lambda: W.sessile_droplet(256, seed=4, radius=60)}[wl]()
+    # the two-stage persistent form on a grid with several tiles per CTA
+    monkeypatch.setenv("LBM_TILE", "2:2" if wl == "tiles2" else "1:0")
     a = lbm.Solver(cfg, precision=prec).set_geometry(arr).step(60)
+    monkeypatch.delenv("LBM_TILE")
     monkeypatch.setenv("LBM_STEP_KERNEL", "fused")
     b = lbm.Solver(cfg, precision=prec).set_geometry(arr).step(60)
     fa, fb = a.fields(), b.fields()
+    if prec == "fp16s":
+        c = lbm.Solver(cfg, precision="fp64").set_geometry(arr).step(60)
+        fc = c.fields()
+        c.close()
     for k in FIELDS:
         e = _l2_rel(fa[k], fb[k])
-        assert e <= (1e-5 if prec == "fp32" else 5e-3), (k, e)
+        bound = 1e-5 if prec == "fp32" else max(1e-5, 2 * _l2_rel(fb[k], fc[k]))
+        assert e <= bound, (k, e, bound)
     da, db = a.diagnostics(compute=True), b.diagnostics(compute=True)
     assert abs(da["material_mass"] - db["material_mass"]) <= 1e-6 * abs(db["material_mass"])
     a.close()

@@ -374,3 +374,26 @@ def test_flat_interface_stays_stationary(O):
     c1 = crossings(f[1])
     assert len(c1) == 2 and np.abs(c1 - c0).max() < 1e-3, (c0, c1)
     assert abs(f[1, 48] - 1.0) < 1e-5 and abs(f[1, 0] + 1.0) < 1e-5
+
+
+@pytest.mark.xfail(strict=True, reason=(
+    "the configured gas/liquid density ratio 0.001 of Sec. 4.2 diverges under the readings "
+    "used (about step 19,000 of this column: the compressed light gas heats past T0, then "
+    "the state turns non-finite; taking the flow's own div u in the enthalpy source does not "
+    "cure it); the workloads run at 0.1"))
+def test_stefan_column_at_the_configured_gas_density_ratio(O):
+    """Records the known limitation: the three-phase Stefan column of Sec. 4.2
+    with rho_g/rho_l = 0.001 (the paper's value) stays finite and bounded
+    (T within [T_b, T0] up to 1 %, |phi| <= 1.02) for 22,000 steps.  Strict
+    xfail: a change of reading that cures it makes this test pass and
+    therefore fail the suite, so the fix cannot go unnoticed."""
+    cfg, arr = W.stefan()
+    rg = 0.001
+    cfg = dict(cfg, rho_g=rg, mu_g=rg * 0.1, cp_g=cfg["cp_l"] * cfg["rho_l"] / rg)
+    o = _run(O, (cfg, arr))
+    o.step(22000)
+    f = o.fields()
+    assert o.diagnostics()["nonfinite"] == 0
+    assert np.isfinite(f["T"]).all() and np.isfinite(f["phi"]).all()
+    assert f["T"].max() <= 1.01 and f["T"].min() >= -1.01
+    assert np.abs(f["phi"]).max() <= 1.02
