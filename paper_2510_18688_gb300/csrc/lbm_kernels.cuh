@@ -69,15 +69,28 @@ __device__ __forceinline__ R qw(int i) {
   return i == 0 ? R(4.0 / 9.0) : (i <= 4 ? R(1.0 / 9.0) : R(1.0 / 36.0));
 }
 
-// Division: IEEE in double; in float the fast approximate form (relative
-// error of a few ulp, far below the float parity bar), or the IEEE one when
-// built with LBM_F32_FAST_DIV=0.
+// Division: IEEE in double.  In float, the quotient from the approximate
+// reciprocal (PTX rcp.approx.f32) with one Newton correction on the exact
+// residual (Markstein's correction step: e = a - q0 b by FMA, q = q0 + e r),
+// which leaves an error of about one ulp without the plain approximate
+// quotient's one-sided bias: an error that repeats every step at a slowly
+// changing node (1 - mdot/2 in the order parameter, the heat capacity in the
+// temperature) would otherwise accumulate.  The divisors are positive normal
+// numbers (densities, heat capacities, relaxation times, 1 - mdot/2).  Built
+// with LBM_F32_FAST_DIV=0, the IEEE quotient instead.
 #ifndef LBM_F32_FAST_DIV
 #define LBM_F32_FAST_DIV 1
 #endif
 __device__ __forceinline__ double qdiv(double a, double b) { return a / b; }
 __device__ __forceinline__ float qdiv(float a, float b) {
-  return LBM_F32_FAST_DIV ? __fdividef(a, b) : __fdiv_rn(a, b);
+#if LBM_F32_FAST_DIV
+  float r;
+  asm("rcp.approx.f32 %0, %1;" : "=f"(r) : "f"(b));
+  const float q0 = a * r;
+  return fmaf(fmaf(-q0, b, a), r, q0);
+#else
+  return __fdiv_rn(a, b);
+#endif
 }
 
 // Per-context constants (derived on the host by lbm_create).

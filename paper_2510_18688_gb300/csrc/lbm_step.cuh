@@ -206,17 +206,16 @@ __device__ __forceinline__ bool upstream_wall(const Geom& g, int x, int y, int i
          (ty < 0 && g.bc[2] != BC_PERIODIC) || (ty >= g.ny && g.bc[3] != BC_PERIODIC);
 }
 
-// Flow collision Eqs. (11), (14)-(16) and push for remainders: fr[i] = f_i -
-// 3 (w_i - delta_i0) p_src(i), dps[i] = p_src(i) - p (p = M.pr, the node's new
-// pressure as stored, which the remainders are referred to; the exact
-// pressure is p + M.prl).  The pressure part of the equilibrium and the
-// references then meet as f*_i - 3 (w_i - delta_i0) p = (1 - 1/tau) (fr_i +
-// 3 (w_i - delta_i0) dps_i) + (rho s_i + 3 (w_i - delta_i0) prl) / tau +
-// (1 - 1/2tau) F_i.
+// Flow collision Eqs. (11), (14)-(16) and push for remainders: fb[i] = f_i -
+// 3 (w_i - delta_i0) p, the populations referred to p = M.pr, the node's new
+// pressure as stored (node_macros forms them; the exact pressure is p +
+// M.prl).  The pressure part of the equilibrium and the references then meet
+// as f*_i - 3 (w_i - delta_i0) p = (1 - 1/tau) fb_i + (rho s_i + 3 (w_i -
+// delta_i0) prl) / tau + (1 - 1/2tau) F_i.
 template <bool INNER, typename S>
 __device__ __forceinline__ void collide_flow_wb(const Geom& g, const Coef<float>& c,
                                                 S* __restrict__ out, int P, int x, int y, int n,
-                                                const float* fr, const float* dps, float rho,
+                                                const float* fb, float rho,
                                                 const Macro<float>& M) {
   const float itau = qdiv(1.f, M.tauf);
   const float omi = 1.f - itau;
@@ -227,9 +226,8 @@ __device__ __forceinline__ void collide_flow_wb(const Geom& g, const Coef<float>
   {
     float F0 = fsym0;
     if (iso) F0 += M.S * (0.f - 2.f / 3.f) * 1.5f;
-    const float base = fr[0] + 3.f * (qw<float>(0) - 1.f) * dps[0];
     push<float, INNER, false>(g, c, out, P, 0, x, y, n,
-                              base * omi +
+                              fb[0] * omi +
                                   itau * (qw<float>(0) * sym0 + 3.f * (qw<float>(0) - 1.f) * M.prl) +
                                   fcoef * qw<float>(0) * F0);
   }
@@ -248,9 +246,8 @@ __device__ __forceinline__ void collide_flow_wb(const Geom& g, const Coef<float>
     const float srcA = 3.f * cF;
     const float Ps = wi * (itau * eqS + fcoef * srcS);
     const float Pa = wi * (itau * eqA + fcoef * srcA);
-    const float bi = fr[i] + 3.f * wi * dps[i], bo = fr[o] + 3.f * wi * dps[o];
-    push<float, INNER, false>(g, c, out, P, i, x, y, n, bi * omi + Ps + Pa);
-    push<float, INNER, false>(g, c, out, P, o, x, y, n, bo * omi + Ps - Pa);
+    push<float, INNER, false>(g, c, out, P, i, x, y, n, fb[i] * omi + Ps + Pa);
+    push<float, INNER, false>(g, c, out, P, o, x, y, n, fb[o] * omi + Ps - Pa);
   }
 }
 
@@ -344,7 +341,8 @@ __device__ __forceinline__ void collide_heat_wb(const Geom& g, const Coef<float>
 // stride sb.  f: the node's flow populations; with well-balanced storage
 // (WB) they are remainders over 3 (w_i - delta_i0) p_src(i), the lagged
 // pressure of the node each came from (the node itself for a population a
-// wall returned), and dps holds p_src(i) - p on return.
+// wall returned), and on return they are referred to the node's new pressure
+// M.pr instead (the form collide_flow_wb takes).
 // sum_i w_i c_i v(x + c_i) over opposite neighbours taken in pairs: the
 // difference of two close neighbour values is exact in float, so a small
 // gradient of a large field (the pressure of a compressed gas, ~1e-9 per node
@@ -361,9 +359,9 @@ __device__ __forceinline__ void grad_pairs(const R* v, int s, R& gx, R& gy) {
 template <typename R, bool WB>
 __device__ __forceinline__ void node_macros(const Geom& g, const Coef<R>& c, int lat, int gx,
                                             int gy, bool inner, const Local<R>& L, R phi0, R pp,
-                                            const R* f, const R* cphi, const R* cfs,
+                                            R* f, const R* cphi, const R* cfs,
                                             const R* crho, int sh, const R* cp,
-                                            const R* cphi0, int sb, Macro<R>& M, R* dps) {
+                                            const R* cphi0, int sb, Macro<R>& M) {
   R gphx = R(0), gphy = R(0), lphi = R(0), lphi0 = R(0), lfs = R(0);
   R grx = R(0), gry = R(0), gpx = R(0), gpy = R(0);
   if (lat & LAT_PHASE) {
@@ -404,6 +402,7 @@ __device__ __forceinline__ void node_macros(const Geom& g, const Coef<R>& c, int
     R jx = (f[1] - f[3]) + (f[5] - f[6]) + (f[8] - f[7]);
     R jy = (f[2] - f[4]) + (f[5] + f[6]) - (f[7] + f[8]);
     R snz = (f[1] + f[2] + f[3] + f[4]) + (f[5] + f[6] + f[7] + f[8]);
+    R dps[WB ? 9 : 1];  // well-balanced storage: p_src(i) - pp, then p_src(i) - p
     if constexpr (WB) {
       // add the moments of the references 3 w_i p_src(i), as differences
       // from the node's own lagged pressure pp (whose share, 3 (1 - w_0) pp
@@ -451,6 +450,10 @@ __device__ __forceinline__ void node_macros(const Geom& g, const Coef<R>& c, int
       M.prl = (pp - (M.pr - bb)) + (dp - bb);
 #pragma unroll
       for (int i = 0; i < 9; i++) dps[i] -= bb;  // p_src(i) - p
+      // the populations referred to the new pressure
+      f[0] += R(3) * (qw<R>(0) - R(1)) * dps[0];
+#pragma unroll
+      for (int i = 1; i < 9; i++) f[i] += R(3) * qw<R>(i) * dps[i];
     } else {
       M.pr = dp;
     }
@@ -703,7 +706,6 @@ __device__ __forceinline__ void step_tile(const Args<R, S>& a, int bx, int by, i
   // links that stay inside the grid need no boundary logic
   const bool inner = IN || (gx > 0 && gx < g.nx - 1 && gy > 0 && gy < g.ny - 1);
   const bool valid_n = IN || valid;
-  R dps[WB ? 9 : 1];  // well-balanced flow storage: p_src(i) - p
   if (valid_n) {
     const int hc = (ty + 1) * HX + (tx + 1);
     if (STASHF && (lat & LAT_FLOW)) {
@@ -711,7 +713,7 @@ __device__ __forceinline__ void step_tile(const Args<R, S>& a, int bx, int by, i
       for (int i = 0; i < 9; i++) f[i] = s_fpop[STASHF ? i : 0][tid];
     }
     node_macros<R, WB>(g, c, lat, gx, gy, inner, L, phi0, pp, f, s_phi + hc, s_fs + hc,
-                       s_rho + hc, HX, s_p + hc, s_phi0 + hc, HX, M, dps);
+                       s_rho + hc, HX, s_p + hc, s_phi0 + hc, HX, M);
     // diagnostics of this state, reduced over the warp before the
     // collisions so that none of their inputs stays live through them
     if (DIAG) diag_values(c, lat, L, M, sg, sh, f, dvals);
@@ -728,8 +730,8 @@ __device__ __forceinline__ void step_tile(const Args<R, S>& a, int bx, int by, i
       S* out = a.pout;
       if (lat & LAT_FLOW) {
         if constexpr (WB) {
-          if (inner) collide_flow_wb<true>(g, c, out, P, gx, gy, n, f, dps, rho, M);
-          else collide_flow_wb<false>(g, c, out, P, gx, gy, n, f, dps, rho, M);
+          if (inner) collide_flow_wb<true>(g, c, out, P, gx, gy, n, f, rho, M);
+          else collide_flow_wb<false>(g, c, out, P, gx, gy, n, f, rho, M);
         } else {
           if (inner) collide_flow<R, true>(g, c, out, P, gx, gy, n, f, rho, M);
           else collide_flow<R, false>(g, c, out, P, gx, gy, n, f, rho, M);

@@ -223,7 +223,7 @@ __device__ __forceinline__ void tile_step(const Args<float, S>& a, const TileSta
   Macro<R> M;
   const bool inner = IN || (gx > 0 && gx < g.nx - 1 && gy > 0 && gy < g.ny - 1);
   const bool valid_n = IN || valid;
-  R f[9], dps[9];
+  R f[9];
   if (valid_n) {
     if (lat & LAT_FLOW) {
 #pragma unroll
@@ -231,7 +231,7 @@ __device__ __forceinline__ void tile_step(const Args<float, S>& a, const TileSta
     }
     node_macros<R, true>(g, c, lat, gx, gy, inner, L, phi0, pp, f, s_phi + hc, s_fs + hc,
                          s_rho + hc, HX, lag + LAG_P * PL + cl, &st.phi0[ty + 1][tx + St::XL],
-                         St::WL, M, dps);
+                         St::WL, M);
     if (DIAG) diag_values(c, lat, L, M, sg, sh, f, dvals);
   } else if (DIAG) {
 #pragma unroll
@@ -242,8 +242,8 @@ __device__ __forceinline__ void tile_step(const Args<float, S>& a, const TileSta
   if (valid_n) {
     S* out = a.pout;
     if (lat & LAT_FLOW) {
-      if (inner) collide_flow_wb<true>(g, c, out, P, gx, gy, n, f, dps, L.rho, M);
-      else collide_flow_wb<false>(g, c, out, P, gx, gy, n, f, dps, L.rho, M);
+      if (inner) collide_flow_wb<true>(g, c, out, P, gx, gy, n, f, L.rho, M);
+      else collide_flow_wb<false>(g, c, out, P, gx, gy, n, f, L.rho, M);
     }
     if (lat & LAT_PHASE) {
       R gq[9];

@@ -64,7 +64,7 @@ def _compare(got, ref, prec, tol=None, fields=FIELDS):
             t = 1e-10 if tol is None else tol
         else:
             e = _vel_l2_rel(got, ref) if k in ("ux", "uy") else _l2_rel(got[k], ref[k])
-            t = (1e-3 if k == "mdot" else 1e-4) if tol is None else tol
+            t = 1e-4 if tol is None else tol
         if not e <= t:
             bad[k] = e
     assert not bad, f"{prec}: fields off the oracle: {bad}"
