@@ -733,10 +733,12 @@ def main():
     if batch is None and not args.no_autotune:
         us, chosen = solvers[0].autotune(64)
         tune = {"chosen": chosen, "us_per_step": us,
-                "variants": "kernel form v//2 (float: 0 one CTA per tile, 1 TMA-staged one "
-                            "stage, 2 TMA-staged two stages 2 CTAs/SM, 3 TMA-staged one "
-                            "stage 3 CTAs/SM; fp64: 0 fused, 1 split) x captured period "
-                            "(v even 32, odd 256); timed back to back without L2 flush"}
+                "variants": "kernel form v//2 (0 one CTA per 32x8 tile; 1 float TMA-staged "
+                            "one stage / fp64 two-kernel split; 2 TMA-staged two stages "
+                            "2 CTAs/SM; 3 TMA-staged one stage 3 CTAs/SM; 4 one CTA per "
+                            "32x4 tile; 5 one CTA per 32x16 tile; -1: not available) x "
+                            "captured period (v even 32, odd 256); timed back to back "
+                            "without L2 flush"}
 
     def step(k):
         if batch is not None:

@@ -422,19 +422,24 @@ int lbm_adjoint_coupled(lbm_ctx* ctx, int64_t nsteps, int every, int observable,
  * library): times the step forms the library has on the context's own grid
  * and state and keeps the fastest for later lbm_step calls.  Variant v is
  * kernel form v / 2 with captured periods of at least 32 steps (v even) or
- * 256 (v odd).  Kernel forms: LBM_FP32 and LBM_FP16S 0 one CTA per 32 x 8
- * tile loading from global memory, 1 the TMA-staged tile kernel with one
- * shared-memory stage and one CTA per tile, 2 the same with two stages and
- * two persistent CTAs per multiprocessor (the copies of the next tile
- * overlap the current one), 3 one stage and three persistent CTAs per
- * multiprocessor; LBM_FP64 0 fused, 1 the two-kernel split; tangent
+ * 256 (v odd).  Kernel forms (form ids; a context times those it has):
+ * 0 one CTA per 32 x 8 tile loading from global memory (every precision);
+ * 1 LBM_FP32/LBM_FP16S: the TMA-staged tile kernel with one shared-memory
+ * stage and one CTA per tile, LBM_FP64: the two-kernel split; 2 (float) the
+ * TMA-staged kernel with two stages and two persistent CTAs per
+ * multiprocessor (the copies of the next tile overlap the current one);
+ * 3 (float) one stage and three persistent CTAs per multiprocessor; 4 one
+ * CTA per 32 x 4 tile; 5 one CTA per 32 x 16 tile (4 and 5: LBM_FP32,
+ * LBM_FP16S, LBM_FP64).  Tangent
  * contexts 0.  Each variant runs steps_per_trial steps twice from the same
  * saved state (the first run warms up and captures; the second is timed
  * with CUDA events on `stream`).  The state, step counter and diagnostics
  * (including partial sums not yet read) are restored afterwards, so the
- * call does not advance the simulation.  out_us (8 doubles, may be NULL):
+ * call does not advance the simulation.  out_us (12 doubles, may be NULL):
  * microseconds per step of each variant (-1 where not run); chosen (may be
- * NULL): the index kept.  Allocates a backup of the state (its population
+ * NULL): the index kept.  The environment variable LBM_KERNEL_FORM=<form id>
+ * read by lbm_create selects a form without timing (ignored where the
+ * context does not have it).  Allocates a backup of the state (its population
  * and lag planes) for the duration of the call and synchronises `stream`.
  * Errors: LBM_ERR_ARG (steps_per_trial < 2), LBM_ERR_STATE before
  * lbm_set_geometry, LBM_ERR_OOM/LBM_ERR_CUDA. */

@@ -58,7 +58,8 @@ struct lbm_ctx {
   // float contexts: the step as the TMA-staged tile kernel (lbm_tile.cuh)
   bool tile;
   bool tile_ok;          // the tile kernel's tensor maps exist (float contexts)
-  int form;              // kernel form (kernel_forms, set_kernel_form)
+  int form;              // kernel form (form_available, set_kernel_form)
+  int ty;                // tile height of the one-CTA-per-tile step (4, 8 or 16)
   int tile_stages;       // shared-memory stages of the tile kernel (1 or 2)
   int tile_grid;         // its CTAs (persistent when fewer than the tiles)
   int sms;               // multiprocessors of the context's device
@@ -71,7 +72,9 @@ struct lbm_ctx {
   bool diag_pending;     // partials written, grid-wide sum not yet taken
   int64_t diag_step;     // state index of the pending partials
   cudaStream_t last_stream;
-  int nblocks;
+  int nblocks;            // 32 x 8 tiles of the grid
+  int diag_nb;            // per-CTA diagnostic partials written by the last diagnosed launch
+  int diag_cap;           // partials the array holds (the most any tile shape writes)
   // captured steps: one period of the step sequence, replayed whole
   bool graphs;           // replay captured periods (default; LBM_STEP_GRAPHS=0 disables)
   cudaStream_t cap_stream;
@@ -88,7 +91,8 @@ struct lbm_ctx {
 namespace {
 
 const uint32_t kMagic = 0x4c424d46u;  // "LBMF"
-constexpr int kAutotuneVariants = 8;   // 4 kernel forms x 2 captured periods
+constexpr int kForms = 6;              // kernel form ids (form_available)
+constexpr int kAutotuneVariants = 2 * kForms;  // kernel forms x 2 captured periods
 const uint32_t kVersion = 2u;  // 2: float states keep g0, h0 relative to references
 
 struct StateHeader {
@@ -215,24 +219,33 @@ void set_tile_config(lbm_ctx* c, int stages, int per_sm) {
   c->tile_grid = per_sm > 0 ? std::max(1, std::min(c->nblocks, per_sm * c->sms)) : c->nblocks;
 }
 
-// Kernel forms of the step (lbm_autotune): float contexts 0 one CTA per
-// tile, 1 TMA-staged, one stage, one CTA per tile, 2 TMA-staged, two stages,
-// two persistent CTAs per SM, 3 TMA-staged, one stage, three persistent CTAs
-// per SM; FP64 contexts 0 fused, 1 two-kernel split; tangent contexts 0.
-int kernel_forms(const lbm_ctx* c) {
-  if (c->tangent) return 1;
-  if (c->p.precision == LBM_FP64) return 2;
-  return c->tile_ok ? 4 : 1;
+// Kernel forms of the step (lbm_autotune): 0 one CTA per 32 x 8 tile;
+// 1 float: TMA-staged, one stage, one CTA per tile / FP64: the two-kernel
+// split; 2 TMA-staged, two stages, two persistent CTAs per SM (float);
+// 3 TMA-staged, one stage, three persistent CTAs per SM (float); 4 one CTA
+// per 32 x 4 tile; 5 one CTA per 32 x 16 tile.  Tangent contexts: 0.
+bool form_available(const lbm_ctx* c, int form) {
+  if (form < 0 || form >= kForms) return false;
+  if (c->tangent) return form == 0;
+  if (form == 0 || form >= 4) return true;
+  if (c->p.precision == LBM_FP64) return form == 1;
+  return c->tile_ok;
+}
+
+// Tiles (CTAs, partials) of a one-CTA-per-tile launch with tiles of height ty.
+int tiles_of(const lbm_ctx* c, int ty) {
+  return ((c->g.nx + lbmk::TX - 1) / lbmk::TX) * lbmk::tiles_y(c->g.ny, ty);
 }
 
 void set_kernel_form(lbm_ctx* c, int form) {
   c->form = form;
+  c->ty = form == 4 ? 4 : (form == 5 ? 16 : lbmk::TY);
   if (c->p.precision == LBM_FP64 && !c->tangent) {
     c->split = form == 1;
     return;
   }
   c->split = false;
-  c->tile = c->tile_ok && form >= 1;
+  c->tile = c->tile_ok && form >= 1 && form <= 3;
   if (form == 1) set_tile_config(c, 1, 0);
   else if (form == 2) set_tile_config(c, 2, 2);
   else if (form == 3) set_tile_config(c, 1, 3);
@@ -271,6 +284,11 @@ Args<R, S> step_args(lbm_ctx* c, const Coef<R>& coef) {
 }
 
 cudaError_t launch(lbm_ctx* c, int mode, bool diag, double* const* outs, cudaStream_t s) {
+  // the step launches one CTA per 32 x ty tile (other forms and the
+  // read-out: per 32 x 8 tile), each writing one set of diagnostic partials
+  const bool shaped = mode == lbmk::MODE_STEP && !c->split && !c->tile;
+  const int ty = shaped ? c->ty : lbmk::TY;
+  if (diag) c->diag_nb = tiles_of(c, ty);
   if (mode == lbmk::MODE_STEP && c->split) {  // FP64 only
     lbmk::SplitArgs<double> a;
     a.a = step_args<double>(c, c->cd);
@@ -283,7 +301,7 @@ cudaError_t launch(lbm_ctx* c, int mode, bool diag, double* const* outs, cudaStr
       return lbmk::launch_tile_f32(tile_args<float>(c, a), diag, c->tile_stages, c->tile_grid, s);
     if (outs)
       for (int k = 0; k < lbmk::NFIELD; k++) a.out[k] = outs[k];
-    return lbmk::launch_step_f32(a, mode, diag, s);
+    return lbmk::launch_step_f32(a, mode, diag, s, ty);
   }
   if (c->tangent) {
     Args<lbmk::Dual> a = step_args<lbmk::Dual>(c, c->ct);
@@ -298,12 +316,12 @@ cudaError_t launch(lbm_ctx* c, int mode, bool diag, double* const* outs, cudaStr
                                     s);
     if (outs)
       for (int k = 0; k < lbmk::NFIELD; k++) a.out[k] = outs[k];
-    return lbmk::launch_step_f16s(a, mode, diag, s);
+    return lbmk::launch_step_f16s(a, mode, diag, s, ty);
   }
   Args<double> a = step_args<double>(c, c->cd);
   if (outs)
     for (int k = 0; k < lbmk::NFIELD; k++) a.out[k] = outs[k];
-  return lbmk::launch_step_f64(a, mode, diag, s);
+  return lbmk::launch_step_f64(a, mode, diag, s, ty);
 }
 
 // Steps of one captured period: the buffer parity repeats every two steps
@@ -475,6 +493,9 @@ int lbm_create(const lbm_params* params, lbm_ctx** out) {
   const size_t dmul = c->tangent ? 2 : 1;  // tangent: values, then derivatives
   const dim3 gd = lbmk::grid_dims(c->g);
   c->nblocks = (int)(gd.x * gd.y);
+  c->ty = lbmk::TY;
+  c->diag_nb = c->nblocks;
+  c->diag_cap = std::max(c->nblocks, tiles_of(c, 4));  // 32 x 4 tiles write the most
   const size_t P = (size_t)c->g.plane;
   cudaError_t e = cudaSuccess;
   for (int b = 0; b < 2 && e == cudaSuccess; b++) {
@@ -485,7 +506,7 @@ int lbm_create(const lbm_params* params, lbm_ctx** out) {
   if (e == cudaSuccess) e = dev_malloc(&c->scratch, lbmk::NSCRATCH * P * c->esize);
   if (e == cudaSuccess) e = dev_malloc((void**)&c->mask, P);
   if (e == cudaSuccess)
-    e = dev_malloc((void**)&c->diag_partial, dmul * lbmk::NDIAG * c->nblocks * sizeof(double));
+    e = dev_malloc((void**)&c->diag_partial, dmul * lbmk::NDIAG * c->diag_cap * sizeof(double));
   if (e == cudaSuccess) e = dev_malloc((void**)&c->diag_out, dmul * (lbmk::NDIAG + 1) * sizeof(double));
   if (e == cudaSuccess) e = cudaMemset(c->mask, 0, P);
   if (e == cudaSuccess) e = dev_malloc((void**)&c->status, sizeof(unsigned));
@@ -521,6 +542,12 @@ int lbm_create(const lbm_params* params, lbm_ctx** out) {
     if (const char* k = std::getenv("LBM_STEP_KERNEL"))
       if (std::strcmp(k, "fused") == 0) form = 0;
     if (form >= 0) set_kernel_form(c, form);
+  }
+  // LBM_KERNEL_FORM=<form id> forces one kernel form where the context has it
+  if (const char* f = std::getenv("LBM_KERNEL_FORM")) {
+    char* end = nullptr;
+    const long v = std::strtol(f, &end, 10);
+    if (end != f && form_available(c, (int)v)) set_kernel_form(c, (int)v);
   }
   if (e == cudaSuccess)
     e = host_alloc((void**)&c->h_diag, dmul * (lbmk::NDIAG + 1) * sizeof(double));
@@ -782,7 +809,7 @@ int lbm_read_diagnostics(lbm_ctx* c, lbm_diag* out) {
   if (!c->have_diag) return fail(c, LBM_ERR_STATE, "no diagnostics computed yet%s");
   cudaError_t e = cudaSuccess;
   if (c->diag_pending) {
-    e = lbmk::launch_diag_finalize(c->diag_partial, c->nblocks, c->diag_out, c->diag_step,
+    e = lbmk::launch_diag_finalize(c->diag_partial, c->diag_nb, c->diag_out, c->diag_step,
                                    c->last_stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "diagnostics finalize launch");
     c->diag_pending = false;
@@ -815,8 +842,8 @@ int lbm_read_tangent_diagnostics(lbm_ctx* c, lbm_diag* out) {
   // the derivative partials follow the value partials
   double* dout = c->diag_out + (lbmk::NDIAG + 1);
   double* hd = c->h_diag + (lbmk::NDIAG + 1);
-  cudaError_t e = lbmk::launch_diag_finalize(c->diag_partial + (size_t)lbmk::NDIAG * c->nblocks,
-                                             c->nblocks, dout, c->diag_step, c->last_stream);
+  cudaError_t e = lbmk::launch_diag_finalize(c->diag_partial + (size_t)lbmk::NDIAG * c->diag_nb,
+                                             c->diag_nb, dout, c->diag_step, c->last_stream);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(hd, dout, (lbmk::NDIAG + 1) * sizeof(double), cudaMemcpyDeviceToHost,
                         c->last_stream);
@@ -1635,7 +1662,7 @@ extern "C" int lbm_autotune(lbm_ctx* c, int steps_per_trial, void* stream, doubl
   const size_t P = (size_t)c->g.plane;
   const size_t pb = 27 * P * c->pop_esize, lb = c->nlag * P * c->esize;
   // the diagnostic partials too: trial steps overwrite them
-  const size_t db = (c->tangent ? 2 : 1) * (size_t)lbmk::NDIAG * c->nblocks * sizeof(double);
+  const size_t db = (c->tangent ? 2 : 1) * (size_t)lbmk::NDIAG * c->diag_cap * sizeof(double);
   void* backup = nullptr;
   cudaError_t e = cudaMalloc(&backup, pb + lb + db);
   if (e != cudaSuccess) return cuda_fail(c, e, "autotune backup allocation");
@@ -1644,7 +1671,7 @@ extern "C" int lbm_autotune(lbm_ctx* c, int steps_per_trial, void* stream, doubl
   const int64_t step = c->step, diag_step = c->diag_step;
   const bool have_diag = c->have_diag, pending = c->diag_pending;
   const bool graphs0 = c->graphs;
-  const int gmin0 = c->graph_min, form0 = c->form;
+  const int gmin0 = c->graph_min, form0 = c->form, diag_nb0 = c->diag_nb;
   e = cudaMemcpyAsync(backup, c->pop[cur], pb, cudaMemcpyDeviceToDevice, s);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync((char*)backup + pb, c->lag[cur], lb, cudaMemcpyDeviceToDevice, s);
@@ -1652,13 +1679,13 @@ extern "C" int lbm_autotune(lbm_ctx* c, int steps_per_trial, void* stream, doubl
     e = cudaMemcpyAsync((char*)backup + pb + lb, c->diag_partial, db, cudaMemcpyDeviceToDevice, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   // variants: kernel form (v / 2) x shortest captured period (32, 256)
-  const int nforms = kernel_forms(c);
   double us[kAutotuneVariants];
   for (int v = 0; v < kAutotuneVariants; v++) us[v] = -1.0;
   cudaEvent_t t0 = nullptr, t1 = nullptr;
   if (e == cudaSuccess) e = cudaEventCreate(&t0);
   if (e == cudaSuccess) e = cudaEventCreate(&t1);
-  for (int v = 0; v < 2 * nforms && e == cudaSuccess; v++) {
+  for (int v = 0; v < kAutotuneVariants && e == cudaSuccess; v++) {
+    if (!form_available(c, v / 2)) continue;
     set_kernel_form(c, v / 2);
     c->graphs = graphs0;
     c->graph_min = (v & 1) ? 256 : 32;
@@ -1692,6 +1719,7 @@ extern "C" int lbm_autotune(lbm_ctx* c, int steps_per_trial, void* stream, doubl
   c->cur = cur;
   c->step = step;
   c->diag_step = diag_step;
+  c->diag_nb = diag_nb0;
   c->have_diag = have_diag;
   c->diag_pending = pending;
   c->gen++;
@@ -1761,6 +1789,7 @@ void note_batch_diag(lbm_batch* b, int64_t first0, int64_t n) {
   for (lbm_ctx* c : b->ctx) {
     c->have_diag = true;
     c->diag_pending = true;
+    c->diag_nb = c->nblocks;  // the batch kernel's 32 x 8 tiles
     c->diag_step = c->step + (last - first0);
   }
 }

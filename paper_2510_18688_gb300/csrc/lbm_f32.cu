@@ -4,20 +4,27 @@
 
 namespace lbmk {
 
-template <int MODE, bool DIAG>
+template <int MODE, bool DIAG, int TYS = TY>
 static void launch_one(const Args<float>& a, cudaStream_t s) {
-  const dim3 grid = grid_dims(a.g), block = block_dims();
+  const dim3 grid = grid_dims(a.g, TYS), block = block_dims(TYS);
   // the all-lattices case is specialised at compile time
   if (a.g.lattices == (LAT_FLOW | LAT_PHASE | LAT_HEAT))
-    lbm_step_kernel<float, MODE, DIAG, 7><<<grid, block, 0, s>>>(a);
+    lbm_step_kernel<float, MODE, DIAG, 7, float, TYS><<<grid, block, 0, s>>>(a);
   else
-    lbm_step_kernel<float, MODE, DIAG, 0><<<grid, block, 0, s>>>(a);
+    lbm_step_kernel<float, MODE, DIAG, 0, float, TYS><<<grid, block, 0, s>>>(a);
 }
 
-cudaError_t launch_step_f32(const Args<float>& a, int mode, bool diag, cudaStream_t s) {
+template <bool DIAG>
+static void launch_shape(const Args<float>& a, int ty, cudaStream_t s) {
+  if (ty == 4) launch_one<MODE_STEP, DIAG, 4>(a, s);
+  else if (ty == 16) launch_one<MODE_STEP, DIAG, 16>(a, s);
+  else launch_one<MODE_STEP, DIAG>(a, s);
+}
+
+cudaError_t launch_step_f32(const Args<float>& a, int mode, bool diag, cudaStream_t s, int ty) {
   if (mode == MODE_STEP) {
-    if (diag) launch_one<MODE_STEP, true>(a, s);
-    else launch_one<MODE_STEP, false>(a, s);
+    if (diag) launch_shape<true>(a, ty, s);
+    else launch_shape<false>(a, ty, s);
   } else {
     if (diag) launch_one<MODE_READ, true>(a, s);
     else launch_one<MODE_READ, false>(a, s);

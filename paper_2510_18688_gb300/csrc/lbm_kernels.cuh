@@ -44,6 +44,18 @@ constexpr int NPART = 3;       // threads per ring node in phase A
 constexpr int NDIAG = 9;
 constexpr int NFIELD = 12;
 static_assert(RING * NPART <= NT, "ring loads must fit one pass of the CTA");
+
+// Tile shapes of the one-CTA-per-tile step: 32 x TY_ nodes (a warp per row,
+// so every shape keeps 128-byte rows), TY_ = 4, 8 (the default above) or 16.
+// The autotuner picks one per grid: short tiles suit grids a few rows high
+// (the one-dimensional columns), tall ones shrink the ring's share (84 ring
+// nodes per 256 at 32 x 8, 100 per 512 at 32 x 16).
+template <int TY_>
+struct Shape {
+  static_assert(TY_ == 4 || TY_ == 8 || TY_ == 16, "tile shapes 32 x 4, 32 x 8, 32 x 16");
+  static constexpr int TY = TY_, HY = TY_ + 2, HN = HX * HY, NT = TX * TY_, RING = HN - NT;
+};
+__host__ __device__ constexpr int tiles_y(int ny, int ty) { return (ny + ty - 1) / ty; }
 enum { BC_PERIODIC = 0, BC_DIRICHLET = 1, BC_ADIABATIC = 2 };
 enum { LAT_FLOW = 1, LAT_PHASE = 2, LAT_HEAT = 4 };
 enum { LAG_FL = 0, LAG_W, LAG_P, LAG_PHUX, LAG_PHUY, LAG_Q, NLAG };
@@ -491,12 +503,13 @@ __device__ __forceinline__ long long stream_target(const Geom& g, int x, int y, 
   return wall >= 0 ? -1 : (long long)ty * g.pitch + tx;
 }
 
-// Halo-ring position k (0 <= k < RING) in the (HX x HY) tile.
+// Halo-ring position k (0 <= k < RING) in the (HX x HY) tile of height TYS.
+template <int TYS = TY>
 __device__ __forceinline__ void ring_pos(int k, int& hx, int& hy) {
   if (k < HX) {
     hx = k; hy = 0;
   } else if (k < 2 * HX) {
-    hx = k - HX; hy = HY - 1;
+    hx = k - HX; hy = TYS + 1;
   } else {
     const int r = k - 2 * HX;  // 2 * TY side nodes
     hy = 1 + (r >> 1);
@@ -579,7 +592,7 @@ __device__ __forceinline__ void block_diag_warps(const R* dvals, R (*s_red)[NDIA
 
 // Stage 2 (every thread; one barrier): the warps' sums in order into
 // partial[k * nb + b] for tile b of nb.
-template <typename R>
+template <typename R, int NW = NT / 32>
 __device__ __forceinline__ void block_diag_finish(const R (*s_red)[NDIAG],
                                                   double* __restrict__ partial, int tid, int b,
                                                   int nb) {
@@ -590,18 +603,18 @@ __device__ __forceinline__ void block_diag_finish(const R (*s_red)[NDIAG],
       // in the next NDIAG * nb
       R acc = R(0);
 #pragma unroll
-      for (int w = 0; w < NT / 32; w++) acc += s_red[w][tid];
+      for (int w = 0; w < NW; w++) acc += s_red[w][tid];
       partial[(long long)tid * nb + b] = acc.v;
       partial[(long long)(NDIAG + tid) * nb + b] = acc.d;
     } else if constexpr (sizeof(R) == 8) {
       double acc = 0.0;
 #pragma unroll
-      for (int w = 0; w < NT / 32; w++) acc += (double)s_red[w][tid];
+      for (int w = 0; w < NW; w++) acc += (double)s_red[w][tid];
       partial[(long long)tid * nb + b] = acc;
     } else {
       R sum = R(0), err = R(0);
 #pragma unroll
-      for (int w = 0; w < NT / 32; w++) {
+      for (int w = 0; w < NW; w++) {
         const R y = s_red[w][tid];
         const R t = sum + y;
         const R yv = t - sum;          // the part of y that went into t

@@ -11,14 +11,17 @@
 
 namespace lbmk {
 
-inline dim3 block_dims() { return dim3(TX, TY, 1); }
-inline dim3 grid_dims(const Geom& g) {
-  return dim3((unsigned)((g.nx + TX - 1) / TX), (unsigned)((g.ny + TY - 1) / TY), 1);
+inline dim3 block_dims(int ty = TY) { return dim3(TX, (unsigned)ty, 1); }
+inline dim3 grid_dims(const Geom& g, int ty = TY) {
+  return dim3((unsigned)((g.nx + TX - 1) / TX), (unsigned)tiles_y(g.ny, ty), 1);
 }
 
-// MODE_STEP or MODE_READ, with or without the fused diagnostics.
-cudaError_t launch_step_f32(const Args<float>& a, int mode, bool diag, cudaStream_t s);
-cudaError_t launch_step_f64(const Args<double>& a, int mode, bool diag, cudaStream_t s);
+// MODE_STEP or MODE_READ, with or without the fused diagnostics; MODE_STEP
+// on 32 x ty tiles (ty = 4, 8 or 16), MODE_READ on 32 x 8.
+cudaError_t launch_step_f32(const Args<float>& a, int mode, bool diag, cudaStream_t s,
+                            int ty = TY);
+cudaError_t launch_step_f64(const Args<double>& a, int mode, bool diag, cudaStream_t s,
+                            int ty = TY);
 // Two-kernel form of MODE_STEP (macro pass, then collide pass).
 cudaError_t launch_split_f64(const SplitArgs<double>& a, bool diag, cudaStream_t s);
 cudaError_t launch_init_f32(const InitArgs<float>& a, cudaStream_t s);
@@ -33,7 +36,8 @@ cudaError_t launch_tile_f32(const TileArgs<float>& t, bool diag, int stages, int
 cudaError_t launch_tile_f16s(const TileArgs<__half>& t, bool diag, int stages, int grid,
                              cudaStream_t s);
 // FP16 population storage, FP32 arithmetic.
-cudaError_t launch_step_f16s(const Args<float, __half>& a, int mode, bool diag, cudaStream_t s);
+cudaError_t launch_step_f16s(const Args<float, __half>& a, int mode, bool diag, cudaStream_t s,
+                             int ty = TY);
 cudaError_t launch_init_f16s(const InitArgs<float, __half>& a, cudaStream_t s);
 // Reverse mode of the enthalpy-lattice step (lbm_adjoint.cuh).
 struct AdjArgs;

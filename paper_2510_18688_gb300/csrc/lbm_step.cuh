@@ -490,20 +490,25 @@ __device__ __forceinline__ void diag_values(const Coef<R>& c, int lat, const Loc
 }
 
 // One tile (bx, by) of one grid: the whole step (or read-out) for its
-// TX x TY nodes.  b / nb: the tile's index and the grid's tile count for the
-// diagnostic partials (b < 0: taken from the CTA's position in its grid).  LATC: compile-time lattice set (7 = all three) or 0
-// (read at run time).  Every thread of the CTA calls it.
-template <typename R, int MODE, bool DIAG, int LATC, typename S = R>
+// TX x TYS nodes (a Shape).  b / nb: the tile's index and the grid's tile
+// count for the diagnostic partials (b < 0: taken from the CTA's position in
+// its grid).  LATC: compile-time lattice set (7 = all three) or 0 (read at
+// run time).  Every thread of the CTA calls it.
+template <typename R, int MODE, bool DIAG, int LATC, typename S = R, int TYS = TY>
 __device__ __forceinline__ void step_tile(const Args<R, S>& a, int bx, int by, int b, int nb) {
+  // the tile's shape; these hide the namespace's 32 x 8 constants
+  constexpr int TY = Shape<TYS>::TY, HN = Shape<TYS>::HN, NT = Shape<TYS>::NT;
+  constexpr int RING = Shape<TYS>::RING;
   const Geom& g = a.g;
   const Coef<R>& c = a.c;
   const int lat = LATC ? LATC : g.lattices;
   const int P = (int)g.plane;  // 27 planes fit in 31 bits (checked at create)
 
   // FP32 steps keep the own node's phase and enthalpy populations in shared
-  // memory between phase A and phase B (18 KB per CTA) instead of reading
-  // them again through L1/L2
-  constexpr bool STASH = sizeof(R) == 4 && MODE == MODE_STEP;
+  // memory between phase A and phase B (18 KB per 256-node CTA) instead of
+  // reading them again through L1/L2; 32 x 16 tiles have no room for it
+  // within the 48 KB of static shared memory and read them again
+  constexpr bool STASH = sizeof(R) == 4 && MODE == MODE_STEP && TYS <= 8;
   constexpr bool STASHF = STASH && LBM_STASH_F;
   __shared__ R s_pop[STASH ? 18 : 1][NT];
   __shared__ R s_fpop[STASHF ? 9 : 1][NT];
@@ -530,10 +535,12 @@ __device__ __forceinline__ void step_tile(const Args<R, S>& a, int bx, int by, i
   const int n = my * g.pitch + mx;
 
   // ---- phase A0: a third of one ring node's phase/enthalpy populations ----
-  if (tid < RING * NPART) {
-    const int k = tid / NPART, part = tid - k * NPART;
+  // (job j: ring node j / NPART, part j % NPART; one pass of the CTA unless
+  // the tile is short)
+  auto ring_load = [&](int job) {
+    const int k = job / NPART, part = job - k * NPART;
     int hx, hy;
-    ring_pos(k, hx, hy);
+    ring_pos<TYS>(k, hx, hy);
     const int rx = wrap_or_clamp(x0 + hx - 1, g.nx, g.bc[0], g.bc[1]);
     const int ry = wrap_or_clamp(y0 + hy - 1, g.ny, g.bc[2], g.bc[3]);
     const int m = ry * g.pitch + rx;
@@ -569,6 +576,11 @@ __device__ __forceinline__ void step_tile(const Args<R, S>& a, int bx, int by, i
     }
     s_rsg[k][part] = sgp;
     s_rsh[k][part] = shp;
+  };
+  if constexpr (RING * NPART <= NT) {
+    if (tid < RING * NPART) ring_load(tid);
+  } else {
+    for (int job = tid; job < RING * NPART; job += NT) ring_load(job);
   }
 
   // ---- phase A1: own node (sums only; f prefetched for phase B) ----------
@@ -660,7 +672,7 @@ __device__ __forceinline__ void step_tile(const Args<R, S>& a, int bx, int by, i
   if (tid < RING) {
     const int k = tid;
     int hx, hy;
-    ring_pos(k, hx, hy);
+    ring_pos<TYS>(k, hx, hy);
     const int hi = hy * HX + hx;
     const R q0 = s_phi0[hi];
     const R wq = s_rw[k];
@@ -799,16 +811,20 @@ __device__ __forceinline__ void step_tile(const Args<R, S>& a, int bx, int by, i
   if (x0 >= 1 && x0 + TX < g.nx && y0 >= 1 && y0 + TY < g.ny) phase_b(std::true_type{});
   else phase_b(std::false_type{});
   if (DIAG) {
-    if (b < 0) block_diag_finish(s_red, a.diag_partial, tid, blockIdx.y * gridDim.x + blockIdx.x,
-                                 gridDim.x * gridDim.y);
-    else block_diag_finish(s_red, a.diag_partial, tid, b, nb);
+    if (b < 0)
+      block_diag_finish<R, NT / 32>(s_red, a.diag_partial, tid,
+                                    blockIdx.y * gridDim.x + blockIdx.x, gridDim.x * gridDim.y);
+    else block_diag_finish<R, NT / 32>(s_red, a.diag_partial, tid, b, nb);
   }
 }
 
-template <typename R, int MODE, bool DIAG, int LATC, typename S = R>
-__global__ void __launch_bounds__(NT, sizeof(R) == 4 ? LBM_MIN_BLOCKS_F32 : 1)
+// One CTA per 32 x TYS tile; float kernels keep the 64-register budget of
+// the 32 x 8 shape (4 CTAs of 256 threads per SM) at every shape.
+template <typename R, int MODE, bool DIAG, int LATC, typename S = R, int TYS = TY>
+__global__ void __launch_bounds__(Shape<TYS>::NT,
+                                  sizeof(R) == 4 ? LBM_MIN_BLOCKS_F32 * TY / TYS : 1)
     lbm_step_kernel(const Args<R, S> a) {
-  step_tile<R, MODE, DIAG, LATC, S>(a, blockIdx.x, blockIdx.y, -1, 0);
+  step_tile<R, MODE, DIAG, LATC, S, TYS>(a, blockIdx.x, blockIdx.y, -1, 0);
 }
 
 // Many independent grids (uneven sizes and parameters) advanced in one

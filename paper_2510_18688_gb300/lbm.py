@@ -293,13 +293,18 @@ def lbm_adjoint_coupled(ctx, nsteps: int, every: int, observable: int, axis: int
     return val.value, list(grad)
 
 
-VARIANTS = ("fused, periods >= 32", "fused, periods >= 256", "split, periods >= 32",
-            "split, periods >= 256")
+# kernel form ids of lbm_autotune (variant v = form v // 2, period v % 2)
+FORMS = ("one CTA per 32x8 tile", "float: TMA-staged, one stage / fp64: two-kernel split",
+         "float: TMA-staged, two stages, 2 persistent CTAs per SM",
+         "float: TMA-staged, one stage, 3 persistent CTAs per SM", "one CTA per 32x4 tile",
+         "one CTA per 32x16 tile")
+N_VARIANTS = 2 * len(FORMS)
+VARIANTS = tuple(f"{f}, periods >= {p}" for f in FORMS for p in (32, 256))
 
 
 def lbm_autotune(ctx, steps_per_trial: int = 64, stream=None):
     """(microseconds per step of each variant, index kept); see include/lbm.h."""
-    us = (ctypes.c_double * 8)()
+    us = (ctypes.c_double * N_VARIANTS)()
     chosen = ctypes.c_int()
     _check(ctx, load().lbm_autotune(ctx, int(steps_per_trial), stream, us, ctypes.byref(chosen)),
            "lbm_autotune")

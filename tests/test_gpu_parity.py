@@ -445,15 +445,60 @@ def test_autotune_keeps_the_state_and_picks_a_variant(env, prec):
     for k in FIELDS:
         assert np.array_equal(before[k], after[k]), k
     assert s.steps_done == 5
-    # FP64: fused and two-kernel split; float: four kernel forms (one CTA
-    # per tile, three TMA-staged tile configurations); x two graph periods
-    n_variants = 4 if prec == "fp64" else 8
-    assert all(u > 0 for u in us[:n_variants]) and all(u == -1.0 for u in us[n_variants:])
-    assert 0 <= chosen < n_variants and us[chosen] == min(us[:n_variants])
+    # kernel forms x two graph periods: every precision one CTA per 32 x 4,
+    # 32 x 8 and 32 x 16 tile (forms 0, 4, 5); FP64 the two-kernel split
+    # (form 1); float the three TMA-staged configurations (forms 1-3)
+    forms = (0, 1, 4, 5) if prec == "fp64" else (0, 1, 2, 3, 4, 5)
+    run = [v for v in range(len(us)) if v // 2 in forms]
+    assert len(us) == 12
+    assert all(us[v] > 0 for v in run)
+    assert all(u == -1.0 for v, u in enumerate(us) if v not in run)
+    assert chosen in run and us[chosen] == min(us[v] for v in run)
     s.step(40)
     if prec != "fp16s":
         _compare(s.fields(), O.from_workload((cfg, arr)).step(45).fields(), prec)
     s.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "fp16s"])
+@pytest.mark.parametrize("form", [4, 0, 5])
+def test_tile_shapes_match_the_oracle(env, prec, form, monkeypatch):
+    """The one-CTA-per-tile step on 32 x 4, 32 x 8 and 32 x 16 tiles (kernel
+    forms 4, 0, 5), forced with LBM_KERNEL_FORM: ragged random states with
+    every branch, and a column four nodes high (the Neumann shape) whose
+    height one 32 x 4 tile fits exactly.  FP64 within 1e-10 of the oracle,
+    FP32 at the parity bar; FP16 storage within twice the 32 x 8 run's
+    distance from FP64 of that run (the same arithmetic; only a flipped
+    binary16 rounding separates them).  The diagnostics fused into the last
+    step (one partial sum per CTA, as many as the shape has tiles) match the
+    oracle's of the state that step read."""
+    O, lbm = env
+    for wl, steps in ((W.random_state(70, 45, seed=41), 80), (W.random_state(37, 19, seed=42), 80),
+                      (W.neumann(), 300)):
+        cfg, arr = wl
+        o = O.from_workload(wl).step(steps - 1)
+        rd = o.diagnostics()
+        ref = o.step(1).fields()
+        monkeypatch.setenv("LBM_KERNEL_FORM", str(form))
+        s = lbm.Solver(cfg, precision=prec, diag_every=1).set_geometry(arr).step(steps)
+        monkeypatch.delenv("LBM_KERNEL_FORM")
+        got, d = s.fields(), s.diagnostics(compute=False)
+        s.close()
+        assert d["step"] == steps - 1
+        if prec == "fp16s":
+            b = lbm.Solver(cfg, precision=prec).set_geometry(arr).step(steps)
+            c = lbm.Solver(cfg, precision="fp64").set_geometry(arr).step(steps)
+            fb, fc = b.fields(), c.fields()
+            b.close()
+            c.close()
+            for k in FIELDS:
+                e = _l2_rel(got[k], fb[k])
+                assert e <= max(1e-5, 2 * _l2_rel(fb[k], fc[k])), (k, e)
+        else:
+            _compare(got, ref, prec)
+        tol = {"fp64": 1e-10, "fp32": 1e-5, "fp16s": 1e-3}[prec]
+        for k in ("mass", "material_mass", "rhoH", "frozen_volume", "phi_sum"):
+            assert abs(d[k] - rd[k]) <= tol * (abs(rd[k]) + cfg["nx"] * cfg["ny"]), (k, d[k], rd[k])
 
 
 @pytest.mark.slow
