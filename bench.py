@@ -143,7 +143,8 @@ def measured_peak():
 
 # the sources the step kernels are compiled from (host API and probes excluded)
 KERNEL_SOURCES = ("lbm_kernels.cuh", "lbm_dual.cuh", "lbm_step.cuh", "lbm_split.cuh",
-                  "lbm_launch.h", "lbm_f32.cu", "lbm_f64.cu", "lbm_f16.cu", "lbm_tan.cu")
+                  "lbm_tile.cuh", "lbm_tma.cuh", "lbm_launch.h", "lbm_f32.cu", "lbm_f64.cu",
+                  "lbm_f16.cu", "lbm_tan.cu")
 
 
 # the sources of the 3-D step kernels
@@ -573,6 +574,11 @@ def fp64_record(lbm, wl, flush, stream, sptr, args, t32_ms):
     cfg, arr = wl
     n = cfg["nx"] * cfg["ny"]
     s = lbm.Solver(cfg, precision="fp64", diag_every=args.diag_every).set_geometry(arr)
+    # the autotuner's kernel form for this grid, as for the FP32 line
+    form = None
+    if not args.no_autotune:
+        us, chosen = s.autotune(16)
+        form = chosen // 2
     k = max(10, min(args.steps, 40))
     for _ in range(3):
         flush()
@@ -594,7 +600,7 @@ def fp64_record(lbm, wl, flush, stream, sptr, args, t32_ms):
     fpn = profiled_value(args.workload, "fp64", "fp64 flops per node")
     ach = fpn * n / (t * 1e-3) / 1e12 if fpn else None
     return {"value": n / (t * 1e-3) / 1e6, "unit": "MLUPS", "ms_per_step": t, "steps": k,
-            "fp32_over_fp64": t / t32_ms,
+            "kernel_form": form, "fp32_over_fp64": t / t32_ms,
             "fp64_pipe": {"achieved": ach, "peak": fma, "unit": "TFLOP/s",
                           "frac": ach / fma if ach else None, "flops_per_node": fpn,
                           "peak_source": "FP64 FMA rate measured in this run"},

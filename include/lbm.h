@@ -67,7 +67,7 @@ typedef enum {
  * Float states carry one more lag plane, the temperature T of the previous
  * step.  LBM_FP16S: the same with the 27 populations in IEEE binary16.
  * Neither storage format is in the paper (which gives no precision);
- * LBM_FP16S trades accuracy for 165 instead of 277 bytes of state traffic
+ * LBM_FP16S trades accuracy for 169 instead of 277 bytes of state traffic
  * per node update.  Batches and lbm_diagnostics_noalloc do not take
  * LBM_FP16S (LBM_ERR_UNSUPPORTED). */
 /* LBM_FP64_TANGENT: the FP64 step in forward-mode (dual-number)
