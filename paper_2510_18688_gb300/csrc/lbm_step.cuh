@@ -521,7 +521,7 @@ __device__ __forceinline__ void step_tile(const Args<R, S>& a, int bx, int by, i
   // the ring and the own node's old temperature and heat capacity
   constexpr bool WB = kShift<R>;
   __shared__ R s_T[WB ? HN : 1], s_rT[WB ? RING : 1];
-  __shared__ R s_Tp[WB && STASH ? 2 : 1][NT];
+  __shared__ R s_Tp[WB ? 2 : 1][NT];
   __shared__ int s_rmask[RING];
   __shared__ R s_red[NT / 32][NDIAG];
 
@@ -629,10 +629,8 @@ __device__ __forceinline__ void step_tile(const Args<R, S>& a, int bx, int by, i
     if (lat & LAT_HEAT) {
       Tp = a.lin[LAG_T * P + n];
       Cp = cap_rn(c, fs_rn(wp, flp, phi0), wp);
-      if (STASH) {
-        s_Tp[0][tid] = Tp;
-        s_Tp[STASH ? 1 : 0][tid] = Cp;
-      }
+      s_Tp[0][tid] = Tp;
+      s_Tp[WB ? 1 : 0][tid] = Cp;
     }
   }
   if (lat & LAT_HEAT) {
@@ -765,11 +763,23 @@ __device__ __forceinline__ void step_tile(const Args<R, S>& a, int bx, int by, i
       }
       if (lat & LAT_HEAT) {
         R hq[9];
+        // well-balanced storage: the node's old temperature and heat capacity
+        R Tq = R(0), Cq = R(0);
+        if constexpr (WB) {
+          Tq = s_Tp[0][tid];
+          Cq = s_Tp[WB ? 1 : 0][tid];
+        }
         if (STASH) {
 #pragma unroll
           for (int i = 0; i < 9; i++) hq[i] = s_pop[STASH ? 9 + i : 0][tid];
         } else if (masked) {
+          // the populations the cold mask sets, as remainders when stored so
           cold_mask_h(c, wp, phi0, hq);
+          if constexpr (WB) {
+            hq[0] -= ref_h0(c, wp, flp, Tq, Cq);
+#pragma unroll
+            for (int i = 1; i < 9; i++) hq[i] -= ref_hi(i <= 4 ? c.wrr1 : c.wrr5, Tq);
+          }
         } else {
 #pragma unroll
           for (int i = 0; i < 9; i++) hq[i] = ldp(pn + (18 + i) * P);
@@ -777,7 +787,6 @@ __device__ __forceinline__ void step_tile(const Args<R, S>& a, int bx, int by, i
         if constexpr (WB) {
           // references: this node's old state, and the new one its rest
           // population is stored against
-          const R Tq = s_Tp[0][tid], Cq = s_Tp[STASH ? 1 : 0][tid];
           const R dref0 = ref_delta(ref_h0(c, L.w, L.fl, T, M.cap), ref_h0(c, wp, flp, Tq, Cq));
           const R aold = ref_hi(c.wrr1, Tq), dold = ref_hi(c.wrr5, Tq);
           const int hc = (ty + 1) * HX + (tx + 1);

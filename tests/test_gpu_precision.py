@@ -65,23 +65,25 @@ CASES = [
     ("stefan 512x8, 5000 steps", lambda: W.stefan(), 5000, (0, 4)),
 ]
 
-# FP16-storage bounds: about 3x the GB300 measurement of each entry (1e-6
-# where the measured error is zero or below 3e-7)
-F16_FIELD = {"droplet": dict(phi=1.5e-4, fs=5.7e-5, fl=1.8e-5, T=3e-5, rhoH=1.5e-4, p=3.9e-3,
-                             ux=1.6e-2, uy=1.6e-2, rho=4.8e-5, mu=1.7e-3, w=8.7e-5, mdot=2.3e-3),
-             "cylinder": dict(phi=2.8e-4, fs=4.5e-5, fl=2e-5, T=2.3e-5, rhoH=1.5e-4, p=3.9e-3,
-                              ux=8.4e-2, uy=8.4e-2, rho=4.5e-5, mu=3.3e-3, w=1.4e-4, mdot=9.7e-4),
-             "random": dict(phi=2.1e-5, fs=1.5e-5, fl=2.8e-5, T=6.9e-5, rhoH=1.7e-5, p=3.3e-3,
-                            ux=1.1e-2, uy=1.1e-2, rho=1.3e-5, mu=2.3e-4, w=1.7e-5, mdot=4.2e-4),
-             "neumann": dict(phi=1e-6, fs=2.7e-5, fl=4.8e-6, T=2.5e-4, rhoH=6e-6, p=1e-6, ux=1e-6,
+# FP16-storage bounds: about 10x the GB300 measurement of each entry (1e-6
+# where the measured error is zero or below 1e-7): a binary16 rounding that
+# flips with a last-bit change of the float arithmetic moves these errors by
+# factors of a few
+F16_FIELD = {"droplet": dict(phi=5e-4, fs=1.9e-4, fl=6e-5, T=1e-4, rhoH=5e-4, p=1.3e-2,
+                             ux=5.4e-2, uy=5.4e-2, rho=1.6e-4, mu=5.7e-3, w=2.9e-4, mdot=7.7e-3),
+             "cylinder": dict(phi=9.4e-4, fs=1.5e-4, fl=6.7e-5, T=7.7e-5, rhoH=5e-4, p=1.3e-2,
+                              ux=2.9e-1, uy=2.9e-1, rho=1.5e-4, mu=1.1e-2, w=4.7e-4, mdot=3.3e-3),
+             "random": dict(phi=7e-5, fs=5e-5, fl=9.4e-5, T=2.3e-4, rhoH=5.7e-5, p=1.1e-2,
+                            ux=3.7e-2, uy=3.7e-2, rho=4.4e-5, mu=7.7e-4, w=5.7e-5, mdot=1.5e-3),
+             "neumann": dict(phi=1e-6, fs=9e-5, fl=1.6e-5, T=8.4e-4, rhoH=2e-5, p=1e-6, ux=1e-6,
                              uy=1e-6, rho=1e-6, mu=1e-6, w=1e-6, mdot=1e-6),
-             "stefan": dict(phi=3.3e-4, fs=3.6e-4, fl=3.9e-6, T=3.3e-4, rhoH=9.6e-5, p=0.17,
-                            ux=1.5, uy=1.5, rho=7.2e-5, mu=6e-3, w=2.4e-4, mdot=1.3e-3)}
-F16_OBS = {"droplet": dict(material_mass=1.7e-6, frozen_volume=2.3e-6, interface_lu=4.2e-4),
-           "cylinder": dict(material_mass=4.5e-5, frozen_volume=6.3e-5, interface_lu=2.1e-4),
-           "random": dict(material_mass=1e-6, frozen_volume=7.6e-6),
-           "neumann": dict(material_mass=1e-6, frozen_volume=6.9e-6),
-           "stefan": dict(material_mass=8.1e-5, frozen_volume=5.2e-4, interface_lu=1.5e-3)}
+             "stefan": dict(phi=1.1e-3, fs=1.3e-3, fl=1.3e-5, T=1.1e-3, rhoH=3.2e-4, p=5.7e-1,
+                            ux=5e0, uy=5e0, rho=2.4e-4, mu=2e-2, w=8e-4, mdot=4.4e-3)}
+F16_OBS = {"droplet": dict(material_mass=5.7e-6, frozen_volume=7.7e-6, interface_lu=1.5e-3),
+           "cylinder": dict(material_mass=1.5e-4, frozen_volume=2.1e-4, interface_lu=7.1e-4),
+           "random": dict(material_mass=1e-6, frozen_volume=2.6e-5),
+           "neumann": dict(material_mass=1e-6, frozen_volume=2.3e-5),
+           "stefan": dict(material_mass=2.7e-4, frozen_volume=1.8e-3, interface_lu=5e-3)}
 
 
 @pytest.mark.parametrize("case", CASES, ids=[c[0].split(",")[0] for c in CASES])
