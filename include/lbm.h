@@ -281,7 +281,13 @@ void lbm_destroy(lbm_ctx* ctx);
  * results agree to the last bit where the compiler contracts both kernels'
  * copies of the arithmetic alike, as the FP64 build does, and otherwise to a
  * few roundings of the working precision).  This is how
- * many small problems fill the GPU.  The batch holds the context pointers
+ * many small problems fill the GPU.  LBM_FP32 batches run as the batched
+ * TMA-staged tile kernel (each tile's inputs copied to shared memory by the
+ * tensor copies of its own context, one CTA per 32 x 8 tile; a copy that
+ * does not arrive within the bounded wait makes that context's next read
+ * return LBM_ERR_TIMEOUT), LBM_FP64 batches, and LBM_FP32 batches under the
+ * environment variable LBM_BATCH_KERNEL=fused, as the one-CTA-per-tile
+ * kernel loading from global memory.  The batch holds the context pointers
  * only and allocates no device memory; the contexts stay usable on their own
  * (lbm_step, lbm_read_fields, diagnostics, checkpoints) and must outlive the
  * batch.

@@ -64,6 +64,7 @@ struct lbm_ctx {
   int tile_grid;         // its CTAs (persistent when fewer than the tiles)
   int sms;               // multiprocessors of the context's device
   CUtensorMap tm_f[2], tm_gh[2], tm_lag[2], tm_phi0, tm_mask;  // per A/B buffer
+  lbmk::TileMaps* d_maps;  // device copy of the maps by parity (FP32: for batches)
   unsigned* status;      // device word: a tile's copies did not arrive in time
   int cur;
   int64_t step;
@@ -422,7 +423,7 @@ void free_all(lbm_ctx* c) {
   if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
   void* dev[] = {c->pop[0], c->pop[1], c->lag[0],     c->lag[1],    c->phi0,   c->mask,
                  c->diag_partial, c->diag_out, c->staging, c->in_stage,
-                 c->scratch, c->status};
+                 c->scratch, c->status, c->d_maps};
   for (void* p : dev)
     if (p) cudaFree(p);
   if (c->h_diag) cudaFreeHost(c->h_diag);
@@ -523,6 +524,19 @@ int lbm_create(const lbm_params* params, lbm_ctx** out) {
     if (e == cudaSuccess && maps)
       e = params->precision == LBM_FP32 ? lbmk::prepare_tile_f32() : lbmk::prepare_tile_f16s();
     c->tile_ok = e == cudaSuccess && maps;
+    if (c->tile_ok && params->precision == LBM_FP32) {
+      // the maps by parity in device memory, for the batched tile kernel
+      lbmk::TileMaps hm[2];
+      for (int b = 0; b < 2; b++) {
+        hm[b].f = c->tm_f[b];
+        hm[b].gh = c->tm_gh[b];
+        hm[b].lag = c->tm_lag[b];
+        hm[b].phi0 = c->tm_phi0;
+        hm[b].mask = c->tm_mask;
+      }
+      e = dev_malloc((void**)&c->d_maps, sizeof(hm));
+      if (e == cudaSuccess) e = cudaMemcpy(c->d_maps, hm, sizeof(hm), cudaMemcpyHostToDevice);
+    }
     // Default kernel form (lbm_autotune measures them all): one CTA per
     // tile from global loads on grids of fewer than eight tiles per
     // multiprocessor, where every tile's loads and compute overlap with
@@ -1750,6 +1764,10 @@ extern "C" int lbm_autotune(lbm_ctx* c, int steps_per_trial, void* stream, doubl
 struct lbm_batch {
   std::vector<lbm_ctx*> ctx;
   int precision;
+  // FP32 batches step as the batched TMA-staged tile kernel (one stage, one
+  // CTA per tile) unless LBM_BATCH_KERNEL=fused; its argument table
+  bool tile;
+  lbmk::TileBatch<float>* ttab;
   cudaStream_t cap_stream;
   cudaGraphExec_t graph;               // one captured period of batch steps
   std::vector<uint64_t> graph_key;     // (parity, generation) per context, phase
@@ -1772,6 +1790,24 @@ bool fill_table(lbm_batch* b, int first, int count, lbmk::BatchTable<R>& t) {
     else coef = (const Coef<R>*)(const void*)&c->cd;
     t.args[i] = step_args<R>(c, *coef);
     t.tile_base[i + 1] = t.tile_base[i] + c->nblocks;
+    if (c->p.lattices != 7u) all = false;
+  }
+  return all;
+}
+
+// The batched tile kernel's table for contexts [first, first + count).
+bool fill_tile_table(lbm_batch* b, int first, int count, lbmk::TileBatch<float>& t) {
+  bool all = true;
+  t.ngrids = count;
+  t.tile_base[0] = 0;
+  t.extra_tx = g_tile_timeout.load() ? 16u : 0u;
+  for (int i = 0; i < count; i++) {
+    lbm_ctx* c = b->ctx[first + i];
+    t.args[i] = step_args<float>(c, c->cf);
+    t.tile_base[i + 1] = t.tile_base[i] + c->nblocks;
+    t.tiles_x[i] = (c->g.nx + lbmk::TX - 1) / lbmk::TX;
+    t.maps[i] = c->d_maps + c->cur;
+    t.status[i] = c->status;
     if (c->p.lattices != 7u) all = false;
   }
   return all;
@@ -1803,8 +1839,14 @@ cudaError_t batch_launches(lbm_batch* b, int64_t nsteps, cudaStream_t s,
     const bool diag = c0->p.diag_every > 0 && (c0->step % c0->p.diag_every) == 0;
     for (int first = 0; first < n; first += lbmk::BATCH_MAX_GRIDS) {
       const int count = std::min(n - first, lbmk::BATCH_MAX_GRIDS);
-      const bool all = fill_table<R>(b, first, count, t);
       cudaError_t e;
+      if (sizeof(R) == 4 && b->tile) {
+        const bool all = fill_tile_table(b, first, count, *b->ttab);
+        e = lbmk::launch_tile_batch_f32(*b->ttab, diag, all, s);
+        if (e != cudaSuccess) return e;
+        continue;
+      }
+      const bool all = fill_table<R>(b, first, count, t);
       if (sizeof(R) == 4)
         e = lbmk::launch_batch_f32(*(const lbmk::BatchTable<float>*)(const void*)&t, diag, all, s);
       else
@@ -1937,6 +1979,17 @@ int lbm_batch_create(lbm_ctx* const* ctxs, int count, lbm_batch** out) {
   if (!b) return LBM_ERR_OOM;
   b->ctx.assign(ctxs, ctxs + count);
   b->precision = ctxs[0]->p.precision;
+  b->tile = b->precision == LBM_FP32;
+  for (int i = 0; i < count; i++) b->tile = b->tile && ctxs[i]->tile_ok && ctxs[i]->d_maps;
+  if (const char* k = std::getenv("LBM_BATCH_KERNEL"))
+    if (std::strcmp(k, "fused") == 0) b->tile = false;
+  if (b->tile) {
+    b->ttab = new (std::nothrow) lbmk::TileBatch<float>();
+    if (!b->ttab) {
+      delete b;
+      return LBM_ERR_OOM;
+    }
+  }
   *out = b;
   return LBM_OK;
 }
@@ -1961,6 +2014,7 @@ void lbm_batch_destroy(lbm_batch* b) {
   if (!b) return;
   if (b->graph) cudaGraphExecDestroy(b->graph);
   if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
+  delete b->ttab;
   delete b;
 }
 

@@ -54,8 +54,11 @@ static cudaError_t prepare_tile_nst() {
   return e;
 }
 
+static cudaError_t prepare_tile1();
+
 cudaError_t prepare_tile_f16s() {
   cudaError_t e = prepare_tile_nst<1>();
+  if (e == cudaSuccess) e = prepare_tile1();
   if (e == cudaSuccess) e = prepare_tile_nst<2>();
   return e;
 }
@@ -73,8 +76,36 @@ static void tile_launch(const TileArgs<__half>& t, bool diag, int grid, cudaStre
   }
 }
 
+template <bool DIAG, int LATC>
+static cudaError_t prepare_tile1_one() {
+  return cudaFuncSetAttribute(lbm_tile1_kernel<__half, DIAG, LATC>,
+                              cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)tile_smem_bytes<__half>(1));
+}
+
+static cudaError_t prepare_tile1() {
+  cudaError_t e = prepare_tile1_one<false, 7>();
+  if (e == cudaSuccess) e = prepare_tile1_one<true, 7>();
+  if (e == cudaSuccess) e = prepare_tile1_one<false, 0>();
+  if (e == cudaSuccess) e = prepare_tile1_one<true, 0>();
+  return e;
+}
+
+// One CTA per tile, one stage: the kernel without the persistent loop.
+static void tile1_launch(const TileArgs<__half>& t, bool diag, cudaStream_t s) {
+  const size_t smem = tile_smem_bytes<__half>(1);
+  if (t.a.g.lattices == (LAT_FLOW | LAT_PHASE | LAT_HEAT)) {
+    if (diag) lbm_tile1_kernel<__half, true, 7><<<t.ntiles, block_dims(), smem, s>>>(t);
+    else lbm_tile1_kernel<__half, false, 7><<<t.ntiles, block_dims(), smem, s>>>(t);
+  } else {
+    if (diag) lbm_tile1_kernel<__half, true, 0><<<t.ntiles, block_dims(), smem, s>>>(t);
+    else lbm_tile1_kernel<__half, false, 0><<<t.ntiles, block_dims(), smem, s>>>(t);
+  }
+}
+
 cudaError_t launch_tile_f16s(const TileArgs<__half>& t, bool diag, int stages, int grid, cudaStream_t s) {
   if (stages == 2) tile_launch<2>(t, diag, grid, s);
+  else if (grid >= t.ntiles) tile1_launch(t, diag, s);
   else tile_launch<1>(t, diag, grid, s);
   return cudaGetLastError();
 }

@@ -67,9 +67,23 @@ static cudaError_t prepare_tile_nst() {
   return e;
 }
 
+template <bool DIAG, int LATC>
+static cudaError_t prepare_tile_batch_one() {
+  return cudaFuncSetAttribute(lbm_tile_batch_kernel<float, DIAG, LATC>,
+                              cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)tile_smem_bytes<float>(1));
+}
+
+static cudaError_t prepare_tile1();
+
 cudaError_t prepare_tile_f32() {
   cudaError_t e = prepare_tile_nst<1>();
+  if (e == cudaSuccess) e = prepare_tile1();
   if (e == cudaSuccess) e = prepare_tile_nst<2>();
+  if (e == cudaSuccess) e = prepare_tile_batch_one<false, 7>();
+  if (e == cudaSuccess) e = prepare_tile_batch_one<true, 7>();
+  if (e == cudaSuccess) e = prepare_tile_batch_one<false, 0>();
+  if (e == cudaSuccess) e = prepare_tile_batch_one<true, 0>();
   return e;
 }
 
@@ -86,9 +100,50 @@ static void tile_launch(const TileArgs<float>& t, bool diag, int grid, cudaStrea
   }
 }
 
+template <bool DIAG, int LATC>
+static cudaError_t prepare_tile1_one() {
+  return cudaFuncSetAttribute(lbm_tile1_kernel<float, DIAG, LATC>,
+                              cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)tile_smem_bytes<float>(1));
+}
+
+static cudaError_t prepare_tile1() {
+  cudaError_t e = prepare_tile1_one<false, 7>();
+  if (e == cudaSuccess) e = prepare_tile1_one<true, 7>();
+  if (e == cudaSuccess) e = prepare_tile1_one<false, 0>();
+  if (e == cudaSuccess) e = prepare_tile1_one<true, 0>();
+  return e;
+}
+
+// One CTA per tile, one stage: the kernel without the persistent loop.
+static void tile1_launch(const TileArgs<float>& t, bool diag, cudaStream_t s) {
+  const size_t smem = tile_smem_bytes<float>(1);
+  if (t.a.g.lattices == (LAT_FLOW | LAT_PHASE | LAT_HEAT)) {
+    if (diag) lbm_tile1_kernel<float, true, 7><<<t.ntiles, block_dims(), smem, s>>>(t);
+    else lbm_tile1_kernel<float, false, 7><<<t.ntiles, block_dims(), smem, s>>>(t);
+  } else {
+    if (diag) lbm_tile1_kernel<float, true, 0><<<t.ntiles, block_dims(), smem, s>>>(t);
+    else lbm_tile1_kernel<float, false, 0><<<t.ntiles, block_dims(), smem, s>>>(t);
+  }
+}
+
 cudaError_t launch_tile_f32(const TileArgs<float>& t, bool diag, int stages, int grid, cudaStream_t s) {
   if (stages == 2) tile_launch<2>(t, diag, grid, s);
+  else if (grid >= t.ntiles) tile1_launch(t, diag, s);
   else tile_launch<1>(t, diag, grid, s);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_tile_batch_f32(const TileBatch<float>& b, bool diag, bool all, cudaStream_t s) {
+  const size_t smem = tile_smem_bytes<float>(1);
+  const int ctas = b.tile_base[b.ngrids];
+  if (all) {
+    if (diag) lbm_tile_batch_kernel<float, true, 7><<<ctas, block_dims(), smem, s>>>(b);
+    else lbm_tile_batch_kernel<float, false, 7><<<ctas, block_dims(), smem, s>>>(b);
+  } else {
+    if (diag) lbm_tile_batch_kernel<float, true, 0><<<ctas, block_dims(), smem, s>>>(b);
+    else lbm_tile_batch_kernel<float, false, 0><<<ctas, block_dims(), smem, s>>>(b);
+  }
   return cudaGetLastError();
 }
 

@@ -29,12 +29,16 @@ cudaError_t launch_init_f32(const InitArgs<float>& a, cudaStream_t s);
 // shared-memory stages on `grid` CTAs (persistent when grid < tiles);
 // prepare_tile_* sets its shared-memory sizes once (call before the first
 // launch, outside stream capture).
-cudaError_t prepare_tile_f32();
+cudaError_t prepare_tile_f32();  // also the batched tile kernel
 cudaError_t prepare_tile_f16s();
 cudaError_t launch_tile_f32(const TileArgs<float>& t, bool diag, int stages, int grid,
                             cudaStream_t s);
 cudaError_t launch_tile_f16s(const TileArgs<__half>& t, bool diag, int stages, int grid,
                              cudaStream_t s);
+// Up to BATCH_MAX_GRIDS FP32 grids in one launch of the one-stage tile
+// kernel, one CTA per 32 x 8 tile.
+cudaError_t launch_tile_batch_f32(const TileBatch<float>& b, bool diag, bool all,
+                                  cudaStream_t s);
 // FP16 population storage, FP32 arithmetic.
 cudaError_t launch_step_f16s(const Args<float, __half>& a, int mode, bool diag, cudaStream_t s,
                              int ty = TY);

@@ -53,6 +53,28 @@ struct TileArgs {
   unsigned extra_tx; // test hook: bytes expected beyond the copies (0)
 };
 
+// The five tensor maps of one grid and buffer parity, as the batched tile
+// kernel reads them from global memory (written by the host before any
+// launch that uses them; 64-byte aligned like every CUtensorMap).
+struct TileMaps {
+  CUtensorMap f, gh, lag, phi0, mask;
+};
+
+// Up to BATCH_MAX_GRIDS float grids in one launch of the TMA-staged tile
+// kernel, one CTA per 32 x 8 tile of the concatenated tile list: the step
+// arguments travel in parameter space as for lbm_batch_kernel, each grid's
+// tensor maps (for its current parity) stay in global memory.
+template <typename S>
+struct TileBatch {
+  int ngrids;
+  int tile_base[BATCH_MAX_GRIDS + 1];  // first tile of each grid; [ngrids] = total
+  int tiles_x[BATCH_MAX_GRIDS];
+  const TileMaps* maps[BATCH_MAX_GRIDS];
+  unsigned* status[BATCH_MAX_GRIDS];   // per grid: a copy did not arrive in time
+  unsigned extra_tx;                   // test hook: bytes expected beyond the copies (0)
+  Args<float, S> args[BATCH_MAX_GRIDS];
+};
+
 // Shared memory of a CTA with NST stages (plus room to align them).
 template <typename S>
 constexpr size_t tile_smem_bytes(int nst) {
@@ -70,18 +92,27 @@ constexpr int tile_min_blocks() {
 __device__ __forceinline__ float lds(const float* p) { return *p; }
 __device__ __forceinline__ float lds(const __half* p) { return __half2float(*p); }
 
-// One tile's inputs into stage st, completing on bar.
+// The inputs of the tile at (x0, y0) into stage st, completing on bar.
+template <typename S>
+__device__ __forceinline__ void tile_issue_maps(const CUtensorMap* mf, const CUtensorMap* mgh,
+                                                const CUtensorMap* mlag, const CUtensorMap* mphi0,
+                                                const CUtensorMap* mmask, unsigned extra_tx,
+                                                TileStage<S>& st, uint64_t* bar, int x0, int y0) {
+  using St = TileStage<S>;
+  mbar_arrive_expect_tx(bar, St::kBytes + extra_tx);
+  tma_load_3d(&st.f[0][0][0], mf, x0, y0, 0, bar);
+  tma_load_3d(&st.gh[0][0][0], mgh, x0 - St::XG, y0 - 1, 9, bar);
+  tma_load_3d(&st.lag[0][0][0], mlag, x0 - St::XL, y0 - 1, 0, bar);
+  tma_load_3d(&st.phi0[0][0], mphi0, x0 - St::XL, y0 - 1, 0, bar);
+  tma_load_3d(&st.mask[0][0], mmask, x0 - St::XM, y0 - 1, 0, bar);
+}
+
+// Tile t of a single grid's launch into stage st, completing on bar.
 template <typename S>
 __device__ __forceinline__ void tile_issue(const TileArgs<S>& ta, TileStage<S>& st,
                                            uint64_t* bar, int t) {
-  using St = TileStage<S>;
-  const int x0 = (t % ta.tiles_x) * TX, y0 = (t / ta.tiles_x) * TY;
-  mbar_arrive_expect_tx(bar, St::kBytes + ta.extra_tx);
-  tma_load_3d(&st.f[0][0][0], &ta.map_f, x0, y0, 0, bar);
-  tma_load_3d(&st.gh[0][0][0], &ta.map_gh, x0 - St::XG, y0 - 1, 9, bar);
-  tma_load_3d(&st.lag[0][0][0], &ta.map_lag, x0 - St::XL, y0 - 1, 0, bar);
-  tma_load_3d(&st.phi0[0][0], &ta.map_phi0, x0 - St::XL, y0 - 1, 0, bar);
-  tma_load_3d(&st.mask[0][0], &ta.map_mask, x0 - St::XM, y0 - 1, 0, bar);
+  tile_issue_maps(&ta.map_f, &ta.map_gh, &ta.map_lag, &ta.map_phi0, &ta.map_mask, ta.extra_tx,
+                  st, bar, (t % ta.tiles_x) * TX, (t / ta.tiles_x) * TY);
 }
 
 // Ring cells (and cells of a ragged tile) outside the grid: the periodic
@@ -352,6 +383,73 @@ __global__ void __launch_bounds__(NT, tile_min_blocks<NST>())
       mbar_wait(&bar[0], k & 1);
     }
   }
+}
+
+// One tile per CTA, one stage, no loop over tiles (kept apart from the
+// persistent loop above, whose bookkeeping costs the registers this form
+// needs): stage the tile at (bx, by) with the given maps, wait (bounded),
+// step it.  On a timeout the grid's status word is set and the CTA waits
+// (bounded) for the late copy before it leaves.
+template <typename S, bool DIAG, int LATC>
+__device__ __forceinline__ void tile_once(const Args<float, S>& a, const CUtensorMap* mf,
+                                          const CUtensorMap* mgh, const CUtensorMap* mlag,
+                                          const CUtensorMap* mphi0, const CUtensorMap* mmask,
+                                          unsigned extra_tx, unsigned* status, int bx, int by,
+                                          int b, int nb) {
+  using St = TileStage<S>;
+  extern __shared__ unsigned char tile_smem[];
+  St* stage = reinterpret_cast<St*>(tile_smem + ((128u - (smem_u32(tile_smem) & 127u)) & 127u));
+  __shared__ __align__(8) uint64_t bar;
+  __shared__ float s_phi[HN], s_fs[HN], s_rho[HN], s_T[HN];
+  __shared__ float s_red[NT / 32][NDIAG];
+  const int tid = threadIdx.y * TX + threadIdx.x;
+  if (tid == 0) {
+    mbar_init(&bar, 1);
+    fence_barrier_init();
+    tile_issue_maps(mf, mgh, mlag, mphi0, mmask, extra_tx, stage[0], &bar, bx * TX, by * TY);
+  }
+  __syncthreads();
+  const bool ok = mbar_wait(&bar, 0);
+  if (__syncthreads_or(!ok)) {
+    if (tid == 0) {
+      atomicExch(status, 1u);
+      mbar_wait(&bar, 0);  // the late copy must land before the CTA leaves
+    }
+    return;
+  }
+  tile_fix_edges(a, stage[0], bx * TX, by * TY, tid);
+  __syncthreads();
+  tile_step<S, DIAG, LATC>(a, stage[0], bx, by, b, nb, s_phi, s_fs, s_rho, s_T, s_red);
+}
+
+// One grid, one CTA per tile, one stage (kernel form 1).
+template <typename S, bool DIAG, int LATC>
+__global__ void __launch_bounds__(NT, tile_min_blocks<1>())
+    lbm_tile1_kernel(const __grid_constant__ TileArgs<S> ta) {
+  const int t = blockIdx.x;
+  tile_once<S, DIAG, LATC>(ta.a, &ta.map_f, &ta.map_gh, &ta.map_lag, &ta.map_phi0, &ta.map_mask,
+                           ta.extra_tx, ta.status, t % ta.tiles_x, t / ta.tiles_x, t, ta.ntiles);
+}
+
+// Many float grids in one launch of the one-stage TMA-staged step: CTA t
+// takes tile t of the concatenated tile list (its grid by bisection over the
+// prefix sums, as lbm_batch_kernel) and stages it with that grid's tensor
+// maps from global memory.
+template <typename S, bool DIAG, int LATC>
+__global__ void __launch_bounds__(NT, tile_min_blocks<1>())
+    lbm_tile_batch_kernel(const __grid_constant__ TileBatch<S> B) {
+  const int t = blockIdx.x;
+  int lo = 0, hi = B.ngrids;  // tile_base[lo] <= t < tile_base[hi]
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (B.tile_base[mid] <= t) lo = mid;
+    else hi = mid;
+  }
+  const int local = t - B.tile_base[lo];
+  const TileMaps* m = B.maps[lo];
+  tile_once<S, DIAG, LATC>(B.args[lo], &m->f, &m->gh, &m->lag, &m->phi0, &m->mask, B.extra_tx,
+                           B.status[lo], local % B.tiles_x[lo], local / B.tiles_x[lo], local,
+                           B.tile_base[lo + 1] - B.tile_base[lo]);
 }
 
 }  // namespace lbmk

@@ -78,3 +78,42 @@ def test_tile_wait_timeout_is_reported(prec, tile, monkeypatch):
         assert np.array_equal(a[k], b[k]), k
     s.close()
     ref.close()
+
+
+def test_batched_tile_wait_timeout_is_reported():
+    """The batched TMA-staged kernel (FP32 batches) waits for each tile's
+    copies with the same bound; with the test hook every wait runs out (no
+    fault, nothing left in flight), each context of the batch reports
+    LBM_ERR_TIMEOUT on its next read, and the batch steps correctly again
+    once the geometry is set anew."""
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2510_18688_gb300 import build, lbm
+    build.build()
+    lbm.load()
+    wls = [W.random_state(70, 45, seed=5), W.random_state(41, 23, seed=6)]
+    ss = [lbm.Solver(c, precision="fp32").set_geometry(a) for c, a in wls]
+    b = lbm.Batch(ss)
+    lbm.lbm_debug_tile_timeout(True)
+    try:
+        b.step(1)
+        for s in ss:
+            with pytest.raises(lbm.LbmError) as e:
+                s.fields()
+            assert e.value.status == -7  # LBM_ERR_TIMEOUT
+    finally:
+        lbm.lbm_debug_tile_timeout(False)
+    for s, (c, a) in zip(ss, wls):
+        s.set_geometry(a)
+    b.step(5)
+    for s, (c, a) in zip(ss, wls):
+        ref = lbm.Solver(c, precision="fp32").set_geometry(a)
+        lbm.Batch([ref]).step(5)
+        x, y = s.fields(), ref.fields()
+        for k in x:
+            assert np.array_equal(x[k], y[k]), k
+        ref.close()
+    b.close()
+    for s in ss:
+        s.close()

@@ -278,14 +278,18 @@ def test_errors_are_status_codes(env):
         lbm.lbm_step(s.ctx, -1)
 
 
-@pytest.mark.parametrize("prec", ["fp64", "fp32"])
-def test_batched_grids_match_single_grids_and_oracle(env, prec):
+@pytest.mark.parametrize("prec,kernel", [("fp64", "fused"), ("fp32", "tile"), ("fp32", "fused")])
+def test_batched_grids_match_single_grids_and_oracle(env, prec, kernel, monkeypatch):
     """Grids of uneven sizes and parameters advanced by one launch per step
     give, grid by grid, the results of lbm_step on each grid alone (bit for
     bit in FP64; within a few FP32 roundings in FP32, where the compiler
-    contracts the two kernels' copies of the step differently), and the
-    oracle's within the parity bar."""
+    contracts the kernels' copies of the step differently), and the oracle's
+    within the parity bar.  FP32 batches run as the batched TMA-staged tile
+    kernel by default and as the one-CTA-per-tile kernel from global loads
+    with LBM_BATCH_KERNEL=fused; both are covered."""
     O, lbm = env
+    if kernel == "fused":
+        monkeypatch.setenv("LBM_BATCH_KERNEL", "fused")
     wls = [W.random_state(45, 19, seed=0), W.random_state(96, 24, seed=3),
            W.random_state(37, 41, seed=2), W.random_state(70, 17, seed=5),
            W.cylinder_droplet(64, seed=1)]
@@ -317,6 +321,29 @@ def test_batched_grids_match_single_grids_and_oracle(env, prec):
         ref = O.from_workload((cfg, arr)).step(steps).fields()
         _compare(fb, ref, prec)
     b.close()
+
+
+def test_fp32_tile_batch_of_many_grids_parities_and_lattice_sets(env):
+    """The batched TMA-staged kernel over 70 small FP32 grids (two launches
+    per step), with mixed lattice sets, and with one grid stepped on its own
+    between batch steps (its tensor maps then belong to the other buffer
+    parity): sampled grids against the oracle at the parity bar."""
+    O, lbm = env
+    wls = [W.random_state(20 + (k % 7) * 5, 10 + (k % 5) * 4, seed=200 + k,
+                          lattices=(7, 5, 2)[k % 3] if k % 4 == 0 else 7) for k in range(70)]
+    ss = [lbm.Solver(c, precision="fp32").set_geometry(a) for c, a in wls]
+    b = lbm.Batch(ss).step(6)
+    ss[3].step(1)
+    ss[66].step(1)
+    b.step(9)
+    for k in (0, 3, 4, 8, 65, 66, 69):
+        cfg, arr = wls[k]
+        assert ss[k].steps_done == (16 if k in (3, 66) else 15)
+        ref = O.from_workload((cfg, arr)).step(ss[k].steps_done).fields()
+        _compare(ss[k].fields(), ref, "fp32")
+    b.close()
+    for s in ss:
+        s.close()
 
 
 def test_batch_with_mixed_lattice_sets(env):
