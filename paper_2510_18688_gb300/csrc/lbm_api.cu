@@ -63,7 +63,7 @@ struct lbm_ctx {
   int tile_stages;       // shared-memory stages of the tile kernel (1 or 2)
   int tile_grid;         // its CTAs (persistent when fewer than the tiles)
   int sms;               // multiprocessors of the context's device
-  CUtensorMap tm_f[2], tm_gh[2], tm_lag[2], tm_phi0, tm_mask;  // per A/B buffer
+  CUtensorMap tm_f[2], tm_gh[2], tm_lag[2], tm_phi0;  // per A/B buffer
   lbmk::TileMaps* d_maps;  // device copy of the maps by parity (FP32: for batches)
   unsigned* status;      // device word: a tile's copies did not arrive in time
   int cur;
@@ -191,8 +191,6 @@ bool make_tile_maps(lbm_ctx* c, CUtensorMapDataType dt) {
   }
   ok = ok && encode_map(&c->tm_phi0, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, sizeof(float), c->phi0, c->g,
                         1, St::WL, lbmk::TY + 2, 1);
-  ok = ok && encode_map(&c->tm_mask, CU_TENSOR_MAP_DATA_TYPE_UINT8, 1, c->mask, c->g, 1, St::WM,
-                        lbmk::TY + 2, 1);
   return ok;
 }
 
@@ -205,7 +203,6 @@ lbmk::TileArgs<S> tile_args(lbm_ctx* c, const lbmk::Args<float, S>& a) {
   t.map_gh = c->tm_gh[c->cur];
   t.map_lag = c->tm_lag[c->cur];
   t.map_phi0 = c->tm_phi0;
-  t.map_mask = c->tm_mask;
   t.tiles_x = (c->g.nx + lbmk::TX - 1) / lbmk::TX;
   t.ntiles = c->nblocks;
   t.status = c->status;
@@ -532,7 +529,6 @@ int lbm_create(const lbm_params* params, lbm_ctx** out) {
         hm[b].gh = c->tm_gh[b];
         hm[b].lag = c->tm_lag[b];
         hm[b].phi0 = c->tm_phi0;
-        hm[b].mask = c->tm_mask;
       }
       e = dev_malloc((void**)&c->d_maps, sizeof(hm));
       if (e == cudaSuccess) e = cudaMemcpy(c->d_maps, hm, sizeof(hm), cudaMemcpyHostToDevice);

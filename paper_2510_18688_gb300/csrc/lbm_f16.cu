@@ -78,9 +78,15 @@ static void tile_launch(const TileArgs<__half>& t, bool diag, int grid, cudaStre
 
 template <bool DIAG, int LATC>
 static cudaError_t prepare_tile1_one() {
-  return cudaFuncSetAttribute(lbm_tile1_kernel<__half, DIAG, LATC>,
-                              cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)tile_smem_bytes<__half>(1));
+  cudaError_t e = cudaFuncSetAttribute(lbm_tile1_kernel<__half, DIAG, LATC>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)tile_smem_bytes<__half>(1));
+  // all of the unified L1/shared storage as shared memory: four CTAs per SM
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(lbm_tile1_kernel<__half, DIAG, LATC>,
+                             cudaFuncAttributePreferredSharedMemoryCarveout,
+                             cudaSharedmemCarveoutMaxShared);
+  return e;
 }
 
 static cudaError_t prepare_tile1() {

@@ -69,9 +69,14 @@ static cudaError_t prepare_tile_nst() {
 
 template <bool DIAG, int LATC>
 static cudaError_t prepare_tile_batch_one() {
-  return cudaFuncSetAttribute(lbm_tile_batch_kernel<float, DIAG, LATC>,
-                              cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)tile_smem_bytes<float>(1));
+  cudaError_t e = cudaFuncSetAttribute(lbm_tile_batch_kernel<float, DIAG, LATC>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)tile_smem_bytes<float>(1));
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(lbm_tile_batch_kernel<float, DIAG, LATC>,
+                             cudaFuncAttributePreferredSharedMemoryCarveout,
+                             cudaSharedmemCarveoutMaxShared);
+  return e;
 }
 
 static cudaError_t prepare_tile1();
@@ -102,9 +107,15 @@ static void tile_launch(const TileArgs<float>& t, bool diag, int grid, cudaStrea
 
 template <bool DIAG, int LATC>
 static cudaError_t prepare_tile1_one() {
-  return cudaFuncSetAttribute(lbm_tile1_kernel<float, DIAG, LATC>,
-                              cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)tile_smem_bytes<float>(1));
+  cudaError_t e = cudaFuncSetAttribute(lbm_tile1_kernel<float, DIAG, LATC>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)tile_smem_bytes<float>(1));
+  // all of the unified L1/shared storage as shared memory: four CTAs per SM
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(lbm_tile1_kernel<float, DIAG, LATC>,
+                             cudaFuncAttributePreferredSharedMemoryCarveout,
+                             cudaSharedmemCarveoutMaxShared);
+  return e;
 }
 
 static cudaError_t prepare_tile1() {

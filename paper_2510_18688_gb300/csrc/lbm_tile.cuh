@@ -11,7 +11,11 @@
 //   f   own flow populations                  box 32 x 8 x 9 planes
 //   gh  phase and enthalpy populations, ring  box (32 + 2 XG) x 10 x 18
 //   lag the 7 lag planes, ring                box 40 x 10 x 7
-//   phi0, mask                                box 40 x 10, 64 x 10
+//   phi0                                      box 40 x 10
+//
+// (the cold mask, one byte per node and read only where the grid has one,
+// comes with plain loads: its box would cost the shared memory that keeps
+// the one-stage kernel at four CTAs per SM)
 //
 // The halo boxes start 16 bytes' worth of columns left of the tile (a TMA
 // box must start on a 16-byte boundary); only the one-node ring is used.
@@ -33,21 +37,19 @@ struct alignas(128) TileStage {
   static constexpr int XG = 16 / (int)sizeof(S);  // ring offset of the population box
   static constexpr int WG = TX + 2 * XG;          // its width
   static constexpr int XL = 4, WL = TX + 2 * XL;  // float lag and phi0 boxes
-  static constexpr int XM = 16, WM = TX + 2 * XM; // byte mask box
   alignas(128) S f[9][TY][TX];
   alignas(128) S gh[18][TY + 2][WG];
   alignas(128) float lag[NLAG + 1][TY + 2][WL];
   alignas(128) float phi0[TY + 2][WL];
-  alignas(128) uint8_t mask[TY + 2][WM];
   static constexpr uint32_t kBytes =
       (uint32_t)(sizeof(S) * (9 * TY * TX + 18 * (TY + 2) * WG) +
-                 sizeof(float) * ((NLAG + 2) * (TY + 2) * WL) + (TY + 2) * WM);
+                 sizeof(float) * ((NLAG + 2) * (TY + 2) * WL));
 };
 
 template <typename S>
 struct TileArgs {
   Args<float, S> a;
-  CUtensorMap map_f, map_gh, map_lag, map_phi0, map_mask;
+  CUtensorMap map_f, map_gh, map_lag, map_phi0;
   int tiles_x, ntiles;
   unsigned* status;  // set to 1 when a copy did not arrive in time
   unsigned extra_tx; // test hook: bytes expected beyond the copies (0)
@@ -57,7 +59,7 @@ struct TileArgs {
 // kernel reads them from global memory (written by the host before any
 // launch that uses them; 64-byte aligned like every CUtensorMap).
 struct TileMaps {
-  CUtensorMap f, gh, lag, phi0, mask;
+  CUtensorMap f, gh, lag, phi0;
 };
 
 // Up to BATCH_MAX_GRIDS float grids in one launch of the TMA-staged tile
@@ -96,7 +98,7 @@ __device__ __forceinline__ float lds(const __half* p) { return __half2float(*p);
 template <typename S>
 __device__ __forceinline__ void tile_issue_maps(const CUtensorMap* mf, const CUtensorMap* mgh,
                                                 const CUtensorMap* mlag, const CUtensorMap* mphi0,
-                                                const CUtensorMap* mmask, unsigned extra_tx,
+                                                unsigned extra_tx,
                                                 TileStage<S>& st, uint64_t* bar, int x0, int y0) {
   using St = TileStage<S>;
   mbar_arrive_expect_tx(bar, St::kBytes + extra_tx);
@@ -104,14 +106,13 @@ __device__ __forceinline__ void tile_issue_maps(const CUtensorMap* mf, const CUt
   tma_load_3d(&st.gh[0][0][0], mgh, x0 - St::XG, y0 - 1, 9, bar);
   tma_load_3d(&st.lag[0][0][0], mlag, x0 - St::XL, y0 - 1, 0, bar);
   tma_load_3d(&st.phi0[0][0], mphi0, x0 - St::XL, y0 - 1, 0, bar);
-  tma_load_3d(&st.mask[0][0], mmask, x0 - St::XM, y0 - 1, 0, bar);
 }
 
 // Tile t of a single grid's launch into stage st, completing on bar.
 template <typename S>
 __device__ __forceinline__ void tile_issue(const TileArgs<S>& ta, TileStage<S>& st,
                                            uint64_t* bar, int t) {
-  tile_issue_maps(&ta.map_f, &ta.map_gh, &ta.map_lag, &ta.map_phi0, &ta.map_mask, ta.extra_tx,
+  tile_issue_maps(&ta.map_f, &ta.map_gh, &ta.map_lag, &ta.map_phi0, ta.extra_tx,
                   st, bar, (t % ta.tiles_x) * TX, (t / ta.tiles_x) * TY);
 }
 
@@ -136,7 +137,6 @@ __device__ __forceinline__ void tile_fix_edges(const Args<float, S>& a, TileStag
 #pragma unroll
     for (int j = 0; j < NLAG + 1; j++) st.lag[j][hy][hx + St::XL - 1] = a.lin[j * P + m];
     st.phi0[hy][hx + St::XL - 1] = a.phi0[m];
-    st.mask[hy][hx + St::XM - 1] = a.mask[m];
   }
 }
 
@@ -171,7 +171,11 @@ __device__ __forceinline__ void tile_step(const Args<float, S>& a, const TileSta
   const R phi0 = st.phi0[ty + 1][tx + St::XL];
   const R flp = lag[LAG_FL * PL + cl], wp = lag[LAG_W * PL + cl];
   const R pp = lag[LAG_P * PL + cl], Qp = lag[LAG_Q * PL + cl];
-  const bool masked = (lat & LAT_HEAT) && g.has_mask && st.mask[ty + 1][tx + St::XM];
+  // the node's mask byte; a cell of a ragged tile beyond the grid takes its
+  // periodic image's or the edge node's, as tile_fix_edges takes its fields
+  const bool masked = (lat & LAT_HEAT) && g.has_mask &&
+                      a.mask[wrap_or_clamp(gy, g.ny, g.bc[2], g.bc[3]) * g.pitch +
+                             wrap_or_clamp(gx, g.nx, g.bc[0], g.bc[1])];
   R Tp = R(0), Cp = R(0);
   if (lat & LAT_HEAT) {
     Tp = lag[LAG_T * PL + cl];
@@ -226,7 +230,13 @@ __device__ __forceinline__ void tile_step(const Args<float, S>& a, const TileSta
     }
     if (lat & LAT_HEAT) {
       R v[9];
-      if (g.has_mask && st.mask[hy][hx - 1 + St::XM]) {
+      // the ring node's mask byte (its periodic image, or the edge node
+      // beyond a wall, as tile_fix_edges takes the other fields)
+      const bool mq =
+          g.has_mask &&
+          a.mask[wrap_or_clamp(y0 + hy - 1, g.ny, g.bc[2], g.bc[3]) * g.pitch +
+                 wrap_or_clamp(x0 + hx - 1, g.nx, g.bc[0], g.bc[1])];
+      if (mq) {
         cold_mask_h(c, wq, q0, v);
         v[0] -= ref_h0(c, wq, flq, Tq, Cq);
 #pragma unroll
@@ -393,7 +403,7 @@ __global__ void __launch_bounds__(NT, tile_min_blocks<NST>())
 template <typename S, bool DIAG, int LATC>
 __device__ __forceinline__ void tile_once(const Args<float, S>& a, const CUtensorMap* mf,
                                           const CUtensorMap* mgh, const CUtensorMap* mlag,
-                                          const CUtensorMap* mphi0, const CUtensorMap* mmask,
+                                          const CUtensorMap* mphi0,
                                           unsigned extra_tx, unsigned* status, int bx, int by,
                                           int b, int nb) {
   using St = TileStage<S>;
@@ -406,7 +416,7 @@ __device__ __forceinline__ void tile_once(const Args<float, S>& a, const CUtenso
   if (tid == 0) {
     mbar_init(&bar, 1);
     fence_barrier_init();
-    tile_issue_maps(mf, mgh, mlag, mphi0, mmask, extra_tx, stage[0], &bar, bx * TX, by * TY);
+    tile_issue_maps(mf, mgh, mlag, mphi0, extra_tx, stage[0], &bar, bx * TX, by * TY);
   }
   __syncthreads();
   const bool ok = mbar_wait(&bar, 0);
@@ -422,12 +432,16 @@ __device__ __forceinline__ void tile_once(const Args<float, S>& a, const CUtenso
   tile_step<S, DIAG, LATC>(a, stage[0], bx, by, b, nb, s_phi, s_fs, s_rho, s_T, s_red);
 }
 
+// CTAs per SM of the loop-free one-stage kernels: four (64 registers, 56 KB
+// of shared memory each).
+constexpr int kTileOnceBlocks = 4;
+
 // One grid, one CTA per tile, one stage (kernel form 1).
 template <typename S, bool DIAG, int LATC>
-__global__ void __launch_bounds__(NT, tile_min_blocks<1>())
+__global__ void __launch_bounds__(NT, kTileOnceBlocks)
     lbm_tile1_kernel(const __grid_constant__ TileArgs<S> ta) {
   const int t = blockIdx.x;
-  tile_once<S, DIAG, LATC>(ta.a, &ta.map_f, &ta.map_gh, &ta.map_lag, &ta.map_phi0, &ta.map_mask,
+  tile_once<S, DIAG, LATC>(ta.a, &ta.map_f, &ta.map_gh, &ta.map_lag, &ta.map_phi0,
                            ta.extra_tx, ta.status, t % ta.tiles_x, t / ta.tiles_x, t, ta.ntiles);
 }
 
@@ -436,7 +450,7 @@ __global__ void __launch_bounds__(NT, tile_min_blocks<1>())
 // prefix sums, as lbm_batch_kernel) and stages it with that grid's tensor
 // maps from global memory.
 template <typename S, bool DIAG, int LATC>
-__global__ void __launch_bounds__(NT, tile_min_blocks<1>())
+__global__ void __launch_bounds__(NT, kTileOnceBlocks)
     lbm_tile_batch_kernel(const __grid_constant__ TileBatch<S> B) {
   const int t = blockIdx.x;
   int lo = 0, hi = B.ngrids;  // tile_base[lo] <= t < tile_base[hi]
@@ -447,7 +461,7 @@ __global__ void __launch_bounds__(NT, tile_min_blocks<1>())
   }
   const int local = t - B.tile_base[lo];
   const TileMaps* m = B.maps[lo];
-  tile_once<S, DIAG, LATC>(B.args[lo], &m->f, &m->gh, &m->lag, &m->phi0, &m->mask, B.extra_tx,
+  tile_once<S, DIAG, LATC>(B.args[lo], &m->f, &m->gh, &m->lag, &m->phi0, B.extra_tx,
                            B.status[lo], local % B.tiles_x[lo], local / B.tiles_x[lo], local,
                            B.tile_base[lo + 1] - B.tile_base[lo]);
 }
