@@ -432,9 +432,12 @@ __device__ __forceinline__ void tile_once(const Args<float, S>& a, const CUtenso
   tile_step<S, DIAG, LATC>(a, stage[0], bx, by, b, nb, s_phi, s_fs, s_rho, s_T, s_red);
 }
 
-// CTAs per SM of the loop-free one-stage kernels: four (64 registers, 56 KB
-// of shared memory each).
+// CTAs per SM of the loop-free one-stage kernels: four for one grid (64
+// registers, 56 KB of shared memory each); three for the batched kernel,
+// whose grid lookup does not fit 64 registers without spills (at four it
+// measured 632 us per step of the 64-grid batch against 610 us at three).
 constexpr int kTileOnceBlocks = 4;
+constexpr int kTileBatchBlocks = 3;
 
 // One grid, one CTA per tile, one stage (kernel form 1).
 template <typename S, bool DIAG, int LATC>
@@ -450,7 +453,7 @@ __global__ void __launch_bounds__(NT, kTileOnceBlocks)
 // prefix sums, as lbm_batch_kernel) and stages it with that grid's tensor
 // maps from global memory.
 template <typename S, bool DIAG, int LATC>
-__global__ void __launch_bounds__(NT, kTileOnceBlocks)
+__global__ void __launch_bounds__(NT, kTileBatchBlocks)
     lbm_tile_batch_kernel(const __grid_constant__ TileBatch<S> B) {
   const int t = blockIdx.x;
   int lo = 0, hi = B.ngrids;  // tile_base[lo] <= t < tile_base[hi]
