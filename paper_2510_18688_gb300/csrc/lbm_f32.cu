@@ -69,14 +69,9 @@ static cudaError_t prepare_tile_nst() {
 
 template <bool DIAG, int LATC>
 static cudaError_t prepare_tile_batch_one() {
-  cudaError_t e = cudaFuncSetAttribute(lbm_tile_batch_kernel<float, DIAG, LATC>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)tile_smem_bytes<float>(1));
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(lbm_tile_batch_kernel<float, DIAG, LATC>,
-                             cudaFuncAttributePreferredSharedMemoryCarveout,
-                             cudaSharedmemCarveoutMaxShared);
-  return e;
+  return cudaFuncSetAttribute(lbm_tile_batch_kernel<float, DIAG, LATC>,
+                              cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)tile_smem_bytes<float>(1));
 }
 
 static cudaError_t prepare_tile1();

@@ -140,13 +140,39 @@ __device__ __forceinline__ void tile_fix_edges(const Args<float, S>& a, TileStag
   }
 }
 
-// The step for one staged tile (bx, by), tile index b of nb.  Every thread
+// The cold-mask bytes of this thread's own cell and (threads below RING) of
+// its ring cell for the tile at (x0, y0): 0 where the grid has no mask.
+// Cells beyond the grid take their periodic image's or the edge node's byte,
+// as tile_fix_edges takes their fields.  Loaded before the wait for the
+// tile's copies, so that their latency overlaps the copies'.
+struct TileMask {
+  uint8_t own, ring;
+};
+template <typename S>
+__device__ __forceinline__ TileMask tile_mask(const Args<float, S>& a, int x0, int y0, int tid) {
+  const Geom& g = a.g;
+  TileMask m{0, 0};
+  if (!g.has_mask) return m;
+  const int tx = tid % TX, ty = tid / TX;
+  m.own = a.mask[wrap_or_clamp(y0 + ty, g.ny, g.bc[2], g.bc[3]) * g.pitch +
+                 wrap_or_clamp(x0 + tx, g.nx, g.bc[0], g.bc[1])];
+  if (tid < RING) {
+    int hx, hy;
+    ring_pos(tid, hx, hy);
+    m.ring = a.mask[wrap_or_clamp(y0 + hy - 1, g.ny, g.bc[2], g.bc[3]) * g.pitch +
+                    wrap_or_clamp(x0 + hx - 1, g.nx, g.bc[0], g.bc[1])];
+  }
+  return m;
+}
+
+// The step for one staged tile (bx, by), tile index b of nb; mk: the
+// thread's mask bytes (tile_mask).  Every thread
 // of the CTA calls it; the caller synchronises before and after.
 template <typename S, bool DIAG, int LATC>
 __device__ __forceinline__ void tile_step(const Args<float, S>& a, const TileStage<S>& st,
                                           int bx, int by, int b, int nb, float* s_phi,
                                           float* s_fs, float* s_rho, float* s_T,
-                                          float (*s_red)[NDIAG]) {
+                                          float (*s_red)[NDIAG], TileMask mk) {
   using St = TileStage<S>;
   using R = float;
   const Geom& g = a.g;
@@ -171,11 +197,7 @@ __device__ __forceinline__ void tile_step(const Args<float, S>& a, const TileSta
   const R phi0 = st.phi0[ty + 1][tx + St::XL];
   const R flp = lag[LAG_FL * PL + cl], wp = lag[LAG_W * PL + cl];
   const R pp = lag[LAG_P * PL + cl], Qp = lag[LAG_Q * PL + cl];
-  // the node's mask byte; a cell of a ragged tile beyond the grid takes its
-  // periodic image's or the edge node's, as tile_fix_edges takes its fields
-  const bool masked = (lat & LAT_HEAT) && g.has_mask &&
-                      a.mask[wrap_or_clamp(gy, g.ny, g.bc[2], g.bc[3]) * g.pitch +
-                             wrap_or_clamp(gx, g.nx, g.bc[0], g.bc[1])];
+  const bool masked = (lat & LAT_HEAT) && mk.own;
   R Tp = R(0), Cp = R(0);
   if (lat & LAT_HEAT) {
     Tp = lag[LAG_T * PL + cl];
@@ -230,13 +252,7 @@ __device__ __forceinline__ void tile_step(const Args<float, S>& a, const TileSta
     }
     if (lat & LAT_HEAT) {
       R v[9];
-      // the ring node's mask byte (its periodic image, or the edge node
-      // beyond a wall, as tile_fix_edges takes the other fields)
-      const bool mq =
-          g.has_mask &&
-          a.mask[wrap_or_clamp(y0 + hy - 1, g.ny, g.bc[2], g.bc[3]) * g.pitch +
-                 wrap_or_clamp(x0 + hx - 1, g.nx, g.bc[0], g.bc[1])];
-      if (mq) {
+      if (mk.ring) {
         cold_mask_h(c, wq, q0, v);
         v[0] -= ref_h0(c, wq, flq, Tq, Cq);
 #pragma unroll
@@ -365,16 +381,17 @@ __global__ void __launch_bounds__(NT, tile_min_blocks<NST>())
       fence_proxy_async();
       tile_issue(ta, stage[s ^ 1], &bar[s ^ 1], tn);
     }
+    const int bx = t % ta.tiles_x, by = t / ta.tiles_x;
+    const TileMask mk = tile_mask(ta.a, bx * TX, by * TY, tid);
     const bool ok = mbar_wait(&bar[s], parity);
     if (__syncthreads_or(!ok)) {
       timed_out = true;
       break;
     }
-    const int bx = t % ta.tiles_x, by = t / ta.tiles_x;
     tile_fix_edges(ta.a, stage[s], bx * TX, by * TY, tid);
     __syncthreads();
     tile_step<S, DIAG, LATC>(ta.a, stage[s], bx, by, t, ta.ntiles, s_phi, s_fs, s_rho, s_T,
-                             s_red);
+                             s_red, mk);
     // this thread's reads (and edge writes) of stage s come before the TMA
     // writes that will refill it
     fence_proxy_async();
@@ -419,6 +436,7 @@ __device__ __forceinline__ void tile_once(const Args<float, S>& a, const CUtenso
     tile_issue_maps(mf, mgh, mlag, mphi0, extra_tx, stage[0], &bar, bx * TX, by * TY);
   }
   __syncthreads();
+  const TileMask mk = tile_mask(a, bx * TX, by * TY, tid);
   const bool ok = mbar_wait(&bar, 0);
   if (__syncthreads_or(!ok)) {
     if (tid == 0) {
@@ -429,7 +447,7 @@ __device__ __forceinline__ void tile_once(const Args<float, S>& a, const CUtenso
   }
   tile_fix_edges(a, stage[0], bx * TX, by * TY, tid);
   __syncthreads();
-  tile_step<S, DIAG, LATC>(a, stage[0], bx, by, b, nb, s_phi, s_fs, s_rho, s_T, s_red);
+  tile_step<S, DIAG, LATC>(a, stage[0], bx, by, b, nb, s_phi, s_fs, s_rho, s_T, s_red, mk);
 }
 
 // CTAs per SM of the loop-free one-stage kernels: four for one grid (64
