@@ -439,7 +439,9 @@ int lbm_adjoint_coupled(lbm_ctx* ctx, int64_t nsteps, int every, int observable,
  * LBM_FP16S, LBM_FP64).  Tangent
  * contexts 0.  Each variant runs steps_per_trial steps twice from the same
  * saved state (the first run warms up and captures; the second is timed
- * with CUDA events on `stream`).  The state, step counter and diagnostics
+ * with CUDA events on `stream`).  The fastest variant is kept, unless the
+ * context's current one is within 2 % of it (then the current one stays).
+ * The state, step counter and diagnostics
  * (including partial sums not yet read) are restored afterwards, so the
  * call does not advance the simulation.  out_us (12 doubles, may be NULL):
  * microseconds per step of each variant (-1 where not run); chosen (may be

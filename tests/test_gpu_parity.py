@@ -485,7 +485,11 @@ def test_autotune_keeps_the_state_and_picks_a_variant(env, prec):
     assert len(us) == 12
     assert all(us[v] > 0 for v in run)
     assert all(u == -1.0 for v, u in enumerate(us) if v not in run)
-    assert chosen in run and us[chosen] == min(us[v] for v in run)
+    # the fastest variant, or the starting one (form 0, period 32: variant 0)
+    # where that is within 2 % of the fastest
+    assert chosen in run
+    assert us[chosen] == min(us[v] for v in run) or (chosen == 0 and
+                                                      us[0] <= 1.02 * min(us[v] for v in run))
     s.step(40)
     if prec != "fp16s":
         _compare(s.fields(), O.from_workload((cfg, arr)).step(45).fields(), prec)
