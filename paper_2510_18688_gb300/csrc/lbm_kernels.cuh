@@ -335,6 +335,13 @@ __device__ __forceinline__ float ref_delta(float r_new, float r_old) {
   return __fsub_rn(r_new, r_old);
 }
 
+// Error-free sum (Knuth's TwoSum): s + e == x + y exactly, s = fl(x + y).
+__device__ __forceinline__ void two_sum(float x, float y, float& s, float& e) {
+  s = __fadd_rn(x, y);
+  const float bv = __fsub_rn(s, x);
+  e = __fadd_rn(__fsub_rn(x, __fsub_rn(s, bv)), __fsub_rn(y, bv));
+}
+
 template <typename R>
 __device__ __forceinline__ R sum_g(const R* v) {
   return (v[0] + v[1] + v[2] + v[3] + v[4] + v[5]) + (v[6] + v[7] + v[8]);

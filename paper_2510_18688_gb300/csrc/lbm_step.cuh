@@ -401,8 +401,12 @@ __device__ __forceinline__ void node_macros(const Geom& g, const Coef<R>& c, int
     const R mu = interp(fs, L.w, c.mu_s, c.mu_l, c.mu_g);
     R jx = (f[1] - f[3]) + (f[5] - f[6]) + (f[8] - f[7]);
     R jy = (f[2] - f[4]) + (f[5] + f[6]) - (f[7] + f[8]);
-    R snz = (f[1] + f[2] + f[3] + f[4]) + (f[5] + f[6] + f[7] + f[8]);
+    // opposite populations summed first: near equilibrium they differ mainly
+    // by the +-3 w_i rho c_i.u part, which then cancels exactly instead of
+    // after a rounding, and the small remainder keeps its precision
+    R snz = ((f[1] + f[3]) + (f[2] + f[4])) + ((f[5] + f[7]) + (f[6] + f[8]));
     R dps[WB ? 9 : 1];  // well-balanced storage: p_src(i) - pp, then p_src(i) - p
+    R dpx = R(0), dpy = R(0);  // the references' share of the momentum
     if constexpr (WB) {
       // add the moments of the references 3 w_i p_src(i), as differences
       // from the node's own lagged pressure pp (whose share, 3 (1 - w_0) pp
@@ -413,24 +417,79 @@ __device__ __forceinline__ void node_macros(const Geom& g, const Coef<R>& c, int
         dps[i] = (!inner && upstream_wall(g, gx, gy, i)) ? R(0)
                                                          : cp[-(qy(i) * sb + qx(i))] - pp;
       const R w1 = qw<R>(1), w5 = qw<R>(5);
-      jx += R(3) * (w1 * (dps[1] - dps[3]) + w5 * ((dps[5] - dps[6]) + (dps[8] - dps[7])));
-      jy += R(3) * (w1 * (dps[2] - dps[4]) + w5 * ((dps[5] + dps[6]) - (dps[7] + dps[8])));
-      snz += R(3) * (w1 * ((dps[1] + dps[2]) + (dps[3] + dps[4])) +
-                     w5 * ((dps[5] + dps[6]) + (dps[7] + dps[8])));
+      dpx = R(3) * (w1 * (dps[1] - dps[3]) + w5 * ((dps[5] - dps[6]) + (dps[8] - dps[7])));
+      dpy = R(3) * (w1 * (dps[2] - dps[4]) + w5 * ((dps[5] + dps[6]) - (dps[7] + dps[8])));
+      jx += dpx;
+      jy += dpy;
+      snz += R(3) * (w1 * ((dps[1] + dps[3]) + (dps[2] + dps[4])) +
+                     w5 * ((dps[5] + dps[7]) + (dps[6] + dps[8])));
     }
     // Eq. (17a,b) with the penalty force f = fs (u_s - u*), u_s = 0
     const R irho = qdiv(R(1), rho);
-    const R usx = (jx + R(0.5) * Fx) * irho, usy = (jy + R(0.5) * Fy) * irho;
-    const R fpx = -fs * usx, fpy = -fs * usy;
-    M.ux = usx + R(0.5) * fpx;
-    M.uy = usy + R(0.5) * fpy;
+    R fpx, fpy;
+    if constexpr (WB) {
+      // Float states: u = (1 - fs/2) (j + F/2) / rho rounded once.  The
+      // weakly damped acoustics of a long run (the closed gas column of the
+      // Stefan problem) carry the velocity's per-step rounding forward: with
+      // the momentum summed in plain float and divided through a rounded
+      // 1/rho the 50,000-step Stefan velocity is 2.5e-4 off the FP64
+      // oracle, with this 6.8e-5.  The momentum of the remainders is kept as
+      // hi + lo (TwoSum over the three pair differences), the quotient of
+      // the high part is corrected by its exact residual (FMA) plus the low
+      // part, all divided by rho.
+      float a1, e1, a2, e2, a3, e3, t, et, h, eh;
+      two_sum(f[1], -f[3], a1, e1);
+      two_sum(f[5], -f[6], a2, e2);
+      two_sum(f[8], -f[7], a3, e3);
+      two_sum(a1, a2, t, et);
+      two_sum(t, a3, h, eh);
+      const float lox = (((e1 + e2) + (e3 + et)) + eh) + dpx;
+      float b1, g1, b2, g2, b3, g3, ty, ety, hy, ehy;
+      two_sum(f[2], -f[4], b1, g1);
+      two_sum(f[5], f[6], b2, g2);
+      two_sum(-f[7], -f[8], b3, g3);
+      two_sum(b1, b2, ty, ety);
+      two_sum(ty, b3, hy, ehy);
+      const float loy = (((g1 + g2) + (g3 + ety)) + ehy) + dpy;
+      float sx, esx, sy, esy;
+      two_sum(h, 0.5f * Fx, sx, esx);
+      two_sum(hy, 0.5f * Fy, sy, esy);
+      const float qx = qdiv(sx, rho), qy = qdiv(sy, rho);
+      const float qxl = (fmaf(-qx, rho, sx) + (esx + lox)) * irho;
+      const float qyl = (fmaf(-qy, rho, sy) + (esy + loy)) * irho;
+      const float k = 1.f - 0.5f * fs;
+      M.ux = fmaf(qx, k, qxl * k);
+      M.uy = fmaf(qy, k, qyl * k);
+      fpx = -fs * (qx + qxl);
+      fpy = -fs * (qy + qyl);
+    } else {
+      const R usx = (jx + R(0.5) * Fx) * irho, usy = (jy + R(0.5) * Fy) * irho;
+      fpx = -fs * usx;
+      fpy = -fs * usy;
+      M.ux = usx + R(0.5) * fpx;
+      M.uy = usy + R(0.5) * fpy;
+    }
     M.uu = M.ux * M.ux + M.uy * M.uy;
     M.S = rho * mdot + M.ux * grx + M.uy * gry;
     // modified force (reading R-FT), lagged pressure (reading R-FP)
     M.Ftx = Fx - (gpx - grx * R(1.0 / 3.0));
     M.Fty = Fy - (gpy - gry * R(1.0 / 3.0));
     M.uFt = M.ux * M.Ftx + M.uy * M.Fty;
-    M.tauf = R(3) * mu * irho + R(0.5);
+    if constexpr (WB) {
+      // tau_f = 3 mu / rho + 1/2 rounded once (the collision's relaxation
+      // rate takes its rounding; with the plain two roundings the Stefan
+      // velocity above stays at 1.2e-4): mu / rho = q0 + qe (qe from the
+      // exact residual of q0, by FMA), then 3 (q0 + qe) + 1/2 with the
+      // errors of 3 q0 (FMA) and of the sum (TwoSum) added back once
+      const float q0 = qdiv(mu, rho);
+      const float qe = fmaf(-q0, rho, mu) * irho;
+      const float t1 = 3.f * q0, t1e = fmaf(3.f, q0, -t1);
+      float sm, se;
+      two_sum(t1, 0.5f, sm, se);
+      M.tauf = sm + (se + (t1e + 3.f * qe));
+    } else {
+      M.tauf = R(3) * mu * irho + R(0.5);
+    }
     M.Gx = Fx + rho * fpx;
     M.Gy = Fy + rho * fpy;
     // F_0 of Eq. (16)
