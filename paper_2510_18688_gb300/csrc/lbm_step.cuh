@@ -406,7 +406,6 @@ __device__ __forceinline__ void node_macros(const Geom& g, const Coef<R>& c, int
     // after a rounding, and the small remainder keeps its precision
     R snz = ((f[1] + f[3]) + (f[2] + f[4])) + ((f[5] + f[7]) + (f[6] + f[8]));
     R dps[WB ? 9 : 1];  // well-balanced storage: p_src(i) - pp, then p_src(i) - p
-    R dpx = R(0), dpy = R(0);  // the references' share of the momentum
     if constexpr (WB) {
       // add the moments of the references 3 w_i p_src(i), as differences
       // from the node's own lagged pressure pp (whose share, 3 (1 - w_0) pp
@@ -417,10 +416,8 @@ __device__ __forceinline__ void node_macros(const Geom& g, const Coef<R>& c, int
         dps[i] = (!inner && upstream_wall(g, gx, gy, i)) ? R(0)
                                                          : cp[-(qy(i) * sb + qx(i))] - pp;
       const R w1 = qw<R>(1), w5 = qw<R>(5);
-      dpx = R(3) * (w1 * (dps[1] - dps[3]) + w5 * ((dps[5] - dps[6]) + (dps[8] - dps[7])));
-      dpy = R(3) * (w1 * (dps[2] - dps[4]) + w5 * ((dps[5] + dps[6]) - (dps[7] + dps[8])));
-      jx += dpx;
-      jy += dpy;
+      jx += R(3) * (w1 * (dps[1] - dps[3]) + w5 * ((dps[5] - dps[6]) + (dps[8] - dps[7])));
+      jy += R(3) * (w1 * (dps[2] - dps[4]) + w5 * ((dps[5] + dps[6]) - (dps[7] + dps[8])));
       snz += R(3) * (w1 * ((dps[1] + dps[3]) + (dps[2] + dps[4])) +
                      w5 * ((dps[5] + dps[7]) + (dps[6] + dps[8])));
     }
@@ -431,32 +428,16 @@ __device__ __forceinline__ void node_macros(const Geom& g, const Coef<R>& c, int
       // Float states: u = (1 - fs/2) (j + F/2) / rho rounded once.  The
       // weakly damped acoustics of a long run (the closed gas column of the
       // Stefan problem) carry the velocity's per-step rounding forward: with
-      // the momentum summed in plain float and divided through a rounded
-      // 1/rho the 50,000-step Stefan velocity is 2.5e-4 off the FP64
-      // oracle, with this 6.8e-5.  The momentum of the remainders is kept as
-      // hi + lo (TwoSum over the three pair differences), the quotient of
-      // the high part is corrected by its exact residual (FMA) plus the low
-      // part, all divided by rho.
-      float a1, e1, a2, e2, a3, e3, t, et, h, eh;
-      two_sum(f[1], -f[3], a1, e1);
-      two_sum(f[5], -f[6], a2, e2);
-      two_sum(f[8], -f[7], a3, e3);
-      two_sum(a1, a2, t, et);
-      two_sum(t, a3, h, eh);
-      const float lox = (((e1 + e2) + (e3 + et)) + eh) + dpx;
-      float b1, g1, b2, g2, b3, g3, ty, ety, hy, ehy;
-      two_sum(f[2], -f[4], b1, g1);
-      two_sum(f[5], f[6], b2, g2);
-      two_sum(-f[7], -f[8], b3, g3);
-      two_sum(b1, b2, ty, ety);
-      two_sum(ty, b3, hy, ehy);
-      const float loy = (((g1 + g2) + (g3 + ety)) + ehy) + dpy;
+      // (j + F/2) multiplied by a rounded 1/rho the 50,000-step Stefan
+      // velocity is 2.5e-4 off the FP64 oracle, with this 7.4e-5.  j + F/2
+      // is kept as s + e (TwoSum), the quotient of s is corrected by its
+      // exact residual (FMA) plus e, divided by rho.
       float sx, esx, sy, esy;
-      two_sum(h, 0.5f * Fx, sx, esx);
-      two_sum(hy, 0.5f * Fy, sy, esy);
+      two_sum(jx, 0.5f * Fx, sx, esx);
+      two_sum(jy, 0.5f * Fy, sy, esy);
       const float qx = qdiv(sx, rho), qy = qdiv(sy, rho);
-      const float qxl = (fmaf(-qx, rho, sx) + (esx + lox)) * irho;
-      const float qyl = (fmaf(-qy, rho, sy) + (esy + loy)) * irho;
+      const float qxl = (fmaf(-qx, rho, sx) + esx) * irho;
+      const float qyl = (fmaf(-qy, rho, sy) + esy) * irho;
       const float k = 1.f - 0.5f * fs;
       M.ux = fmaf(qx, k, qxl * k);
       M.uy = fmaf(qy, k, qyl * k);
@@ -476,9 +457,10 @@ __device__ __forceinline__ void node_macros(const Geom& g, const Coef<R>& c, int
     M.Fty = Fy - (gpy - gry * R(1.0 / 3.0));
     M.uFt = M.ux * M.Ftx + M.uy * M.Fty;
     if constexpr (WB) {
-      // tau_f = 3 mu / rho + 1/2 rounded once (the collision's relaxation
-      // rate takes its rounding; with the plain two roundings the Stefan
-      // velocity above stays at 1.2e-4): mu / rho = q0 + qe (qe from the
+      // tau_f = 3 mu / rho + 1/2 rounded once (with the velocity above but
+      // tau_f from two roundings the Stefan velocity stays at 1.2e-4; the
+      // same tau_f alone, velocity as before, leaves it at 2.5e-4):
+      // mu / rho = q0 + qe (qe from the
       // exact residual of q0, by FMA), then 3 (q0 + qe) + 1/2 with the
       // errors of 3 q0 (FMA) and of the sum (TwoSum) added back once
       const float q0 = qdiv(mu, rho);
